@@ -1,0 +1,247 @@
+"""CPU oracle for the FMM of Dehnen (arXiv 1405.2255): TEST INFRASTRUCTURE.
+
+A plain serial FP64 C implementation (``fmm_oracle.c``) plus this ctypes
+wrapper.  Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may use it.  It shares no code with the GPU library and never
+calls it; the product path must not import this package.
+
+Parity status per function (the pins live in tests/test_oracle_*.py):
+  harmonics     pinned: Table 3 closed forms, Upsilon/Theta relation (App. A.3),
+                addition theorem (App. A.4) against 1/|r - x|.
+  P2M/M2M       pinned: M2M(P2M) equals P2M at the new centre (exact shift);
+                power bounds of eq. (14).
+  M2L/L2L/L2P   pinned: against direct summation (converges as p grows), strict
+                bound eq. (12), L2L exactness, L2P gradient vs finite differences.
+  MEB           pinned: brute force over support sets on small point sets.
+  walk / FMM    pinned: reduction to direct summation (eps -> 0), N <= leaf size,
+                whole-FMM error vs brute force, Plummer closed form, momentum.
+  direct sum    pinned: two-body and symmetric closed forms, Plummer closed form.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fmm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE FP64, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+class Params(C.Structure):
+    _fields_ = [("p", C.c_int), ("eps", C.c_double), ("mac", C.c_int), ("theta_crit", C.c_double),
+                ("leaf_size", C.c_int), ("p2p_c", C.c_double), ("scale_src", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("ncells", C.c_long), ("nleaves", C.c_long), ("n_m2l", C.c_long), ("n_p2p", C.c_long),
+                ("p2p_interactions", C.c_long), ("coincident", C.c_long), ("est_m2l", C.c_long),
+                ("est_p2p", C.c_long), ("depth", C.c_int)]
+
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_lp = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def _declare(L):
+    L.orc_upsilon_re.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, _dp]
+    L.orc_theta_re.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, _dp]
+    L.orc_p2m.argtypes = [C.c_int, C.c_long, _dp, _dp, _dp, _dp, _dp]
+    for f in (L.orc_m2m, L.orc_m2l, L.orc_l2l):
+        f.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_l2p.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.POINTER(C.c_double), _dp]
+    L.orc_power.argtypes = [C.c_int, _dp, _dp, _dp]
+    L.orc_direct.argtypes = [C.c_long, _dp, _dp, C.c_double, C.c_long, C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.c_void_p]
+    L.orc_direct.restype = C.c_long
+    L.orc_meb_points.argtypes = [C.c_int, _dp, _dp, C.POINTER(C.c_double)]
+    L.orc_meb_balls.argtypes = [C.c_int, _dp, _dp, _dp, C.POINTER(C.c_double)]
+    L.orc_fmm.argtypes = [C.c_long, _dp, _dp, C.c_double, C.POINTER(Params), C.c_void_p]
+    L.orc_fmm.restype = C.c_void_p
+    L.orc_run_free.argtypes = [C.c_void_p]
+    L.orc_run_outputs.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_run_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+    L.orc_run_ncells.argtypes = [C.c_void_p]
+    L.orc_run_ncells.restype = C.c_long
+    L.orc_run_cells.argtypes = [C.c_void_p, _lp, _dp]
+    L.orc_run_lists.argtypes = [C.c_void_p, _lp, _lp]
+    L.orc_run_perm.argtypes = [C.c_void_p, _lp]
+    L.orc_run_scale.argtypes = [C.c_void_p, _dp]
+
+
+def _c3(v):
+    return np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(3))
+
+
+def ncoef(p):
+    return (p + 1) * (p + 1)
+
+
+def idx(n, m):
+    """index of (n, m) in a full complex harmonic array"""
+    return n * n + n + m
+
+
+def upsilon(p, r):
+    re, im = np.zeros(ncoef(p)), np.zeros(ncoef(p))
+    lib().orc_upsilon_re(p, float(r[0]), float(r[1]), float(r[2]), re, im)
+    return re + 1j * im
+
+
+def theta(p, r):
+    re, im = np.zeros(ncoef(p)), np.zeros(ncoef(p))
+    lib().orc_theta_re(p, float(r[0]), float(r[1]), float(r[2]), re, im)
+    return re + 1j * im
+
+
+def _split(c):
+    c = np.asarray(c, dtype=np.complex128)
+    return np.ascontiguousarray(c.real), np.ascontiguousarray(c.imag)
+
+
+def p2m(p, x, mu, z):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    re, im = np.zeros(ncoef(p)), np.zeros(ncoef(p))
+    lib().orc_p2m(p, len(mu), x, np.ascontiguousarray(mu, dtype=np.float64), _c3(z), re, im)
+    return re + 1j * im
+
+
+def _shift(fn, p, X, a, b):
+    xr, xi = _split(X)
+    re, im = np.zeros(ncoef(p)), np.zeros(ncoef(p))
+    fn(p, xr, xi, _c3(a), _c3(b), re, im)
+    return re + 1j * im
+
+
+def m2m(p, M, z, zp):
+    return _shift(lib().orc_m2m, p, M, z, zp)
+
+
+def m2l(p, M, zA, sB):
+    return _shift(lib().orc_m2l, p, M, zA, sB)
+
+
+def l2l(p, F, s, sp):
+    return _shift(lib().orc_l2l, p, F, s, sp)
+
+
+def l2p(p, F, s, xb):
+    fr, fi = _split(F)
+    psi = C.c_double()
+    a = np.zeros(3)
+    lib().orc_l2p(p, fr, fi, _c3(s), _c3(xb), C.byref(psi), a)
+    return psi.value, a
+
+
+def power(p, M):
+    mr, mi = _split(M)
+    P = np.zeros(p + 1)
+    lib().orc_power(p, mr, mi, P)
+    return P
+
+
+def direct(x, mu, G=1.0, sinks=None):
+    """Direct FP64 sums of eqs. (1) and (6); returns psi, acc, f, coincident."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    n = len(mu)
+    if sinks is None:
+        ns, sp = n, None
+    else:
+        sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+        ns, sp = len(sinks), sinks.ctypes.data
+    psi, acc, f = np.zeros(max(ns, 1)), np.zeros((max(ns, 1), 3)), np.zeros(max(ns, 1))
+    coin = lib().orc_direct(n, x, mu, G, ns, sp, psi.ctypes.data, acc.ctypes.data, f.ctypes.data)
+    return psi[:ns], acc[:ns], f[:ns], coin
+
+
+def meb_points(pts):
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    c, r = np.zeros(3), C.c_double()
+    lib().orc_meb_points(len(pts), pts, c, C.byref(r))
+    return c, r.value
+
+
+def meb_balls(cen, rad):
+    cen = np.ascontiguousarray(cen, dtype=np.float64)
+    rad = np.ascontiguousarray(rad, dtype=np.float64)
+    c, r = np.zeros(3), C.c_double()
+    ok = lib().orc_meb_balls(len(rad), cen, rad, c, C.byref(r))
+    return (c, r.value) if ok else (None, None)
+
+
+MAC_A, MAC_F, MAC_THETA = 0, 1, 2
+
+
+@dataclass
+class Run:
+    psi: np.ndarray
+    acc: np.ndarray
+    stats: dict
+    cells_int: np.ndarray   # [nc,5] level, leaf, first, count, nchild
+    cells_dbl: np.ndarray   # [nc,6] s[3], rho, mass, minscale
+    m2l: np.ndarray         # [n_m2l,2] (source cell, sink cell)
+    p2p: np.ndarray         # [n_p2p,2]
+    perm: np.ndarray
+    scale: np.ndarray       # per sorted particle
+
+
+def fmm(x, mu, G=1.0, p=6, eps=1e-7, mac=MAC_A, theta_crit=0.5, leaf_size=32, p2p_c=1.0,
+        scale=None, keep=True):
+    """Run the oracle FMM; raises ValueError on invalid input."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    prm = Params(p, eps, mac, theta_crit, leaf_size, p2p_c, 1 if scale is not None else 0)
+    sc = None
+    if scale is not None:
+        sc = np.ascontiguousarray(scale, dtype=np.float64)
+    L = lib()
+    h = L.orc_fmm(len(mu), x, mu, G, C.byref(prm), sc.ctypes.data if sc is not None else None)
+    if not h:
+        raise ValueError("oracle rejected the input")
+    try:
+        n = len(mu)
+        psi, acc = np.zeros(max(n, 1)), np.zeros((max(n, 1), 3))
+        L.orc_run_outputs(h, psi, acc)
+        st = Stats()
+        L.orc_run_stats(h, C.byref(st))
+        stats = {k: getattr(st, k) for k, _ in Stats._fields_}
+        if keep and n > 0:
+            nc = L.orc_run_ncells(h)
+            ci, cd = np.zeros((nc, 5), dtype=np.int64), np.zeros((nc, 6))
+            L.orc_run_cells(h, ci, cd)
+            m2 = np.zeros((max(st.n_m2l, 1), 2), dtype=np.int64)
+            pp = np.zeros((max(st.n_p2p, 1), 2), dtype=np.int64)
+            L.orc_run_lists(h, m2, pp)
+            perm = np.zeros(n, dtype=np.int64)
+            L.orc_run_perm(h, perm)
+            scl = np.zeros(n)
+            L.orc_run_scale(h, scl)
+            return Run(psi[:n], acc[:n], stats, ci, cd, m2[:st.n_m2l], pp[:st.n_p2p], perm, scl)
+        return Run(psi[:n], acc[:n], stats, None, None, None, None, None, None)
+    finally:
+        L.orc_run_free(h)
