@@ -1,0 +1,172 @@
+/*
+ * gb3fmm.h -- C ABI of the GB300 fast multipole method for unsoftened gravity
+ * (Dehnen, "A fast multipole method for stellar dynamics", arXiv 1405.2255).
+ *
+ * The library computes, for N particles with positions x_b and masses mu_b,
+ * the (negative) potential and the acceleration of eq. (1):
+ *
+ *     psi_b = sum_{a != b} G mu_a / |x_b - x_a|,      acc_b = grad psi_b
+ *           = sum_{a != b} G mu_a (x_a - x_b) / |x_a - x_b|^3,
+ *
+ * approximated by the FMM of Sec. 2 (P2M, M2M, dual tree walk with M2L and P2P,
+ * L2L, L2P) under the error-balanced multipole-acceptance criteria of
+ * eqs. (18a,b).  The free parameters are the expansion order p and the accuracy
+ * parameter eps (Sec. 6).  psi is the paper's Psi: it is POSITIVE, the physical
+ * potential is -psi.
+ *
+ * Conventions for every call:
+ *   - Return 0 on success or a negative FMM_E_* code.  No C++ exception crosses
+ *     the ABI.  fmm_last_error(ctx) gives a one-line description of the last
+ *     failure on that context.
+ *   - Particle arrays are array-of-structures FP64: x[n][3] (x, y, z of particle i
+ *     at x[3i..3i+2]), mu[n], psi[n], acc[n][3], in the caller's particle order.
+ *   - Pointers documented as "device" must point to memory of the context's
+ *     device (cudaMalloc'd, or torch tensors' data_ptr()).  Pointers documented as
+ *     "host" are ordinary CPU memory.  The caller owns all input and output
+ *     buffers; the context owns its workspace (tree, expansions, lists).
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Device
+ *     calls are asynchronous with respect to the host unless stated otherwise;
+ *     inputs must stay valid until the stream has reached the call's end.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef GB3FMM_H
+#define GB3FMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define FMM_OK            0
+#define FMM_E_INVALID    -1   /* NaN/Inf position, mu < 0, p outside [1,20], eps <= 0, bad sizes */
+#define FMM_E_OOM        -2   /* device allocation failed */
+#define FMM_E_ADMISSION  -3   /* serving: footprint above the context's memory budget */
+#define FMM_E_CUDA       -4   /* a CUDA runtime call failed */
+#define FMM_E_TIMEOUT    -5   /* a bounded device or host wait ran out */
+#define FMM_E_OVERFLOW   -6   /* an internal capacity could not be grown */
+#define FMM_E_NOTFOUND   -7   /* unknown system id or ticket */
+#define FMM_E_BUSY       -8   /* the request is not finished yet (fmm_poll) */
+
+/* multipole-acceptance criteria */
+#define FMM_MAC_A      0  /* eq. (18a): theta<1 and E~ M_A/r^2 < eps min_{b in B} a_b  */
+#define FMM_MAC_F      1  /* eq. (18b): theta<1 and E~ M_A/r^2 < eps min_{b in B} f_b  */
+#define FMM_MAC_THETA  2  /* eq. (9):   theta < theta_crit (geometric, for tests)       */
+
+/* arithmetic of the path */
+#define FMM_PREC_FP64   0  /* every step in IEEE FP64                                   */
+#define FMM_PREC_MIXED  1  /* P2P in FP32 on two-float leaf-relative positions with
+                              compensated accumulation; everything else FP64          */
+
+/* source of the acceleration scale used by (18a)/(18b) */
+#define FMM_SCALE_ESTIMATE 0  /* low-order FMM estimate (Sec. 5.3.2)                  */
+#define FMM_SCALE_CALLER   1  /* per-particle scale array passed to fmm_evaluate      */
+
+typedef struct {
+    int    p;           /* expansion order, 1..20 (Sec. 2.1)                          */
+    double eps;         /* accuracy parameter of eqs. (18a,b), > 0                     */
+    int    mac;         /* FMM_MAC_*                                                   */
+    double theta_crit;  /* opening angle for FMM_MAC_THETA, in (0,1)                   */
+    int    leaf_size;   /* a cell holding more particles is split (1..4096)            */
+    double p2p_c;       /* a pair (A,B) is summed directly when N_A N_B < p2p_c p^3     */
+    int    precision;   /* FMM_PREC_*                                                  */
+    int    scale_src;   /* FMM_SCALE_*                                                 */
+} fmm_params;
+
+typedef struct {
+    /* counts of the last evaluation */
+    int64_t n, ncells, nleaves, n_m2l, n_p2p, p2p_interactions, coincident;
+    int64_t est_m2l, est_p2p;
+    int     depth, p;
+    double  eps;
+    int     leaf_size;
+    /* device time per phase in milliseconds (CUDA events on the call's stream) */
+    float   t_tree, t_estimate, t_up, t_walk, t_m2l, t_p2p, t_down, t_total;
+} fmm_stats;
+
+typedef struct fmm_ctx fmm_ctx;
+
+/* Default parameters: p = 8, eps = 1e-7, (18a) with the low-order estimate,
+ * leaf_size = 64, p2p_c = 8, mixed precision.  Host pointer, filled in. */
+void fmm_default_params(fmm_params* out);
+
+/* Create a context on CUDA device `device` (the device becomes current for the
+ * calling thread).  `params` (host, may be NULL for defaults) is copied.  The
+ * context allocates its workspace lazily and keeps it for later calls. */
+int fmm_create(fmm_ctx** out, const fmm_params* params, int device);
+
+/* Replace the parameters of an existing context (host pointer, copied). */
+int fmm_set_params(fmm_ctx* ctx, const fmm_params* params);
+
+/* One force evaluation (Sec. 2.2.2; the phases of Table 2): tree build, scale
+ * estimate, upward pass, dual tree walk, M2L, P2P, downward pass.
+ *   n      number of particles, 0 <= n < 2^31 (0 is a no-op)
+ *   x      device, [n][3] FP64 positions
+ *   mu     device, [n] FP64 masses, >= 0
+ *   G      gravitational constant (psi and acc scale with it)
+ *   scale  device, [n] FP64 per-particle a_b (MAC_A) or f_b (MAC_F) when
+ *          params.scale_src == FMM_SCALE_CALLER, else ignored (may be NULL)
+ *   psi    device, [n] FP64 out: potential (positive, eq. 1)
+ *   acc    device, [n][3] FP64 out: acceleration
+ *   stream cudaStream_t or NULL
+ *   stats  host, may be NULL: counts and phase times (filling it synchronises
+ *          the stream)
+ * The call returns once the work is queued, or after the stream is synchronised
+ * when stats != NULL.  The tree build reads a handful of counts back to the
+ * host, so the call always waits for the tree phase of its own stream.
+ * Pairs at distance 0 contribute nothing and are counted in stats->coincident.
+ * FMM_E_INVALID is returned for NaN/Inf positions or negative masses (checked on
+ * the device; outputs are left unspecified in that case). */
+int fmm_evaluate(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G,
+                 const double* scale, double* psi, double* acc, void* stream, fmm_stats* stats);
+
+/* As fmm_evaluate, but x, mu, psi and acc are HOST pointers; the context copies
+ * the inputs to its own device buffers and the outputs back, and synchronises
+ * the stream before returning (the end-to-end call). */
+int fmm_evaluate_host(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G,
+                      double* psi, double* acc, void* stream, fmm_stats* stats);
+
+/* Direct summation of eq. (1) (and f_b of eq. (6) if f != NULL) on the GPU in
+ * FP64 for the sinks listed in `sinks` (device int64 [nsinks] indices into the
+ * n sources; NULL means all n particles are sinks, nsinks ignored).  Outputs
+ * psi [nsinks], acc [nsinks][3], f [nsinks] (device; f may be NULL) in the
+ * order of `sinks`.  Coincident pairs are skipped. */
+int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G,
+               int64_t nsinks, const int64_t* sinks, double* psi, double* acc, double* f,
+               void* stream);
+
+/* Many independent systems in one call (the batched ensemble).  System s holds
+ * particles [offsets[s], offsets[s+1]) of x/mu/psi/acc (device arrays laid out as
+ * for fmm_evaluate); offsets is a HOST int64 array of nsys+1 entries starting at 0;
+ * G is a HOST array of nsys constants.  Systems share no interactions. */
+int fmm_evaluate_batch(fmm_ctx* ctx, int nsys, const int64_t* offsets, const double* x,
+                       const double* mu, const double* G, double* psi, double* acc,
+                       void* stream, fmm_stats* stats);
+
+/* Copy the context's view of the last evaluation to HOST buffers, for tests:
+ * cells (ncells x 5 int64: level, leaf, first, count, nchild; ncells x 6 double:
+ * centre x,y,z, rho, mass, minscale), the M2L and P2P lists as (source cell,
+ * sink cell) int64 pairs, and perm[n] (sorted position -> caller index).  Any
+ * pointer may be NULL; counts are in the last stats. */
+int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t* m2l,
+                   int64_t* p2p, int64_t* perm, double* scale_sorted);
+
+int fmm_last_stats(fmm_ctx* ctx, fmm_stats* out);
+
+/* Release the context and all of its device memory. */
+int fmm_destroy(fmm_ctx* ctx);
+
+/* Static description of an error code. */
+const char* fmm_strerror(int code);
+
+/* Description of the last failure on ctx (empty string if none). */
+const char* fmm_last_error(fmm_ctx* ctx);
+
+/* Version string of the library. */
+const char* fmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB3FMM_H */

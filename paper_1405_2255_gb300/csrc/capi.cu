@@ -1,0 +1,733 @@
+// capi.cu -- the C ABI of include/gb3fmm.h: the context, its device workspace, and
+// the order of the phases of one evaluation (the call stack of Sec. 2.2.2 and the
+// phases of Table 2: tree, estimate, up, walk, down).
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace gb3 {
+extern thread_local char g_cuda_msg[256];
+}
+using namespace gb3;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+int ensure(Buf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return 0;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&b.p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            snprintf(g_cuda_msg, sizeof g_cuda_msg, "cudaMalloc of %zu bytes failed", bytes);
+            return FMM_E_OOM;
+        }
+        want = bytes;
+    }
+    b.bytes = want;
+    return 0;
+}
+void release(Buf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+template <class T>
+T* P(Buf& b) {
+    return (T*)b.p;
+}
+
+enum { EV_START, EV_TREE, EV_EST, EV_UP, EV_WALK, EV_M2L, EV_P2P, EV_DOWN, EV_END, EV_N };
+
+}  // namespace
+
+struct fmm_ctx {
+    fmm_params prm;
+    int device = 0;
+    char err[512] = {0};
+    fmm_stats last;
+    // host-API staging
+    Buf hx, hmu, hpsi, hacc;
+    // particles and sort
+    Buf bounds, status, counters, coin, dtotal;
+    Buf keys, keys_alt, idx, idx_alt, rtmp, xm, perm, xhi, xlo;
+    // cells
+    Buf first, count, child, nchild, parent, level, sr, cr, mass, minscale;
+    Buf split_nchild, split_oct, split_offs, scan_tmp, leaves, leaf_flag, leaf_pos, rad_tmp;
+    // expansions
+    Buf M, F, Pw, binom, M1, F1, Ff;
+    // walk
+    Buf front0, front1, m2l, p2p, sort_tmp, seg_start, seg_end, est_m2l, est_p2p, m2l_seg_start, m2l_seg_end;
+    long long front_cap = 0, m2l_cap = 0, p2p_cap = 0, est_m2l_cap = 0, est_p2p_cap = 0;
+    // per particle results (sorted order)
+    Buf psi_far, acc_far, psi_near, acc_near, scale_sorted;
+    unsigned long long* h_counters = nullptr;  // pinned
+    int* h_int = nullptr;                      // pinned
+    cudaEvent_t ev[EV_N];
+    bool ev_ok = false;
+    // tree shape of the last evaluation
+    std::vector<int> lev_start;
+    int n = 0, ncells = 0, nleaves = 0;
+    long long n_m2l = 0, n_p2p = 0, n_est_m2l = 0, n_est_p2p = 0;
+};
+
+static int fail(fmm_ctx* ctx, int code, const char* msg) {
+    if (ctx) snprintf(ctx->err, sizeof ctx->err, "%s", msg);
+    return code;
+}
+static int fail_cuda(fmm_ctx* ctx, int code) {
+    if (ctx) snprintf(ctx->err, sizeof ctx->err, "%s", g_cuda_msg);
+    return code;
+}
+
+#define TRY(expr)                                     \
+    do {                                              \
+        int _rc = (expr);                             \
+        if (_rc) return fail_cuda(ctx, _rc);          \
+    } while (0)
+#define CU(expr) TRY(([&]() -> int { GB3_CUDA_TRY(expr); return 0; })())
+
+static Cells cells_of(fmm_ctx* ctx) {
+    Cells c;
+    c.first = P<int>(ctx->first);
+    c.count = P<int>(ctx->count);
+    c.child = P<int>(ctx->child);
+    c.nchild = P<int>(ctx->nchild);
+    c.parent = P<int>(ctx->parent);
+    c.level = P<int>(ctx->level);
+    c.sr = P<d4>(ctx->sr);
+    c.cr = P<d4>(ctx->cr);
+    c.mass = P<double>(ctx->mass);
+    c.minscale = P<double>(ctx->minscale);
+    return c;
+}
+
+static int check_params(const fmm_params* p) {
+    if (p->p < 1 || p->p > kMaxP) return FMM_E_INVALID;
+    if (p->mac != FMM_MAC_A && p->mac != FMM_MAC_F && p->mac != FMM_MAC_THETA) return FMM_E_INVALID;
+    if (p->mac != FMM_MAC_THETA && !(p->eps > 0)) return FMM_E_INVALID;
+    if (p->mac == FMM_MAC_THETA && !(p->theta_crit > 0 && p->theta_crit < 1)) return FMM_E_INVALID;
+    if (p->leaf_size < 1 || p->leaf_size > 4096) return FMM_E_INVALID;
+    if (!(p->p2p_c >= 0)) return FMM_E_INVALID;
+    if (p->precision != FMM_PREC_FP64 && p->precision != FMM_PREC_MIXED) return FMM_E_INVALID;
+    if (p->scale_src != FMM_SCALE_ESTIMATE && p->scale_src != FMM_SCALE_CALLER) return FMM_E_INVALID;
+    return 0;
+}
+
+// ------------------------------------------------------------------ tree (A1-A4)
+__global__ void k_root(Cells c, int n) {
+    c.first[0] = 0;
+    c.count[0] = n;
+    c.level[0] = 0;
+    c.parent[0] = -1;
+    c.child[0] = -1;
+    c.nchild[0] = 0;
+}
+__global__ void k_leaf_flags(const int* __restrict__ nchild, int nc, int* __restrict__ flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) flag[i] = nchild[i] == 0;
+}
+__global__ void k_leaf_compact(const int* __restrict__ flag, const int* __restrict__ pos, int nc, int* __restrict__ leaves) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+        if (flag[i]) leaves[pos[i]] = i;
+}
+
+static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cudaStream_t s) {
+    const int leaf = ctx->prm.leaf_size;
+    TRY(ensure(ctx->keys, sizeof(uint64_t) * n));
+    TRY(ensure(ctx->keys_alt, sizeof(uint64_t) * n));
+    TRY(ensure(ctx->idx, sizeof(int) * n));
+    TRY(ensure(ctx->idx_alt, sizeof(int) * n));
+    TRY(ensure(ctx->rtmp, sizeof(int) * radix_tmp_ints(n)));
+    TRY(ensure(ctx->xm, sizeof(d4) * n));
+    TRY(ensure(ctx->perm, sizeof(int) * n));
+    launch_bounds(x, mu, n, P<unsigned long long>(ctx->bounds), P<unsigned>(ctx->status), s);
+    launch_keys(x, n, P<unsigned long long>(ctx->bounds), P<uint64_t>(ctx->keys), P<int>(ctx->idx), s);
+    radix_sort_pairs(P<uint64_t>(ctx->keys), P<int>(ctx->idx), P<uint64_t>(ctx->keys_alt), P<int>(ctx->idx_alt), n,
+                     P<int>(ctx->rtmp), s);
+    launch_gather(x, mu, P<int>(ctx->idx), n, P<d4>(ctx->xm), P<int>(ctx->perm), s);
+
+    // cell capacity: leaves <= n, internal cells hold > leaf particles, <= 21 levels
+    long long cap = (long long)n + 21LL * (n / (leaf + 1)) + 64;
+    Buf* ib[] = {&ctx->first, &ctx->count, &ctx->child, &ctx->nchild, &ctx->parent, &ctx->level};
+    for (Buf* b : ib) TRY(ensure(*b, sizeof(int) * cap));
+    TRY(ensure(ctx->sr, sizeof(d4) * cap));
+    TRY(ensure(ctx->cr, sizeof(d4) * cap));
+    TRY(ensure(ctx->mass, sizeof(double) * cap));
+    TRY(ensure(ctx->minscale, sizeof(double) * cap));
+    Cells c = cells_of(ctx);
+    k_root<<<1, 1, 0, s>>>(c, n);
+    ctx->lev_start.assign({0, 1});
+    for (int L = 0;; ++L) {
+        int b = ctx->lev_start[L], e = ctx->lev_start[L + 1];
+        int ncl = e - b;
+        if (ncl <= 0) break;
+        TRY(ensure(ctx->split_nchild, sizeof(int) * ncl));
+        TRY(ensure(ctx->split_oct, sizeof(int) * 9 * (size_t)ncl));
+        TRY(ensure(ctx->split_offs, sizeof(int) * ncl));
+        TRY(ensure(ctx->scan_tmp, sizeof(int) * scan_tmp_ints(std::max<long long>(ncl, cap))));
+        launch_split_level(P<uint64_t>(ctx->keys), c, b, e, L, leaf, P<int>(ctx->split_nchild), P<int>(ctx->split_oct),
+                           P<int>(ctx->split_offs), P<int>(ctx->scan_tmp), P<int>(ctx->dtotal), s);
+        CU(cudaMemcpyAsync(ctx->h_int, ctx->dtotal.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        int tot = ctx->h_int[0];
+        if (tot <= 0) break;
+        if ((long long)e + tot > cap) return fail(ctx, FMM_E_OVERFLOW, "cell capacity exceeded");
+        ctx->lev_start.push_back(e + tot);
+    }
+    int nc = ctx->lev_start.back();
+    ctx->ncells = nc;
+    // leaves
+    TRY(ensure(ctx->leaf_flag, sizeof(int) * nc));
+    TRY(ensure(ctx->leaf_pos, sizeof(int) * nc));
+    TRY(ensure(ctx->leaves, sizeof(int) * nc));
+    TRY(ensure(ctx->scan_tmp, sizeof(int) * scan_tmp_ints(nc)));
+    k_leaf_flags<<<grid_for(nc, 256), 256, 0, s>>>(c.nchild, nc, P<int>(ctx->leaf_flag));
+    scan_exclusive_i32(P<int>(ctx->leaf_flag), P<int>(ctx->leaf_pos), nc, P<int>(ctx->dtotal), P<int>(ctx->scan_tmp), s);
+    k_leaf_compact<<<grid_for(nc, 256), 256, 0, s>>>(P<int>(ctx->leaf_flag), P<int>(ctx->leaf_pos), nc, P<int>(ctx->leaves));
+    CU(cudaMemcpyAsync(ctx->h_int, ctx->dtotal.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    ctx->nleaves = ctx->h_int[0];
+    unsigned st = 0;
+    CU(cudaMemcpy(&st, ctx->status.p, sizeof st, cudaMemcpyDeviceToHost));
+    if (st & kStatInvalid) return fail(ctx, FMM_E_INVALID, "non-finite position or mass, or negative mass");
+
+    // geometry: leaves, then internal cells bottom-up
+    int nlev = (int)ctx->lev_start.size() - 1;
+    int maxlev_cells = 0;
+    for (int L = 0; L < nlev; ++L) maxlev_cells = std::max(maxlev_cells, ctx->lev_start[L + 1] - ctx->lev_start[L]);
+    TRY(ensure(ctx->rad_tmp, sizeof(unsigned long long) * 2 * (size_t)maxlev_cells));
+    launch_leaf_geometry(P<d4>(ctx->xm), c, P<int>(ctx->leaves), ctx->nleaves, P<unsigned>(ctx->status), s);
+    for (int L = nlev - 1; L >= 0; --L)
+        launch_internal_geometry(P<d4>(ctx->xm), c, ctx->lev_start[L], ctx->lev_start[L + 1], n,
+                                 P<unsigned long long>(ctx->rad_tmp), P<unsigned>(ctx->status), s);
+    return 0;
+}
+
+// ------------------------------------------------------------------ walk driver (A8)
+static int run_walk(fmm_ctx* ctx, WalkParams wp, Buf& m2l, long long& m2l_cap, Buf& p2p, long long& p2p_cap,
+                    long long* n_m2l, long long* n_p2p, cudaStream_t s) {
+    Cells c = cells_of(ctx);
+    const int nc = ctx->ncells;
+    if (ctx->front_cap == 0) ctx->front_cap = std::max<long long>(1 << 16, 32LL * nc);
+    if (m2l_cap == 0) m2l_cap = std::max<long long>(1 << 16, 64LL * nc);
+    if (p2p_cap == 0) p2p_cap = std::max<long long>(1 << 16, 32LL * nc);
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        TRY(ensure(ctx->front0, sizeof(int2) * ctx->front_cap));
+        TRY(ensure(ctx->front1, sizeof(int2) * ctx->front_cap));
+        TRY(ensure(m2l, sizeof(int2) * m2l_cap));
+        TRY(ensure(p2p, sizeof(int2) * p2p_cap));
+        WalkBuffers wb;
+        wb.front[0] = P<int2>(ctx->front0);
+        wb.front[1] = P<int2>(ctx->front1);
+        wb.front_cap = ctx->front_cap;
+        wb.m2l = P<int2>(m2l);
+        wb.m2l_cap = m2l_cap;
+        wb.p2p = P<int2>(p2p);
+        wb.p2p_cap = p2p_cap;
+        wb.counters = P<unsigned long long>(ctx->counters);
+        int2 root = make_int2(0, 0);
+        CU(cudaMemcpyAsync(wb.front[0], &root, sizeof root, cudaMemcpyHostToDevice, s));
+        CU(cudaMemsetAsync(wb.counters, 0, 4 * sizeof(unsigned long long), s));
+        long long nfront = 1;
+        int cur = 0;
+        bool overflow = false;
+        long long need_front = 0;
+        while (nfront > 0) {
+            CU(cudaMemsetAsync(wb.counters, 0, sizeof(unsigned long long), s));
+            launch_walk_step(c, wp, wb.front[cur], nfront, wb.front[cur ^ 1], wb, s);
+            CU(cudaMemcpyAsync(ctx->h_counters, wb.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            need_front = std::max<long long>(need_front, (long long)ctx->h_counters[0]);
+            if (ctx->h_counters[3]) {
+                overflow = true;
+                break;
+            }
+            nfront = (long long)ctx->h_counters[0];
+            cur ^= 1;
+        }
+        if (!overflow) {
+            *n_m2l = (long long)ctx->h_counters[1];
+            *n_p2p = (long long)ctx->h_counters[2];
+            return 0;
+        }
+        // grow what overflowed (the counters hold at least the demand seen so far) and redo the walk
+        if ((long long)ctx->h_counters[0] > ctx->front_cap || need_front > ctx->front_cap)
+            ctx->front_cap = std::max<long long>(2 * ctx->front_cap, 2 * need_front);
+        if ((long long)ctx->h_counters[1] > m2l_cap) m2l_cap = std::max<long long>(2 * m2l_cap, 2 * (long long)ctx->h_counters[1]);
+        if ((long long)ctx->h_counters[2] > p2p_cap) p2p_cap = std::max<long long>(2 * p2p_cap, 2 * (long long)ctx->h_counters[2]);
+    }
+    return fail(ctx, FMM_E_OVERFLOW, "walk lists could not be grown enough");
+}
+
+static int sort_and_segment(fmm_ctx* ctx, Buf& list, long long npairs, Buf& seg_start, Buf& seg_end, cudaStream_t s) {
+    TRY(ensure(ctx->sort_tmp, list_sort_tmp_bytes(npairs)));
+    TRY(ensure(seg_start, sizeof(int) * ctx->ncells));
+    TRY(ensure(seg_end, sizeof(int) * ctx->ncells));
+    sort_pairs_by_sink(P<int2>(list), npairs, ctx->ncells, ctx->sort_tmp.p, s);
+    launch_segments(P<int2>(list), npairs, ctx->ncells, P<int>(seg_start), P<int>(seg_end), s);
+    return 0;
+}
+
+// ------------------------------------------------------------------ the low-order scale (A7)
+static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
+    const int n = ctx->n, nc = ctx->ncells;
+    Cells c = cells_of(ctx);
+    const bool want_f = ctx->prm.mac == FMM_MAC_F;
+    const int nlev = (int)ctx->lev_start.size() - 1;
+    WalkParams wp;
+    memset(&wp, 0, sizeof wp);
+    wp.p = want_f ? 0 : 1;
+    wp.mac = kMacEstimate;
+    wp.p2p_thresh = ctx->prm.p2p_c * (double)ctx->prm.p * ctx->prm.p * ctx->prm.p;
+    wp.use_com = 1;
+    TRY(run_walk(ctx, wp, ctx->est_m2l, ctx->est_m2l_cap, ctx->est_p2p, ctx->est_p2p_cap, &ctx->n_est_m2l,
+                 &ctx->n_est_p2p, s));
+    TRY(sort_and_segment(ctx, ctx->est_m2l, ctx->n_est_m2l, ctx->m2l_seg_start, ctx->m2l_seg_end, s));
+    // P2P segments of the estimate reuse seg_start/seg_end of the main lists (written later)
+    TRY(ensure(ctx->seg_start, sizeof(int) * nc));
+    TRY(ensure(ctx->seg_end, sizeof(int) * nc));
+    TRY(ensure(ctx->sort_tmp, list_sort_tmp_bytes(ctx->n_est_p2p)));
+    sort_pairs_by_sink(P<int2>(ctx->est_p2p), ctx->n_est_p2p, nc, ctx->sort_tmp.p, s);
+    launch_segments(P<int2>(ctx->est_p2p), ctx->n_est_p2p, nc, P<int>(ctx->seg_start), P<int>(ctx->seg_end), s);
+    double* scale = P<double>(ctx->scale_sorted);
+    if (want_f) {
+        TRY(ensure(ctx->Ff, sizeof(double) * nc));
+        launch_f_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), nc, c,
+                     P<double>(ctx->Ff), s);
+        for (int L = 1; L < nlev; ++L) launch_f_down_level(c, ctx->lev_start[L], ctx->lev_start[L + 1], P<double>(ctx->Ff), s);
+        launch_f_p2p(P<d4>(ctx->xm), c, P<int2>(ctx->est_p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
+                     P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->Ff), scale, s);
+        return 0;
+    }
+    const int pe = 1, nco = ncoef(pe);
+    TRY(ensure(ctx->M1, sizeof(double) * nco * (size_t)nc));
+    TRY(ensure(ctx->F1, sizeof(double) * nco * (size_t)nc));
+    CU(cudaMemsetAsync(ctx->F1.p, 0, sizeof(double) * nco * (size_t)nc, s));
+    launch_p2m(P<d4>(ctx->xm), c, c.cr, P<int>(ctx->leaves), ctx->nleaves, pe, P<double>(ctx->M1), s);
+    for (int L = nlev - 1; L >= 0; --L)
+        launch_m2m_level(c, c.cr, ctx->lev_start[L], ctx->lev_start[L + 1], pe, P<double>(ctx->M1), s);
+    launch_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), nullptr, nc, c.cr,
+               P<double>(ctx->M1), pe, P<double>(ctx->F1), s);
+    for (int L = 1; L < nlev; ++L) launch_l2l_level(c, c.cr, ctx->lev_start[L], ctx->lev_start[L + 1], pe, P<double>(ctx->F1), s);
+    launch_l2p(P<d4>(ctx->xm), c, c.cr, P<int>(ctx->leaves), ctx->nleaves, pe, P<double>(ctx->F1),
+               P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
+    unsigned long long* dummy = P<unsigned long long>(ctx->counters) + 4;
+    if (ctx->prm.precision == FMM_PREC_MIXED)
+        launch_p2p_mixed(P<d4>(ctx->xm), P<float4>(ctx->xhi), P<float4>(ctx->xlo), c, P<int2>(ctx->est_p2p),
+                         P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
+                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), dummy, s);
+    else
+        launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->est_p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
+                        P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), dummy, s);
+    launch_norm_scale(nullptr, P<double>(ctx->acc_far), P<double>(ctx->acc_near), n, scale, s);
+    return 0;
+}
+
+// ------------------------------------------------------------------ one evaluation
+static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* mu, double G, const double* scale,
+                           double* psi, double* acc, cudaStream_t s, fmm_stats* stats) {
+    const fmm_params& prm = ctx->prm;
+    if (check_params(&prm)) return fail(ctx, FMM_E_INVALID, "invalid parameters");
+    memset(&ctx->last, 0, sizeof ctx->last);
+    ctx->last.n = n;
+    ctx->last.p = prm.p;
+    ctx->last.eps = prm.eps;
+    ctx->last.leaf_size = prm.leaf_size;
+    ctx->n = n;
+    ctx->ncells = ctx->nleaves = 0;
+    ctx->n_m2l = ctx->n_p2p = ctx->n_est_m2l = ctx->n_est_p2p = 0;
+    if (n == 0) {
+        if (stats) *stats = ctx->last;
+        return 0;
+    }
+    if (prm.scale_src == FMM_SCALE_CALLER && prm.mac != FMM_MAC_THETA && !scale)
+        return fail(ctx, FMM_E_INVALID, "scale_src = caller but scale == NULL");
+    const bool timing = stats != nullptr && ctx->ev_ok;
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_START], s));
+    CU(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), s));
+    CU(cudaMemsetAsync(ctx->coin.p, 0, sizeof(unsigned long long), s));
+    TRY(build_tree(ctx, n, x, mu, s));
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_TREE], s));
+    const int nc = ctx->ncells, nco = ncoef(prm.p);
+    const int nlev = (int)ctx->lev_start.size() - 1;
+    Cells c = cells_of(ctx);
+    TRY(ensure(ctx->psi_far, sizeof(double) * n));
+    TRY(ensure(ctx->acc_far, sizeof(double) * 3 * (size_t)n));
+    TRY(ensure(ctx->psi_near, sizeof(double) * n));
+    TRY(ensure(ctx->acc_near, sizeof(double) * 3 * (size_t)n));
+    TRY(ensure(ctx->scale_sorted, sizeof(double) * n));
+    if (prm.precision == FMM_PREC_MIXED) {
+        TRY(ensure(ctx->xhi, sizeof(float4) * n));
+        TRY(ensure(ctx->xlo, sizeof(float4) * n));
+        launch_split_positions(P<d4>(ctx->xm), n, P<float4>(ctx->xhi), P<float4>(ctx->xlo), s);
+    }
+
+    // A7: acceleration scale for the MAC and its per-cell minimum
+    if (prm.mac != FMM_MAC_THETA) {
+        if (prm.scale_src == FMM_SCALE_CALLER)
+            launch_scale_from_caller(scale, P<int>(ctx->perm), n, P<double>(ctx->scale_sorted), s);
+        else
+            TRY(estimate_scale(ctx, s));
+        launch_minscale_leaves(P<double>(ctx->scale_sorted), c, P<int>(ctx->leaves), ctx->nleaves, s);
+        for (int L = nlev - 1; L >= 0; --L) launch_minscale_level(c, ctx->lev_start[L], ctx->lev_start[L + 1], s);
+    }
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_EST], s));
+
+    // A5-A6: upward pass
+    TRY(ensure(ctx->M, sizeof(double) * nco * (size_t)nc));
+    TRY(ensure(ctx->F, sizeof(double) * nco * (size_t)nc));
+    TRY(ensure(ctx->Pw, sizeof(double) * (prm.p + 1) * (size_t)nc));
+    TRY(ensure(ctx->binom, sizeof(double) * (kMaxP + 1)));
+    {
+        double bn[kMaxP + 1];
+        bn[0] = 1;
+        for (int k = 1; k <= prm.p; ++k) bn[k] = bn[k - 1] * (prm.p - k + 1) / k;
+        CU(cudaMemcpyAsync(ctx->binom.p, bn, sizeof(double) * (prm.p + 1), cudaMemcpyHostToDevice, s));
+    }
+    launch_p2m(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->M), s);
+    for (int L = nlev - 1; L >= 0; --L)
+        launch_m2m_level(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->M), s);
+    launch_power(P<double>(ctx->M), nc, prm.p, P<double>(ctx->Pw), s);
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_UP], s));
+
+    // A8: dual tree walk
+    WalkParams wp;
+    wp.p = prm.p;
+    wp.mac = prm.mac;
+    wp.eps = prm.eps;
+    wp.theta_crit = prm.theta_crit;
+    wp.p2p_thresh = prm.p2p_c * (double)prm.p * prm.p * prm.p;
+    wp.P = P<double>(ctx->Pw);
+    wp.binom = P<double>(ctx->binom);
+    wp.use_com = 0;
+    TRY(run_walk(ctx, wp, ctx->m2l, ctx->m2l_cap, ctx->p2p, ctx->p2p_cap, &ctx->n_m2l, &ctx->n_p2p, s));
+    TRY(sort_and_segment(ctx, ctx->m2l, ctx->n_m2l, ctx->m2l_seg_start, ctx->m2l_seg_end, s));
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_WALK], s));
+
+    // A9: M2L
+    CU(cudaMemsetAsync(ctx->F.p, 0, sizeof(double) * nco * (size_t)nc, s));
+    launch_m2l(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), nullptr, nc, c.sr,
+               P<double>(ctx->M), prm.p, P<double>(ctx->F), s);
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_M2L], s));
+
+    // A10: P2P
+    TRY(sort_and_segment(ctx, ctx->p2p, ctx->n_p2p, ctx->seg_start, ctx->seg_end, s));
+    if (prm.precision == FMM_PREC_MIXED)
+        launch_p2p_mixed(P<d4>(ctx->xm), P<float4>(ctx->xhi), P<float4>(ctx->xlo), c, P<int2>(ctx->p2p),
+                         P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
+                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), P<unsigned long long>(ctx->coin), s);
+    else
+        launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
+                        P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near),
+                        P<unsigned long long>(ctx->coin), s);
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_P2P], s));
+
+    // A11-A12: L2L, L2P, combine and scatter
+    for (int L = 1; L < nlev; ++L) launch_l2l_level(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->F), s);
+    launch_l2p(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->F),
+               P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
+    launch_finish(P<double>(ctx->psi_far), P<double>(ctx->acc_far), P<double>(ctx->psi_near), P<double>(ctx->acc_near),
+                  P<int>(ctx->perm), n, G, psi, acc, s);
+    if (timing) {
+        CU(cudaEventRecord(ctx->ev[EV_DOWN], s));
+        CU(cudaEventRecord(ctx->ev[EV_END], s));
+    }
+    CU(cudaGetLastError());
+
+    ctx->last.ncells = nc;
+    ctx->last.nleaves = ctx->nleaves;
+    ctx->last.n_m2l = ctx->n_m2l;
+    ctx->last.n_p2p = ctx->n_p2p;
+    ctx->last.est_m2l = ctx->n_est_m2l;
+    ctx->last.est_p2p = ctx->n_est_p2p;
+    ctx->last.depth = nlev - 1;
+    if (stats) {
+        CU(cudaStreamSynchronize(s));
+        unsigned long long coin = 0;
+        CU(cudaMemcpy(&coin, ctx->coin.p, sizeof coin, cudaMemcpyDeviceToHost));
+        ctx->last.coincident = (long long)coin - n;
+        // p2p particle interactions from the list
+        std::vector<int2> pl(ctx->n_p2p);
+        std::vector<int> cnt(nc);
+        if (ctx->n_p2p) CU(cudaMemcpy(pl.data(), ctx->p2p.p, sizeof(int2) * ctx->n_p2p, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(cnt.data(), ctx->count.p, sizeof(int) * nc, cudaMemcpyDeviceToHost));
+        long long inter = 0;
+        for (auto& e : pl) inter += (long long)cnt[e.x] * cnt[e.y] - (e.x == e.y ? cnt[e.x] : 0);
+        ctx->last.p2p_interactions = inter;
+        if (timing) {
+            float t;
+            auto el = [&](int a, int b) {
+                cudaEventElapsedTime(&t, ctx->ev[a], ctx->ev[b]);
+                return t;
+            };
+            ctx->last.t_tree = el(EV_START, EV_TREE);
+            ctx->last.t_estimate = el(EV_TREE, EV_EST);
+            ctx->last.t_up = el(EV_EST, EV_UP);
+            ctx->last.t_walk = el(EV_UP, EV_WALK);
+            ctx->last.t_m2l = el(EV_WALK, EV_M2L);
+            ctx->last.t_p2p = el(EV_M2L, EV_P2P);
+            ctx->last.t_down = el(EV_P2P, EV_DOWN);
+            ctx->last.t_total = el(EV_START, EV_END);
+        }
+        *stats = ctx->last;
+    }
+    return 0;
+}
+
+// ================================================================== C ABI
+extern "C" {
+
+void fmm_default_params(fmm_params* out) {
+    if (!out) return;
+    out->p = 8;
+    out->eps = 1e-7;
+    out->mac = FMM_MAC_A;
+    out->theta_crit = 0.5;
+    out->leaf_size = 64;
+    out->p2p_c = 8.0;
+    out->precision = FMM_PREC_MIXED;
+    out->scale_src = FMM_SCALE_ESTIMATE;
+}
+
+int fmm_create(fmm_ctx** out, const fmm_params* params, int device) {
+    if (!out) return FMM_E_INVALID;
+    *out = nullptr;
+    fmm_params prm;
+    if (params) prm = *params;
+    else fmm_default_params(&prm);
+    if (check_params(&prm)) return FMM_E_INVALID;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return FMM_E_CUDA;
+    }
+    fmm_ctx* ctx = new (std::nothrow) fmm_ctx();
+    if (!ctx) return FMM_E_OOM;
+    ctx->prm = prm;
+    ctx->device = device;
+    memset(&ctx->last, 0, sizeof ctx->last);
+    int rc = 0;
+    if (!rc) rc = ensure(ctx->bounds, 6 * sizeof(unsigned long long));
+    if (!rc) rc = ensure(ctx->status, 16);
+    if (!rc) rc = ensure(ctx->counters, 8 * sizeof(unsigned long long));
+    if (!rc) rc = ensure(ctx->coin, 16);
+    if (!rc) rc = ensure(ctx->dtotal, 16);
+    if (!rc && cudaMallocHost((void**)&ctx->h_counters, 8 * sizeof(unsigned long long)) != cudaSuccess) rc = FMM_E_OOM;
+    if (!rc && cudaMallocHost((void**)&ctx->h_int, 16 * sizeof(int)) != cudaSuccess) rc = FMM_E_OOM;
+    if (!rc) {
+        ctx->ev_ok = true;
+        for (int i = 0; i < EV_N; ++i)
+            if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) ctx->ev_ok = false;
+    }
+    if (rc) {
+        cudaGetLastError();
+        fmm_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return 0;
+}
+
+int fmm_set_params(fmm_ctx* ctx, const fmm_params* params) {
+    if (!ctx || !params) return FMM_E_INVALID;
+    if (check_params(params)) return fail(ctx, FMM_E_INVALID, "invalid parameters");
+    ctx->prm = *params;
+    return 0;
+}
+
+int fmm_evaluate(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, const double* scale,
+                 double* psi, double* acc, void* stream, fmm_stats* stats) {
+    if (!ctx) return FMM_E_INVALID;
+    ctx->err[0] = 0;
+    if (n < 0 || n > 0x7fffffffLL) return fail(ctx, FMM_E_INVALID, "n out of range");
+    if (n > 0 && (!x || !mu || !psi || !acc)) return fail(ctx, FMM_E_INVALID, "NULL buffer");
+    if (!std::isfinite(G)) return fail(ctx, FMM_E_INVALID, "G is not finite");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, FMM_E_CUDA, "cudaSetDevice failed");
+    return evaluate_device(ctx, (int)n, x, mu, G, scale, psi, acc, (cudaStream_t)stream, stats);
+}
+
+int fmm_evaluate_host(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, double* psi, double* acc,
+                      void* stream, fmm_stats* stats) {
+    if (!ctx) return FMM_E_INVALID;
+    ctx->err[0] = 0;
+    if (n < 0 || n > 0x7fffffffLL) return fail(ctx, FMM_E_INVALID, "n out of range");
+    if (n == 0) return 0;
+    if (!x || !mu || !psi || !acc) return fail(ctx, FMM_E_INVALID, "NULL buffer");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, FMM_E_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(ensure(ctx->hx, sizeof(double) * 3 * (size_t)n));
+    TRY(ensure(ctx->hmu, sizeof(double) * (size_t)n));
+    TRY(ensure(ctx->hpsi, sizeof(double) * (size_t)n));
+    TRY(ensure(ctx->hacc, sizeof(double) * 3 * (size_t)n));
+    CU(cudaMemcpyAsync(ctx->hx.p, x, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(ctx->hmu.p, mu, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, s));
+    int rc = evaluate_device(ctx, (int)n, P<double>(ctx->hx), P<double>(ctx->hmu), G, nullptr, P<double>(ctx->hpsi),
+                             P<double>(ctx->hacc), s, stats);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(psi, ctx->hpsi.p, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(acc, ctx->hacc.p, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return 0;
+}
+
+int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, int64_t nsinks,
+               const int64_t* sinks, double* psi, double* acc, double* f, void* stream) {
+    if (!ctx) return FMM_E_INVALID;
+    ctx->err[0] = 0;
+    if (n < 0 || n > 0x7fffffffLL) return fail(ctx, FMM_E_INVALID, "n out of range");
+    if (!sinks) nsinks = n;
+    if (nsinks < 0 || nsinks > 0x7fffffffLL) return fail(ctx, FMM_E_INVALID, "nsinks out of range");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, FMM_E_CUDA, "cudaSetDevice failed");
+    launch_direct(x, mu, (int)n, G, sinks, (int)nsinks, psi, acc, f, (cudaStream_t)stream);
+    CU(cudaGetLastError());
+    return 0;
+}
+
+int fmm_evaluate_batch(fmm_ctx* ctx, int nsys, const int64_t* offsets, const double* x, const double* mu,
+                       const double* G, double* psi, double* acc, void* stream, fmm_stats* stats) {
+    if (!ctx || nsys < 0 || (nsys > 0 && (!offsets || !G))) return FMM_E_INVALID;
+    fmm_stats tot;
+    memset(&tot, 0, sizeof tot);
+    for (int i = 0; i < nsys; ++i) {
+        int64_t a = offsets[i], b = offsets[i + 1];
+        if (b < a) return fail(ctx, FMM_E_INVALID, "offsets not increasing");
+        fmm_stats st;
+        int rc = fmm_evaluate(ctx, b - a, x + 3 * a, mu + a, G[i], nullptr, psi + a, acc + 3 * a, stream,
+                              stats ? &st : nullptr);
+        if (rc) return rc;
+        if (stats) {
+            tot.n += st.n;
+            tot.ncells += st.ncells;
+            tot.nleaves += st.nleaves;
+            tot.n_m2l += st.n_m2l;
+            tot.n_p2p += st.n_p2p;
+            tot.p2p_interactions += st.p2p_interactions;
+            tot.coincident += st.coincident;
+            tot.t_total += st.t_total;
+        }
+    }
+    if (stats) *stats = tot;
+    return 0;
+}
+
+int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t* m2l, int64_t* p2p, int64_t* perm,
+                   double* scale_sorted) {
+    if (!ctx) return FMM_E_INVALID;
+    const int nc = ctx->ncells, n = ctx->n;
+    CU(cudaDeviceSynchronize());
+    if (cells_int || cells_dbl) {
+        std::vector<int> lv(nc), fi(nc), co(nc), nch(nc);
+        std::vector<d4> sr(nc);
+        std::vector<double> ms(nc), mn(nc);
+        if (nc) {
+            CU(cudaMemcpy(lv.data(), ctx->level.p, sizeof(int) * nc, cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(fi.data(), ctx->first.p, sizeof(int) * nc, cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(co.data(), ctx->count.p, sizeof(int) * nc, cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(nch.data(), ctx->nchild.p, sizeof(int) * nc, cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(sr.data(), ctx->sr.p, sizeof(d4) * nc, cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(ms.data(), ctx->mass.p, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(mn.data(), ctx->minscale.p, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+        }
+        for (int i = 0; i < nc; ++i) {
+            if (cells_int) {
+                cells_int[5 * i] = lv[i];
+                cells_int[5 * i + 1] = nch[i] == 0;
+                cells_int[5 * i + 2] = fi[i];
+                cells_int[5 * i + 3] = co[i];
+                cells_int[5 * i + 4] = nch[i];
+            }
+            if (cells_dbl) {
+                cells_dbl[6 * i] = sr[i].x;
+                cells_dbl[6 * i + 1] = sr[i].y;
+                cells_dbl[6 * i + 2] = sr[i].z;
+                cells_dbl[6 * i + 3] = sr[i].w;
+                cells_dbl[6 * i + 4] = ms[i];
+                cells_dbl[6 * i + 5] = mn[i];
+            }
+        }
+    }
+    auto dump_list = [&](Buf& b, long long cnt, int64_t* out) -> int {
+        if (!out || cnt <= 0) return 0;
+        std::vector<int2> v(cnt);
+        GB3_CUDA_TRY(cudaMemcpy(v.data(), b.p, sizeof(int2) * cnt, cudaMemcpyDeviceToHost));
+        for (long long i = 0; i < cnt; ++i) {
+            out[2 * i] = v[i].x;
+            out[2 * i + 1] = v[i].y;
+        }
+        return 0;
+    };
+    TRY(dump_list(ctx->m2l, ctx->n_m2l, m2l));
+    TRY(dump_list(ctx->p2p, ctx->n_p2p, p2p));
+    if (perm && n) {
+        std::vector<int> pv(n);
+        CU(cudaMemcpy(pv.data(), ctx->perm.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; ++i) perm[i] = pv[i];
+    }
+    if (scale_sorted && n && ctx->scale_sorted.p) CU(cudaMemcpy(scale_sorted, ctx->scale_sorted.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return 0;
+}
+
+int fmm_last_stats(fmm_ctx* ctx, fmm_stats* out) {
+    if (!ctx || !out) return FMM_E_INVALID;
+    *out = ctx->last;
+    return 0;
+}
+
+int fmm_destroy(fmm_ctx* ctx) {
+    if (!ctx) return 0;
+    cudaSetDevice(ctx->device);
+    Buf* all[] = {&ctx->hx, &ctx->hmu, &ctx->hpsi, &ctx->hacc, &ctx->bounds, &ctx->status, &ctx->counters, &ctx->coin,
+                  &ctx->dtotal, &ctx->keys, &ctx->keys_alt, &ctx->idx, &ctx->idx_alt, &ctx->rtmp, &ctx->xm, &ctx->perm,
+                  &ctx->xhi, &ctx->xlo, &ctx->first, &ctx->count, &ctx->child, &ctx->nchild, &ctx->parent, &ctx->level,
+                  &ctx->sr, &ctx->cr, &ctx->mass, &ctx->minscale, &ctx->split_nchild, &ctx->split_oct,
+                  &ctx->split_offs, &ctx->scan_tmp, &ctx->leaves, &ctx->leaf_flag, &ctx->leaf_pos, &ctx->rad_tmp,
+                  &ctx->M, &ctx->F, &ctx->Pw, &ctx->binom, &ctx->M1, &ctx->F1, &ctx->Ff, &ctx->front0, &ctx->front1,
+                  &ctx->m2l, &ctx->p2p, &ctx->sort_tmp, &ctx->seg_start, &ctx->seg_end, &ctx->est_m2l, &ctx->est_p2p,
+                  &ctx->m2l_seg_start, &ctx->m2l_seg_end, &ctx->psi_far, &ctx->acc_far, &ctx->psi_near,
+                  &ctx->acc_near, &ctx->scale_sorted};
+    for (Buf* b : all) release(*b);
+    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    if (ctx->h_int) cudaFreeHost(ctx->h_int);
+    if (ctx->ev_ok)
+        for (int i = 0; i < EV_N; ++i) cudaEventDestroy(ctx->ev[i]);
+    delete ctx;
+    return 0;
+}
+
+const char* fmm_strerror(int code) {
+    switch (code) {
+        case FMM_OK: return "ok";
+        case FMM_E_INVALID: return "invalid argument or input";
+        case FMM_E_OOM: return "device allocation failed";
+        case FMM_E_ADMISSION: return "footprint above the memory budget";
+        case FMM_E_CUDA: return "CUDA runtime error";
+        case FMM_E_TIMEOUT: return "bounded wait ran out";
+        case FMM_E_OVERFLOW: return "internal capacity exceeded";
+        case FMM_E_NOTFOUND: return "unknown system or ticket";
+        case FMM_E_BUSY: return "not finished";
+        default: return "unknown error";
+    }
+}
+
+const char* fmm_last_error(fmm_ctx* ctx) { return ctx ? ctx->err : ""; }
+
+const char* fmm_version(void) { return "gb3fmm 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// common.cuh -- shared device types and helpers of the GB300 FMM library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+#include <string.h>
+
+#include "../../include/gb3fmm.h"
+
+namespace gb3 {
+
+constexpr int kMaxP = 20;        // largest expansion order supported (p <= 20, Sec. 6.1)
+constexpr int kMaxLevel = 21;    // 21 bits per axis in a 63-bit Morton key
+constexpr int kWarp = 32;
+
+__host__ __device__ inline int ncoef(int p) { return (p + 1) * (p + 1); }
+// index of (n, m), -n <= m <= n, in a (p+1)^2 array of real or complex coefficients
+__host__ __device__ inline int cix(int n, int m) { return n * n + n + m; }
+
+// device status word bits (OR-ed by kernels, read by the host)
+enum : unsigned {
+    kStatInvalid = 1u,      // NaN/Inf position or negative mass
+    kStatOverflow = 2u,     // a list or frontier capacity was exceeded
+    kStatMeb = 4u,          // a smallest-ball computation found no valid support set
+};
+
+// 32-byte aligned quadruple of doubles (one 256-bit load)
+struct __align__(32) d4 {
+    double x, y, z, w;
+};
+__host__ __device__ inline d4 mk4(double x, double y, double z, double w) { return d4{x, y, z, w}; }
+
+// ---------------------------------------------------------------- complex FP64
+struct cd {
+    double re, im;
+};
+__host__ __device__ inline cd mkc(double r, double i) { return cd{r, i}; }
+__host__ __device__ inline cd operator+(cd a, cd b) { return cd{a.re + b.re, a.im + b.im}; }
+__host__ __device__ inline cd operator-(cd a, cd b) { return cd{a.re - b.re, a.im - b.im}; }
+__host__ __device__ inline cd operator*(cd a, cd b) {
+    return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__host__ __device__ inline cd operator*(double s, cd a) { return cd{s * a.re, s * a.im}; }
+__host__ __device__ inline cd conjc(cd a) { return cd{a.re, -a.im}; }
+// a += x * y
+__host__ __device__ inline void cmac(cd& a, cd x, cd y) {
+    a.re = fma(x.re, y.re, a.re);
+    a.re = fma(-x.im, y.im, a.re);
+    a.im = fma(x.re, y.im, a.im);
+    a.im = fma(x.im, y.re, a.im);
+}
+
+// Real storage of (p+1)^2 coefficients (App. A.3.2): slot cix(n, m) holds
+// Re X_n^m for m >= 0 and Im X_n^{|m|} for m < 0.  Complex values for any m
+// follow from the symmetry X_n^{-m} = (-1)^m conj(X_n^m).
+__host__ __device__ inline cd load_real_storage(const double* R, int n, int m) {
+    int am = m < 0 ? -m : m;
+    cd v = cd{R[cix(n, am)], am ? R[cix(n, -am)] : 0.0};
+    if (m < 0) {
+        v.im = -v.im;
+        if (am & 1) { v.re = -v.re; v.im = -v.im; }
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- error helpers
+#define GB3_CUDA_TRY(expr)                                                          \
+    do {                                                                            \
+        cudaError_t _e = (expr);                                                    \
+        if (_e != cudaSuccess) return ::gb3::cuda_fail(_e, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+inline unsigned grid_for(long long n, int block, long long cap = 152LL * 64) {
+    long long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+// ---------------------------------------------------------------- scans
+// Exclusive prefix sum of n int32 values (device) into out (device); the total is
+// written to *d_total (device) when not NULL.  tmp must hold scan_tmp_ints(n) ints.
+size_t scan_tmp_ints(long long n);
+void scan_exclusive_i32(const int* in, int* out, long long n, int* d_total, int* tmp, cudaStream_t s);
+
+// ---------------------------------------------------------------- warp helpers
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ inline double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// order-preserving map of a double to uint64 (for atomicMin/atomicMax on doubles)
+__device__ inline unsigned long long dbl_key(double d) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ inline double key_dbl(unsigned long long k) {
+    unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)u);
+}
+__host__ inline double key_dbl_host(unsigned long long k) {
+    unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+    double d;
+    memcpy(&d, &u, sizeof d);
+    return d;
+}
+
+}  // namespace gb3

@@ -1,0 +1,481 @@
+// interact.cu -- A9-A12 of the path: M2L (eq. 3b), L2L (eq. 5), L2P (eqs. 3a, 7),
+// P2P (eq. 1) in FP64 and in mixed precision, the p = 0 kernels of the low-order
+// f estimate (Sec. 5.3.2), and the final scatter to the caller's order.
+#include "harmonics.cuh"
+#include "kernels.cuh"
+
+namespace gb3 {
+
+// ---------------------------------------------------------------- M2L
+// One warp per sink cell B; its sources (a segment of the sorted M2L list) pass
+// through shared memory one at a time: lanes 0..p build the columns of
+// Theta(s_B - z_A), all lanes expand conj(M_A); each lane then accumulates its
+// scheduled outputs F_n^m(s_B) in registers.
+__global__ void __launch_bounds__(128) k_m2l(const int2* __restrict__ list, const int* __restrict__ seg_start,
+                                             const int* __restrict__ seg_end, int ncells, const d4* __restrict__ cen,
+                                             const double* __restrict__ M, int p, double* __restrict__ F,
+                                             LaneSched sched) {
+    extern __shared__ cd csm[];
+    const int wpb = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nco = ncoef(p);
+    cd* T = csm + (size_t)wid * 2 * nco;
+    cd* Mc = T + nco;
+    for (int B = blockIdx.x * wpb + wid; B < ncells; B += gridDim.x * wpb) {
+        const int e0 = seg_start[B], e1 = seg_end[B];
+        if (e1 <= e0) continue;
+        const d4 sB = cen[B];
+        const int cnt = sched.cnt[lane];
+        cd acc[kMaxPerLane];
+#pragma unroll
+        for (int q = 0; q < kMaxPerLane; ++q) acc[q] = mkc(0.0, 0.0);
+        for (int e = e0; e < e1; ++e) {
+            const int A = list[e].x;
+            const d4 zA = cen[A];
+            if (lane <= p) theta_column(p, lane, sB.x - zA.x, sB.y - zA.y, sB.z - zA.z, T);
+            expand_real(p, M + (size_t)A * nco, Mc, true, lane, 32);
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < kMaxPerLane; ++q)
+                if (q < cnt) acc[q] = acc[q] + contract(p, sched.n[lane][q], sched.m[lane][q], Mc, T);
+            __syncwarp();
+        }
+        double* out = F + (size_t)B * nco;
+#pragma unroll
+        for (int q = 0; q < kMaxPerLane; ++q) {
+            if (q < cnt) {
+                int n = sched.n[lane][q], m = sched.m[lane][q];
+                out[cix(n, m)] = acc[q].re;
+                if (m) out[cix(n, -m)] = acc[q].im;
+            }
+        }
+    }
+}
+
+void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, const int* /*sinks*/, int ncells,
+                const d4* cen, const double* M, int p, double* F, cudaStream_t s) {
+    if (ncells <= 0) return;
+    const int wpb = 4;
+    size_t sm = (size_t)wpb * 2 * ncoef(p) * sizeof(cd);
+    LaneSched sched = make_lane_sched(p, kSchedDown);
+    unsigned g = (unsigned)((ncells + wpb - 1) / wpb);
+    if (g > 152u * 32u) g = 152u * 32u;
+    k_m2l<<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, ncells, cen, M, p, F, sched);
+}
+
+// ---------------------------------------------------------------- L2L
+// F_n^m(s') += sum_{k<=p-n} sum_l Upsilon_k^{l*}(s - s') F_{n+k}^{m+l}(s) for every
+// cell of one level (s = its parent's centre), one warp per cell.
+__global__ void __launch_bounds__(128) k_l2l(Cells c, const d4* __restrict__ cen, int lev_begin, int lev_end, int p,
+                                             double* __restrict__ F, LaneSched sched) {
+    extern __shared__ cd csm[];
+    const int wpb = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nco = ncoef(p);
+    cd* X = csm + (size_t)wid * 2 * nco;
+    cd* Y = X + nco;
+    int cell = lev_begin + blockIdx.x * wpb + wid;
+    if (cell >= lev_end) return;
+    int par = c.parent[cell];
+    const d4 s = cen[par], sp = cen[cell];
+    if (lane <= p) upsilon_column(p, lane, s.x - sp.x, s.y - sp.y, s.z - sp.z, X, true);
+    expand_real(p, F + (size_t)par * nco, Y, false, lane, 32);
+    __syncwarp();
+    double* out = F + (size_t)cell * nco;
+    const int cnt = sched.cnt[lane];
+    for (int q = 0; q < cnt; ++q) {
+        int n = sched.n[lane][q], m = sched.m[lane][q];
+        cd v = contract(p, n, m, X, Y);
+        out[cix(n, m)] += v.re;
+        if (m) out[cix(n, -m)] += v.im;
+    }
+}
+
+void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F, cudaStream_t s) {
+    int ncl = lev_end - lev_begin;
+    if (ncl <= 0) return;
+    const int wpb = 4;
+    size_t sm = (size_t)wpb * 2 * ncoef(p) * sizeof(cd);
+    LaneSched sched = make_lane_sched(p, kSchedDown);
+    k_l2l<<<(ncl + wpb - 1) / wpb, wpb * 32, sm, s>>>(c, cen, lev_begin, lev_end, p, F, sched);
+}
+
+// ---------------------------------------------------------------- L2P
+// Psi_n^m(x_b) = sum_{k<=p-n} sum_l Upsilon_k^{l*}(s_B - x_b) F_{n+k}^{m+l}(s_B) for
+// n = 0, 1; psi = Psi_0^0, a = -(Re Psi_1^1, Im Psi_1^1, Psi_1^0).  One block per
+// leaf, F in shared memory, one thread per particle streaming the Upsilon columns.
+constexpr int kL2PThreads = 64;
+__global__ void __launch_bounds__(kL2PThreads) k_l2p(const d4* __restrict__ xm, Cells c, const d4* __restrict__ cen,
+                                                     const int* __restrict__ leaves, int nleaves, int p,
+                                                     const double* __restrict__ F, double* __restrict__ psi,
+                                                     double* __restrict__ acc) {
+    extern __shared__ cd Fc[];
+    const int nco = ncoef(p);
+    for (int t = blockIdx.x; t < nleaves; t += gridDim.x) {
+        const int cell = leaves[t];
+        __syncthreads();
+        expand_real(p, F + (size_t)cell * nco, Fc, false, threadIdx.x, blockDim.x);
+        __syncthreads();
+        const d4 s = cen[cell];
+        const int first = c.first[cell], count = c.count[cell];
+        for (int j = threadIdx.x; j < count; j += blockDim.x) {
+            const d4 xb = xm[first + j];
+            const double x = s.x - xb.x, y = s.y - xb.y, z = s.z - xb.z;
+            const double r2 = x * x + y * y + z * z;
+            double p00 = 0.0;
+            cd p10 = mkc(0.0, 0.0), p11 = mkc(0.0, 0.0);
+            cd d = mkc(1.0, 0.0);
+            for (int l = 0; l <= p; ++l) {
+                if (l > 0) {
+                    double sc = 1.0 / (2.0 * l);
+                    d = cd{sc * (x * d.re - y * d.im), sc * (x * d.im + y * d.re)};
+                }
+                const double sg = (l & 1) ? -1.0 : 1.0;
+                cd prev2 = mkc(0.0, 0.0), prev = d;
+                for (int k = l; k <= p; ++k) {
+                    cd Y;
+                    if (k == l) Y = d;
+                    else {
+                        double inv = 1.0 / (double)(k * k - l * l);
+                        double a = (2.0 * k - 1.0) * z;
+                        Y = cd{(a * prev.re - r2 * prev2.re) * inv, (a * prev.im - r2 * prev2.im) * inv};
+                        prev2 = prev;
+                        prev = Y;
+                    }
+                    const cd Xp = conjc(Y);                 // X_k^l
+                    const cd Xn = cd{sg * Y.re, sg * Y.im};  // X_k^{-l} = (-1)^l Upsilon_k^l
+                    const cd* Fk = Fc + k * k + k;
+                    if (l == 0) p00 += Xp.re * Fk[0].re - Xp.im * Fk[0].im;
+                    else p00 += 2.0 * (Xp.re * Fk[l].re - Xp.im * Fk[l].im);
+                    if (k < p) {
+                        const cd* Fk1 = Fc + (k + 1) * (k + 1) + (k + 1);
+                        cmac(p10, Xp, Fk1[l]);
+                        cmac(p11, Xp, Fk1[1 + l]);
+                        if (l > 0) {
+                            cmac(p10, Xn, Fk1[-l]);
+                            cmac(p11, Xn, Fk1[1 - l]);
+                        }
+                    }
+                }
+            }
+            const int i = first + j;
+            psi[i] = p00;
+            acc[3 * (size_t)i] = -p11.re;
+            acc[3 * (size_t)i + 1] = -p11.im;
+            acc[3 * (size_t)i + 2] = -p10.re;
+        }
+    }
+}
+
+void launch_l2p(const d4* xm, Cells c, const d4* cen, const int* leaves, int nleaves, int p, const double* F,
+                double* psi, double* acc, cudaStream_t s) {
+    if (nleaves <= 0) return;
+    size_t sm = (size_t)ncoef(p) * sizeof(cd);
+    unsigned g = nleaves < 152 * 64 ? nleaves : 152 * 64;
+    k_l2p<<<g, kL2PThreads, sm, s>>>(xm, c, cen, leaves, nleaves, p, F, psi, acc);
+}
+
+// ---------------------------------------------------------------- P2P, FP64
+// One block per sink leaf.  Its sources are the P2P segments of the leaf and of
+// all its ancestors (a pair (A, B) with B internal covers every leaf below B).
+constexpr int kP2PThreads = 64;
+
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_fp64(const d4* __restrict__ xm, Cells c,
+                                                          const int2* __restrict__ list,
+                                                          const int* __restrict__ seg_start,
+                                                          const int* __restrict__ seg_end,
+                                                          const int* __restrict__ leaves, int nleaves,
+                                                          double* __restrict__ psi, double* __restrict__ acc,
+                                                          unsigned long long* coincident) {
+    __shared__ d4 tile[kP2PThreads];
+    unsigned long long ncoin = 0;
+    for (int t = blockIdx.x; t < nleaves; t += gridDim.x) {
+        const int leaf = leaves[t];
+        const int first = c.first[leaf], count = c.count[leaf];
+        for (int s0 = 0; s0 < count; s0 += kP2PThreads) {
+            const int i = first + s0 + threadIdx.x;
+            const bool active = s0 + threadIdx.x < count;
+            d4 xb = active ? xm[i] : mk4(0, 0, 0, 0);
+            double ps = 0, ax = 0, ay = 0, az = 0;
+            for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
+                const int e0 = seg_start[cell], e1 = seg_end[cell];
+                for (int e = e0; e < e1; ++e) {
+                    const int A = list[e].x;
+                    const int af = c.first[A], an = c.count[A];
+                    for (int j0 = 0; j0 < an; j0 += kP2PThreads) {
+                        __syncthreads();
+                        if (j0 + threadIdx.x < an) tile[threadIdx.x] = xm[af + j0 + threadIdx.x];
+                        __syncthreads();
+                        const int nt = min(kP2PThreads, an - j0);
+                        if (active) {
+                            for (int j = 0; j < nt; ++j) {
+                                const d4 q = tile[j];
+                                const double dx = q.x - xb.x, dy = q.y - xb.y, dz = q.z - xb.z;
+                                const double r2 = dx * dx + dy * dy + dz * dz;
+                                if (r2 > 0.0) {
+                                    const double rinv = rsqrt(r2);
+                                    const double qm = q.w * rinv;
+                                    const double q3 = qm * rinv * rinv;
+                                    ps += qm;
+                                    ax = fma(q3, dx, ax);
+                                    ay = fma(q3, dy, ay);
+                                    az = fma(q3, dz, az);
+                                } else {
+                                    ++ncoin;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            if (active) {
+                psi[i] = ps;
+                acc[3 * (size_t)i] = ax;
+                acc[3 * (size_t)i + 1] = ay;
+                acc[3 * (size_t)i + 2] = az;
+            }
+        }
+    }
+    if (ncoin) atomicAdd(coincident, ncoin);
+}
+
+void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_start, const int* seg_end,
+                     const int* leaves, int nleaves, double* psi, double* acc, unsigned long long* coincident,
+                     cudaStream_t s) {
+    if (nleaves <= 0) return;
+    unsigned g = nleaves < 152 * 64 ? nleaves : 152 * 64;
+    k_p2p_fp64<<<g, kP2PThreads, 0, s>>>(xm, c, list, seg_start, seg_end, leaves, nleaves, psi, acc, coincident);
+}
+
+// ---------------------------------------------------------------- P2P, mixed
+// Positions as two floats (hi + lo); a source is made relative to the sink leaf's
+// centre with an error-free difference (TwoSum) when it is staged, so that
+// dx = (hi_a - hi_b) + (lo_a - lo_b) keeps its relative accuracy even for close
+// pairs.  Pair terms are FP32; each tile's FP32 sums are added to two-float
+// accumulators (TwoSum), so the sum over tiles is compensated.
+__global__ void k_split_positions(const d4* __restrict__ xm, int n, float4* __restrict__ xhi, float4* __restrict__ xlo) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        d4 v = xm[i];
+        float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
+        xhi[i] = make_float4(hx, hy, hz, (float)v.w);
+        xlo[i] = make_float4((float)(v.x - (double)hx), (float)(v.y - (double)hy), (float)(v.z - (double)hz), 0.f);
+    }
+}
+void launch_split_positions(const d4* xm, int n, float4* xhi, float4* xlo, cudaStream_t s) {
+    if (n > 0) k_split_positions<<<grid_for(n, 256), 256, 0, s>>>(xm, n, xhi, xlo);
+}
+
+struct ff {
+    float hi, lo;
+};
+__device__ inline ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff{s, e};
+}
+// (a_hi + a_lo) - (b_hi + b_lo) as a normalised two-float
+__device__ inline ff ff_sub(float ahi, float alo, float bhi, float blo) {
+    ff s = two_sum(ahi, -bhi);
+    float lo = __fadd_rn(s.lo, __fsub_rn(alo, blo));
+    float hi = __fadd_rn(s.hi, lo);
+    lo = __fsub_rn(lo, __fsub_rn(hi, s.hi));
+    return ff{hi, lo};
+}
+__device__ inline void ff_acc(ff& a, float v) {
+    ff s = two_sum(a.hi, v);
+    float lo = __fadd_rn(a.lo, s.lo);
+    a.hi = __fadd_rn(s.hi, lo);
+    a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
+}
+
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(const float4* __restrict__ xhi, const float4* __restrict__ xlo,
+                                                           Cells c, const int2* __restrict__ list,
+                                                           const int* __restrict__ seg_start,
+                                                           const int* __restrict__ seg_end,
+                                                           const int* __restrict__ leaves, int nleaves,
+                                                           double* __restrict__ psi, double* __restrict__ acc,
+                                                           unsigned long long* coincident) {
+    __shared__ float4 th[kP2PThreads];
+    __shared__ float4 tl[kP2PThreads];
+    unsigned long long ncoin = 0;
+    for (int t = blockIdx.x; t < nleaves; t += gridDim.x) {
+        const int leaf = leaves[t];
+        const int first = c.first[leaf], count = c.count[leaf];
+        const d4 sc = c.sr[leaf];
+        const float shx = (float)sc.x, shy = (float)sc.y, shz = (float)sc.z;
+        const float slx = (float)(sc.x - (double)shx), sly = (float)(sc.y - (double)shy), slz = (float)(sc.z - (double)shz);
+        for (int s0 = 0; s0 < count; s0 += kP2PThreads) {
+            const int i = first + s0 + threadIdx.x;
+            const bool active = s0 + threadIdx.x < count;
+            float bhx = 0, bhy = 0, bhz = 0, blx = 0, bly = 0, blz = 0;
+            if (active) {
+                float4 h = xhi[i], l = xlo[i];
+                ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly), rz = ff_sub(h.z, l.z, shz, slz);
+                bhx = rx.hi; blx = rx.lo; bhy = ry.hi; bly = ry.lo; bhz = rz.hi; blz = rz.lo;
+            }
+            ff aps = {0, 0}, aax = {0, 0}, aay = {0, 0}, aaz = {0, 0};
+            for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
+                const int e0 = seg_start[cell], e1 = seg_end[cell];
+                for (int e = e0; e < e1; ++e) {
+                    const int A = list[e].x;
+                    const int af = c.first[A], an = c.count[A];
+                    for (int j0 = 0; j0 < an; j0 += kP2PThreads) {
+                        __syncthreads();
+                        if (j0 + threadIdx.x < an) {
+                            float4 h = xhi[af + j0 + threadIdx.x], l = xlo[af + j0 + threadIdx.x];
+                            ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly),
+                               rz = ff_sub(h.z, l.z, shz, slz);
+                            th[threadIdx.x] = make_float4(rx.hi, ry.hi, rz.hi, h.w);
+                            tl[threadIdx.x] = make_float4(rx.lo, ry.lo, rz.lo, 0.f);
+                        }
+                        __syncthreads();
+                        const int nt = min(kP2PThreads, an - j0);
+                        if (active) {
+                            float ps = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll 8
+                            for (int j = 0; j < nt; ++j) {
+                                const float4 qh = th[j], ql = tl[j];
+                                const float dx = (qh.x - bhx) + (ql.x - blx);
+                                const float dy = (qh.y - bhy) + (ql.y - bly);
+                                const float dz = (qh.z - bhz) + (ql.z - blz);
+                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                                ncoin += (r2 == 0.f);
+                                const float qm = qh.w * rinv;
+                                const float q3 = qm * rinv * rinv;
+                                ps += qm;
+                                ax = fmaf(q3, dx, ax);
+                                ay = fmaf(q3, dy, ay);
+                                az = fmaf(q3, dz, az);
+                            }
+                            ff_acc(aps, ps);
+                            ff_acc(aax, ax);
+                            ff_acc(aay, ay);
+                            ff_acc(aaz, az);
+                        }
+                    }
+                }
+            }
+            if (active) {
+                psi[i] = (double)aps.hi + (double)aps.lo;
+                acc[3 * (size_t)i] = (double)aax.hi + (double)aax.lo;
+                acc[3 * (size_t)i + 1] = (double)aay.hi + (double)aay.lo;
+                acc[3 * (size_t)i + 2] = (double)aaz.hi + (double)aaz.lo;
+            }
+        }
+    }
+    if (ncoin) atomicAdd(coincident, ncoin);
+}
+
+void launch_p2p_mixed(const d4* /*xm*/, const float4* xhi, const float4* xlo, Cells c, const int2* list,
+                      const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* psi,
+                      double* acc, unsigned long long* coincident, cudaStream_t s) {
+    if (nleaves <= 0) return;
+    unsigned g = nleaves < 152 * 64 ? nleaves : 152 * 64;
+    k_p2p_mixed<<<g, kP2PThreads, 0, s>>>(xhi, xlo, c, list, seg_start, seg_end, leaves, nleaves, psi, acc, coincident);
+}
+
+// ---------------------------------------------------------------- low-order f estimate
+// p = 0 with the 1/r^2 kernel (Sec. 5.3.2): the "M2L" is F_B += M_A / |s_B - z_A|^2
+// about the centres of mass; one thread per sink, its segment in list order.
+__global__ void k_f_m2l(const int2* __restrict__ list, const int* __restrict__ seg_start, const int* __restrict__ seg_end,
+                        int ncells, Cells c, double* __restrict__ Ff) {
+    int B = blockIdx.x * blockDim.x + threadIdx.x;
+    if (B >= ncells) return;
+    const d4 sb = c.cr[B];
+    double f = 0;
+    for (int e = seg_start[B]; e < seg_end[B]; ++e) {
+        int A = list[e].x;
+        d4 za = c.cr[A];
+        double dx = sb.x - za.x, dy = sb.y - za.y, dz = sb.z - za.z;
+        f += c.mass[A] / (dx * dx + dy * dy + dz * dz);
+    }
+    Ff[B] = f;
+}
+void launch_f_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* Ff,
+                  cudaStream_t s) {
+    if (ncells > 0) k_f_m2l<<<(ncells + 127) / 128, 128, 0, s>>>(list, seg_start, seg_end, ncells, c, Ff);
+}
+__global__ void k_f_down(Cells c, int lev_begin, int lev_end, double* __restrict__ Ff) {
+    int cell = lev_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= lev_end) return;
+    Ff[cell] += Ff[c.parent[cell]];
+}
+void launch_f_down_level(Cells c, int lev_begin, int lev_end, double* Ff, cudaStream_t s) {
+    int ncl = lev_end - lev_begin;
+    if (ncl > 0) k_f_down<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end, Ff);
+}
+__global__ void __launch_bounds__(kP2PThreads) k_f_p2p(const d4* __restrict__ xm, Cells c, const int2* __restrict__ list,
+                                                       const int* __restrict__ seg_start, const int* __restrict__ seg_end,
+                                                       const int* __restrict__ leaves, int nleaves,
+                                                       const double* __restrict__ Ff, double* __restrict__ fout) {
+    __shared__ d4 tile[kP2PThreads];
+    for (int t = blockIdx.x; t < nleaves; t += gridDim.x) {
+        const int leaf = leaves[t];
+        const int first = c.first[leaf], count = c.count[leaf];
+        for (int s0 = 0; s0 < count; s0 += kP2PThreads) {
+            const int i = first + s0 + threadIdx.x;
+            const bool active = s0 + threadIdx.x < count;
+            d4 xb = active ? xm[i] : mk4(0, 0, 0, 0);
+            double f = 0;
+            for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
+                for (int e = seg_start[cell]; e < seg_end[cell]; ++e) {
+                    const int A = list[e].x;
+                    const int af = c.first[A], an = c.count[A];
+                    for (int j0 = 0; j0 < an; j0 += kP2PThreads) {
+                        __syncthreads();
+                        if (j0 + threadIdx.x < an) tile[threadIdx.x] = xm[af + j0 + threadIdx.x];
+                        __syncthreads();
+                        const int nt = min(kP2PThreads, an - j0);
+                        if (active)
+                            for (int j = 0; j < nt; ++j) {
+                                const d4 q = tile[j];
+                                const double dx = q.x - xb.x, dy = q.y - xb.y, dz = q.z - xb.z;
+                                const double r2 = dx * dx + dy * dy + dz * dz;
+                                if (r2 > 0.0) f += q.w / r2;
+                            }
+                    }
+                }
+            }
+            if (active) fout[i] = Ff[leaf] + f;
+        }
+    }
+}
+void launch_f_p2p(const d4* xm, Cells c, const int2* list, const int* seg_start, const int* seg_end,
+                  const int* leaves, int nleaves, const double* Ff, double* f_sorted, cudaStream_t s) {
+    if (nleaves <= 0) return;
+    unsigned g = nleaves < 152 * 64 ? nleaves : 152 * 64;
+    k_f_p2p<<<g, kP2PThreads, 0, s>>>(xm, c, list, seg_start, seg_end, leaves, nleaves, Ff, f_sorted);
+}
+
+__global__ void k_norm_scale(const double* __restrict__ af, const double* __restrict__ an, int n,
+                             double* __restrict__ scale) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double x = af[3 * (size_t)i] + an[3 * (size_t)i], y = af[3 * (size_t)i + 1] + an[3 * (size_t)i + 1],
+               z = af[3 * (size_t)i + 2] + an[3 * (size_t)i + 2];
+        scale[i] = sqrt(x * x + y * y + z * z);
+    }
+}
+void launch_norm_scale(const double* /*psi_far*/, const double* acc_far, const double* acc_near, int n, double* scale,
+                       cudaStream_t s) {
+    if (n > 0) k_norm_scale<<<grid_for(n, 256), 256, 0, s>>>(acc_far, acc_near, n, scale);
+}
+
+// ---------------------------------------------------------------- finish (A12)
+__global__ void k_finish(const double* __restrict__ pf, const double* __restrict__ af, const double* __restrict__ pn,
+                         const double* __restrict__ an, const int* __restrict__ perm, int n, double G,
+                         double* __restrict__ psi, double* __restrict__ acc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int o = perm[i];
+        psi[o] = G * (pf[i] + pn[i]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[3 * (size_t)o + d] = G * (af[3 * (size_t)i + d] + an[3 * (size_t)i + d]);
+    }
+}
+void launch_finish(const double* psi_far, const double* acc_far, const double* psi_near, const double* acc_near,
+                   const int* perm, int n, double G, double* psi, double* acc, cudaStream_t s) {
+    if (n > 0) k_finish<<<grid_for(n, 256), 256, 0, s>>>(psi_far, acc_far, psi_near, acc_near, perm, n, G, psi, acc);
+}
+
+}  // namespace gb3

@@ -1,0 +1,137 @@
+// kernels.cuh -- device data layout and the launchers of every phase of the path.
+//
+// Layout in HBM (all arrays owned by the context's workspace):
+//   particles, sorted by Morton key:  xm[n] d4 (x, y, z, mu), perm[n] int
+//   (sorted -> caller index), keys[n] uint64.
+//   cells in breadth-first order (level by level, each level in key order):
+//   first/count (particle range), child/nchild (daughters are contiguous),
+//   parent, level; sr[c] d4 (s = z, rho), cr[c] d4 (centre of mass,
+//   rho about it), mass[c], minscale[c]; expansions M[c][(p+1)^2] and
+//   F[c][(p+1)^2] in the real storage of App. A.3.2; power P[c][p+1].
+//   interaction lists: int2 (source cell, sink cell), sorted by (sink, source).
+#pragma once
+#include "common.cuh"
+
+namespace gb3 {
+
+struct Cells {
+    int* first;
+    int* count;
+    int* child;
+    int* nchild;
+    int* parent;
+    int* level;
+    d4* sr;      // expansion centre s = z and radius rho (Sec. 4, Sec. 5.1.1)
+    d4* cr;      // centre of mass and radius about it (low-order estimate)
+    double* mass;
+    double* minscale; // min over the cell's sinks of the MAC scale (eqs. 18a,b)
+};
+
+// ---------------------------------------------------------------- tree (tree.cu)
+// A1: bounding box + validation; bounds[6] = dbl_key of (min x,y,z, max x,y,z)
+void launch_bounds(const double* x, const double* mu, int n, unsigned long long* bounds,
+                   unsigned* status, cudaStream_t s);
+// A2: Morton keys and the (key, index) radix sort; returns the buffers holding the result
+void launch_keys(const double* x, int n, const unsigned long long* bounds, uint64_t* keys, int* idx,
+                 cudaStream_t s);
+size_t radix_tmp_ints(long long n);
+// LSD passes over key bits [begin_bit, end_bit); returns 1 if the result is in the _alt buffers
+int radix_sort_pairs_bits(uint64_t* keys, int* idx, uint64_t* keys_alt, int* idx_alt, long long n, int* tmp,
+                          int begin_bit, int end_bit, cudaStream_t s);
+void radix_sort_pairs(uint64_t* keys, int* idx, uint64_t* keys_alt, int* idx_alt, int n, int* tmp,
+                      cudaStream_t s);
+void launch_gather(const double* x, const double* mu, const int* idx, int n, d4* xm, int* perm,
+                   cudaStream_t s);
+// A3: one level of the top-down build.  Cells [lev_begin, lev_end) are split;
+// nchild_tmp/oct_tmp are scratch of the level's size.  Daughters are appended at
+// lev_end; *d_total receives their number.
+void launch_split_level(const uint64_t* keys, Cells c, int lev_begin, int lev_end, int level, int leaf_size,
+                        int* nchild_tmp, int* oct_tmp, int* offs_tmp, int* scan_tmp, int* d_total,
+                        cudaStream_t s);
+// A4: geometry.  Leaves: smallest enclosing ball of the particles, rho, mass,
+// centre of mass.  Internal cells of one level: smallest ball of the daughter balls,
+// mass and centre of mass from the daughters, then the exact radii over particles.
+void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves, unsigned* status,
+                          cudaStream_t s);
+void launch_internal_geometry(const d4* xm, Cells c, int lev_begin, int lev_end, int n,
+                              unsigned long long* rad_tmp, unsigned* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- upward (upward.cu)
+// P2M (eq. 3c) at leaves about centre cen (sr or cr), M2M (eq. 4) for the internal
+// cells of one level, multipole power (eq. 14).
+void launch_p2m(const d4* xm, Cells c, const d4* cen, const int* leaves, int nleaves, int p,
+                double* M, cudaStream_t s);
+void launch_m2m_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* M,
+                      cudaStream_t s);
+void launch_power(const double* M, int ncells, int p, double* P, cudaStream_t s);
+// minimum of a per-particle scale over leaves, then over the daughters of one level
+void launch_minscale_leaves(const double* scale_sorted, Cells c, const int* leaves, int nleaves,
+                            cudaStream_t s);
+void launch_minscale_level(Cells c, int lev_begin, int lev_end, cudaStream_t s);
+void launch_scale_from_caller(const double* scale, const int* perm, int n, double* scale_sorted,
+                              cudaStream_t s);
+
+// ---------------------------------------------------------------- walk (walk.cu)
+struct WalkParams {
+    int p;              // expansion order used in E_{A->B}
+    int mac;            // FMM_MAC_* or kMacEstimate
+    double eps, theta_crit, p2p_thresh;
+    const double* P;    // multipole power [nc][p+1]
+    const double* binom;// device C(p,k)
+    int use_com;        // radii/centres from cr (estimator) instead of sr
+};
+constexpr int kMacEstimate = 3;  // theta < 1 only (low-order estimate, Sec. 5.3.2)
+
+struct WalkBuffers {
+    int2* front[2];
+    long long front_cap;
+    int2* m2l;
+    long long m2l_cap;
+    int2* p2p;
+    long long p2p_cap;
+    unsigned long long* counters;  // [0] next frontier, [1] m2l, [2] p2p, [3] overflow flag
+};
+void launch_walk_step(Cells c, WalkParams wp, const int2* front_in, long long nfront, int2* front_out,
+                      WalkBuffers wb, cudaStream_t s);
+// sort a pair list by (sink, source), then mark per-sink segments [seg_start, seg_end)
+size_t list_sort_tmp_bytes(long long npairs);
+void sort_pairs_by_sink(int2* list, long long npairs, int ncells, void* tmp, cudaStream_t s);
+void launch_segments(const int2* list, long long npairs, int ncells, int* seg_start, int* seg_end,
+                     cudaStream_t s);
+
+// ---------------------------------------------------------------- interactions (interact.cu)
+void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, const int* sinks, int nsinks,
+                const d4* cen, const double* M, int p, double* F, cudaStream_t s);
+void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F,
+                      cudaStream_t s);
+// L2P (eqs. 3a, 7) for every particle of every leaf: psi_far, acc_far (sorted order)
+void launch_l2p(const d4* xm, Cells c, const d4* cen, const int* leaves, int nleaves, int p,
+                const double* F, double* psi, double* acc, cudaStream_t s);
+// P2P (eq. 1) into psi_near/acc_near (sorted order): every leaf takes the sources of
+// its own P2P segment and those of its ancestors' segments.
+void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_start,
+                     const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc,
+                     unsigned long long* coincident, cudaStream_t s);
+void launch_p2p_mixed(const d4* xm, const float4* xhi, const float4* xlo, Cells c, const int2* list,
+                      const int* seg_start, const int* seg_end, const int* leaves, int nleaves,
+                      double* psi, double* acc, unsigned long long* coincident, cudaStream_t s);
+void launch_split_positions(const d4* xm, int n, float4* xhi, float4* xlo, cudaStream_t s);
+// low-order f estimate (p = 0, 1/r^2 kernel): M2L, pass-down, P2P, evaluation
+void launch_f_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* Ff,
+                  cudaStream_t s);
+void launch_f_down_level(Cells c, int lev_begin, int lev_end, double* Ff, cudaStream_t s);
+void launch_f_p2p(const d4* xm, Cells c, const int2* list, const int* seg_start, const int* seg_end,
+                  const int* leaves, int nleaves, const double* Ff, double* f_sorted, cudaStream_t s);
+// |far + near| of the p = 1 estimate into the per-particle scale
+void launch_norm_scale(const double* psi_far, const double* acc_far, const double* acc_near, int n,
+                       double* scale, cudaStream_t s);
+// combine far + near, multiply by G and scatter to the caller's order (A12)
+void launch_finish(const double* psi_far, const double* acc_far, const double* psi_near,
+                   const double* acc_near, const int* perm, int n, double G, double* psi, double* acc,
+                   cudaStream_t s);
+
+// ---------------------------------------------------------------- direct (direct.cu)
+void launch_direct(const double* x, const double* mu, int n, double G, const int64_t* sinks, int nsinks,
+                   double* psi, double* acc, double* f, cudaStream_t s);
+
+}  // namespace gb3

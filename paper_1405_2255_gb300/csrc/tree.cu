@@ -1,0 +1,653 @@
+// tree.cu -- A1-A4 of the path: bounds and validation, Morton keys, radix sort,
+// the top-down oct-tree build, and the cell geometry (expansion centres, radii,
+// masses, centres of mass).
+//
+// Compiled with --fmad=false: the decision quantities (keys, centres, radii) are
+// plain IEEE FP64 sums and products, so that the tree and the acceptance tests do
+// not depend on how a compiler contracts them.
+#include "kernels.cuh"
+
+namespace gb3 {
+
+// ------------------------------------------------------------------ A1 bounds
+__global__ void k_bounds_init(unsigned long long* b) {
+    int i = threadIdx.x;
+    if (i < 3) b[i] = ~0ull;
+    else if (i < 6) b[i] = 0ull;
+}
+
+__global__ void k_bounds(const double* __restrict__ x, const double* __restrict__ mu, int n,
+                         unsigned long long* bounds, unsigned* status) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double v[3] = {x[3 * (long long)i], x[3 * (long long)i + 1], x[3 * (long long)i + 2]};
+        double m = mu[i];
+        bad |= !(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(m) && m >= 0.0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = fmin(lo[d], v[d]);
+            hi[d] = fmax(hi[d], v[d]);
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = warp_min(lo[d]);
+        hi[d] = warp_max(hi[d]);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatInvalid);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (lo[d] <= hi[d]) {
+                atomicMin(&bounds[d], dbl_key(lo[d]));
+                atomicMax(&bounds[3 + d], dbl_key(hi[d]));
+            }
+        }
+    }
+}
+
+void launch_bounds(const double* x, const double* mu, int n, unsigned long long* bounds, unsigned* status,
+                   cudaStream_t s) {
+    k_bounds_init<<<1, 32, 0, s>>>(bounds);
+    if (n > 0) k_bounds<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, mu, n, bounds, status);
+}
+
+// ------------------------------------------------------------------ A2 keys
+__device__ inline uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffull;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+// Root cube: side = max extent * (1 + 2^-20), anchored at the lower corner.
+__device__ inline void root_cube(const unsigned long long* bounds, double lo[3], double& side) {
+    double ext = 0;
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = key_dbl(bounds[d]);
+        double e = key_dbl(bounds[3 + d]) - lo[d];
+        if (e > ext) ext = e;
+    }
+    side = ext * (1.0 + 0x1p-20);
+    if (!(side > 0)) side = 1.0;
+}
+
+__global__ void k_keys(const double* __restrict__ x, int n, const unsigned long long* __restrict__ bounds,
+                       uint64_t* __restrict__ keys, int* __restrict__ idx) {
+    double lo[3], side;
+    root_cube(bounds, lo, side);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t q[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double t = (x[3 * (long long)i + d] - lo[d]) / side;
+            double u = t * 2097152.0;
+            double f = floor(u);
+            long long v = (long long)f;
+            if (v < 0) v = 0;
+            if (v > 2097151) v = 2097151;
+            q[d] = (uint32_t)v;
+        }
+        keys[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+        idx[i] = i;
+    }
+}
+
+void launch_keys(const double* x, int n, const unsigned long long* bounds, uint64_t* keys, int* idx,
+                 cudaStream_t s) {
+    if (n > 0) k_keys<<<grid_for(n, 256), 256, 0, s>>>(x, n, bounds, keys, idx);
+}
+
+// ------------------------------------------------------------------ A2 radix sort
+// Stable LSD radix sort of (key, index) pairs, 8 bits per pass, 8 passes over the
+// 63 key bits.  Per pass: a digit histogram per tile, a device-wide exclusive scan
+// in digit-major order, and a stable scatter that ranks equal digits inside the
+// tile in item order with warp match masks.
+constexpr int kRsThreads = 256;
+constexpr int kRsRounds = 16;
+constexpr int kRsTile = kRsThreads * kRsRounds;
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t* __restrict__ keys, int n, int shift,
+                                                        int* __restrict__ hist, int nblocks) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    long long base = (long long)blockIdx.x * kRsTile;
+    for (int r = 0; r < kRsRounds; ++r) {
+        long long i = base + r * kRsThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* __restrict__ kin,
+                                                           const int* __restrict__ vin,
+                                                           uint64_t* __restrict__ kout, int* __restrict__ vout,
+                                                           int n, int shift, const int* __restrict__ offs,
+                                                           int nblocks) {
+    __shared__ int running[256];
+    __shared__ int wc[kRsThreads / 32][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    running[threadIdx.x] = offs[threadIdx.x * nblocks + blockIdx.x];
+    long long base = (long long)blockIdx.x * kRsTile;
+    for (int r = 0; r < kRsRounds; ++r) {
+#pragma unroll
+        for (int k = 0; k < kRsThreads / 32; ++k) wc[k][threadIdx.x] = 0;
+        __syncthreads();
+        long long i = base + r * kRsThreads + threadIdx.x;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0;
+        int val = valid ? vin[i] : 0;
+        int d = valid ? (int)((key >> shift) & 255) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & ((1u << lane) - 1));
+        int leader = __ffs(peers) - 1;
+        if (valid && lane == leader) wc[w][d] = __popc(peers);
+        __syncthreads();
+        {   // per digit: exclusive prefix over the warps of this round
+            int dg = threadIdx.x;
+            int b = running[dg];
+#pragma unroll
+            for (int k = 0; k < kRsThreads / 32; ++k) {
+                int c = wc[k][dg];
+                wc[k][dg] = b;
+                b += c;
+            }
+            running[dg] = b;
+        }
+        __syncthreads();
+        if (valid) {
+            int dst = wc[w][d] + rank;
+            kout[dst] = key;
+            vout[dst] = val;
+        }
+        __syncthreads();
+    }
+}
+
+size_t radix_tmp_ints(long long n) {
+    long long nb = (n + kRsTile - 1) / kRsTile;
+    if (nb < 1) nb = 1;
+    return (size_t)(2 * 256 * nb) + scan_tmp_ints(256 * nb) + 8;
+}
+
+int radix_sort_pairs_bits(uint64_t* keys, int* idx, uint64_t* keys_alt, int* idx_alt, long long n, int* tmp,
+                          int begin_bit, int end_bit, cudaStream_t s) {
+    if (n <= 1) return 0;
+    int nb = (int)((n + kRsTile - 1) / kRsTile);
+    int* hist = tmp;
+    int* offs = tmp + 256 * nb;
+    int* stmp = tmp + 2 * 256 * nb;
+    uint64_t *ka = keys, *kb = keys_alt;
+    int *va = idx, *vb = idx_alt;
+    int flips = 0;
+    for (int shift = begin_bit; shift < end_bit; shift += 8) {
+        k_rs_hist<<<nb, kRsThreads, 0, s>>>(ka, (int)n, shift, hist, nb);
+        scan_exclusive_i32(hist, offs, 256LL * nb, nullptr, stmp, s);
+        k_rs_scatter<<<nb, kRsThreads, 0, s>>>(ka, va, kb, vb, (int)n, shift, offs, nb);
+        uint64_t* tk = ka; ka = kb; kb = tk;
+        int* tv = va; va = vb; vb = tv;
+        flips ^= 1;
+    }
+    return flips;
+}
+
+void radix_sort_pairs(uint64_t* keys, int* idx, uint64_t* keys_alt, int* idx_alt, int n, int* tmp,
+                      cudaStream_t s) {
+    // 8 passes over the 63 key bits: the result is back in (keys, idx)
+    radix_sort_pairs_bits(keys, idx, keys_alt, idx_alt, n, tmp, 0, 64, s);
+}
+
+__global__ void k_gather(const double* __restrict__ x, const double* __restrict__ mu, const int* __restrict__ idx,
+                         int n, d4* __restrict__ xm, int* __restrict__ perm) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int j = idx[i];
+        xm[i] = mk4(x[3 * (long long)j], x[3 * (long long)j + 1], x[3 * (long long)j + 2], mu[j]);
+        perm[i] = j;
+    }
+}
+
+void launch_gather(const double* x, const double* mu, const int* idx, int n, d4* xm, int* perm,
+                   cudaStream_t s) {
+    if (n > 0) k_gather<<<grid_for(n, 256), 256, 0, s>>>(x, mu, idx, n, xm, perm);
+}
+
+// ------------------------------------------------------------------ A3 oct-tree
+// A cell of level L holding more than leaf_size particles (and L < 21) is split
+// into its non-empty octants, in key order.  One warp per cell; lane o < 8 finds
+// the first particle whose level-(L+1) digit is >= o by binary search.
+__global__ void k_split(const uint64_t* __restrict__ keys, Cells c, int lev_begin, int lev_end, int level,
+                        int leaf_size, int* __restrict__ nchild_tmp, int* __restrict__ oct_tmp) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    int cell = lev_begin + warp;
+    if (cell >= lev_end) return;
+    int first = c.first[cell], count = c.count[cell];
+    bool split = count > leaf_size && level < kMaxLevel;
+    int b = first + count;
+    if (split && lane < 8) {
+        int shift = 3 * (kMaxLevel - (level + 1));
+        int lo = first, hi = first + count;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            int dg = (int)((keys[mid] >> shift) & 7);
+            if (dg < lane) lo = mid + 1;
+            else hi = mid;
+        }
+        b = lo;
+    }
+    int bnext = __shfl_down_sync(0xffffffffu, b, 1);
+    int size = (lane < 8) ? ((lane == 7 ? first + count : bnext) - b) : 0;
+    unsigned nonempty = __ballot_sync(0xffffffffu, split && lane < 8 && size > 0);
+    if (lane < 8) oct_tmp[9 * (long long)warp + lane] = b;
+    if (lane == 8) oct_tmp[9 * (long long)warp + 8] = first + count;
+    if (lane == 0) nchild_tmp[warp] = split ? __popc(nonempty) : 0;
+}
+
+__global__ void k_write_children(Cells c, int lev_begin, int lev_end, int level, const int* __restrict__ nchild_tmp,
+                                 const int* __restrict__ oct_tmp, const int* __restrict__ offs) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    int cell = lev_begin + w;
+    if (cell >= lev_end) return;
+    int nc = nchild_tmp[w];
+    int base = lev_end + offs[w];
+    c.nchild[cell] = nc;
+    c.child[cell] = nc ? base : -1;
+    if (!nc) return;
+    int k = 0;
+    for (int o = 0; o < 8; ++o) {
+        int b0 = oct_tmp[9 * (long long)w + o], b1 = oct_tmp[9 * (long long)w + o + 1];
+        if (b1 > b0) {
+            int d = base + k++;
+            c.first[d] = b0;
+            c.count[d] = b1 - b0;
+            c.level[d] = level + 1;
+            c.parent[d] = cell;
+            c.nchild[d] = 0;
+            c.child[d] = -1;
+        }
+    }
+}
+
+void launch_split_level(const uint64_t* keys, Cells c, int lev_begin, int lev_end, int level, int leaf_size,
+                        int* nchild_tmp, int* oct_tmp, int* offs_tmp, int* scan_tmp, int* d_total,
+                        cudaStream_t s) {
+    int ncl = lev_end - lev_begin;
+    k_split<<<(unsigned)(((long long)ncl * 32 + 255) / 256), 256, 0, s>>>(keys, c, lev_begin, lev_end, level,
+                                                                         leaf_size, nchild_tmp, oct_tmp);
+    scan_exclusive_i32(nchild_tmp, offs_tmp, ncl, d_total, scan_tmp, s);
+    k_write_children<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, level, nchild_tmp, oct_tmp, offs_tmp);
+}
+
+// ------------------------------------------------------------------ A4 geometry
+// Smallest enclosing balls (Sec. 5.1.1).  support_ball: the smallest ball whose
+// boundary touches each of k <= 4 balls (c_i, r_i) from inside, centre in the
+// affine hull of the c_i: with u = c - c_0 = sum_j lam_j d_j, d_j = c_j - c_0,
+// the tangency conditions give G lam = a + R b (G the Gram matrix of the d_j,
+// a_j = (|d_j|^2 - r_j^2 + r_0^2)/2, b_j = r_j - r_0), and |u| = R - r_0 gives a
+// quadratic in R.  With all r_i = 0 it is the circumsphere of the points.
+__device__ bool solve_small_dev(int k, double A[3][3], double b0[3], double b1[3], double x0[3], double x1[3]) {
+    double M[3][5];
+    double scale = 0;
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j)
+            if (fabs(A[i][j]) > scale) scale = fabs(A[i][j]);
+    if (scale == 0) return false;
+    for (int i = 0; i < k; ++i) {
+        for (int j = 0; j < k; ++j) M[i][j] = A[i][j];
+        M[i][k] = b0[i];
+        M[i][k + 1] = b1[i];
+    }
+    for (int col = 0; col < k; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < k; ++r)
+            if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+        if (fabs(M[piv][col]) <= 1e-12 * scale) return false;
+        if (piv != col)
+            for (int j = 0; j < k + 2; ++j) {
+                double t = M[col][j];
+                M[col][j] = M[piv][j];
+                M[piv][j] = t;
+            }
+        for (int r = col + 1; r < k; ++r) {
+            double fct = M[r][col] / M[col][col];
+            for (int j = col; j < k + 2; ++j) M[r][j] -= fct * M[col][j];
+        }
+    }
+    for (int r = k - 1; r >= 0; --r) {
+        double s0 = M[r][k], s1 = M[r][k + 1];
+        for (int j = r + 1; j < k; ++j) {
+            s0 -= M[r][j] * x0[j];
+            s1 -= M[r][j] * x1[j];
+        }
+        x0[r] = s0 / M[r][r];
+        x1[r] = s1 / M[r][r];
+    }
+    return true;
+}
+
+__device__ bool support_ball_dev(int k, const double (*c)[3], const double* r, double oc[3], double& orad) {
+    if (k == 1) {
+        oc[0] = c[0][0]; oc[1] = c[0][1]; oc[2] = c[0][2];
+        orad = r[0];
+        return true;
+    }
+    int q = k - 1;
+    double D[3][3], G[3][3], a[3], b[3], la[3], lb[3];
+    for (int j = 0; j < q; ++j)
+        for (int d = 0; d < 3; ++d) D[j][d] = c[j + 1][d] - c[0][d];
+    for (int i = 0; i < q; ++i) {
+        for (int j = 0; j < q; ++j) G[i][j] = D[i][0] * D[j][0] + D[i][1] * D[j][1] + D[i][2] * D[j][2];
+        a[i] = 0.5 * (G[i][i] - r[i + 1] * r[i + 1] + r[0] * r[0]);
+        b[i] = r[i + 1] - r[0];
+    }
+    if (!solve_small_dev(q, G, a, b, la, lb)) return false;
+    double A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    for (int j = 0; j < q; ++j)
+        for (int d = 0; d < 3; ++d) {
+            A[d] += la[j] * D[j][d];
+            B[d] += lb[j] * D[j][d];
+        }
+    double qa = B[0] * B[0] + B[1] * B[1] + B[2] * B[2] - 1.0;
+    double qb = A[0] * B[0] + A[1] * B[1] + A[2] * B[2] + r[0];
+    double qc = A[0] * A[0] + A[1] * A[1] + A[2] * A[2] - r[0] * r[0];
+    double rmax = r[0];
+    for (int i = 1; i < k; ++i)
+        if (r[i] > rmax) rmax = r[i];
+    double R;
+    if (fabs(qa) < 1e-14) {
+        if (qb == 0) return false;
+        R = -qc / (2.0 * qb);
+    } else {
+        double disc = qb * qb - qa * qc;
+        if (disc < 0) {
+            if (disc < -1e-12 * (qb * qb + fabs(qa * qc))) return false;
+            disc = 0;
+        }
+        double sq = sqrt(disc);
+        double r1 = (-qb - sq) / qa, r2 = (-qb + sq) / qa;
+        double lo = r1 < r2 ? r1 : r2, hi = r1 < r2 ? r2 : r1;
+        double tol = 1e-12 * (fabs(rmax) + 1e-300);
+        if (lo >= rmax - tol) R = lo;
+        else if (hi >= rmax - tol) R = hi;
+        else return false;
+    }
+    if (!(R >= 0) || R < rmax - 1e-12 * (rmax + 1e-300)) return false;
+    for (int d = 0; d < 3; ++d) oc[d] = c[0][d] + A[d] + R * B[d];
+    orad = R;
+    return true;
+}
+
+__device__ inline double dist3_dev(const double a[3], const double b[3]) {
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+// Welzl's b_md(empty, R): the smallest ball with the support points on its boundary
+__device__ void trivial_ball_dev(int nr, const double (*R)[3], double c[3], double& rad) {
+    const double zr[4] = {0, 0, 0, 0};
+    if (nr == 0) {
+        c[0] = c[1] = c[2] = 0;
+        rad = -1.0;
+        return;
+    }
+    if (support_ball_dev(nr, R, zr, c, rad)) return;
+    double best = -1;
+    for (int mask = 1; mask < (1 << nr); ++mask) {
+        double sub[4][3];
+        int k = 0;
+        for (int i = 0; i < nr; ++i)
+            if (mask & (1 << i)) {
+                for (int d = 0; d < 3; ++d) sub[k][d] = R[i][d];
+                ++k;
+            }
+        double cc[3], rr;
+        if (!support_ball_dev(k, sub, zr, cc, rr)) continue;
+        bool ok = true;
+        for (int i = 0; i < nr; ++i)
+            if (dist3_dev(R[i], cc) > rr * (1 + 1e-12) + 1e-300) {
+                ok = false;
+                break;
+            }
+        if (ok && (best < 0 || rr < best)) {
+            best = rr;
+            c[0] = cc[0]; c[1] = cc[1]; c[2] = cc[2];
+            rad = rr;
+        }
+    }
+}
+
+__device__ inline bool in_ball_dev(const double p[3], const double c[3], double rad) {
+    if (rad < 0) return false;
+    return dist3_dev(p, c) <= rad * (1.0 + 1e-12);
+}
+
+__device__ inline void ld3(const d4* xm, int i, double p[3]) {
+    d4 v = xm[i];
+    p[0] = v.x; p[1] = v.y; p[2] = v.z;
+}
+
+// Welzl's recursion for points, unrolled into its four nested levels: each level
+// runs over a prefix of the points and restarts the next level with one more
+// support point when a point falls outside.
+__device__ void meb_points_dev(const d4* P, int n, double c[3], double& rad) {
+    double R[4][3], q[3];
+    double c0[3], r0;
+    trivial_ball_dev(0, R, c0, r0);
+    for (int i = 0; i < n; ++i) {
+        ld3(P, i, q);
+        if (in_ball_dev(q, c0, r0)) continue;
+        for (int d = 0; d < 3; ++d) R[0][d] = q[d];
+        double c1[3], r1;
+        trivial_ball_dev(1, R, c1, r1);
+        for (int j = 0; j < i; ++j) {
+            ld3(P, j, q);
+            if (in_ball_dev(q, c1, r1)) continue;
+            for (int d = 0; d < 3; ++d) R[1][d] = q[d];
+            double c2[3], r2;
+            trivial_ball_dev(2, R, c2, r2);
+            for (int k = 0; k < j; ++k) {
+                ld3(P, k, q);
+                if (in_ball_dev(q, c2, r2)) continue;
+                for (int d = 0; d < 3; ++d) R[2][d] = q[d];
+                double c3[3], r3;
+                trivial_ball_dev(3, R, c3, r3);
+                for (int l = 0; l < k; ++l) {
+                    ld3(P, l, q);
+                    if (in_ball_dev(q, c3, r3)) continue;
+                    for (int d = 0; d < 3; ++d) R[3][d] = q[d];
+                    trivial_ball_dev(4, R, c3, r3);
+                }
+                for (int d = 0; d < 3; ++d) c2[d] = c3[d];
+                r2 = r3;
+            }
+            for (int d = 0; d < 3; ++d) c1[d] = c2[d];
+            r1 = r2;
+        }
+        for (int d = 0; d < 3; ++d) c0[d] = c1[d];
+        r0 = r1;
+    }
+    for (int d = 0; d < 3; ++d) c[d] = c0[d];
+    rad = r0 < 0 ? 0 : r0;
+}
+
+__global__ void k_leaf_geometry(const d4* __restrict__ xm, Cells c, const int* __restrict__ leaves,
+                                int nleaves, unsigned* status) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nleaves) return;
+    int cell = leaves[t];
+    int first = c.first[cell], count = c.count[cell];
+    const d4* X = xm + first;
+    double s[3], rad;
+    meb_points_dev(X, count, s, rad);
+    double rmax = 0, m = 0, mx[3] = {0, 0, 0};
+    for (int i = 0; i < count; ++i) {
+        double p[3];
+        ld3(X, i, p);
+        double r = dist3_dev(p, s);
+        if (r > rmax) rmax = r;
+        double w = X[i].w;
+        m += w;
+        for (int k = 0; k < 3; ++k) mx[k] += w * p[k];
+    }
+    double com[3];
+    for (int k = 0; k < 3; ++k) com[k] = (m > 0) ? mx[k] / m : s[k];
+    double rc = 0;
+    for (int i = 0; i < count; ++i) {
+        double p[3];
+        ld3(X, i, p);
+        double r = dist3_dev(p, com);
+        if (r > rc) rc = r;
+    }
+    c.sr[cell] = mk4(s[0], s[1], s[2], rmax);
+    c.cr[cell] = mk4(com[0], com[1], com[2], rc);
+    c.mass[cell] = m;
+}
+
+void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves, unsigned* status,
+                          cudaStream_t s) {
+    if (nleaves > 0) k_leaf_geometry<<<(nleaves + 127) / 128, 128, 0, s>>>(xm, c, leaves, nleaves, status);
+}
+
+// Internal cells of one level: smallest ball enclosing the daughter balls (s_d, rho_d),
+// as the smallest support ball (over all subsets of 1..4 daughters, enumerated by
+// mask) that contains every daughter ball.  One warp per cell, lanes take masks;
+// ties go to the smaller mask.
+__global__ void k_internal_meb(Cells c, int lev_begin, int lev_end, unsigned* status) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    int cell = lev_begin + warp;
+    if (cell >= lev_end) return;
+    int nch = c.nchild[cell];
+    if (nch == 0) return;  // leaves are done
+    int ch = c.child[cell];
+    double cen[8][3], rad[8];
+    double m = 0, mx[3] = {0, 0, 0};
+    for (int i = 0; i < nch; ++i) {
+        d4 v = c.sr[ch + i];
+        cen[i][0] = v.x; cen[i][1] = v.y; cen[i][2] = v.z;
+        rad[i] = v.w;
+        double md = c.mass[ch + i];
+        d4 cm = c.cr[ch + i];
+        m += md;
+        mx[0] += md * cm.x; mx[1] += md * cm.y; mx[2] += md * cm.z;
+    }
+    double best = -1, bc[3] = {0, 0, 0};
+    int bmask = 1 << 30;
+    for (int mask = 1 + lane; mask < (1 << nch); mask += 32) {
+        if (__popc(mask) > 4) continue;
+        double sc[4][3], sr[4];
+        int k = 0;
+        for (int i = 0; i < nch; ++i)
+            if (mask & (1 << i)) {
+                for (int d = 0; d < 3; ++d) sc[k][d] = cen[i][d];
+                sr[k] = rad[i];
+                ++k;
+            }
+        double cc[3], rr;
+        if (!support_ball_dev(k, sc, sr, cc, rr)) continue;
+        bool ok = true;
+        for (int i = 0; i < nch; ++i)
+            if (dist3_dev(cen[i], cc) + rad[i] > rr * (1 + 1e-12) + 1e-300) {
+                ok = false;
+                break;
+            }
+        if (ok && (best < 0 || rr < best)) {
+            best = rr;
+            bmask = mask;
+            bc[0] = cc[0]; bc[1] = cc[1]; bc[2] = cc[2];
+        }
+    }
+    // warp argmin of (radius, mask)
+    for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int om = __shfl_xor_sync(0xffffffffu, bmask, o);
+        double o0 = __shfl_xor_sync(0xffffffffu, bc[0], o);
+        double o1 = __shfl_xor_sync(0xffffffffu, bc[1], o);
+        double o2 = __shfl_xor_sync(0xffffffffu, bc[2], o);
+        bool take = (ob >= 0) && (best < 0 || ob < best || (ob == best && om < bmask));
+        if (take) {
+            best = ob; bmask = om;
+            bc[0] = o0; bc[1] = o1; bc[2] = o2;
+        }
+    }
+    if (lane == 0) {
+        if (best < 0) {  // no valid support set (should not happen): fall back to the first daughter's centre
+            atomicOr(status, kStatMeb);
+            bc[0] = cen[0][0]; bc[1] = cen[0][1]; bc[2] = cen[0][2];
+        }
+        double com[3];
+        for (int k = 0; k < 3; ++k) com[k] = (m > 0) ? mx[k] / m : bc[k];
+        c.sr[cell] = mk4(bc[0], bc[1], bc[2], 0.0);
+        c.cr[cell] = mk4(com[0], com[1], com[2], 0.0);
+        c.mass[cell] = m;
+    }
+}
+
+// exact radii of the internal cells of one level: max over their particles of
+// |x - s| and |x - com|; particle-parallel with a warp max per run of equal cells
+__global__ void k_internal_radii(const d4* __restrict__ xm, Cells c, int lev_begin, int lev_end,
+                                 unsigned long long* __restrict__ rad_tmp) {
+    // the level's cells cover particles [pbeg, pend) (cells of a level are in key order)
+    const int pbeg = c.first[lev_begin];
+    const int pend = c.first[lev_end - 1] + c.count[lev_end - 1];
+    for (int i0 = blockIdx.x * blockDim.x; i0 < pend - pbeg; i0 += gridDim.x * blockDim.x) {
+        int i = pbeg + i0 + threadIdx.x;
+        int cell = -1;
+        double d2 = 0, e2 = 0;
+        if (i < pend) {
+            int lo = lev_begin, hi = lev_end - 1;  // last cell with first <= i
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (c.first[mid] <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            if (i >= c.first[lo] && i < c.first[lo] + c.count[lo] && c.nchild[lo] > 0) {
+                cell = lo;
+                d4 p = xm[i];
+                d4 s = c.sr[cell], m = c.cr[cell];
+                double dx = p.x - s.x, dy = p.y - s.y, dz = p.z - s.z;
+                d2 = dx * dx + dy * dy + dz * dz;
+                double ex = p.x - m.x, ey = p.y - m.y, ez = p.z - m.z;
+                e2 = ex * ex + ey * ey + ez * ez;
+            }
+        }
+        int c0 = __shfl_sync(0xffffffffu, cell, 0);
+        if (__all_sync(0xffffffffu, cell == c0)) {
+            d2 = warp_max(d2);
+            e2 = warp_max(e2);
+            if ((threadIdx.x & 31) == 0 && c0 >= 0) {
+                atomicMax(&rad_tmp[2 * (c0 - lev_begin)], dbl_key(d2));
+                atomicMax(&rad_tmp[2 * (c0 - lev_begin) + 1], dbl_key(e2));
+            }
+        } else if (cell >= 0) {
+            atomicMax(&rad_tmp[2 * (cell - lev_begin)], dbl_key(d2));
+            atomicMax(&rad_tmp[2 * (cell - lev_begin) + 1], dbl_key(e2));
+        }
+    }
+}
+
+__global__ void k_internal_radii_finish(Cells c, int lev_begin, int lev_end,
+                                        const unsigned long long* __restrict__ rad_tmp) {
+    int cell = lev_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= lev_end || c.nchild[cell] == 0) return;
+    double d2 = key_dbl(rad_tmp[2 * (cell - lev_begin)]);
+    double e2 = key_dbl(rad_tmp[2 * (cell - lev_begin) + 1]);
+    c.sr[cell].w = sqrt(d2);
+    c.cr[cell].w = sqrt(e2);
+}
+
+void launch_internal_geometry(const d4* xm, Cells c, int lev_begin, int lev_end, int n,
+                              unsigned long long* rad_tmp, unsigned* status, cudaStream_t s) {
+    int ncl = lev_end - lev_begin;
+    if (ncl <= 0) return;
+    k_internal_meb<<<(unsigned)(((long long)ncl * 32 + 255) / 256), 256, 0, s>>>(c, lev_begin, lev_end, status);
+    cudaMemsetAsync(rad_tmp, 0, sizeof(unsigned long long) * 2 * ncl, s);
+    k_internal_radii<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xm, c, lev_begin, lev_end, rad_tmp);
+    k_internal_radii_finish<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, rad_tmp);
+}
+
+}  // namespace gb3

@@ -1,0 +1,178 @@
+// walk.cu -- A8 of the path: the one-sided dual tree walk (Sec. 2.2.2) with the
+// acceptance criteria of eqs. (9), (15)-(18), run breadth-first: every step takes
+// the current frontier of cell pairs and writes M2L pairs, P2P pairs and the next
+// frontier.  Afterwards the lists are sorted by (sink, source), which fixes the
+// order in which every sink accumulates its interactions.
+#include "kernels.cuh"
+
+namespace gb3 {
+
+// exclusive warp prefix of v; returns the warp total in *tot
+__device__ inline unsigned warp_excl(unsigned v, unsigned* tot) {
+    const int lane = threadIdx.x & 31;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    *tot = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+// reserve `mine` slots in a list for each lane; returns the lane's first slot or -1 on overflow
+__device__ inline long long warp_reserve(unsigned mine, unsigned long long* counter, long long cap,
+                                         unsigned long long* overflow) {
+    unsigned tot;
+    unsigned ex = warp_excl(mine, &tot);
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == 31 && tot) base = atomicAdd(counter, (unsigned long long)tot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    if (tot && (long long)(base + tot) > cap) {
+        if ((threadIdx.x & 31) == 31) atomicOr(overflow, 1ull);
+        return -1;
+    }
+    return (long long)(base + ex);
+}
+
+enum : int { kActNone = 0, kActM2L, kActP2P, kActSelf, kActSplitA, kActSplitB };
+
+__global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in, long long nfront,
+                       int2* __restrict__ front_out, WalkBuffers wb) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < nfront; base += stride) {
+        long long i = base + threadIdx.x;
+        int act = kActNone, A = -1, B = -1, nchA = 0, nchB = 0, chA = 0, chB = 0;
+        if (i < nfront) {
+            int2 pr = front_in[i];
+            A = pr.x;
+            B = pr.y;
+            int cntA = c.count[A], cntB = c.count[B];
+            nchA = c.nchild[A];
+            nchB = c.nchild[B];
+            chA = c.child[A];
+            chB = c.child[B];
+            if ((double)cntA * (double)cntB < wp.p2p_thresh) {
+                act = kActP2P;  // reading R-p2p: direct summation is preferable
+            } else if (A == B) {
+                act = nchA ? kActSelf : kActP2P;
+            } else {
+                d4 za = wp.use_com ? c.cr[A] : c.sr[A];
+                d4 sb = wp.use_com ? c.cr[B] : c.sr[B];
+                double ra = za.w, rb = sb.w;
+                double dx = sb.x - za.x, dy = sb.y - za.y, dz = sb.z - za.z;
+                double r = sqrt(dx * dx + dy * dy + dz * dz);
+                double theta = (ra + rb) / r;  // eq. (9)
+                bool accept;
+                if (wp.mac == FMM_MAC_THETA) accept = theta < wp.theta_crit;
+                else if (!(theta < 1.0)) accept = false;
+                else if (wp.mac == kMacEstimate) accept = true;
+                else {
+                    // E~_{A->B} M_A / r^2 (eqs. 15-17) without dividing by M_A:
+                    // 8 max/(rhoA+rhoB) * sum_k C(p,k) P_k rhoB^{p-k} / r^{p+2}
+                    const double* P = wp.P + (size_t)A * (wp.p + 1);
+                    double rinv = 1.0 / r, u = rb * rinv, rk = 1.0, h = 0.0;
+                    for (int k = 0; k <= wp.p; ++k) {
+                        h = h * u + wp.binom[k] * (P[k] * rk);
+                        rk *= rinv;
+                    }
+                    double mx = ra > rb ? ra : rb;
+                    double fac = (ra + rb > 0) ? 8.0 * mx / (ra + rb) : 8.0;
+                    double lhs = fac * h / (r * r);
+                    accept = lhs < wp.eps * c.minscale[B];  // eqs. (18a,b)
+                }
+                if (accept) act = kActM2L;
+                else if (!nchA && !nchB) act = kActP2P;
+                else {
+                    bool split_a = ra >= rb;
+                    if (!nchA) split_a = false;
+                    if (!nchB) split_a = true;
+                    act = split_a ? kActSplitA : kActSplitB;
+                }
+            }
+        }
+        unsigned nm = act == kActM2L, np = act == kActP2P;
+        unsigned nf = act == kActSelf ? nchA * nchA : act == kActSplitA ? nchA : act == kActSplitB ? nchB : 0;
+        long long om = warp_reserve(nm, &wb.counters[1], wb.m2l_cap, &wb.counters[3]);
+        long long op = warp_reserve(np, &wb.counters[2], wb.p2p_cap, &wb.counters[3]);
+        long long of = warp_reserve(nf, &wb.counters[0], wb.front_cap, &wb.counters[3]);
+        if (nm && om >= 0) wb.m2l[om] = make_int2(A, B);
+        if (np && op >= 0) wb.p2p[op] = make_int2(A, B);
+        if (nf && of >= 0) {
+            if (act == kActSelf) {
+                for (int a = 0; a < nchA; ++a)
+                    for (int b = 0; b < nchA; ++b) front_out[of + a * nchA + b] = make_int2(chA + a, chA + b);
+            } else if (act == kActSplitA) {
+                for (int a = 0; a < nchA; ++a) front_out[of + a] = make_int2(chA + a, B);
+            } else {
+                for (int b = 0; b < nchB; ++b) front_out[of + b] = make_int2(A, chB + b);
+            }
+        }
+    }
+}
+
+void launch_walk_step(Cells c, WalkParams wp, const int2* front_in, long long nfront, int2* front_out,
+                      WalkBuffers wb, cudaStream_t s) {
+    if (nfront <= 0) return;
+    k_walk<<<grid_for(nfront, 256, 152 * 16), 256, 0, s>>>(c, wp, front_in, nfront, front_out, wb);
+}
+
+// ---------------------------------------------------------------- list sort
+static int bits_for(long long v) {
+    int b = 1;
+    while ((1LL << b) < v) ++b;
+    return b;
+}
+
+__global__ void k_pack_pairs(const int2* __restrict__ list, long long n, int sb, uint64_t* __restrict__ keys,
+                             int* __restrict__ idx) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int2 v = list[i];
+        keys[i] = ((uint64_t)(unsigned)v.y << sb) | (uint64_t)(unsigned)v.x;
+        idx[i] = 0;
+    }
+}
+__global__ void k_unpack_pairs(const uint64_t* __restrict__ keys, long long n, int sb, int2* __restrict__ list) {
+    const uint64_t mask = (1ull << sb) - 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+        list[i] = make_int2((int)(k & mask), (int)(k >> sb));
+    }
+}
+
+size_t list_sort_tmp_bytes(long long npairs) {
+    size_t n = (size_t)(npairs > 0 ? npairs : 1);
+    return n * (2 * sizeof(uint64_t) + 2 * sizeof(int)) + radix_tmp_ints(n) * sizeof(int) + 256;
+}
+
+void sort_pairs_by_sink(int2* list, long long npairs, int ncells, void* tmp, cudaStream_t s) {
+    if (npairs <= 1) return;
+    int sb = bits_for(ncells);
+    uint64_t* k0 = (uint64_t*)tmp;
+    uint64_t* k1 = k0 + npairs;
+    int* i0 = (int*)(k1 + npairs);
+    int* i1 = i0 + npairs;
+    int* rtmp = i1 + npairs;
+    unsigned g = grid_for(npairs, 256);
+    k_pack_pairs<<<g, 256, 0, s>>>(list, npairs, sb, k0, i0);
+    int end_bit = 2 * sb;
+    int flip = radix_sort_pairs_bits(k0, i0, k1, i1, npairs, rtmp, 0, end_bit, s);
+    k_unpack_pairs<<<g, 256, 0, s>>>(flip ? k1 : k0, npairs, sb, list);
+}
+
+__global__ void k_segments(const int2* __restrict__ list, long long n, int* __restrict__ seg_start,
+                           int* __restrict__ seg_end) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int b = list[i].y;
+        if (i == 0 || list[i - 1].y != b) seg_start[b] = (int)i;
+        if (i == n - 1 || list[i + 1].y != b) seg_end[b] = (int)(i + 1);
+    }
+}
+
+void launch_segments(const int2* list, long long npairs, int ncells, int* seg_start, int* seg_end, cudaStream_t s) {
+    cudaMemsetAsync(seg_start, 0, sizeof(int) * (size_t)ncells, s);
+    cudaMemsetAsync(seg_end, 0, sizeof(int) * (size_t)ncells, s);
+    if (npairs > 0) k_segments<<<grid_for(npairs, 256), 256, 0, s>>>(list, npairs, seg_start, seg_end);
+}
+
+}  // namespace gb3

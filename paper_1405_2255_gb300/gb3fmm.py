@@ -1,0 +1,231 @@
+"""Python binding of the C ABI in include/gb3fmm.h (argument marshalling only).
+
+Every step of the force evaluation runs in the CUDA library libgb3fmm.so built
+from ``csrc/``; this module only passes pointers and sizes.  It raises
+``RuntimeError`` when the library is missing: there is no CPU fallback.
+
+Device buffers are torch CUDA tensors (float64, contiguous); host buffers of the
+``*_host`` calls are numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgb3fmm.so")
+
+FMM_OK, FMM_E_INVALID, FMM_E_OOM, FMM_E_ADMISSION, FMM_E_CUDA = 0, -1, -2, -3, -4
+FMM_E_TIMEOUT, FMM_E_OVERFLOW, FMM_E_NOTFOUND, FMM_E_BUSY = -5, -6, -7, -8
+FMM_MAC_A, FMM_MAC_F, FMM_MAC_THETA = 0, 1, 2
+FMM_PREC_FP64, FMM_PREC_MIXED = 0, 1
+FMM_SCALE_ESTIMATE, FMM_SCALE_CALLER = 0, 1
+
+
+class fmm_params(C.Structure):
+    _fields_ = [("p", C.c_int), ("eps", C.c_double), ("mac", C.c_int), ("theta_crit", C.c_double),
+                ("leaf_size", C.c_int), ("p2p_c", C.c_double), ("precision", C.c_int), ("scale_src", C.c_int)]
+
+
+class fmm_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("ncells", C.c_int64), ("nleaves", C.c_int64), ("n_m2l", C.c_int64),
+                ("n_p2p", C.c_int64), ("p2p_interactions", C.c_int64), ("coincident", C.c_int64),
+                ("est_m2l", C.c_int64), ("est_p2p", C.c_int64), ("depth", C.c_int), ("p", C.c_int),
+                ("eps", C.c_double), ("leaf_size", C.c_int),
+                ("t_tree", C.c_float), ("t_estimate", C.c_float), ("t_up", C.c_float), ("t_walk", C.c_float),
+                ("t_m2l", C.c_float), ("t_p2p", C.c_float), ("t_down", C.c_float), ("t_total", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every symbol include/gb3fmm.h declares
+EXPORTS = ["fmm_default_params", "fmm_create", "fmm_set_params", "fmm_evaluate", "fmm_evaluate_host",
+           "fmm_direct", "fmm_evaluate_batch", "fmm_debug_dump", "fmm_last_stats", "fmm_destroy",
+           "fmm_strerror", "fmm_last_error", "fmm_version"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgb3fmm.so (build it first with ``paper_1405_2255_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgb3fmm.so not found at {path}: run __graft_entry__.build() first")
+    L = C.CDLL(path)
+    vp, i64, dbl, ci = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    L.fmm_default_params.argtypes = [C.POINTER(fmm_params)]
+    L.fmm_default_params.restype = None
+    L.fmm_create.argtypes = [C.POINTER(vp), C.POINTER(fmm_params), ci]
+    L.fmm_set_params.argtypes = [vp, C.POINTER(fmm_params)]
+    L.fmm_evaluate.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, vp, C.POINTER(fmm_stats)]
+    L.fmm_evaluate_host.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, C.POINTER(fmm_stats)]
+    L.fmm_direct.argtypes = [vp, i64, vp, vp, dbl, i64, vp, vp, vp, vp, vp]
+    L.fmm_evaluate_batch.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp, vp, C.POINTER(fmm_stats)]
+    L.fmm_debug_dump.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.fmm_last_stats.argtypes = [vp, C.POINTER(fmm_stats)]
+    L.fmm_destroy.argtypes = [vp]
+    L.fmm_strerror.argtypes = [ci]
+    L.fmm_strerror.restype = C.c_char_p
+    L.fmm_last_error.argtypes = [vp]
+    L.fmm_last_error.restype = C.c_char_p
+    L.fmm_version.argtypes = []
+    L.fmm_version.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("fmm_strerror", "fmm_last_error", "fmm_version", "fmm_default_params"):
+            getattr(L, name).restype = ci
+    _lib = L
+    return L
+
+
+class FMMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+def _check(rc, ctx=None):
+    if rc != 0:
+        L = load()
+        detail = L.fmm_last_error(ctx).decode() if ctx else ""
+        raise FMMError(rc, f"{L.fmm_strerror(rc).decode()}: {detail}")
+
+
+def fmm_default_params() -> fmm_params:
+    p = fmm_params()
+    load().fmm_default_params(C.byref(p))
+    return p
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    assert t.is_cuda and t.is_contiguous(), "device buffers must be contiguous CUDA tensors"
+    assert t.dtype in (torch.float64, torch.int64), t.dtype
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Context:
+    """Owns one fmm_ctx (device workspace); the methods are the C entry points."""
+
+    def __init__(self, params: fmm_params | None = None, device: int = 0, **kw):
+        self.L = load()
+        if params is None:
+            params = fmm_default_params()
+        for k, v in kw.items():
+            setattr(params, k, v)
+        self.params = params
+        h = C.c_void_p()
+        _check(self.L.fmm_create(C.byref(h), C.byref(params), device))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.fmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            setattr(self.params, k, v)
+        _check(self.L.fmm_set_params(self.h, C.byref(self.params)), self.h)
+
+    def fmm_evaluate(self, x, mu, G=1.0, psi=None, acc=None, scale=None, stream=None, stats=False):
+        """x: [n,3] float64 CUDA tensor, mu: [n]; returns (psi, acc[, stats dict])."""
+        import torch
+        n = mu.shape[0]
+        if psi is None:
+            psi = torch.empty(n, dtype=torch.float64, device=mu.device)
+        if acc is None:
+            acc = torch.empty((n, 3), dtype=torch.float64, device=mu.device)
+        st = fmm_stats() if stats else None
+        rc = self.L.fmm_evaluate(self.h, n, _ptr(x), _ptr(mu), float(G), _ptr(scale), _ptr(psi), _ptr(acc),
+                                 _stream(stream), C.byref(st) if st is not None else None)
+        _check(rc, self.h)
+        return (psi, acc, st.as_dict()) if stats else (psi, acc)
+
+    def fmm_evaluate_host(self, x: np.ndarray, mu: np.ndarray, G=1.0, psi=None, acc=None, stream=None, stats=False):
+        """Host numpy in and out (the end-to-end call: copies inside)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        n = len(mu)
+        psi = np.empty(n) if psi is None else psi
+        acc = np.empty((n, 3)) if acc is None else acc
+        st = fmm_stats() if stats else None
+        s = 0 if stream is None else _stream(stream)
+        rc = self.L.fmm_evaluate_host(self.h, n, x.ctypes.data, mu.ctypes.data, float(G), psi.ctypes.data,
+                                      acc.ctypes.data, s, C.byref(st) if st is not None else None)
+        _check(rc, self.h)
+        return (psi, acc, st.as_dict()) if stats else (psi, acc)
+
+    def fmm_direct(self, x, mu, G=1.0, sinks=None, want_f=False, stream=None):
+        """GPU FP64 direct summation for the sinks (int64 CUDA tensor or None = all)."""
+        import torch
+        n = mu.shape[0]
+        ns = n if sinks is None else sinks.shape[0]
+        psi = torch.empty(ns, dtype=torch.float64, device=mu.device)
+        acc = torch.empty((ns, 3), dtype=torch.float64, device=mu.device)
+        f = torch.empty(ns, dtype=torch.float64, device=mu.device) if want_f else None
+        _check(self.L.fmm_direct(self.h, n, _ptr(x), _ptr(mu), float(G), ns, _ptr(sinks), _ptr(psi), _ptr(acc),
+                                 _ptr(f), _stream(stream)), self.h)
+        return (psi, acc, f) if want_f else (psi, acc)
+
+    def fmm_evaluate_batch(self, offsets: np.ndarray, x, mu, G, psi=None, acc=None, stream=None, stats=False):
+        import torch
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        G = np.ascontiguousarray(np.broadcast_to(np.asarray(G, dtype=np.float64), (len(offsets) - 1,)))
+        n = int(offsets[-1])
+        if psi is None:
+            psi = torch.empty(n, dtype=torch.float64, device=mu.device)
+        if acc is None:
+            acc = torch.empty((n, 3), dtype=torch.float64, device=mu.device)
+        st = fmm_stats() if stats else None
+        _check(self.L.fmm_evaluate_batch(self.h, len(offsets) - 1, offsets.ctypes.data, _ptr(x), _ptr(mu),
+                                         G.ctypes.data, _ptr(psi), _ptr(acc), _stream(stream),
+                                         C.byref(st) if st is not None else None), self.h)
+        return (psi, acc, st.as_dict()) if stats else (psi, acc)
+
+    def fmm_last_stats(self) -> dict:
+        st = fmm_stats()
+        _check(self.L.fmm_last_stats(self.h, C.byref(st)), self.h)
+        return st.as_dict()
+
+    def fmm_debug_dump(self) -> dict:
+        st = self.fmm_last_stats()
+        n, nc = int(st["n"]), int(st["ncells"])
+        ci = np.zeros((max(nc, 1), 5), dtype=np.int64)
+        cd = np.zeros((max(nc, 1), 6))
+        m2l = np.zeros((max(st["n_m2l"], 1), 2), dtype=np.int64)
+        p2p = np.zeros((max(st["n_p2p"], 1), 2), dtype=np.int64)
+        perm = np.zeros(max(n, 1), dtype=np.int64)
+        scale = np.zeros(max(n, 1))
+        _check(self.L.fmm_debug_dump(self.h, ci.ctypes.data, cd.ctypes.data, m2l.ctypes.data, p2p.ctypes.data,
+                                     perm.ctypes.data, scale.ctypes.data), self.h)
+        return {"cells_int": ci[:nc], "cells_dbl": cd[:nc], "m2l": m2l[:st["n_m2l"]], "p2p": p2p[:st["n_p2p"]],
+                "perm": perm[:n], "scale": scale[:n], "stats": st}
+
+
+def fmm_version() -> str:
+    return load().fmm_version().decode()
+
+
+def fmm_strerror(code: int) -> str:
+    return load().fmm_strerror(code).decode()

@@ -1,0 +1,203 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by
+element, on the same seeded inputs.  FP64 mode must match the oracle's FMM to
+max |a_gpu - a_orc| / |a_orc| <= 1e-10 (and its tree and interaction lists
+exactly); the GPU FP64 direct sum must match the oracle's to 1e-12."""
+import numpy as np
+import pytest
+
+from paper_1405_2255_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PARITY_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_2255_gb300 import build
+    build.build()
+    from paper_1405_2255_gb300 import gb3fmm
+    gb3fmm.load()
+    return gb3fmm
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def _rel(a, ref):
+    return np.linalg.norm(a - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+
+
+def _cell_ids(ci):
+    # identity of a cell: (first, count, level)
+    return [tuple(r) for r in ci[:, [2, 3, 0]]]
+
+
+def _run_both(g, orc, x, mu, G=1.0, **kw):
+    prm = dict(p=6, eps=1e-7, mac=0, theta_crit=0.5, leaf_size=16, p2p_c=1.0)
+    prm.update(kw)
+    ctx = g.Context(precision=g.FMM_PREC_FP64, **{k: v for k, v in prm.items()})
+    psi, acc, st = ctx.fmm_evaluate(_dev(x), _dev(mu), G, stats=True)
+    dump = ctx.fmm_debug_dump()
+    ctx.close()
+    run = orc.fmm(x, mu, G=G, **prm)
+    return psi.cpu().numpy(), acc.cpu().numpy(), st, dump, run
+
+
+def _compare_structure(dump, run):
+    gi, oi = _cell_ids(dump["cells_int"]), _cell_ids(run.cells_int)
+    assert sorted(gi) == sorted(oi), "trees differ"
+    # centres and radii per cell
+    go = {k: i for i, k in enumerate(gi)}
+    idx = np.array([go[k] for k in oi])
+    gd, od = dump["cells_dbl"][idx], run.cells_dbl
+    scale = np.maximum(od[:, 3], 1e-300)
+    assert np.max(np.linalg.norm(gd[:, :3] - od[:, :3], axis=1) / scale) < 1e-12
+    assert np.max(np.abs(gd[:, 3] - od[:, 3]) / scale) < 1e-12
+    # interaction lists as sets of (source id, sink id)
+    def pairs(lst, ids):
+        return sorted((ids[a], ids[b]) for a, b in lst)
+    assert np.array_equal(dump["perm"], run.perm)
+    gm, om = pairs(dump["m2l"], gi), pairs(run.m2l, oi)
+    gp, op = pairs(dump["p2p"], gi), pairs(run.p2p, oi)
+    flips = len(set(gm) ^ set(om)) + len(set(gp) ^ set(op))
+    return flips, len(gm), len(gp)
+
+
+def test_direct_fp64_matches_oracle(g, orc):
+    x, mu = inputs.config_input(1)
+    ctx = g.Context()
+    psi, acc = ctx.fmm_direct(_dev(x), _dev(mu), 1.0)
+    p_o, a_o, f_o, _ = orc.direct(x, mu)
+    assert np.max(np.abs(psi.cpu().numpy() - p_o) / p_o) < 1e-12
+    assert np.max(_rel(acc.cpu().numpy(), a_o)) < 1e-12
+    # sampled sinks with the f scale
+    import torch
+    sinks = torch.arange(0, len(mu), 37, dtype=torch.int64, device="cuda:0")
+    psi, acc, f = ctx.fmm_direct(_dev(x), _dev(mu), 2.0, sinks=sinks, want_f=True)
+    s = sinks.cpu().numpy()
+    assert np.max(np.abs(f.cpu().numpy() - 2 * f_o[s]) / f_o[s]) < 1e-12
+    assert np.max(_rel(acc.cpu().numpy(), 2 * a_o[s])) < 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", [
+    dict(eps=1e-5), dict(eps=1e-7), dict(mac=2, theta_crit=0.5), dict(mac=1, eps=1e-6),
+    dict(eps=1e-6, p=10, leaf_size=32), dict(eps=1e-6, p=3, leaf_size=8, p2p_c=0.0),
+])
+def test_fmm_fp64_matches_oracle(g, orc, case):
+    """Plummer N=4096 (the small configuration): tree, lists and forces vs the oracle."""
+    x, mu = inputs.config_input(1)
+    psi, acc, st, dump, run = _run_both(g, orc, x, mu, **case)
+    flips, nm, npp = _compare_structure(dump, run)
+    assert flips == 0
+    if case.get("eps", 1) >= 1e-6 or case.get("mac") == 2:
+        assert st["n_m2l"] > 0
+    assert st["n_m2l"] == run.stats["n_m2l"] and st["n_p2p"] == run.stats["n_p2p"]
+    assert st["p2p_interactions"] == run.stats["p2p_interactions"]
+    assert np.max(_rel(acc, run.acc)) <= PARITY_TOL
+    assert np.max(np.abs(psi - run.psi) / run.psi) <= PARITY_TOL
+
+
+def test_estimate_scale_matches_oracle(g, orc):
+    x, mu = inputs.config_input(1)
+    for mac in (0, 1):
+        _, _, _, dump, run = _run_both(g, orc, x, mu, mac=mac, eps=1e-6)
+        assert np.max(np.abs(dump["scale"] - run.scale) / run.scale) < 1e-10
+
+
+@pytest.mark.parametrize("n,leaf", [(1, 16), (2, 16), (17, 16), (100, 1), (3001, 16), (5000, 64)])
+def test_sizes_and_ragged_tails(g, orc, n, leaf):
+    x, mu = inputs.plummer(n, 101 + n)
+    psi, acc, st, dump, run = _run_both(g, orc, x, mu, G=0.7, leaf_size=leaf, eps=1e-6)
+    flips, _, _ = _compare_structure(dump, run)
+    assert flips == 0
+    if n == 1:
+        assert psi[0] == 0 and np.all(acc == 0)
+        return
+    assert np.max(_rel(acc, run.acc)) <= PARITY_TOL
+
+
+def test_empty_input(g):
+    import torch
+    ctx = g.Context()
+    e = torch.zeros((0, 3), dtype=torch.float64, device="cuda:0")
+    psi, acc = ctx.fmm_evaluate(e, torch.zeros(0, dtype=torch.float64, device="cuda:0"))
+    assert psi.numel() == 0
+    ctx.close()
+
+
+def test_cusp_with_point_mass(g, orc):
+    x, mu = inputs.dehnen(6000, inputs.BASE_SEED + 3)
+    psi, acc, st, dump, run = _run_both(g, orc, x, mu, p=8, eps=1e-6, leaf_size=16)
+    flips, _, _ = _compare_structure(dump, run)
+    assert flips == 0
+    assert np.max(_rel(acc, run.acc)) <= PARITY_TOL
+
+
+def test_coincident_particles(g, orc):
+    x, mu = inputs.plummer(500, 7)
+    x[10] = x[11]
+    x[20] = x[21] = x[22]
+    psi, acc, st, dump, run = _run_both(g, orc, x, mu, leaf_size=4, eps=1e-6)
+    assert st["coincident"] == run.stats["coincident"] == 2 + 6
+    assert np.all(np.isfinite(acc))
+    assert np.max(_rel(acc, run.acc)) <= PARITY_TOL
+
+
+def test_invalid_input_is_rejected(g):
+    x, mu = inputs.plummer(100, 3)
+    ctx = g.Context()
+    bad = x.copy()
+    bad[5, 1] = np.nan
+    with pytest.raises(g.FMMError) as e:
+        ctx.fmm_evaluate(_dev(bad), _dev(mu))
+    assert e.value.code == g.FMM_E_INVALID
+    m2 = mu.copy()
+    m2[3] = -1
+    with pytest.raises(g.FMMError):
+        ctx.fmm_evaluate(_dev(x), _dev(m2))
+    # the context stays usable
+    psi, acc = ctx.fmm_evaluate(_dev(x), _dev(mu))
+    assert np.all(np.isfinite(acc.cpu().numpy()))
+    ctx.close()
+
+
+def test_mixed_precision_accuracy(g, orc):
+    """Mixed mode (FP32 compensated P2P): accuracy against FP64 direct summation."""
+    x, mu = inputs.config_input(1)
+    _, a_t, _, _ = orc.direct(x, mu)
+    ctx = g.Context(p=6, eps=1e-7, leaf_size=32, p2p_c=4.0, precision=g.FMM_PREC_MIXED)
+    psi, acc = ctx.fmm_evaluate(_dev(x), _dev(mu))
+    e = _rel(acc.cpu().numpy(), a_t)
+    assert np.sqrt(np.mean(e ** 2)) < 1e-7
+    ctx.close()
+
+
+def test_host_entry_matches_device_entry(g):
+    x, mu = inputs.plummer(3000, 9)
+    ctx = g.Context(p=5, eps=1e-6, precision=g.FMM_PREC_FP64)
+    psi_d, acc_d = ctx.fmm_evaluate(_dev(x), _dev(mu), 1.3)
+    psi_h, acc_h = ctx.fmm_evaluate_host(x, mu, 1.3)
+    assert np.array_equal(psi_h, psi_d.cpu().numpy())
+    assert np.array_equal(acc_h, acc_d.cpu().numpy())
+    ctx.close()
+
+
+def test_batch_equals_alone(g):
+    systems = inputs.ensemble(6, inputs.BASE_SEED + 4)
+    xs = np.concatenate([s[0] for s in systems])
+    ms = np.concatenate([s[1] for s in systems])
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
+    ctx = g.Context(p=6, eps=1e-6, precision=g.FMM_PREC_FP64)
+    psi, acc = ctx.fmm_evaluate_batch(off, _dev(xs), _dev(ms), np.ones(len(systems)))
+    acc = acc.cpu().numpy()
+    for i, (x, mu) in enumerate(systems):
+        _, a1 = ctx.fmm_evaluate(_dev(x), _dev(mu))
+        assert np.max(_rel(acc[off[i]:off[i + 1]], a1.cpu().numpy())) <= 1e-12
+    ctx.close()
