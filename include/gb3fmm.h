@@ -83,6 +83,8 @@ typedef struct {
     int     leaf_size;
     /* device time per phase in milliseconds (CUDA events on the call's stream) */
     float   t_tree, t_estimate, t_up, t_walk, t_m2l, t_p2p, t_down, t_total;
+    /* number of kernels the library launched for the evaluation */
+    int64_t launches;
 } fmm_stats;
 
 typedef struct fmm_ctx fmm_ctx;
@@ -152,7 +154,14 @@ int fmm_evaluate_batch(fmm_ctx* ctx, int nsys, const int64_t* offsets, const dou
 int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t* m2l,
                    int64_t* p2p, int64_t* perm, double* scale_sorted);
 
+/* Counts and phase times of the last evaluation on ctx (HOST out).  Phase events
+ * are recorded on every evaluation; this call waits for the last one to finish. */
 int fmm_last_stats(fmm_ctx* ctx, fmm_stats* out);
+
+/* Measure the device's FP64 (DFMA) and FP32 (FFMA) throughput in TFLOP/s with
+ * two short register-only loops on the current device (HOST outs; about 50 ms).
+ * These are the roofline denominators of the ALU-bound kernels. */
+int fmm_alu_peaks(double* fp64_tflops, double* fp32_tflops);
 
 /* Release the context and all of its device memory. */
 int fmm_destroy(fmm_ctx* ctx);

@@ -83,6 +83,7 @@ struct fmm_ctx {
     int* h_int = nullptr;                      // pinned
     cudaEvent_t ev[EV_N];
     bool ev_ok = false;
+    bool timed = false;  // the events of the last evaluation were recorded
     // tree shape of the last evaluation
     std::vector<int> lev_start;
     int n = 0, ncells = 0, nleaves = 0;
@@ -173,7 +174,7 @@ static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cu
     TRY(ensure(ctx->mass, sizeof(double) * cap));
     TRY(ensure(ctx->minscale, sizeof(double) * cap));
     Cells c = cells_of(ctx);
-    k_root<<<1, 1, 0, s>>>(c, n);
+    k_root<<<1, 1, 0, s>>>(c, n); note_launch();
     ctx->lev_start.assign({0, 1});
     for (int L = 0;; ++L) {
         int b = ctx->lev_start[L], e = ctx->lev_start[L + 1];
@@ -199,9 +200,9 @@ static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cu
     TRY(ensure(ctx->leaf_pos, sizeof(int) * nc));
     TRY(ensure(ctx->leaves, sizeof(int) * nc));
     TRY(ensure(ctx->scan_tmp, sizeof(int) * scan_tmp_ints(nc)));
-    k_leaf_flags<<<grid_for(nc, 256), 256, 0, s>>>(c.nchild, nc, P<int>(ctx->leaf_flag));
+    k_leaf_flags<<<grid_for(nc, 256), 256, 0, s>>>(c.nchild, nc, P<int>(ctx->leaf_flag)); note_launch();
     scan_exclusive_i32(P<int>(ctx->leaf_flag), P<int>(ctx->leaf_pos), nc, P<int>(ctx->dtotal), P<int>(ctx->scan_tmp), s);
-    k_leaf_compact<<<grid_for(nc, 256), 256, 0, s>>>(P<int>(ctx->leaf_flag), P<int>(ctx->leaf_pos), nc, P<int>(ctx->leaves));
+    k_leaf_compact<<<grid_for(nc, 256), 256, 0, s>>>(P<int>(ctx->leaf_flag), P<int>(ctx->leaf_pos), nc, P<int>(ctx->leaves)); note_launch();
     CU(cudaMemcpyAsync(ctx->h_int, ctx->dtotal.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     ctx->nleaves = ctx->h_int[0];
@@ -341,6 +342,26 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     return 0;
 }
 
+// phase times of the last evaluation from its events (waits for the last event)
+static int phase_times(fmm_ctx* ctx) {
+    if (!ctx->timed) return 0;
+    CU(cudaEventSynchronize(ctx->ev[EV_END]));
+    float t;
+    auto el = [&](int a, int b) {
+        cudaEventElapsedTime(&t, ctx->ev[a], ctx->ev[b]);
+        return t;
+    };
+    ctx->last.t_tree = el(EV_START, EV_TREE);
+    ctx->last.t_estimate = el(EV_TREE, EV_EST);
+    ctx->last.t_up = el(EV_EST, EV_UP);
+    ctx->last.t_walk = el(EV_UP, EV_WALK);
+    ctx->last.t_m2l = el(EV_WALK, EV_M2L);
+    ctx->last.t_p2p = el(EV_M2L, EV_P2P);
+    ctx->last.t_down = el(EV_P2P, EV_DOWN);
+    ctx->last.t_total = el(EV_START, EV_END);
+    return 0;
+}
+
 // ------------------------------------------------------------------ one evaluation
 static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* mu, double G, const double* scale,
                            double* psi, double* acc, cudaStream_t s, fmm_stats* stats) {
@@ -360,7 +381,9 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     }
     if (prm.scale_src == FMM_SCALE_CALLER && prm.mac != FMM_MAC_THETA && !scale)
         return fail(ctx, FMM_E_INVALID, "scale_src = caller but scale == NULL");
-    const bool timing = stats != nullptr && ctx->ev_ok;
+    const bool timing = ctx->ev_ok;
+    const long long launches0 = launches_so_far();
+    ctx->timed = false;
     if (timing) CU(cudaEventRecord(ctx->ev[EV_START], s));
     CU(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), s));
     CU(cudaMemsetAsync(ctx->coin.p, 0, sizeof(unsigned long long), s));
@@ -459,6 +482,8 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     ctx->last.est_m2l = ctx->n_est_m2l;
     ctx->last.est_p2p = ctx->n_est_p2p;
     ctx->last.depth = nlev - 1;
+    ctx->last.launches = launches_so_far() - launches0;
+    ctx->timed = timing;
     if (stats) {
         CU(cudaStreamSynchronize(s));
         unsigned long long coin = 0;
@@ -472,21 +497,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         long long inter = 0;
         for (auto& e : pl) inter += (long long)cnt[e.x] * cnt[e.y] - (e.x == e.y ? cnt[e.x] : 0);
         ctx->last.p2p_interactions = inter;
-        if (timing) {
-            float t;
-            auto el = [&](int a, int b) {
-                cudaEventElapsedTime(&t, ctx->ev[a], ctx->ev[b]);
-                return t;
-            };
-            ctx->last.t_tree = el(EV_START, EV_TREE);
-            ctx->last.t_estimate = el(EV_TREE, EV_EST);
-            ctx->last.t_up = el(EV_EST, EV_UP);
-            ctx->last.t_walk = el(EV_UP, EV_WALK);
-            ctx->last.t_m2l = el(EV_WALK, EV_M2L);
-            ctx->last.t_p2p = el(EV_M2L, EV_P2P);
-            ctx->last.t_down = el(EV_P2P, EV_DOWN);
-            ctx->last.t_total = el(EV_START, EV_END);
-        }
+        TRY(phase_times(ctx));
         *stats = ctx->last;
     }
     return 0;
@@ -686,8 +697,14 @@ int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t*
 
 int fmm_last_stats(fmm_ctx* ctx, fmm_stats* out) {
     if (!ctx || !out) return FMM_E_INVALID;
+    TRY(phase_times(ctx));
     *out = ctx->last;
     return 0;
+}
+
+int fmm_alu_peaks(double* fp64_tflops, double* fp32_tflops) {
+    if (!fp64_tflops || !fp32_tflops) return FMM_E_INVALID;
+    return alu_peaks(fp64_tflops, fp32_tflops);
 }
 
 int fmm_destroy(fmm_ctx* ctx) {

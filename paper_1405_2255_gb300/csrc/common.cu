@@ -14,6 +14,10 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     return FMM_E_CUDA;
 }
 
+thread_local long long g_launches = 0;
+void note_launch() { ++g_launches; }
+long long launches_so_far() { return g_launches; }
+
 // ---------------------------------------------------------------- scan
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
@@ -98,19 +102,19 @@ size_t scan_tmp_ints(long long n) {
 
 void scan_exclusive_i32(const int* in, int* out, long long n, int* d_total, int* tmp, cudaStream_t s) {
     if (n <= 0) {
-        if (d_total) k_zero_total<<<1, 1, 0, s>>>(d_total);
+        if (d_total) k_zero_total<<<1, 1, 0, s>>>(d_total); note_launch();
         return;
     }
     long long nchunks = (n + kScanChunk - 1) / kScanChunk;
     if (nchunks == 1) {
-        k_chunk_scan<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, d_total, 1);
+        k_chunk_scan<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, d_total, 1); note_launch();
         return;
     }
     int* sums = tmp;
     int* sums_scan = tmp + nchunks;
-    k_chunk_sums<<<(unsigned)nchunks, kScanThreads, 0, s>>>(in, n, sums);
+    k_chunk_sums<<<(unsigned)nchunks, kScanThreads, 0, s>>>(in, n, sums); note_launch();
     scan_exclusive_i32(sums, sums_scan, nchunks, nullptr, tmp + 2 * nchunks + 1, s);
-    k_chunk_scan<<<(unsigned)nchunks, kScanThreads, 0, s>>>(in, out, n, sums_scan, d_total, nchunks);
+    k_chunk_scan<<<(unsigned)nchunks, kScanThreads, 0, s>>>(in, out, n, sums_scan, d_total, nchunks); note_launch();
 }
 
 }  // namespace gb3

@@ -72,6 +72,10 @@ __host__ __device__ inline cd load_real_storage(const double* R, int n, int m) {
 
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 
+// count of kernels launched by this host thread (reported in fmm_stats.launches)
+void note_launch();
+long long launches_so_far();
+
 inline unsigned grid_for(long long n, int block, long long cap = 152LL * 64) {
     long long g = (n + block - 1) / block;
     if (g < 1) g = 1;

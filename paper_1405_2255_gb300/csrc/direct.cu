@@ -54,7 +54,7 @@ void launch_direct(const double* x, const double* mu, int n, double G, const int
                    double* psi, double* acc, double* f, cudaStream_t s) {
     if (nsinks <= 0) return;
     unsigned g = grid_for(nsinks, kDirThreads, 152 * 32);
-    k_direct<<<g, kDirThreads, 0, s>>>(x, mu, n, G, sinks, nsinks, psi, acc, f);
+    k_direct<<<g, kDirThreads, 0, s>>>(x, mu, n, G, sinks, nsinks, psi, acc, f); note_launch();
 }
 
 }  // namespace gb3

@@ -67,7 +67,7 @@ __device__ inline void theta_column(int p, int m, double x, double y, double z, 
 __device__ inline void expand_real(int p, const double* R, cd* out, bool conj_out, int lane, int nlanes) {
     const int nc = ncoef(p);
     for (int i = lane; i < nc; i += nlanes) {
-        int n = (int)sqrt((double)i);
+        int n = (int)sqrtf((float)i);
         while (n * n > i) --n;
         while ((n + 1) * (n + 1) <= i) ++n;
         int m = i - n * n - n;

@@ -60,7 +60,7 @@ void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, cons
     LaneSched sched = make_lane_sched(p, kSchedDown);
     unsigned g = (unsigned)((ncells + wpb - 1) / wpb);
     if (g > 152u * 32u) g = 152u * 32u;
-    k_m2l<<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, ncells, cen, M, p, F, sched);
+    k_m2l<<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, ncells, cen, M, p, F, sched); note_launch();
 }
 
 // ---------------------------------------------------------------- L2L
@@ -97,7 +97,7 @@ void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p,
     const int wpb = 4;
     size_t sm = (size_t)wpb * 2 * ncoef(p) * sizeof(cd);
     LaneSched sched = make_lane_sched(p, kSchedDown);
-    k_l2l<<<(ncl + wpb - 1) / wpb, wpb * 32, sm, s>>>(c, cen, lev_begin, lev_end, p, F, sched);
+    k_l2l<<<(ncl + wpb - 1) / wpb, wpb * 32, sm, s>>>(c, cen, lev_begin, lev_end, p, F, sched); note_launch();
 }
 
 // ---------------------------------------------------------------- L2P
@@ -172,57 +172,59 @@ void launch_l2p(const d4* xm, Cells c, const d4* cen, const int* leaves, int nle
     if (nleaves <= 0) return;
     size_t sm = (size_t)ncoef(p) * sizeof(cd);
     unsigned g = nleaves < 152 * 64 ? nleaves : 152 * 64;
-    k_l2p<<<g, kL2PThreads, sm, s>>>(xm, c, cen, leaves, nleaves, p, F, psi, acc);
+    k_l2p<<<g, kL2PThreads, sm, s>>>(xm, c, cen, leaves, nleaves, p, F, psi, acc); note_launch();
 }
 
 // ---------------------------------------------------------------- P2P, FP64
-// One block per sink leaf.  Its sources are the P2P segments of the leaf and of
-// all its ancestors (a pair (A, B) with B internal covers every leaf below B).
-constexpr int kP2PThreads = 64;
+// One warp per chunk of up to 32 sinks of a leaf (lane = sink).  The sources are
+// the P2P segments of the leaf and of all its ancestors (a pair (A, B) with B
+// internal covers every leaf below B); they pass through a warp-private tile of
+// 32 in shared memory.
+constexpr int kP2PWarps = 4;
 
-__global__ void __launch_bounds__(kP2PThreads) k_p2p_fp64(const d4* __restrict__ xm, Cells c,
-                                                          const int2* __restrict__ list,
-                                                          const int* __restrict__ seg_start,
-                                                          const int* __restrict__ seg_end,
-                                                          const int* __restrict__ leaves, int nleaves,
-                                                          double* __restrict__ psi, double* __restrict__ acc,
-                                                          unsigned long long* coincident) {
-    __shared__ d4 tile[kP2PThreads];
+__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_fp64(const d4* __restrict__ xm, Cells c,
+                                                             const int2* __restrict__ list,
+                                                             const int* __restrict__ seg_start,
+                                                             const int* __restrict__ seg_end,
+                                                             const int* __restrict__ leaves, int nleaves,
+                                                             double* __restrict__ psi, double* __restrict__ acc,
+                                                             unsigned long long* coincident) {
+    __shared__ d4 tile_all[kP2PWarps][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    d4* tile = tile_all[wid];
     unsigned long long ncoin = 0;
-    for (int t = blockIdx.x; t < nleaves; t += gridDim.x) {
+    for (int t = blockIdx.x * kP2PWarps + wid; t < nleaves; t += gridDim.x * kP2PWarps) {
         const int leaf = leaves[t];
         const int first = c.first[leaf], count = c.count[leaf];
-        for (int s0 = 0; s0 < count; s0 += kP2PThreads) {
-            const int i = first + s0 + threadIdx.x;
-            const bool active = s0 + threadIdx.x < count;
-            d4 xb = active ? xm[i] : mk4(0, 0, 0, 0);
+        for (int s0 = 0; s0 < count; s0 += 32) {
+            const int i = first + s0 + lane;
+            const bool active = s0 + lane < count;
+            const d4 xb = active ? xm[i] : mk4(0, 0, 0, 0);
             double ps = 0, ax = 0, ay = 0, az = 0;
             for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
                 const int e0 = seg_start[cell], e1 = seg_end[cell];
                 for (int e = e0; e < e1; ++e) {
                     const int A = list[e].x;
                     const int af = c.first[A], an = c.count[A];
-                    for (int j0 = 0; j0 < an; j0 += kP2PThreads) {
-                        __syncthreads();
-                        if (j0 + threadIdx.x < an) tile[threadIdx.x] = xm[af + j0 + threadIdx.x];
-                        __syncthreads();
-                        const int nt = min(kP2PThreads, an - j0);
-                        if (active) {
-                            for (int j = 0; j < nt; ++j) {
-                                const d4 q = tile[j];
-                                const double dx = q.x - xb.x, dy = q.y - xb.y, dz = q.z - xb.z;
-                                const double r2 = dx * dx + dy * dy + dz * dz;
-                                if (r2 > 0.0) {
-                                    const double rinv = rsqrt(r2);
-                                    const double qm = q.w * rinv;
-                                    const double q3 = qm * rinv * rinv;
-                                    ps += qm;
-                                    ax = fma(q3, dx, ax);
-                                    ay = fma(q3, dy, ay);
-                                    az = fma(q3, dz, az);
-                                } else {
-                                    ++ncoin;
-                                }
+                    for (int j0 = 0; j0 < an; j0 += 32) {
+                        __syncwarp();
+                        if (j0 + lane < an) tile[lane] = xm[af + j0 + lane];
+                        __syncwarp();
+                        const int nt = min(32, an - j0);
+                        for (int j = 0; j < nt; ++j) {
+                            const d4 q = tile[j];
+                            const double dx = q.x - xb.x, dy = q.y - xb.y, dz = q.z - xb.z;
+                            const double r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 > 0.0) {
+                                const double rinv = rsqrt(r2);
+                                const double qm = q.w * rinv;
+                                const double q3 = qm * rinv * rinv;
+                                ps += qm;
+                                ax = fma(q3, dx, ax);
+                                ay = fma(q3, dy, ay);
+                                az = fma(q3, dz, az);
+                            } else {
+                                ncoin += active;
                             }
                         }
                     }
@@ -239,12 +241,18 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_fp64(const d4* __restrict__
     if (ncoin) atomicAdd(coincident, ncoin);
 }
 
+static unsigned p2p_grid(int nleaves) {
+    long long g = ((long long)nleaves + kP2PWarps - 1) / kP2PWarps;
+    return (unsigned)(g < 152 * 48 ? g : 152 * 48);
+}
+
 void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_start, const int* seg_end,
                      const int* leaves, int nleaves, double* psi, double* acc, unsigned long long* coincident,
                      cudaStream_t s) {
     if (nleaves <= 0) return;
-    unsigned g = nleaves < 152 * 64 ? nleaves : 152 * 64;
-    k_p2p_fp64<<<g, kP2PThreads, 0, s>>>(xm, c, list, seg_start, seg_end, leaves, nleaves, psi, acc, coincident);
+    k_p2p_fp64<<<p2p_grid(nleaves), kP2PWarps * 32, 0, s>>>(xm, c, list, seg_start, seg_end, leaves, nleaves, psi,
+                                                            acc, coincident);
+    note_launch();
 }
 
 // ---------------------------------------------------------------- P2P, mixed
@@ -262,7 +270,7 @@ __global__ void k_split_positions(const d4* __restrict__ xm, int n, float4* __re
     }
 }
 void launch_split_positions(const d4* xm, int n, float4* xhi, float4* xlo, cudaStream_t s) {
-    if (n > 0) k_split_positions<<<grid_for(n, 256), 256, 0, s>>>(xm, n, xhi, xlo);
+    if (n > 0) k_split_positions<<<grid_for(n, 256), 256, 0, s>>>(xm, n, xhi, xlo); note_launch();
 }
 
 struct ff {
@@ -289,71 +297,76 @@ __device__ inline void ff_acc(ff& a, float v) {
     a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
 }
 
-__global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(const float4* __restrict__ xhi, const float4* __restrict__ xlo,
-                                                           Cells c, const int2* __restrict__ list,
-                                                           const int* __restrict__ seg_start,
-                                                           const int* __restrict__ seg_end,
-                                                           const int* __restrict__ leaves, int nleaves,
-                                                           double* __restrict__ psi, double* __restrict__ acc,
-                                                           unsigned long long* coincident) {
-    __shared__ float4 th[kP2PThreads];
-    __shared__ float4 tl[kP2PThreads];
-    unsigned long long ncoin = 0;
-    for (int t = blockIdx.x; t < nleaves; t += gridDim.x) {
+__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __restrict__ xhi,
+                                                              const float4* __restrict__ xlo, Cells c,
+                                                              const int2* __restrict__ list,
+                                                              const int* __restrict__ seg_start,
+                                                              const int* __restrict__ seg_end,
+                                                              const int* __restrict__ leaves, int nleaves,
+                                                              double* __restrict__ psi, double* __restrict__ acc,
+                                                              unsigned long long* coincident) {
+    __shared__ float4 th_all[kP2PWarps][32];
+    __shared__ float4 tl_all[kP2PWarps][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4* th = th_all[wid];
+    float4* tl = tl_all[wid];
+    unsigned ncoin = 0;
+    for (int t = blockIdx.x * kP2PWarps + wid; t < nleaves; t += gridDim.x * kP2PWarps) {
         const int leaf = leaves[t];
         const int first = c.first[leaf], count = c.count[leaf];
         const d4 sc = c.sr[leaf];
         const float shx = (float)sc.x, shy = (float)sc.y, shz = (float)sc.z;
-        const float slx = (float)(sc.x - (double)shx), sly = (float)(sc.y - (double)shy), slz = (float)(sc.z - (double)shz);
-        for (int s0 = 0; s0 < count; s0 += kP2PThreads) {
-            const int i = first + s0 + threadIdx.x;
-            const bool active = s0 + threadIdx.x < count;
+        const float slx = (float)(sc.x - (double)shx), sly = (float)(sc.y - (double)shy),
+                    slz = (float)(sc.z - (double)shz);
+        for (int s0 = 0; s0 < count; s0 += 32) {
+            const int i = first + s0 + lane;
+            const bool active = s0 + lane < count;
             float bhx = 0, bhy = 0, bhz = 0, blx = 0, bly = 0, blz = 0;
             if (active) {
-                float4 h = xhi[i], l = xlo[i];
-                ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly), rz = ff_sub(h.z, l.z, shz, slz);
+                const float4 h = xhi[i], l = xlo[i];
+                const ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly), rz = ff_sub(h.z, l.z, shz, slz);
                 bhx = rx.hi; blx = rx.lo; bhy = ry.hi; bly = ry.lo; bhz = rz.hi; blz = rz.lo;
             }
             ff aps = {0, 0}, aax = {0, 0}, aay = {0, 0}, aaz = {0, 0};
+            unsigned cc = 0;
             for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
                 const int e0 = seg_start[cell], e1 = seg_end[cell];
                 for (int e = e0; e < e1; ++e) {
                     const int A = list[e].x;
                     const int af = c.first[A], an = c.count[A];
-                    for (int j0 = 0; j0 < an; j0 += kP2PThreads) {
-                        __syncthreads();
-                        if (j0 + threadIdx.x < an) {
-                            float4 h = xhi[af + j0 + threadIdx.x], l = xlo[af + j0 + threadIdx.x];
-                            ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly),
-                               rz = ff_sub(h.z, l.z, shz, slz);
-                            th[threadIdx.x] = make_float4(rx.hi, ry.hi, rz.hi, h.w);
-                            tl[threadIdx.x] = make_float4(rx.lo, ry.lo, rz.lo, 0.f);
+                    for (int j0 = 0; j0 < an; j0 += 32) {
+                        __syncwarp();
+                        if (j0 + lane < an) {
+                            const float4 h = xhi[af + j0 + lane], l = xlo[af + j0 + lane];
+                            const ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly),
+                                     rz = ff_sub(h.z, l.z, shz, slz);
+                            th[lane] = make_float4(rx.hi, ry.hi, rz.hi, h.w);
+                            tl[lane] = make_float4(rx.lo, ry.lo, rz.lo, 0.f);
                         }
-                        __syncthreads();
-                        const int nt = min(kP2PThreads, an - j0);
-                        if (active) {
-                            float ps = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-#pragma unroll 8
-                            for (int j = 0; j < nt; ++j) {
-                                const float4 qh = th[j], ql = tl[j];
-                                const float dx = (qh.x - bhx) + (ql.x - blx);
-                                const float dy = (qh.y - bhy) + (ql.y - bly);
-                                const float dz = (qh.z - bhz) + (ql.z - blz);
-                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                                ncoin += (r2 == 0.f);
-                                const float qm = qh.w * rinv;
-                                const float q3 = qm * rinv * rinv;
-                                ps += qm;
-                                ax = fmaf(q3, dx, ax);
-                                ay = fmaf(q3, dy, ay);
-                                az = fmaf(q3, dz, az);
-                            }
-                            ff_acc(aps, ps);
-                            ff_acc(aax, ax);
-                            ff_acc(aay, ay);
-                            ff_acc(aaz, az);
+                        __syncwarp();
+                        const int nt = min(32, an - j0);
+                        float ps = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll 4
+                        for (int j = 0; j < nt; ++j) {
+                            const float4 qh = th[j], ql = tl[j];
+                            const float dx = (qh.x - bhx) + (ql.x - blx);
+                            const float dy = (qh.y - bhy) + (ql.y - bly);
+                            const float dz = (qh.z - bhz) + (ql.z - blz);
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            const bool nz = r2 > 0.f;
+                            const float rinv = nz ? rsqrtf(r2) : 0.f;
+                            cc += !nz;
+                            const float qm = qh.w * rinv;
+                            const float q3 = qm * rinv * rinv;
+                            ps += qm;
+                            ax = fmaf(q3, dx, ax);
+                            ay = fmaf(q3, dy, ay);
+                            az = fmaf(q3, dz, az);
                         }
+                        ff_acc(aps, ps);
+                        ff_acc(aax, ax);
+                        ff_acc(aay, ay);
+                        ff_acc(aaz, az);
                     }
                 }
             }
@@ -362,18 +375,20 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(const float4* __restr
                 acc[3 * (size_t)i] = (double)aax.hi + (double)aax.lo;
                 acc[3 * (size_t)i + 1] = (double)aay.hi + (double)aay.lo;
                 acc[3 * (size_t)i + 2] = (double)aaz.hi + (double)aaz.lo;
+                ncoin += cc;
             }
         }
     }
-    if (ncoin) atomicAdd(coincident, ncoin);
+    if (ncoin) atomicAdd(coincident, (unsigned long long)ncoin);
 }
 
 void launch_p2p_mixed(const d4* /*xm*/, const float4* xhi, const float4* xlo, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* psi,
                       double* acc, unsigned long long* coincident, cudaStream_t s) {
     if (nleaves <= 0) return;
-    unsigned g = nleaves < 152 * 64 ? nleaves : 152 * 64;
-    k_p2p_mixed<<<g, kP2PThreads, 0, s>>>(xhi, xlo, c, list, seg_start, seg_end, leaves, nleaves, psi, acc, coincident);
+    k_p2p_mixed<<<p2p_grid(nleaves), kP2PWarps * 32, 0, s>>>(xhi, xlo, c, list, seg_start, seg_end, leaves, nleaves,
+                                                             psi, acc, coincident);
+    note_launch();
 }
 
 // ---------------------------------------------------------------- low-order f estimate
@@ -395,7 +410,7 @@ __global__ void k_f_m2l(const int2* __restrict__ list, const int* __restrict__ s
 }
 void launch_f_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* Ff,
                   cudaStream_t s) {
-    if (ncells > 0) k_f_m2l<<<(ncells + 127) / 128, 128, 0, s>>>(list, seg_start, seg_end, ncells, c, Ff);
+    if (ncells > 0) k_f_m2l<<<(ncells + 127) / 128, 128, 0, s>>>(list, seg_start, seg_end, ncells, c, Ff); note_launch();
 }
 __global__ void k_f_down(Cells c, int lev_begin, int lev_end, double* __restrict__ Ff) {
     int cell = lev_begin + blockIdx.x * blockDim.x + threadIdx.x;
@@ -404,37 +419,40 @@ __global__ void k_f_down(Cells c, int lev_begin, int lev_end, double* __restrict
 }
 void launch_f_down_level(Cells c, int lev_begin, int lev_end, double* Ff, cudaStream_t s) {
     int ncl = lev_end - lev_begin;
-    if (ncl > 0) k_f_down<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end, Ff);
+    if (ncl > 0) k_f_down<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end, Ff); note_launch();
 }
-__global__ void __launch_bounds__(kP2PThreads) k_f_p2p(const d4* __restrict__ xm, Cells c, const int2* __restrict__ list,
-                                                       const int* __restrict__ seg_start, const int* __restrict__ seg_end,
-                                                       const int* __restrict__ leaves, int nleaves,
-                                                       const double* __restrict__ Ff, double* __restrict__ fout) {
-    __shared__ d4 tile[kP2PThreads];
-    for (int t = blockIdx.x; t < nleaves; t += gridDim.x) {
+__global__ void __launch_bounds__(kP2PWarps * 32) k_f_p2p(const d4* __restrict__ xm, Cells c,
+                                                          const int2* __restrict__ list,
+                                                          const int* __restrict__ seg_start,
+                                                          const int* __restrict__ seg_end,
+                                                          const int* __restrict__ leaves, int nleaves,
+                                                          const double* __restrict__ Ff, double* __restrict__ fout) {
+    __shared__ d4 tile_all[kP2PWarps][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    d4* tile = tile_all[wid];
+    for (int t = blockIdx.x * kP2PWarps + wid; t < nleaves; t += gridDim.x * kP2PWarps) {
         const int leaf = leaves[t];
         const int first = c.first[leaf], count = c.count[leaf];
-        for (int s0 = 0; s0 < count; s0 += kP2PThreads) {
-            const int i = first + s0 + threadIdx.x;
-            const bool active = s0 + threadIdx.x < count;
-            d4 xb = active ? xm[i] : mk4(0, 0, 0, 0);
+        for (int s0 = 0; s0 < count; s0 += 32) {
+            const int i = first + s0 + lane;
+            const bool active = s0 + lane < count;
+            const d4 xb = active ? xm[i] : mk4(0, 0, 0, 0);
             double f = 0;
             for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
                 for (int e = seg_start[cell]; e < seg_end[cell]; ++e) {
                     const int A = list[e].x;
                     const int af = c.first[A], an = c.count[A];
-                    for (int j0 = 0; j0 < an; j0 += kP2PThreads) {
-                        __syncthreads();
-                        if (j0 + threadIdx.x < an) tile[threadIdx.x] = xm[af + j0 + threadIdx.x];
-                        __syncthreads();
-                        const int nt = min(kP2PThreads, an - j0);
-                        if (active)
-                            for (int j = 0; j < nt; ++j) {
-                                const d4 q = tile[j];
-                                const double dx = q.x - xb.x, dy = q.y - xb.y, dz = q.z - xb.z;
-                                const double r2 = dx * dx + dy * dy + dz * dz;
-                                if (r2 > 0.0) f += q.w / r2;
-                            }
+                    for (int j0 = 0; j0 < an; j0 += 32) {
+                        __syncwarp();
+                        if (j0 + lane < an) tile[lane] = xm[af + j0 + lane];
+                        __syncwarp();
+                        const int nt = min(32, an - j0);
+                        for (int j = 0; j < nt; ++j) {
+                            const d4 q = tile[j];
+                            const double dx = q.x - xb.x, dy = q.y - xb.y, dz = q.z - xb.z;
+                            const double r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 > 0.0) f += q.w / r2;
+                        }
                     }
                 }
             }
@@ -445,8 +463,8 @@ __global__ void __launch_bounds__(kP2PThreads) k_f_p2p(const d4* __restrict__ xm
 void launch_f_p2p(const d4* xm, Cells c, const int2* list, const int* seg_start, const int* seg_end,
                   const int* leaves, int nleaves, const double* Ff, double* f_sorted, cudaStream_t s) {
     if (nleaves <= 0) return;
-    unsigned g = nleaves < 152 * 64 ? nleaves : 152 * 64;
-    k_f_p2p<<<g, kP2PThreads, 0, s>>>(xm, c, list, seg_start, seg_end, leaves, nleaves, Ff, f_sorted);
+    k_f_p2p<<<p2p_grid(nleaves), kP2PWarps * 32, 0, s>>>(xm, c, list, seg_start, seg_end, leaves, nleaves, Ff, f_sorted);
+    note_launch();
 }
 
 __global__ void k_norm_scale(const double* __restrict__ af, const double* __restrict__ an, int n,
@@ -459,7 +477,7 @@ __global__ void k_norm_scale(const double* __restrict__ af, const double* __rest
 }
 void launch_norm_scale(const double* /*psi_far*/, const double* acc_far, const double* acc_near, int n, double* scale,
                        cudaStream_t s) {
-    if (n > 0) k_norm_scale<<<grid_for(n, 256), 256, 0, s>>>(acc_far, acc_near, n, scale);
+    if (n > 0) k_norm_scale<<<grid_for(n, 256), 256, 0, s>>>(acc_far, acc_near, n, scale); note_launch();
 }
 
 // ---------------------------------------------------------------- finish (A12)
@@ -475,7 +493,7 @@ __global__ void k_finish(const double* __restrict__ pf, const double* __restrict
 }
 void launch_finish(const double* psi_far, const double* acc_far, const double* psi_near, const double* acc_near,
                    const int* perm, int n, double G, double* psi, double* acc, cudaStream_t s) {
-    if (n > 0) k_finish<<<grid_for(n, 256), 256, 0, s>>>(psi_far, acc_far, psi_near, acc_near, perm, n, G, psi, acc);
+    if (n > 0) k_finish<<<grid_for(n, 256), 256, 0, s>>>(psi_far, acc_far, psi_near, acc_near, perm, n, G, psi, acc); note_launch();
 }
 
 }  // namespace gb3

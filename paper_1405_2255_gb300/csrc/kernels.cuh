@@ -130,6 +130,9 @@ void launch_finish(const double* psi_far, const double* acc_far, const double* p
                    const double* acc_near, const int* perm, int n, double G, double* psi, double* acc,
                    cudaStream_t s);
 
+// ---------------------------------------------------------------- peaks (peaks.cu)
+int alu_peaks(double* fp64_tflops, double* fp32_tflops);
+
 // ---------------------------------------------------------------- direct (direct.cu)
 void launch_direct(const double* x, const double* mu, int n, double G, const int64_t* sinks, int nsinks,
                    double* psi, double* acc, double* f, cudaStream_t s);

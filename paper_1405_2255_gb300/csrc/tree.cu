@@ -49,8 +49,8 @@ __global__ void k_bounds(const double* __restrict__ x, const double* __restrict_
 
 void launch_bounds(const double* x, const double* mu, int n, unsigned long long* bounds, unsigned* status,
                    cudaStream_t s) {
-    k_bounds_init<<<1, 32, 0, s>>>(bounds);
-    if (n > 0) k_bounds<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, mu, n, bounds, status);
+    k_bounds_init<<<1, 32, 0, s>>>(bounds); note_launch();
+    if (n > 0) k_bounds<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, mu, n, bounds, status); note_launch();
 }
 
 // ------------------------------------------------------------------ A2 keys
@@ -99,7 +99,7 @@ __global__ void k_keys(const double* __restrict__ x, int n, const unsigned long 
 
 void launch_keys(const double* x, int n, const unsigned long long* bounds, uint64_t* keys, int* idx,
                  cudaStream_t s) {
-    if (n > 0) k_keys<<<grid_for(n, 256), 256, 0, s>>>(x, n, bounds, keys, idx);
+    if (n > 0) k_keys<<<grid_for(n, 256), 256, 0, s>>>(x, n, bounds, keys, idx); note_launch();
 }
 
 // ------------------------------------------------------------------ A2 radix sort
@@ -187,9 +187,9 @@ int radix_sort_pairs_bits(uint64_t* keys, int* idx, uint64_t* keys_alt, int* idx
     int *va = idx, *vb = idx_alt;
     int flips = 0;
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
-        k_rs_hist<<<nb, kRsThreads, 0, s>>>(ka, (int)n, shift, hist, nb);
+        k_rs_hist<<<nb, kRsThreads, 0, s>>>(ka, (int)n, shift, hist, nb); note_launch();
         scan_exclusive_i32(hist, offs, 256LL * nb, nullptr, stmp, s);
-        k_rs_scatter<<<nb, kRsThreads, 0, s>>>(ka, va, kb, vb, (int)n, shift, offs, nb);
+        k_rs_scatter<<<nb, kRsThreads, 0, s>>>(ka, va, kb, vb, (int)n, shift, offs, nb); note_launch();
         uint64_t* tk = ka; ka = kb; kb = tk;
         int* tv = va; va = vb; vb = tv;
         flips ^= 1;
@@ -214,7 +214,7 @@ __global__ void k_gather(const double* __restrict__ x, const double* __restrict_
 
 void launch_gather(const double* x, const double* mu, const int* idx, int n, d4* xm, int* perm,
                    cudaStream_t s) {
-    if (n > 0) k_gather<<<grid_for(n, 256), 256, 0, s>>>(x, mu, idx, n, xm, perm);
+    if (n > 0) k_gather<<<grid_for(n, 256), 256, 0, s>>>(x, mu, idx, n, xm, perm); note_launch();
 }
 
 // ------------------------------------------------------------------ A3 oct-tree
@@ -278,9 +278,9 @@ void launch_split_level(const uint64_t* keys, Cells c, int lev_begin, int lev_en
                         cudaStream_t s) {
     int ncl = lev_end - lev_begin;
     k_split<<<(unsigned)(((long long)ncl * 32 + 255) / 256), 256, 0, s>>>(keys, c, lev_begin, lev_end, level,
-                                                                         leaf_size, nchild_tmp, oct_tmp);
+                                                                         leaf_size, nchild_tmp, oct_tmp); note_launch();
     scan_exclusive_i32(nchild_tmp, offs_tmp, ncl, d_total, scan_tmp, s);
-    k_write_children<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, level, nchild_tmp, oct_tmp, offs_tmp);
+    k_write_children<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, level, nchild_tmp, oct_tmp, offs_tmp); note_launch();
 }
 
 // ------------------------------------------------------------------ A4 geometry
@@ -431,61 +431,78 @@ __device__ inline void ld3(const d4* xm, int i, double p[3]) {
     p[0] = v.x; p[1] = v.y; p[2] = v.z;
 }
 
-// Welzl's recursion for points, unrolled into its four nested levels: each level
-// runs over a prefix of the points and restarts the next level with one more
-// support point when a point falls outside.
-__device__ void meb_points_dev(const d4* P, int n, double c[3], double& rad) {
-    double R[4][3], q[3];
-    double c0[3], r0;
+// Welzl's recursion for points (smallest ball of P with R on its boundary):
+// W(i, R) scans P[0..i) in order and, at the first point outside the current
+// ball, restarts one level deeper with that point added to R.
+// Warp form of the same recursion: each level scans its prefix 32 points at a
+// time with a ballot for the first point outside the current ball, so the
+// sequence of balls is exactly that of the sequential loops above.
+__device__ int first_outside(const d4* P, int from, int to, const double c[3], double rad, int lane) {
+    for (int b = from; b < to; b += 32) {
+        int i = b + lane;
+        bool out = false;
+        if (i < to) {
+            double q[3];
+            ld3(P, i, q);
+            out = !in_ball_dev(q, c, rad);
+        }
+        unsigned m = __ballot_sync(0xffffffffu, out);
+        if (m) return b + __ffs(m) - 1;
+    }
+    return -1;
+}
+
+__device__ void meb_points_warp(const d4* P, int n, double c[3], double& rad, int lane) {
+    double R[4][3];
+    double c0[3], r0, c1[3], r1, c2[3], r2, c3[3], r3;
     trivial_ball_dev(0, R, c0, r0);
-    for (int i = 0; i < n; ++i) {
-        ld3(P, i, q);
-        if (in_ball_dev(q, c0, r0)) continue;
-        for (int d = 0; d < 3; ++d) R[0][d] = q[d];
-        double c1[3], r1;
+    int i = first_outside(P, 0, n, c0, r0, lane);
+    while (i >= 0) {
+        ld3(P, i, R[0]);
         trivial_ball_dev(1, R, c1, r1);
-        for (int j = 0; j < i; ++j) {
-            ld3(P, j, q);
-            if (in_ball_dev(q, c1, r1)) continue;
-            for (int d = 0; d < 3; ++d) R[1][d] = q[d];
-            double c2[3], r2;
+        int j = first_outside(P, 0, i, c1, r1, lane);
+        while (j >= 0) {
+            ld3(P, j, R[1]);
             trivial_ball_dev(2, R, c2, r2);
-            for (int k = 0; k < j; ++k) {
-                ld3(P, k, q);
-                if (in_ball_dev(q, c2, r2)) continue;
-                for (int d = 0; d < 3; ++d) R[2][d] = q[d];
-                double c3[3], r3;
+            int k = first_outside(P, 0, j, c2, r2, lane);
+            while (k >= 0) {
+                ld3(P, k, R[2]);
                 trivial_ball_dev(3, R, c3, r3);
-                for (int l = 0; l < k; ++l) {
-                    ld3(P, l, q);
-                    if (in_ball_dev(q, c3, r3)) continue;
-                    for (int d = 0; d < 3; ++d) R[3][d] = q[d];
+                int l = first_outside(P, 0, k, c3, r3, lane);
+                while (l >= 0) {
+                    ld3(P, l, R[3]);
                     trivial_ball_dev(4, R, c3, r3);
+                    l = first_outside(P, l + 1, k, c3, r3, lane);
                 }
                 for (int d = 0; d < 3; ++d) c2[d] = c3[d];
                 r2 = r3;
+                k = first_outside(P, k + 1, j, c2, r2, lane);
             }
             for (int d = 0; d < 3; ++d) c1[d] = c2[d];
             r1 = r2;
+            j = first_outside(P, j + 1, i, c1, r1, lane);
         }
         for (int d = 0; d < 3; ++d) c0[d] = c1[d];
         r0 = r1;
+        i = first_outside(P, i + 1, n, c0, r0, lane);
     }
     for (int d = 0; d < 3; ++d) c[d] = c0[d];
     rad = r0 < 0 ? 0 : r0;
 }
 
-__global__ void k_leaf_geometry(const d4* __restrict__ xm, Cells c, const int* __restrict__ leaves,
-                                int nleaves, unsigned* status) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per leaf: smallest enclosing ball, exact radius, mass, centre of mass
+__global__ void k_leaf_geometry(const d4* __restrict__ xm, Cells c, const int* __restrict__ leaves, int nleaves,
+                                unsigned* status) {
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= nleaves) return;
-    int cell = leaves[t];
-    int first = c.first[cell], count = c.count[cell];
+    const int cell = leaves[t];
+    const int first = c.first[cell], count = c.count[cell];
     const d4* X = xm + first;
     double s[3], rad;
-    meb_points_dev(X, count, s, rad);
+    meb_points_warp(X, count, s, rad, lane);
     double rmax = 0, m = 0, mx[3] = {0, 0, 0};
-    for (int i = 0; i < count; ++i) {
+    for (int i = lane; i < count; i += 32) {
         double p[3];
         ld3(X, i, p);
         double r = dist3_dev(p, s);
@@ -494,23 +511,32 @@ __global__ void k_leaf_geometry(const d4* __restrict__ xm, Cells c, const int* _
         m += w;
         for (int k = 0; k < 3; ++k) mx[k] += w * p[k];
     }
+    rmax = warp_max(rmax);
+    m = warp_sum(m);
+    for (int k = 0; k < 3; ++k) mx[k] = warp_sum(mx[k]);
     double com[3];
     for (int k = 0; k < 3; ++k) com[k] = (m > 0) ? mx[k] / m : s[k];
     double rc = 0;
-    for (int i = 0; i < count; ++i) {
+    for (int i = lane; i < count; i += 32) {
         double p[3];
         ld3(X, i, p);
         double r = dist3_dev(p, com);
         if (r > rc) rc = r;
     }
-    c.sr[cell] = mk4(s[0], s[1], s[2], rmax);
-    c.cr[cell] = mk4(com[0], com[1], com[2], rc);
-    c.mass[cell] = m;
+    rc = warp_max(rc);
+    if (lane == 0) {
+        c.sr[cell] = mk4(s[0], s[1], s[2], rmax);
+        c.cr[cell] = mk4(com[0], com[1], com[2], rc);
+        c.mass[cell] = m;
+    }
 }
 
 void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves, unsigned* status,
                           cudaStream_t s) {
-    if (nleaves > 0) k_leaf_geometry<<<(nleaves + 127) / 128, 128, 0, s>>>(xm, c, leaves, nleaves, status);
+    if (nleaves > 0) {
+        k_leaf_geometry<<<(unsigned)(((long long)nleaves * 32 + 127) / 128), 128, 0, s>>>(xm, c, leaves, nleaves, status);
+        note_launch();
+    }
 }
 
 // Internal cells of one level: smallest ball enclosing the daughter balls (s_d, rho_d),
@@ -644,10 +670,10 @@ void launch_internal_geometry(const d4* xm, Cells c, int lev_begin, int lev_end,
                               unsigned long long* rad_tmp, unsigned* status, cudaStream_t s) {
     int ncl = lev_end - lev_begin;
     if (ncl <= 0) return;
-    k_internal_meb<<<(unsigned)(((long long)ncl * 32 + 255) / 256), 256, 0, s>>>(c, lev_begin, lev_end, status);
+    k_internal_meb<<<(unsigned)(((long long)ncl * 32 + 255) / 256), 256, 0, s>>>(c, lev_begin, lev_end, status); note_launch();
     cudaMemsetAsync(rad_tmp, 0, sizeof(unsigned long long) * 2 * ncl, s);
-    k_internal_radii<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xm, c, lev_begin, lev_end, rad_tmp);
-    k_internal_radii_finish<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, rad_tmp);
+    k_internal_radii<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xm, c, lev_begin, lev_end, rad_tmp); note_launch();
+    k_internal_radii_finish<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, rad_tmp); note_launch();
 }
 
 }  // namespace gb3

@@ -99,7 +99,7 @@ void launch_p2m(const d4* xm, Cells c, const d4* cen, const int* leaves, int nle
     if (nleaves <= 0) return;
     const int wpb = 4;
     size_t sm = (size_t)wpb * ncoef(p) * sizeof(double);
-    k_p2m<<<(nleaves + wpb - 1) / wpb, wpb * 32, sm, s>>>(xm, c, cen, leaves, nleaves, p, M);
+    k_p2m<<<(nleaves + wpb - 1) / wpb, wpb * 32, sm, s>>>(xm, c, cen, leaves, nleaves, p, M); note_launch();
 }
 
 // ---------------------------------------------------------------- M2M
@@ -160,7 +160,7 @@ void launch_m2m_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p,
     const int wpb = 4;
     size_t sm = (size_t)wpb * 2 * ncoef(p) * sizeof(cd);
     LaneSched sched = make_lane_sched(p, kSchedUp);
-    k_m2m<<<(ncl + wpb - 1) / wpb, wpb * 32, sm, s>>>(c, cen, lev_begin, lev_end, p, M, sched);
+    k_m2m<<<(ncl + wpb - 1) / wpb, wpb * 32, sm, s>>>(c, cen, lev_begin, lev_end, p, M, sched); note_launch();
 }
 
 // ---------------------------------------------------------------- power
@@ -189,7 +189,7 @@ void launch_power(const double* M, int ncells, int p, double* P, cudaStream_t s)
         cudaMemcpyToSymbol(c_fact, f, sizeof f);
         init = true;
     }
-    if (ncells > 0) k_power<<<(ncells + 127) / 128, 128, 0, s>>>(M, ncells, p, P);
+    if (ncells > 0) k_power<<<(ncells + 127) / 128, 128, 0, s>>>(M, ncells, p, P); note_launch();
 }
 
 // ---------------------------------------------------------------- min scale
@@ -203,7 +203,7 @@ __global__ void k_minscale_leaves(const double* __restrict__ sc, Cells c, const 
     c.minscale[cell] = m;
 }
 void launch_minscale_leaves(const double* scale_sorted, Cells c, const int* leaves, int nleaves, cudaStream_t s) {
-    if (nleaves > 0) k_minscale_leaves<<<(nleaves + 127) / 128, 128, 0, s>>>(scale_sorted, c, leaves, nleaves);
+    if (nleaves > 0) k_minscale_leaves<<<(nleaves + 127) / 128, 128, 0, s>>>(scale_sorted, c, leaves, nleaves); note_launch();
 }
 __global__ void k_minscale_level(Cells c, int lev_begin, int lev_end) {
     int cell = lev_begin + blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,14 +216,14 @@ __global__ void k_minscale_level(Cells c, int lev_begin, int lev_end) {
 }
 void launch_minscale_level(Cells c, int lev_begin, int lev_end, cudaStream_t s) {
     int ncl = lev_end - lev_begin;
-    if (ncl > 0) k_minscale_level<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end);
+    if (ncl > 0) k_minscale_level<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end); note_launch();
 }
 __global__ void k_scale_from_caller(const double* __restrict__ scale, const int* __restrict__ perm, int n,
                                     double* __restrict__ out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = scale[perm[i]];
 }
 void launch_scale_from_caller(const double* scale, const int* perm, int n, double* scale_sorted, cudaStream_t s) {
-    if (n > 0) k_scale_from_caller<<<grid_for(n, 256), 256, 0, s>>>(scale, perm, n, scale_sorted);
+    if (n > 0) k_scale_from_caller<<<grid_for(n, 256), 256, 0, s>>>(scale, perm, n, scale_sorted); note_launch();
 }
 
 }  // namespace gb3

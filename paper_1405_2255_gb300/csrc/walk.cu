@@ -114,7 +114,7 @@ __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in
 void launch_walk_step(Cells c, WalkParams wp, const int2* front_in, long long nfront, int2* front_out,
                       WalkBuffers wb, cudaStream_t s) {
     if (nfront <= 0) return;
-    k_walk<<<grid_for(nfront, 256, 152 * 16), 256, 0, s>>>(c, wp, front_in, nfront, front_out, wb);
+    k_walk<<<grid_for(nfront, 256, 152 * 16), 256, 0, s>>>(c, wp, front_in, nfront, front_out, wb); note_launch();
 }
 
 // ---------------------------------------------------------------- list sort
@@ -154,10 +154,10 @@ void sort_pairs_by_sink(int2* list, long long npairs, int ncells, void* tmp, cud
     int* i1 = i0 + npairs;
     int* rtmp = i1 + npairs;
     unsigned g = grid_for(npairs, 256);
-    k_pack_pairs<<<g, 256, 0, s>>>(list, npairs, sb, k0, i0);
+    k_pack_pairs<<<g, 256, 0, s>>>(list, npairs, sb, k0, i0); note_launch();
     int end_bit = 2 * sb;
     int flip = radix_sort_pairs_bits(k0, i0, k1, i1, npairs, rtmp, 0, end_bit, s);
-    k_unpack_pairs<<<g, 256, 0, s>>>(flip ? k1 : k0, npairs, sb, list);
+    k_unpack_pairs<<<g, 256, 0, s>>>(flip ? k1 : k0, npairs, sb, list); note_launch();
 }
 
 __global__ void k_segments(const int2* __restrict__ list, long long n, int* __restrict__ seg_start,
@@ -172,7 +172,7 @@ __global__ void k_segments(const int2* __restrict__ list, long long n, int* __re
 void launch_segments(const int2* list, long long npairs, int ncells, int* seg_start, int* seg_end, cudaStream_t s) {
     cudaMemsetAsync(seg_start, 0, sizeof(int) * (size_t)ncells, s);
     cudaMemsetAsync(seg_end, 0, sizeof(int) * (size_t)ncells, s);
-    if (npairs > 0) k_segments<<<grid_for(npairs, 256), 256, 0, s>>>(list, npairs, seg_start, seg_end);
+    if (npairs > 0) k_segments<<<grid_for(npairs, 256), 256, 0, s>>>(list, npairs, seg_start, seg_end); note_launch();
 }
 
 }  // namespace gb3

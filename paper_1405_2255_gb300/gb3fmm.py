@@ -36,7 +36,8 @@ class fmm_stats(C.Structure):
                 ("est_m2l", C.c_int64), ("est_p2p", C.c_int64), ("depth", C.c_int), ("p", C.c_int),
                 ("eps", C.c_double), ("leaf_size", C.c_int),
                 ("t_tree", C.c_float), ("t_estimate", C.c_float), ("t_up", C.c_float), ("t_walk", C.c_float),
-                ("t_m2l", C.c_float), ("t_p2p", C.c_float), ("t_down", C.c_float), ("t_total", C.c_float)]
+                ("t_m2l", C.c_float), ("t_p2p", C.c_float), ("t_down", C.c_float), ("t_total", C.c_float),
+                ("launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -45,7 +46,7 @@ class fmm_stats(C.Structure):
 # every symbol include/gb3fmm.h declares
 EXPORTS = ["fmm_default_params", "fmm_create", "fmm_set_params", "fmm_evaluate", "fmm_evaluate_host",
            "fmm_direct", "fmm_evaluate_batch", "fmm_debug_dump", "fmm_last_stats", "fmm_destroy",
-           "fmm_strerror", "fmm_last_error", "fmm_version"]
+           "fmm_strerror", "fmm_last_error", "fmm_version", "fmm_alu_peaks"]
 
 _lib = None
 
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH):
     L.fmm_strerror.restype = C.c_char_p
     L.fmm_last_error.argtypes = [vp]
     L.fmm_last_error.restype = C.c_char_p
+    L.fmm_alu_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.fmm_version.argtypes = []
     L.fmm_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -221,6 +223,13 @@ class Context:
                                      perm.ctypes.data, scale.ctypes.data), self.h)
         return {"cells_int": ci[:nc], "cells_dbl": cd[:nc], "m2l": m2l[:st["n_m2l"]], "p2p": p2p[:st["n_p2p"]],
                 "perm": perm[:n], "scale": scale[:n], "stats": st}
+
+
+def fmm_alu_peaks() -> tuple[float, float]:
+    """Measured (FP64 DFMA, FP32 FFMA) throughput of the current device in TFLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    _check(load().fmm_alu_peaks(C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def fmm_version() -> str:
