@@ -72,6 +72,8 @@ typedef struct {
     double p2p_c;       /* a pair (A,B) is summed directly when N_A N_B < p2p_c p^3     */
     int    precision;   /* FMM_PREC_*                                                  */
     int    scale_src;   /* FMM_SCALE_*                                                 */
+    int    p2p_two_float; /* mixed P2P: 1 = dx from two-float positions (hi + lo) relative
+                             to the sink leaf's centre; 0 = from their FP32 high parts only */
 } fmm_params;
 
 typedef struct {
@@ -90,7 +92,8 @@ typedef struct {
 typedef struct fmm_ctx fmm_ctx;
 
 /* Default parameters: p = 8, eps = 1e-7, (18a) with the low-order estimate,
- * leaf_size = 64, p2p_c = 8, mixed precision.  Host pointer, filled in. */
+ * leaf_size = 64, p2p_c = 8, mixed precision with two-float P2P positions.
+ * Host pointer, filled in. */
 void fmm_default_params(fmm_params* out);
 
 /* Create a context on CUDA device `device` (the device becomes current for the

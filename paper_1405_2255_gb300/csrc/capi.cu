@@ -75,7 +75,7 @@ struct fmm_ctx {
     // expansions
     Buf M, F, Pw, binom, M1, F1, Ff;
     // walk
-    Buf front0, front1, m2l, p2p, sort_tmp, seg_start, seg_end, est_m2l, est_p2p, m2l_seg_start, m2l_seg_end;
+    Buf front0, front1, m2l, p2p, sort_tmp, m2l_tmp, seg_start, seg_end, est_m2l, est_p2p, m2l_seg_start, m2l_seg_end;
     long long front_cap = 0, m2l_cap = 0, p2p_cap = 0, est_m2l_cap = 0, est_p2p_cap = 0;
     // per particle results (sorted order)
     Buf psi_far, acc_far, psi_near, acc_near, scale_sorted;
@@ -325,19 +325,19 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     launch_p2m(P<d4>(ctx->xm), c, c.cr, P<int>(ctx->leaves), ctx->nleaves, pe, P<double>(ctx->M1), s);
     for (int L = nlev - 1; L >= 0; --L)
         launch_m2m_level(c, c.cr, ctx->lev_start[L], ctx->lev_start[L + 1], pe, P<double>(ctx->M1), s);
-    launch_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), nullptr, nc, c.cr,
+    TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc)));
+    launch_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc, c.cr,
                P<double>(ctx->M1), pe, P<double>(ctx->F1), s);
     for (int L = 1; L < nlev; ++L) launch_l2l_level(c, c.cr, ctx->lev_start[L], ctx->lev_start[L + 1], pe, P<double>(ctx->F1), s);
     launch_l2p(P<d4>(ctx->xm), c, c.cr, P<int>(ctx->leaves), ctx->nleaves, pe, P<double>(ctx->F1),
                P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
-    unsigned long long* dummy = P<unsigned long long>(ctx->counters) + 4;
     if (ctx->prm.precision == FMM_PREC_MIXED)
         launch_p2p_mixed(P<d4>(ctx->xm), P<float4>(ctx->xhi), P<float4>(ctx->xlo), c, P<int2>(ctx->est_p2p),
                          P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
-                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), dummy, s);
+                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), false, s);
     else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->est_p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
-                        P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), dummy, s);
+                        P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
     launch_norm_scale(nullptr, P<double>(ctx->acc_far), P<double>(ctx->acc_near), n, scale, s);
     return 0;
 }
@@ -447,7 +447,8 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
 
     // A9: M2L
     CU(cudaMemsetAsync(ctx->F.p, 0, sizeof(double) * nco * (size_t)nc, s));
-    launch_m2l(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), nullptr, nc, c.sr,
+    TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc)));
+    launch_m2l(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc, c.sr,
                P<double>(ctx->M), prm.p, P<double>(ctx->F), s);
     if (timing) CU(cudaEventRecord(ctx->ev[EV_M2L], s));
 
@@ -456,11 +457,11 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     if (prm.precision == FMM_PREC_MIXED)
         launch_p2p_mixed(P<d4>(ctx->xm), P<float4>(ctx->xhi), P<float4>(ctx->xlo), c, P<int2>(ctx->p2p),
                          P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
-                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), P<unsigned long long>(ctx->coin), s);
+                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), prm.p2p_two_float != 0, s);
     else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
-                        P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near),
-                        P<unsigned long long>(ctx->coin), s);
+                        P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
+    launch_coincident(P<d4>(ctx->xm), P<uint64_t>(ctx->keys), n, P<unsigned long long>(ctx->coin), s);
     if (timing) CU(cudaEventRecord(ctx->ev[EV_P2P], s));
 
     // A11-A12: L2L, L2P, combine and scatter
@@ -488,7 +489,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         CU(cudaStreamSynchronize(s));
         unsigned long long coin = 0;
         CU(cudaMemcpy(&coin, ctx->coin.p, sizeof coin, cudaMemcpyDeviceToHost));
-        ctx->last.coincident = (long long)coin - n;
+        ctx->last.coincident = (long long)coin;
         // p2p particle interactions from the list
         std::vector<int2> pl(ctx->n_p2p);
         std::vector<int> cnt(nc);
@@ -516,6 +517,7 @@ void fmm_default_params(fmm_params* out) {
     out->p2p_c = 8.0;
     out->precision = FMM_PREC_MIXED;
     out->scale_src = FMM_SCALE_ESTIMATE;
+    out->p2p_two_float = 1;
 }
 
 int fmm_create(fmm_ctx** out, const fmm_params* params, int device) {
@@ -716,7 +718,7 @@ int fmm_destroy(fmm_ctx* ctx) {
                   &ctx->sr, &ctx->cr, &ctx->mass, &ctx->minscale, &ctx->split_nchild, &ctx->split_oct,
                   &ctx->split_offs, &ctx->scan_tmp, &ctx->leaves, &ctx->leaf_flag, &ctx->leaf_pos, &ctx->rad_tmp,
                   &ctx->M, &ctx->F, &ctx->Pw, &ctx->binom, &ctx->M1, &ctx->F1, &ctx->Ff, &ctx->front0, &ctx->front1,
-                  &ctx->m2l, &ctx->p2p, &ctx->sort_tmp, &ctx->seg_start, &ctx->seg_end, &ctx->est_m2l, &ctx->est_p2p,
+                  &ctx->m2l, &ctx->p2p, &ctx->sort_tmp, &ctx->m2l_tmp, &ctx->seg_start, &ctx->seg_end, &ctx->est_m2l, &ctx->est_p2p,
                   &ctx->m2l_seg_start, &ctx->m2l_seg_end, &ctx->psi_far, &ctx->acc_far, &ctx->psi_near,
                   &ctx->acc_near, &ctx->scale_sorted};
     for (Buf* b : all) release(*b);

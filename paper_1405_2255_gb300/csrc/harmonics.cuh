@@ -5,6 +5,33 @@
 
 namespace gb3 {
 
+// Recurrence coefficients as doubles (no integer-to-FP64 conversions in the loops):
+// c_tw[n] = 2n - 1, c_inv_up[n][m] = 1 / (n^2 - m^2), c_th_b[n][m] = (n-1)^2 - m^2.
+struct RecTables {
+    double tw[kMaxP + 2];
+    double inv_up[kMaxP + 1][kMaxP + 1];
+    double th_b[kMaxP + 1][kMaxP + 1];
+    double inv_2j[kMaxP + 1];  // 1 / (2j)
+};
+// one copy per translation unit (no relocatable device code); each unit that
+// launches kernels using the recurrences calls init_rec_tables() first
+static __constant__ RecTables c_rec;
+static inline void init_rec_tables() {
+    static bool done = false;
+    if (done) return;
+    RecTables t;
+    memset(&t, 0, sizeof t);
+    for (int n = 0; n <= kMaxP + 1; ++n) t.tw[n] = 2.0 * n - 1.0;
+    for (int n = 0; n <= kMaxP; ++n)
+        for (int m = 0; m <= kMaxP; ++m) {
+            t.inv_up[n][m] = (n * n != m * m) ? 1.0 / (double)(n * n - m * m) : 0.0;
+            t.th_b[n][m] = (double)((n - 1) * (n - 1) - m * m);
+        }
+    for (int j = 1; j <= kMaxP; ++j) t.inv_2j[j] = 1.0 / (2.0 * j);
+    cudaMemcpyToSymbol(c_rec, &t, sizeof t);
+    done = true;
+}
+
 // One column m >= 0 of the regular harmonics Upsilon_n^m(r), n = m..p, written to
 // the full complex array out[cix(n, +-m)] (negative m by X_n^{-m} = (-1)^m X_n^{m*}).
 // Diagonal: Upsilon_m^m = prod_{j<=m} (x+iy)/(2j); then
@@ -14,7 +41,7 @@ __device__ inline void upsilon_column(int p, int m, double x, double y, double z
     const double r2 = x * x + y * y + z * z;
     cd d = mkc(1.0, 0.0);
     for (int j = 1; j <= m; ++j) {
-        double s = 1.0 / (2.0 * j);
+        double s = c_rec.inv_2j[j];
         d = cd{s * (x * d.re - y * d.im), s * (x * d.im + y * d.re)};
     }
     cd prev2 = mkc(0.0, 0.0), prev = d;
@@ -23,8 +50,8 @@ __device__ inline void upsilon_column(int p, int m, double x, double y, double z
         cd v;
         if (n == m) v = d;
         else {
-            double inv = 1.0 / (double)(n * n - m * m);
-            double a = (2.0 * n - 1.0) * z;
+            double inv = c_rec.inv_up[n][m];
+            double a = c_rec.tw[n] * z;
             v = cd{(a * prev.re - r2 * prev2.re) * inv, (a * prev.im - r2 * prev2.im) * inv};
             prev2 = prev;
             prev = v;
@@ -43,7 +70,7 @@ __device__ inline void theta_column(int p, int m, double x, double y, double z, 
     const double ir2 = 1.0 / r2;
     cd d = mkc(sqrt(ir2), 0.0);
     for (int j = 1; j <= m; ++j) {
-        double s = (2.0 * j - 1.0) * ir2;
+        double s = c_rec.tw[j] * ir2;
         d = cd{s * (x * d.re - y * d.im), s * (x * d.im + y * d.re)};
     }
     cd prev2 = mkc(0.0, 0.0), prev = d;
@@ -52,8 +79,8 @@ __device__ inline void theta_column(int p, int m, double x, double y, double z, 
         cd v;
         if (n == m) v = d;
         else {
-            double a = (2.0 * n - 1.0) * z;
-            double b = (double)((n - 1) * (n - 1) - m * m);
+            double a = c_rec.tw[n] * z;
+            double b = c_rec.th_b[n][m];
             v = cd{(a * prev.re - b * prev2.re) * ir2, (a * prev.im - b * prev2.im) * ir2};
             prev2 = prev;
             prev = v;

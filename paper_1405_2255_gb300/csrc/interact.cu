@@ -10,25 +10,31 @@ namespace gb3 {
 // One warp per sink cell B; its sources (a segment of the sorted M2L list) pass
 // through shared memory one at a time: lanes 0..p build the columns of
 // Theta(s_B - z_A), all lanes expand conj(M_A); each lane then accumulates its
-// scheduled outputs F_n^m(s_B) in registers.
+// scheduled outputs F_n^m(s_B) in registers.  Warps take sinks from an atomic
+// counter over the sinks ordered by decreasing list length.
+template <int MAXQ>
 __global__ void __launch_bounds__(128) k_m2l(const int2* __restrict__ list, const int* __restrict__ seg_start,
-                                             const int* __restrict__ seg_end, int ncells, const d4* __restrict__ cen,
+                                             const int* __restrict__ seg_end, const int* __restrict__ order,
+                                             int nsinks, unsigned* __restrict__ work, const d4* __restrict__ cen,
                                              const double* __restrict__ M, int p, double* __restrict__ F,
                                              LaneSched sched) {
     extern __shared__ cd csm[];
-    const int wpb = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nco = ncoef(p);
     cd* T = csm + (size_t)wid * 2 * nco;
     cd* Mc = T + nco;
-    for (int B = blockIdx.x * wpb + wid; B < ncells; B += gridDim.x * wpb) {
+    const int cnt = sched.cnt[lane];
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(work, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= (unsigned)nsinks) break;
+        const int B = order[w];
         const int e0 = seg_start[B], e1 = seg_end[B];
-        if (e1 <= e0) continue;
         const d4 sB = cen[B];
-        const int cnt = sched.cnt[lane];
-        cd acc[kMaxPerLane];
+        cd acc[MAXQ];
 #pragma unroll
-        for (int q = 0; q < kMaxPerLane; ++q) acc[q] = mkc(0.0, 0.0);
+        for (int q = 0; q < MAXQ; ++q) acc[q] = mkc(0.0, 0.0);
         for (int e = e0; e < e1; ++e) {
             const int A = list[e].x;
             const d4 zA = cen[A];
@@ -36,13 +42,13 @@ __global__ void __launch_bounds__(128) k_m2l(const int2* __restrict__ list, cons
             expand_real(p, M + (size_t)A * nco, Mc, true, lane, 32);
             __syncwarp();
 #pragma unroll
-            for (int q = 0; q < kMaxPerLane; ++q)
+            for (int q = 0; q < MAXQ; ++q)
                 if (q < cnt) acc[q] = acc[q] + contract(p, sched.n[lane][q], sched.m[lane][q], Mc, T);
             __syncwarp();
         }
         double* out = F + (size_t)B * nco;
 #pragma unroll
-        for (int q = 0; q < kMaxPerLane; ++q) {
+        for (int q = 0; q < MAXQ; ++q) {
             if (q < cnt) {
                 int n = sched.n[lane][q], m = sched.m[lane][q];
                 out[cix(n, m)] = acc[q].re;
@@ -52,15 +58,67 @@ __global__ void __launch_bounds__(128) k_m2l(const int2* __restrict__ list, cons
     }
 }
 
-void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, const int* /*sinks*/, int ncells,
-                const d4* cen, const double* M, int p, double* F, cudaStream_t s) {
+// sinks with a non-empty M2L segment, ordered by decreasing segment length
+__global__ void k_sink_keys(const int* __restrict__ seg_start, const int* __restrict__ seg_end, int ncells,
+                            uint64_t* __restrict__ keys, int* __restrict__ vals) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += gridDim.x * blockDim.x) {
+        unsigned len = (unsigned)(seg_end[i] - seg_start[i]);
+        keys[i] = ((uint64_t)(0xffffffu - min(len, 0xffffffu)) << 32) | (unsigned)i;
+        vals[i] = len ? 1 : 0;
+    }
+}
+__global__ void k_sink_order(const uint64_t* __restrict__ keys, int ncells, int* __restrict__ order,
+                             unsigned* __restrict__ nsinks) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+        unsigned len = 0xffffffu - (unsigned)(k >> 32);
+        order[i] = (int)(k & 0xffffffffu);
+        if (len && (i == ncells - 1 || (0xffffffu - (unsigned)(keys[i + 1] >> 32)) == 0)) *nsinks = (unsigned)(i + 1);
+    }
+}
+
+size_t m2l_tmp_bytes(int ncells) {
+    size_t n = (size_t)(ncells > 0 ? ncells : 1);
+    return n * (2 * sizeof(uint64_t) + 3 * sizeof(int)) + radix_tmp_ints(n) * sizeof(int) + 64;
+}
+
+void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells, const d4* cen,
+                const double* M, int p, double* F, cudaStream_t s) {
     if (ncells <= 0) return;
+    init_rec_tables();
+    // order the sinks by decreasing work
+    uint64_t* k0 = (uint64_t*)tmp;
+    uint64_t* k1 = k0 + ncells;
+    int* v0 = (int*)(k1 + ncells);
+    int* v1 = v0 + ncells;
+    int* order = v1 + ncells;
+    unsigned* work = (unsigned*)(order + ncells);  // [0] counter, [1] number of sinks
+    int* rtmp = (int*)(work + 4);
+    cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
+    k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
+    int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 0, 56, s);
+    k_sink_order<<<grid_for(ncells, 256), 256, 0, s>>>(flip ? k1 : k0, ncells, order, work + 1); note_launch();
     const int wpb = 4;
     size_t sm = (size_t)wpb * 2 * ncoef(p) * sizeof(cd);
     LaneSched sched = make_lane_sched(p, kSchedDown);
-    unsigned g = (unsigned)((ncells + wpb - 1) / wpb);
-    if (g > 152u * 32u) g = 152u * 32u;
-    k_m2l<<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, ncells, cen, M, p, F, sched); note_launch();
+    int maxq = 0;
+    for (int l = 0; l < 32; ++l) maxq = sched.cnt[l] > maxq ? sched.cnt[l] : maxq;
+    int dev = 0, nsm = 152, bps = 4;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+#define GB3_M2L(Q)                                                                                         \
+    do {                                                                                                   \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l<Q>, wpb * 32, sm);                       \
+        unsigned g = (unsigned)(nsm * (bps > 0 ? bps : 1));                                                \
+        k_m2l<Q><<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, order, ncells, work, cen, M, p, F, sched); \
+        note_launch();                                                                                     \
+    } while (0)
+    // every cell is visited (empty segments cost one counter step); the order puts them last
+    if (maxq <= 4) GB3_M2L(4);
+    else if (maxq <= 8) GB3_M2L(8);
+    else if (maxq <= 12) GB3_M2L(12);
+    else GB3_M2L(24);
+#undef GB3_M2L
 }
 
 // ---------------------------------------------------------------- L2L
@@ -97,6 +155,7 @@ void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p,
     const int wpb = 4;
     size_t sm = (size_t)wpb * 2 * ncoef(p) * sizeof(cd);
     LaneSched sched = make_lane_sched(p, kSchedDown);
+    init_rec_tables();
     k_l2l<<<(ncl + wpb - 1) / wpb, wpb * 32, sm, s>>>(c, cen, lev_begin, lev_end, p, F, sched); note_launch();
 }
 
@@ -187,12 +246,10 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_fp64(const d4* __restric
                                                              const int* __restrict__ seg_start,
                                                              const int* __restrict__ seg_end,
                                                              const int* __restrict__ leaves, int nleaves,
-                                                             double* __restrict__ psi, double* __restrict__ acc,
-                                                             unsigned long long* coincident) {
+                                                             double* __restrict__ psi, double* __restrict__ acc) {
     __shared__ d4 tile_all[kP2PWarps][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     d4* tile = tile_all[wid];
-    unsigned long long ncoin = 0;
     for (int t = blockIdx.x * kP2PWarps + wid; t < nleaves; t += gridDim.x * kP2PWarps) {
         const int leaf = leaves[t];
         const int first = c.first[leaf], count = c.count[leaf];
@@ -223,8 +280,6 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_fp64(const d4* __restric
                                 ax = fma(q3, dx, ax);
                                 ay = fma(q3, dy, ay);
                                 az = fma(q3, dz, az);
-                            } else {
-                                ncoin += active;
                             }
                         }
                     }
@@ -238,7 +293,6 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_fp64(const d4* __restric
             }
         }
     }
-    if (ncoin) atomicAdd(coincident, ncoin);
 }
 
 static unsigned p2p_grid(int nleaves) {
@@ -247,11 +301,10 @@ static unsigned p2p_grid(int nleaves) {
 }
 
 void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_start, const int* seg_end,
-                     const int* leaves, int nleaves, double* psi, double* acc, unsigned long long* coincident,
-                     cudaStream_t s) {
+                     const int* leaves, int nleaves, double* psi, double* acc, cudaStream_t s) {
     if (nleaves <= 0) return;
     k_p2p_fp64<<<p2p_grid(nleaves), kP2PWarps * 32, 0, s>>>(xm, c, list, seg_start, seg_end, leaves, nleaves, psi,
-                                                            acc, coincident);
+                                                            acc);
     note_launch();
 }
 
@@ -290,6 +343,13 @@ __device__ inline ff ff_sub(float ahi, float alo, float bhi, float blo) {
     lo = __fsub_rn(lo, __fsub_rn(hi, s.hi));
     return ff{hi, lo};
 }
+__device__ inline void ff_add_shfl(ff& a, int o) {
+    float h = __shfl_xor_sync(0xffffffffu, a.hi, o), l = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    ff s = two_sum(a.hi, h);
+    float lo = __fadd_rn(__fadd_rn(a.lo, l), s.lo);
+    a.hi = __fadd_rn(s.hi, lo);
+    a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
+}
 __device__ inline void ff_acc(ff& a, float v) {
     ff s = two_sum(a.hi, v);
     float lo = __fadd_rn(a.lo, s.lo);
@@ -297,20 +357,54 @@ __device__ inline void ff_acc(ff& a, float v) {
     a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
 }
 
+// The mixed kernel streams the sink's sources through a warp-private tile that is
+// filled from consecutive source cells (so small cells do not leave it half
+// empty).  A chunk of n_s <= 32 sinks is replicated R = 1, 2 or 4 times across
+// the warp (lane = r * (32/R) + sink), replica r taking every R-th source of a
+// tile; the replicas' partial sums are added at the end.  Tiles that hold a
+// source cell containing the sink leaf skip the r = 0 pairs (the sink itself and
+// coincident particles); all other tiles need no test, since particles of
+// different leaves are never coincident.  TWO_FLOAT selects dx = (hi_a - hi_b) +
+// (lo_a - lo_b) instead of dx = hi_a - hi_b.
+template <bool TWO_FLOAT, bool GUARD>
+__device__ __forceinline__ void p2p_tile(const float4* __restrict__ th, const float4* __restrict__ tl, int nt, int r0,
+                                         int R, float bhx, float bhy, float bhz, float blx, float bly, float blz,
+                                         float& ps, float& ax, float& ay, float& az) {
+#pragma unroll 4
+    for (int j = r0; j < nt; j += R) {
+        const float4 qh = th[j];
+        float dx = qh.x - bhx, dy = qh.y - bhy, dz = qh.z - bhz;
+        if (TWO_FLOAT) {
+            const float4 ql = tl[j];
+            dx += ql.x - blx;
+            dy += ql.y - bly;
+            dz += ql.z - blz;
+        }
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float rinv = rsqrtf(r2);
+        if (GUARD) rinv = r2 > 0.f ? rinv : 0.f;
+        const float qm = qh.w * rinv;
+        const float q3 = qm * rinv * rinv;
+        ps += qm;
+        ax = fmaf(q3, dx, ax);
+        ay = fmaf(q3, dy, ay);
+        az = fmaf(q3, dz, az);
+    }
+}
+
+template <bool TWO_FLOAT>
 __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __restrict__ xhi,
                                                               const float4* __restrict__ xlo, Cells c,
                                                               const int2* __restrict__ list,
                                                               const int* __restrict__ seg_start,
                                                               const int* __restrict__ seg_end,
                                                               const int* __restrict__ leaves, int nleaves,
-                                                              double* __restrict__ psi, double* __restrict__ acc,
-                                                              unsigned long long* coincident) {
+                                                              double* __restrict__ psi, double* __restrict__ acc) {
     __shared__ float4 th_all[kP2PWarps][32];
-    __shared__ float4 tl_all[kP2PWarps][32];
+    __shared__ float4 tl_all[kP2PWarps][TWO_FLOAT ? 32 : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float4* th = th_all[wid];
     float4* tl = tl_all[wid];
-    unsigned ncoin = 0;
     for (int t = blockIdx.x * kP2PWarps + wid; t < nleaves; t += gridDim.x * kP2PWarps) {
         const int leaf = leaves[t];
         const int first = c.first[leaf], count = c.count[leaf];
@@ -319,8 +413,12 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __re
         const float slx = (float)(sc.x - (double)shx), sly = (float)(sc.y - (double)shy),
                     slz = (float)(sc.z - (double)shz);
         for (int s0 = 0; s0 < count; s0 += 32) {
-            const int i = first + s0 + lane;
-            const bool active = s0 + lane < count;
+            const int chunk = min(32, count - s0);
+            const int R = chunk <= 8 ? 4 : (chunk <= 16 ? 2 : 1);
+            const int S = 32 / R;
+            const int sink = lane % S, rep = lane / S;
+            const bool active = sink < chunk;
+            const int i = first + s0 + sink;
             float bhx = 0, bhy = 0, bhz = 0, blx = 0, bly = 0, blz = 0;
             if (active) {
                 const float4 h = xhi[i], l = xlo[i];
@@ -328,66 +426,99 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __re
                 bhx = rx.hi; blx = rx.lo; bhy = ry.hi; bly = ry.lo; bhz = rz.hi; blz = rz.lo;
             }
             ff aps = {0, 0}, aax = {0, 0}, aay = {0, 0}, aaz = {0, 0};
-            unsigned cc = 0;
+            float ps = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+            int fill = 0, since = 0;
+            bool guard = false;
+            auto flush_tile = [&](int nt) {
+                __syncwarp();
+                if (guard)
+                    p2p_tile<TWO_FLOAT, true>(th, tl, nt, rep, R, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+                else
+                    p2p_tile<TWO_FLOAT, false>(th, tl, nt, rep, R, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+                since += 32;
+                if (since >= 32 * R) {  // fold the FP32 partials into the two-float sums every ~32 pairs
+                    ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
+                    ps = ax = ay = az = 0.f;
+                    since = 0;
+                }
+                __syncwarp();
+            };
             for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
                 const int e0 = seg_start[cell], e1 = seg_end[cell];
                 for (int e = e0; e < e1; ++e) {
                     const int A = list[e].x;
                     const int af = c.first[A], an = c.count[A];
-                    for (int j0 = 0; j0 < an; j0 += 32) {
-                        __syncwarp();
-                        if (j0 + lane < an) {
-                            const float4 h = xhi[af + j0 + lane], l = xlo[af + j0 + lane];
+                    const bool contains = af <= first && first < af + an;
+                    for (int off = 0; off < an;) {
+                        const int k = min(32 - fill, an - off);
+                        if (lane < k) {
+                            const int j = af + off + lane;
+                            const float4 h = xhi[j], l = xlo[j];
                             const ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly),
                                      rz = ff_sub(h.z, l.z, shz, slz);
-                            th[lane] = make_float4(rx.hi, ry.hi, rz.hi, h.w);
-                            tl[lane] = make_float4(rx.lo, ry.lo, rz.lo, 0.f);
+                            th[fill + lane] = make_float4(rx.hi, ry.hi, rz.hi, h.w);
+                            if (TWO_FLOAT) tl[fill + lane] = make_float4(rx.lo, ry.lo, rz.lo, 0.f);
                         }
-                        __syncwarp();
-                        const int nt = min(32, an - j0);
-                        float ps = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-#pragma unroll 4
-                        for (int j = 0; j < nt; ++j) {
-                            const float4 qh = th[j], ql = tl[j];
-                            const float dx = (qh.x - bhx) + (ql.x - blx);
-                            const float dy = (qh.y - bhy) + (ql.y - bly);
-                            const float dz = (qh.z - bhz) + (ql.z - blz);
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            const bool nz = r2 > 0.f;
-                            const float rinv = nz ? rsqrtf(r2) : 0.f;
-                            cc += !nz;
-                            const float qm = qh.w * rinv;
-                            const float q3 = qm * rinv * rinv;
-                            ps += qm;
-                            ax = fmaf(q3, dx, ax);
-                            ay = fmaf(q3, dy, ay);
-                            az = fmaf(q3, dz, az);
+                        guard |= contains;
+                        fill += k;
+                        off += k;
+                        if (fill == 32) {
+                            flush_tile(32);
+                            fill = 0;
+                            guard = false;
                         }
-                        ff_acc(aps, ps);
-                        ff_acc(aax, ax);
-                        ff_acc(aay, ay);
-                        ff_acc(aaz, az);
                     }
                 }
             }
-            if (active) {
+            if (fill) flush_tile(fill);
+            ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
+            // add the replicas' partial sums (lanes sink, sink + S, ...)
+            for (int o = S; o < 32; o <<= 1) {
+                ff_add_shfl(aps, o); ff_add_shfl(aax, o); ff_add_shfl(aay, o); ff_add_shfl(aaz, o);
+            }
+            if (active && rep == 0) {
                 psi[i] = (double)aps.hi + (double)aps.lo;
                 acc[3 * (size_t)i] = (double)aax.hi + (double)aax.lo;
                 acc[3 * (size_t)i + 1] = (double)aay.hi + (double)aay.lo;
                 acc[3 * (size_t)i + 2] = (double)aaz.hi + (double)aaz.lo;
-                ncoin += cc;
             }
         }
     }
-    if (ncoin) atomicAdd(coincident, (unsigned long long)ncoin);
+}
+
+// number of ordered pairs (a != b) at distance 0: equal positions have equal keys,
+// so they sit next to each other in key order inside one leaf
+__global__ void k_coincident(const d4* __restrict__ xm, const uint64_t* __restrict__ keys, int n,
+                             unsigned long long* coincident) {
+    unsigned long long cnt = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const d4 p = xm[i];
+        for (int j = i - 1; j >= 0 && keys[j] == keys[i]; --j) {
+            const d4 q = xm[j];
+            cnt += (q.x == p.x && q.y == p.y && q.z == p.z) ? 2 : 0;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(coincident, cnt);
+}
+
+void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s) {
+    if (n > 1) {
+        k_coincident<<<grid_for(n, 256), 256, 0, s>>>(xm, keys, n, coincident);
+        note_launch();
+    }
 }
 
 void launch_p2p_mixed(const d4* /*xm*/, const float4* xhi, const float4* xlo, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* psi,
-                      double* acc, unsigned long long* coincident, cudaStream_t s) {
+                      double* acc, bool two_float, cudaStream_t s) {
     if (nleaves <= 0) return;
-    k_p2p_mixed<<<p2p_grid(nleaves), kP2PWarps * 32, 0, s>>>(xhi, xlo, c, list, seg_start, seg_end, leaves, nleaves,
-                                                             psi, acc, coincident);
+    if (two_float)
+        k_p2p_mixed<true><<<p2p_grid(nleaves), kP2PWarps * 32, 0, s>>>(xhi, xlo, c, list, seg_start, seg_end, leaves,
+                                                                       nleaves, psi, acc);
+    else
+        k_p2p_mixed<false><<<p2p_grid(nleaves), kP2PWarps * 32, 0, s>>>(xhi, xlo, c, list, seg_start, seg_end, leaves,
+                                                                        nleaves, psi, acc);
     note_launch();
 }
 

@@ -100,7 +100,8 @@ void launch_segments(const int2* list, long long npairs, int ncells, int* seg_st
                      cudaStream_t s);
 
 // ---------------------------------------------------------------- interactions (interact.cu)
-void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, const int* sinks, int nsinks,
+size_t m2l_tmp_bytes(int ncells);
+void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells,
                 const d4* cen, const double* M, int p, double* F, cudaStream_t s);
 void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F,
                       cudaStream_t s);
@@ -110,11 +111,13 @@ void launch_l2p(const d4* xm, Cells c, const d4* cen, const int* leaves, int nle
 // P2P (eq. 1) into psi_near/acc_near (sorted order): every leaf takes the sources of
 // its own P2P segment and those of its ancestors' segments.
 void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_start,
-                     const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc,
-                     unsigned long long* coincident, cudaStream_t s);
+                     const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc, cudaStream_t s);
+// two_float: dx from two-float leaf-relative positions; otherwise from their FP32 high parts
 void launch_p2p_mixed(const d4* xm, const float4* xhi, const float4* xlo, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves,
-                      double* psi, double* acc, unsigned long long* coincident, cudaStream_t s);
+                      double* psi, double* acc, bool two_float, cudaStream_t s);
+// ordered pairs of distinct particles at distance 0 (sorted keys and positions)
+void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s);
 void launch_split_positions(const d4* xm, int n, float4* xhi, float4* xlo, cudaStream_t s);
 // low-order f estimate (p = 0, 1/r^2 kernel): M2L, pass-down, P2P, evaluation
 void launch_f_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* Ff,

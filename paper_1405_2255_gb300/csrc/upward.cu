@@ -160,6 +160,7 @@ void launch_m2m_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p,
     const int wpb = 4;
     size_t sm = (size_t)wpb * 2 * ncoef(p) * sizeof(cd);
     LaneSched sched = make_lane_sched(p, kSchedUp);
+    init_rec_tables();
     k_m2m<<<(ncl + wpb - 1) / wpb, wpb * 32, sm, s>>>(c, cen, lev_begin, lev_end, p, M, sched); note_launch();
 }
 
