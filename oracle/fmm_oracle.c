@@ -28,10 +28,11 @@
  *           each triplet; sort by (key, original index).
  *   R-leaf  a cell is split iff it holds more than leaf_size particles and is above
  *           depth 21; daughters are the non-empty octants in key order.
- *   R-ses   leaf centre: exact smallest enclosing ball of its particles (Welzl);
- *           internal centre: exact smallest ball enclosing the daughters' balls
- *           (s_d, rho_d) (by enumeration of support sets of up to 4 balls);
- *           rho = exact max over the cell's particles of |x - s|.
+ *   R-ses   leaf centre: smallest enclosing ball of its particles (Welzl);
+ *           internal centre: smallest ball enclosing the daughters' balls
+ *           (s_d, rho_d) (enumeration of support sets of up to 4 balls); both in
+ *           IEEE single precision relative to the cell's first particle / first
+ *           daughter centre; rho = exact FP64 max over the particles of |x - s|.
  *   R-p2p   a pair (A,B) is summed directly when N_A*N_B < p2p_c * p^3 (checked
  *           first: the descendants of such a pair would all be summed directly).
  *   R-split split the cell with the larger rho (ties: A); never a leaf; A = B
@@ -333,14 +334,24 @@ long orc_direct(long n, const double *x, const double *mu, double G, long ns, co
 /* Smallest enclosing balls (Sec. 5.1.1; reading R-ses)                       */
 /* ------------------------------------------------------------------------- */
 
-/* Solve a k x k symmetric system (k <= 3) by Gaussian elimination with partial
- * pivoting.  Returns 0 when (numerically) singular. */
-static int solve_small(int k, double A[3][3], double b[2][3], double x[2][3])
+/* The balls are computed in IEEE single precision in coordinates relative to a
+ * reference point of the cell (its first particle, or its first daughter's
+ * centre); the centre is converted back to FP64 and the radius rho is then
+ * recomputed exactly in FP64 over the cell's particles (Sec. 4), so the
+ * single-precision ball only decides where the expansion centre sits.
+ * Tolerances: support sets are singular below 1e-6 of the Gram scale, a point
+ * or ball counts as inside within a relative 1e-5 of the radius. */
+#define MEB_SING 1e-6f
+#define MEB_IN 1e-5f
+
+/* Solve a k x k symmetric system (k <= 3) with two right-hand sides by Gaussian
+ * elimination with partial pivoting.  Returns 0 when (numerically) singular. */
+static int solve_small(int k, float A[3][3], float b[2][3], float x[2][3])
 {
-    double M[3][5];
-    double scale = 0;
+    float M[3][5];
+    float scale = 0;
     for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) if (fabs(A[i][j]) > scale) scale = fabs(A[i][j]);
+        for (int j = 0; j < k; ++j) if (fabsf(A[i][j]) > scale) scale = fabsf(A[i][j]);
     if (scale == 0) return 0;
     for (int i = 0; i < k; ++i) {
         for (int j = 0; j < k; ++j) M[i][j] = A[i][j];
@@ -349,17 +360,17 @@ static int solve_small(int k, double A[3][3], double b[2][3], double x[2][3])
     }
     for (int c = 0; c < k; ++c) {
         int piv = c;
-        for (int r = c + 1; r < k; ++r) if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
-        if (fabs(M[piv][c]) <= 1e-12 * scale) return 0;
-        if (piv != c) for (int j = 0; j < k + 2; ++j) { double t = M[c][j]; M[c][j] = M[piv][j]; M[piv][j] = t; }
+        for (int r = c + 1; r < k; ++r) if (fabsf(M[r][c]) > fabsf(M[piv][c])) piv = r;
+        if (fabsf(M[piv][c]) <= MEB_SING * scale) return 0;
+        if (piv != c) for (int j = 0; j < k + 2; ++j) { float t = M[c][j]; M[c][j] = M[piv][j]; M[piv][j] = t; }
         for (int r = c + 1; r < k; ++r) {
-            double fct = M[r][c] / M[c][c];
+            float fct = M[r][c] / M[c][c];
             for (int j = c; j < k + 2; ++j) M[r][j] -= fct * M[c][j];
         }
     }
     for (int rhs = 0; rhs < 2; ++rhs)
         for (int r = k - 1; r >= 0; --r) {
-            double s = M[r][k + rhs];
+            float s = M[r][k + rhs];
             for (int j = r + 1; j < k; ++j) s -= M[r][j] * x[rhs][j];
             x[rhs][r] = s / M[r][r];
         }
@@ -368,9 +379,12 @@ static int solve_small(int k, double A[3][3], double b[2][3], double x[2][3])
 
 /* The smallest ball whose boundary touches every ball of the support set
  * {(c_i, r_i)} from inside (|c - c_i| + r_i = R), with its centre in the affine hull
- * of the c_i.  With all r_i = 0 this is the circumsphere through the points.
+ * of the c_i: with u = c - c_0 = sum_j lam_j d_j, d_j = c_j - c_0, the tangency
+ * conditions give G lam = a + R b (G the Gram matrix of the d_j,
+ * a_j = (|d_j|^2 - r_j^2 + r_0^2)/2, b_j = r_j - r_0) and |u| = R - r_0 a quadratic
+ * in R.  With all r_i = 0 it is the circumsphere through the points.
  * Returns 0 if there is no such ball (degenerate support set). */
-static int support_ball(int k, const double c[][3], const double *r, double out_c[3], double *out_r)
+static int support_ball(int k, const float c[][3], const float *r, float out_c[3], float *out_r)
 {
     if (k == 1) {
         for (int d = 0; d < 3; ++d) out_c[d] = c[0][d];
@@ -378,47 +392,52 @@ static int support_ball(int k, const double c[][3], const double *r, double out_
         return 1;
     }
     int q = k - 1;
-    double D[3][3], G[3][3], rhs[2][3], sol[2][3];
+    float D[3][3], G[3][3], rhs[2][3], sol[2][3];
     for (int j = 0; j < q; ++j)
         for (int d = 0; d < 3; ++d) D[j][d] = c[j + 1][d] - c[0][d];
     for (int i = 0; i < q; ++i) {
         for (int j = 0; j < q; ++j) G[i][j] = D[i][0] * D[j][0] + D[i][1] * D[j][1] + D[i][2] * D[j][2];
-        rhs[0][i] = 0.5 * (G[i][i] - r[i + 1] * r[i + 1] + r[0] * r[0]);
+        rhs[0][i] = 0.5f * (G[i][i] - r[i + 1] * r[i + 1] + r[0] * r[0]);
         rhs[1][i] = r[i + 1] - r[0];
     }
     if (!solve_small(q, G, rhs, sol)) return 0;
-    double A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    float A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     for (int j = 0; j < q; ++j)
         for (int d = 0; d < 3; ++d) { A[d] += sol[0][j] * D[j][d]; B[d] += sol[1][j] * D[j][d]; }
-    double qa = B[0] * B[0] + B[1] * B[1] + B[2] * B[2] - 1.0;
-    double qb = A[0] * B[0] + A[1] * B[1] + A[2] * B[2] + r[0];
-    double qc = A[0] * A[0] + A[1] * A[1] + A[2] * A[2] - r[0] * r[0];
-    double rmax = r[0];
+    float qa = B[0] * B[0] + B[1] * B[1] + B[2] * B[2] - 1.0f;
+    float qb = A[0] * B[0] + A[1] * B[1] + A[2] * B[2] + r[0];
+    float qc = A[0] * A[0] + A[1] * A[1] + A[2] * A[2] - r[0] * r[0];
+    float rmax = r[0];
     for (int i = 1; i < k; ++i) if (r[i] > rmax) rmax = r[i];
-    double R = -1.0;
-    if (fabs(qa) < 1e-14) {
+    float R = -1.0f;
+    if (fabsf(qa) < 1e-6f) {
         if (qb == 0) return 0;
-        R = -qc / (2.0 * qb);
+        R = -qc / (2.0f * qb);
     } else {
-        double disc = qb * qb - qa * qc;
+        float disc = qb * qb - qa * qc;
         if (disc < 0) {
-            if (disc < -1e-12 * (qb * qb + fabs(qa * qc))) return 0;
+            if (disc < -MEB_SING * (qb * qb + fabsf(qa * qc))) return 0;
             disc = 0;
         }
-        double sq = sqrt(disc);
-        double r1 = (-qb - sq) / qa, r2 = (-qb + sq) / qa;
-        double lo = r1 < r2 ? r1 : r2, hi = r1 < r2 ? r2 : r1;
-        double tol = 1e-12 * (fabs(rmax) + 1e-300);
+        float sq = sqrtf(disc);
+        float r1 = (-qb - sq) / qa, r2 = (-qb + sq) / qa;
+        float lo = r1 < r2 ? r1 : r2, hi = r1 < r2 ? r2 : r1;
+        float tol = MEB_SING * fabsf(rmax);
         if (lo >= rmax - tol) R = lo;
         else if (hi >= rmax - tol) R = hi;
         else return 0;
     }
-    if (!(R >= 0) || R < rmax - 1e-12 * (rmax + 1e-300)) return 0;
+    if (!(R >= 0) || R < rmax - MEB_SING * rmax) return 0;
     for (int d = 0; d < 3; ++d) out_c[d] = c[0][d] + A[d] + R * B[d];
     *out_r = R;
     return 1;
 }
 
+static inline float dist3f(const float a[3], const float b[3])
+{
+    float dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return sqrtf(dx * dx + dy * dy + dz * dz);
+}
 static inline double dist3(const double a[3], const double b[3])
 {
     double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
@@ -426,75 +445,87 @@ static inline double dist3(const double a[3], const double b[3])
 }
 
 /* smallest ball with all support points on its boundary (Welzl's b_md(empty, R)) */
-static void trivial_ball(int nr, const double R[][3], double c[3], double *rad)
+static void trivial_ball(int nr, const float R[][3], float c[3], float *rad)
 {
-    double zr[4] = {0, 0, 0, 0};
-    if (nr == 0) { c[0] = c[1] = c[2] = 0; *rad = -1.0; return; }
+    const float zr[4] = {0, 0, 0, 0};
+    if (nr == 0) { c[0] = c[1] = c[2] = 0; *rad = -1.0f; return; }
     if (support_ball(nr, R, zr, c, rad)) return;
-    /* degenerate support set: fall back to the smallest ball through a subset that
-     * still contains every support point */
-    double best = -1;
+    /* degenerate support set: the smallest ball through a subset that still
+     * contains every support point */
+    float best = -1;
     for (int mask = 1; mask < (1 << nr); ++mask) {
-        double sub[4][3]; int k = 0;
+        float sub[4][3]; int k = 0;
         for (int i = 0; i < nr; ++i) if (mask & (1 << i)) { for (int d = 0; d < 3; ++d) sub[k][d] = R[i][d]; ++k; }
-        double cc[3], rr;
+        float cc[3], rr;
         if (!support_ball(k, sub, zr, cc, &rr)) continue;
         int ok = 1;
-        for (int i = 0; i < nr; ++i) if (dist3(R[i], cc) > rr * (1 + 1e-12) + 1e-300) { ok = 0; break; }
+        for (int i = 0; i < nr; ++i) if (dist3f(R[i], cc) > rr * (1.0f + MEB_IN)) { ok = 0; break; }
         if (ok && (best < 0 || rr < best)) { best = rr; c[0] = cc[0]; c[1] = cc[1]; c[2] = cc[2]; *rad = rr; }
     }
 }
 
-static inline int in_ball(const double pt[3], const double c[3], double rad)
+static inline int in_ball(const float pt[3], const float c[3], float rad)
 {
     if (rad < 0) return 0;
-    return dist3(pt, c) <= rad * (1.0 + 1e-12);
+    return dist3f(pt, c) <= rad * (1.0f + MEB_IN);
 }
 
 /* Welzl's recursion: the smallest ball enclosing P[0..np) with R on its boundary */
-static void welzl(int np, const double P[][3], int nr, double R[4][3], double c[3], double *rad)
+static void welzl(int np, const float P[][3], int nr, float R[4][3], float c[3], float *rad)
 {
-    if (np == 0 || nr == 4) { trivial_ball(nr, (const double(*)[3])R, c, rad); return; }
+    if (np == 0 || nr == 4) { trivial_ball(nr, (const float(*)[3])R, c, rad); return; }
     welzl(np - 1, P, nr, R, c, rad);
     if (in_ball(P[np - 1], c, *rad)) return;
     for (int d = 0; d < 3; ++d) R[nr][d] = P[np - 1][d];
     welzl(np - 1, P, nr + 1, R, c, rad);
 }
 
-/* smallest enclosing ball of n points (exact up to rounding) */
+/* smallest enclosing ball of n points: single precision, relative to the first point */
 int orc_meb_points(int n, const double *pts, double c[3], double *rad)
 {
-    double R[4][3];
     if (n <= 0) { c[0] = c[1] = c[2] = 0; *rad = 0; return 0; }
-    welzl(n, (const double(*)[3])pts, 0, R, c, rad);
-    if (*rad < 0) *rad = 0;
+    float (*P)[3] = malloc(sizeof(float[3]) * n);
+    for (int i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) P[i][d] = (float)(pts[3 * i + d] - pts[d]);
+    float R[4][3], cf[3], rf;
+    welzl(n, (const float(*)[3])P, 0, R, cf, &rf);
+    free(P);
+    for (int d = 0; d < 3; ++d) c[d] = pts[d] + (double)cf[d];
+    *rad = rf < 0 ? 0.0 : (double)rf;
     return 1;
 }
 
 /* smallest ball enclosing n <= 8 balls: the smallest, over all support sets of 1..4
- * balls, of the support balls that contain every ball */
+ * balls (enumerated by bit mask), of the support balls that contain every ball;
+ * single precision, relative to the first ball's centre */
 int orc_meb_balls(int n, const double *cen, const double *radii, double c[3], double *rad)
 {
-    double best = -1;
+    float C[8][3], Rr[8];
+    for (int i = 0; i < n; ++i) {
+        for (int d = 0; d < 3; ++d) C[i][d] = (float)(cen[3 * i + d] - cen[d]);
+        Rr[i] = (float)radii[i];
+    }
+    float best = -1, bc[3] = {0, 0, 0};
     for (int mask = 1; mask < (1 << n); ++mask) {
-        int k = 0; double sc[4][3], sr[4];
+        int k = 0; float sc[4][3], sr[4];
         for (int i = 0; i < n && k <= 4; ++i)
             if (mask & (1 << i)) {
                 if (k == 4) { k = 5; break; }
-                for (int d = 0; d < 3; ++d) sc[k][d] = cen[3 * i + d];
-                sr[k] = radii[i];
+                for (int d = 0; d < 3; ++d) sc[k][d] = C[i][d];
+                sr[k] = Rr[i];
                 ++k;
             }
         if (k > 4) continue;
-        double cc[3], rr;
-        if (!support_ball(k, (const double(*)[3])sc, sr, cc, &rr)) continue;
+        float cc[3], rr;
+        if (!support_ball(k, (const float(*)[3])sc, sr, cc, &rr)) continue;
         int ok = 1;
         for (int i = 0; i < n; ++i)
-            if (dist3(&cen[3 * i], cc) + radii[i] > rr * (1 + 1e-12) + 1e-300) { ok = 0; break; }
-        if (ok && (best < 0 || rr < best)) { best = rr; c[0] = cc[0]; c[1] = cc[1]; c[2] = cc[2]; }
+            if (dist3f(C[i], cc) + Rr[i] > rr * (1.0f + MEB_IN)) { ok = 0; break; }
+        if (ok && (best < 0 || rr < best)) { best = rr; bc[0] = cc[0]; bc[1] = cc[1]; bc[2] = cc[2]; }
     }
     if (best < 0) return 0;
-    *rad = best;
+    for (int d = 0; d < 3; ++d) c[d] = cen[d] + (double)bc[d];
+    *rad = (double)best;
     return 1;
 }
 
@@ -653,7 +684,8 @@ static void cell_geometry(tree_t *t, long ci)
             for (int k = 0; k < 3; ++k) cen[3 * j + k] = d->s[k];
             rad[j] = d->rho;
         }
-        orc_meb_balls((int)c->nchild, cen, rad, c->s, &c->rho);
+        if (!orc_meb_balls((int)c->nchild, cen, rad, c->s, &c->rho))
+            for (int k = 0; k < 3; ++k) c->s[k] = cen[k]; /* no valid support set: first daughter's centre */
     }
     double rmax = 0, m = 0, mx[3] = {0, 0, 0};
     for (long i = 0; i < c->count; ++i) {

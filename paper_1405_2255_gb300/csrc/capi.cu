@@ -325,7 +325,7 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     launch_p2m(P<d4>(ctx->xm), c, c.cr, P<int>(ctx->leaves), ctx->nleaves, pe, P<double>(ctx->M1), s);
     for (int L = nlev - 1; L >= 0; --L)
         launch_m2m_level(c, c.cr, ctx->lev_start[L], ctx->lev_start[L + 1], pe, P<double>(ctx->M1), s);
-    TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc)));
+    TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc, pe)));
     launch_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc, c.cr,
                P<double>(ctx->M1), pe, P<double>(ctx->F1), s);
     for (int L = 1; L < nlev; ++L) launch_l2l_level(c, c.cr, ctx->lev_start[L], ctx->lev_start[L + 1], pe, P<double>(ctx->F1), s);
@@ -447,7 +447,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
 
     // A9: M2L
     CU(cudaMemsetAsync(ctx->F.p, 0, sizeof(double) * nco * (size_t)nc, s));
-    TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc)));
+    TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc, prm.p)));
     launch_m2l(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc, c.sr,
                P<double>(ctx->M), prm.p, P<double>(ctx->F), s);
     if (timing) CU(cudaEventRecord(ctx->ev[EV_M2L], s));

@@ -7,22 +7,40 @@
 namespace gb3 {
 
 // ---------------------------------------------------------------- M2L
-// One warp per sink cell B; its sources (a segment of the sorted M2L list) pass
-// through shared memory one at a time: lanes 0..p build the columns of
-// Theta(s_B - z_A), all lanes expand conj(M_A); each lane then accumulates its
-// scheduled outputs F_n^m(s_B) in registers.  Warps take sinks from an atomic
-// counter over the sinks ordered by decreasing list length.
-template <int MAXQ>
-__global__ void __launch_bounds__(128) k_m2l(const int2* __restrict__ list, const int* __restrict__ seg_start,
-                                             const int* __restrict__ seg_end, const int* __restrict__ order,
-                                             int nsinks, unsigned* __restrict__ work, const d4* __restrict__ cen,
-                                             const double* __restrict__ M, int p, double* __restrict__ F,
-                                             LaneSched sched) {
+// conj(M_A) of every cell as a full complex array (all m), once per evaluation, so
+// that M2L reads it instead of re-expanding the real storage for every pair
+__global__ void k_expand_conj(const double* __restrict__ M, int ncells, int p, cd* __restrict__ Mc) {
+    const int nco = ncoef(p);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)ncells * nco;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int cell = (int)(t / nco), i = (int)(t % nco);
+        int n = (int)sqrtf((float)i);
+        while (n * n > i) --n;
+        while ((n + 1) * (n + 1) <= i) ++n;
+        const cd v = load_real_storage(M + (size_t)cell * nco, n, i - n * n - n);
+        Mc[t] = conjc(v);
+    }
+}
+
+// One warp per sink cell B.  Its sources (a segment of the sorted M2L list) are
+// taken NB at a time: the warp copies conj(M_A) of the NB sources to shared
+// memory and builds Theta(s_B - z_A) for all NB pairs at once (32/NB lanes per
+// pair, each lane a few m-columns), so that the serial recurrences of one pair
+// do not leave the other lanes idle; then each lane accumulates its scheduled
+// outputs F_n^m(s_B) over the NB pairs in registers.  Warps take sinks from an
+// atomic counter over the sinks ordered by decreasing list length.
+template <int MAXQ, int NB>
+__global__ void __launch_bounds__(64) k_m2l(const int2* __restrict__ list, const int* __restrict__ seg_start,
+                                            const int* __restrict__ seg_end, const int* __restrict__ order,
+                                            int nsinks, unsigned* __restrict__ work, const d4* __restrict__ cen,
+                                            const cd* __restrict__ Mc, int p, double* __restrict__ F,
+                                            LaneSched sched) {
     extern __shared__ cd csm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nco = ncoef(p);
-    cd* T = csm + (size_t)wid * 2 * nco;
-    cd* Mc = T + nco;
+    cd* T = csm + (size_t)wid * 2 * NB * nco;  // [NB][nco]
+    cd* Mb = T + NB * nco;                     // [NB][nco]
+    constexpr int LPP = 32 / NB;               // lanes per pair while building Theta
     const int cnt = sched.cnt[lane];
     for (;;) {
         unsigned w = 0;
@@ -31,19 +49,34 @@ __global__ void __launch_bounds__(128) k_m2l(const int2* __restrict__ list, cons
         if (w >= (unsigned)nsinks) break;
         const int B = order[w];
         const int e0 = seg_start[B], e1 = seg_end[B];
+        if (e1 <= e0) continue;
         const d4 sB = cen[B];
         cd acc[MAXQ];
 #pragma unroll
         for (int q = 0; q < MAXQ; ++q) acc[q] = mkc(0.0, 0.0);
-        for (int e = e0; e < e1; ++e) {
-            const int A = list[e].x;
-            const d4 zA = cen[A];
-            if (lane <= p) theta_column(p, lane, sB.x - zA.x, sB.y - zA.y, sB.z - zA.z, T);
-            expand_real(p, M + (size_t)A * nco, Mc, true, lane, 32);
+        for (int eb = e0; eb < e1; eb += NB) {
+            const int nb = min(NB, e1 - eb);
+            // conj(M) of the batch
+            for (int b = 0; b < nb; ++b) {
+                const cd* src = Mc + (size_t)list[eb + b].x * nco;
+                for (int i = lane; i < nco; i += 32) Mb[b * nco + i] = src[i];
+            }
+            // Theta of the batch
+            {
+                const int b = lane / LPP, sub = lane % LPP;
+                if (b < nb) {
+                    const d4 zA = cen[list[eb + b].x];
+                    const double x = sB.x - zA.x, y = sB.y - zA.y, z = sB.z - zA.z;
+                    for (int m = sub; m <= p; m += LPP) theta_column(p, m, x, y, z, T + b * nco);
+                }
+            }
             __syncwarp();
+            for (int b = 0; b < nb; ++b) {
 #pragma unroll
-            for (int q = 0; q < MAXQ; ++q)
-                if (q < cnt) acc[q] = acc[q] + contract(p, sched.n[lane][q], sched.m[lane][q], Mc, T);
+                for (int q = 0; q < MAXQ; ++q)
+                    if (q < cnt)
+                        acc[q] = acc[q] + contract(p, sched.n[lane][q], sched.m[lane][q], Mb + b * nco, T + b * nco);
+            }
             __syncwarp();
         }
         double* out = F + (size_t)B * nco;
@@ -77,9 +110,26 @@ __global__ void k_sink_order(const uint64_t* __restrict__ keys, int ncells, int*
     }
 }
 
-size_t m2l_tmp_bytes(int ncells) {
+size_t m2l_tmp_bytes(int ncells, int p) {
     size_t n = (size_t)(ncells > 0 ? ncells : 1);
-    return n * (2 * sizeof(uint64_t) + 3 * sizeof(int)) + radix_tmp_ints(n) * sizeof(int) + 64;
+    return n * (2 * sizeof(uint64_t) + 3 * sizeof(int)) + radix_tmp_ints(n) * sizeof(int) + 256 +
+           n * (size_t)ncoef(p) * sizeof(cd);
+}
+
+template <int MAXQ, int NB>
+static void m2l_launch(const int2* list, const int* seg_start, const int* seg_end, const int* order, int ncells,
+                       unsigned* work, const d4* cen, const cd* Mc, int p, double* F, const LaneSched& sched,
+                       cudaStream_t s) {
+    const int wpb = 2;
+    size_t sm = (size_t)wpb * 2 * NB * ncoef(p) * sizeof(cd);
+    cudaFuncSetAttribute(k_m2l<MAXQ, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int dev = 0, nsm = 152, bps = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l<MAXQ, NB>, wpb * 32, sm);
+    unsigned g = (unsigned)(nsm * (bps > 0 ? bps : 1));
+    k_m2l<MAXQ, NB><<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, order, ncells, work, cen, Mc, p, F, sched);
+    note_launch();
 }
 
 void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells, const d4* cen,
@@ -94,31 +144,25 @@ void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void
     int* order = v1 + ncells;
     unsigned* work = (unsigned*)(order + ncells);  // [0] counter, [1] number of sinks
     int* rtmp = (int*)(work + 4);
+    cd* Mc = (cd*)(((uintptr_t)(rtmp + radix_tmp_ints(ncells)) + 255) & ~(uintptr_t)255);
     cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
     k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
     int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 0, 56, s);
     k_sink_order<<<grid_for(ncells, 256), 256, 0, s>>>(flip ? k1 : k0, ncells, order, work + 1); note_launch();
-    const int wpb = 4;
-    size_t sm = (size_t)wpb * 2 * ncoef(p) * sizeof(cd);
+    k_expand_conj<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(M, ncells, p, Mc); note_launch();
     LaneSched sched = make_lane_sched(p, kSchedDown);
     int maxq = 0;
     for (int l = 0; l < 32; ++l) maxq = sched.cnt[l] > maxq ? sched.cnt[l] : maxq;
-    int dev = 0, nsm = 152, bps = 4;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-#define GB3_M2L(Q)                                                                                         \
-    do {                                                                                                   \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l<Q>, wpb * 32, sm);                       \
-        unsigned g = (unsigned)(nsm * (bps > 0 ? bps : 1));                                                \
-        k_m2l<Q><<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, order, ncells, work, cen, M, p, F, sched); \
-        note_launch();                                                                                     \
-    } while (0)
     // every cell is visited (empty segments cost one counter step); the order puts them last
-    if (maxq <= 4) GB3_M2L(4);
-    else if (maxq <= 8) GB3_M2L(8);
-    else if (maxq <= 12) GB3_M2L(12);
-    else GB3_M2L(24);
-#undef GB3_M2L
+    if (p <= 12) {
+        if (maxq <= 4) m2l_launch<4, 8>(list, seg_start, seg_end, order, ncells, work, cen, Mc, p, F, sched, s);
+        else m2l_launch<8, 8>(list, seg_start, seg_end, order, ncells, work, cen, Mc, p, F, sched, s);
+    } else if (p <= 16) {
+        if (maxq <= 8) m2l_launch<8, 4>(list, seg_start, seg_end, order, ncells, work, cen, Mc, p, F, sched, s);
+        else m2l_launch<12, 4>(list, seg_start, seg_end, order, ncells, work, cen, Mc, p, F, sched, s);
+    } else {
+        m2l_launch<24, 2>(list, seg_start, seg_end, order, ncells, work, cen, Mc, p, F, sched, s);
+    }
 }
 
 // ---------------------------------------------------------------- L2L

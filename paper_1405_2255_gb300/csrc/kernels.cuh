@@ -100,7 +100,7 @@ void launch_segments(const int2* list, long long npairs, int ncells, int* seg_st
                      cudaStream_t s);
 
 // ---------------------------------------------------------------- interactions (interact.cu)
-size_t m2l_tmp_bytes(int ncells);
+size_t m2l_tmp_bytes(int ncells, int p);
 void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells,
                 const d4* cen, const double* M, int p, double* F, cudaStream_t s);
 void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F,

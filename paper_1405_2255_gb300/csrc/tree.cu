@@ -284,18 +284,27 @@ void launch_split_level(const uint64_t* keys, Cells c, int lev_begin, int lev_en
 }
 
 // ------------------------------------------------------------------ A4 geometry
-// Smallest enclosing balls (Sec. 5.1.1).  support_ball: the smallest ball whose
-// boundary touches each of k <= 4 balls (c_i, r_i) from inside, centre in the
-// affine hull of the c_i: with u = c - c_0 = sum_j lam_j d_j, d_j = c_j - c_0,
-// the tangency conditions give G lam = a + R b (G the Gram matrix of the d_j,
-// a_j = (|d_j|^2 - r_j^2 + r_0^2)/2, b_j = r_j - r_0), and |u| = R - r_0 gives a
-// quadratic in R.  With all r_i = 0 it is the circumsphere of the points.
-__device__ bool solve_small_dev(int k, double A[3][3], double b0[3], double b1[3], double x0[3], double x1[3]) {
-    double M[3][5];
-    double scale = 0;
+// Expansion centres z = s = centre of the smallest enclosing sphere (Sec. 5.1.1).
+// The balls are computed in IEEE single precision in coordinates relative to a
+// reference point of the cell (its first particle, or its first daughter's
+// centre); the centre is converted back to FP64 and the radius rho is then
+// recomputed exactly in FP64 over the cell's particles (Sec. 4).  Single
+// precision keeps these small serial solves off the scarce FP64 pipe.
+// support_ball: the smallest ball whose boundary touches each of k <= 4 balls
+// (c_i, r_i) from inside, centre in the affine hull of the c_i: with
+// u = c - c_0 = sum_j lam_j d_j, d_j = c_j - c_0, the tangency conditions give
+// G lam = a + R b (G the Gram matrix of the d_j, a_j = (|d_j|^2 - r_j^2 + r_0^2)/2,
+// b_j = r_j - r_0), and |u| = R - r_0 gives a quadratic in R.  With all r_i = 0 it
+// is the circumsphere of the points.
+constexpr float kMebSing = 1e-6f;  // singular support set (relative to the Gram scale)
+constexpr float kMebIn = 1e-5f;    // inside tolerance, relative to the radius
+
+__device__ bool solve_small_dev(int k, float A[3][3], float b0[3], float b1[3], float x0[3], float x1[3]) {
+    float M[3][5];
+    float scale = 0;
     for (int i = 0; i < k; ++i)
         for (int j = 0; j < k; ++j)
-            if (fabs(A[i][j]) > scale) scale = fabs(A[i][j]);
+            if (fabsf(A[i][j]) > scale) scale = fabsf(A[i][j]);
     if (scale == 0) return false;
     for (int i = 0; i < k; ++i) {
         for (int j = 0; j < k; ++j) M[i][j] = A[i][j];
@@ -305,21 +314,21 @@ __device__ bool solve_small_dev(int k, double A[3][3], double b0[3], double b1[3
     for (int col = 0; col < k; ++col) {
         int piv = col;
         for (int r = col + 1; r < k; ++r)
-            if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
-        if (fabs(M[piv][col]) <= 1e-12 * scale) return false;
+            if (fabsf(M[r][col]) > fabsf(M[piv][col])) piv = r;
+        if (fabsf(M[piv][col]) <= kMebSing * scale) return false;
         if (piv != col)
             for (int j = 0; j < k + 2; ++j) {
-                double t = M[col][j];
+                float t = M[col][j];
                 M[col][j] = M[piv][j];
                 M[piv][j] = t;
             }
         for (int r = col + 1; r < k; ++r) {
-            double fct = M[r][col] / M[col][col];
+            float fct = M[r][col] / M[col][col];
             for (int j = col; j < k + 2; ++j) M[r][j] -= fct * M[col][j];
         }
     }
     for (int r = k - 1; r >= 0; --r) {
-        double s0 = M[r][k], s1 = M[r][k + 1];
+        float s0 = M[r][k], s1 = M[r][k + 1];
         for (int j = r + 1; j < k; ++j) {
             s0 -= M[r][j] * x0[j];
             s1 -= M[r][j] * x1[j];
@@ -330,86 +339,90 @@ __device__ bool solve_small_dev(int k, double A[3][3], double b0[3], double b1[3
     return true;
 }
 
-__device__ bool support_ball_dev(int k, const double (*c)[3], const double* r, double oc[3], double& orad) {
+__device__ bool support_ball_dev(int k, const float (*c)[3], const float* r, float oc[3], float& orad) {
     if (k == 1) {
         oc[0] = c[0][0]; oc[1] = c[0][1]; oc[2] = c[0][2];
         orad = r[0];
         return true;
     }
     int q = k - 1;
-    double D[3][3], G[3][3], a[3], b[3], la[3], lb[3];
+    float D[3][3], G[3][3], a[3], b[3], la[3], lb[3];
     for (int j = 0; j < q; ++j)
         for (int d = 0; d < 3; ++d) D[j][d] = c[j + 1][d] - c[0][d];
     for (int i = 0; i < q; ++i) {
         for (int j = 0; j < q; ++j) G[i][j] = D[i][0] * D[j][0] + D[i][1] * D[j][1] + D[i][2] * D[j][2];
-        a[i] = 0.5 * (G[i][i] - r[i + 1] * r[i + 1] + r[0] * r[0]);
+        a[i] = 0.5f * (G[i][i] - r[i + 1] * r[i + 1] + r[0] * r[0]);
         b[i] = r[i + 1] - r[0];
     }
     if (!solve_small_dev(q, G, a, b, la, lb)) return false;
-    double A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    float A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     for (int j = 0; j < q; ++j)
         for (int d = 0; d < 3; ++d) {
             A[d] += la[j] * D[j][d];
             B[d] += lb[j] * D[j][d];
         }
-    double qa = B[0] * B[0] + B[1] * B[1] + B[2] * B[2] - 1.0;
-    double qb = A[0] * B[0] + A[1] * B[1] + A[2] * B[2] + r[0];
-    double qc = A[0] * A[0] + A[1] * A[1] + A[2] * A[2] - r[0] * r[0];
-    double rmax = r[0];
+    float qa = B[0] * B[0] + B[1] * B[1] + B[2] * B[2] - 1.0f;
+    float qb = A[0] * B[0] + A[1] * B[1] + A[2] * B[2] + r[0];
+    float qc = A[0] * A[0] + A[1] * A[1] + A[2] * A[2] - r[0] * r[0];
+    float rmax = r[0];
     for (int i = 1; i < k; ++i)
         if (r[i] > rmax) rmax = r[i];
-    double R;
-    if (fabs(qa) < 1e-14) {
+    float R;
+    if (fabsf(qa) < 1e-6f) {
         if (qb == 0) return false;
-        R = -qc / (2.0 * qb);
+        R = -qc / (2.0f * qb);
     } else {
-        double disc = qb * qb - qa * qc;
+        float disc = qb * qb - qa * qc;
         if (disc < 0) {
-            if (disc < -1e-12 * (qb * qb + fabs(qa * qc))) return false;
+            if (disc < -kMebSing * (qb * qb + fabsf(qa * qc))) return false;
             disc = 0;
         }
-        double sq = sqrt(disc);
-        double r1 = (-qb - sq) / qa, r2 = (-qb + sq) / qa;
-        double lo = r1 < r2 ? r1 : r2, hi = r1 < r2 ? r2 : r1;
-        double tol = 1e-12 * (fabs(rmax) + 1e-300);
+        float sq = sqrtf(disc);
+        float r1 = (-qb - sq) / qa, r2 = (-qb + sq) / qa;
+        float lo = r1 < r2 ? r1 : r2, hi = r1 < r2 ? r2 : r1;
+        float tol = kMebSing * fabsf(rmax);
         if (lo >= rmax - tol) R = lo;
         else if (hi >= rmax - tol) R = hi;
         else return false;
     }
-    if (!(R >= 0) || R < rmax - 1e-12 * (rmax + 1e-300)) return false;
+    if (!(R >= 0) || R < rmax - kMebSing * rmax) return false;
     for (int d = 0; d < 3; ++d) oc[d] = c[0][d] + A[d] + R * B[d];
     orad = R;
     return true;
 }
 
+__device__ inline float dist3f_dev(const float a[3], const float b[3]) {
+    float dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return sqrtf(dx * dx + dy * dy + dz * dz);
+}
 __device__ inline double dist3_dev(const double a[3], const double b[3]) {
     double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
     return sqrt(dx * dx + dy * dy + dz * dz);
 }
 
 // Welzl's b_md(empty, R): the smallest ball with the support points on its boundary
-__device__ void trivial_ball_dev(int nr, const double (*R)[3], double c[3], double& rad) {
-    const double zr[4] = {0, 0, 0, 0};
+__device__ void trivial_ball_dev(int nr, const float (*R)[3], float c[3], float& rad) {
+    const float zr[4] = {0, 0, 0, 0};
     if (nr == 0) {
         c[0] = c[1] = c[2] = 0;
-        rad = -1.0;
+        rad = -1.0f;
         return;
     }
     if (support_ball_dev(nr, R, zr, c, rad)) return;
-    double best = -1;
+    float best = -1;
     for (int mask = 1; mask < (1 << nr); ++mask) {
-        double sub[4][3];
+        float sub[4][3];
         int k = 0;
         for (int i = 0; i < nr; ++i)
             if (mask & (1 << i)) {
                 for (int d = 0; d < 3; ++d) sub[k][d] = R[i][d];
                 ++k;
             }
-        double cc[3], rr;
+        float cc[3], rr;
         if (!support_ball_dev(k, sub, zr, cc, rr)) continue;
         bool ok = true;
         for (int i = 0; i < nr; ++i)
-            if (dist3_dev(R[i], cc) > rr * (1 + 1e-12) + 1e-300) {
+            if (dist3f_dev(R[i], cc) > rr * (1.0f + kMebIn)) {
                 ok = false;
                 break;
             }
@@ -421,9 +434,9 @@ __device__ void trivial_ball_dev(int nr, const double (*R)[3], double c[3], doub
     }
 }
 
-__device__ inline bool in_ball_dev(const double p[3], const double c[3], double rad) {
+__device__ inline bool in_ball_dev(const float p[3], const float c[3], float rad) {
     if (rad < 0) return false;
-    return dist3_dev(p, c) <= rad * (1.0 + 1e-12);
+    return dist3f_dev(p, c) <= rad * (1.0f + kMebIn);
 }
 
 __device__ inline void ld3(const d4* xm, int i, double p[3]) {
@@ -431,19 +444,35 @@ __device__ inline void ld3(const d4* xm, int i, double p[3]) {
     p[0] = v.x; p[1] = v.y; p[2] = v.z;
 }
 
+// leaf points relative to the first one, in single precision: from the warp's
+// shared buffer (first kMebBuf points) or converted on the fly
+constexpr int kMebBuf = 128;
+struct LeafPts {
+    const float (*buf)[3];
+    const d4* X;
+    double o[3];
+    __device__ inline void get(int i, float q[3]) const {
+        if (i < kMebBuf) {
+            q[0] = buf[i][0]; q[1] = buf[i][1]; q[2] = buf[i][2];
+        } else {
+            d4 v = X[i];
+            q[0] = (float)(v.x - o[0]); q[1] = (float)(v.y - o[1]); q[2] = (float)(v.z - o[2]);
+        }
+    }
+};
+
 // Welzl's recursion for points (smallest ball of P with R on its boundary):
 // W(i, R) scans P[0..i) in order and, at the first point outside the current
-// ball, restarts one level deeper with that point added to R.
-// Warp form of the same recursion: each level scans its prefix 32 points at a
-// time with a ballot for the first point outside the current ball, so the
-// sequence of balls is exactly that of the sequential loops above.
-__device__ int first_outside(const d4* P, int from, int to, const double c[3], double rad, int lane) {
+// ball, restarts one level deeper with that point added to R.  The warp form
+// below scans each prefix 32 points at a time with a ballot for the first point
+// outside, so the sequence of balls is exactly that of the sequential recursion.
+__device__ int first_outside(const LeafPts& P, int from, int to, const float c[3], float rad, int lane) {
     for (int b = from; b < to; b += 32) {
         int i = b + lane;
         bool out = false;
         if (i < to) {
-            double q[3];
-            ld3(P, i, q);
+            float q[3];
+            P.get(i, q);
             out = !in_ball_dev(q, c, rad);
         }
         unsigned m = __ballot_sync(0xffffffffu, out);
@@ -452,25 +481,25 @@ __device__ int first_outside(const d4* P, int from, int to, const double c[3], d
     return -1;
 }
 
-__device__ void meb_points_warp(const d4* P, int n, double c[3], double& rad, int lane) {
-    double R[4][3];
-    double c0[3], r0, c1[3], r1, c2[3], r2, c3[3], r3;
+__device__ void meb_points_warp(const LeafPts& P, int n, float c[3], float& rad, int lane) {
+    float R[4][3];
+    float c0[3], r0, c1[3], r1, c2[3], r2, c3[3], r3;
     trivial_ball_dev(0, R, c0, r0);
     int i = first_outside(P, 0, n, c0, r0, lane);
     while (i >= 0) {
-        ld3(P, i, R[0]);
+        P.get(i, R[0]);
         trivial_ball_dev(1, R, c1, r1);
         int j = first_outside(P, 0, i, c1, r1, lane);
         while (j >= 0) {
-            ld3(P, j, R[1]);
+            P.get(j, R[1]);
             trivial_ball_dev(2, R, c2, r2);
             int k = first_outside(P, 0, j, c2, r2, lane);
             while (k >= 0) {
-                ld3(P, k, R[2]);
+                P.get(k, R[2]);
                 trivial_ball_dev(3, R, c3, r3);
                 int l = first_outside(P, 0, k, c3, r3, lane);
                 while (l >= 0) {
-                    ld3(P, l, R[3]);
+                    P.get(l, R[3]);
                     trivial_ball_dev(4, R, c3, r3);
                     l = first_outside(P, l + 1, k, c3, r3, lane);
                 }
@@ -491,16 +520,31 @@ __device__ void meb_points_warp(const d4* P, int n, double c[3], double& rad, in
 }
 
 // one warp per leaf: smallest enclosing ball, exact radius, mass, centre of mass
-__global__ void k_leaf_geometry(const d4* __restrict__ xm, Cells c, const int* __restrict__ leaves, int nleaves,
-                                unsigned* status) {
-    const int lane = threadIdx.x & 31;
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+constexpr int kGeoWarps = 4;
+__global__ void __launch_bounds__(kGeoWarps * 32) k_leaf_geometry(const d4* __restrict__ xm, Cells c,
+                                                                 const int* __restrict__ leaves, int nleaves,
+                                                                 unsigned* status) {
+    __shared__ float pbuf[kGeoWarps][kMebBuf][3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int t = blockIdx.x * kGeoWarps + wid;
     if (t >= nleaves) return;
     const int cell = leaves[t];
     const int first = c.first[cell], count = c.count[cell];
     const d4* X = xm + first;
-    double s[3], rad;
-    meb_points_warp(X, count, s, rad, lane);
+    LeafPts P;
+    P.buf = pbuf[wid];
+    P.X = X;
+    ld3(X, 0, P.o);
+    for (int i = lane; i < count && i < kMebBuf; i += 32) {
+        d4 v = X[i];
+        pbuf[wid][i][0] = (float)(v.x - P.o[0]);
+        pbuf[wid][i][1] = (float)(v.y - P.o[1]);
+        pbuf[wid][i][2] = (float)(v.z - P.o[2]);
+    }
+    __syncwarp();
+    float cf[3], radf;
+    meb_points_warp(P, count, cf, radf, lane);
+    double s[3] = {P.o[0] + (double)cf[0], P.o[1] + (double)cf[1], P.o[2] + (double)cf[2]};
     double rmax = 0, m = 0, mx[3] = {0, 0, 0};
     for (int i = lane; i < count; i += 32) {
         double p[3];
@@ -534,15 +578,16 @@ __global__ void k_leaf_geometry(const d4* __restrict__ xm, Cells c, const int* _
 void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves, unsigned* status,
                           cudaStream_t s) {
     if (nleaves > 0) {
-        k_leaf_geometry<<<(unsigned)(((long long)nleaves * 32 + 127) / 128), 128, 0, s>>>(xm, c, leaves, nleaves, status);
+        k_leaf_geometry<<<(nleaves + kGeoWarps - 1) / kGeoWarps, kGeoWarps * 32, 0, s>>>(xm, c, leaves, nleaves,
+                                                                                       status);
         note_launch();
     }
 }
 
 // Internal cells of one level: smallest ball enclosing the daughter balls (s_d, rho_d),
 // as the smallest support ball (over all subsets of 1..4 daughters, enumerated by
-// mask) that contains every daughter ball.  One warp per cell, lanes take masks;
-// ties go to the smaller mask.
+// mask) that contains every daughter ball; single precision relative to the first
+// daughter's centre.  One warp per cell, lanes take masks; ties go to the smaller mask.
 __global__ void k_internal_meb(Cells c, int lev_begin, int lev_end, unsigned* status) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     int cell = lev_begin + warp;
@@ -550,22 +595,25 @@ __global__ void k_internal_meb(Cells c, int lev_begin, int lev_end, unsigned* st
     int nch = c.nchild[cell];
     if (nch == 0) return;  // leaves are done
     int ch = c.child[cell];
-    double cen[8][3], rad[8];
+    const d4 o = c.sr[ch];
+    float cen[8][3], rad[8];
     double m = 0, mx[3] = {0, 0, 0};
     for (int i = 0; i < nch; ++i) {
         d4 v = c.sr[ch + i];
-        cen[i][0] = v.x; cen[i][1] = v.y; cen[i][2] = v.z;
-        rad[i] = v.w;
+        cen[i][0] = (float)(v.x - o.x);
+        cen[i][1] = (float)(v.y - o.y);
+        cen[i][2] = (float)(v.z - o.z);
+        rad[i] = (float)v.w;
         double md = c.mass[ch + i];
         d4 cm = c.cr[ch + i];
         m += md;
         mx[0] += md * cm.x; mx[1] += md * cm.y; mx[2] += md * cm.z;
     }
-    double best = -1, bc[3] = {0, 0, 0};
+    float best = -1, bc[3] = {0, 0, 0};
     int bmask = 1 << 30;
     for (int mask = 1 + lane; mask < (1 << nch); mask += 32) {
         if (__popc(mask) > 4) continue;
-        double sc[4][3], sr[4];
+        float sc[4][3], sr[4];
         int k = 0;
         for (int i = 0; i < nch; ++i)
             if (mask & (1 << i)) {
@@ -573,11 +621,11 @@ __global__ void k_internal_meb(Cells c, int lev_begin, int lev_end, unsigned* st
                 sr[k] = rad[i];
                 ++k;
             }
-        double cc[3], rr;
+        float cc[3], rr;
         if (!support_ball_dev(k, sc, sr, cc, rr)) continue;
         bool ok = true;
         for (int i = 0; i < nch; ++i)
-            if (dist3_dev(cen[i], cc) + rad[i] > rr * (1 + 1e-12) + 1e-300) {
+            if (dist3f_dev(cen[i], cc) + rad[i] > rr * (1.0f + kMebIn)) {
                 ok = false;
                 break;
             }
@@ -588,12 +636,12 @@ __global__ void k_internal_meb(Cells c, int lev_begin, int lev_end, unsigned* st
         }
     }
     // warp argmin of (radius, mask)
-    for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int om = __shfl_xor_sync(0xffffffffu, bmask, o);
-        double o0 = __shfl_xor_sync(0xffffffffu, bc[0], o);
-        double o1 = __shfl_xor_sync(0xffffffffu, bc[1], o);
-        double o2 = __shfl_xor_sync(0xffffffffu, bc[2], o);
+    for (int off = 16; off > 0; off >>= 1) {
+        float ob = __shfl_xor_sync(0xffffffffu, best, off);
+        int om = __shfl_xor_sync(0xffffffffu, bmask, off);
+        float o0 = __shfl_xor_sync(0xffffffffu, bc[0], off);
+        float o1 = __shfl_xor_sync(0xffffffffu, bc[1], off);
+        float o2 = __shfl_xor_sync(0xffffffffu, bc[2], off);
         bool take = (ob >= 0) && (best < 0 || ob < best || (ob == best && om < bmask));
         if (take) {
             best = ob; bmask = om;
@@ -601,13 +649,14 @@ __global__ void k_internal_meb(Cells c, int lev_begin, int lev_end, unsigned* st
         }
     }
     if (lane == 0) {
-        if (best < 0) {  // no valid support set (should not happen): fall back to the first daughter's centre
+        if (best < 0) {  // no valid support set: the first daughter's centre
             atomicOr(status, kStatMeb);
-            bc[0] = cen[0][0]; bc[1] = cen[0][1]; bc[2] = cen[0][2];
+            bc[0] = bc[1] = bc[2] = 0.f;
         }
+        double s[3] = {o.x + (double)bc[0], o.y + (double)bc[1], o.z + (double)bc[2]};
         double com[3];
-        for (int k = 0; k < 3; ++k) com[k] = (m > 0) ? mx[k] / m : bc[k];
-        c.sr[cell] = mk4(bc[0], bc[1], bc[2], 0.0);
+        for (int k = 0; k < 3; ++k) com[k] = (m > 0) ? mx[k] / m : s[k];
+        c.sr[cell] = mk4(s[0], s[1], s[2], 0.0);
         c.cr[cell] = mk4(com[0], com[1], com[2], 0.0);
         c.mass[cell] = m;
     }
