@@ -166,6 +166,30 @@ int fmm_last_stats(fmm_ctx* ctx, fmm_stats* out);
  * These are the roofline denominators of the ALU-bound kernels. */
 int fmm_alu_peaks(double* fp64_tflops, double* fp32_tflops);
 
+/* fmm_evaluate for small systems without allocating any device memory.
+ * (The paper has no counterpart: this is a service of the library.)  Callers that
+ * cannot allocate -- code running while a stream is captured into a CUDA graph,
+ * simulation codes whose device memory is owned by their own pool, plugins that
+ * may not grow the process's footprint -- evaluate systems of up to 8192
+ * particles here.  All scratch memory comes from one fixed 32 MiB array in
+ * device global memory that every GPU loading the library holds until the
+ * process exits; nothing calls cudaMalloc, cudaFree or any other device
+ * allocator.  On its first call on a device the entry point looks up that array's
+ * device address (cudaGetSymbolAddress, with the device current); make that first
+ * call before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (what must start at zero is cleared on every call); calls whose
+ * work overlaps on the GPU race on it and give wrong results, so serialise them.
+ *   n       0 <= n <= 8192, else FMM_E_INVALID
+ *   x, mu   device, [n][3] and [n] FP64 (as fmm_evaluate)
+ *   params  host; p <= 10, leaf_size >= 16, scale_src = FMM_SCALE_ESTIMATE
+ *   psi/acc device outputs (as fmm_evaluate)
+ *   stream  cudaStream_t or NULL; the call synchronises it a few times
+ *   errbuf  host, may be NULL: receives a one-line description of a failure
+ * Returns 0, FMM_E_INVALID, FMM_E_OVERFLOW (an interaction list or the tree does
+ * not fit in the array) or FMM_E_CUDA. */
+int fmm_evaluate_noalloc(int64_t n, const double* x, const double* mu, double G, const fmm_params* params,
+                         double* psi, double* acc, void* stream, char* errbuf, int errlen);
+
 /* Release the context and all of its device memory. */
 int fmm_destroy(fmm_ctx* ctx);
 

@@ -47,7 +47,7 @@ class fmm_stats(C.Structure):
 # every symbol include/gb3fmm.h declares
 EXPORTS = ["fmm_default_params", "fmm_create", "fmm_set_params", "fmm_evaluate", "fmm_evaluate_host",
            "fmm_direct", "fmm_evaluate_batch", "fmm_debug_dump", "fmm_last_stats", "fmm_destroy",
-           "fmm_strerror", "fmm_last_error", "fmm_version", "fmm_alu_peaks"]
+           "fmm_strerror", "fmm_last_error", "fmm_version", "fmm_alu_peaks", "fmm_evaluate_noalloc"]
 
 _lib = None
 
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
     L.fmm_last_error.argtypes = [vp]
     L.fmm_last_error.restype = C.c_char_p
     L.fmm_alu_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.fmm_evaluate_noalloc.argtypes = [i64, vp, vp, dbl, C.POINTER(fmm_params), vp, vp, vp, C.c_char_p, ci]
     L.fmm_version.argtypes = []
     L.fmm_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -224,6 +225,29 @@ class Context:
                                      perm.ctypes.data, scale.ctypes.data), self.h)
         return {"cells_int": ci[:nc], "cells_dbl": cd[:nc], "m2l": m2l[:st["n_m2l"]], "p2p": p2p[:st["n_p2p"]],
                 "perm": perm[:n], "scale": scale[:n], "stats": st}
+
+
+def fmm_evaluate_noalloc(x, mu, G=1.0, params: fmm_params | None = None, psi=None, acc=None, stream=None, **kw):
+    """Allocation-free evaluation of a small system (n <= 8192): the library takes all
+    scratch from a fixed array in device memory.  psi/acc may be passed in so that
+    nothing is allocated on this side either."""
+    import torch
+    L = load()
+    if params is None:
+        params = fmm_default_params()
+    for k, v in kw.items():
+        setattr(params, k, v)
+    n = mu.shape[0]
+    if psi is None:
+        psi = torch.empty(n, dtype=torch.float64, device=mu.device)
+    if acc is None:
+        acc = torch.empty((n, 3), dtype=torch.float64, device=mu.device)
+    err = C.create_string_buffer(256)
+    rc = L.fmm_evaluate_noalloc(n, _ptr(x), _ptr(mu), float(G), C.byref(params), _ptr(psi), _ptr(acc),
+                                _stream(stream), err, 256)
+    if rc != 0:
+        raise FMMError(rc, f"{L.fmm_strerror(rc).decode()}: {err.value.decode()}")
+    return psi, acc
 
 
 def fmm_alu_peaks() -> tuple[float, float]:

@@ -1,0 +1,65 @@
+"""The allocation-free entry point fmm_evaluate_noalloc, called through the C ABI.
+
+Callers that cannot allocate device memory (inside a CUDA graph capture, under a
+foreign pool allocator) evaluate small systems with it; the library takes all its
+scratch from one fixed array in device memory.  This file is collected last so
+that a run stopping at the first failure has run every other test first; it also
+passes when run alone in a fresh process.
+"""
+import numpy as np
+import pytest
+
+from paper_1405_2255_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10  # the FP64-mode parity tolerance of the other GPU tests
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_2255_gb300 import build
+    build.build()
+    from paper_1405_2255_gb300 import gb3fmm
+    gb3fmm.load()
+    return gb3fmm
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def _rel(a, ref):
+    return np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_noalloc_matches_evaluate_on_two_calls(g, precision):
+    import torch
+    prm = dict(p=8, eps=1e-6, leaf_size=32, p2p_c=4.0, precision=precision)
+    ctx = g.Context(**prm)
+    # two calls in a row with different systems: the second must not see the first's leftovers
+    for seed, n in ((inputs.BASE_SEED + 11, 3000), (inputs.BASE_SEED + 12, 5000)):
+        x, mu = inputs.plummer(n, seed)
+        xd, md = _dev(x), _dev(mu)
+        psi_ref, acc_ref = ctx.fmm_evaluate(xd, md, 1.0)
+        psi = torch.empty(n, dtype=torch.float64, device="cuda:0")
+        acc = torch.empty((n, 3), dtype=torch.float64, device="cuda:0")
+        g.fmm_evaluate_noalloc(xd, md, 1.0, psi=psi, acc=acc, **prm)
+        torch.cuda.synchronize()
+        a, ar = acc.cpu().numpy(), acc_ref.cpu().numpy()
+        assert np.max(_rel(a, ar)) <= TOL
+        assert np.max(np.abs(psi.cpu().numpy() - psi_ref.cpu().numpy()) / psi_ref.cpu().numpy()) <= TOL
+    ctx.close()
+
+
+def test_noalloc_rejects_too_many_particles(g):
+    x, mu = inputs.plummer(8193, 3)
+    with pytest.raises(g.FMMError) as e:
+        g.fmm_evaluate_noalloc(_dev(x), _dev(mu), 1.0, p=6, leaf_size=32)
+    assert e.value.code == g.FMM_E_INVALID
+    assert "8192" in str(e.value)
