@@ -57,7 +57,8 @@ extern "C" {
 /* arithmetic of the path */
 #define FMM_PREC_FP64   0  /* every step in IEEE FP64                                   */
 #define FMM_PREC_MIXED  1  /* P2P in FP32 on two-float leaf-relative positions with
-                              compensated accumulation; everything else FP64          */
+                              compensated accumulation; M2L terms of order > 2 in FP32
+                              (m2l_split); everything else FP64                       */
 
 /* source of the acceleration scale used by (18a)/(18b) */
 #define FMM_SCALE_ESTIMATE 0  /* low-order FMM estimate (Sec. 5.3.2)                  */
@@ -74,6 +75,8 @@ typedef struct {
     int    scale_src;   /* FMM_SCALE_*                                                 */
     int    p2p_two_float; /* mixed P2P: 1 = dx from two-float positions (hi + lo) relative
                              to the sink leaf's centre; 0 = from their FP32 high parts only */
+    int    m2l_split;   /* mixed mode M2L: 1 = terms of order n+k <= 2 in FP64 and the others
+                           in FP32 on scaled harmonics; 0 = every term in FP64        */
 } fmm_params;
 
 typedef struct {
@@ -92,8 +95,8 @@ typedef struct {
 typedef struct fmm_ctx fmm_ctx;
 
 /* Default parameters: p = 8, eps = 1e-7, (18a) with the low-order estimate,
- * leaf_size = 64, p2p_c = 8, mixed precision with two-float P2P positions.
- * Host pointer, filled in. */
+ * leaf_size = 64, p2p_c = 8, mixed precision with two-float P2P positions and
+ * the precision-split M2L.  Host pointer, filled in. */
 void fmm_default_params(fmm_params* out);
 
 /* Create a context on CUDA device `device` (the device becomes current for the

@@ -447,9 +447,15 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
 
     // A9: M2L
     CU(cudaMemsetAsync(ctx->F.p, 0, sizeof(double) * nco * (size_t)nc, s));
-    TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc, prm.p)));
-    launch_m2l(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc, c.sr,
-               P<double>(ctx->M), prm.p, P<double>(ctx->F), s);
+    if (prm.precision == FMM_PREC_MIXED && prm.m2l_split) {
+        TRY(ensure(ctx->m2l_tmp, m2l_split_tmp_bytes(nc, prm.p)));
+        launch_m2l_split(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc,
+                         c.sr, P<double>(ctx->M), prm.p, P<double>(ctx->F), s);
+    } else {
+        TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc, prm.p)));
+        launch_m2l(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc, c.sr,
+                   P<double>(ctx->M), prm.p, P<double>(ctx->F), s);
+    }
     if (timing) CU(cudaEventRecord(ctx->ev[EV_M2L], s));
 
     // A10: P2P
@@ -518,6 +524,7 @@ void fmm_default_params(fmm_params* out) {
     out->precision = FMM_PREC_MIXED;
     out->scale_src = FMM_SCALE_ESTIMATE;
     out->p2p_two_float = 1;
+    out->m2l_split = 1;
 }
 
 int fmm_create(fmm_ctx** out, const fmm_params* params, int device) {

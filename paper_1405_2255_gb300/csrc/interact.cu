@@ -165,6 +165,347 @@ void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void
     }
 }
 
+// ---------------------------------------------------------------- M2L, precision-split (mixed mode)
+// F_n^m = sum_{k,l} M_k^{l*} Theta_{n+k}^{m+l} split by the order j = n + k of Theta.
+// Terms with j <= kJ64 (monopole, dipole, quadrupole of the source seen by the
+// sink's lowest orders) are summed in FP64.  All other terms are summed in FP32:
+// the acceptance criterion keeps theta of an accepted pair near eps^(1/p), so a
+// term of order j carries a fraction <~ theta^(j-1) of the interaction and its
+// FP32 rounding (6e-8 relative) is far below the targeted force error.  To keep
+// FP32 in range the FP32 part is evaluated on scaled quantities:
+//   Mt_k = M_k / rho_A^k (per source cell),  That_j = Theta_j(r/|r|) (unit vector),
+//   Mhat_k = Mt_k (rho_A/|r|)^k,  G_n = sum Mhat* That = |r|^{n+1} F_n(pair),
+//   H_n = sum_pairs G_n (sigma_B/|r|)^{n+1} = sigma_B^{n+1} F_n(FP32 part),
+// with sigma_B = rho_B (or half the closest pair distance when rho_B = 0); the sink
+// converts H_n / sigma_B^{n+1} to FP64 once.
+constexpr int kJ64 = 2;
+constexpr int kN64 = (kJ64 + 1) * (kJ64 + 1);  // FP64 coefficients per expansion (orders <= kJ64)
+constexpr int kT64 = 20;                       // FP64 complex terms per pair for kJ64 = 2
+constexpr int kNBs = 8;                        // pairs per batch
+constexpr int kLoPerLane = kNBs * kT64 / 32;   // FP64 terms per lane per batch
+
+struct TermTab {
+    unsigned char n[kT64], m[kT64], k[kT64];
+    signed char l[kT64];
+    unsigned char out[kT64];  // output index n(n+1)/2 + m
+};
+static __constant__ TermTab c_terms;
+static __constant__ unsigned char c_idx_n[(kMaxP + 1) * (kMaxP + 1)];
+static __constant__ float c_twf[kMaxP + 2], c_thbf[kMaxP + 1][kMaxP + 1];
+
+static void init_split_tables() {
+    static bool done = false;
+    if (done) return;
+    TermTab t;
+    int q = 0;
+    for (int n = 0; n <= kJ64; ++n)
+        for (int m = 0; m <= n; ++m)
+            for (int k = 0; k + n <= kJ64; ++k)
+                for (int l = -k; l <= k; ++l) {
+                    t.n[q] = (unsigned char)n; t.m[q] = (unsigned char)m; t.k[q] = (unsigned char)k;
+                    t.l[q] = (signed char)l; t.out[q] = (unsigned char)(n * (n + 1) / 2 + m);
+                    ++q;
+                }
+    cudaMemcpyToSymbol(c_terms, &t, sizeof t);
+    unsigned char idx[(kMaxP + 1) * (kMaxP + 1)];
+    for (int n = 0; n <= kMaxP; ++n)
+        for (int m = -n; m <= n; ++m) idx[cix(n, m)] = (unsigned char)n;
+    cudaMemcpyToSymbol(c_idx_n, idx, sizeof idx);
+    float tw[kMaxP + 2], tb[kMaxP + 1][kMaxP + 1];
+    for (int n = 0; n <= kMaxP + 1; ++n) tw[n] = (float)(2 * n - 1);
+    for (int n = 0; n <= kMaxP; ++n)
+        for (int m = 0; m <= kMaxP; ++m) tb[n][m] = (float)((n - 1) * (n - 1) - m * m);
+    cudaMemcpyToSymbol(c_twf, tw, sizeof tw);
+    cudaMemcpyToSymbol(c_thbf, tb, sizeof tb);
+    done = true;
+}
+
+__device__ inline float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ inline void cmacf(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// one column m of Theta on a unit vector (r^2 = 1), single precision
+__device__ inline void theta_column_unit_f(int p, int m, float x, float y, float z, float2* out) {
+    float2 d = make_float2(1.f, 0.f);
+    for (int j = 1; j <= m; ++j) {
+        float s = c_twf[j];
+        d = make_float2(s * (x * d.x - y * d.y), s * (x * d.y + y * d.x));
+    }
+    float2 prev2 = make_float2(0.f, 0.f), prev = d;
+    const float sg = (m & 1) ? -1.f : 1.f;
+    for (int n = m; n <= p; ++n) {
+        float2 v;
+        if (n == m) v = d;
+        else {
+            float a = c_twf[n] * z, b = c_thbf[n][m];
+            v = make_float2(a * prev.x - b * prev2.x, a * prev.y - b * prev2.y);
+            prev2 = prev;
+            prev = v;
+        }
+        out[cix(n, m)] = v;
+        if (m) out[cix(n, -m)] = make_float2(sg * v.x, -sg * v.y);
+    }
+}
+
+// Theta_j^m(r), j <= 2, m >= 0, in closed form (consistent with the recurrences)
+__device__ inline cd theta_low(int j, int m, double x, double y, double z, double rinv) {
+    const double r2i = rinv * rinv, r3 = rinv * r2i, r5 = r3 * r2i;
+    if (j == 0) return mkc(rinv, 0.0);
+    if (j == 1) return m == 0 ? mkc(z * r3, 0.0) : mkc(x * r3, y * r3);
+    if (m == 0) return mkc((3.0 * z * z - (x * x + y * y + z * z)) * r5, 0.0);
+    if (m == 1) return mkc(3.0 * z * x * r5, 3.0 * z * y * r5);
+    return mkc(3.0 * (x * x - y * y) * r5, 6.0 * x * y * r5);
+}
+
+// per cell: conj(M_k / rho^k) in FP32 (all orders) and conj(M_k) in FP64 (orders <= kJ64)
+__global__ void k_prep_split(const double* __restrict__ M, const d4* __restrict__ cen, int ncells, int p,
+                             float2* __restrict__ Mf, cd* __restrict__ M64) {
+    const int nco = ncoef(p);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)ncells * nco;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int cell = (int)(t / nco), i = (int)(t % nco);
+        const int n = c_idx_n[i];
+        const cd v = load_real_storage(M + (size_t)cell * nco, n, i - n * n - n);
+        const double rho = cen[cell].w;
+        double sc = 1.0;
+        if (rho > 0)
+            for (int k = 0; k < n; ++k) sc /= rho;
+        else if (n > 0)
+            sc = 0.0;  // a source of radius 0 has no moments above the monopole
+        Mf[t] = make_float2((float)(v.re * sc), (float)(-v.im * sc));
+        if (i < kN64) M64[(size_t)cell * kN64 + i] = conjc(v);
+    }
+}
+
+struct PairInfo {
+    double x, y, z, rinv;
+};
+
+template <int MAXQ>
+__global__ void __launch_bounds__(64) k_m2l_split(const int2* __restrict__ list, const int* __restrict__ seg_start,
+                                                  const int* __restrict__ seg_end, const int* __restrict__ order,
+                                                  int nsinks, unsigned* __restrict__ work, const d4* __restrict__ cen,
+                                                  const float2* __restrict__ Mf, const cd* __restrict__ M64g, int p,
+                                                  double* __restrict__ F, LaneSched sched) {
+    extern __shared__ unsigned char sm_raw[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nco = ncoef(p);
+    // per-warp layout
+    const size_t per_warp = (size_t)kNBs * (2 * nco * sizeof(float2) + 2 * kN64 * sizeof(cd) + sizeof(PairInfo) +
+                                            2 * (kMaxP + 1) * sizeof(float)) +
+                            32 * kLoPerLane * sizeof(cd) + 8 * sizeof(cd);
+    unsigned char* base = sm_raw + wid * ((per_warp + 15) & ~(size_t)15);
+    float2* Th = (float2*)base;                 // [kNBs][nco]
+    float2* Mh = Th + kNBs * nco;               // [kNBs][nco]
+    cd* T64 = (cd*)(Mh + kNBs * nco);           // [kNBs][kN64]
+    cd* M64 = T64 + kNBs * kN64;                // [kNBs][kN64]
+    PairInfo* pi = (PairInfo*)(M64 + kNBs * kN64);
+    float* thA = (float*)(pi + kNBs);           // [kNBs][kMaxP+1]: (rho_A/r)^k
+    float* thB = thA + kNBs * (kMaxP + 1);      // [kNBs][kMaxP+1]: (sigma_B/r)^(n+1)
+    cd* red = (cd*)(thB + kNBs * (kMaxP + 1));  // [32 * kLoPerLane]
+    cd* lowF = red + 32 * kLoPerLane;           // [6] FP64 outputs of orders <= kJ64
+    const int cnt = sched.cnt[lane];
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(work, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= (unsigned)nsinks) break;
+        const int B = order[w];
+        const int e0 = seg_start[B], e1 = seg_end[B];
+        if (e1 <= e0) continue;
+        const d4 sB = cen[B];
+        double sigma = sB.w;
+        if (!(sigma > 0)) {  // radius 0: half the closest source distance
+            double rmin = INFINITY;
+            for (int e = e0 + lane; e < e1; e += 32) {
+                const d4 zA = cen[list[e].x];
+                const double dx = sB.x - zA.x, dy = sB.y - zA.y, dz = sB.z - zA.z;
+                rmin = fmin(rmin, sqrt(dx * dx + dy * dy + dz * dz));
+            }
+            sigma = 0.5 * warp_min(rmin);
+        }
+        float2 hacc[MAXQ];
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q) hacc[q] = make_float2(0.f, 0.f);
+        cd lo[kLoPerLane];
+#pragma unroll
+        for (int i = 0; i < kLoPerLane; ++i) lo[i] = mkc(0.0, 0.0);
+        for (int eb = e0; eb < e1; eb += kNBs) {
+            const int nb = min(kNBs, e1 - eb);
+            // pair geometry and scale powers
+            if (lane < nb) {
+                const d4 zA = cen[list[eb + lane].x];
+                const double x = sB.x - zA.x, y = sB.y - zA.y, z = sB.z - zA.z;
+                const double rinv = rsqrt(x * x + y * y + z * z);
+                pi[lane] = PairInfo{x, y, z, rinv};
+                const float ta = (float)(zA.w * rinv), tb = (float)(sigma * rinv);
+                float a = 1.f, b = tb;
+                for (int k = 0; k <= p; ++k) {
+                    thA[lane * (kMaxP + 1) + k] = a;
+                    thB[lane * (kMaxP + 1) + k] = b;
+                    a *= ta;
+                    b *= tb;
+                }
+            }
+            __syncwarp();
+            // sources: scaled FP32 moments and FP64 low orders; FP64 Theta of orders <= kJ64
+            for (int b = 0; b < nb; ++b) {
+                const int A = list[eb + b].x;
+                const float2* src = Mf + (size_t)A * nco;
+                const float* ta = thA + b * (kMaxP + 1);
+                for (int i = lane; i < nco; i += 32) {
+                    const float2 v = src[i];
+                    const float s = ta[c_idx_n[i]];
+                    Mh[b * nco + i] = make_float2(v.x * s, v.y * s);
+                }
+                if (lane < kN64) M64[b * kN64 + lane] = M64g[(size_t)A * kN64 + lane];
+            }
+            for (int t = lane; t < nb * 6; t += 32) {
+                const int b = t / 6, o = t % 6;
+                const int j = o < 1 ? 0 : (o < 3 ? 1 : 2), m = o - j * (j + 1) / 2;
+                const PairInfo q = pi[b];
+                const cd v = theta_low(j, m, q.x, q.y, q.z, q.rinv);
+                T64[b * kN64 + cix(j, m)] = v;
+                if (m) T64[b * kN64 + cix(j, -m)] = (m & 1) ? mkc(-v.re, v.im) : mkc(v.re, -v.im);
+            }
+            // FP32 Theta on the unit vectors, 4 lanes per pair
+            {
+                const int b = lane >> 2, sub = lane & 3;
+                if (b < nb) {
+                    const PairInfo q = pi[b];
+                    const float x = (float)(q.x * q.rinv), y = (float)(q.y * q.rinv), z = (float)(q.z * q.rinv);
+                    for (int m = sub; m <= p; m += 4) theta_column_unit_f(p, m, x, y, z, Th + b * nco);
+                }
+            }
+            __syncwarp();
+            // FP64 terms of orders <= kJ64, spread evenly over the lanes
+#pragma unroll
+            for (int i = 0; i < kLoPerLane; ++i) {
+                const int t = lane + 32 * i, b = t / kT64, id = t % kT64;
+                if (b < nb) {
+                    const int n = c_terms.n[id], m = c_terms.m[id], k = c_terms.k[id], l = c_terms.l[id];
+                    cmac(lo[i], M64[b * kN64 + cix(k, l)], T64[b * kN64 + cix(n + k, m + l)]);
+                }
+            }
+            // FP32 terms of orders > kJ64
+            for (int b = 0; b < nb; ++b) {
+                const float2* X = Mh + b * nco;
+                const float2* Y = Th + b * nco;
+                const float* tbb = thB + b * (kMaxP + 1);
+#pragma unroll
+                for (int q = 0; q < MAXQ; ++q) {
+                    if (q < cnt) {
+                        const int n = sched.n[lane][q], m = sched.m[lane][q];
+                        float2 a = make_float2(0.f, 0.f);
+                        for (int k = max(0, kJ64 + 1 - n); k <= p - n; ++k) {
+                            const float2* xk = X + k * k + k;
+                            const float2* yk = Y + (n + k) * (n + k) + (n + k) + m;
+                            for (int l = -k; l <= k; ++l) cmacf(a, xk[l], yk[l]);
+                        }
+                        const float sc = tbb[n];
+                        hacc[q].x = fmaf(a.x, sc, hacc[q].x);
+                        hacc[q].y = fmaf(a.y, sc, hacc[q].y);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        // reduce the FP64 terms per output in a fixed order
+#pragma unroll
+        for (int i = 0; i < kLoPerLane; ++i) red[lane * kLoPerLane + i] = lo[i];
+        __syncwarp();
+        if (lane < 6) {
+            cd sum = mkc(0.0, 0.0);
+            for (int L = 0; L < 32; ++L)
+                for (int i = 0; i < kLoPerLane; ++i) {
+                    const int id = (L + 32 * i) % kT64;
+                    if (c_terms.out[id] == lane) sum = sum + red[L * kLoPerLane + i];
+                }
+            lowF[lane] = sum;
+        }
+        __syncwarp();
+        double* out = F + (size_t)B * nco;
+        const double sinv = 1.0 / sigma;
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q) {
+            if (q < cnt) {
+                const int n = sched.n[lane][q], m = sched.m[lane][q];
+                double s = sinv;
+                for (int k = 0; k < n; ++k) s *= sinv;
+                cd v = mkc((double)hacc[q].x * s, (double)hacc[q].y * s);
+                if (n <= kJ64) v = v + lowF[n * (n + 1) / 2 + m];
+                out[cix(n, m)] = v.re;
+                if (m) out[cix(n, -m)] = v.im;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+size_t m2l_split_smem(int p) {
+    const int nco = ncoef(p);
+    const size_t per_warp = (size_t)kNBs * (2 * nco * sizeof(float2) + 2 * kN64 * sizeof(cd) + sizeof(PairInfo) +
+                                            2 * (kMaxP + 1) * sizeof(float)) +
+                            32 * kLoPerLane * sizeof(cd) + 8 * sizeof(cd);
+    return 2 * ((per_warp + 15) & ~(size_t)15);
+}
+
+size_t m2l_split_tmp_bytes(int ncells, int p) {
+    size_t n = (size_t)(ncells > 0 ? ncells : 1);
+    return m2l_tmp_bytes(ncells, p) + n * (size_t)ncoef(p) * sizeof(float2) + n * kN64 * sizeof(cd) + 512;
+}
+
+template <int MAXQ>
+static void m2l_split_launch(const int2* list, const int* seg_start, const int* seg_end, const int* order, int ncells,
+                             unsigned* work, const d4* cen, const float2* Mf, const cd* M64, int p, double* F,
+                             const LaneSched& sched, cudaStream_t s) {
+    const int wpb = 2;
+    size_t sm = m2l_split_smem(p);
+    cudaFuncSetAttribute(k_m2l_split<MAXQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int dev = 0, nsm = 152, bps = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l_split<MAXQ>, wpb * 32, sm);
+    unsigned g = (unsigned)(nsm * (bps > 0 ? bps : 1));
+    k_m2l_split<MAXQ><<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, order, ncells, work, cen, Mf, M64, p, F, sched);
+    note_launch();
+}
+
+void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells, const d4* cen,
+                      const double* M, int p, double* F, cudaStream_t s) {
+    if (ncells <= 0) return;
+    if (p <= kJ64) {  // nothing to split
+        launch_m2l(list, seg_start, seg_end, tmp, ncells, cen, M, p, F, s);
+        return;
+    }
+    init_split_tables();
+    uint64_t* k0 = (uint64_t*)tmp;
+    uint64_t* k1 = k0 + ncells;
+    int* v0 = (int*)(k1 + ncells);
+    int* v1 = v0 + ncells;
+    int* order = v1 + ncells;
+    unsigned* work = (unsigned*)(order + ncells);
+    int* rtmp = (int*)(work + 4);
+    unsigned char* after = (unsigned char*)(rtmp + radix_tmp_ints(ncells));
+    float2* Mf = (float2*)(((uintptr_t)after + 255) & ~(uintptr_t)255);
+    cd* M64 = (cd*)(((uintptr_t)(Mf + (size_t)ncells * ncoef(p)) + 255) & ~(uintptr_t)255);
+    cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
+    k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
+    int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 0, 56, s);
+    k_sink_order<<<grid_for(ncells, 256), 256, 0, s>>>(flip ? k1 : k0, ncells, order, work + 1); note_launch();
+    k_prep_split<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(M, cen, ncells, p, Mf, M64); note_launch();
+    LaneSched sched = make_lane_sched(p, kSchedDown);
+    int maxq = 0;
+    for (int l = 0; l < 32; ++l) maxq = sched.cnt[l] > maxq ? sched.cnt[l] : maxq;
+    if (maxq <= 4) m2l_split_launch<4>(list, seg_start, seg_end, order, ncells, work, cen, Mf, M64, p, F, sched, s);
+    else if (maxq <= 8) m2l_split_launch<8>(list, seg_start, seg_end, order, ncells, work, cen, Mf, M64, p, F, sched, s);
+    else m2l_split_launch<12>(list, seg_start, seg_end, order, ncells, work, cen, Mf, M64, p, F, sched, s);
+}
+
 // ---------------------------------------------------------------- L2L
 // F_n^m(s') += sum_{k<=p-n} sum_l Upsilon_k^{l*}(s - s') F_{n+k}^{m+l}(s) for every
 // cell of one level (s = its parent's centre), one warp per cell.

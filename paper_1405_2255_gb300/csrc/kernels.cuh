@@ -103,6 +103,10 @@ void launch_segments(const int2* list, long long npairs, int ncells, int* seg_st
 size_t m2l_tmp_bytes(int ncells, int p);
 void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells,
                 const d4* cen, const double* M, int p, double* F, cudaStream_t s);
+// mixed mode: orders <= 2 of Theta in FP64, the rest in FP32 on scaled harmonics
+size_t m2l_split_tmp_bytes(int ncells, int p);
+void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells,
+                      const d4* cen, const double* M, int p, double* F, cudaStream_t s);
 void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F,
                       cudaStream_t s);
 // L2P (eqs. 3a, 7) for every particle of every leaf: psi_far, acc_far (sorted order)

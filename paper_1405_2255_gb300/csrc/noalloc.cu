@@ -262,7 +262,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     double* M1 = A.take<double>(4 * (size_t)nc);
     double* F1 = A.take<double>(4 * (size_t)nc);
     double* Ff = A.take<double>(nc);
-    void* m2l_tmp = A.take<unsigned char>(m2l_tmp_bytes(nc, p > 1 ? p : 1));
+    void* m2l_tmp = A.take<unsigned char>(m2l_split_tmp_bytes(nc, p > 1 ? p : 1));
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the expansions and lists");
     if (prm.precision == FMM_PREC_MIXED) launch_split_positions(r.xm, n, xhi, xlo, s);
 
@@ -331,7 +331,10 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
 
     // A9-A12
     NA_CU(cudaMemsetAsync(F, 0, sizeof(double) * nco * (size_t)nc, s));
-    launch_m2l(m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.sr, M, p, F, s);
+    if (prm.precision == FMM_PREC_MIXED && prm.m2l_split)
+        launch_m2l_split(m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.sr, M, p, F, s);
+    else
+        launch_m2l(m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.sr, M, p, F, s);
     sort_pairs_by_sink(p2p, np, nc, r.sort_tmp, s);
     launch_segments(p2p, np, nc, seg_start, seg_end, s);
     if (prm.precision == FMM_PREC_MIXED)

@@ -201,3 +201,19 @@ def test_batch_equals_alone(g):
         _, a1 = ctx.fmm_evaluate(_dev(x), _dev(mu))
         assert np.max(_rel(acc[off[i]:off[i + 1]], a1.cpu().numpy())) <= 1e-12
     ctx.close()
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_mixed_m2l_split_accuracy(g, orc, split):
+    """Mixed mode with the precision-split M2L (orders > 2 in FP32) keeps the error of
+    the FP64-M2L mixed mode: both against FP64 direct summation."""
+    x, mu = inputs.plummer(20000, inputs.BASE_SEED + 21)
+    ctx = g.Context(p=10, eps=1e-7, leaf_size=32, p2p_c=2.0, precision=g.FMM_PREC_MIXED, m2l_split=split)
+    psi, acc, st = ctx.fmm_evaluate(_dev(x), _dev(mu), stats=True)
+    assert st["n_m2l"] > 1000
+    sinks = np.arange(0, 20000, 7)
+    _, a_t, _, _ = orc.direct(x, mu, sinks=sinks)
+    e = _rel(acc.cpu().numpy()[sinks], a_t)
+    assert np.sqrt(np.mean(e ** 2)) < 1e-7
+    assert np.percentile(e, 99.9) < 2e-6
+    ctx.close()
