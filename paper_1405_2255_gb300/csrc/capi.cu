@@ -425,9 +425,13 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         for (int k = 1; k <= prm.p; ++k) bn[k] = bn[k - 1] * (prm.p - k + 1) / k;
         CU(cudaMemcpyAsync(ctx->binom.p, bn, sizeof(double) * (prm.p + 1), cudaMemcpyHostToDevice, s));
     }
-    launch_p2m(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->M), s);
-    for (int L = nlev - 1; L >= 0; --L)
-        launch_m2m_level(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->M), s);
+    const bool split = prm.precision == FMM_PREC_MIXED && prm.m2l_split;
+    if (split) launch_p2m_split(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->M), s);
+    else launch_p2m(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->M), s);
+    for (int L = nlev - 1; L >= 0; --L) {
+        if (split) launch_m2m_split(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->M), s);
+        else launch_m2m_level(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->M), s);
+    }
     launch_power(P<double>(ctx->M), nc, prm.p, P<double>(ctx->Pw), s);
     if (timing) CU(cudaEventRecord(ctx->ev[EV_UP], s));
 
@@ -447,7 +451,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
 
     // A9: M2L
     CU(cudaMemsetAsync(ctx->F.p, 0, sizeof(double) * nco * (size_t)nc, s));
-    if (prm.precision == FMM_PREC_MIXED && prm.m2l_split) {
+    if (split) {
         TRY(ensure(ctx->m2l_tmp, m2l_split_tmp_bytes(nc, prm.p)));
         launch_m2l_split(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc,
                          c.sr, P<double>(ctx->M), prm.p, P<double>(ctx->F), s);
@@ -471,9 +475,16 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     if (timing) CU(cudaEventRecord(ctx->ev[EV_P2P], s));
 
     // A11-A12: L2L, L2P, combine and scatter
-    for (int L = 1; L < nlev; ++L) launch_l2l_level(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->F), s);
-    launch_l2p(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->F),
-               P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
+    for (int L = 1; L < nlev; ++L) {
+        if (split) launch_l2l_split(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->F), s);
+        else launch_l2l_level(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->F), s);
+    }
+    if (split)
+        launch_l2p_split(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->F),
+                         P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
+    else
+        launch_l2p(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->F),
+                   P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
     launch_finish(P<double>(ctx->psi_far), P<double>(ctx->acc_far), P<double>(ctx->psi_near), P<double>(ctx->acc_near),
                   P<int>(ctx->perm), n, G, psi, acc, s);
     if (timing) {

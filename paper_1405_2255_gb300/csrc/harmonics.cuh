@@ -90,6 +90,14 @@ __device__ inline void theta_column(int p, int m, double x, double y, double z, 
     }
 }
 
+// complex FP32 multiply-accumulate: acc += a * b
+__device__ inline void cmacf(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
 // expand a real-storage expansion into a full complex array (optionally conjugated)
 __device__ inline void expand_real(int p, const double* R, cd* out, bool conj_out, int lane, int nlanes) {
     const int nc = ncoef(p);

@@ -220,13 +220,6 @@ static void init_split_tables() {
     done = true;
 }
 
-__device__ inline float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ inline void cmacf(float2& acc, float2 a, float2 b) {
-    acc.x = fmaf(a.x, b.x, acc.x);
-    acc.x = fmaf(-a.y, b.y, acc.x);
-    acc.y = fmaf(a.x, b.y, acc.y);
-    acc.y = fmaf(a.y, b.x, acc.y);
-}
 
 // one column m of Theta on a unit vector (r^2 = 1), single precision
 __device__ inline void theta_column_unit_f(int p, int m, float x, float y, float z, float2* out) {

@@ -112,6 +112,13 @@ void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p,
 // L2P (eqs. 3a, 7) for every particle of every leaf: psi_far, acc_far (sorted order)
 void launch_l2p(const d4* xm, Cells c, const d4* cen, const int* leaves, int nleaves, int p,
                 const double* F, double* psi, double* acc, cudaStream_t s);
+// mixed mode: P2M and L2P with orders <= 2 in FP64 and higher orders in FP32 (split.cu)
+void launch_p2m_split(const d4* xm, Cells c, const d4* cen, const int* leaves, int nleaves, int p, double* M,
+                      cudaStream_t s);
+void launch_l2p_split(const d4* xm, Cells c, const d4* cen, const int* leaves, int nleaves, int p, const double* F,
+                      double* psi, double* acc, cudaStream_t s);
+void launch_m2m_split(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* M, cudaStream_t s);
+void launch_l2l_split(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F, cudaStream_t s);
 // P2P (eq. 1) into psi_near/acc_near (sorted order): every leaf takes the sources of
 // its own P2P segment and those of its ancestors' segments.
 void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_start,

@@ -309,8 +309,13 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     bn[0] = 1;
     for (int k = 1; k <= p; ++k) bn[k] = bn[k - 1] * (p - k + 1) / k;
     NA_CU(cudaMemcpyAsync(binom, bn, sizeof(double) * (p + 1), cudaMemcpyHostToDevice, s));
-    launch_p2m(r.xm, r.c, r.c.sr, r.leaves, r.nleaves, p, M, s);
-    for (int L = nl - 1; L >= 0; --L) launch_m2m_level(r.c, r.c.sr, r.lev[L], r.lev[L + 1], p, M, s);
+    const bool split = prm.precision == FMM_PREC_MIXED && prm.m2l_split;
+    if (split) launch_p2m_split(r.xm, r.c, r.c.sr, r.leaves, r.nleaves, p, M, s);
+    else launch_p2m(r.xm, r.c, r.c.sr, r.leaves, r.nleaves, p, M, s);
+    for (int L = nl - 1; L >= 0; --L) {
+        if (split) launch_m2m_split(r.c, r.c.sr, r.lev[L], r.lev[L + 1], p, M, s);
+        else launch_m2m_level(r.c, r.c.sr, r.lev[L], r.lev[L + 1], p, M, s);
+    }
     launch_power(M, nc, p, Pw, s);
 
     // A8: dual tree walk
@@ -331,7 +336,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
 
     // A9-A12
     NA_CU(cudaMemsetAsync(F, 0, sizeof(double) * nco * (size_t)nc, s));
-    if (prm.precision == FMM_PREC_MIXED && prm.m2l_split)
+    if (split)
         launch_m2l_split(m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.sr, M, p, F, s);
     else
         launch_m2l(m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.sr, M, p, F, s);
@@ -342,8 +347,12 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
                          prm.p2p_two_float != 0, s);
     else
         launch_p2p_fp64(r.xm, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
-    for (int L = 1; L < nl; ++L) launch_l2l_level(r.c, r.c.sr, r.lev[L], r.lev[L + 1], p, F, s);
-    launch_l2p(r.xm, r.c, r.c.sr, r.leaves, r.nleaves, p, F, psi_far, acc_far, s);
+    for (int L = 1; L < nl; ++L) {
+        if (split) launch_l2l_split(r.c, r.c.sr, r.lev[L], r.lev[L + 1], p, F, s);
+        else launch_l2l_level(r.c, r.c.sr, r.lev[L], r.lev[L + 1], p, F, s);
+    }
+    if (split) launch_l2p_split(r.xm, r.c, r.c.sr, r.leaves, r.nleaves, p, F, psi_far, acc_far, s);
+    else launch_l2p(r.xm, r.c, r.c.sr, r.leaves, r.nleaves, p, F, psi_far, acc_far, s);
     launch_finish(psi_far, acc_far, psi_near, acc_near, r.perm, n, G, psi, acc, s);
     NA_CU(cudaGetLastError());
     return 0;
