@@ -452,7 +452,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     // A9: M2L
     CU(cudaMemsetAsync(ctx->F.p, 0, sizeof(double) * nco * (size_t)nc, s));
     if (split) {
-        TRY(ensure(ctx->m2l_tmp, m2l_split_tmp_bytes(nc, prm.p)));
+        TRY(ensure(ctx->m2l_tmp, m2l_split_tmp_bytes(nc, prm.p, ctx->n_m2l)));
         launch_m2l_split(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc,
                          c.sr, P<double>(ctx->M), prm.p, P<double>(ctx->F), s);
     } else {

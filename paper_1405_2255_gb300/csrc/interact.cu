@@ -278,12 +278,15 @@ struct PairInfo {
     double x, y, z, rinv;
 };
 
+constexpr int kChunk = 32;  // M2L pairs per work item
+
 template <int MAXQ>
 __global__ void __launch_bounds__(64) k_m2l_split(const int2* __restrict__ list, const int* __restrict__ seg_start,
                                                   const int* __restrict__ seg_end, const int* __restrict__ order,
-                                                  int nsinks, unsigned* __restrict__ work, const d4* __restrict__ cen,
+                                                  const int* __restrict__ item_start, int ncells,
+                                                  unsigned* __restrict__ work, const d4* __restrict__ cen,
                                                   const float2* __restrict__ Mf, const cd* __restrict__ M64g, int p,
-                                                  double* __restrict__ F, LaneSched sched) {
+                                                  double* __restrict__ part, LaneSched sched) {
     extern __shared__ unsigned char sm_raw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nco = ncoef(p);
@@ -302,19 +305,27 @@ __global__ void __launch_bounds__(64) k_m2l_split(const int2* __restrict__ list,
     cd* red = (cd*)(thB + kNBs * (kMaxP + 1));  // [32 * kLoPerLane]
     cd* lowF = red + 32 * kLoPerLane;           // [6] FP64 outputs of orders <= kJ64
     const int cnt = sched.cnt[lane];
+    const unsigned nitems = work[2], nsinks = work[1];
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= (unsigned)nsinks) break;
-        const int B = order[w];
-        const int e0 = seg_start[B], e1 = seg_end[B];
-        if (e1 <= e0) continue;
+        if (w >= nitems) break;
+        // the sorted sink this item belongs to: last i with item_start[i] <= w
+        int lo_i = 0, hi_i = (int)nsinks - 1;
+        while (lo_i < hi_i) {
+            const int mid = (lo_i + hi_i + 1) >> 1;
+            if ((unsigned)item_start[mid] <= w) lo_i = mid;
+            else hi_i = mid - 1;
+        }
+        const int B = order[lo_i];
+        const int s0 = seg_start[B], s1 = seg_end[B];
+        const int e0 = s0 + (int)(w - (unsigned)item_start[lo_i]) * kChunk, e1 = min(e0 + kChunk, s1);
         const d4 sB = cen[B];
         double sigma = sB.w;
-        if (!(sigma > 0)) {  // radius 0: half the closest source distance
+        if (!(sigma > 0)) {  // radius 0: half the closest source distance (over the whole list)
             double rmin = INFINITY;
-            for (int e = e0 + lane; e < e1; e += 32) {
+            for (int e = s0 + lane; e < s1; e += 32) {
                 const d4 zA = cen[list[e].x];
                 const double dx = sB.x - zA.x, dy = sB.y - zA.y, dz = sB.z - zA.z;
                 rmin = fmin(rmin, sqrt(dx * dx + dy * dy + dz * dz));
@@ -421,7 +432,7 @@ __global__ void __launch_bounds__(64) k_m2l_split(const int2* __restrict__ list,
             lowF[lane] = sum;
         }
         __syncwarp();
-        double* out = F + (size_t)B * nco;
+        double* out = part + (size_t)w * nco;
         const double sinv = 1.0 / sigma;
 #pragma unroll
         for (int q = 0; q < MAXQ; ++q) {
@@ -447,15 +458,43 @@ size_t m2l_split_smem(int p) {
     return 2 * ((per_warp + 15) & ~(size_t)15);
 }
 
-size_t m2l_split_tmp_bytes(int ncells, int p) {
+size_t m2l_split_tmp_bytes(int ncells, int p, long long npairs) {
     size_t n = (size_t)(ncells > 0 ? ncells : 1);
-    return m2l_tmp_bytes(ncells, p) + n * (size_t)ncoef(p) * sizeof(float2) + n * kN64 * sizeof(cd) + 512;
+    size_t items = (size_t)(npairs / kChunk) + n + 1;
+    return m2l_tmp_bytes(ncells, p) + n * (size_t)ncoef(p) * sizeof(float2) + n * kN64 * sizeof(cd) +
+           2 * n * sizeof(int) + scan_tmp_ints(n) * sizeof(int) + items * (size_t)ncoef(p) * sizeof(double) + 2048;
+}
+
+// chunks per sorted sink
+__global__ void k_item_counts(const int* __restrict__ order, const int* __restrict__ seg_start,
+                              const int* __restrict__ seg_end, int ncells, int* __restrict__ cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += gridDim.x * blockDim.x) {
+        const int B = order[i];
+        const int len = seg_end[B] - seg_start[B];
+        cnt[i] = (len + kChunk - 1) / kChunk;
+    }
+}
+
+// F_B = sum of its chunks' partial expansions, in chunk order
+__global__ void k_m2l_reduce(const int* __restrict__ order, const int* __restrict__ item_start,
+                             const int* __restrict__ cnt, const unsigned* __restrict__ work, int ncells, int nco,
+                             const double* __restrict__ part, double* __restrict__ F) {
+    const unsigned nsinks = work[1];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)ncells * nco;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / nco), j = (int)(t % nco);
+        if ((unsigned)i >= nsinks) continue;
+        const int a = item_start[i], b = a + cnt[i];
+        double v = 0.0;
+        for (int w = a; w < b; ++w) v += part[(size_t)w * nco + j];
+        F[(size_t)order[i] * nco + j] = v;
+    }
 }
 
 template <int MAXQ>
-static void m2l_split_launch(const int2* list, const int* seg_start, const int* seg_end, const int* order, int ncells,
-                             unsigned* work, const d4* cen, const float2* Mf, const cd* M64, int p, double* F,
-                             const LaneSched& sched, cudaStream_t s) {
+static void m2l_split_launch(const int2* list, const int* seg_start, const int* seg_end, const int* order,
+                             const int* item_start, int ncells, unsigned* work, const d4* cen, const float2* Mf,
+                             const cd* M64, int p, double* part, const LaneSched& sched, cudaStream_t s) {
     const int wpb = 2;
     size_t sm = m2l_split_smem(p);
     cudaFuncSetAttribute(k_m2l_split<MAXQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -464,7 +503,8 @@ static void m2l_split_launch(const int2* list, const int* seg_start, const int* 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l_split<MAXQ>, wpb * 32, sm);
     unsigned g = (unsigned)(nsm * (bps > 0 ? bps : 1));
-    k_m2l_split<MAXQ><<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, order, ncells, work, cen, Mf, M64, p, F, sched);
+    k_m2l_split<MAXQ><<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, order, item_start, ncells, work, cen, Mf, M64,
+                                              p, part, sched);
     note_launch();
 }
 
@@ -481,22 +521,34 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     int* v0 = (int*)(k1 + ncells);
     int* v1 = v0 + ncells;
     int* order = v1 + ncells;
-    unsigned* work = (unsigned*)(order + ncells);
+    unsigned* work = (unsigned*)(order + ncells);  // [0] item counter, [1] sinks, [2] items
     int* rtmp = (int*)(work + 4);
     unsigned char* after = (unsigned char*)(rtmp + radix_tmp_ints(ncells));
     float2* Mf = (float2*)(((uintptr_t)after + 255) & ~(uintptr_t)255);
     cd* M64 = (cd*)(((uintptr_t)(Mf + (size_t)ncells * ncoef(p)) + 255) & ~(uintptr_t)255);
+    int* cnt = (int*)(M64 + (size_t)ncells * kN64);
+    int* item_start = cnt + ncells;
+    int* stmp = item_start + ncells;
+    double* part = (double*)(((uintptr_t)(stmp + scan_tmp_ints(ncells)) + 255) & ~(uintptr_t)255);
     cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
     k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
     int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 0, 56, s);
     k_sink_order<<<grid_for(ncells, 256), 256, 0, s>>>(flip ? k1 : k0, ncells, order, work + 1); note_launch();
+    k_item_counts<<<grid_for(ncells, 256), 256, 0, s>>>(order, seg_start, seg_end, ncells, cnt); note_launch();
+    scan_exclusive_i32(cnt, item_start, ncells, (int*)(work + 2), stmp, s);
     k_prep_split<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(M, cen, ncells, p, Mf, M64); note_launch();
     LaneSched sched = make_lane_sched(p, kSchedDown);
     int maxq = 0;
     for (int l = 0; l < 32; ++l) maxq = sched.cnt[l] > maxq ? sched.cnt[l] : maxq;
-    if (maxq <= 4) m2l_split_launch<4>(list, seg_start, seg_end, order, ncells, work, cen, Mf, M64, p, F, sched, s);
-    else if (maxq <= 8) m2l_split_launch<8>(list, seg_start, seg_end, order, ncells, work, cen, Mf, M64, p, F, sched, s);
-    else m2l_split_launch<12>(list, seg_start, seg_end, order, ncells, work, cen, Mf, M64, p, F, sched, s);
+    if (maxq <= 4)
+        m2l_split_launch<4>(list, seg_start, seg_end, order, item_start, ncells, work, cen, Mf, M64, p, part, sched, s);
+    else if (maxq <= 8)
+        m2l_split_launch<8>(list, seg_start, seg_end, order, item_start, ncells, work, cen, Mf, M64, p, part, sched, s);
+    else
+        m2l_split_launch<12>(list, seg_start, seg_end, order, item_start, ncells, work, cen, Mf, M64, p, part, sched, s);
+    k_m2l_reduce<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(order, item_start, cnt, work, ncells,
+                                                                            ncoef(p), part, F);
+    note_launch();
 }
 
 // ---------------------------------------------------------------- L2L

@@ -104,7 +104,7 @@ size_t m2l_tmp_bytes(int ncells, int p);
 void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells,
                 const d4* cen, const double* M, int p, double* F, cudaStream_t s);
 // mixed mode: orders <= 2 of Theta in FP64, the rest in FP32 on scaled harmonics
-size_t m2l_split_tmp_bytes(int ncells, int p);
+size_t m2l_split_tmp_bytes(int ncells, int p, long long npairs);
 void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells,
                       const d4* cen, const double* M, int p, double* F, cudaStream_t s);
 void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F,

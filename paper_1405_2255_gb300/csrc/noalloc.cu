@@ -262,7 +262,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     double* M1 = A.take<double>(4 * (size_t)nc);
     double* F1 = A.take<double>(4 * (size_t)nc);
     double* Ff = A.take<double>(nc);
-    void* m2l_tmp = A.take<unsigned char>(m2l_split_tmp_bytes(nc, p > 1 ? p : 1));
+    void* m2l_tmp = A.take<unsigned char>(m2l_split_tmp_bytes(nc, p > 1 ? p : 1, kListCap));
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the expansions and lists");
     if (prm.precision == FMM_PREC_MIXED) launch_split_positions(r.xm, n, xhi, xlo, s);
 
