@@ -181,8 +181,8 @@ void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void
 constexpr int kJ64 = 2;
 constexpr int kN64 = (kJ64 + 1) * (kJ64 + 1);  // FP64 coefficients per expansion (orders <= kJ64)
 constexpr int kT64 = 20;                       // FP64 complex terms per pair for kJ64 = 2
-constexpr int kNBs = 8;                        // pairs per batch
-constexpr int kLoPerLane = kNBs * kT64 / 32;   // FP64 terms per lane per batch
+constexpr int kNBs = 4;                        // pairs per batch
+constexpr int kLoPerLane = (kNBs * kT64 + 31) / 32;  // FP64 terms per lane per batch
 
 struct TermTab {
     unsigned char n[kT64], m[kT64], k[kT64];
@@ -376,13 +376,14 @@ __global__ void __launch_bounds__(64) k_m2l_split(const int2* __restrict__ list,
                 T64[b * kN64 + cix(j, m)] = v;
                 if (m) T64[b * kN64 + cix(j, -m)] = (m & 1) ? mkc(-v.re, v.im) : mkc(v.re, -v.im);
             }
-            // FP32 Theta on the unit vectors, 4 lanes per pair
+            // FP32 Theta on the unit vectors, 32/kNBs lanes per pair
             {
-                const int b = lane >> 2, sub = lane & 3;
+                constexpr int LPP = 32 / kNBs;
+                const int b = lane / LPP, sub = lane % LPP;
                 if (b < nb) {
                     const PairInfo q = pi[b];
                     const float x = (float)(q.x * q.rinv), y = (float)(q.y * q.rinv), z = (float)(q.z * q.rinv);
-                    for (int m = sub; m <= p; m += 4) theta_column_unit_f(p, m, x, y, z, Th + b * nco);
+                    for (int m = sub; m <= p; m += LPP) theta_column_unit_f(p, m, x, y, z, Th + b * nco);
                 }
             }
             __syncwarp();
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(64) k_m2l_split(const int2* __restrict__ list,
 #pragma unroll
             for (int i = 0; i < kLoPerLane; ++i) {
                 const int t = lane + 32 * i, b = t / kT64, id = t % kT64;
-                if (b < nb) {
+                if (t < kNBs * kT64 && b < nb) {
                     const int n = c_terms.n[id], m = c_terms.m[id], k = c_terms.k[id], l = c_terms.l[id];
                     cmac(lo[i], M64[b * kN64 + cix(k, l)], T64[b * kN64 + cix(n + k, m + l)]);
                 }
@@ -404,12 +405,19 @@ __global__ void __launch_bounds__(64) k_m2l_split(const int2* __restrict__ list,
                 for (int q = 0; q < MAXQ; ++q) {
                     if (q < cnt) {
                         const int n = sched.n[lane][q], m = sched.m[lane][q];
-                        float2 a = make_float2(0.f, 0.f);
+                        float2 a = make_float2(0.f, 0.f), a2 = make_float2(0.f, 0.f);
                         for (int k = max(0, kJ64 + 1 - n); k <= p - n; ++k) {
                             const float2* xk = X + k * k + k;
                             const float2* yk = Y + (n + k) * (n + k) + (n + k) + m;
-                            for (int l = -k; l <= k; ++l) cmacf(a, xk[l], yk[l]);
+                            int l = -k;
+                            for (; l < k; l += 2) {
+                                cmacf(a, xk[l], yk[l]);
+                                cmacf(a2, xk[l + 1], yk[l + 1]);
+                            }
+                            cmacf(a, xk[k], yk[k]);
                         }
+                        a.x += a2.x;
+                        a.y += a2.y;
                         const float sc = tbb[n];
                         hacc[q].x = fmaf(a.x, sc, hacc[q].x);
                         hacc[q].y = fmaf(a.y, sc, hacc[q].y);
@@ -426,8 +434,9 @@ __global__ void __launch_bounds__(64) k_m2l_split(const int2* __restrict__ list,
             cd sum = mkc(0.0, 0.0);
             for (int L = 0; L < 32; ++L)
                 for (int i = 0; i < kLoPerLane; ++i) {
-                    const int id = (L + 32 * i) % kT64;
-                    if (c_terms.out[id] == lane) sum = sum + red[L * kLoPerLane + i];
+                    const int t = L + 32 * i;
+                    if (t >= kNBs * kT64) continue;
+                    if (c_terms.out[t % kT64] == lane) sum = sum + red[L * kLoPerLane + i];
                 }
             lowF[lane] = sum;
         }
