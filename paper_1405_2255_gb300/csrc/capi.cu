@@ -75,7 +75,7 @@ struct fmm_ctx {
     // expansions
     Buf M, F, Pw, binom, M1, F1, Ff;
     // walk
-    Buf front0, front1, m2l, p2p, sort_tmp, m2l_tmp, seg_start, seg_end, est_m2l, est_p2p, m2l_seg_start, m2l_seg_end;
+    Buf front0, front1, m2l, p2p, sort_tmp, m2l_tmp, p2p_tmp, seg_start, seg_end, est_m2l, est_p2p, m2l_seg_start, m2l_seg_end;
     long long front_cap = 0, m2l_cap = 0, p2p_cap = 0, est_m2l_cap = 0, est_p2p_cap = 0;
     // per particle results (sorted order)
     Buf psi_far, acc_far, psi_near, acc_near, scale_sorted;
@@ -332,9 +332,12 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     launch_l2p(P<d4>(ctx->xm), c, c.cr, P<int>(ctx->leaves), ctx->nleaves, pe, P<double>(ctx->F1),
                P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
     if (ctx->prm.precision == FMM_PREC_MIXED)
+    {
+        TRY(ensure(ctx->p2p_tmp, p2p_tmp_bytes(ctx->nleaves)));
         launch_p2p_mixed(P<d4>(ctx->xm), P<float4>(ctx->xhi), P<float4>(ctx->xlo), c, P<int2>(ctx->est_p2p),
                          P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
-                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), false, s);
+                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), false, ctx->p2p_tmp.p, s);
+    }
     else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->est_p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
                         P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
@@ -465,9 +468,13 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     // A10: P2P
     TRY(sort_and_segment(ctx, ctx->p2p, ctx->n_p2p, ctx->seg_start, ctx->seg_end, s));
     if (prm.precision == FMM_PREC_MIXED)
+    {
+        TRY(ensure(ctx->p2p_tmp, p2p_tmp_bytes(ctx->nleaves)));
         launch_p2p_mixed(P<d4>(ctx->xm), P<float4>(ctx->xhi), P<float4>(ctx->xlo), c, P<int2>(ctx->p2p),
                          P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
-                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), prm.p2p_two_float != 0, s);
+                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), prm.p2p_two_float != 0,
+                         ctx->p2p_tmp.p, s);
+    }
     else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
                         P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
@@ -736,7 +743,7 @@ int fmm_destroy(fmm_ctx* ctx) {
                   &ctx->sr, &ctx->cr, &ctx->mass, &ctx->minscale, &ctx->split_nchild, &ctx->split_oct,
                   &ctx->split_offs, &ctx->scan_tmp, &ctx->leaves, &ctx->leaf_flag, &ctx->leaf_pos, &ctx->rad_tmp,
                   &ctx->M, &ctx->F, &ctx->Pw, &ctx->binom, &ctx->M1, &ctx->F1, &ctx->Ff, &ctx->front0, &ctx->front1,
-                  &ctx->m2l, &ctx->p2p, &ctx->sort_tmp, &ctx->m2l_tmp, &ctx->seg_start, &ctx->seg_end, &ctx->est_m2l, &ctx->est_p2p,
+                  &ctx->m2l, &ctx->p2p, &ctx->sort_tmp, &ctx->m2l_tmp, &ctx->p2p_tmp, &ctx->seg_start, &ctx->seg_end, &ctx->est_m2l, &ctx->est_p2p,
                   &ctx->m2l_seg_start, &ctx->m2l_seg_end, &ctx->psi_far, &ctx->acc_far, &ctx->psi_near,
                   &ctx->acc_near, &ctx->scale_sorted};
     for (Buf* b : all) release(*b);

@@ -837,15 +837,20 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __re
                                                               const int2* __restrict__ list,
                                                               const int* __restrict__ seg_start,
                                                               const int* __restrict__ seg_end,
-                                                              const int* __restrict__ leaves, int nleaves,
+                                                              const int* __restrict__ order, int nleaves,
+                                                              unsigned* __restrict__ counter,
                                                               double* __restrict__ psi, double* __restrict__ acc) {
     __shared__ float4 th_all[kP2PWarps][32];
     __shared__ float4 tl_all[kP2PWarps][TWO_FLOAT ? 32 : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float4* th = th_all[wid];
     float4* tl = tl_all[wid];
-    for (int t = blockIdx.x * kP2PWarps + wid; t < nleaves; t += gridDim.x * kP2PWarps) {
-        const int leaf = leaves[t];
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(counter, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= (unsigned)nleaves) break;
+        const int leaf = order[w];
         const int first = c.first[leaf], count = c.count[leaf];
         const d4 sc = c.sr[leaf];
         const float shx = (float)sc.x, shy = (float)sc.y, shz = (float)sc.z;
@@ -948,16 +953,63 @@ void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long 
     }
 }
 
+// P2P work of a leaf: its sink chunks times the sources of its own and its ancestors'
+// segments; leaves are processed in decreasing order of it, taken from an atomic counter
+__global__ void k_p2p_work(Cells c, const int2* __restrict__ list, const int* __restrict__ seg_start,
+                           const int* __restrict__ seg_end, const int* __restrict__ leaves, int nleaves,
+                           uint64_t* __restrict__ keys, int* __restrict__ vals) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nleaves; t += gridDim.x * blockDim.x) {
+        const int leaf = leaves[t];
+        unsigned long long src = 0;
+        for (int cell = leaf; cell >= 0; cell = c.parent[cell])
+            for (int e = seg_start[cell]; e < seg_end[cell]; ++e) src += c.count[list[e].x];
+        unsigned long long work = src * (unsigned long long)((c.count[leaf] + 31) / 32);
+        const unsigned w32 = work > 0xffffffffull ? 0xffffffffu : (unsigned)work;
+        keys[t] = ((uint64_t)(0xffffffffu - w32) << 32) | (unsigned)t;
+        vals[t] = 0;
+    }
+}
+__global__ void k_p2p_order(const uint64_t* __restrict__ keys, const int* __restrict__ leaves, int nleaves,
+                            int* __restrict__ order) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nleaves; t += gridDim.x * blockDim.x)
+        order[t] = leaves[(int)(keys[t] & 0xffffffffu)];
+}
+
+size_t p2p_tmp_bytes(int nleaves) {
+    size_t n = (size_t)(nleaves > 0 ? nleaves : 1);
+    return n * (2 * sizeof(uint64_t) + 3 * sizeof(int)) + radix_tmp_ints(n) * sizeof(int) + 512;
+}
+
 void launch_p2p_mixed(const d4* /*xm*/, const float4* xhi, const float4* xlo, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* psi,
-                      double* acc, bool two_float, cudaStream_t s) {
+                      double* acc, bool two_float, void* tmp, cudaStream_t s) {
     if (nleaves <= 0) return;
-    if (two_float)
-        k_p2p_mixed<true><<<p2p_grid(nleaves), kP2PWarps * 32, 0, s>>>(xhi, xlo, c, list, seg_start, seg_end, leaves,
-                                                                       nleaves, psi, acc);
-    else
-        k_p2p_mixed<false><<<p2p_grid(nleaves), kP2PWarps * 32, 0, s>>>(xhi, xlo, c, list, seg_start, seg_end, leaves,
-                                                                        nleaves, psi, acc);
+    uint64_t* k0 = (uint64_t*)tmp;
+    uint64_t* k1 = k0 + nleaves;
+    int* v0 = (int*)(k1 + nleaves);
+    int* v1 = v0 + nleaves;
+    int* order = v1 + nleaves;
+    unsigned* counter = (unsigned*)(order + nleaves);
+    int* rtmp = (int*)(counter + 4);
+    cudaMemsetAsync(counter, 0, 4 * sizeof(unsigned), s);
+    k_p2p_work<<<grid_for(nleaves, 128), 128, 0, s>>>(c, list, seg_start, seg_end, leaves, nleaves, k0, v0);
+    note_launch();
+    const int flip = radix_sort_pairs_bits(k0, v0, k1, v1, nleaves, rtmp, 0, 64, s);
+    k_p2p_order<<<grid_for(nleaves, 256), 256, 0, s>>>(flip ? k1 : k0, leaves, nleaves, order);
+    note_launch();
+    int dev = 0, nsm = 152, bps = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (two_float) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_p2p_mixed<true>, kP2PWarps * 32, 0);
+        k_p2p_mixed<true><<<nsm * (bps > 0 ? bps : 1), kP2PWarps * 32, 0, s>>>(xhi, xlo, c, list, seg_start, seg_end,
+                                                                             order, nleaves, counter, psi, acc);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_p2p_mixed<false>, kP2PWarps * 32, 0);
+        k_p2p_mixed<false><<<nsm * (bps > 0 ? bps : 1), kP2PWarps * 32, 0, s>>>(xhi, xlo, c, list, seg_start,
+                                                                              seg_end, order, nleaves, counter, psi,
+                                                                              acc);
+    }
     note_launch();
 }
 

@@ -124,9 +124,10 @@ void launch_l2l_split(Cells c, const d4* cen, int lev_begin, int lev_end, int p,
 void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_start,
                      const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc, cudaStream_t s);
 // two_float: dx from two-float leaf-relative positions; otherwise from their FP32 high parts
+size_t p2p_tmp_bytes(int nleaves);
 void launch_p2p_mixed(const d4* xm, const float4* xhi, const float4* xlo, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves,
-                      double* psi, double* acc, bool two_float, cudaStream_t s);
+                      double* psi, double* acc, bool two_float, void* tmp, cudaStream_t s);
 // ordered pairs of distinct particles at distance 0 (sorted keys and positions)
 void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s);
 void launch_split_positions(const d4* xm, int n, float4* xhi, float4* xlo, cudaStream_t s);

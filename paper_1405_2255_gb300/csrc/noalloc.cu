@@ -263,6 +263,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     double* F1 = A.take<double>(4 * (size_t)nc);
     double* Ff = A.take<double>(nc);
     void* m2l_tmp = A.take<unsigned char>(m2l_split_tmp_bytes(nc, p > 1 ? p : 1, kListCap));
+    void* p2p_tmp = A.take<unsigned char>(p2p_tmp_bytes(r.nleaves));
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the expansions and lists");
     if (prm.precision == FMM_PREC_MIXED) launch_split_positions(r.xm, n, xhi, xlo, s);
 
@@ -295,7 +296,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
             launch_l2p(r.xm, r.c, r.c.cr, r.leaves, r.nleaves, 1, F1, psi_far, acc_far, s);
             if (prm.precision == FMM_PREC_MIXED)
                 launch_p2p_mixed(r.xm, xhi, xlo, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near,
-                                 acc_near, false, s);
+                                 acc_near, false, p2p_tmp, s);
             else
                 launch_p2p_fp64(r.xm, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
             launch_norm_scale(nullptr, acc_far, acc_near, n, scale, s);
@@ -344,7 +345,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     launch_segments(p2p, np, nc, seg_start, seg_end, s);
     if (prm.precision == FMM_PREC_MIXED)
         launch_p2p_mixed(r.xm, xhi, xlo, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near,
-                         prm.p2p_two_float != 0, s);
+                         prm.p2p_two_float != 0, p2p_tmp, s);
     else
         launch_p2p_fp64(r.xm, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
     for (int L = 1; L < nl; ++L) {
