@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __re
                                                               unsigned* __restrict__ counter,
                                                               double* __restrict__ psi, double* __restrict__ acc) {
     __shared__ float4 th_all[kP2PWarps][32];
-    __shared__ float4 tl_all[kP2PWarps][32];
+    __shared__ float4 tl_all[kP2PWarps][TWO_FLOAT ? 32 : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float4* th = th_all[wid];
     float4* tl = tl_all[wid];
@@ -875,132 +875,78 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __re
         const int leaf = order[w];
         const int first = c.first[leaf], count = c.count[leaf];
         const d4 sc = c.sr[leaf];
-        const float rhoB = (float)sc.w;
         const float shx = (float)sc.x, shy = (float)sc.y, shz = (float)sc.z;
         const float slx = (float)(sc.x - (double)shx), sly = (float)(sc.y - (double)shy),
                     slz = (float)(sc.z - (double)shz);
-        for (int g0 = 0; g0 < count; g0 += 96) {
-            const int ng = min(96, count - g0);
-            P2PChunk ch[3];
-            int nch = 0;
-            {
-                int rem = ng, off = 0;
-                while (rem > 0 && nch < 3) {
-                    int S;
-                    if (nch == 2 || rem <= 4) {
-                        S = 1;
-                        while (S < rem && S < 32) S <<= 1;
-                    } else {
-                        S = 32;
-                        while (S > rem) S >>= 1;
-                    }
-                    const int n = min(S, rem);
-                    P2PChunk& k = ch[nch];
-                    k.S = S;
-                    k.R = 32 / S;
-                    k.rep = lane / S;
-                    k.n = n;
-                    k.off = off;
-                    k.since = 0;
-                    k.ps = k.ax = k.ay = k.az = 0.f;
-                    k.aps = k.aax = k.aay = k.aaz = ff{0.f, 0.f};
-                    const int sink = lane % S;
-                    k.bhx = k.bhy = k.bhz = k.blx = k.bly = k.blz = 0.f;
-                    if (sink < n) {
-                        const int i = first + g0 + off + sink;
-                        const float4 h = xhi[i], l = xlo[i];
-                        const ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly),
-                                 rz = ff_sub(h.z, l.z, shz, slz);
-                        k.bhx = rx.hi; k.blx = rx.lo; k.bhy = ry.hi; k.bly = ry.lo; k.bhz = rz.hi; k.blz = rz.lo;
-                    }
-                    off += n;
-                    rem -= n;
-                    ++nch;
-                }
+        for (int s0 = 0; s0 < count; s0 += 32) {
+            const int chunk = min(32, count - s0);
+            const int R = chunk <= 8 ? 4 : (chunk <= 16 ? 2 : 1);
+            const int S = 32 / R;
+            const int sink = lane % S, rep = lane / S;
+            const bool active = sink < chunk;
+            const int i = first + s0 + sink;
+            float bhx = 0, bhy = 0, bhz = 0, blx = 0, bly = 0, blz = 0;
+            if (active) {
+                const float4 h = xhi[i], l = xlo[i];
+                const ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly), rz = ff_sub(h.z, l.z, shz, slz);
+                bhx = rx.hi; blx = rx.lo; bhy = ry.hi; bly = ry.lo; bhz = rz.hi; blz = rz.lo;
             }
-            for (int pass = 0; pass < 2; ++pass) {
-                const bool near_pass = pass == 0;
-                int fill = 0;
-                bool guard = false;
-                auto flush_tile = [&](int nt) {
-                    __syncwarp();
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        if (q < nch) {
-                            P2PChunk& k = ch[q];
-                            if (near_pass) {
-                                if (guard)
-                                    p2p_tile<TWO_FLOAT, true>(th, tl, nt, k.rep, k.R, k.bhx, k.bhy, k.bhz, k.blx, k.bly,
-                                                              k.blz, k.ps, k.ax, k.ay, k.az);
-                                else
-                                    p2p_tile<TWO_FLOAT, false>(th, tl, nt, k.rep, k.R, k.bhx, k.bhy, k.bhz, k.blx,
-                                                               k.bly, k.blz, k.ps, k.ax, k.ay, k.az);
-                            } else {
-                                p2p_tile<false, false>(th, tl, nt, k.rep, k.R, k.bhx, k.bhy, k.bhz, k.blx, k.bly, k.blz,
-                                                       k.ps, k.ax, k.ay, k.az);
-                            }
-                            k.since += (nt + k.R - 1) / k.R;
-                            if (k.since >= 32) p2p_fold(k);
+            ff aps = {0, 0}, aax = {0, 0}, aay = {0, 0}, aaz = {0, 0};
+            float ps = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+            int fill = 0, since = 0;
+            bool guard = false;
+            auto flush_tile = [&](int nt) {
+                __syncwarp();
+                if (guard)
+                    p2p_tile<TWO_FLOAT, true>(th, tl, nt, rep, R, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+                else
+                    p2p_tile<TWO_FLOAT, false>(th, tl, nt, rep, R, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+                since += 32;
+                if (since >= 32 * R) {  // fold the FP32 partials into the two-float sums every ~32 pairs
+                    ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
+                    ps = ax = ay = az = 0.f;
+                    since = 0;
+                }
+                __syncwarp();
+            };
+            for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
+                const int e0 = seg_start[cell], e1 = seg_end[cell];
+                for (int e = e0; e < e1; ++e) {
+                    const int A = list[e].x;
+                    const int af = c.first[A], an = c.count[A];
+                    const bool contains = af <= first && first < af + an;
+                    for (int off = 0; off < an;) {
+                        const int k = min(32 - fill, an - off);
+                        if (lane < k) {
+                            const int j = af + off + lane;
+                            const float4 h = xhi[j], l = xlo[j];
+                            const ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly),
+                                     rz = ff_sub(h.z, l.z, shz, slz);
+                            th[fill + lane] = make_float4(rx.hi, ry.hi, rz.hi, h.w);
+                            if (TWO_FLOAT) tl[fill + lane] = make_float4(rx.lo, ry.lo, rz.lo, 0.f);
                         }
-                    }
-                    __syncwarp();
-                };
-                for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
-                    const int e0 = seg_start[cell], e1 = seg_end[cell];
-                    for (int e = e0; e < e1; ++e) {
-                        const int A = list[e].x;
-                        const int af = c.first[A], an = c.count[A];
-                        const bool contains = af <= first && first < af + an;
-                        const d4 sa = c.sr[A];
-                        const float dx = (float)sa.x - shx, dy = (float)sa.y - shy, dz = (float)sa.z - shz;
-                        const float d = sqrtf(dx * dx + dy * dy + dz * dz);
-                        const bool far = !contains && (d - (float)sa.w > 4.f * rhoB);
-                        if (far == near_pass) continue;
-                        for (int off = 0; off < an;) {
-                            const int k = min(32 - fill, an - off);
-                            if (lane < k) {
-                                const int j = af + off + lane;
-                                const float4 h = xhi[j], l = xlo[j];
-                                if (near_pass) {
-                                    const ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly),
-                                             rz = ff_sub(h.z, l.z, shz, slz);
-                                    th[fill + lane] = make_float4(rx.hi, ry.hi, rz.hi, h.w);
-                                    tl[fill + lane] = make_float4(rx.lo, ry.lo, rz.lo, 0.f);
-                                } else {
-                                    th[fill + lane] = make_float4((h.x - shx) + (l.x - slx), (h.y - shy) + (l.y - sly),
-                                                                  (h.z - shz) + (l.z - slz), h.w);
-                                }
-                            }
-                            guard |= contains;
-                            fill += k;
-                            off += k;
-                            if (fill == 32) {
-                                flush_tile(32);
-                                fill = 0;
-                                guard = false;
-                            }
+                        guard |= contains;
+                        fill += k;
+                        off += k;
+                        if (fill == 32) {
+                            flush_tile(32);
+                            fill = 0;
+                            guard = false;
                         }
                     }
                 }
-                if (fill) flush_tile(fill);
             }
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                if (q < nch) {
-                    P2PChunk& k = ch[q];
-                    p2p_fold(k);
-                    for (int o = k.S; o < 32; o <<= 1) {
-                        ff_add_shfl(k.aps, o); ff_add_shfl(k.aax, o); ff_add_shfl(k.aay, o); ff_add_shfl(k.aaz, o);
-                    }
-                    const int sink = lane % k.S;
-                    if (k.rep == 0 && sink < k.n) {
-                        const int i = first + g0 + k.off + sink;
-                        psi[i] = (double)k.aps.hi + (double)k.aps.lo;
-                        acc[3 * (size_t)i] = (double)k.aax.hi + (double)k.aax.lo;
-                        acc[3 * (size_t)i + 1] = (double)k.aay.hi + (double)k.aay.lo;
-                        acc[3 * (size_t)i + 2] = (double)k.aaz.hi + (double)k.aaz.lo;
-                    }
-                }
+            if (fill) flush_tile(fill);
+            ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
+            // add the replicas' partial sums (lanes sink, sink + S, ...)
+            for (int o = S; o < 32; o <<= 1) {
+                ff_add_shfl(aps, o); ff_add_shfl(aax, o); ff_add_shfl(aay, o); ff_add_shfl(aaz, o);
+            }
+            if (active && rep == 0) {
+                psi[i] = (double)aps.hi + (double)aps.lo;
+                acc[3 * (size_t)i] = (double)aax.hi + (double)aax.lo;
+                acc[3 * (size_t)i + 1] = (double)aay.hi + (double)aay.lo;
+                acc[3 * (size_t)i + 2] = (double)aaz.hi + (double)aaz.lo;
             }
         }
     }
