@@ -50,6 +50,29 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+# ALU peaks derived from the unit counts and the maximum SM clock: 152 SMs x 128 FP32
+# lanes x 2 flops (FFMA) x 2070 MHz; FP64 is the part's nominal 1.25 TFLOP/s
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def max_over_ranks(v, world, device=None):
+    """Maximum of a per-rank float over all ranks (the slowest rank sets the job time)."""
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_per_rank, world, seconds):
+    """Whole-job throughput under weak scaling: every rank's particles over the max time."""
+    return n_per_rank * world / seconds
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -201,13 +224,8 @@ def main():
             launches += int(st["launches"])
         torch.cuda.synchronize(dev)
     barrier()
-    ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1)]))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = a.n * world / (ms * 1e-3)
+    ms = max_over_ranks(np.mean([e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1)]), world, dev)
+    value = job_value(a.n, world, ms * 1e-3)
 
     # accuracy of the timed configuration: GPU FP64 direct sum on sampled sinks
     rng = np.random.default_rng(rank)
@@ -225,22 +243,20 @@ def main():
     _, _, full = ctx.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc, stats=True)
     t_m2l = float(np.mean([s["t_m2l"] for s in phase])) * 1e-3
     t_p2p = float(np.mean([s["t_p2p"] for s in phase])) * 1e-3
-    fp64_peak, fp32_peak = g.fmm_alu_peaks()
+    loop64, loop32 = g.fmm_alu_peaks()
+    mixed = prec == g.FMM_PREC_MIXED
+    pk, loop = (FP32_PEAK_TFLOPS, loop32) if mixed else (FP64_PEAK_TFLOPS, loop64)
+    src = ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz" if mixed
+           else "nominal FP64 rate of the part (1.25 TFLOP/s)")
     if t_m2l >= t_p2p:
         achieved = full["n_m2l"] * m2l_flops(a.p) / t_m2l / 1e12
-        mixed = prec == g.FMM_PREC_MIXED
-        pk = fp32_peak if mixed else fp64_peak
-        roof = {"kernel": "k_m2l_split (eq. 3b, orders > 2 in FP32)" if mixed else "k_m2l (eq. 3b, FP64)",
-                "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                "traffic": None,
-                "peak_source": ("FP32 FFMA" if mixed else "FP64 DFMA") + " loop measured by fmm_alu_peaks on this GPU"}
+        kern = "k_m2l_split (eq. 3b, orders > 2 in FP32)" if mixed else "k_m2l (eq. 3b, FP64)"
     else:
-        flops_p2p = 20.0 * full["p2p_interactions"]
-        pk = fp32_peak if prec == g.FMM_PREC_MIXED else fp64_peak
-        achieved = flops_p2p / t_p2p / 1e12
-        roof = {"kernel": "k_p2p (eq. 1)", "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": achieved / pk, "traffic": None,
-                "peak_source": "FFMA/DFMA loop measured by fmm_alu_peaks on this GPU"}
+        achieved = 20.0 * full["p2p_interactions"] / t_p2p / 1e12
+        kern = "k_p2p_mixed (eq. 1, FP32 two-float)" if mixed else "k_p2p_fp64 (eq. 1)"
+    roof = {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+            "frac": achieved / pk, "traffic": None, "peak_source": src,
+            "peak_loop_measured": loop, "frac_of_loop": achieved / loop}
 
     extras = {}
     if not a.no_extras and rank == 0:
@@ -273,12 +289,7 @@ def main():
         t0 = time.perf_counter()
         ctx.fmm_evaluate_host(xh, mh, 1.0, psi=ph, acc=ah, stream=stream)
         te.append(time.perf_counter() - t0)
-    t_e2e = float(np.mean(te))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(np.mean(te), world, dev)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -301,7 +312,7 @@ def main():
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == g.FMM_PREC_MIXED else "f64", "data": "synthetic",
             "config": cfg,
-            "e2e": {"value": a.n * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * a.n,
+            "e2e": {"value": job_value(a.n, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": 32 * a.n,
                     "d2h_bytes_per_step": 32 * a.n},
             "roofline": roof, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary(),
         }

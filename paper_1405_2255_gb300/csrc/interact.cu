@@ -831,28 +831,8 @@ __device__ __forceinline__ void p2p_tile(const float4* __restrict__ th, const fl
     }
 }
 
-// Sinks of a leaf are taken in groups of up to 96 and each group is cut into at
-// most three chunks of power-of-two size S (32, 16, ..., 1); in chunk c lane L holds
-// sink L % S and takes every (32/S)-th source of a staged tile, so small and
-// ragged leaves still keep most lanes busy, and one staged tile serves all chunks.
-// Sources are streamed in two passes over the leaf's P2P segments: first the
-// "near" cells (within 4 leaf radii of the leaf centre, including the leaf
-// itself), whose pairs form dx from the two-float positions, then the "far"
-// cells, for which dx from the FP32 high parts is already accurate to FP32
-// rounding (|dx| >= 3 rho_B).
-struct P2PChunk {
-    float bhx, bhy, bhz, blx, bly, blz;
-    float ps, ax, ay, az;
-    ff aps, aax, aay, aaz;
-    int rep, R, S, n, off, since;
-};
-
-__device__ inline void p2p_fold(P2PChunk& k) {
-    ff_acc(k.aps, k.ps); ff_acc(k.aax, k.ax); ff_acc(k.aay, k.ay); ff_acc(k.aaz, k.az);
-    k.ps = k.ax = k.ay = k.az = 0.f;
-    k.since = 0;
-}
-
+// One warp per sink leaf, leaves taken in decreasing order of work from an atomic
+// counter; sources come from the P2P segments of the leaf and of its ancestors.
 template <bool TWO_FLOAT>
 __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __restrict__ xhi,
                                                               const float4* __restrict__ xlo, Cells c,
