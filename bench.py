@@ -43,7 +43,15 @@ def parse():
     ap.add_argument("--c", type=float, default=4.0)
     ap.add_argument("--cpu-sample", type=int, default=50000)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-mode and direct-sum comparisons")
-    return ap.parse_args()
+    ap.add_argument("--workload", default="plummer", choices=["plummer", "cusp", "ensemble", "serve"],
+                    help="plummer: one N=1e6 sphere (default); cusp: gamma=1.5 model with a central point mass; "
+                         "ensemble: 256 spheres of 1e3..1e5 in one forest; serve: 64 systems of 1e4..2e6 "
+                         "served at 0.8 of capacity (Poisson arrivals)")
+    ap.add_argument("--requests", type=int, default=384, help="serve: requests in the open-loop run")
+    a = ap.parse_args()
+    if a.workload == "cusp" and a.n == 1_000_000:
+        a.n = 10_000_000
+    return a
 
 
 def dist_env():
@@ -65,6 +73,16 @@ def max_over_ranks(v, world, device=None):
     import torch.distributed as dist
     t = torch.tensor([float(v)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, world, device=None):
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -133,10 +151,10 @@ def m2l_flops(p):
     return 8 * sum((n + 1) * (p - n + 1) ** 2 for n in range(p + 1))
 
 
-def oracle_run(n, p, eps, leaf, c, seed):
+def oracle_run(n, p, eps, leaf, c, seed, model="plummer"):
     import oracle
     from paper_1405_2255_gb300 import inputs
-    x, mu = inputs.plummer(n, seed)
+    x, mu = (inputs.dehnen if model == "cusp" else inputs.plummer)(n, seed)
     t = time.perf_counter()
     oracle.fmm(x, mu, p=p, eps=eps, leaf_size=leaf, p2p_c=c, keep=False)
     return time.perf_counter() - t
@@ -168,7 +186,263 @@ def reference_arm(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def roofline(g, a, prec, phase, full):
+    """Achieved vs peak of the dominant kernel: algorithmic flops of the run's own lists
+    over its CUDA-event phase time averaged over the timed steps."""
+    t_m2l = float(np.mean([s["t_m2l"] for s in phase])) * 1e-3
+    t_p2p = float(np.mean([s["t_p2p"] for s in phase])) * 1e-3
+    loop64, loop32 = g.fmm_alu_peaks()
+    mixed = prec == g.FMM_PREC_MIXED
+    pk, loop = (FP32_PEAK_TFLOPS, loop32) if mixed else (FP64_PEAK_TFLOPS, loop64)
+    src = ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz" if mixed
+           else "nominal FP64 rate of the part (1.25 TFLOP/s)")
+    if t_m2l >= t_p2p:
+        achieved = full["n_m2l"] * m2l_flops(a.p) / t_m2l / 1e12
+        kern = "k_m2l_split (eq. 3b, orders > 2 in FP32)" if mixed else "k_m2l (eq. 3b, FP64)"
+    else:
+        achieved = 20.0 * full["p2p_interactions"] / t_p2p / 1e12
+        kern = "k_p2p_mixed (eq. 1, FP32 two-float)" if mixed else "k_p2p_fp64 (eq. 1)"
+    return {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+            "frac": achieved / pk, "traffic": None, "peak_source": src,
+            "peak_loop_measured": loop, "frac_of_loop": achieved / loop,
+            "phase_share": {"m2l": t_m2l / (float(np.mean([s["t_total"] for s in phase])) * 1e-3),
+                            "p2p": t_p2p / (float(np.mean([s["t_total"] for s in phase])) * 1e-3)}}
+
+
+def sampled_error(ctx, xt, mt, acc, idx, dev, G=1.0):
+    """rms and 99.9th percentile of |a - a_direct| / |a_direct| over the sinks idx
+    (FP64 direct sums over all sources on the GPU)."""
+    import torch
+    sinks = torch.from_numpy(np.asarray(idx, dtype=np.int64)).to(dev)
+    _, acc_t = ctx.fmm_direct(xt, mt, G, sinks=sinks)
+    e = (torch.linalg.norm(acc[sinks] - acc_t, dim=1) / torch.linalg.norm(acc_t, dim=1)).cpu().numpy()
+    return e
+
+
+def cpu_sample_line(a, model="plummer"):
+    import oracle
+    from paper_1405_2255_gb300 import inputs
+    oracle.build()
+    tcpu = oracle_run(a.cpu_sample, a.p, a.eps, a.leaf, a.c, inputs.BASE_SEED + 2, model)
+    return {"value": a.cpu_sample / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle FMM (serial C, FP64) on a {model} system of N={a.cpu_sample} of the same "
+                      f"recipe and parameters, one evaluation ({tcpu:.1f} s)"}
+
+
+def run_ensemble(a, g, dev, local, rank, world, prec):
+    """256 Plummer spheres of N log-uniform in [1e3, 1e5] with Kroupa-like masses,
+    evaluated together as one forest per step (fmm_evaluate_batch)."""
+    import torch
+    from paper_1405_2255_gb300 import inputs
+    systems = inputs.ensemble(256, inputs.BASE_SEED + 4 + 7919 * rank)
+    sizes = np.array([len(m) for _, m in systems])
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    ntot = int(off[-1])
+    xs = np.concatenate([s[0] for s in systems])
+    ms = np.concatenate([s[1] for s in systems])
+    xt, mt = torch.from_numpy(xs).to(dev), torch.from_numpy(ms).to(dev)
+    psi = torch.empty(ntot, dtype=torch.float64, device=dev)
+    acc = torch.empty((ntot, 3), dtype=torch.float64, device=dev)
+    G = np.ones(len(systems))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = g.Context(p=a.p, eps=a.eps, leaf_size=a.leaf, p2p_c=a.c, precision=prec, device=local)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(a.warmup, 3)):
+        ctx.fmm_evaluate_batch(off, xt, mt, G, psi=psi, acc=acc)
+    torch.cuda.synchronize(dev)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    phase, launches = [], 0
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(a.steps):
+            flush.zero_()
+            ev0[k].record(stream)
+            ctx.fmm_evaluate_batch(off, xt, mt, G, psi=psi, acc=acc)
+            ev1[k].record(stream)
+            st = ctx.fmm_last_stats()
+            phase.append(st)
+            launches += int(st["launches"])
+        torch.cuda.synchronize(dev)
+    ms_step = max_over_ranks(np.mean([e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1)]), world, dev)
+    value = job_value(ntot, world, ms_step * 1e-3)
+    _, _, full = ctx.fmm_evaluate_batch(off, xt, mt, G, psi=psi, acc=acc, stats=True)
+    roof = roofline(g, a, prec, phase, full)
+    # accuracy: 16 sinks of every system against the FP64 direct sum over that system
+    rng = np.random.default_rng(rank)
+    errs = []
+    for i in range(len(systems)):
+        n = int(sizes[i])
+        sl = slice(int(off[i]), int(off[i + 1]))
+        idx = np.sort(rng.choice(n, min(n, 16), replace=False))
+        errs.append(sampled_error(ctx, xt[sl], mt[sl], acc[sl], idx, dev))
+    e = np.concatenate(errs)
+    extras = {}
+    if not a.no_extras and rank == 0:
+        # the same systems one call each (no forest)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(len(systems)):
+            sl = slice(int(off[i]), int(off[i + 1]))
+            ctx.fmm_evaluate(xt[sl], mt[sl], 1.0, psi=psi[sl], acc=acc[sl])
+        torch.cuda.synchronize(dev)
+        extras["one_call_per_system_value"] = ntot / (time.perf_counter() - t0)
+    # end to end: pinned host inputs in, the forest evaluation, results back to pinned host memory
+    xh, mh = torch.from_numpy(xs).pin_memory(), torch.from_numpy(ms).pin_memory()
+    ah = torch.empty((ntot, 3), dtype=torch.float64).pin_memory()
+    ph = torch.empty(ntot, dtype=torch.float64).pin_memory()
+    te = []
+    for k in range(a.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        xt.copy_(xh, non_blocking=True)
+        mt.copy_(mh, non_blocking=True)
+        ctx.fmm_evaluate_batch(off, xt, mt, G, psi=psi, acc=acc)
+        ph.copy_(psi, non_blocking=True)
+        ah.copy_(acc, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if k:
+            te.append(time.perf_counter() - t0)
+    t_e2e = max_over_ranks(np.mean(te), world, dev)
+    cpu = cpu_sample_line(a) if rank == 0 and world == 1 else None
+    if rank == 0:
+        cfg = {"workload": "ensemble256_plummer_kroupa", "systems": len(systems), "n_total": ntot,
+               "n_range": [int(sizes.min()), int(sizes.max())],
+               "model": "256 truncated Plummer spheres, N log-uniform in [1e3, 1e5], Kroupa-like masses",
+               "p": a.p, "eps": a.eps, "mac": "18a (low-order a estimate)", "leaf_size": a.leaf, "p2p_c": a.c,
+               "precision": a.precision, "l2": "flushed between steps (256 MiB write)",
+               "parallelism": "one forest per call; replicas across GPUs",
+               "rms_rel_err": float(np.sqrt(np.mean(e ** 2))), "p999_rel_err": float(np.percentile(e, 99.9)),
+               "err_sinks": int(len(e)),
+               "phase_ms": {k: float(np.mean([s[k] for s in phase])) for k in
+                            ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total")}}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if prec == g.FMM_PREC_MIXED else "f64",
+                "data": "synthetic", "config": cfg,
+                "e2e": {"value": job_value(ntot, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": 32 * ntot,
+                        "d2h_bytes_per_step": 32 * ntot},
+                "roofline": roof, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary()}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_serve(a, g, dev, local, rank, world, prec):
+    """64 concurrent simulations (half Plummer, half gamma = 1.5 cusps, N log-uniform in
+    [1e4, 2e6]) served by the request loop.  Capacity is measured closed-loop (all
+    systems submitted at once); then requests arrive as a Poisson process at 0.8 of
+    that capacity, each system taking the next request once its previous result is
+    back, and latency is counted from arrival to completion."""
+    import torch
+    from paper_1405_2255_gb300 import inputs
+    systems = inputs.served_systems(64, inputs.BASE_SEED + 5 + 7919 * rank)
+    sizes = np.array([len(m) for _, m in systems])
+    dx = [torch.from_numpy(x).to(dev) for x, _ in systems]
+    dm = [torch.from_numpy(m).to(dev) for _, m in systems]
+    dp = [torch.empty(n, dtype=torch.float64, device=dev) for n in sizes]
+    da = [torch.empty((n, 3), dtype=torch.float64, device=dev) for n in sizes]
+    ctx = g.Context(p=a.p, eps=a.eps, leaf_size=a.leaf, p2p_c=a.c, precision=prec, device=local)
+    ctx.fmm_serve_config(0, 2)
+    ids = [ctx.fmm_system_register(int(n)) for n in sizes]
+    torch.cuda.synchronize(dev)
+
+    def closed_loop():
+        t0 = time.perf_counter()
+        tks = [ctx.fmm_submit(i, dx[k], dm[k], 1.0, dp[k], da[k]) for k, i in enumerate(ids)]
+        for t in tks:
+            ctx.fmm_poll(t, -1)
+        return time.perf_counter() - t0
+
+    for _ in range(max(a.warmup, 3)):
+        closed_loop()
+    caps = [closed_loop() for _ in range(max(a.steps, 1))]
+    t_cap = float(np.median(caps))
+    capacity = float(sizes.sum()) / t_cap
+    # open loop: aggregate Poisson arrivals at 0.8 capacity, systems in turn
+    nreq = a.requests
+    rate = 0.8 * capacity / float(sizes.mean())
+    arrivals = inputs.poisson_arrivals(nreq, rate, inputs.BASE_SEED + 5 + 31 * rank)
+    order = np.arange(nreq) % len(systems)
+    backlog = [[] for _ in systems]
+    inflight = {}
+    lat, done_n = [], 0
+    nxt = 0
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        while nxt < nreq or inflight or any(backlog):
+            now = time.perf_counter() - t0
+            while nxt < nreq and arrivals[nxt] <= now:
+                k = int(order[nxt])
+                backlog[k].append(arrivals[nxt])
+                nxt += 1
+            for k in range(len(systems)):
+                if backlog[k] and k not in inflight:
+                    t_arr = backlog[k].pop(0)
+                    ts = time.perf_counter() - t0
+                    inflight[k] = (ctx.fmm_submit(ids[k], dx[k], dm[k], 1.0, dp[k], da[k]), t_arr, ts)
+            for k in list(inflight):
+                tk, t_arr, ts = inflight[k]
+                l = ctx.fmm_poll(tk, 0)
+                if l is not None:
+                    lat.append(ts + l - t_arr)
+                    done_n += int(sizes[k])
+                    del inflight[k]
+            time.sleep(2e-4)
+        elapsed = time.perf_counter() - t0
+    value = done_n / elapsed
+    lat_ms = 1e3 * np.array(lat)
+    # the results of the last requests against each system alone, and their accuracy
+    alone = g.Context(p=a.p, eps=a.eps, leaf_size=a.leaf, p2p_c=a.c, precision=prec, device=local)
+    same = 0
+    errs = []
+    rng = np.random.default_rng(rank)
+    for k in range(len(systems)):
+        p1, a1 = alone.fmm_evaluate(dx[k], dm[k], 1.0)
+        same += int(torch.equal(a1, da[k]) and torch.equal(p1, dp[k]))
+        idx = np.sort(rng.choice(int(sizes[k]), 64, replace=False))
+        if k % 2 == 1:
+            idx[0] = 0  # the cusps' central point mass
+        errs.append(sampled_error(alone, dx[k], dm[k], da[k], np.unique(idx), dev))
+    e = np.concatenate(errs)
+    alone.close()
+    cpu = cpu_sample_line(a) if rank == 0 and world == 1 else None
+    value = sum_over_ranks(done_n, world, dev) / max_over_ranks(elapsed, world, dev)
+    if rank == 0:
+        cfg = {"workload": "serve64_plummer_cusp", "systems": len(systems), "n_total": int(sizes.sum()),
+               "n_range": [int(sizes.min()), int(sizes.max())],
+               "model": "32 truncated Plummer spheres + 32 gamma=1.5 cusps with 1% central point mass, "
+                        "N log-uniform in [1e4, 2e6]",
+               "p": a.p, "eps": a.eps, "mac": "18a (low-order a estimate)", "leaf_size": a.leaf, "p2p_c": a.c,
+               "precision": a.precision, "slots": 2, "requests": nreq, "load": 0.8,
+               "capacity_pf_s": capacity, "closed_loop_ms": 1e3 * t_cap,
+               "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                              "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
+               "results_equal_alone": f"{same}/{len(systems)}",
+               "rms_rel_err": float(np.sqrt(np.mean(e ** 2))), "p999_rel_err": float(np.percentile(e, 99.9)),
+               "err_sinks": int(len(e)), "l2": "inputs larger than L2 (19M particles resident)",
+               "parallelism": "2 slots with continuous batching; replicas across GPUs"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": nreq,
+                "warmup": a.warmup, "ms_per_step": float(lat_ms.mean()), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if prec == g.FMM_PREC_MIXED else "f64", "data": "synthetic", "config": cfg,
+                "e2e": None, "roofline": None, "cpu_baseline": cpu, "gpu_launches": None,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def config_of(a):
+    if a.workload == "cusp":
+        return {"workload": f"cusp_n{a.n}", "n": a.n,
+                "model": "Dehnen gamma=1.5 truncated at 30 scale radii, equal masses, 1% central point mass",
+                "p": a.p, "eps": a.eps, "mac": "18a (low-order a estimate)", "leaf_size": a.leaf, "p2p_c": a.c,
+                "precision": a.precision, "l2": "inputs larger than L2 (320 MB of positions)",
+                "parallelism": "replicas"}
     return {"workload": f"plummer_n{a.n}", "n": a.n, "model": "truncated Plummer sphere R_t=30, equal masses",
             "p": a.p, "eps": a.eps, "mac": "18a (low-order a estimate)", "leaf_size": a.leaf, "p2p_c": a.c,
             "precision": a.precision, "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas"}
@@ -189,7 +463,14 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     g.load()
     prec = g.FMM_PREC_MIXED if a.precision == "mixed" else g.FMM_PREC_FP64
-    x, mu = inputs.plummer(a.n, inputs.BASE_SEED + 2 + 7919 * rank)
+    if a.workload == "ensemble":
+        return run_ensemble(a, g, dev, local, rank, world, prec)
+    if a.workload == "serve":
+        return run_serve(a, g, dev, local, rank, world, prec)
+    if a.workload == "cusp":
+        x, mu = inputs.dehnen(a.n, inputs.BASE_SEED + 3 + 7919 * rank)
+    else:
+        x, mu = inputs.plummer(a.n, inputs.BASE_SEED + 2 + 7919 * rank)
     xt = torch.from_numpy(x).to(dev)
     mt = torch.from_numpy(mu).to(dev)
     psi = torch.empty(a.n, dtype=torch.float64, device=dev)
@@ -230,7 +511,11 @@ def main():
     # accuracy of the timed configuration: GPU FP64 direct sum on sampled sinks
     rng = np.random.default_rng(rank)
     ns = min(a.n, 4096)
-    sinks = torch.from_numpy(np.sort(rng.choice(a.n, ns, replace=False)).astype(np.int64)).to(dev)
+    pick = rng.choice(a.n, ns, replace=False)
+    if a.workload == "cusp":
+        pick[0] = 0  # the central point mass is always in the sample
+    sinks = torch.from_numpy(np.sort(np.unique(pick)).astype(np.int64)).to(dev)
+    ns = int(sinks.numel())
     torch.cuda.synchronize(dev)
     td0 = time.perf_counter()
     _, acc_t = ctx.fmm_direct(xt, mt, 1.0, sinks=sinks)
@@ -241,22 +526,7 @@ def main():
 
     # roofline of the dominant kernel (phase times averaged over the timed steps)
     _, _, full = ctx.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc, stats=True)
-    t_m2l = float(np.mean([s["t_m2l"] for s in phase])) * 1e-3
-    t_p2p = float(np.mean([s["t_p2p"] for s in phase])) * 1e-3
-    loop64, loop32 = g.fmm_alu_peaks()
-    mixed = prec == g.FMM_PREC_MIXED
-    pk, loop = (FP32_PEAK_TFLOPS, loop32) if mixed else (FP64_PEAK_TFLOPS, loop64)
-    src = ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz" if mixed
-           else "nominal FP64 rate of the part (1.25 TFLOP/s)")
-    if t_m2l >= t_p2p:
-        achieved = full["n_m2l"] * m2l_flops(a.p) / t_m2l / 1e12
-        kern = "k_m2l_split (eq. 3b, orders > 2 in FP32)" if mixed else "k_m2l (eq. 3b, FP64)"
-    else:
-        achieved = 20.0 * full["p2p_interactions"] / t_p2p / 1e12
-        kern = "k_p2p_mixed (eq. 1, FP32 two-float)" if mixed else "k_p2p_fp64 (eq. 1)"
-    roof = {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-            "frac": achieved / pk, "traffic": None, "peak_source": src,
-            "peak_loop_measured": loop, "frac_of_loop": achieved / loop}
+    roof = roofline(g, a, prec, phase, full)
 
     extras = {}
     if not a.no_extras and rank == 0:
@@ -291,14 +561,7 @@ def main():
         te.append(time.perf_counter() - t0)
     t_e2e = max_over_ranks(np.mean(te), world, dev)
 
-    cpu = None
-    if rank == 0 and world == 1:
-        import oracle
-        oracle.build()
-        tcpu = oracle_run(a.cpu_sample, a.p, a.eps, a.leaf, a.c, inputs.BASE_SEED + 2)
-        cpu = {"value": a.cpu_sample / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle FMM (serial C, FP64) on a Plummer sphere of N={a.cpu_sample} of the same "
-                         f"recipe and parameters, one evaluation ({tcpu:.1f} s)"}
+    cpu = cpu_sample_line(a, "cusp" if a.workload == "cusp" else "plummer") if rank == 0 and world == 1 else None
 
     if rank == 0:
         cfg = config_of(a)

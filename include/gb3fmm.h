@@ -47,7 +47,7 @@ extern "C" {
 #define FMM_E_TIMEOUT    -5   /* a bounded device or host wait ran out */
 #define FMM_E_OVERFLOW   -6   /* an internal capacity could not be grown */
 #define FMM_E_NOTFOUND   -7   /* unknown system id or ticket */
-#define FMM_E_BUSY       -8   /* the request is not finished yet (fmm_poll) */
+#define FMM_E_BUSY       -8   /* not finished yet (fmm_poll), or a request already in flight */
 
 /* multipole-acceptance criteria */
 #define FMM_MAC_A      0  /* eq. (18a): theta<1 and E~ M_A/r^2 < eps min_{b in B} a_b  */
@@ -146,11 +146,60 @@ int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, doubl
 
 /* Many independent systems in one call (the batched ensemble).  System s holds
  * particles [offsets[s], offsets[s+1]) of x/mu/psi/acc (device arrays laid out as
- * for fmm_evaluate); offsets is a HOST int64 array of nsys+1 entries starting at 0;
- * G is a HOST array of nsys constants.  Systems share no interactions. */
+ * for fmm_evaluate); offsets is a HOST int64 array of nsys+1 non-decreasing entries
+ * starting at 0 (empty systems allowed, at most 2^31-1 particles in all); G is a
+ * HOST array of nsys finite constants.  Systems share no interactions.  All systems
+ * are evaluated together as one forest (one root per non-empty system, one set of
+ * launches per phase); each system's tree, lists and results are those it gets
+ * alone in fmm_evaluate with the same parameters (bit for bit).  The scale source
+ * must be FMM_SCALE_ESTIMATE (or the MAC geometric).  Returns after the stream has
+ * completed; stats (HOST, may be NULL) cover the whole forest.  Errors as for
+ * fmm_evaluate, plus FMM_E_INVALID for bad offsets or G. */
 int fmm_evaluate_batch(fmm_ctx* ctx, int nsys, const int64_t* offsets, const double* x,
                        const double* mu, const double* G, double* psi, double* acc,
                        void* stream, fmm_stats* stats);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop for many independent systems (concurrent cluster simulations)
+ * whose force requests arrive over time.  The paper has no counterpart: this is
+ * the batching and admission around its evaluation.
+ *
+ * The context runs `slots` workers, each with its own stream and workspace.  A
+ * free slot takes every queued request (in arrival order) whose summed footprints
+ * fit its share budget/slots and evaluates them as one forest
+ * (fmm_evaluate_batch), so results are bit for bit those of each system alone;
+ * slots run concurrently on the device.  Requests arriving while others run wait
+ * in the queue for the next free slot.
+ *
+ * fmm_serve_config: optional, before the first fmm_system_register (else
+ *   FMM_E_BUSY).  budget_bytes = device memory the slots' workspaces may hold
+ *   (0: 80 % of the device's free memory at the first registration); slots in
+ *   [0, 16] (0: 2).
+ * fmm_footprint_bytes: the workspace bound used for admission, for n particles
+ *   and the given parameters (NULL: defaults); -1 for invalid arguments.
+ * fmm_system_register: a system of n particles (fixed for its lifetime);
+ *   FMM_E_ADMISSION if its footprint exceeds one slot's share.  *sys_id >= 0.
+ * fmm_submit: one force request: x [n][3], mu [n] DEVICE arrays that must hold
+ *   their values when the call is made (synchronise the stream that wrote them);
+ *   psi [n], acc [n][3] DEVICE outputs, written before fmm_poll reports completion
+ *   and not to be touched until then.  G finite.  At most one request per system
+ *   in flight (else FMM_E_BUSY); unknown sys_id: FMM_E_NOTFOUND.  *ticket > 0.
+ * fmm_poll: wait up to timeout_ms (0: do not wait, < 0: no limit) for a ticket.
+ *   Returns FMM_E_BUSY if it has not completed, else the request's result code
+ *   (0 or an FMM_E_* of its evaluation); a completed ticket is retired, and
+ *   *latency_s (may be NULL) is the time from fmm_submit to completion.
+ * fmm_system_release: forget a system (FMM_E_BUSY while it has a request in flight).
+ * fmm_workspace_bytes: device bytes currently held by the context and its slots.
+ * fmm_destroy waits for the queued requests to finish before stopping the slots.
+ * The serving calls are thread-safe among themselves. */
+int fmm_serve_config(fmm_ctx* ctx, uint64_t budget_bytes, int slots);
+int64_t fmm_footprint_bytes(const fmm_params* params, int64_t n);
+int fmm_system_register(fmm_ctx* ctx, int64_t n, int* sys_id);
+int fmm_submit(fmm_ctx* ctx, int sys_id, const double* x, const double* mu, double G, double* psi,
+               double* acc, uint64_t* ticket);
+int fmm_poll(fmm_ctx* ctx, uint64_t ticket, int timeout_ms, double* latency_s);
+int fmm_system_release(fmm_ctx* ctx, int sys_id);
+uint64_t fmm_workspace_bytes(fmm_ctx* ctx);
 
 /* Copy the context's view of the last evaluation to HOST buffers, for tests:
  * cells (ncells x 5 int64: level, leaf, first, count, nchild; ncells x 6 double:

@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "--expt-relaxed-constexpr"]
 # decision quantities (keys, centres, radii) are computed without FMA contraction
 PER_FILE = {"tree.cu": ["--fmad=false"]}
-SOURCES = ["common.cu", "tree.cu", "upward.cu", "walk.cu", "interact.cu", "direct.cu", "split.cu", "peaks.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["common.cu", "tree.cu", "upward.cu", "walk.cu", "interact.cu", "direct.cu", "split.cu", "peaks.cu", "capi.cu", "noalloc.cu", "serve.cu"]
 
 
 def nvcc() -> str:
@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(_compile, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

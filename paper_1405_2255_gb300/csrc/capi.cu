@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "serve.cuh"
 
 namespace gb3 {
 extern thread_local char g_cuda_msg[256];
@@ -84,6 +85,20 @@ struct fmm_ctx {
     cudaEvent_t ev[EV_N];
     bool ev_ok = false;
     bool timed = false;  // the events of the last evaluation were recorded
+    gb3::Serve* serve = nullptr;  // the serving loop (serve.cu), created on first use
+    // ensemble of the current evaluation (nsys = 0: one system): system offsets and G
+    // on the device, roots (first, count) of the non-empty systems
+    Buf sys_off, sys_G, sys_roots, skey, skey_alt, spos, spos_alt;
+    int nsys = 0, nroots = 1;
+    std::vector<Buf*> bufs() {
+        return {&hx, &hmu, &hpsi, &hacc, &bounds, &status, &counters, &coin, &dtotal, &keys, &keys_alt, &idx,
+                &idx_alt, &rtmp, &xm, &perm, &xhi, &xlo, &first, &count, &child, &nchild, &parent, &level, &sr,
+                &cr, &mass, &minscale, &split_nchild, &split_oct, &split_offs, &scan_tmp, &leaves, &leaf_flag,
+                &leaf_pos, &rad_tmp, &M, &F, &Pw, &binom, &M1, &F1, &Ff, &front0, &front1, &m2l, &p2p,
+                &sort_tmp, &m2l_tmp, &p2p_tmp, &seg_start, &seg_end, &est_m2l, &est_p2p, &m2l_seg_start,
+                &m2l_seg_end, &psi_far, &acc_far, &psi_near, &acc_near, &scale_sorted, &sys_off, &sys_G,
+                &sys_roots, &skey, &skey_alt, &spos, &spos_alt};
+    }
     // tree shape of the last evaluation
     std::vector<int> lev_start;
     int n = 0, ncells = 0, nleaves = 0;
@@ -98,6 +113,13 @@ static int fail_cuda(fmm_ctx* ctx, int code) {
     if (ctx) snprintf(ctx->err, sizeof ctx->err, "%s", g_cuda_msg);
     return code;
 }
+
+namespace gb3 {
+Serve*& ctx_serve(fmm_ctx* ctx) { return ctx->serve; }
+const fmm_params* ctx_params(fmm_ctx* ctx) { return &ctx->prm; }
+int ctx_device(fmm_ctx* ctx) { return ctx->device; }
+int ctx_fail(fmm_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
+}  // namespace gb3
 
 #define TRY(expr)                                     \
     do {                                              \
@@ -142,6 +164,17 @@ __global__ void k_root(Cells c, int n) {
     c.child[0] = -1;
     c.nchild[0] = 0;
 }
+// one root per non-empty system of an ensemble (roots[r] = first, count)
+__global__ void k_roots(Cells c, const int2* __restrict__ roots, int nroots) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nroots; r += gridDim.x * blockDim.x) {
+        c.first[r] = roots[r].x;
+        c.count[r] = roots[r].y;
+        c.level[r] = 0;
+        c.parent[r] = -1;
+        c.child[r] = -1;
+        c.nchild[r] = 0;
+    }
+}
 __global__ void k_leaf_flags(const int* __restrict__ nchild, int nc, int* __restrict__ flag) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) flag[i] = nchild[i] == 0;
 }
@@ -159,14 +192,35 @@ static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cu
     TRY(ensure(ctx->rtmp, sizeof(int) * radix_tmp_ints(n)));
     TRY(ensure(ctx->xm, sizeof(d4) * n));
     TRY(ensure(ctx->perm, sizeof(int) * n));
-    launch_bounds(x, mu, n, P<unsigned long long>(ctx->bounds), P<unsigned>(ctx->status), s);
-    launch_keys(x, n, P<unsigned long long>(ctx->bounds), P<uint64_t>(ctx->keys), P<int>(ctx->idx), s);
-    radix_sort_pairs(P<uint64_t>(ctx->keys), P<int>(ctx->idx), P<uint64_t>(ctx->keys_alt), P<int>(ctx->idx_alt), n,
-                     P<int>(ctx->rtmp), s);
+    const int nsys = ctx->nsys;
+    if (nsys == 0) {
+        launch_bounds(x, mu, n, P<unsigned long long>(ctx->bounds), P<unsigned>(ctx->status), s);
+        launch_keys(x, n, P<unsigned long long>(ctx->bounds), P<uint64_t>(ctx->keys), P<int>(ctx->idx), s);
+        radix_sort_pairs(P<uint64_t>(ctx->keys), P<int>(ctx->idx), P<uint64_t>(ctx->keys_alt), P<int>(ctx->idx_alt),
+                         n, P<int>(ctx->rtmp), s);
+    } else {
+        // forest: per-system bounds and keys, sort by key, then (stably) by system
+        TRY(ensure(ctx->bounds, sizeof(unsigned long long) * 6 * (size_t)nsys));
+        TRY(ensure(ctx->skey, sizeof(uint64_t) * n));
+        TRY(ensure(ctx->skey_alt, sizeof(uint64_t) * n));
+        TRY(ensure(ctx->spos, sizeof(int) * n));
+        TRY(ensure(ctx->spos_alt, sizeof(int) * n));
+        const int* off = P<int>(ctx->sys_off);
+        launch_bounds_sys(x, mu, n, off, nsys, P<unsigned long long>(ctx->bounds), P<unsigned>(ctx->status), s);
+        launch_keys_sys(x, n, off, nsys, P<unsigned long long>(ctx->bounds), P<uint64_t>(ctx->keys), P<int>(ctx->idx), s);
+        radix_sort_pairs(P<uint64_t>(ctx->keys), P<int>(ctx->idx), P<uint64_t>(ctx->keys_alt), P<int>(ctx->idx_alt),
+                         n, P<int>(ctx->rtmp), s);
+        sort_by_system(P<uint64_t>(ctx->keys), P<int>(ctx->idx), n, off, nsys, P<uint64_t>(ctx->skey),
+                       P<uint64_t>(ctx->skey_alt), P<int>(ctx->spos), P<int>(ctx->spos_alt), P<int>(ctx->rtmp),
+                       P<uint64_t>(ctx->keys_alt), P<int>(ctx->idx_alt), s);
+        std::swap(ctx->keys, ctx->keys_alt);
+        std::swap(ctx->idx, ctx->idx_alt);
+    }
     launch_gather(x, mu, P<int>(ctx->idx), n, P<d4>(ctx->xm), P<int>(ctx->perm), s);
 
     // cell capacity: leaves <= n, internal cells hold > leaf particles, <= 21 levels
-    long long cap = (long long)n + 21LL * (n / (leaf + 1)) + 64;
+    const int nroots = ctx->nroots;
+    long long cap = (long long)n + 21LL * (n / (leaf + 1)) + nroots + 64;
     Buf* ib[] = {&ctx->first, &ctx->count, &ctx->child, &ctx->nchild, &ctx->parent, &ctx->level};
     for (Buf* b : ib) TRY(ensure(*b, sizeof(int) * cap));
     TRY(ensure(ctx->sr, sizeof(d4) * cap));
@@ -174,8 +228,12 @@ static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cu
     TRY(ensure(ctx->mass, sizeof(double) * cap));
     TRY(ensure(ctx->minscale, sizeof(double) * cap));
     Cells c = cells_of(ctx);
-    k_root<<<1, 1, 0, s>>>(c, n); note_launch();
-    ctx->lev_start.assign({0, 1});
+    if (nsys == 0) {
+        k_root<<<1, 1, 0, s>>>(c, n); note_launch();
+    } else {
+        k_roots<<<grid_for(nroots, 256), 256, 0, s>>>(c, P<int2>(ctx->sys_roots), nroots); note_launch();
+    }
+    ctx->lev_start.assign({0, nroots});
     for (int L = 0;; ++L) {
         int b = ctx->lev_start[L], e = ctx->lev_start[L + 1];
         int ncl = e - b;
@@ -244,10 +302,9 @@ static int run_walk(fmm_ctx* ctx, WalkParams wp, Buf& m2l, long long& m2l_cap, B
         wb.p2p = P<int2>(p2p);
         wb.p2p_cap = p2p_cap;
         wb.counters = P<unsigned long long>(ctx->counters);
-        int2 root = make_int2(0, 0);
-        CU(cudaMemcpyAsync(wb.front[0], &root, sizeof root, cudaMemcpyHostToDevice, s));
+        launch_walk_roots(wb.front[0], ctx->nroots, s);
         CU(cudaMemsetAsync(wb.counters, 0, 4 * sizeof(unsigned long long), s));
-        long long nfront = 1;
+        long long nfront = ctx->nroots;
         int cur = 0;
         bool overflow = false;
         long long need_front = 0;
@@ -478,7 +535,9 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
                         P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
-    launch_coincident(P<d4>(ctx->xm), P<uint64_t>(ctx->keys), n, P<unsigned long long>(ctx->coin), s);
+    const int* sys_off = ctx->nsys ? P<int>(ctx->sys_off) : nullptr;
+    launch_coincident(P<d4>(ctx->xm), P<uint64_t>(ctx->keys), n, P<unsigned long long>(ctx->coin), s, sys_off,
+                      ctx->nsys);
     if (timing) CU(cudaEventRecord(ctx->ev[EV_P2P], s));
 
     // A11-A12: L2L, L2P, combine and scatter
@@ -493,7 +552,8 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         launch_l2p(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->F),
                    P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
     launch_finish(P<double>(ctx->psi_far), P<double>(ctx->acc_far), P<double>(ctx->psi_near), P<double>(ctx->acc_near),
-                  P<int>(ctx->perm), n, G, psi, acc, s);
+                  P<int>(ctx->perm), n, G, psi, acc, s, sys_off, ctx->nsys ? P<double>(ctx->sys_G) : nullptr,
+                  ctx->nsys);
     if (timing) {
         CU(cudaEventRecord(ctx->ev[EV_DOWN], s));
         CU(cudaEventRecord(ctx->ev[EV_END], s));
@@ -641,27 +701,44 @@ int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, doubl
 int fmm_evaluate_batch(fmm_ctx* ctx, int nsys, const int64_t* offsets, const double* x, const double* mu,
                        const double* G, double* psi, double* acc, void* stream, fmm_stats* stats) {
     if (!ctx || nsys < 0 || (nsys > 0 && (!offsets || !G))) return FMM_E_INVALID;
-    fmm_stats tot;
-    memset(&tot, 0, sizeof tot);
-    for (int i = 0; i < nsys; ++i) {
-        int64_t a = offsets[i], b = offsets[i + 1];
-        if (b < a) return fail(ctx, FMM_E_INVALID, "offsets not increasing");
-        fmm_stats st;
-        int rc = fmm_evaluate(ctx, b - a, x + 3 * a, mu + a, G[i], nullptr, psi + a, acc + 3 * a, stream,
-                              stats ? &st : nullptr);
-        if (rc) return rc;
-        if (stats) {
-            tot.n += st.n;
-            tot.ncells += st.ncells;
-            tot.nleaves += st.nleaves;
-            tot.n_m2l += st.n_m2l;
-            tot.n_p2p += st.n_p2p;
-            tot.p2p_interactions += st.p2p_interactions;
-            tot.coincident += st.coincident;
-            tot.t_total += st.t_total;
-        }
+    if (nsys == 0) {
+        if (stats) memset(stats, 0, sizeof *stats);
+        return 0;
     }
-    if (stats) *stats = tot;
+    ctx->err[0] = 0;
+    if (offsets[0] != 0) return fail(ctx, FMM_E_INVALID, "offsets[0] must be 0");
+    for (int k = 0; k < nsys; ++k)
+        if (!std::isfinite(G[k])) return fail(ctx, FMM_E_INVALID, "G is not finite");
+    std::vector<int> off(nsys + 1);
+    std::vector<int2> roots;
+    for (int k = 0; k < nsys; ++k) {
+        if (offsets[k + 1] < offsets[k]) return fail(ctx, FMM_E_INVALID, "offsets not increasing");
+        if (offsets[k + 1] > (int64_t)INT32_MAX) return fail(ctx, FMM_E_INVALID, "more than 2^31-1 particles in all");
+        off[k] = (int)offsets[k];
+        if (offsets[k + 1] > offsets[k]) roots.push_back(make_int2((int)offsets[k], (int)(offsets[k + 1] - offsets[k])));
+    }
+    off[nsys] = (int)offsets[nsys];
+    const int n = off[nsys];
+    if (nsys == 1) return fmm_evaluate(ctx, n, x, mu, G[0], nullptr, psi, acc, stream, stats);
+    if (n > 0 && (!x || !mu || !psi || !acc)) return fail(ctx, FMM_E_INVALID, "null array");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, FMM_E_CUDA, "cudaSetDevice failed");
+    TRY(ensure(ctx->sys_off, sizeof(int) * (nsys + 1)));
+    TRY(ensure(ctx->sys_G, sizeof(double) * nsys));
+    TRY(ensure(ctx->sys_roots, sizeof(int2) * std::max<size_t>(1, roots.size())));
+    CU(cudaMemcpyAsync(ctx->sys_off.p, off.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(ctx->sys_G.p, G, sizeof(double) * nsys, cudaMemcpyHostToDevice, s));
+    if (!roots.empty())
+        CU(cudaMemcpyAsync(ctx->sys_roots.p, roots.data(), sizeof(int2) * roots.size(), cudaMemcpyHostToDevice, s));
+    // the host arrays above are pageable and local: wait for the copies before returning
+    ctx->nsys = nsys;
+    ctx->nroots = (int)roots.size();
+    int rc = evaluate_device(ctx, n, x, mu, 1.0, nullptr, psi, acc, s, stats);
+    cudaError_t e = cudaStreamSynchronize(s);
+    ctx->nsys = 0;
+    ctx->nroots = 1;
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(ctx, FMM_E_CUDA, cudaGetErrorString(e));
     return 0;
 }
 
@@ -734,19 +811,53 @@ int fmm_alu_peaks(double* fp64_tflops, double* fp32_tflops) {
     return alu_peaks(fp64_tflops, fp32_tflops);
 }
 
+uint64_t fmm_workspace_bytes(fmm_ctx* ctx) {
+    if (!ctx) return 0;
+    uint64_t b = 0;
+    for (Buf* x : ctx->bufs()) b += x->bytes;
+    return b + serve_workspace_bytes(ctx->serve);
+}
+
+// Workspace bound for n particles.  The particle and cell arrays follow from the
+// allocation sizes (with the 25 % growth of every buffer); the interaction lists,
+// their sort scratch and the M2L partial sums depend on the input and on (p, eps,
+// leaf), so they are bounded per cell with allowances measured on truncated Plummer
+// spheres and gamma = 1.5 cusps from 2e3 to 1e6 particles over p = 4..16,
+// eps = 1e-4..1e-9, leaf = 8..64 (cells <= 4.7 n / leaf; per cell at most ~160 M2L,
+// ~490 P2P, ~13 estimate-M2L and ~41 estimate-P2P pairs), with a margin.
+constexpr double kCellsPerLeafN = 4.7;      // cells built <= this * n / leaf + 64
+constexpr double kM2LPerCell = 200.0;       // main M2L pairs per cell
+constexpr double kP2PPerCell = 600.0;       // main P2P pairs per cell
+constexpr double kEstPerCell = 64.0;        // estimate M2L + P2P pairs per cell
+constexpr double kPairBytes = 50.0;         // list entry with growth slack + sort scratch
+
+int64_t fmm_footprint_bytes(const fmm_params* prm, int64_t n) {
+    fmm_params d;
+    if (!prm) {
+        fmm_default_params(&d);
+        prm = &d;
+    }
+    if (n < 0 || check_params(prm)) return -1;
+    const double leaf = prm->leaf_size, P = (prm->p + 1.0) * (prm->p + 1.0), nd = (double)n;
+    // particle arrays (sorted copies, keys, two-float positions, near/far results,
+    // ensemble sort keys, a serving slot's staging)
+    const double particles = 1.25 * 264.0 * nd;
+    // cell arrays sized by the cell capacity n + 21 n / (leaf + 1)
+    const double cap = nd + 21.0 * std::floor(nd / (leaf + 1.0)) + 64.0;
+    const double cellcap = 1.25 * 104.0 * cap;
+    // per cell built: M, F, their FP32/FP64 split copies and M2L scratch, power,
+    // the low-order estimate and per-cell scratch; then the lists
+    const double cells = kCellsPerLeafN * nd / leaf + 64.0;
+    const double per_cell = 1.25 * 48.0 * P + 2000.0 + kM2LPerCell * (kPairBytes + 1.25 * 8.0 * P / 32.0) +
+                            (kP2PPerCell + kEstPerCell) * kPairBytes;
+    return (int64_t)(particles + cellcap + per_cell * cells) + (int64_t)(16 << 20);
+}
+
 int fmm_destroy(fmm_ctx* ctx) {
     if (!ctx) return 0;
     cudaSetDevice(ctx->device);
-    Buf* all[] = {&ctx->hx, &ctx->hmu, &ctx->hpsi, &ctx->hacc, &ctx->bounds, &ctx->status, &ctx->counters, &ctx->coin,
-                  &ctx->dtotal, &ctx->keys, &ctx->keys_alt, &ctx->idx, &ctx->idx_alt, &ctx->rtmp, &ctx->xm, &ctx->perm,
-                  &ctx->xhi, &ctx->xlo, &ctx->first, &ctx->count, &ctx->child, &ctx->nchild, &ctx->parent, &ctx->level,
-                  &ctx->sr, &ctx->cr, &ctx->mass, &ctx->minscale, &ctx->split_nchild, &ctx->split_oct,
-                  &ctx->split_offs, &ctx->scan_tmp, &ctx->leaves, &ctx->leaf_flag, &ctx->leaf_pos, &ctx->rad_tmp,
-                  &ctx->M, &ctx->F, &ctx->Pw, &ctx->binom, &ctx->M1, &ctx->F1, &ctx->Ff, &ctx->front0, &ctx->front1,
-                  &ctx->m2l, &ctx->p2p, &ctx->sort_tmp, &ctx->m2l_tmp, &ctx->p2p_tmp, &ctx->seg_start, &ctx->seg_end, &ctx->est_m2l, &ctx->est_p2p,
-                  &ctx->m2l_seg_start, &ctx->m2l_seg_end, &ctx->psi_far, &ctx->acc_far, &ctx->psi_near,
-                  &ctx->acc_near, &ctx->scale_sorted};
-    for (Buf* b : all) release(*b);
+    if (ctx->serve) serve_destroy(ctx->serve);
+    for (Buf* b : ctx->bufs()) release(*b);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     if (ctx->h_int) cudaFreeHost(ctx->h_int);
     if (ctx->ev_ok)

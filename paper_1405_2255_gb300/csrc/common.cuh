@@ -5,9 +5,28 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "../../include/gb3fmm.h"
 
 namespace gb3 {
+
+// Run an initialisation (an upload of __constant__ tables, which every device holds
+// separately) once per device, safely from several host threads.
+struct DeviceOnce {
+    std::mutex m;
+    unsigned long long done = 0;
+};
+template <class F>
+inline void once_per_device(DeviceOnce& o, F&& init) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(o.m);
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (o.done & bit) return;
+    init();
+    o.done |= bit;
+}
 
 constexpr int kMaxP = 20;        // largest expansion order supported (p <= 20, Sec. 6.1)
 constexpr int kMaxLevel = 21;    // 21 bits per axis in a 63-bit Morton key

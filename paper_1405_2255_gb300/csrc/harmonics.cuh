@@ -17,19 +17,19 @@ struct RecTables {
 // launches kernels using the recurrences calls init_rec_tables() first
 static __constant__ RecTables c_rec;
 static inline void init_rec_tables() {
-    static bool done = false;
-    if (done) return;
-    RecTables t;
-    memset(&t, 0, sizeof t);
-    for (int n = 0; n <= kMaxP + 1; ++n) t.tw[n] = 2.0 * n - 1.0;
-    for (int n = 0; n <= kMaxP; ++n)
-        for (int m = 0; m <= kMaxP; ++m) {
-            t.inv_up[n][m] = (n * n != m * m) ? 1.0 / (double)(n * n - m * m) : 0.0;
-            t.th_b[n][m] = (double)((n - 1) * (n - 1) - m * m);
-        }
-    for (int j = 1; j <= kMaxP; ++j) t.inv_2j[j] = 1.0 / (2.0 * j);
-    cudaMemcpyToSymbol(c_rec, &t, sizeof t);
-    done = true;
+    static DeviceOnce once;
+    once_per_device(once, [] {
+        RecTables t;
+        memset(&t, 0, sizeof t);
+        for (int n = 0; n <= kMaxP + 1; ++n) t.tw[n] = 2.0 * n - 1.0;
+        for (int n = 0; n <= kMaxP; ++n)
+            for (int m = 0; m <= kMaxP; ++m) {
+                t.inv_up[n][m] = (n * n != m * m) ? 1.0 / (double)(n * n - m * m) : 0.0;
+                t.th_b[n][m] = (double)((n - 1) * (n - 1) - m * m);
+            }
+        for (int j = 1; j <= kMaxP; ++j) t.inv_2j[j] = 1.0 / (2.0 * j);
+        cudaMemcpyToSymbol(c_rec, &t, sizeof t);
+    });
 }
 
 // One column m >= 0 of the regular harmonics Upsilon_n^m(r), n = m..p, written to

@@ -194,30 +194,30 @@ static __constant__ unsigned char c_idx_n[(kMaxP + 1) * (kMaxP + 1)];
 static __constant__ float c_twf[kMaxP + 2], c_thbf[kMaxP + 1][kMaxP + 1];
 
 static void init_split_tables() {
-    static bool done = false;
-    if (done) return;
-    TermTab t;
-    int q = 0;
-    for (int n = 0; n <= kJ64; ++n)
-        for (int m = 0; m <= n; ++m)
-            for (int k = 0; k + n <= kJ64; ++k)
-                for (int l = -k; l <= k; ++l) {
-                    t.n[q] = (unsigned char)n; t.m[q] = (unsigned char)m; t.k[q] = (unsigned char)k;
-                    t.l[q] = (signed char)l; t.out[q] = (unsigned char)(n * (n + 1) / 2 + m);
-                    ++q;
-                }
-    cudaMemcpyToSymbol(c_terms, &t, sizeof t);
-    unsigned char idx[(kMaxP + 1) * (kMaxP + 1)];
-    for (int n = 0; n <= kMaxP; ++n)
-        for (int m = -n; m <= n; ++m) idx[cix(n, m)] = (unsigned char)n;
-    cudaMemcpyToSymbol(c_idx_n, idx, sizeof idx);
-    float tw[kMaxP + 2], tb[kMaxP + 1][kMaxP + 1];
-    for (int n = 0; n <= kMaxP + 1; ++n) tw[n] = (float)(2 * n - 1);
-    for (int n = 0; n <= kMaxP; ++n)
-        for (int m = 0; m <= kMaxP; ++m) tb[n][m] = (float)((n - 1) * (n - 1) - m * m);
-    cudaMemcpyToSymbol(c_twf, tw, sizeof tw);
-    cudaMemcpyToSymbol(c_thbf, tb, sizeof tb);
-    done = true;
+    static DeviceOnce once;
+    once_per_device(once, [] {
+        TermTab t;
+        int q = 0;
+        for (int n = 0; n <= kJ64; ++n)
+            for (int m = 0; m <= n; ++m)
+                for (int k = 0; k + n <= kJ64; ++k)
+                    for (int l = -k; l <= k; ++l) {
+                        t.n[q] = (unsigned char)n; t.m[q] = (unsigned char)m; t.k[q] = (unsigned char)k;
+                        t.l[q] = (signed char)l; t.out[q] = (unsigned char)(n * (n + 1) / 2 + m);
+                        ++q;
+                    }
+        cudaMemcpyToSymbol(c_terms, &t, sizeof t);
+        unsigned char idx[(kMaxP + 1) * (kMaxP + 1)];
+        for (int n = 0; n <= kMaxP; ++n)
+            for (int m = -n; m <= n; ++m) idx[cix(n, m)] = (unsigned char)n;
+        cudaMemcpyToSymbol(c_idx_n, idx, sizeof idx);
+        float tw[kMaxP + 2], tb[kMaxP + 1][kMaxP + 1];
+        for (int n = 0; n <= kMaxP + 1; ++n) tw[n] = (float)(2 * n - 1);
+        for (int n = 0; n <= kMaxP; ++n)
+            for (int m = 0; m <= kMaxP; ++m) tb[n][m] = (float)((n - 1) * (n - 1) - m * m);
+        cudaMemcpyToSymbol(c_twf, tw, sizeof tw);
+        cudaMemcpyToSymbol(c_thbf, tb, sizeof tb);
+    });
 }
 
 
@@ -935,11 +935,21 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __re
 // number of ordered pairs (a != b) at distance 0: equal positions have equal keys,
 // so they sit next to each other in key order inside one leaf
 __global__ void k_coincident(const d4* __restrict__ xm, const uint64_t* __restrict__ keys, int n,
-                             unsigned long long* coincident) {
+                             unsigned long long* coincident, const int* __restrict__ off, int nsys) {
     unsigned long long cnt = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const d4 p = xm[i];
-        for (int j = i - 1; j >= 0 && keys[j] == keys[i]; --j) {
+        int j0 = 0;  // first particle of i's system (systems keep their blocks when sorted)
+        if (off) {
+            int lo = 0, hi = nsys - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (off[mid] <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            j0 = off[lo];
+        }
+        for (int j = i - 1; j >= j0 && keys[j] == keys[i]; --j) {
             const d4 q = xm[j];
             cnt += (q.x == p.x && q.y == p.y && q.z == p.z) ? 2 : 0;
         }
@@ -948,9 +958,10 @@ __global__ void k_coincident(const d4* __restrict__ xm, const uint64_t* __restri
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(coincident, cnt);
 }
 
-void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s) {
+void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s,
+                       const int* off, int nsys) {
     if (n > 1) {
-        k_coincident<<<grid_for(n, 256), 256, 0, s>>>(xm, keys, n, coincident);
+        k_coincident<<<grid_for(n, 256), 256, 0, s>>>(xm, keys, n, coincident, off, nsys);
         note_launch();
     }
 }
@@ -1107,17 +1118,31 @@ void launch_norm_scale(const double* /*psi_far*/, const double* acc_far, const d
 // ---------------------------------------------------------------- finish (A12)
 __global__ void k_finish(const double* __restrict__ pf, const double* __restrict__ af, const double* __restrict__ pn,
                          const double* __restrict__ an, const int* __restrict__ perm, int n, double G,
-                         double* __restrict__ psi, double* __restrict__ acc) {
+                         double* __restrict__ psi, double* __restrict__ acc, const int* __restrict__ off,
+                         const double* __restrict__ Gsys, int nsys) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int o = perm[i];
+        if (Gsys) {  // the system of sorted particle i (systems keep their blocks when sorted)
+            int lo = 0, hi = nsys - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (off[mid] <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            G = Gsys[lo];
+        }
         psi[o] = G * (pf[i] + pn[i]);
 #pragma unroll
         for (int d = 0; d < 3; ++d) acc[3 * (size_t)o + d] = G * (af[3 * (size_t)i + d] + an[3 * (size_t)i + d]);
     }
 }
 void launch_finish(const double* psi_far, const double* acc_far, const double* psi_near, const double* acc_near,
-                   const int* perm, int n, double G, double* psi, double* acc, cudaStream_t s) {
-    if (n > 0) k_finish<<<grid_for(n, 256), 256, 0, s>>>(psi_far, acc_far, psi_near, acc_near, perm, n, G, psi, acc); note_launch();
+                   const int* perm, int n, double G, double* psi, double* acc, cudaStream_t s, const int* off,
+                   const double* Gsys, int nsys) {
+    if (n > 0)
+        k_finish<<<grid_for(n, 256), 256, 0, s>>>(psi_far, acc_far, psi_near, acc_near, perm, n, G, psi, acc, off,
+                                                  Gsys, nsys);
+    note_launch();
 }
 
 }  // namespace gb3

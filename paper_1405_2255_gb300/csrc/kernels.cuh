@@ -42,6 +42,17 @@ void radix_sort_pairs(uint64_t* keys, int* idx, uint64_t* keys_alt, int* idx_alt
                       cudaStream_t s);
 void launch_gather(const double* x, const double* mu, const int* idx, int n, d4* xm, int* perm,
                    cudaStream_t s);
+// A1-A2 for an ensemble of nsys systems, system k = caller particles [off[k], off[k+1])
+// (off on the device): per-system bounds (bounds[6k..6k+5]) and keys in the system's
+// own root cube; then a stable sort of the key-sorted (keys, idx) by system into
+// (keys_out, idx_out), so that each system keeps its block and its key order.
+void launch_bounds_sys(const double* x, const double* mu, int n, const int* off, int nsys,
+                       unsigned long long* bounds, unsigned* status, cudaStream_t s);
+void launch_keys_sys(const double* x, int n, const int* off, int nsys, const unsigned long long* bounds,
+                     uint64_t* keys, int* idx, cudaStream_t s);
+int sort_by_system(const uint64_t* keys, const int* idx, int n, const int* off, int nsys, uint64_t* skey,
+                   uint64_t* skey_alt, int* pos, int* pos_alt, int* tmp, uint64_t* keys_out, int* idx_out,
+                   cudaStream_t s);
 // A3: one level of the top-down build.  Cells [lev_begin, lev_end) are split;
 // nchild_tmp/oct_tmp are scratch of the level's size.  Daughters are appended at
 // lev_end; *d_total receives their number.
@@ -91,6 +102,8 @@ struct WalkBuffers {
     long long p2p_cap;
     unsigned long long* counters;  // [0] next frontier, [1] m2l, [2] p2p, [3] overflow flag
 };
+// the first frontier: (r, r) for the roots r = 0 .. nroots-1
+void launch_walk_roots(int2* front, int nroots, cudaStream_t s);
 void launch_walk_step(Cells c, WalkParams wp, const int2* front_in, long long nfront, int2* front_out,
                       WalkBuffers wb, cudaStream_t s);
 // sort a pair list by (sink, source), then mark per-sink segments [seg_start, seg_end)
@@ -128,8 +141,10 @@ size_t p2p_tmp_bytes(int nleaves);
 void launch_p2p_mixed(const d4* xm, const float4* xhi, const float4* xlo, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves,
                       double* psi, double* acc, bool two_float, void* tmp, cudaStream_t s);
-// ordered pairs of distinct particles at distance 0 (sorted keys and positions)
-void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s);
+// ordered pairs of distinct particles at distance 0 (sorted keys and positions); with
+// an ensemble (off != nullptr) only pairs inside one system count
+void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s,
+                       const int* off = nullptr, int nsys = 0);
 void launch_split_positions(const d4* xm, int n, float4* xhi, float4* xlo, cudaStream_t s);
 // low-order f estimate (p = 0, 1/r^2 kernel): M2L, pass-down, P2P, evaluation
 void launch_f_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* Ff,
@@ -141,9 +156,10 @@ void launch_f_p2p(const d4* xm, Cells c, const int2* list, const int* seg_start,
 void launch_norm_scale(const double* psi_far, const double* acc_far, const double* acc_near, int n,
                        double* scale, cudaStream_t s);
 // combine far + near, multiply by G and scatter to the caller's order (A12)
+// (ensemble: Gsys[k] for the caller particles [off[k], off[k+1]) instead of G)
 void launch_finish(const double* psi_far, const double* acc_far, const double* psi_near,
                    const double* acc_near, const int* perm, int n, double G, double* psi, double* acc,
-                   cudaStream_t s);
+                   cudaStream_t s, const int* off = nullptr, const double* Gsys = nullptr, int nsys = 0);
 
 // ---------------------------------------------------------------- peaks (peaks.cu)
 int alu_peaks(double* fp64_tflops, double* fp32_tflops);

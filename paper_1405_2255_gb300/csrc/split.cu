@@ -14,18 +14,18 @@ static __constant__ float c_twf2[kMaxP + 2];                // 2n - 1
 static __constant__ float c_inv2jf[kMaxP + 1];              // 1 / (2j)
 
 static void init_split_up_tables() {
-    static bool done = false;
-    if (done) return;
-    float a[kMaxP + 1][kMaxP + 1], b[kMaxP + 2], c[kMaxP + 1];
-    for (int n = 0; n <= kMaxP; ++n)
-        for (int m = 0; m <= kMaxP; ++m) a[n][m] = (n * n != m * m) ? 1.0f / (float)(n * n - m * m) : 0.f;
-    for (int n = 0; n <= kMaxP + 1; ++n) b[n] = (float)(2 * n - 1);
-    c[0] = 0.f;
-    for (int j = 1; j <= kMaxP; ++j) c[j] = 1.0f / (2.0f * j);
-    cudaMemcpyToSymbol(c_inv_upf, a, sizeof a);
-    cudaMemcpyToSymbol(c_twf2, b, sizeof b);
-    cudaMemcpyToSymbol(c_inv2jf, c, sizeof c);
-    done = true;
+    static DeviceOnce once;
+    once_per_device(once, [] {
+        float a[kMaxP + 1][kMaxP + 1], b[kMaxP + 2], c[kMaxP + 1];
+        for (int n = 0; n <= kMaxP; ++n)
+            for (int m = 0; m <= kMaxP; ++m) a[n][m] = (n * n != m * m) ? 1.0f / (float)(n * n - m * m) : 0.f;
+        for (int n = 0; n <= kMaxP + 1; ++n) b[n] = (float)(2 * n - 1);
+        c[0] = 0.f;
+        for (int j = 1; j <= kMaxP; ++j) c[j] = 1.0f / (2.0f * j);
+        cudaMemcpyToSymbol(c_inv_upf, a, sizeof a);
+        cudaMemcpyToSymbol(c_twf2, b, sizeof b);
+        cudaMemcpyToSymbol(c_inv2jf, c, sizeof c);
+    });
 }
 
 __device__ inline float warp_sumf(float v) {

@@ -76,23 +76,28 @@ __device__ inline void root_cube(const unsigned long long* bounds, double lo[3],
     if (!(side > 0)) side = 1.0;
 }
 
+// 21 bits per axis of (x - lo) / side, interleaved x-major
+__device__ inline uint64_t morton_key(const double* __restrict__ xi, const double lo[3], double side) {
+    uint32_t q[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double t = (xi[d] - lo[d]) / side;
+        double u = t * 2097152.0;
+        double f = floor(u);
+        long long v = (long long)f;
+        if (v < 0) v = 0;
+        if (v > 2097151) v = 2097151;
+        q[d] = (uint32_t)v;
+    }
+    return (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+}
+
 __global__ void k_keys(const double* __restrict__ x, int n, const unsigned long long* __restrict__ bounds,
                        uint64_t* __restrict__ keys, int* __restrict__ idx) {
     double lo[3], side;
     root_cube(bounds, lo, side);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t q[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            double t = (x[3 * (long long)i + d] - lo[d]) / side;
-            double u = t * 2097152.0;
-            double f = floor(u);
-            long long v = (long long)f;
-            if (v < 0) v = 0;
-            if (v > 2097151) v = 2097151;
-            q[d] = (uint32_t)v;
-        }
-        keys[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+        keys[i] = morton_key(x + 3 * (long long)i, lo, side);
         idx[i] = i;
     }
 }
@@ -100,6 +105,115 @@ __global__ void k_keys(const double* __restrict__ x, int n, const unsigned long 
 void launch_keys(const double* x, int n, const unsigned long long* bounds, uint64_t* keys, int* idx,
                  cudaStream_t s) {
     if (n > 0) k_keys<<<grid_for(n, 256), 256, 0, s>>>(x, n, bounds, keys, idx); note_launch();
+}
+
+// ------------------------------------------------------------------ A1-A2 for an ensemble
+// An ensemble of independent systems (contiguous particle ranges off[k] .. off[k+1]
+// of the caller's arrays) is built as a forest: every system gets the bounding box,
+// root cube and keys it would get alone, and its particles stay in their own block
+// after sorting, so each tree is exactly the tree of the system alone.
+__device__ inline int system_of(const int* __restrict__ off, int nsys, int i) {
+    int lo = 0, hi = nsys - 1;  // last k with off[k] <= i
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_bounds_init_sys(unsigned long long* b, int nsys) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 6 * nsys; i += gridDim.x * blockDim.x)
+        b[i] = (i % 6) < 3 ? ~0ull : 0ull;
+}
+
+__global__ void k_bounds_sys(const double* __restrict__ x, const double* __restrict__ mu, int n,
+                             const int* __restrict__ off, int nsys, unsigned long long* bounds, unsigned* status) {
+    const int lane = threadIdx.x & 31;
+    for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        int k = -1;
+        bool bad = false;
+        if (i < n) {
+            k = system_of(off, nsys, i);
+            double v[3] = {x[3 * (long long)i], x[3 * (long long)i + 1], x[3 * (long long)i + 2]};
+            double m = mu[i];
+            bad = !(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(m) && m >= 0.0);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) lo[d] = hi[d] = v[d];
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStatInvalid);
+        const int k0 = __shfl_sync(0xffffffffu, k, 0);
+        if (__all_sync(0xffffffffu, k == k0)) {  // the whole warp in one system: reduce first
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = warp_min(lo[d]);
+                hi[d] = warp_max(hi[d]);
+            }
+            if (lane == 0 && k0 >= 0)
+                for (int d = 0; d < 3; ++d) {
+                    atomicMin(&bounds[6 * k0 + d], dbl_key(lo[d]));
+                    atomicMax(&bounds[6 * k0 + 3 + d], dbl_key(hi[d]));
+                }
+        } else if (k >= 0) {
+            for (int d = 0; d < 3; ++d) {
+                atomicMin(&bounds[6 * k + d], dbl_key(lo[d]));
+                atomicMax(&bounds[6 * k + 3 + d], dbl_key(hi[d]));
+            }
+        }
+    }
+}
+
+void launch_bounds_sys(const double* x, const double* mu, int n, const int* off, int nsys,
+                       unsigned long long* bounds, unsigned* status, cudaStream_t s) {
+    k_bounds_init_sys<<<grid_for(6LL * nsys, 256), 256, 0, s>>>(bounds, nsys); note_launch();
+    if (n > 0) k_bounds_sys<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, mu, n, off, nsys, bounds, status); note_launch();
+}
+
+__global__ void k_keys_sys(const double* __restrict__ x, int n, const int* __restrict__ off, int nsys,
+                           const unsigned long long* __restrict__ bounds, uint64_t* __restrict__ keys,
+                           int* __restrict__ idx) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double lo[3], side;
+        root_cube(bounds + 6 * system_of(off, nsys, i), lo, side);
+        keys[i] = morton_key(x + 3 * (long long)i, lo, side);
+        idx[i] = i;
+    }
+}
+
+void launch_keys_sys(const double* x, int n, const int* off, int nsys, const unsigned long long* bounds,
+                     uint64_t* keys, int* idx, cudaStream_t s) {
+    if (n > 0) k_keys_sys<<<grid_for(n, 256), 256, 0, s>>>(x, n, off, nsys, bounds, keys, idx); note_launch();
+}
+
+// second stage of the ensemble sort: a stable sort of the key-sorted items by system
+__global__ void k_system_keys(const int* __restrict__ idx, int n, const int* __restrict__ off, int nsys,
+                              uint64_t* __restrict__ skey, int* __restrict__ pos) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        skey[i] = (uint64_t)system_of(off, nsys, idx[i]);
+        pos[i] = i;
+    }
+}
+__global__ void k_take(const uint64_t* __restrict__ kin, const int* __restrict__ vin, const int* __restrict__ pos,
+                       int n, uint64_t* __restrict__ kout, int* __restrict__ vout) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int j = pos[i];
+        kout[i] = kin[j];
+        vout[i] = vin[j];
+    }
+}
+
+int sort_by_system(const uint64_t* keys, const int* idx, int n, const int* off, int nsys, uint64_t* skey,
+                   uint64_t* skey_alt, int* pos, int* pos_alt, int* tmp, uint64_t* keys_out, int* idx_out,
+                   cudaStream_t s) {
+    if (n <= 0) return 0;
+    int bits = 8;
+    while (bits < 32 && (1LL << bits) < nsys) bits += 8;
+    k_system_keys<<<grid_for(n, 256), 256, 0, s>>>(idx, n, off, nsys, skey, pos); note_launch();
+    const int flip = radix_sort_pairs_bits(skey, pos, skey_alt, pos_alt, n, tmp, 0, bits, s);
+    k_take<<<grid_for(n, 256), 256, 0, s>>>(keys, idx, flip ? pos_alt : pos, n, keys_out, idx_out); note_launch();
+    return 0;
 }
 
 // ------------------------------------------------------------------ A2 radix sort

@@ -182,14 +182,13 @@ __global__ void k_power(const double* __restrict__ M, int ncells, int p, double*
 }
 
 void launch_power(const double* M, int ncells, int p, double* P, cudaStream_t s) {
-    static bool init = false;
-    if (!init) {
+    static DeviceOnce once;
+    once_per_device(once, [] {
         double f[41];
         f[0] = 1;
         for (int i = 1; i <= 40; ++i) f[i] = f[i - 1] * i;
         cudaMemcpyToSymbol(c_fact, f, sizeof f);
-        init = true;
-    }
+    });
     if (ncells > 0) k_power<<<(ncells + 127) / 128, 128, 0, s>>>(M, ncells, p, P); note_launch();
 }
 

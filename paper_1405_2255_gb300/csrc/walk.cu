@@ -111,6 +111,13 @@ __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in
     }
 }
 
+__global__ void k_walk_roots(int2* front, int nroots) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nroots; r += gridDim.x * blockDim.x) front[r] = make_int2(r, r);
+}
+void launch_walk_roots(int2* front, int nroots, cudaStream_t s) {
+    if (nroots > 0) k_walk_roots<<<grid_for(nroots, 256), 256, 0, s>>>(front, nroots); note_launch();
+}
+
 void launch_walk_step(Cells c, WalkParams wp, const int2* front_in, long long nfront, int2* front_out,
                       WalkBuffers wb, cudaStream_t s) {
     if (nfront <= 0) return;

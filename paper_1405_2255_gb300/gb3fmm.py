@@ -47,7 +47,9 @@ class fmm_stats(C.Structure):
 # every symbol include/gb3fmm.h declares
 EXPORTS = ["fmm_default_params", "fmm_create", "fmm_set_params", "fmm_evaluate", "fmm_evaluate_host",
            "fmm_direct", "fmm_evaluate_batch", "fmm_debug_dump", "fmm_last_stats", "fmm_destroy",
-           "fmm_strerror", "fmm_last_error", "fmm_version", "fmm_alu_peaks", "fmm_evaluate_noalloc"]
+           "fmm_strerror", "fmm_last_error", "fmm_version", "fmm_alu_peaks", "fmm_evaluate_noalloc",
+           "fmm_serve_config", "fmm_footprint_bytes", "fmm_system_register", "fmm_submit", "fmm_poll",
+           "fmm_system_release", "fmm_workspace_bytes"]
 
 _lib = None
 
@@ -80,8 +82,18 @@ def load(path: str = LIB_PATH):
     L.fmm_evaluate_noalloc.argtypes = [i64, vp, vp, dbl, C.POINTER(fmm_params), vp, vp, vp, C.c_char_p, ci]
     L.fmm_version.argtypes = []
     L.fmm_version.restype = C.c_char_p
+    L.fmm_serve_config.argtypes = [vp, C.c_uint64, ci]
+    L.fmm_footprint_bytes.argtypes = [C.POINTER(fmm_params), i64]
+    L.fmm_footprint_bytes.restype = i64
+    L.fmm_system_register.argtypes = [vp, i64, C.POINTER(ci)]
+    L.fmm_submit.argtypes = [vp, ci, vp, vp, dbl, vp, vp, C.POINTER(C.c_uint64)]
+    L.fmm_poll.argtypes = [vp, C.c_uint64, ci, C.POINTER(C.c_double)]
+    L.fmm_system_release.argtypes = [vp, ci]
+    L.fmm_workspace_bytes.argtypes = [vp]
+    L.fmm_workspace_bytes.restype = C.c_uint64
     for name in EXPORTS:
-        if name not in ("fmm_strerror", "fmm_last_error", "fmm_version", "fmm_default_params"):
+        if name not in ("fmm_strerror", "fmm_last_error", "fmm_version", "fmm_default_params",
+                        "fmm_footprint_bytes", "fmm_workspace_bytes"):
             getattr(L, name).restype = ci
     _lib = L
     return L
@@ -207,6 +219,39 @@ class Context:
                                          C.byref(st) if st is not None else None), self.h)
         return (psi, acc, st.as_dict()) if stats else (psi, acc)
 
+    # ---- serving: continuous batching of requests from many systems
+    def fmm_serve_config(self, budget_bytes: int = 0, slots: int = 0):
+        _check(self.L.fmm_serve_config(self.h, int(budget_bytes), int(slots)), self.h)
+
+    def fmm_system_register(self, n: int) -> int:
+        sid = C.c_int()
+        _check(self.L.fmm_system_register(self.h, int(n), C.byref(sid)), self.h)
+        return sid.value
+
+    def fmm_submit(self, sys_id: int, x, mu, G, psi, acc) -> int:
+        """Queue one force request (device tensors; x and mu must be ready, psi/acc
+        are written before fmm_poll reports completion)."""
+        t = C.c_uint64()
+        _check(self.L.fmm_submit(self.h, int(sys_id), _ptr(x), _ptr(mu), float(G), _ptr(psi), _ptr(acc),
+                                 C.byref(t)), self.h)
+        return t.value
+
+    def fmm_poll(self, ticket: int, timeout_ms: int = -1):
+        """None while the request runs (after timeout_ms), else its latency in seconds;
+        raises FMMError if its evaluation failed."""
+        lat = C.c_double()
+        rc = self.L.fmm_poll(self.h, int(ticket), int(timeout_ms), C.byref(lat))
+        if rc == FMM_E_BUSY:
+            return None
+        _check(rc, self.h)
+        return lat.value
+
+    def fmm_system_release(self, sys_id: int):
+        _check(self.L.fmm_system_release(self.h, int(sys_id)), self.h)
+
+    def fmm_workspace_bytes(self) -> int:
+        return int(self.L.fmm_workspace_bytes(self.h))
+
     def fmm_last_stats(self) -> dict:
         st = fmm_stats()
         _check(self.L.fmm_last_stats(self.h, C.byref(st)), self.h)
@@ -248,6 +293,15 @@ def fmm_evaluate_noalloc(x, mu, G=1.0, params: fmm_params | None = None, psi=Non
     if rc != 0:
         raise FMMError(rc, f"{L.fmm_strerror(rc).decode()}: {err.value.decode()}")
     return psi, acc
+
+
+def fmm_footprint_bytes(n: int, params: fmm_params | None = None, **kw) -> int:
+    """The serving loop's workspace bound for a system of n particles."""
+    if params is None:
+        params = fmm_default_params()
+    for k, v in kw.items():
+        setattr(params, k, v)
+    return int(load().fmm_footprint_bytes(C.byref(params), int(n)))
 
 
 def fmm_alu_peaks() -> tuple[float, float]:

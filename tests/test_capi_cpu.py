@@ -57,3 +57,14 @@ def test_create_rejects_bad_params(lib):
     p = gb3fmm.fmm_default_params()
     p.eps = -1.0
     assert lib.fmm_create(ctypes.byref(h), ctypes.byref(p), 0) == gb3fmm.FMM_E_INVALID
+
+
+def test_footprint_is_host_only_and_monotone(lib):
+    from paper_1405_2255_gb300 import gb3fmm
+    fp = [gb3fmm.fmm_footprint_bytes(n) for n in (0, 1, 1000, 10**5, 10**6, 10**7)]
+    assert all(b > a for a, b in zip(fp, fp[1:]))
+    # larger expansions and smaller leaves need more room per particle
+    assert gb3fmm.fmm_footprint_bytes(10**6, p=12) > gb3fmm.fmm_footprint_bytes(10**6, p=8)
+    assert gb3fmm.fmm_footprint_bytes(10**6, leaf_size=16) > gb3fmm.fmm_footprint_bytes(10**6, leaf_size=64)
+    assert gb3fmm.fmm_footprint_bytes(-1) == -1
+    assert gb3fmm.fmm_footprint_bytes(10, p=0) == -1

@@ -189,17 +189,84 @@ def test_host_entry_matches_device_entry(g):
     ctx.close()
 
 
-def test_batch_equals_alone(g):
-    systems = inputs.ensemble(6, inputs.BASE_SEED + 4)
+def _ensemble_with_gaps(nsys, seed):
+    systems = inputs.ensemble(nsys, seed)
+    # an empty system and a one-particle system among them
+    systems.insert(1, (np.zeros((0, 3)), np.zeros(0)))
+    x1, m1 = inputs.plummer(1, seed + 17)
+    systems.insert(3, (x1, m1))
+    return systems
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_equals_alone(g, prec):
+    """The ensemble is evaluated as one forest; every system's result is bit for bit
+    the one it gets alone (same tree, same lists in the same order, same kernels)."""
+    systems = _ensemble_with_gaps(6, inputs.BASE_SEED + 4)
     xs = np.concatenate([s[0] for s in systems])
     ms = np.concatenate([s[1] for s in systems])
     off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
-    ctx = g.Context(p=6, eps=1e-6, precision=g.FMM_PREC_FP64)
-    psi, acc = ctx.fmm_evaluate_batch(off, _dev(xs), _dev(ms), np.ones(len(systems)))
+    Gs = 0.5 + np.arange(len(systems))
+    p = g.FMM_PREC_FP64 if prec == "fp64" else g.FMM_PREC_MIXED
+    ctx = g.Context(p=6, eps=1e-6, leaf_size=32, p2p_c=2.0, precision=p)
+    psi, acc, st = ctx.fmm_evaluate_batch(off, _dev(xs), _dev(ms), Gs, stats=True)
+    psi, acc = psi.cpu().numpy(), acc.cpu().numpy()
+    n_m2l = n_p2p = inter = 0
+    for i, (x, mu) in enumerate(systems):
+        if len(mu) == 0:
+            continue
+        p1, a1, s1 = ctx.fmm_evaluate(_dev(x), _dev(mu), Gs[i], stats=True)
+        assert np.array_equal(acc[off[i]:off[i + 1]], a1.cpu().numpy()), i
+        assert np.array_equal(psi[off[i]:off[i + 1]], p1.cpu().numpy()), i
+        n_m2l += s1["n_m2l"]
+        n_p2p += s1["n_p2p"]
+        inter += s1["p2p_interactions"]
+    assert (st["n_m2l"], st["n_p2p"], st["p2p_interactions"]) == (n_m2l, n_p2p, inter)
+    assert st["n"] == len(ms)
+    ctx.close()
+
+
+def test_batch_identical_systems_are_not_coincident(g):
+    """Two copies of one system in an ensemble: equal positions in different systems
+    are no coincident pairs, and both copies get the same forces."""
+    x, mu = inputs.plummer(3000, 99)
+    off = np.array([0, 3000, 6000])
+    ctx = g.Context(p=5, eps=1e-6, precision=g.FMM_PREC_FP64)
+    psi, acc, st = ctx.fmm_evaluate_batch(off, _dev(np.concatenate([x, x])), _dev(np.concatenate([mu, mu])), 1.0,
+                                          stats=True)
+    acc = acc.cpu().numpy()
+    assert st["coincident"] == 0
+    assert np.array_equal(acc[:3000], acc[3000:])
+    ctx.close()
+
+
+def test_batch_matches_oracle(g, orc):
+    """Each system of a small FP64 ensemble against the oracle run on it alone."""
+    systems = _ensemble_with_gaps(3, inputs.BASE_SEED + 40)
+    systems = [(x[:2500], mu[:2500]) for x, mu in systems]
+    xs = np.concatenate([s[0] for s in systems])
+    ms = np.concatenate([s[1] for s in systems])
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
+    prm = dict(p=6, eps=1e-6, leaf_size=16, p2p_c=1.0)
+    ctx = g.Context(precision=g.FMM_PREC_FP64, **prm)
+    psi, acc = ctx.fmm_evaluate_batch(off, _dev(xs), _dev(ms), 1.0)
     acc = acc.cpu().numpy()
     for i, (x, mu) in enumerate(systems):
-        _, a1 = ctx.fmm_evaluate(_dev(x), _dev(mu))
-        assert np.max(_rel(acc[off[i]:off[i + 1]], a1.cpu().numpy())) <= 1e-12
+        if len(mu) < 2:
+            continue
+        run = orc.fmm(x, mu, **prm)
+        assert np.max(_rel(acc[off[i]:off[i + 1]], run.acc)) <= PARITY_TOL
+    ctx.close()
+
+
+def test_batch_rejects_bad_offsets(g):
+    x, mu = inputs.plummer(100, 3)
+    ctx = g.Context()
+    for off in ([1, 50, 100], [0, 60, 50, 100]):
+        with pytest.raises(g.FMMError):
+            ctx.fmm_evaluate_batch(np.array(off), _dev(x), _dev(mu), 1.0)
+    with pytest.raises(g.FMMError):
+        ctx.fmm_evaluate_batch(np.array([0, 50, 100]), _dev(x), _dev(mu), np.array([1.0, np.inf]))
     ctx.close()
 
 
