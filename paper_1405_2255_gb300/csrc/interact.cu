@@ -748,11 +748,10 @@ void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_sta
 }
 
 // ---------------------------------------------------------------- P2P, mixed
-// Positions as two floats (hi + lo); a source is made relative to the sink leaf's
-// centre with an error-free difference (TwoSum) when it is staged, so that
+// Positions as two floats (hi + lo, exact to 2^-48 relative), so that
 // dx = (hi_a - hi_b) + (lo_a - lo_b) keeps its relative accuracy even for close
-// pairs.  Pair terms are FP32; each tile's FP32 sums are added to two-float
-// accumulators (TwoSum), so the sum over tiles is compensated.
+// pairs.  Pair terms are FP32; the FP32 sums of every ~32 pairs are added to
+// two-float accumulators (TwoSum), so the sum over tiles is compensated.
 __global__ void k_split_positions(const d4* __restrict__ xm, int n, float4* __restrict__ xhi, float4* __restrict__ xlo) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         d4 v = xm[i];
@@ -774,14 +773,6 @@ __device__ inline ff two_sum(float a, float b) {
     float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
     return ff{s, e};
 }
-// (a_hi + a_lo) - (b_hi + b_lo) as a normalised two-float
-__device__ inline ff ff_sub(float ahi, float alo, float bhi, float blo) {
-    ff s = two_sum(ahi, -bhi);
-    float lo = __fadd_rn(s.lo, __fsub_rn(alo, blo));
-    float hi = __fadd_rn(s.hi, lo);
-    lo = __fsub_rn(lo, __fsub_rn(hi, s.hi));
-    return ff{hi, lo};
-}
 __device__ inline void ff_add_shfl(ff& a, int o) {
     float h = __shfl_xor_sync(0xffffffffu, a.hi, o), l = __shfl_xor_sync(0xffffffffu, a.lo, o);
     ff s = two_sum(a.hi, h);
@@ -796,45 +787,124 @@ __device__ inline void ff_acc(ff& a, float v) {
     a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
 }
 
-// The mixed kernel streams the sink's sources through a warp-private tile that is
-// filled from consecutive source cells (so small cells do not leave it half
-// empty).  A chunk of n_s <= 32 sinks is replicated R = 1, 2 or 4 times across
-// the warp (lane = r * (32/R) + sink), replica r taking every R-th source of a
-// tile; the replicas' partial sums are added at the end.  Tiles that hold a
-// source cell containing the sink leaf skip the r = 0 pairs (the sink itself and
-// coincident particles); all other tiles need no test, since particles of
-// different leaves are never coincident.  TWO_FLOAT selects dx = (hi_a - hi_b) +
-// (lo_a - lo_b) instead of dx = hi_a - hi_b.
+// The mixed kernel streams the sink's sources through warp-private tiles of 32 that
+// are filled from consecutive source cells (so small cells do not leave a tile half
+// empty).  Positions are two-float copies of the FP64 positions (hi = fl32(x),
+// lo = fl32(x - hi)); dx = (hi_a - hi_b) + (lo_a - lo_b) then carries one FP32
+// rounding relative to |dx| itself, not to |x|, so no per-leaf change of origin is
+// needed and a tile is filled by plain 16-byte copies (cp.async), double buffered so
+// that the next tile's loads overlap the current tile's pairs.  A chunk of n_s <= 32
+// sinks is replicated R = 1, 2 or 4 times across the warp (lane = r * (32/R) +
+// sink), replica r taking every R-th source of a tile; the replicas' partial sums
+// are added at the end.  Tiles that hold a source cell containing the sink leaf
+// skip the r = 0 pairs (the sink itself and coincident particles); all other tiles
+// need no test, since particles of different leaves are never coincident.
+// TWO_FLOAT = false uses the high parts alone (the low-order scale estimate).
 template <bool TWO_FLOAT, bool GUARD>
-__device__ __forceinline__ void p2p_tile(const float4* __restrict__ th, const float4* __restrict__ tl, int nt, int r0,
-                                         int R, float bhx, float bhy, float bhz, float blx, float bly, float blz,
+__device__ __forceinline__ void p2p_pair(const float4* __restrict__ th, const float4* __restrict__ tl, int j,
+                                         float bhx, float bhy, float bhz, float blx, float bly, float blz,
                                          float& ps, float& ax, float& ay, float& az) {
+    const float4 qh = th[j];
+    float dx = qh.x - bhx, dy = qh.y - bhy, dz = qh.z - bhz;
+    if (TWO_FLOAT) {
+        const float4 ql = tl[j];
+        dx += ql.x - blx;
+        dy += ql.y - bly;
+        dz += ql.z - blz;
+    }
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float rinv = rsqrtf(r2);
+    if (GUARD) rinv = r2 > 0.f ? rinv : 0.f;
+    const float qm = qh.w * rinv;
+    const float q3 = qm * rinv * rinv;
+    ps += qm;
+    ax = fmaf(q3, dx, ax);
+    ay = fmaf(q3, dy, ay);
+    az = fmaf(q3, dz, az);
+}
+// replica r0 of R takes sources r0, r0 + R, ... of a tile of nt; a full tile has a
+// trip count known at compile time
+template <bool TWO_FLOAT, bool GUARD, int R>
+__device__ __forceinline__ void p2p_tile(const float4* __restrict__ th, const float4* __restrict__ tl, int nt, int r0,
+                                         float bhx, float bhy, float bhz, float blx, float bly, float blz,
+                                         float& ps, float& ax, float& ay, float& az) {
+    if (nt == 32) {
+#pragma unroll 8
+        for (int k = 0; k < 32 / R; ++k)
+            p2p_pair<TWO_FLOAT, GUARD>(th, tl, r0 + R * k, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+    } else {
 #pragma unroll 4
-    for (int j = r0; j < nt; j += R) {
-        const float4 qh = th[j];
-        float dx = qh.x - bhx, dy = qh.y - bhy, dz = qh.z - bhz;
-        if (TWO_FLOAT) {
-            const float4 ql = tl[j];
-            dx += ql.x - blx;
-            dy += ql.y - bly;
-            dz += ql.z - blz;
-        }
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float rinv = rsqrtf(r2);
-        if (GUARD) rinv = r2 > 0.f ? rinv : 0.f;
-        const float qm = qh.w * rinv;
-        const float q3 = qm * rinv * rinv;
-        ps += qm;
-        ax = fmaf(q3, dx, ax);
-        ay = fmaf(q3, dy, ay);
-        az = fmaf(q3, dz, az);
+        for (int j = r0; j < nt; j += R)
+            p2p_pair<TWO_FLOAT, GUARD>(th, tl, j, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
     }
 }
+template <bool TWO_FLOAT, bool GUARD>
+__device__ __forceinline__ void p2p_tile_r(const float4* __restrict__ th, const float4* __restrict__ tl, int nt,
+                                           int r0, int R, float bhx, float bhy, float bhz, float blx, float bly,
+                                           float blz, float& ps, float& ax, float& ay, float& az) {
+    if (R == 1) p2p_tile<TWO_FLOAT, GUARD, 1>(th, tl, nt, r0, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+    else if (R == 2) p2p_tile<TWO_FLOAT, GUARD, 2>(th, tl, nt, r0, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+    else p2p_tile<TWO_FLOAT, GUARD, 4>(th, tl, nt, r0, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// The sources of one sink leaf: the entries of its own P2P segment, then those of
+// each ancestor's segment; fill() copies the next <= 32 source particles into a tile.
+struct SrcCursor {
+    int cell, e, e1, af, an, off;
+    bool contains;
+    __device__ void start(const int* seg_start, const int* seg_end, int leaf) {
+        cell = leaf;
+        e = seg_start[leaf];
+        e1 = seg_end[leaf];
+        af = an = off = 0;
+        contains = false;
+    }
+    template <bool TWO_FLOAT>
+    __device__ int fill(const Cells& c, const int2* __restrict__ list, const int* __restrict__ seg_start,
+                        const int* __restrict__ seg_end, const float4* __restrict__ xhi,
+                        const float4* __restrict__ xlo, int first, int lane, float4* th, float4* tl, bool& guard) {
+        int n = 0;
+        guard = false;
+        if (cell < 0) return 0;  // exhausted
+        while (n < 32) {
+            if (off == an) {  // next source cell
+                while (e == e1) {
+                    cell = c.parent[cell];
+                    if (cell < 0) return n;
+                    e = seg_start[cell];
+                    e1 = seg_end[cell];
+                }
+                const int A = list[e++].x;
+                af = c.first[A];
+                an = c.count[A];
+                off = 0;
+                contains = af <= first && first < af + an;
+                continue;
+            }
+            const int k = min(32 - n, an - off);
+            if (lane < k) {
+                cp_async16(th + n + lane, xhi + af + off + lane);
+                if (TWO_FLOAT) cp_async16(tl + n + lane, xlo + af + off + lane);
+            }
+            guard |= contains;
+            n += k;
+            off += k;
+        }
+        return n;
+    }
+};
 
 // One warp per sink leaf, leaves taken in decreasing order of work from an atomic
-// counter; sources come from the P2P segments of the leaf and of its ancestors.
+// counter.
 template <bool TWO_FLOAT>
-__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __restrict__ xhi,
+__global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(const float4* __restrict__ xhi,
                                                               const float4* __restrict__ xlo, Cells c,
                                                               const int2* __restrict__ list,
                                                               const int* __restrict__ seg_start,
@@ -842,11 +912,9 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __re
                                                               const int* __restrict__ order, int nleaves,
                                                               unsigned* __restrict__ counter,
                                                               double* __restrict__ psi, double* __restrict__ acc) {
-    __shared__ float4 th_all[kP2PWarps][32];
-    __shared__ float4 tl_all[kP2PWarps][TWO_FLOAT ? 32 : 1];
+    __shared__ __align__(16) float4 th_all[kP2PWarps][2][32];
+    __shared__ __align__(16) float4 tl_all[kP2PWarps][2][TWO_FLOAT ? 32 : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float4* th = th_all[wid];
-    float4* tl = tl_all[wid];
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(counter, 1u);
@@ -854,10 +922,6 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __re
         if (w >= (unsigned)nleaves) break;
         const int leaf = order[w];
         const int first = c.first[leaf], count = c.count[leaf];
-        const d4 sc = c.sr[leaf];
-        const float shx = (float)sc.x, shy = (float)sc.y, shz = (float)sc.z;
-        const float slx = (float)(sc.x - (double)shx), sly = (float)(sc.y - (double)shy),
-                    slz = (float)(sc.z - (double)shz);
         for (int s0 = 0; s0 < count; s0 += 32) {
             const int chunk = min(32, count - s0);
             const int R = chunk <= 8 ? 4 : (chunk <= 16 ? 2 : 1);
@@ -867,56 +931,47 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_mixed(const float4* __re
             const int i = first + s0 + sink;
             float bhx = 0, bhy = 0, bhz = 0, blx = 0, bly = 0, blz = 0;
             if (active) {
-                const float4 h = xhi[i], l = xlo[i];
-                const ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly), rz = ff_sub(h.z, l.z, shz, slz);
-                bhx = rx.hi; blx = rx.lo; bhy = ry.hi; bly = ry.lo; bhz = rz.hi; blz = rz.lo;
+                const float4 h = xhi[i];
+                bhx = h.x; bhy = h.y; bhz = h.z;
+                if (TWO_FLOAT) {
+                    const float4 l = xlo[i];
+                    blx = l.x; bly = l.y; blz = l.z;
+                }
             }
             ff aps = {0, 0}, aax = {0, 0}, aay = {0, 0}, aaz = {0, 0};
             float ps = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-            int fill = 0, since = 0;
-            bool guard = false;
-            auto flush_tile = [&](int nt) {
+            int since = 0;
+            SrcCursor cur;
+            cur.start(seg_start, seg_end, leaf);
+            int b = 0;
+            bool guard = false, guard_next = false;
+            int nt = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, xhi, xlo, first, lane, th_all[wid][0],
+                                         tl_all[wid][0], guard);
+            cp_async_commit();
+            while (nt > 0) {
+                // issue the next tile, then wait for the current one
+                const int nn = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, xhi, xlo, first, lane,
+                                                   th_all[wid][b ^ 1], tl_all[wid][b ^ 1], guard_next);
+                cp_async_commit();
+                cp_async_wait1();
                 __syncwarp();
                 if (guard)
-                    p2p_tile<TWO_FLOAT, true>(th, tl, nt, rep, R, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+                    p2p_tile_r<TWO_FLOAT, true>(th_all[wid][b], tl_all[wid][TWO_FLOAT ? b : 0], nt, rep, R, bhx, bhy,
+                                                bhz, blx, bly, blz, ps, ax, ay, az);
                 else
-                    p2p_tile<TWO_FLOAT, false>(th, tl, nt, rep, R, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+                    p2p_tile_r<TWO_FLOAT, false>(th_all[wid][b], tl_all[wid][TWO_FLOAT ? b : 0], nt, rep, R, bhx,
+                                                 bhy, bhz, blx, bly, blz, ps, ax, ay, az);
                 since += 32;
                 if (since >= 32 * R) {  // fold the FP32 partials into the two-float sums every ~32 pairs
                     ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
                     ps = ax = ay = az = 0.f;
                     since = 0;
                 }
-                __syncwarp();
-            };
-            for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
-                const int e0 = seg_start[cell], e1 = seg_end[cell];
-                for (int e = e0; e < e1; ++e) {
-                    const int A = list[e].x;
-                    const int af = c.first[A], an = c.count[A];
-                    const bool contains = af <= first && first < af + an;
-                    for (int off = 0; off < an;) {
-                        const int k = min(32 - fill, an - off);
-                        if (lane < k) {
-                            const int j = af + off + lane;
-                            const float4 h = xhi[j], l = xlo[j];
-                            const ff rx = ff_sub(h.x, l.x, shx, slx), ry = ff_sub(h.y, l.y, shy, sly),
-                                     rz = ff_sub(h.z, l.z, shz, slz);
-                            th[fill + lane] = make_float4(rx.hi, ry.hi, rz.hi, h.w);
-                            if (TWO_FLOAT) tl[fill + lane] = make_float4(rx.lo, ry.lo, rz.lo, 0.f);
-                        }
-                        guard |= contains;
-                        fill += k;
-                        off += k;
-                        if (fill == 32) {
-                            flush_tile(32);
-                            fill = 0;
-                            guard = false;
-                        }
-                    }
-                }
+                __syncwarp();  // every lane is done with tile b before it is refilled
+                b ^= 1;
+                nt = nn;
+                guard = guard_next;
             }
-            if (fill) flush_tile(fill);
             ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
             // add the replicas' partial sums (lanes sink, sink + S, ...)
             for (int o = S; o < 32; o <<= 1) {
