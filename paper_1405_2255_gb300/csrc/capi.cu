@@ -376,15 +376,10 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
         return 0;
     }
     const int pe = 1, nco = ncoef(pe);
-    TRY(ensure(ctx->M1, sizeof(double) * nco * (size_t)nc));
     TRY(ensure(ctx->F1, sizeof(double) * nco * (size_t)nc));
-    CU(cudaMemsetAsync(ctx->F1.p, 0, sizeof(double) * nco * (size_t)nc, s));
-    launch_p2m(P<d4>(ctx->xm), c, c.cr, P<int>(ctx->leaves), ctx->nleaves, pe, P<double>(ctx->M1), s);
-    for (int L = nlev - 1; L >= 0; --L)
-        launch_m2m_level(c, c.cr, ctx->lev_start[L], ctx->lev_start[L + 1], pe, P<double>(ctx->M1), s);
-    TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc, pe)));
-    launch_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc, c.cr,
-               P<double>(ctx->M1), pe, P<double>(ctx->F1), s);
+    // multipoles about the centres of mass: the masses and centres of the geometry pass
+    launch_est_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), nc, c,
+                   P<double>(ctx->F1), s);
     for (int L = 1; L < nlev; ++L) launch_l2l_level(c, c.cr, ctx->lev_start[L], ctx->lev_start[L + 1], pe, P<double>(ctx->F1), s);
     launch_l2p(P<d4>(ctx->xm), c, c.cr, P<int>(ctx->leaves), ctx->nleaves, pe, P<double>(ctx->F1),
                P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);

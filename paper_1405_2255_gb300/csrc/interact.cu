@@ -254,23 +254,31 @@ __device__ inline cd theta_low(int j, int m, double x, double y, double z, doubl
     return mkc(3.0 * (x * x - y * y) * r5, 6.0 * x * y * r5);
 }
 
-// per cell: conj(M_k / rho^k) in FP32 (all orders) and conj(M_k) in FP64 (orders <= kJ64)
+// per cell: conj(M_k / rho^k) in FP32 (all orders) and conj(M_k) in FP64 (orders <= kJ64);
+// one warp per cell, lane n holding rho^-n
 __global__ void k_prep_split(const double* __restrict__ M, const d4* __restrict__ cen, int ncells, int p,
                              float2* __restrict__ Mf, cd* __restrict__ M64) {
-    const int nco = ncoef(p);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)ncells * nco;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int cell = (int)(t / nco), i = (int)(t % nco);
-        const int n = c_idx_n[i];
-        const cd v = load_real_storage(M + (size_t)cell * nco, n, i - n * n - n);
+    const int nco = ncoef(p), lane = threadIdx.x & 31;
+    for (long long cell = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; cell < ncells;
+         cell += ((long long)gridDim.x * blockDim.x) >> 5) {
         const double rho = cen[cell].w;
-        double sc = 1.0;
-        if (rho > 0)
-            for (int k = 0; k < n; ++k) sc /= rho;
-        else if (n > 0)
-            sc = 0.0;  // a source of radius 0 has no moments above the monopole
-        Mf[t] = make_float2((float)(v.re * sc), (float)(-v.im * sc));
-        if (i < kN64) M64[(size_t)cell * kN64 + i] = conjc(v);
+        double pw = lane == 0 ? 1.0 : 0.0;  // a source of radius 0 has no moments above the monopole
+        if (rho > 0 && lane > 0 && lane <= p) {
+            const double rinv = 1.0 / rho;
+            pw = rinv;
+            for (int k = 1; k < lane; ++k) pw *= rinv;
+        }
+        const double* R = M + (size_t)cell * nco;
+        for (int i0 = 0; i0 < nco; i0 += 32) {  // uniform trip count: the shuffle needs every lane
+            const int i = i0 + lane;
+            const int n = i < nco ? c_idx_n[i] : 0;
+            const double sc = __shfl_sync(0xffffffffu, pw, n);
+            if (i < nco) {
+                const cd v = load_real_storage(R, n, i - n * n - n);
+                Mf[(size_t)cell * nco + i] = make_float2((float)(v.re * sc), (float)(-v.im * sc));
+                if (i < kN64) M64[(size_t)cell * kN64 + i] = conjc(v);
+            }
+        }
     }
 }
 
@@ -545,7 +553,7 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     k_sink_order<<<grid_for(ncells, 256), 256, 0, s>>>(flip ? k1 : k0, ncells, order, work + 1); note_launch();
     k_item_counts<<<grid_for(ncells, 256), 256, 0, s>>>(order, seg_start, seg_end, ncells, cnt); note_launch();
     scan_exclusive_i32(cnt, item_start, ncells, (int*)(work + 2), stmp, s);
-    k_prep_split<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(M, cen, ncells, p, Mf, M64); note_launch();
+    k_prep_split<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mf, M64); note_launch();
     LaneSched sched = make_lane_sched(p, kSchedDown);
     int maxq = 0;
     for (int l = 0; l < 32; ++l) maxq = sched.cnt[l] > maxq ? sched.cnt[l] : maxq;
@@ -1097,6 +1105,36 @@ __global__ void k_f_m2l(const int2* __restrict__ list, const int* __restrict__ s
         f += c.mass[A] / (dx * dx + dy * dy + dz * dz);
     }
     Ff[B] = f;
+}
+// p = 1 M2L of the acceleration estimate (Sec. 5.3.2) with multipoles about the
+// centres of mass: the dipole about the centre of mass vanishes, so eq. (3b) keeps
+// only the monopole, F_n^m = M_A Theta_n^m(s_B - z_A) for n <= 1 (real storage:
+// F_0^0, Im F_1^1, F_1^0, Re F_1^1).  One thread per sink cell, sources in list order.
+__global__ void k_est_m2l(const int2* __restrict__ list, const int* __restrict__ seg_start,
+                          const int* __restrict__ seg_end, int ncells, Cells c, double* __restrict__ F1) {
+    const int B = blockIdx.x * blockDim.x + threadIdx.x;
+    if (B >= ncells) return;
+    const d4 sb = c.cr[B];
+    double f0 = 0, fx = 0, fy = 0, fz = 0;
+    for (int e = seg_start[B]; e < seg_end[B]; ++e) {
+        const int A = list[e].x;
+        const d4 za = c.cr[A];
+        const double x = sb.x - za.x, y = sb.y - za.y, z = sb.z - za.z;
+        const double rinv = 1.0 / sqrt(x * x + y * y + z * z);
+        const double q = c.mass[A] * rinv, q3 = q * rinv * rinv;
+        f0 += q;
+        fx += q3 * x;
+        fy += q3 * y;
+        fz += q3 * z;
+    }
+    F1[4 * (size_t)B] = f0;
+    F1[4 * (size_t)B + 1] = fy;
+    F1[4 * (size_t)B + 2] = fz;
+    F1[4 * (size_t)B + 3] = fx;
+}
+void launch_est_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* F1,
+                    cudaStream_t s) {
+    if (ncells > 0) k_est_m2l<<<(ncells + 127) / 128, 128, 0, s>>>(list, seg_start, seg_end, ncells, c, F1); note_launch();
 }
 void launch_f_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* Ff,
                   cudaStream_t s) {

@@ -152,6 +152,10 @@ void launch_f_m2l(const int2* list, const int* seg_start, const int* seg_end, in
 void launch_f_down_level(Cells c, int lev_begin, int lev_end, double* Ff, cudaStream_t s);
 void launch_f_p2p(const d4* xm, Cells c, const int2* list, const int* seg_start, const int* seg_end,
                   const int* leaves, int nleaves, const double* Ff, double* f_sorted, cudaStream_t s);
+// p = 1 M2L of the acceleration estimate from the monopoles about the centres of mass
+// (the dipole vanishes there) into F1[nc][4]
+void launch_est_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* F1,
+                    cudaStream_t s);
 // |far + near| of the p = 1 estimate into the per-particle scale
 void launch_norm_scale(const double* psi_far, const double* acc_far, const double* acc_near, int n,
                        double* scale, cudaStream_t s);
