@@ -198,7 +198,7 @@ def roofline(g, a, prec, phase, full):
            else "nominal FP64 rate of the part (1.25 TFLOP/s)")
     if t_m2l >= t_p2p:
         achieved = full["n_m2l"] * m2l_flops(a.p) / t_m2l / 1e12
-        kern = "k_m2l_split (eq. 3b, orders > 2 in FP32)" if mixed else "k_m2l (eq. 3b, FP64)"
+        kern = "k_m2l_rounds (eq. 3b, orders > 2 in FP32)" if mixed else "k_m2l (eq. 3b, FP64)"
     else:
         achieved = 20.0 * full["p2p_interactions"] / t_p2p / 1e12
         kern = "k_p2p_mixed (eq. 1, FP32 two-float)" if mixed else "k_p2p_fp64 (eq. 1)"

@@ -181,8 +181,6 @@ void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void
 constexpr int kJ64 = 2;
 constexpr int kN64 = (kJ64 + 1) * (kJ64 + 1);  // FP64 coefficients per expansion (orders <= kJ64)
 constexpr int kT64 = 20;                       // FP64 complex terms per pair for kJ64 = 2
-constexpr int kNBs = 4;                        // pairs per batch
-constexpr int kLoPerLane = (kNBs * kT64 + 31) / 32;  // FP64 terms per lane per batch
 
 struct TermTab {
     unsigned char n[kT64], m[kT64], k[kT64];
@@ -191,7 +189,6 @@ struct TermTab {
 };
 static __constant__ TermTab c_terms;
 static __constant__ unsigned char c_idx_n[(kMaxP + 1) * (kMaxP + 1)];
-static __constant__ float c_twf[kMaxP + 2], c_thbf[kMaxP + 1][kMaxP + 1];
 
 static void init_split_tables() {
     static DeviceOnce once;
@@ -211,38 +208,9 @@ static void init_split_tables() {
         for (int n = 0; n <= kMaxP; ++n)
             for (int m = -n; m <= n; ++m) idx[cix(n, m)] = (unsigned char)n;
         cudaMemcpyToSymbol(c_idx_n, idx, sizeof idx);
-        float tw[kMaxP + 2], tb[kMaxP + 1][kMaxP + 1];
-        for (int n = 0; n <= kMaxP + 1; ++n) tw[n] = (float)(2 * n - 1);
-        for (int n = 0; n <= kMaxP; ++n)
-            for (int m = 0; m <= kMaxP; ++m) tb[n][m] = (float)((n - 1) * (n - 1) - m * m);
-        cudaMemcpyToSymbol(c_twf, tw, sizeof tw);
-        cudaMemcpyToSymbol(c_thbf, tb, sizeof tb);
     });
 }
 
-
-// one column m of Theta on a unit vector (r^2 = 1), single precision
-__device__ inline void theta_column_unit_f(int p, int m, float x, float y, float z, float2* out) {
-    float2 d = make_float2(1.f, 0.f);
-    for (int j = 1; j <= m; ++j) {
-        float s = c_twf[j];
-        d = make_float2(s * (x * d.x - y * d.y), s * (x * d.y + y * d.x));
-    }
-    float2 prev2 = make_float2(0.f, 0.f), prev = d;
-    const float sg = (m & 1) ? -1.f : 1.f;
-    for (int n = m; n <= p; ++n) {
-        float2 v;
-        if (n == m) v = d;
-        else {
-            float a = c_twf[n] * z, b = c_thbf[n][m];
-            v = make_float2(a * prev.x - b * prev2.x, a * prev.y - b * prev2.y);
-            prev2 = prev;
-            prev = v;
-        }
-        out[cix(n, m)] = v;
-        if (m) out[cix(n, -m)] = make_float2(sg * v.x, -sg * v.y);
-    }
-}
 
 // Theta_j^m(r), j <= 2, m >= 0, in closed form (consistent with the recurrences)
 __device__ inline cd theta_low(int j, int m, double x, double y, double z, double rinv) {
@@ -288,38 +256,101 @@ struct PairInfo {
 
 constexpr int kChunk = 32;  // M2L pairs per work item
 
-template <int MAXQ>
-__global__ void __launch_bounds__(64, 2) k_m2l_split(const int2* __restrict__ list, const int* __restrict__ seg_start,
-                                                  const int* __restrict__ seg_end, const int* __restrict__ order,
-                                                  const int* __restrict__ item_start, int ncells,
-                                                  unsigned* __restrict__ work, const d4* __restrict__ cen,
-                                                  const float2* __restrict__ Mf, const cd* __restrict__ M64g, int p,
-                                                  double* __restrict__ part, LaneSched sched) {
-    extern __shared__ unsigned char sm_raw[];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nco = ncoef(p);
-    // per-warp layout
-    const size_t per_warp = (size_t)kNBs * (2 * nco * sizeof(float2) + 2 * kN64 * sizeof(cd) + sizeof(PairInfo) +
-                                            2 * (kMaxP + 1) * sizeof(float)) +
-                            32 * kLoPerLane * sizeof(cd) + 8 * sizeof(cd);
-    unsigned char* base = sm_raw + wid * ((per_warp + 15) & ~(size_t)15);
-    float2* Th = (float2*)base;                 // [kNBs][nco]
-    float2* Mh = Th + kNBs * nco;               // [kNBs][nco]
-    cd* T64 = (cd*)(Mh + kNBs * nco);           // [kNBs][kN64]
-    cd* M64 = T64 + kNBs * kN64;                // [kNBs][kN64]
-    PairInfo* pi = (PairInfo*)(M64 + kNBs * kN64);
-    float* thA = (float*)(pi + kNBs);           // [kNBs][kMaxP+1]: (rho_A/r)^k
-    float* thB = thA + kNBs * (kMaxP + 1);      // [kNBs][kMaxP+1]: (sigma_B/r)^(n+1)
-    cd* red = (cd*)(thB + kNBs * (kMaxP + 1));  // [32 * kLoPerLane]
-    cd* lowF = red + 32 * kLoPerLane;           // [6] FP64 outputs of orders <= kJ64
-    const int cnt = sched.cnt[lane];
+// ---------------------------------------------------------------- split M2L by rounds of equal n
+// Terms of order n + k <= 2 are summed in FP64 (spread over the lanes), the others
+// in FP32 on the scaled quantities above.  A batch of up to kRB pairs of one sink
+// is processed order by order: for output order n every lane takes one (pair, m)
+// unit, so all lanes run the same k and l loops (their lengths depend on n only),
+// and the units of a round are summed over the pairs in pair order.
+constexpr int kRoundsBatch = 4;  // pairs per batch (the per-warp shared memory sets the occupancy)
+
+template <int kRB>
+struct RoundsSmem {
+    static constexpr int kRBLo = (kRB * kT64 + 31) / 32;  // FP64 terms per lane per batch
+    int nco;
+    size_t Mh, Th, pi, thA, thB, res, outs, M64, T64, red, lowF, idx, terms, total;
+    __host__ __device__ RoundsSmem(int p) {
+        nco = (p + 1) * (p + 1);
+        size_t o = 0;
+        auto take = [&](size_t bytes) {
+            const size_t at = o;
+            o = (o + bytes + 15) & ~(size_t)15;
+            return at;
+        };
+        Mh = take((size_t)kRB * nco * sizeof(float2));
+        Th = take((size_t)kRB * nco * sizeof(float2));
+        pi = take(kRB * sizeof(PairInfo));
+        thA = take(kRB * (kMaxP + 2) * sizeof(float));
+        thB = take(kRB * (kMaxP + 2) * sizeof(float));
+        res = take((size_t)kRB * (kMaxP + 1) * sizeof(float2));
+        outs = take((size_t)nco * sizeof(double));
+        M64 = take(kRB * kN64 * sizeof(cd));
+        T64 = take(kRB * kN64 * sizeof(cd));
+        red = take(32 * kRBLo * sizeof(cd));
+        lowF = take(8 * sizeof(cd));
+        idx = take((size_t)nco);
+        terms = take(sizeof(TermTab));
+        total = o;
+    }
+};
+
+// one column m of Theta on a unit vector into full complex storage (coefficients of
+// the recurrences computed in place: no lane-dependent constant-memory reads)
+__device__ inline void theta_column_unit_f2(int p, int m, float x, float y, float z, float2* out) {
+    float2 d = make_float2(1.f, 0.f);
+    for (int j = 1; j <= m; ++j) {
+        const float s = (float)(2 * j - 1);
+        d = make_float2(s * (x * d.x - y * d.y), s * (x * d.y + y * d.x));
+    }
+    float2 prev2 = make_float2(0.f, 0.f), prev = d;
+    const float sg = (m & 1) ? -1.f : 1.f;
+    for (int n = m; n <= p; ++n) {
+        float2 v = d;
+        if (n > m) {
+            const float a = (float)(2 * n - 1) * z, b = (float)((n - 1) * (n - 1) - m * m);
+            v = make_float2(a * prev.x - b * prev2.x, a * prev.y - b * prev2.y);
+            prev2 = prev;
+            prev = v;
+        }
+        out[n * n + n + m] = v;
+        if (m) out[n * n + n - m] = make_float2(sg * v.x, -sg * v.y);
+    }
+}
+
+template <int kRB>
+__global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ list,
+                                                       const int* __restrict__ seg_start,
+                                                       const int* __restrict__ seg_end, const int* __restrict__ order,
+                                                       const int* __restrict__ item_start,
+                                                       unsigned* __restrict__ work, const d4* __restrict__ cen,
+                                                       const float2* __restrict__ Mf, const cd* __restrict__ M64g,
+                                                       int p, double* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const RoundsSmem<kRB> L(p);
+    constexpr int kRBLo = RoundsSmem<kRB>::kRBLo;
+    const int nco = L.nco, lane = threadIdx.x;
+    float2* Mh = (float2*)(sm_raw + L.Mh);    // [kRB][nco]
+    float2* Th = (float2*)(sm_raw + L.Th);    // [kRB][nco]
+    PairInfo* pi = (PairInfo*)(sm_raw + L.pi);
+    float* thA = (float*)(sm_raw + L.thA);    // [kRB][kMaxP+2]: (rho_A/r)^k
+    float* thB = (float*)(sm_raw + L.thB);    // [kRB][kMaxP+2]: (sigma_B/r)^k
+    float2* res = (float2*)(sm_raw + L.res);  // [kRB * (n+1)] results of one order
+    double* outs = (double*)(sm_raw + L.outs);
+    cd* M64 = (cd*)(sm_raw + L.M64);
+    cd* T64 = (cd*)(sm_raw + L.T64);
+    cd* red = (cd*)(sm_raw + L.red);
+    cd* lowF = (cd*)(sm_raw + L.lowF);
+    unsigned char* idx_n = sm_raw + L.idx;
+    TermTab* terms = (TermTab*)(sm_raw + L.terms);
+    for (int i = lane; i < nco; i += 32) idx_n[i] = c_idx_n[i];
+    if (lane == 0) *terms = c_terms;
+    __syncwarp();
     const unsigned nitems = work[2], nsinks = work[1];
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(work, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= nitems) break;
-        // the sorted sink this item belongs to: last i with item_start[i] <= w
         int lo_i = 0, hi_i = (int)nsinks - 1;
         while (lo_i < hi_i) {
             const int mid = (lo_i + hi_i + 1) >> 1;
@@ -340,42 +371,40 @@ __global__ void __launch_bounds__(64, 2) k_m2l_split(const int2* __restrict__ li
             }
             sigma = 0.5 * warp_min(rmin);
         }
-        float2 hacc[MAXQ];
+        for (int i = lane; i < nco; i += 32) outs[i] = 0.0;
+        cd lo[kRBLo];
 #pragma unroll
-        for (int q = 0; q < MAXQ; ++q) hacc[q] = make_float2(0.f, 0.f);
-        cd lo[kLoPerLane];
-#pragma unroll
-        for (int i = 0; i < kLoPerLane; ++i) lo[i] = mkc(0.0, 0.0);
-        for (int eb = e0; eb < e1; eb += kNBs) {
-            const int nb = min(kNBs, e1 - eb);
-            // pair geometry and scale powers
+        for (int i = 0; i < kRBLo; ++i) lo[i] = mkc(0.0, 0.0);
+        for (int eb = e0; eb < e1; eb += kRB) {
+            const int nb = min(kRB, e1 - eb);
             if (lane < nb) {
                 const d4 zA = cen[list[eb + lane].x];
                 const double x = sB.x - zA.x, y = sB.y - zA.y, z = sB.z - zA.z;
                 const double rinv = rsqrt(x * x + y * y + z * z);
                 pi[lane] = PairInfo{x, y, z, rinv};
                 const float ta = (float)(zA.w * rinv), tb = (float)(sigma * rinv);
-                float a = 1.f, b = tb;
-                for (int k = 0; k <= p; ++k) {
-                    thA[lane * (kMaxP + 1) + k] = a;
-                    thB[lane * (kMaxP + 1) + k] = b;
+                float a = 1.f, b = 1.f;
+                for (int k = 0; k <= p + 1; ++k) {
+                    thA[lane * (kMaxP + 2) + k] = a;
+                    thB[lane * (kMaxP + 2) + k] = b;
                     a *= ta;
                     b *= tb;
                 }
             }
             __syncwarp();
-            // sources: scaled FP32 moments and FP64 low orders; FP64 Theta of orders <= kJ64
+            // scaled FP32 moments and FP64 low orders of the batch's sources
             for (int b = 0; b < nb; ++b) {
                 const int A = list[eb + b].x;
                 const float2* src = Mf + (size_t)A * nco;
-                const float* ta = thA + b * (kMaxP + 1);
+                const float* ta = thA + b * (kMaxP + 2);
                 for (int i = lane; i < nco; i += 32) {
                     const float2 v = src[i];
-                    const float s = ta[c_idx_n[i]];
-                    Mh[b * nco + i] = make_float2(v.x * s, v.y * s);
+                    const float sc = ta[idx_n[i]];
+                    Mh[b * nco + i] = make_float2(v.x * sc, v.y * sc);
                 }
                 if (lane < kN64) M64[b * kN64 + lane] = M64g[(size_t)A * kN64 + lane];
             }
+            // FP64 Theta of orders <= kJ64
             for (int t = lane; t < nb * 6; t += 32) {
                 const int b = t / 6, o = t % 6;
                 const int j = o < 1 ? 0 : (o < 3 ? 1 : 2), m = o - j * (j + 1) / 2;
@@ -384,95 +413,114 @@ __global__ void __launch_bounds__(64, 2) k_m2l_split(const int2* __restrict__ li
                 T64[b * kN64 + cix(j, m)] = v;
                 if (m) T64[b * kN64 + cix(j, -m)] = (m & 1) ? mkc(-v.re, v.im) : mkc(v.re, -v.im);
             }
-            // FP32 Theta on the unit vectors, 32/kNBs lanes per pair
-            {
-                constexpr int LPP = 32 / kNBs;
-                const int b = lane / LPP, sub = lane % LPP;
-                if (b < nb) {
-                    const PairInfo q = pi[b];
-                    const float x = (float)(q.x * q.rinv), y = (float)(q.y * q.rinv), z = (float)(q.z * q.rinv);
-                    for (int m = sub; m <= p; m += LPP) theta_column_unit_f(p, m, x, y, z, Th + b * nco);
-                }
+            // FP32 Theta on the unit vectors: one column (pair, m) per lane and round
+            for (int t = lane; t < nb * (p + 1); t += 32) {
+                const int b = t / (p + 1), m = t % (p + 1);
+                const PairInfo q = pi[b];
+                theta_column_unit_f2(p, m, (float)(q.x * q.rinv), (float)(q.y * q.rinv), (float)(q.z * q.rinv),
+                                     Th + b * nco);
             }
             __syncwarp();
-            // FP64 terms of orders <= kJ64, spread evenly over the lanes
+            // FP64 terms of orders n + k <= kJ64, spread over the lanes
 #pragma unroll
-            for (int i = 0; i < kLoPerLane; ++i) {
+            for (int i = 0; i < kRBLo; ++i) {
                 const int t = lane + 32 * i, b = t / kT64, id = t % kT64;
-                if (t < kNBs * kT64 && b < nb) {
-                    const int n = c_terms.n[id], m = c_terms.m[id], k = c_terms.k[id], l = c_terms.l[id];
+                if (t < kRB * kT64 && b < nb) {
+                    const int n = terms->n[id], m = terms->m[id], k = terms->k[id], l = terms->l[id];
                     cmac(lo[i], M64[b * kN64 + cix(k, l)], T64[b * kN64 + cix(n + k, m + l)]);
                 }
             }
-            // FP32 terms of orders > kJ64
-            for (int b = 0; b < nb; ++b) {
-                const float2* X = Mh + b * nco;
-                const float2* Y = Th + b * nco;
-                const float* tbb = thB + b * (kMaxP + 1);
-#pragma unroll
-                for (int q = 0; q < MAXQ; ++q) {
-                    if (q < cnt) {
-                        const int n = sched.n[lane][q], m = sched.m[lane][q];
-                        float2 a = make_float2(0.f, 0.f), a2 = make_float2(0.f, 0.f);
-                        for (int k = max(0, kJ64 + 1 - n); k <= p - n; ++k) {
-                            const float2* xk = X + k * k + k;
-                            const float2* yk = Y + (n + k) * (n + k) + (n + k) + m;
-                            int l = -k;
-                            for (; l < k; l += 2) {
-                                cmacf(a, xk[l], yk[l]);
-                                cmacf(a2, xk[l + 1], yk[l + 1]);
-                            }
-                            cmacf(a, xk[k], yk[k]);
+            // FP32 terms of orders n + k > kJ64: order by order, one (pair, m) unit per lane
+            for (int n = 0; n <= p; ++n) {
+                const int kmin = n > kJ64 ? 0 : kJ64 + 1 - n;
+                if (kmin > p - n) continue;
+                const int units = nb * (n + 1);
+                for (int u0 = 0; u0 < units; u0 += 32) {
+                    const int u = u0 + lane;
+                    const bool act = u < units;
+                    const int b = act ? u / (n + 1) : 0, m = act ? u % (n + 1) : 0;
+                    const float2* X = Mh + b * nco;
+                    const float2* Y = Th + b * nco;
+                    float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+                    for (int k = kmin; k <= p - n; ++k) {
+                        const float2* xk = X + k * k;
+                        const float2* yk = Y + (n + k) * (n + k) + n + m;
+                        // l = -k .. k, i.e. offsets 0 .. 2k of xk and yk
+                        int o = 0;
+                        for (; o + 3 <= 2 * k; o += 4) {
+                            const float2 x0 = xk[o], x1 = xk[o + 1], x2 = xk[o + 2], x3 = xk[o + 3];
+                            const float2 y0 = yk[o], y1 = yk[o + 1], y2 = yk[o + 2], y3 = yk[o + 3];
+                            cmacf(a0, x0, y0);
+                            cmacf(a1, x1, y1);
+                            cmacf(a2, x2, y2);
+                            cmacf(a3, x3, y3);
                         }
-                        a.x += a2.x;
-                        a.y += a2.y;
-                        const float sc = tbb[n];
-                        hacc[q].x = fmaf(a.x, sc, hacc[q].x);
-                        hacc[q].y = fmaf(a.y, sc, hacc[q].y);
+                        for (; o <= 2 * k; ++o) cmacf(a0, xk[o], yk[o]);
+                    }
+                    if (act) {
+                        const float sc = thB[b * (kMaxP + 2) + n + 1];
+                        res[u] = make_float2((a0.x + a1.x + a2.x + a3.x) * sc, (a0.y + a1.y + a2.y + a3.y) * sc);
                     }
                 }
+                __syncwarp();
+                for (int m = lane; m <= n; m += 32) {
+                    float2 t = res[m];
+                    for (int b = 1; b < nb; ++b) {
+                        const float2 v = res[b * (n + 1) + m];
+                        t.x += v.x;
+                        t.y += v.y;
+                    }
+                    outs[n * n + n + m] += (double)t.x;
+                    if (m) outs[n * n + n - m] += (double)t.y;
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
         // reduce the FP64 terms per output in a fixed order
 #pragma unroll
-        for (int i = 0; i < kLoPerLane; ++i) red[lane * kLoPerLane + i] = lo[i];
+        for (int i = 0; i < kRBLo; ++i) red[lane * kRBLo + i] = lo[i];
         __syncwarp();
         if (lane < 6) {
             cd sum = mkc(0.0, 0.0);
-            for (int L = 0; L < 32; ++L)
-                for (int i = 0; i < kLoPerLane; ++i) {
-                    const int t = L + 32 * i;
-                    if (t >= kNBs * kT64) continue;
-                    if (c_terms.out[t % kT64] == lane) sum = sum + red[L * kLoPerLane + i];
+            for (int Ln = 0; Ln < 32; ++Ln)
+                for (int i = 0; i < kRBLo; ++i) {
+                    const int t = Ln + 32 * i;
+                    if (t >= kRB * kT64) continue;
+                    if (terms->out[t % kT64] == lane) sum = sum + red[Ln * kRBLo + i];
                 }
             lowF[lane] = sum;
         }
         __syncwarp();
         double* out = part + (size_t)w * nco;
         const double sinv = 1.0 / sigma;
-#pragma unroll
-        for (int q = 0; q < MAXQ; ++q) {
-            if (q < cnt) {
-                const int n = sched.n[lane][q], m = sched.m[lane][q];
-                double s = sinv;
-                for (int k = 0; k < n; ++k) s *= sinv;
-                cd v = mkc((double)hacc[q].x * s, (double)hacc[q].y * s);
-                if (n <= kJ64) v = v + lowF[n * (n + 1) / 2 + m];
-                out[cix(n, m)] = v.re;
-                if (m) out[cix(n, -m)] = v.im;
+        for (int i = lane; i < nco; i += 32) {
+            const int n = idx_n[i], m = i - n * n - n;
+            double sc = sinv;
+            for (int k = 0; k < n; ++k) sc *= sinv;
+            double v = outs[i] * sc;
+            if (n <= kJ64) {
+                const cd lv = lowF[n * (n + 1) / 2 + (m < 0 ? -m : m)];
+                v += m >= 0 ? lv.re : lv.im;
             }
+            out[i] = v;
         }
         __syncwarp();
     }
 }
 
-size_t m2l_split_smem(int p) {
-    const int nco = ncoef(p);
-    const size_t per_warp = (size_t)kNBs * (2 * nco * sizeof(float2) + 2 * kN64 * sizeof(cd) + sizeof(PairInfo) +
-                                            2 * (kMaxP + 1) * sizeof(float)) +
-                            32 * kLoPerLane * sizeof(cd) + 8 * sizeof(cd);
-    return 2 * ((per_warp + 15) & ~(size_t)15);
+template <int kRB>
+static void m2l_rounds_launch(const int2* list, const int* seg_start, const int* seg_end, const int* order,
+                              const int* item_start, unsigned* work, const d4* cen, const float2* Mf, const cd* M64,
+                              int p, double* part, cudaStream_t s) {
+    const size_t sm = RoundsSmem<kRB>(p).total;
+    cudaFuncSetAttribute(k_m2l_rounds<kRB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int dev = 0, nsm = 152, bps = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l_rounds<kRB>, 32, sm);
+    const unsigned g = (unsigned)(nsm * (bps > 0 ? bps : 1));
+    k_m2l_rounds<kRB><<<g, 32, sm, s>>>(list, seg_start, seg_end, order, item_start, work, cen, Mf, M64, p, part);
+    note_launch();
 }
 
 size_t m2l_split_tmp_bytes(int ncells, int p, long long npairs) {
@@ -508,23 +556,6 @@ __global__ void k_m2l_reduce(const int* __restrict__ order, const int* __restric
     }
 }
 
-template <int MAXQ>
-static void m2l_split_launch(const int2* list, const int* seg_start, const int* seg_end, const int* order,
-                             const int* item_start, int ncells, unsigned* work, const d4* cen, const float2* Mf,
-                             const cd* M64, int p, double* part, const LaneSched& sched, cudaStream_t s) {
-    const int wpb = 2;
-    size_t sm = m2l_split_smem(p);
-    cudaFuncSetAttribute(k_m2l_split<MAXQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    int dev = 0, nsm = 152, bps = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l_split<MAXQ>, wpb * 32, sm);
-    unsigned g = (unsigned)(nsm * (bps > 0 ? bps : 1));
-    k_m2l_split<MAXQ><<<g, wpb * 32, sm, s>>>(list, seg_start, seg_end, order, item_start, ncells, work, cen, Mf, M64,
-                                              p, part, sched);
-    note_launch();
-}
-
 void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells, const d4* cen,
                       const double* M, int p, double* F, cudaStream_t s) {
     if (ncells <= 0) return;
@@ -554,15 +585,7 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     k_item_counts<<<grid_for(ncells, 256), 256, 0, s>>>(order, seg_start, seg_end, ncells, cnt); note_launch();
     scan_exclusive_i32(cnt, item_start, ncells, (int*)(work + 2), stmp, s);
     k_prep_split<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mf, M64); note_launch();
-    LaneSched sched = make_lane_sched(p, kSchedDown);
-    int maxq = 0;
-    for (int l = 0; l < 32; ++l) maxq = sched.cnt[l] > maxq ? sched.cnt[l] : maxq;
-    if (maxq <= 4)
-        m2l_split_launch<4>(list, seg_start, seg_end, order, item_start, ncells, work, cen, Mf, M64, p, part, sched, s);
-    else if (maxq <= 8)
-        m2l_split_launch<8>(list, seg_start, seg_end, order, item_start, ncells, work, cen, Mf, M64, p, part, sched, s);
-    else
-        m2l_split_launch<12>(list, seg_start, seg_end, order, item_start, ncells, work, cen, Mf, M64, p, part, sched, s);
+    m2l_rounds_launch<kRoundsBatch>(list, seg_start, seg_end, order, item_start, work, cen, Mf, M64, p, part, s);
     k_m2l_reduce<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(order, item_start, cnt, work, ncells,
                                                                             ncoef(p), part, F);
     note_launch();
