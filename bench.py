@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--p", type=int, default=12)
-    ap.add_argument("--eps", type=float, default=2e-7)
+    ap.add_argument("--eps", type=float, default=2.5e-7)
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--c", type=float, default=4.0)
     ap.add_argument("--cpu-sample", type=int, default=50000)
@@ -48,6 +48,8 @@ def parse():
                          "ensemble: 256 spheres of 1e3..1e5 in one forest; serve: 64 systems of 1e4..2e6 "
                          "served at 0.8 of capacity (Poisson arrivals)")
     ap.add_argument("--requests", type=int, default=384, help="serve: requests in the open-loop run")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose (p, eps, leaf, p2p_c) for rms 1e-7 on the workload first (untimed)")
     a = ap.parse_args()
     if a.workload == "cusp" and a.n == 1_000_000:
         a.n = 10_000_000
@@ -473,6 +475,13 @@ def main():
         x, mu = inputs.plummer(a.n, inputs.BASE_SEED + 2 + 7919 * rank)
     xt = torch.from_numpy(x).to(dev)
     mt = torch.from_numpy(mu).to(dev)
+    tuned = None
+    if a.autotune:
+        from paper_1405_2255_gb300 import autotune
+        r = autotune.tune(xt, mt, target_rms=1e-7, precision=prec)
+        a.p, a.eps, a.leaf, a.c = r.best.p, r.best.eps, r.best.leaf_size, r.best.p2p_c
+        tuned = {"seconds": r.seconds, "candidates": len(r.tried), "target_rms": r.target_rms,
+                 "tuning_rms": r.best.rms, "tuning_ms": r.best.ms}
     psi = torch.empty(a.n, dtype=torch.float64, device=dev)
     acc = torch.empty((a.n, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -565,6 +574,8 @@ def main():
 
     if rank == 0:
         cfg = config_of(a)
+        if tuned:
+            cfg["autotune"] = tuned
         cfg.update({"rms_rel_err": rms, "p999_rel_err": p999, "err_sinks": int(ns),
                     "phase_ms": {k: float(np.mean([s[k] for s in phase])) for k in
                                  ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total")},

@@ -284,3 +284,24 @@ def test_mixed_m2l_split_accuracy(g, orc, split):
     assert np.sqrt(np.mean(e ** 2)) < 1e-7
     assert np.percentile(e, 99.9) < 2e-6
     ctx.close()
+
+
+def test_autotune_meets_target(g):
+    """The tuner's choice reaches the target rms on its own sample and is the fastest
+    of the candidates that did."""
+    from paper_1405_2255_gb300 import autotune
+    x, mu = inputs.plummer(30000, inputs.BASE_SEED + 61)
+    r = autotune.tune(_dev(x), _dev(mu), target_rms=1e-6, ps=(6, 8), leaves=(32, 64), cs=(2.0,), nsinks=1024,
+                      eps0=1e-6)
+    assert r.best.rms <= 1e-6 and r.best.eps > 0
+    ok = [c for c in r.tried if c.rms <= 1e-6]
+    assert r.best.ms == min(c.ms for c in ok)
+    # the chosen parameters reproduce the accuracy on an independent sample of sinks
+    ctx = g.Context(precision=g.FMM_PREC_MIXED, **r.params())
+    _, acc = ctx.fmm_evaluate(_dev(x), _dev(mu))
+    sinks = np.arange(5, 30000, 29)
+    import torch
+    _, a_t = ctx.fmm_direct(_dev(x), _dev(mu), 1.0, sinks=torch.from_numpy(sinks).to("cuda:0"))
+    e = _rel(acc.cpu().numpy()[sinks], a_t.cpu().numpy())
+    assert np.sqrt(np.mean(e ** 2)) < 1.5e-6
+    ctx.close()
