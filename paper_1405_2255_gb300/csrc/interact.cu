@@ -804,9 +804,8 @@ __device__ inline ff two_sum(float a, float b) {
     float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
     return ff{s, e};
 }
-// a += the two-float value of lane src (every lane takes part in the shuffle)
-__device__ inline void ff_add_from(ff& a, int src) {
-    float h = __shfl_sync(0xffffffffu, a.hi, src), l = __shfl_sync(0xffffffffu, a.lo, src);
+__device__ inline void ff_add_shfl(ff& a, int o) {
+    float h = __shfl_xor_sync(0xffffffffu, a.hi, o), l = __shfl_xor_sync(0xffffffffu, a.lo, o);
     ff s = two_sum(a.hi, h);
     float lo = __fadd_rn(__fadd_rn(a.lo, l), s.lo);
     a.hi = __fadd_rn(s.hi, lo);
@@ -860,7 +859,7 @@ template <bool TWO_FLOAT, bool GUARD, int R>
 __device__ __forceinline__ void p2p_tile(const float4* __restrict__ th, const float4* __restrict__ tl, int nt, int r0,
                                          float bhx, float bhy, float bhz, float blx, float bly, float blz,
                                          float& ps, float& ax, float& ay, float& az) {
-    if (32 % R == 0 && nt == 32) {
+    if (nt == 32) {
 #pragma unroll 8
         for (int k = 0; k < 32 / R; ++k)
             p2p_pair<TWO_FLOAT, GUARD>(th, tl, r0 + R * k, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
@@ -870,28 +869,13 @@ __device__ __forceinline__ void p2p_tile(const float4* __restrict__ th, const fl
             p2p_pair<TWO_FLOAT, GUARD>(th, tl, j, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
     }
 }
-// the replica counts used: the largest of these with R * chunk <= 32
-__host__ __device__ inline int p2p_replicas(int chunk) {
-    const int q = 32 / chunk;
-    return q >= 32 ? 32 : q >= 16 ? 16 : q >= 8 ? 8 : q >= 6 ? 6 : q >= 5 ? 5 : q >= 4 ? 4 : q >= 3 ? 3 : q >= 2 ? 2 : 1;
-}
 template <bool TWO_FLOAT, bool GUARD>
 __device__ __forceinline__ void p2p_tile_r(const float4* __restrict__ th, const float4* __restrict__ tl, int nt,
                                            int r0, int R, float bhx, float bhy, float bhz, float blx, float bly,
                                            float blz, float& ps, float& ax, float& ay, float& az) {
-#define GB3_TILE(RR) p2p_tile<TWO_FLOAT, GUARD, RR>(th, tl, nt, r0, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az)
-    switch (R) {
-        case 1: GB3_TILE(1); break;
-        case 2: GB3_TILE(2); break;
-        case 3: GB3_TILE(3); break;
-        case 4: GB3_TILE(4); break;
-        case 5: GB3_TILE(5); break;
-        case 6: GB3_TILE(6); break;
-        case 8: GB3_TILE(8); break;
-        case 16: GB3_TILE(16); break;
-        default: GB3_TILE(32); break;
-    }
-#undef GB3_TILE
+    if (R == 1) p2p_tile<TWO_FLOAT, GUARD, 1>(th, tl, nt, r0, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+    else if (R == 2) p2p_tile<TWO_FLOAT, GUARD, 2>(th, tl, nt, r0, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+    else p2p_tile<TWO_FLOAT, GUARD, 4>(th, tl, nt, r0, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -951,7 +935,7 @@ struct SrcCursor {
 // One warp per sink leaf, leaves taken in decreasing order of work from an atomic
 // counter.
 template <bool TWO_FLOAT>
-__global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float4* __restrict__ xhi,
+__global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(const float4* __restrict__ xhi,
                                                               const float4* __restrict__ xlo, Cells c,
                                                               const int2* __restrict__ list,
                                                               const int* __restrict__ seg_start,
@@ -971,9 +955,10 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float4* _
         const int first = c.first[leaf], count = c.count[leaf];
         for (int s0 = 0; s0 < count; s0 += 32) {
             const int chunk = min(32, count - s0);
-            const int R = p2p_replicas(chunk), S = chunk;  // lane = rep * S + sink
+            const int R = chunk <= 8 ? 4 : (chunk <= 16 ? 2 : 1);
+            const int S = 32 / R;
             const int sink = lane % S, rep = lane / S;
-            const bool active = rep < R;
+            const bool active = sink < chunk;
             const int i = first + s0 + sink;
             float bhx = 0, bhy = 0, bhz = 0, blx = 0, bly = 0, blz = 0;
             if (active) {
@@ -1019,10 +1004,9 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float4* _
                 guard = guard_next;
             }
             ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
-            // add the replicas' partial sums into replica 0 (lanes sink + S, sink + 2S, ... in order)
-            for (int r = 1; r < R; ++r) {
-                const int src = min(lane + r * S, 31);
-                ff_add_from(aps, src); ff_add_from(aax, src); ff_add_from(aay, src); ff_add_from(aaz, src);
+            // add the replicas' partial sums (lanes sink, sink + S, ...)
+            for (int o = S; o < 32; o <<= 1) {
+                ff_add_shfl(aps, o); ff_add_shfl(aax, o); ff_add_shfl(aay, o); ff_add_shfl(aaz, o);
             }
             if (active && rep == 0) {
                 psi[i] = (double)aps.hi + (double)aps.lo;

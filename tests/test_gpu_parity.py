@@ -305,3 +305,17 @@ def test_autotune_meets_target(g):
     e = _rel(acc.cpu().numpy()[sinks], a_t.cpu().numpy())
     assert np.sqrt(np.mean(e ** 2)) < 1.5e-6
     ctx.close()
+
+
+@pytest.mark.parametrize("leaf", [1, 3, 8, 20, 40])
+def test_mixed_small_leaves(g, orc, leaf):
+    """Mixed P2P with every chunk size a small leaf produces (1..40 sinks: replica counts
+    32..1) against the FP64 direct sum."""
+    x, mu = inputs.plummer(3000, inputs.BASE_SEED + 70 + leaf)
+    ctx = g.Context(p=8, eps=1e-8, leaf_size=leaf, p2p_c=4.0, precision=g.FMM_PREC_MIXED)
+    psi, acc = ctx.fmm_evaluate(_dev(x), _dev(mu))
+    _, a_t, _, _ = orc.direct(x, mu)
+    e = _rel(acc.cpu().numpy(), a_t)
+    assert np.all(np.isfinite(e))
+    assert np.sqrt(np.mean(e ** 2)) < 1e-7
+    ctx.close()
