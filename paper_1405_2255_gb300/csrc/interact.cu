@@ -317,6 +317,31 @@ __device__ inline void theta_column_unit_f2(int p, int m, float x, float y, floa
     }
 }
 
+// sum over l = -k..k of X_k^l Y^{m+l}: offsets 0..2k of x and y, unrolled for each k
+template <int K>
+__device__ __forceinline__ void m2l_row_k(const float2* __restrict__ x, const float2* __restrict__ y, float2& a0,
+                                          float2& a1, float2& a2, float2& a3) {
+#pragma unroll
+    for (int o = 0; o <= 2 * K; o += 4) {
+        cmacf(a0, x[o], y[o]);
+        if (o + 1 <= 2 * K) cmacf(a1, x[o + 1], y[o + 1]);
+        if (o + 2 <= 2 * K) cmacf(a2, x[o + 2], y[o + 2]);
+        if (o + 3 <= 2 * K) cmacf(a3, x[o + 3], y[o + 3]);
+    }
+}
+__device__ __forceinline__ void m2l_row(int k, const float2* __restrict__ x, const float2* __restrict__ y, float2& a0,
+                                        float2& a1, float2& a2, float2& a3) {
+#define GB3_ROW(K) \
+    case K: m2l_row_k<K>(x, y, a0, a1, a2, a3); break;
+    switch (k) {
+        GB3_ROW(0) GB3_ROW(1) GB3_ROW(2) GB3_ROW(3) GB3_ROW(4) GB3_ROW(5) GB3_ROW(6) GB3_ROW(7) GB3_ROW(8)
+        GB3_ROW(9) GB3_ROW(10) GB3_ROW(11) GB3_ROW(12) GB3_ROW(13) GB3_ROW(14) GB3_ROW(15) GB3_ROW(16)
+        GB3_ROW(17) GB3_ROW(18) GB3_ROW(19)
+        default: m2l_row_k<20>(x, y, a0, a1, a2, a3); break;
+    }
+#undef GB3_ROW
+}
+
 template <int kRB>
 __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ list,
                                                        const int* __restrict__ seg_start,
@@ -442,21 +467,8 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
                     const float2* X = Mh + b * nco;
                     const float2* Y = Th + b * nco;
                     float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
-                    for (int k = kmin; k <= p - n; ++k) {
-                        const float2* xk = X + k * k;
-                        const float2* yk = Y + (n + k) * (n + k) + n + m;
-                        // l = -k .. k, i.e. offsets 0 .. 2k of xk and yk
-                        int o = 0;
-                        for (; o + 3 <= 2 * k; o += 4) {
-                            const float2 x0 = xk[o], x1 = xk[o + 1], x2 = xk[o + 2], x3 = xk[o + 3];
-                            const float2 y0 = yk[o], y1 = yk[o + 1], y2 = yk[o + 2], y3 = yk[o + 3];
-                            cmacf(a0, x0, y0);
-                            cmacf(a1, x1, y1);
-                            cmacf(a2, x2, y2);
-                            cmacf(a3, x3, y3);
-                        }
-                        for (; o <= 2 * k; ++o) cmacf(a0, xk[o], yk[o]);
-                    }
+                    for (int k = kmin; k <= p - n; ++k)
+                        m2l_row(k, X + k * k, Y + (n + k) * (n + k) + n + m, a0, a1, a2, a3);
                     if (act) {
                         const float sc = thB[b * (kMaxP + 2) + n + 1];
                         res[u] = make_float2((a0.x + a1.x + a2.x + a3.x) * sc, (a0.y + a1.y + a2.y + a3.y) * sc);
