@@ -28,7 +28,8 @@
  *           each triplet; sort by (key, original index).
  *   R-leaf  a cell is split iff it holds more than leaf_size particles and is above
  *           depth 21; daughters are the non-empty octants in key order.
- *   R-ses   leaf centre: smallest enclosing ball of its particles (Welzl);
+ *   R-ses   leaf centre: smallest enclosing ball of its particles (Welzl, the
+ *           first 128 particles taken in bit-reversed index order);
  *           internal centre: smallest ball enclosing the daughters' balls
  *           (s_d, rho_d) (enumeration of support sets of up to 4 balls); both in
  *           IEEE single precision relative to the cell's first particle / first
@@ -480,13 +481,35 @@ static void welzl(int np, const float P[][3], int nr, float R[4][3], float c[3],
     welzl(np - 1, P, nr + 1, R, c, rad);
 }
 
+/* The order in which Welzl's recursion takes the points (reading R-ses): the first
+ * min(n, 128) points in bit-reversed index order, i.e. t = 0, 1, 2, ... over the
+ * smallest power of two K >= min(n, 128), taking bitreverse_K(t) whenever it is
+ * below min(n, 128); any further points in index order.  Points of a leaf come in
+ * key order, which is spatially coherent and makes the recursion restart often;
+ * the bit-reversed order visits them spread out.  The ball is the same (it is
+ * unique); only the work changes. */
+static void meb_order(int n, int *order)
+{
+    int m = n < 128 ? n : 128, K = 1, bits = 0, k = 0;
+    while (K < m) { K <<= 1; ++bits; }
+    for (int t = 0; t < K; ++t) {
+        int v = 0;
+        for (int b = 0; b < bits; ++b) if (t & (1 << b)) v |= 1 << (bits - 1 - b);
+        if (v < m) order[k++] = v;
+    }
+    for (int i = m; i < n; ++i) order[k++] = i;
+}
+
 /* smallest enclosing ball of n points: single precision, relative to the first point */
 int orc_meb_points(int n, const double *pts, double c[3], double *rad)
 {
     if (n <= 0) { c[0] = c[1] = c[2] = 0; *rad = 0; return 0; }
     float (*P)[3] = malloc(sizeof(float[3]) * n);
+    int *order = malloc(sizeof(int) * n);
+    meb_order(n, order);
     for (int i = 0; i < n; ++i)
-        for (int d = 0; d < 3; ++d) P[i][d] = (float)(pts[3 * i + d] - pts[d]);
+        for (int d = 0; d < 3; ++d) P[i][d] = (float)(pts[3 * order[i] + d] - pts[d]);
+    free(order);
     float R[4][3], cf[3], rf;
     welzl(n, (const float(*)[3])P, 0, R, cf, &rf);
     free(P);

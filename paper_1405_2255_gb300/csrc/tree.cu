@@ -558,8 +558,9 @@ __device__ inline void ld3(const d4* xm, int i, double p[3]) {
     p[0] = v.x; p[1] = v.y; p[2] = v.z;
 }
 
-// leaf points relative to the first one, in single precision: from the warp's
-// shared buffer (first kMebBuf points) or converted on the fly
+// leaf points relative to the first one, in single precision, in the order of
+// Welzl's recursion: from the warp's shared buffer (the first kMebBuf positions of
+// that order) or converted on the fly
 constexpr int kMebBuf = 128;
 struct LeafPts {
     const float (*buf)[3];
@@ -649,11 +650,32 @@ __global__ void __launch_bounds__(kGeoWarps * 32) k_leaf_geometry(const d4* __re
     P.buf = pbuf[wid];
     P.X = X;
     ld3(X, 0, P.o);
-    for (int i = lane; i < count && i < kMebBuf; i += 32) {
-        d4 v = X[i];
-        pbuf[wid][i][0] = (float)(v.x - P.o[0]);
-        pbuf[wid][i][1] = (float)(v.y - P.o[1]);
-        pbuf[wid][i][2] = (float)(v.z - P.o[2]);
+    // the buffer holds the first min(count, kMebBuf) points in the order Welzl's
+    // recursion takes them: bit-reversed index order (t = 0, 1, ... over the next
+    // power of two, keeping bitreverse(t) when it is below the count); points past
+    // the buffer follow in index order
+    {
+        const int m = count < kMebBuf ? count : kMebBuf;
+        int K = 1, bits = 0;
+        while (K < m) {
+            K <<= 1;
+            ++bits;
+        }
+        int base = 0;
+        for (int t0 = 0; t0 < K; t0 += 32) {
+            const int t = t0 + lane;
+            const int v = bits ? (int)(__brev((unsigned)t) >> (32 - bits)) : 0;
+            const bool valid = t < K && v < m;
+            const unsigned msk = __ballot_sync(0xffffffffu, valid);
+            if (valid) {
+                const int k = base + __popc(msk & ((1u << lane) - 1u));
+                const d4 q = X[v];
+                pbuf[wid][k][0] = (float)(q.x - P.o[0]);
+                pbuf[wid][k][1] = (float)(q.y - P.o[1]);
+                pbuf[wid][k][2] = (float)(q.z - P.o[2]);
+            }
+            base += __popc(msk);
+        }
     }
     __syncwarp();
     float cf[3], radf;
