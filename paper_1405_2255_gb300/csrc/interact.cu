@@ -722,6 +722,7 @@ void launch_l2p(const d4* xm, Cells c, const d4* cen, const int* leaves, int nle
 // internal covers every leaf below B); they pass through a warp-private tile of
 // 32 in shared memory.
 constexpr int kP2PWarps = 4;
+constexpr int kP2PTile = 128;  // sources per staged tile at the largest replica count (4 x 32)
 
 __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_fp64(const d4* __restrict__ xm, Cells c,
                                                              const int2* __restrict__ list,
@@ -871,9 +872,9 @@ template <bool TWO_FLOAT, bool GUARD, int R>
 __device__ __forceinline__ void p2p_tile(const float4* __restrict__ th, const float4* __restrict__ tl, int nt, int r0,
                                          float bhx, float bhy, float bhz, float blx, float bly, float blz,
                                          float& ps, float& ax, float& ay, float& az) {
-    if (nt == 32) {
+    if (nt == 32 * R) {  // a full tile: 32 sources per replica
 #pragma unroll 8
-        for (int k = 0; k < 32 / R; ++k)
+        for (int k = 0; k < 32; ++k)
             p2p_pair<TWO_FLOAT, GUARD>(th, tl, r0 + R * k, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
     } else {
 #pragma unroll 4
@@ -912,11 +913,12 @@ struct SrcCursor {
     template <bool TWO_FLOAT>
     __device__ int fill(const Cells& c, const int2* __restrict__ list, const int* __restrict__ seg_start,
                         const int* __restrict__ seg_end, const float4* __restrict__ xhi,
-                        const float4* __restrict__ xlo, int first, int lane, float4* th, float4* tl, bool& guard) {
+                        const float4* __restrict__ xlo, int first, int lane, int T, float4* th, float4* tl,
+                        bool& guard) {
         int n = 0;
         guard = false;
         if (cell < 0) return 0;  // exhausted
-        while (n < 32) {
+        while (n < T) {
             if (off == an) {  // next source cell
                 while (e == e1) {
                     cell = c.parent[cell];
@@ -931,10 +933,10 @@ struct SrcCursor {
                 contains = af <= first && first < af + an;
                 continue;
             }
-            const int k = min(32 - n, an - off);
-            if (lane < k) {
-                cp_async16(th + n + lane, xhi + af + off + lane);
-                if (TWO_FLOAT) cp_async16(tl + n + lane, xlo + af + off + lane);
+            const int k = min(T - n, an - off);
+            for (int q = lane; q < k; q += 32) {
+                cp_async16(th + n + q, xhi + af + off + q);
+                if (TWO_FLOAT) cp_async16(tl + n + q, xlo + af + off + q);
             }
             guard |= contains;
             n += k;
@@ -955,8 +957,8 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(const float4* _
                                                               const int* __restrict__ order, int nleaves,
                                                               unsigned* __restrict__ counter,
                                                               double* __restrict__ psi, double* __restrict__ acc) {
-    __shared__ __align__(16) float4 th_all[kP2PWarps][2][32];
-    __shared__ __align__(16) float4 tl_all[kP2PWarps][2][TWO_FLOAT ? 32 : 1];
+    __shared__ __align__(16) float4 th_all[kP2PWarps][2][kP2PTile];
+    __shared__ __align__(16) float4 tl_all[kP2PWarps][2][TWO_FLOAT ? kP2PTile : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (;;) {
         unsigned w = 0;
@@ -983,17 +985,17 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(const float4* _
             }
             ff aps = {0, 0}, aax = {0, 0}, aay = {0, 0}, aaz = {0, 0};
             float ps = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-            int since = 0;
             SrcCursor cur;
             cur.start(seg_start, seg_end, leaf);
             int b = 0;
             bool guard = false, guard_next = false;
-            int nt = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, xhi, xlo, first, lane, th_all[wid][0],
+            const int T = 32 * R;  // sources per tile: 32 for every replica
+            int nt = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, xhi, xlo, first, lane, T, th_all[wid][0],
                                          tl_all[wid][0], guard);
             cp_async_commit();
             while (nt > 0) {
                 // issue the next tile, then wait for the current one
-                const int nn = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, xhi, xlo, first, lane,
+                const int nn = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, xhi, xlo, first, lane, T,
                                                    th_all[wid][b ^ 1], tl_all[wid][b ^ 1], guard_next);
                 cp_async_commit();
                 cp_async_wait1();
@@ -1004,12 +1006,9 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(const float4* _
                 else
                     p2p_tile_r<TWO_FLOAT, false>(th_all[wid][b], tl_all[wid][TWO_FLOAT ? b : 0], nt, rep, R, bhx,
                                                  bhy, bhz, blx, bly, blz, ps, ax, ay, az);
-                since += 32;
-                if (since >= 32 * R) {  // fold the FP32 partials into the two-float sums every ~32 pairs
-                    ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
-                    ps = ax = ay = az = 0.f;
-                    since = 0;
-                }
+                // fold the FP32 partials (<= 32 pairs per lane) into the two-float sums
+                ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
+                ps = ax = ay = az = 0.f;
                 __syncwarp();  // every lane is done with tile b before it is refilled
                 b ^= 1;
                 nt = nn;
