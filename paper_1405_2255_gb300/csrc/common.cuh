@@ -36,6 +36,16 @@ __host__ __device__ inline int ncoef(int p) { return (p + 1) * (p + 1); }
 // index of (n, m), -n <= m <= n, in a (p+1)^2 array of real or complex coefficients
 __host__ __device__ inline int cix(int n, int m) { return n * n + n + m; }
 
+// t[k] = x^k for k = 0..n (n < 32), lane k forming its power by repeated products (the
+// rounding of a serial loop); the caller synchronises the warp before reading t
+__device__ inline void warp_pow_table(double x, int n, int lane, double* t) {
+    if (lane <= n) {
+        double v = 1.0;
+        for (int k = 0; k < lane; ++k) v *= x;
+        t[lane] = v;
+    }
+}
+
 // device status word bits (OR-ed by kernels, read by the host)
 enum : unsigned {
     kStatInvalid = 1u,      // NaN/Inf position or negative mass

@@ -268,7 +268,7 @@ template <int kRB>
 struct RoundsSmem {
     static constexpr int kRBLo = (kRB * kT64 + 31) / 32;  // FP64 terms per lane per batch
     int nco;
-    size_t Mh, Th, pi, thA, thB, res, outs, M64, T64, red, lowF, idx, terms, total;
+    size_t Mh, Th, pi, thA, thB, res, outs, M64, T64, red, lowF, idx, terms, pws, total;
     __host__ __device__ RoundsSmem(int p) {
         nco = (p + 1) * (p + 1);
         size_t o = 0;
@@ -290,6 +290,7 @@ struct RoundsSmem {
         lowF = take(8 * sizeof(cd));
         idx = take((size_t)nco);
         terms = take(sizeof(TermTab));
+        pws = take((kMaxP + 2) * sizeof(double));
         total = o;
     }
 };
@@ -367,6 +368,7 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
     cd* lowF = (cd*)(sm_raw + L.lowF);
     unsigned char* idx_n = sm_raw + L.idx;
     TermTab* terms = (TermTab*)(sm_raw + L.terms);
+    double* pws = (double*)(sm_raw + L.pws);  // sigma_B^-n
     for (int i = lane; i < nco; i += 32) idx_n[i] = c_idx_n[i];
     if (lane == 0) *terms = c_terms;
     __syncwarp();
@@ -504,12 +506,11 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
         }
         __syncwarp();
         double* out = part + (size_t)w * nco;
-        const double sinv = 1.0 / sigma;
+        warp_pow_table(1.0 / sigma, p + 1, lane, pws);
+        __syncwarp();
         for (int i = lane; i < nco; i += 32) {
             const int n = idx_n[i], m = i - n * n - n;
-            double sc = sinv;
-            for (int k = 0; k < n; ++k) sc *= sinv;
-            double v = outs[i] * sc;
+            double v = outs[i] * pws[n + 1];
             if (n <= kJ64) {
                 const cd lv = lowF[n * (n + 1) / 2 + (m < 0 ? -m : m)];
                 v += m >= 0 ? lv.re : lv.im;

@@ -117,15 +117,17 @@ __global__ void __launch_bounds__(kSplitWarps * 32) k_p2m_split(const d4* __rest
     for (int k = 0; k < 9; ++k) lo[k] = warp_sum(lo[k]);
     __syncwarp();
     double* out = M + (size_t)cell * nco;
+    __shared__ double pw_all[kSplitWarps][kMaxP + 1];
+    double* pw = pw_all[wid];
+    warp_pow_table(rho, p, lane, pw);
+    __syncwarp();
     if (lane == 0)
         for (int k = 0; k < 9 && k < nco; ++k) out[k] = lo[k];
     for (int i = 9 + lane; i < nco; i += 32) {
         int n = (int)sqrtf((float)i);
         while (n * n > i) --n;
         while ((n + 1) * (n + 1) <= i) ++n;
-        double s = 1.0;
-        for (int k = 0; k < n; ++k) s *= rho;
-        out[i] = (double)acc[i] * s;
+        out[i] = (double)acc[i] * pw[n];
     }
 }
 
@@ -165,13 +167,16 @@ __global__ void __launch_bounds__(kSplitWarps * 32) k_l2p_split(const d4* __rest
     const d4 s = cen[cell];
     const double rho = s.w;
     const double* Fr = F + (size_t)cell * nco;
+    __shared__ double pw_all[kSplitWarps][kMaxP + 1];
+    double* pw = pw_all[wid];
+    warp_pow_table(rho, p, lane, pw);
+    __syncwarp();
     for (int i = lane; i < nco; i += 32) {
         int n = (int)sqrtf((float)i);
         while (n * n > i) --n;
         while ((n + 1) * (n + 1) <= i) ++n;
         const cd v = load_real_storage(Fr, n, i - n * n - n);
-        double sc = 1.0;
-        for (int k = 0; k < n; ++k) sc *= rho;
+        const double sc = pw[n];
         Fh[i] = make_float2((float)(v.re * sc), (float)(v.im * sc));
         if (i < 16) F64[i] = v;
     }
@@ -340,6 +345,11 @@ __global__ void __launch_bounds__(128) k_m2m_split(Cells c, const d4* __restrict
     const d4 zp = cen[cell];
     const double rho = zp.w, inv = rho > 0 ? 1.0 / rho : 0.0;
     const int cnt = sched.cnt[lane];
+    __shared__ double pwi_all[4][kMaxP + 1], pwr_all[4][kMaxP + 1];
+    double *pwi = pwi_all[wid], *pwr = pwr_all[wid];  // rho^-n, rho^n
+    warp_pow_table(inv, p, lane, pwi);
+    warp_pow_table(rho, p, lane, pwr);
+    __syncwarp();
     float2 a32[MAXQ];
     cd a64[MAXQ];
 #pragma unroll
@@ -356,8 +366,7 @@ __global__ void __launch_bounds__(128) k_m2m_split(Cells c, const d4* __restrict
         for (int i = lane; i < nco; i += 32) {
             const int n = n_of(i);
             const cd v = load_real_storage(Md, n, i - n * n - n);
-            double sc = 1.0;
-            for (int k = 0; k < n; ++k) sc *= inv;
+            const double sc = pwi[n];
             Mt[i] = make_float2((float)(v.re * sc), (float)(v.im * sc));
             if (i < 9) M64[i] = v;
         }
@@ -395,8 +404,7 @@ __global__ void __launch_bounds__(128) k_m2m_split(Cells c, const d4* __restrict
             const int n = sched.n[lane][q], m = sched.m[lane][q];
             cd v = a64[q];
             if (n > 2) {
-                double sc = 1.0;
-                for (int k = 0; k < n; ++k) sc *= rho;
+                const double sc = pwr[n];
                 v = mkc((double)a32[q].x * sc, (double)a32[q].y * sc);
             }
             out[cix(n, m)] = v.re;
@@ -451,13 +459,17 @@ __global__ void __launch_bounds__(128) k_l2l_split(Cells c, const d4* __restrict
         return;
     }
     const double inv = 1.0 / rho;
+    __shared__ double pwi_all[4][kMaxP + 1], pwr_all[4][kMaxP + 1];
+    double *pwi = pwi_all[wid], *pwr = pwr_all[wid];  // rho^-n, rho^n
+    warp_pow_table(inv, p, lane, pwi);
+    warp_pow_table(rho, p, lane, pwr);
+    __syncwarp();
     const double vx = s.x - sp.x, vy = s.y - sp.y, vz = s.z - sp.z;
     if (lane <= p) upsilon_column_f(p, lane, (float)(vx * inv), (float)(vy * inv), (float)(vz * inv), Yh, true);
     for (int i = lane; i < nco; i += 32) {
         const int n = n_of(i);
         const cd v = load_real_storage(Fp, n, i - n * n - n);
-        double sc = 1.0;
-        for (int k = 0; k < n; ++k) sc *= rho;
+        const double sc = pwr[n];
         Fh[i] = make_float2((float)(v.re * sc), (float)(v.im * sc));
         if (i < 9) F64[i] = v;
     }
@@ -475,8 +487,7 @@ __global__ void __launch_bounds__(128) k_l2l_split(Cells c, const d4* __restrict
             const float2* yk = Fh + (n + k) * (n + k) + (n + k) + m;
             for (int l = -k; l <= k; ++l) cmacf(v32, xk[l], yk[l]);
         }
-        double sc = 1.0;
-        for (int k = 0; k < n; ++k) sc *= inv;
+        const double sc = pwi[n];
         out[cix(n, m)] += v64.re + (double)v32.x * sc;
         if (m) out[cix(n, -m)] += v64.im + (double)v32.y * sc;
     }
