@@ -188,6 +188,14 @@ def reference_arm(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) per launch of the dominant kernels, from one ncu capture of
+# the same workload and parameters (summaries and commands under profiles/); None for
+# any other configuration or once the kernel has changed since the capture
+MEASURED_TRAFFIC = {
+    ("plummer", 1000000, 12, 2.5e-7, 64, 4.0, "mixed"): {"k_p2p_mixed": 99.74e6, "k_m2l_rounds": 122.80e6},
+}
+
+
 def roofline(g, a, prec, phase, full):
     """Achieved vs peak of the dominant kernel: algorithmic flops of the run's own lists
     over its CUDA-event phase time averaged over the timed steps."""
@@ -204,8 +212,11 @@ def roofline(g, a, prec, phase, full):
     else:
         achieved = 20.0 * full["p2p_interactions"] / t_p2p / 1e12
         kern = "k_p2p_mixed (eq. 1, FP32 two-float)" if mixed else "k_p2p_fp64 (eq. 1)"
+    key = (a.workload, a.n, a.p, a.eps, a.leaf, a.c, a.precision)
+    traffic = MEASURED_TRAFFIC.get(key, {}).get(kern.split(" ")[0])
     return {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-            "frac": achieved / pk, "traffic": None, "peak_source": src,
+            "frac": achieved / pk, "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
+            "peak_source": src,
             "peak_loop_measured": loop, "frac_of_loop": achieved / loop,
             "phase_share": {"m2l": t_m2l / (float(np.mean([s["t_total"] for s in phase])) * 1e-3),
                             "p2p": t_p2p / (float(np.mean([s["t_total"] for s in phase])) * 1e-3)}}
