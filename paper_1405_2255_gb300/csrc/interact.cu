@@ -268,7 +268,7 @@ template <int kRB>
 struct RoundsSmem {
     static constexpr int kRBLo = (kRB * kT64 + 31) / 32;  // FP64 terms per lane per batch
     int nco;
-    size_t Mh, Th, pi, thA, thB, res, outs, M64, T64, red, lowF, idx, terms, pws, total;
+    size_t Mh, Th, pi, thA, thB, res, outs, unit, M64, T64, red, lowF, idx, terms, pws, total;
     __host__ __device__ RoundsSmem(int p) {
         nco = (p + 1) * (p + 1);
         size_t o = 0;
@@ -283,7 +283,8 @@ struct RoundsSmem {
         thA = take(kRB * (kMaxP + 2) * sizeof(float));
         thB = take(kRB * (kMaxP + 2) * sizeof(float));
         res = take((size_t)kRB * (kMaxP + 1) * sizeof(float2));
-        outs = take((size_t)nco * sizeof(double));
+        outs = take((size_t)nco * sizeof(float));
+        unit = take(kRB * sizeof(float4));
         M64 = take(kRB * kN64 * sizeof(cd));
         T64 = take(kRB * kN64 * sizeof(cd));
         red = take(32 * kRBLo * sizeof(cd));
@@ -361,7 +362,8 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
     float* thA = (float*)(sm_raw + L.thA);    // [kRB][kMaxP+2]: (rho_A/r)^k
     float* thB = (float*)(sm_raw + L.thB);    // [kRB][kMaxP+2]: (sigma_B/r)^k
     float2* res = (float2*)(sm_raw + L.res);  // [kRB * (n+1)] results of one order
-    double* outs = (double*)(sm_raw + L.outs);
+    float* outs = (float*)(sm_raw + L.outs);     // FP32 part of the item's outputs
+    float4* unit = (float4*)(sm_raw + L.unit);   // [kRB] unit vectors of the batch's pairs
     cd* M64 = (cd*)(sm_raw + L.M64);
     cd* T64 = (cd*)(sm_raw + L.T64);
     cd* red = (cd*)(sm_raw + L.red);
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
             }
             sigma = 0.5 * warp_min(rmin);
         }
-        for (int i = lane; i < nco; i += 32) outs[i] = 0.0;
+        for (int i = lane; i < nco; i += 32) outs[i] = 0.f;
         cd lo[kRBLo];
 #pragma unroll
         for (int i = 0; i < kRBLo; ++i) lo[i] = mkc(0.0, 0.0);
@@ -409,6 +411,7 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
                 const double x = sB.x - zA.x, y = sB.y - zA.y, z = sB.z - zA.z;
                 const double rinv = rsqrt(x * x + y * y + z * z);
                 pi[lane] = PairInfo{x, y, z, rinv};
+                unit[lane] = make_float4((float)(x * rinv), (float)(y * rinv), (float)(z * rinv), 0.f);
                 const float ta = (float)(zA.w * rinv), tb = (float)(sigma * rinv);
                 float a = 1.f, b = 1.f;
                 for (int k = 0; k <= p + 1; ++k) {
@@ -443,9 +446,8 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
             // FP32 Theta on the unit vectors: one column (pair, m) per lane and round
             for (int t = lane; t < nb * (p + 1); t += 32) {
                 const int b = t / (p + 1), m = t % (p + 1);
-                const PairInfo q = pi[b];
-                theta_column_unit_f2(p, m, (float)(q.x * q.rinv), (float)(q.y * q.rinv), (float)(q.z * q.rinv),
-                                     Th + b * nco);
+                const float4 q = unit[b];
+                theta_column_unit_f2(p, m, q.x, q.y, q.z, Th + b * nco);
             }
             __syncwarp();
             // FP64 terms of orders n + k <= kJ64, spread over the lanes
@@ -484,8 +486,8 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
                         t.x += v.x;
                         t.y += v.y;
                     }
-                    outs[n * n + n + m] += (double)t.x;
-                    if (m) outs[n * n + n - m] += (double)t.y;
+                    outs[n * n + n + m] += t.x;
+                    if (m) outs[n * n + n - m] += t.y;
                 }
                 __syncwarp();
             }
@@ -510,7 +512,7 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
         __syncwarp();
         for (int i = lane; i < nco; i += 32) {
             const int n = idx_n[i], m = i - n * n - n;
-            double v = outs[i] * pws[n + 1];
+            double v = (double)outs[i] * pws[n + 1];
             if (n <= kJ64) {
                 const cd lv = lowF[n * (n + 1) / 2 + (m < 0 ? -m : m)];
                 v += m >= 0 ? lv.re : lv.im;
