@@ -509,10 +509,6 @@ __device__ inline float dist3f_dev(const float a[3], const float b[3]) {
     float dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
     return sqrtf(dx * dx + dy * dy + dz * dz);
 }
-__device__ inline double dist3_dev(const double a[3], const double b[3]) {
-    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
-    return sqrt(dx * dx + dy * dy + dz * dz);
-}
 
 // Welzl's b_md(empty, R): the smallest ball with the support points on its boundary
 __device__ void trivial_ball_dev(int nr, const float (*R)[3], float c[3], float& rad) {
@@ -681,29 +677,33 @@ __global__ void __launch_bounds__(kGeoWarps * 32) k_leaf_geometry(const d4* __re
     float cf[3], radf;
     meb_points_warp(P, count, cf, radf, lane);
     double s[3] = {P.o[0] + (double)cf[0], P.o[1] + (double)cf[1], P.o[2] + (double)cf[2]};
-    double rmax = 0, m = 0, mx[3] = {0, 0, 0};
+    // radii as the square root of the largest squared distance (sqrt is monotonic and
+    // correctly rounded, so this equals the largest distance)
+    double r2max = 0, m = 0, mx[3] = {0, 0, 0};
     for (int i = lane; i < count; i += 32) {
         double p[3];
         ld3(X, i, p);
-        double r = dist3_dev(p, s);
-        if (r > rmax) rmax = r;
+        const double dx = p[0] - s[0], dy = p[1] - s[1], dz = p[2] - s[2];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 > r2max) r2max = r2;
         double w = X[i].w;
         m += w;
         for (int k = 0; k < 3; ++k) mx[k] += w * p[k];
     }
-    rmax = warp_max(rmax);
+    const double rmax = sqrt(warp_max(r2max));
     m = warp_sum(m);
     for (int k = 0; k < 3; ++k) mx[k] = warp_sum(mx[k]);
     double com[3];
     for (int k = 0; k < 3; ++k) com[k] = (m > 0) ? mx[k] / m : s[k];
-    double rc = 0;
+    double rc2 = 0;
     for (int i = lane; i < count; i += 32) {
         double p[3];
         ld3(X, i, p);
-        double r = dist3_dev(p, com);
-        if (r > rc) rc = r;
+        const double dx = p[0] - com[0], dy = p[1] - com[1], dz = p[2] - com[2];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 > rc2) rc2 = r2;
     }
-    rc = warp_max(rc);
+    const double rc = sqrt(warp_max(rc2));
     if (lane == 0) {
         c.sr[cell] = mk4(s[0], s[1], s[2], rmax);
         c.cr[cell] = mk4(com[0], com[1], com[2], rc);
