@@ -386,7 +386,7 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     if (ctx->prm.precision == FMM_PREC_MIXED)
     {
         TRY(ensure(ctx->p2p_tmp, p2p_tmp_bytes(ctx->nleaves)));
-        launch_p2p_mixed(P<d4>(ctx->xm), P<float4>(ctx->xhi), P<float4>(ctx->xlo), c, P<int2>(ctx->est_p2p),
+        launch_p2p_mixed(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), ctx->n, c, P<int2>(ctx->est_p2p),
                          P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
                          P<double>(ctx->psi_near), P<double>(ctx->acc_near), false, ctx->p2p_tmp.p, s);
     }
@@ -455,7 +455,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     if (prm.precision == FMM_PREC_MIXED) {
         TRY(ensure(ctx->xhi, sizeof(float4) * n));
         TRY(ensure(ctx->xlo, sizeof(float4) * n));
-        launch_split_positions(P<d4>(ctx->xm), n, P<float4>(ctx->xhi), P<float4>(ctx->xlo), s);
+        launch_split_positions(P<d4>(ctx->xm), n, P<float>(ctx->xhi), P<float>(ctx->xlo), s);
     }
 
     // A7: acceleration scale for the MAC and its per-cell minimum
@@ -522,7 +522,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     if (prm.precision == FMM_PREC_MIXED)
     {
         TRY(ensure(ctx->p2p_tmp, p2p_tmp_bytes(ctx->nleaves)));
-        launch_p2p_mixed(P<d4>(ctx->xm), P<float4>(ctx->xhi), P<float4>(ctx->xlo), c, P<int2>(ctx->p2p),
+        launch_p2p_mixed(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), ctx->n, c, P<int2>(ctx->p2p),
                          P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
                          P<double>(ctx->psi_near), P<double>(ctx->acc_near), prm.p2p_two_float != 0,
                          ctx->p2p_tmp.p, s);

@@ -799,16 +799,23 @@ void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_sta
 // dx = (hi_a - hi_b) + (lo_a - lo_b) keeps its relative accuracy even for close
 // pairs.  Pair terms are FP32; the FP32 sums of every ~32 pairs are added to
 // two-float accumulators (TwoSum), so the sum over tiles is compensated.
-__global__ void k_split_positions(const d4* __restrict__ xm, int n, float4* __restrict__ xhi, float4* __restrict__ xlo) {
+// Layout (structure of arrays, n floats each): hi = [X | Y | Z | W] (high parts of the
+// position and the mass), lo = [XL | YL | ZL] (low parts).
+__global__ void k_split_positions(const d4* __restrict__ xm, int n, float* __restrict__ hi, float* __restrict__ lo) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         d4 v = xm[i];
-        float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
-        xhi[i] = make_float4(hx, hy, hz, (float)v.w);
-        xlo[i] = make_float4((float)(v.x - (double)hx), (float)(v.y - (double)hy), (float)(v.z - (double)hz), 0.f);
+        const float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
+        hi[i] = hx;
+        hi[n + i] = hy;
+        hi[2 * (size_t)n + i] = hz;
+        hi[3 * (size_t)n + i] = (float)v.w;
+        lo[i] = (float)(v.x - (double)hx);
+        lo[n + i] = (float)(v.y - (double)hy);
+        lo[2 * (size_t)n + i] = (float)(v.z - (double)hz);
     }
 }
-void launch_split_positions(const d4* xm, int n, float4* xhi, float4* xlo, cudaStream_t s) {
-    if (n > 0) k_split_positions<<<grid_for(n, 256), 256, 0, s>>>(xm, n, xhi, xlo); note_launch();
+void launch_split_positions(const d4* xm, int n, float* hi, float* lo, cudaStream_t s) {
+    if (n > 0) k_split_positions<<<grid_for(n, 256), 256, 0, s>>>(xm, n, hi, lo); note_launch();
 }
 
 struct ff {
@@ -834,75 +841,130 @@ __device__ inline void ff_acc(ff& a, float v) {
     a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
 }
 
-// The mixed kernel streams the sink's sources through warp-private tiles of 32 that
-// are filled from consecutive source cells (so small cells do not leave a tile half
-// empty).  Positions are two-float copies of the FP64 positions (hi = fl32(x),
-// lo = fl32(x - hi)); dx = (hi_a - hi_b) + (lo_a - lo_b) then carries one FP32
-// rounding relative to |dx| itself, not to |x|, so no per-leaf change of origin is
-// needed and a tile is filled by plain 16-byte copies (cp.async), double buffered so
-// that the next tile's loads overlap the current tile's pairs.  A chunk of n_s <= 32
-// sinks is replicated R = 1, 2 or 4 times across the warp (lane = r * (32/R) +
-// sink), replica r taking every R-th source of a tile; the replicas' partial sums
-// are added at the end.  Tiles that hold a source cell containing the sink leaf
-// skip the r = 0 pairs (the sink itself and coincident particles); all other tiles
-// need no test, since particles of different leaves are never coincident.
-// TWO_FLOAT = false uses the high parts alone (the low-order scale estimate).
-template <bool TWO_FLOAT, bool GUARD>
-__device__ __forceinline__ void p2p_pair(const float4* __restrict__ th, const float4* __restrict__ tl, int j,
-                                         float bhx, float bhy, float bhz, float blx, float bly, float blz,
-                                         float& ps, float& ax, float& ay, float& az) {
-    const float4 qh = th[j];
-    float dx = qh.x - bhx, dy = qh.y - bhy, dz = qh.z - bhz;
-    if (TWO_FLOAT) {
-        const float4 ql = tl[j];
-        dx += ql.x - blx;
-        dy += ql.y - bly;
-        dz += ql.z - blz;
-    }
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float rinv = rsqrtf(r2);
-    if (GUARD) rinv = r2 > 0.f ? rinv : 0.f;
-    const float qm = qh.w * rinv;
-    const float q3 = qm * rinv * rinv;
-    ps += qm;
-    ax = fmaf(q3, dx, ax);
-    ay = fmaf(q3, dy, ay);
-    az = fmaf(q3, dz, az);
+// The mixed kernel streams the sink's sources through warp-private tiles filled from
+// consecutive source cells (so small cells do not leave a tile half empty).  dx =
+// (hi_a - hi_b) + (lo_a - lo_b) carries one FP32 rounding relative to |dx| itself, so
+// no per-leaf change of origin is needed: a tile is filled by plain 4-byte copies
+// (cp.async) of the structure-of-arrays positions, double buffered so that the next
+// tile's loads overlap the current tile's pairs.  The pair terms run two sources at a
+// time in packed FP32 (f32x2) arithmetic, four sources per shared-memory load.  A chunk
+// of s <= 32 sinks is replicated R = 1, 2 or 4 times across the warp (lane = r * (32/R)
+// + sink), replica r taking every R-th group of four sources; the replicas' sums are
+// added at the end.  Tiles that hold a source cell containing the sink leaf skip the
+// r = 0 pairs (the sink itself and coincident particles); all other tiles need no
+// test, since particles of different leaves are never coincident.  A partial tile is
+// padded to a whole group with massless sources far away.  TWO_FLOAT = false uses the
+// high parts alone (the low-order scale estimate).
+typedef unsigned long long f2;  // two packed floats
+__device__ __forceinline__ f2 f2_pack(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
 }
-// replica r0 of R takes sources r0, r0 + R, ... of a tile of nt; a full tile has a
-// trip count known at compile time
-template <bool TWO_FLOAT, bool GUARD, int R>
-__device__ __forceinline__ void p2p_tile(const float4* __restrict__ th, const float4* __restrict__ tl, int nt, int r0,
-                                         float bhx, float bhy, float bhz, float blx, float bly, float blz,
-                                         float& ps, float& ax, float& ay, float& az) {
-    if (nt == 32 * R) {  // a full tile: 32 sources per replica
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k)
-            p2p_pair<TWO_FLOAT, GUARD>(th, tl, r0 + R * k, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
-    } else {
-#pragma unroll 4
-        for (int j = r0; j < nt; j += R)
-            p2p_pair<TWO_FLOAT, GUARD>(th, tl, j, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
-    }
+__device__ __forceinline__ void f2_unpack(f2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
 }
-template <bool TWO_FLOAT, bool GUARD>
-__device__ __forceinline__ void p2p_tile_r(const float4* __restrict__ th, const float4* __restrict__ tl, int nt,
-                                           int r0, int R, float bhx, float bhy, float bhz, float blx, float bly,
-                                           float blz, float& ps, float& ax, float& ay, float& az) {
-    if (R == 1) p2p_tile<TWO_FLOAT, GUARD, 1>(th, tl, nt, r0, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
-    else if (R == 2) p2p_tile<TWO_FLOAT, GUARD, 2>(th, tl, nt, r0, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
-    else p2p_tile<TWO_FLOAT, GUARD, 4>(th, tl, nt, r0, bhx, bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+// the sink of a lane, its coordinates duplicated in both halves
+struct SinkPk {
+    f2 hx, hy, hz, lx, ly, lz;
+};
+struct AccPk {
+    f2 ps, ax, ay, az;
+};
+
+// two sources (x, y, z, w high parts; x, y, z low parts as packed pairs) against the sink
+template <bool TWO_FLOAT, bool GUARD>
+__device__ __forceinline__ void p2p_pair2(f2 X, f2 Y, f2 Z, f2 W, f2 XL, f2 YL, f2 ZL, const SinkPk& b, AccPk& a) {
+    f2 dx = f2_sub(X, b.hx), dy = f2_sub(Y, b.hy), dz = f2_sub(Z, b.hz);
+    if (TWO_FLOAT) {
+        dx = f2_add(dx, f2_sub(XL, b.lx));
+        dy = f2_add(dy, f2_sub(YL, b.ly));
+        dz = f2_add(dz, f2_sub(ZL, b.lz));
+    }
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float r2a, r2b;
+    f2_unpack(r2, r2a, r2b);
+    float ia = rsqrtf(r2a), ib = rsqrtf(r2b);
+    if (GUARD) {
+        ia = r2a > 0.f ? ia : 0.f;
+        ib = r2b > 0.f ? ib : 0.f;
+    }
+    const f2 rinv = f2_pack(ia, ib);
+    const f2 qm = f2_mul(W, rinv);
+    const f2 q3 = f2_mul(qm, f2_mul(rinv, rinv));
+    a.ps = f2_add(a.ps, qm);
+    a.ax = f2_fma(q3, dx, a.ax);
+    a.ay = f2_fma(q3, dy, a.ay);
+    a.az = f2_fma(q3, dz, a.az);
+}
+
+// one group of four sources of the tile (index g) against the sink
+template <bool TWO_FLOAT, bool GUARD>
+__device__ __forceinline__ void p2p_group(const float* __restrict__ T, int g, const SinkPk& b, AccPk& a) {
+    const float4 X = ((const float4*)(T + 0 * kP2PTile))[g], Y = ((const float4*)(T + 1 * kP2PTile))[g],
+                 Z = ((const float4*)(T + 2 * kP2PTile))[g], W = ((const float4*)(T + 3 * kP2PTile))[g];
+    float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), YL = XL, ZL = XL;
+    if (TWO_FLOAT) {
+        XL = ((const float4*)(T + 4 * kP2PTile))[g];
+        YL = ((const float4*)(T + 5 * kP2PTile))[g];
+        ZL = ((const float4*)(T + 6 * kP2PTile))[g];
+    }
+    p2p_pair2<TWO_FLOAT, GUARD>(f2_pack(X.x, X.y), f2_pack(Y.x, Y.y), f2_pack(Z.x, Z.y), f2_pack(W.x, W.y),
+                                f2_pack(XL.x, XL.y), f2_pack(YL.x, YL.y), f2_pack(ZL.x, ZL.y), b, a);
+    p2p_pair2<TWO_FLOAT, GUARD>(f2_pack(X.z, X.w), f2_pack(Y.z, Y.w), f2_pack(Z.z, Z.w), f2_pack(W.z, W.w),
+                                f2_pack(XL.z, XL.w), f2_pack(YL.z, YL.w), f2_pack(ZL.z, ZL.w), b, a);
+}
+
+// replica r0 of R takes groups r0, r0 + R, ... of a tile of ng groups; a full tile
+// (8 groups per replica) has a trip count known at compile time
+template <bool TWO_FLOAT, bool GUARD, int R>
+__device__ __forceinline__ void p2p_tile(const float* __restrict__ T, int ng, int r0, const SinkPk& b, AccPk& a) {
+    if (ng == 8 * R) {
+#pragma unroll 2
+        for (int k = 0; k < 8; ++k) p2p_group<TWO_FLOAT, GUARD>(T, r0 + R * k, b, a);
+    } else {
+        for (int g = r0; g < ng; g += R) p2p_group<TWO_FLOAT, GUARD>(T, g, b, a);
+    }
+}
+template <bool TWO_FLOAT, bool GUARD>
+__device__ __forceinline__ void p2p_tile_r(const float* __restrict__ T, int ng, int r0, int R, const SinkPk& b,
+                                           AccPk& a) {
+    if (R == 1) p2p_tile<TWO_FLOAT, GUARD, 1>(T, ng, r0, b, a);
+    else if (R == 2) p2p_tile<TWO_FLOAT, GUARD, 2>(T, ng, r0, b, a);
+    else p2p_tile<TWO_FLOAT, GUARD, 4>(T, ng, r0, b, a);
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // The sources of one sink leaf: the entries of its own P2P segment, then those of
-// each ancestor's segment; fill() copies the next <= 32 source particles into a tile.
+// each ancestor's segment; fill() copies the next <= T source particles into a tile
+// (structure of arrays: X, Y, Z, W[, XL, YL, ZL] at stride kP2PTile).
 struct SrcCursor {
     int cell, e, e1, af, an, off;
     bool contains;
@@ -915,17 +977,17 @@ struct SrcCursor {
     }
     template <bool TWO_FLOAT>
     __device__ int fill(const Cells& c, const int2* __restrict__ list, const int* __restrict__ seg_start,
-                        const int* __restrict__ seg_end, const float4* __restrict__ xhi,
-                        const float4* __restrict__ xlo, int first, int lane, int T, float4* th, float4* tl,
+                        const int* __restrict__ seg_end, const float* __restrict__ hi,
+                        const float* __restrict__ lo, size_t n, int first, int lane, int T, float* tile,
                         bool& guard) {
-        int n = 0;
+        int m = 0;
         guard = false;
         if (cell < 0) return 0;  // exhausted
-        while (n < T) {
+        while (m < T) {
             if (off == an) {  // next source cell
                 while (e == e1) {
                     cell = c.parent[cell];
-                    if (cell < 0) return n;
+                    if (cell < 0) return m;
                     e = seg_start[cell];
                     e1 = seg_end[cell];
                 }
@@ -936,33 +998,39 @@ struct SrcCursor {
                 contains = af <= first && first < af + an;
                 continue;
             }
-            const int k = min(T - n, an - off);
+            const int k = min(T - m, an - off);
             for (int q = lane; q < k; q += 32) {
-                cp_async16(th + n + q, xhi + af + off + q);
-                if (TWO_FLOAT) cp_async16(tl + n + q, xlo + af + off + q);
+                const size_t j = (size_t)af + off + q;
+                float* t = tile + m + q;
+#pragma unroll
+                for (int d = 0; d < 4; ++d) cp_async4(t + d * kP2PTile, hi + d * n + j);
+                if (TWO_FLOAT)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) cp_async4(t + (4 + d) * kP2PTile, lo + d * n + j);
             }
             guard |= contains;
-            n += k;
+            m += k;
             off += k;
         }
-        return n;
+        return m;
     }
 };
 
 // One warp per sink leaf, leaves taken in decreasing order of work from an atomic
-// counter.
+// counter; sources come from the P2P segments of the leaf and of its ancestors.
 template <bool TWO_FLOAT>
-__global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(const float4* __restrict__ xhi,
-                                                              const float4* __restrict__ xlo, Cells c,
-                                                              const int2* __restrict__ list,
-                                                              const int* __restrict__ seg_start,
-                                                              const int* __restrict__ seg_end,
-                                                              const int* __restrict__ order, int nleaves,
-                                                              unsigned* __restrict__ counter,
-                                                              double* __restrict__ psi, double* __restrict__ acc) {
-    __shared__ __align__(16) float4 th_all[kP2PWarps][2][kP2PTile];
-    __shared__ __align__(16) float4 tl_all[kP2PWarps][2][TWO_FLOAT ? kP2PTile : 1];
+__global__ void __launch_bounds__(kP2PWarps * 32, 4) k_p2p_mixed(const float* __restrict__ hi,
+                                                                 const float* __restrict__ lo, int n, Cells c,
+                                                                 const int2* __restrict__ list,
+                                                                 const int* __restrict__ seg_start,
+                                                                 const int* __restrict__ seg_end,
+                                                                 const int* __restrict__ order, int nleaves,
+                                                                 unsigned* __restrict__ counter,
+                                                                 double* __restrict__ psi, double* __restrict__ acc) {
+    constexpr int NA = TWO_FLOAT ? 7 : 4;  // arrays per tile
+    __shared__ __align__(16) float tiles[kP2PWarps][2][NA * kP2PTile];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t nn = (size_t)n;
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(counter, 1u);
@@ -979,45 +1047,59 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(const float4* _
             const int i = first + s0 + sink;
             float bhx = 0, bhy = 0, bhz = 0, blx = 0, bly = 0, blz = 0;
             if (active) {
-                const float4 h = xhi[i];
-                bhx = h.x; bhy = h.y; bhz = h.z;
+                bhx = hi[i];
+                bhy = hi[nn + i];
+                bhz = hi[2 * nn + i];
                 if (TWO_FLOAT) {
-                    const float4 l = xlo[i];
-                    blx = l.x; bly = l.y; blz = l.z;
+                    blx = lo[i];
+                    bly = lo[nn + i];
+                    blz = lo[2 * nn + i];
                 }
             }
+            const SinkPk b{f2_pack(bhx, bhx), f2_pack(bhy, bhy), f2_pack(bhz, bhz),
+                           f2_pack(blx, blx), f2_pack(bly, bly), f2_pack(blz, blz)};
+            const f2 zero = f2_pack(0.f, 0.f);
+            AccPk a{zero, zero, zero, zero};
             ff aps = {0, 0}, aax = {0, 0}, aay = {0, 0}, aaz = {0, 0};
-            float ps = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
             SrcCursor cur;
             cur.start(seg_start, seg_end, leaf);
-            int b = 0;
+            const int T = 32 * R;  // sources per tile: eight groups of four for every replica
+            int bb = 0;
             bool guard = false, guard_next = false;
-            const int T = 32 * R;  // sources per tile: 32 for every replica
-            int nt = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, xhi, xlo, first, lane, T, th_all[wid][0],
-                                         tl_all[wid][0], guard);
+            int nt = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, hi, lo, nn, first, lane, T, tiles[wid][0],
+                                         guard);
             cp_async_commit();
             while (nt > 0) {
                 // issue the next tile, then wait for the current one
-                const int nn = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, xhi, xlo, first, lane, T,
-                                                   th_all[wid][b ^ 1], tl_all[wid][b ^ 1], guard_next);
+                const int nx = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, hi, lo, nn, first, lane, T,
+                                                   tiles[wid][bb ^ 1], guard_next);
                 cp_async_commit();
                 cp_async_wait1();
+                float* tile = tiles[wid][bb];
+                const int ng = (nt + 3) >> 2;
+                if (lane < 4 * ng - nt) {  // pad to whole groups: massless, far away
+                    float* t = tile + nt + lane;
+                    t[0] = 1e15f;
+                    t[kP2PTile] = 1e15f;
+                    t[2 * kP2PTile] = 1e15f;
+                    t[3 * kP2PTile] = 0.f;
+                    if (TWO_FLOAT) t[4 * kP2PTile] = t[5 * kP2PTile] = t[6 * kP2PTile] = 0.f;
+                }
                 __syncwarp();
-                if (guard)
-                    p2p_tile_r<TWO_FLOAT, true>(th_all[wid][b], tl_all[wid][TWO_FLOAT ? b : 0], nt, rep, R, bhx, bhy,
-                                                bhz, blx, bly, blz, ps, ax, ay, az);
-                else
-                    p2p_tile_r<TWO_FLOAT, false>(th_all[wid][b], tl_all[wid][TWO_FLOAT ? b : 0], nt, rep, R, bhx,
-                                                 bhy, bhz, blx, bly, blz, ps, ax, ay, az);
+                if (guard) p2p_tile_r<TWO_FLOAT, true>(tile, ng, rep, R, b, a);
+                else p2p_tile_r<TWO_FLOAT, false>(tile, ng, rep, R, b, a);
                 // fold the FP32 partials (<= 32 pairs per lane) into the two-float sums
-                ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
-                ps = ax = ay = az = 0.f;
-                __syncwarp();  // every lane is done with tile b before it is refilled
-                b ^= 1;
-                nt = nn;
+                float u0, u1;
+                f2_unpack(a.ps, u0, u1); ff_acc(aps, u0 + u1);
+                f2_unpack(a.ax, u0, u1); ff_acc(aax, u0 + u1);
+                f2_unpack(a.ay, u0, u1); ff_acc(aay, u0 + u1);
+                f2_unpack(a.az, u0, u1); ff_acc(aaz, u0 + u1);
+                a = AccPk{zero, zero, zero, zero};
+                __syncwarp();  // every lane is done with the tile before it is refilled
+                bb ^= 1;
+                nt = nx;
                 guard = guard_next;
             }
-            ff_acc(aps, ps); ff_acc(aax, ax); ff_acc(aay, ay); ff_acc(aaz, az);
             // add the replicas' partial sums (lanes sink, sink + S, ...)
             for (int o = S; o < 32; o <<= 1) {
                 ff_add_shfl(aps, o); ff_add_shfl(aax, o); ff_add_shfl(aay, o); ff_add_shfl(aaz, o);
@@ -1093,7 +1175,7 @@ size_t p2p_tmp_bytes(int nleaves) {
     return n * (2 * sizeof(uint64_t) + 3 * sizeof(int)) + radix_tmp_ints(n) * sizeof(int) + 512;
 }
 
-void launch_p2p_mixed(const d4* /*xm*/, const float4* xhi, const float4* xlo, Cells c, const int2* list,
+void launch_p2p_mixed(const d4* /*xm*/, const float* hi, const float* lo, int n, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* psi,
                       double* acc, bool two_float, void* tmp, cudaStream_t s) {
     if (nleaves <= 0) return;
@@ -1115,11 +1197,11 @@ void launch_p2p_mixed(const d4* /*xm*/, const float4* xhi, const float4* xlo, Ce
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (two_float) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_p2p_mixed<true>, kP2PWarps * 32, 0);
-        k_p2p_mixed<true><<<nsm * (bps > 0 ? bps : 1), kP2PWarps * 32, 0, s>>>(xhi, xlo, c, list, seg_start, seg_end,
+        k_p2p_mixed<true><<<nsm * (bps > 0 ? bps : 1), kP2PWarps * 32, 0, s>>>(hi, lo, n, c, list, seg_start, seg_end,
                                                                              order, nleaves, counter, psi, acc);
     } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_p2p_mixed<false>, kP2PWarps * 32, 0);
-        k_p2p_mixed<false><<<nsm * (bps > 0 ? bps : 1), kP2PWarps * 32, 0, s>>>(xhi, xlo, c, list, seg_start,
+        k_p2p_mixed<false><<<nsm * (bps > 0 ? bps : 1), kP2PWarps * 32, 0, s>>>(hi, lo, n, c, list, seg_start,
                                                                               seg_end, order, nleaves, counter, psi,
                                                                               acc);
     }

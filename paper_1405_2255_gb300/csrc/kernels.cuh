@@ -138,14 +138,16 @@ void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_sta
                      const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc, cudaStream_t s);
 // two_float: dx from two-float leaf-relative positions; otherwise from their FP32 high parts
 size_t p2p_tmp_bytes(int nleaves);
-void launch_p2p_mixed(const d4* xm, const float4* xhi, const float4* xlo, Cells c, const int2* list,
+void launch_p2p_mixed(const d4* xm, const float* hi, const float* lo, int n, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves,
                       double* psi, double* acc, bool two_float, void* tmp, cudaStream_t s);
 // ordered pairs of distinct particles at distance 0 (sorted keys and positions); with
 // an ensemble (off != nullptr) only pairs inside one system count
 void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s,
                        const int* off = nullptr, int nsys = 0);
-void launch_split_positions(const d4* xm, int n, float4* xhi, float4* xlo, cudaStream_t s);
+// two-float positions in structure-of-arrays form: hi = [X | Y | Z | W] (4n floats),
+// lo = [XL | YL | ZL] (3n floats)
+void launch_split_positions(const d4* xm, int n, float* hi, float* lo, cudaStream_t s);
 // low-order f estimate (p = 0, 1/r^2 kernel): M2L, pass-down, P2P, evaluation
 void launch_f_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* Ff,
                   cudaStream_t s);

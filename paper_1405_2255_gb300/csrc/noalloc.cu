@@ -241,8 +241,8 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     double* psi_near = A.take<double>(n);
     double* acc_near = A.take<double>(3 * (size_t)n);
     double* scale = A.take<double>(n);
-    float4* xhi = A.take<float4>(n);
-    float4* xlo = A.take<float4>(n);
+    float* xhi = (float*)A.take<float4>(n);  // 4n floats: X | Y | Z | W
+    float* xlo = (float*)A.take<float4>(n);  // 3n floats used: XL | YL | ZL
     r.front0 = A.take<int2>(kFrontCap);
     r.front1 = A.take<int2>(kFrontCap);
     int2* m2l = A.take<int2>(kListCap);
@@ -295,7 +295,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
             for (int L = 1; L < nl; ++L) launch_l2l_level(r.c, r.c.cr, r.lev[L], r.lev[L + 1], 1, F1, s);
             launch_l2p(r.xm, r.c, r.c.cr, r.leaves, r.nleaves, 1, F1, psi_far, acc_far, s);
             if (prm.precision == FMM_PREC_MIXED)
-                launch_p2p_mixed(r.xm, xhi, xlo, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near,
+                launch_p2p_mixed(r.xm, xhi, xlo, n, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near,
                                  acc_near, false, p2p_tmp, s);
             else
                 launch_p2p_fp64(r.xm, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
@@ -344,7 +344,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     sort_pairs_by_sink(p2p, np, nc, r.sort_tmp, s);
     launch_segments(p2p, np, nc, seg_start, seg_end, s);
     if (prm.precision == FMM_PREC_MIXED)
-        launch_p2p_mixed(r.xm, xhi, xlo, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near,
+        launch_p2p_mixed(r.xm, xhi, xlo, n, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near,
                          prm.p2p_two_float != 0, p2p_tmp, s);
     else
         launch_p2p_fp64(r.xm, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
