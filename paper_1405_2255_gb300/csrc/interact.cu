@@ -1019,7 +1019,7 @@ struct SrcCursor {
 // One warp per sink leaf, leaves taken in decreasing order of work from an atomic
 // counter; sources come from the P2P segments of the leaf and of its ancestors.
 template <bool TWO_FLOAT>
-__global__ void __launch_bounds__(kP2PWarps * 32, 4) k_p2p_mixed(const float* __restrict__ hi,
+__global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float* __restrict__ hi,
                                                                  const float* __restrict__ lo, int n, Cells c,
                                                                  const int2* __restrict__ list,
                                                                  const int* __restrict__ seg_start,
