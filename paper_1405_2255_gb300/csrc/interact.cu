@@ -944,6 +944,7 @@ __device__ __forceinline__ void p2p_tile(const float* __restrict__ T, int ng, in
 #pragma unroll 2
         for (int k = 0; k < 8; ++k) p2p_group<TWO_FLOAT, GUARD>(T, r0 + R * k, b, a);
     } else {
+#pragma unroll 1
         for (int g = r0; g < ng; g += R) p2p_group<TWO_FLOAT, GUARD>(T, g, b, a);
     }
 }
