@@ -326,39 +326,43 @@ __device__ inline int n_of(int i) {
 // ---------------------------------------------------------------- M2M
 // M_n^m(z') = sum_{k<=n} sum_l Upsilon_k^l(z - z') M_{n-k}^{m-l}(z): outputs n <= 2 in FP64,
 // outputs n >= 3 in FP32 as Mhat_n = M_n / rho'^n = sum Uhat_k Mt_{n-k} with
-// Uhat_k = Upsilon_k((z - z')/rho'), Mt_j = M_j(z) / rho'^j.  One warp per parent.
+// Uhat_k = Upsilon_k((z - z')/rho'), Mt_j = M_j(z) / rho'^j.  One block per parent and one
+// warp per daughter; the daughters' contributions are then summed in daughter order.
+constexpr int kM2MWarps = 8;
+__host__ __device__ inline size_t m2m_warp_bytes(int p) {
+    return ((size_t)2 * ncoef(p) * sizeof(float2) + 18 * sizeof(cd) + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t m2m_smem_bytes(int p) {
+    const size_t nout = (size_t)(p + 1) * (p + 2) / 2;
+    return kM2MWarps * m2m_warp_bytes(p) + kM2MWarps * nout * sizeof(float2) + kM2MWarps * 6 * sizeof(cd);
+}
 template <int MAXQ>
-__global__ void __launch_bounds__(128) k_m2m_split(Cells c, const d4* __restrict__ cen, int lev_begin, int lev_end,
-                                                   int p, double* __restrict__ M, LaneSched sched) {
-    extern __shared__ unsigned char sraw[];
+__global__ void __launch_bounds__(kM2MWarps * 32) k_m2m_split(Cells c, const d4* __restrict__ cen, int lev_begin,
+                                                               int lev_end, int p, double* __restrict__ M,
+                                                               LaneSched sched) {
+    extern __shared__ __align__(16) unsigned char sraw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nco = ncoef(p);
-    const size_t per_warp = ((size_t)2 * nco * sizeof(float2) + 18 * sizeof(cd) + 15) & ~(size_t)15;
+    const int nco = ncoef(p), nout = (p + 1) * (p + 2) / 2;
+    const size_t per_warp = m2m_warp_bytes(p);
     float2* Yh = (float2*)(sraw + wid * per_warp);
     float2* Mt = Yh + nco;
     cd* Y64 = (cd*)(Mt + nco);
     cd* M64 = Y64 + 9;
-    const int cell = lev_begin + blockIdx.x * 4 + wid;
+    float2* r32 = (float2*)(sraw + kM2MWarps * per_warp);  // [kM2MWarps][nout]
+    cd* r64 = (cd*)(r32 + kM2MWarps * nout);                // [kM2MWarps][6]
+    __shared__ double pwi[kMaxP + 1], pwr[kMaxP + 1];        // rho^-n, rho^n
+    const int cell = lev_begin + blockIdx.x;
     if (cell >= lev_end) return;
     const int nch = c.nchild[cell];
-    if (nch == 0) return;
+    if (nch == 0) return;  // leaves
     const d4 zp = cen[cell];
     const double rho = zp.w, inv = rho > 0 ? 1.0 / rho : 0.0;
-    const int cnt = sched.cnt[lane];
-    __shared__ double pwi_all[4][kMaxP + 1], pwr_all[4][kMaxP + 1];
-    double *pwi = pwi_all[wid], *pwr = pwr_all[wid];  // rho^-n, rho^n
-    warp_pow_table(inv, p, lane, pwi);
-    warp_pow_table(rho, p, lane, pwr);
-    __syncwarp();
-    float2 a32[MAXQ];
-    cd a64[MAXQ];
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-        a32[q] = make_float2(0.f, 0.f);
-        a64[q] = mkc(0.0, 0.0);
-    }
-    for (int j = 0; j < nch; ++j) {
-        const int d = c.child[cell] + j;
+    if (wid == 0) warp_pow_table(inv, p, lane, pwi);
+    if (wid == 1) warp_pow_table(rho, p, lane, pwr);
+    __syncthreads();
+    if (wid < nch) {
+        const int cnt = sched.cnt[lane];
+        const int d = c.child[cell] + wid;
         const d4 z = cen[d];
         const double vx = z.x - zp.x, vy = z.y - zp.y, vz = z.z - zp.z;
         if (lane <= p) upsilon_column_f(p, lane, (float)(vx * inv), (float)(vy * inv), (float)(vz * inv), Yh, false);
@@ -376,40 +380,50 @@ __global__ void __launch_bounds__(128) k_m2m_split(Cells c, const d4* __restrict
         for (int q = 0; q < MAXQ; ++q) {
             if (q < cnt) {
                 const int n = sched.n[lane][q], m = sched.m[lane][q];
+                const int o = n * (n + 1) / 2 + m;
                 if (n <= 2) {
-                    cd s = mkc(0.0, 0.0);
+                    cd sum = mkc(0.0, 0.0);
                     for (int k = 0; k <= n; ++k) {
                         const int nn = n - k;
                         for (int l = max(-k, m - nn); l <= min(k, m + nn); ++l)
-                            cmac(s, Y64[cix(k, l)], M64[cix(nn, m - l)]);
+                            cmac(sum, Y64[cix(k, l)], M64[cix(nn, m - l)]);
                     }
-                    a64[q] = a64[q] + s;
-                } else if (rho > 0) {
-                    float2 s = make_float2(0.f, 0.f);
-                    for (int k = 0; k <= n; ++k) {
-                        const int nn = n - k;
-                        for (int l = max(-k, m - nn); l <= min(k, m + nn); ++l) cmacf(s, Yh[cix(k, l)], Mt[cix(nn, m - l)]);
-                    }
-                    a32[q].x += s.x;
-                    a32[q].y += s.y;
+                    r64[wid * 6 + o] = sum;
+                } else {
+                    float2 sum = make_float2(0.f, 0.f);
+                    if (rho > 0)
+                        for (int k = 0; k <= n; ++k) {
+                            const int nn = n - k;
+                            for (int l = max(-k, m - nn); l <= min(k, m + nn); ++l)
+                                cmacf(sum, Yh[cix(k, l)], Mt[cix(nn, m - l)]);
+                        }
+                    r32[wid * nout + o] = sum;
                 }
             }
         }
-        __syncwarp();
     }
+    __syncthreads();
+    // the parent's moments: the daughters' terms summed in daughter order
     double* out = M + (size_t)cell * nco;
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-        if (q < cnt) {
-            const int n = sched.n[lane][q], m = sched.m[lane][q];
-            cd v = a64[q];
-            if (n > 2) {
-                const double sc = pwr[n];
-                v = mkc((double)a32[q].x * sc, (double)a32[q].y * sc);
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= o) ++n;
+        const int m = o - n * (n + 1) / 2;
+        cd v;
+        if (n <= 2) {
+            v = mkc(0.0, 0.0);
+            for (int j = 0; j < nch; ++j) v = v + r64[j * 6 + o];
+        } else {
+            float2 a = make_float2(0.f, 0.f);
+            for (int j = 0; j < nch; ++j) {
+                a.x += r32[j * nout + o].x;
+                a.y += r32[j * nout + o].y;
             }
-            out[cix(n, m)] = v.re;
-            if (m) out[cix(n, -m)] = v.im;
+            const double sc = pwr[n];
+            v = mkc((double)a.x * sc, (double)a.y * sc);
         }
+        out[cix(n, m)] = v.re;
+        if (m) out[cix(n, -m)] = v.im;
     }
 }
 
@@ -424,11 +438,18 @@ void launch_m2m_split(Cells c, const d4* cen, int lev_begin, int lev_end, int p,
     LaneSched sched = make_lane_sched(p, kSchedUp);
     int maxq = 0;
     for (int l = 0; l < 32; ++l) maxq = sched.cnt[l] > maxq ? sched.cnt[l] : maxq;
-    const size_t per_warp = ((size_t)2 * ncoef(p) * sizeof(float2) + 18 * sizeof(cd) + 15) & ~(size_t)15;
-    const unsigned g = (unsigned)((ncl + 3) / 4);
-    if (maxq <= 4) k_m2m_split<4><<<g, 128, 4 * per_warp, s>>>(c, cen, lev_begin, lev_end, p, M, sched);
-    else if (maxq <= 8) k_m2m_split<8><<<g, 128, 4 * per_warp, s>>>(c, cen, lev_begin, lev_end, p, M, sched);
-    else k_m2m_split<24><<<g, 128, 4 * per_warp, s>>>(c, cen, lev_begin, lev_end, p, M, sched);
+    const size_t sm = m2m_smem_bytes(p);
+    const unsigned g = (unsigned)ncl;  // one block per cell of the level (leaves return at once)
+    if (maxq <= 4) {
+        cudaFuncSetAttribute(k_m2m_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_m2m_split<4><<<g, kM2MWarps * 32, sm, s>>>(c, cen, lev_begin, lev_end, p, M, sched);
+    } else if (maxq <= 8) {
+        cudaFuncSetAttribute(k_m2m_split<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_m2m_split<8><<<g, kM2MWarps * 32, sm, s>>>(c, cen, lev_begin, lev_end, p, M, sched);
+    } else {
+        cudaFuncSetAttribute(k_m2m_split<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_m2m_split<24><<<g, kM2MWarps * 32, sm, s>>>(c, cen, lev_begin, lev_end, p, M, sched);
+    }
     note_launch();
 }
 
