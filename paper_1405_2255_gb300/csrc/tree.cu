@@ -724,31 +724,31 @@ void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves,
 // as the smallest support ball (over all subsets of 1..4 daughters, enumerated by
 // mask) that contains every daughter ball; single precision relative to the first
 // daughter's centre.  One warp per cell, lanes take masks; ties go to the smaller mask.
-__global__ void k_internal_meb(Cells c, int lev_begin, int lev_end, unsigned* status) {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    int cell = lev_begin + warp;
+// one block of kMebWarps warps per internal cell; warp w tries the support sets with
+// bit masks 1 + 32 w + lane (at most 4 daughters), and the block keeps the smallest
+// valid ball (ties: the smaller mask)
+constexpr int kMebWarps = 8;
+__global__ void __launch_bounds__(kMebWarps * 32) k_internal_meb(Cells c, int lev_begin, int lev_end,
+                                                                 unsigned* status) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int cell = lev_begin + blockIdx.x;
     if (cell >= lev_end) return;
-    int nch = c.nchild[cell];
+    const int nch = c.nchild[cell];
     if (nch == 0) return;  // leaves are done
-    int ch = c.child[cell];
+    const int ch = c.child[cell];
     const d4 o = c.sr[ch];
     float cen[8][3], rad[8];
-    double m = 0, mx[3] = {0, 0, 0};
     for (int i = 0; i < nch; ++i) {
         d4 v = c.sr[ch + i];
         cen[i][0] = (float)(v.x - o.x);
         cen[i][1] = (float)(v.y - o.y);
         cen[i][2] = (float)(v.z - o.z);
         rad[i] = (float)v.w;
-        double md = c.mass[ch + i];
-        d4 cm = c.cr[ch + i];
-        m += md;
-        mx[0] += md * cm.x; mx[1] += md * cm.y; mx[2] += md * cm.z;
     }
     float best = -1, bc[3] = {0, 0, 0};
     int bmask = 1 << 30;
-    for (int mask = 1 + lane; mask < (1 << nch); mask += 32) {
-        if (__popc(mask) > 4) continue;
+    const int mask = 1 + lane + 32 * wid;
+    if (mask < (1 << nch) && __popc(mask) <= 4) {
         float sc[4][3], sr[4];
         int k = 0;
         for (int i = 0; i < nch; ++i)
@@ -758,20 +758,21 @@ __global__ void k_internal_meb(Cells c, int lev_begin, int lev_end, unsigned* st
                 ++k;
             }
         float cc[3], rr;
-        if (!support_ball_dev(k, sc, sr, cc, rr)) continue;
-        bool ok = true;
-        for (int i = 0; i < nch; ++i)
-            if (dist3f_dev(cen[i], cc) + rad[i] > rr * (1.0f + kMebIn)) {
-                ok = false;
-                break;
+        if (support_ball_dev(k, sc, sr, cc, rr)) {
+            bool ok = true;
+            for (int i = 0; i < nch; ++i)
+                if (dist3f_dev(cen[i], cc) + rad[i] > rr * (1.0f + kMebIn)) {
+                    ok = false;
+                    break;
+                }
+            if (ok) {
+                best = rr;
+                bmask = mask;
+                bc[0] = cc[0]; bc[1] = cc[1]; bc[2] = cc[2];
             }
-        if (ok && (best < 0 || rr < best)) {
-            best = rr;
-            bmask = mask;
-            bc[0] = cc[0]; bc[1] = cc[1]; bc[2] = cc[2];
         }
     }
-    // warp argmin of (radius, mask)
+    // warp argmin of (radius, mask), then across the warps
     for (int off = 16; off > 0; off >>= 1) {
         float ob = __shfl_xor_sync(0xffffffffu, best, off);
         int om = __shfl_xor_sync(0xffffffffu, bmask, off);
@@ -784,10 +785,33 @@ __global__ void k_internal_meb(Cells c, int lev_begin, int lev_end, unsigned* st
             bc[0] = o0; bc[1] = o1; bc[2] = o2;
         }
     }
+    __shared__ float wbest[kMebWarps], wbc[kMebWarps][3];
+    __shared__ int wmask[kMebWarps];
     if (lane == 0) {
+        wbest[wid] = best;
+        wmask[wid] = bmask;
+        wbc[wid][0] = bc[0]; wbc[wid][1] = bc[1]; wbc[wid][2] = bc[2];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kMebWarps; ++w) {
+            const float ob = wbest[w];
+            const int om = wmask[w];
+            if ((ob >= 0) && (best < 0 || ob < best || (ob == best && om < bmask))) {
+                best = ob; bmask = om;
+                bc[0] = wbc[w][0]; bc[1] = wbc[w][1]; bc[2] = wbc[w][2];
+            }
+        }
         if (best < 0) {  // no valid support set: the first daughter's centre
             atomicOr(status, kStatMeb);
             bc[0] = bc[1] = bc[2] = 0.f;
+        }
+        double m = 0, mx[3] = {0, 0, 0};
+        for (int i = 0; i < nch; ++i) {
+            const double md = c.mass[ch + i];
+            const d4 cm = c.cr[ch + i];
+            m += md;
+            mx[0] += md * cm.x; mx[1] += md * cm.y; mx[2] += md * cm.z;
         }
         double s[3] = {o.x + (double)bc[0], o.y + (double)bc[1], o.z + (double)bc[2]};
         double com[3];
@@ -855,7 +879,7 @@ void launch_internal_geometry(const d4* xm, Cells c, int lev_begin, int lev_end,
                               unsigned long long* rad_tmp, unsigned* status, cudaStream_t s) {
     int ncl = lev_end - lev_begin;
     if (ncl <= 0) return;
-    k_internal_meb<<<(unsigned)(((long long)ncl * 32 + 255) / 256), 256, 0, s>>>(c, lev_begin, lev_end, status); note_launch();
+    k_internal_meb<<<(unsigned)ncl, kMebWarps * 32, 0, s>>>(c, lev_begin, lev_end, status); note_launch();
     cudaMemsetAsync(rad_tmp, 0, sizeof(unsigned long long) * 2 * ncl, s);
     k_internal_radii<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xm, c, lev_begin, lev_end, rad_tmp); note_launch();
     k_internal_radii_finish<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, rad_tmp); note_launch();
