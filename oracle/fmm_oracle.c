@@ -35,7 +35,8 @@
  *           IEEE single precision relative to the cell's first particle / first
  *           daughter centre; rho = exact FP64 max over the particles of |x - s|.
  *   R-p2p   a pair (A,B) is summed directly when N_A*N_B < p2p_c * p^3 (checked
- *           first: the descendants of such a pair would all be summed directly).
+ *           first: the descendants of such a pair would all be summed directly),
+ *           p being the order of the expansion in use (1 or 0 in the estimate).
  *   R-split split the cell with the larger rho (ties: A); never a leaf; A = B
  *           splits into all ordered daughter pairs.
  *   R-mac   (18a,b) as strict inequalities; E~ M_A/r^2 is evaluated without
@@ -865,7 +866,8 @@ static void estimate_scale(orc_run *run, int want_f, double *scale)
     }
     walk_t w = {0};
     w.t = t; w.p = pe; w.mac = MAC_EST; w.use_com = 1;
-    w.p2p_thresh = run->prm.p2p_c * pow((double)run->prm.p, 3);
+    /* reading R-p2p: the threshold uses the order of the expansion in use, here pe */
+    w.p2p_thresh = run->prm.p2p_c * pow((double)pe, 3);
     walk(&w, 0, 0);
     run->st.est_m2l = w.m2l.n; run->st.est_p2p = w.p2p.n;
     for (long i = 0; i < w.m2l.n; ++i) {

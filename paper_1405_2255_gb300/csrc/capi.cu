@@ -354,7 +354,7 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     memset(&wp, 0, sizeof wp);
     wp.p = want_f ? 0 : 1;
     wp.mac = kMacEstimate;
-    wp.p2p_thresh = ctx->prm.p2p_c * (double)ctx->prm.p * ctx->prm.p * ctx->prm.p;
+    wp.p2p_thresh = ctx->prm.p2p_c * (double)wp.p * wp.p * wp.p;  // the estimate's own order (reading R-p2p)
     wp.use_com = 1;
     TRY(run_walk(ctx, wp, ctx->est_m2l, ctx->est_m2l_cap, ctx->est_p2p, ctx->est_p2p_cap, &ctx->n_est_m2l,
                  &ctx->n_est_p2p, s));

@@ -274,7 +274,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
         memset(&ew, 0, sizeof ew);
         ew.p = want_f ? 0 : 1;
         ew.mac = kMacEstimate;
-        ew.p2p_thresh = prm.p2p_c * (double)p * p * p;
+        ew.p2p_thresh = prm.p2p_c * (double)ew.p * ew.p * ew.p;  // the estimate's own order
         ew.use_com = 1;
         long long nm = 0, np = 0;
         int rc = walk_na(r, ew, est_m2l, kEstCap, est_p2p, kEstCap, &nm, &np);
