@@ -37,9 +37,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--p", type=int, default=12)
-    ap.add_argument("--eps", type=float, default=2.5e-7)
-    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--p", type=int, default=14)
+    ap.add_argument("--eps", type=float, default=3.5e-7)
+    ap.add_argument("--leaf", type=int, default=80)
     ap.add_argument("--c", type=float, default=4.0)
     ap.add_argument("--cpu-sample", type=int, default=50000)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-mode and direct-sum comparisons")
@@ -54,8 +54,8 @@ def parse():
     if a.workload == "cusp":
         if a.n == 1_000_000:
             a.n = 10_000_000
-        if a.eps == 2.5e-7:  # the cusp reaches rms 9.9e-8 at 2.5e-7: keep a margin below 1e-7
-            a.eps = 2e-7
+        if a.eps == 3.5e-7:  # the cusp needs a smaller eps for the same rms error
+            a.eps = 2.8e-7
     return a
 
 
