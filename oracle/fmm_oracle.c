@@ -29,7 +29,8 @@
  *   R-leaf  a cell is split iff it holds more than leaf_size particles and is above
  *           depth 21; daughters are the non-empty octants in key order.
  *   R-ses   leaf centre: smallest enclosing ball of its particles (Welzl, the
- *           first 128 particles taken in bit-reversed index order);
+ *           first 128 particles taken in bit-reversed index order; with the
+ *           move-to-front rule for leaves of at most 128 particles);
  *           internal centre: smallest ball enclosing the daughters' balls
  *           (s_d, rho_d) (enumeration of support sets of up to 4 balls); both in
  *           IEEE single precision relative to the cell's first particle / first
@@ -501,6 +502,25 @@ static void meb_order(int n, int *order)
     for (int i = m; i < n; ++i) order[k++] = i;
 }
 
+/* Welzl's recursion with the move-to-front rule (Gaertner): the smallest ball
+ * enclosing L[0..end) with R on its boundary; a point found outside is moved to the
+ * front of L after the recursion it starts, so later scans meet it first.  Used for
+ * up to 128 points (reading R-ses). */
+static void welzl_mtf(int end, float (*L)[3], int nr, float R[4][3], float c[3], float *rad)
+{
+    trivial_ball(nr, (const float(*)[3])R, c, rad);
+    if (nr == 4) return;
+    for (int i = 0; i < end; ++i) {
+        if (in_ball(L[i], c, *rad)) continue;
+        for (int d = 0; d < 3; ++d) R[nr][d] = L[i][d];
+        welzl_mtf(i, L, nr + 1, R, c, rad);
+        float t[3] = {L[i][0], L[i][1], L[i][2]};
+        for (int j = i; j > 0; --j)
+            for (int d = 0; d < 3; ++d) L[j][d] = L[j - 1][d];
+        for (int d = 0; d < 3; ++d) L[0][d] = t[d];
+    }
+}
+
 /* smallest enclosing ball of n points: single precision, relative to the first point */
 int orc_meb_points(int n, const double *pts, double c[3], double *rad)
 {
@@ -512,7 +532,8 @@ int orc_meb_points(int n, const double *pts, double c[3], double *rad)
         for (int d = 0; d < 3; ++d) P[i][d] = (float)(pts[3 * order[i] + d] - pts[d]);
     free(order);
     float R[4][3], cf[3], rf;
-    welzl(n, (const float(*)[3])P, 0, R, cf, &rf);
+    if (n <= 128) welzl_mtf(n, P, 0, R, cf, &rf);
+    else welzl(n, (const float(*)[3])P, 0, R, cf, &rf);
     free(P);
     for (int d = 0; d < 3; ++d) c[d] = pts[d] + (double)cf[d];
     *rad = rf < 0 ? 0.0 : (double)rf;

@@ -630,6 +630,87 @@ __device__ void meb_points_warp(const LeafPts& P, int n, float c[3], float& rad,
     rad = r0 < 0 ? 0 : r0;
 }
 
+// Welzl's recursion with the move-to-front rule for leaves held entirely in the
+// warp's buffer (at most kMebBuf points): a point found outside is moved to the front
+// of the list once the level it starts has finished, so later scans meet it first.
+// The nested loops are the recursion levels 0..3 (a fourth support point ends it).
+__device__ int first_outside_buf(const float (*L)[3], int from, int to, const float c[3], float rad, int lane) {
+    for (int b = from; b < to; b += 32) {
+        const int i = b + lane;
+        const bool out = i < to && !in_ball_dev(L[i], c, rad);
+        const unsigned m = __ballot_sync(0xffffffffu, out);
+        if (m) return b + __ffs(m) - 1;
+    }
+    return -1;
+}
+// L[0..i] <- (L[i], L[0], ..., L[i-1])
+__device__ void move_to_front(float (*L)[3], int i, int lane) {
+    float v[kMebBuf / 32][3];
+#pragma unroll
+    for (int t = 0; t < kMebBuf / 32; ++t) {
+        const int j = lane + 32 * t;
+        if (j <= i) {
+            v[t][0] = L[j][0];
+            v[t][1] = L[j][1];
+            v[t][2] = L[j][2];
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kMebBuf / 32; ++t) {
+        const int j = lane + 32 * t;
+        if (j <= i) {
+            const int d = j == i ? 0 : j + 1;
+            L[d][0] = v[t][0];
+            L[d][1] = v[t][1];
+            L[d][2] = v[t][2];
+        }
+    }
+    __syncwarp();
+}
+__device__ inline void cp3(float d[3], const float s[3]) {
+    d[0] = s[0];
+    d[1] = s[1];
+    d[2] = s[2];
+}
+__device__ void meb_points_mtf_warp(float (*L)[3], int n, float c[3], float& rad, int lane) {
+    float R[4][3];
+    float c0[3], r0, c1[3], r1, c2[3], r2, c3[3], r3;
+    trivial_ball_dev(0, R, c0, r0);
+    for (int i0 = first_outside_buf(L, 0, n, c0, r0, lane); i0 >= 0;
+         i0 = first_outside_buf(L, i0 + 1, n, c0, r0, lane)) {
+        cp3(R[0], L[i0]);
+        trivial_ball_dev(1, R, c1, r1);
+        for (int i1 = first_outside_buf(L, 0, i0, c1, r1, lane); i1 >= 0;
+             i1 = first_outside_buf(L, i1 + 1, i0, c1, r1, lane)) {
+            cp3(R[1], L[i1]);
+            trivial_ball_dev(2, R, c2, r2);
+            for (int i2 = first_outside_buf(L, 0, i1, c2, r2, lane); i2 >= 0;
+                 i2 = first_outside_buf(L, i2 + 1, i1, c2, r2, lane)) {
+                cp3(R[2], L[i2]);
+                trivial_ball_dev(3, R, c3, r3);
+                for (int i3 = first_outside_buf(L, 0, i2, c3, r3, lane); i3 >= 0;
+                     i3 = first_outside_buf(L, i3 + 1, i2, c3, r3, lane)) {
+                    cp3(R[3], L[i3]);
+                    trivial_ball_dev(4, R, c3, r3);
+                    move_to_front(L, i3, lane);
+                }
+                cp3(c2, c3);
+                r2 = r3;
+                move_to_front(L, i2, lane);
+            }
+            cp3(c1, c2);
+            r1 = r2;
+            move_to_front(L, i1, lane);
+        }
+        cp3(c0, c1);
+        r0 = r1;
+        move_to_front(L, i0, lane);
+    }
+    cp3(c, c0);
+    rad = r0 < 0 ? 0 : r0;
+}
+
 // one warp per leaf: smallest enclosing ball, exact radius, mass, centre of mass
 constexpr int kGeoWarps = 4;
 __global__ void __launch_bounds__(kGeoWarps * 32) k_leaf_geometry(const d4* __restrict__ xm, Cells c,
@@ -675,7 +756,8 @@ __global__ void __launch_bounds__(kGeoWarps * 32) k_leaf_geometry(const d4* __re
     }
     __syncwarp();
     float cf[3], radf;
-    meb_points_warp(P, count, cf, radf, lane);
+    if (count <= kMebBuf) meb_points_mtf_warp(pbuf[wid], count, cf, radf, lane);
+    else meb_points_warp(P, count, cf, radf, lane);
     double s[3] = {P.o[0] + (double)cf[0], P.o[1] + (double)cf[1], P.o[2] + (double)cf[2]};
     // radii as the square root of the largest squared distance (sqrt is monotonic and
     // correctly rounded, so this equals the largest distance)
