@@ -123,6 +123,18 @@ def test_sizes_and_ragged_tails(g, orc, n, leaf):
     assert np.max(_rel(acc, run.acc)) <= PARITY_TOL
 
 
+def test_large_leaves_match_oracle(g, orc):
+    """Leaves above 128 particles take the enclosing-ball recursion without move-to-front
+    (and partly from global memory): tree, centres and forces still match the oracle."""
+    x, mu = inputs.plummer(3000, inputs.BASE_SEED + 80)
+    psi, acc, st, dump, run = _run_both(g, orc, x, mu, p=6, eps=1e-6, leaf_size=200)
+    ci = dump["cells_int"]
+    assert ci[ci[:, 1] == 1, 3].max() > 128  # some leaf holds more than 128 particles
+    flips, _, _ = _compare_structure(dump, run)
+    assert flips == 0
+    assert np.max(_rel(acc, run.acc)) <= PARITY_TOL
+
+
 def test_empty_input(g):
     import torch
     ctx = g.Context()
