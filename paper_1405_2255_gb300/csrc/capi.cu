@@ -121,10 +121,11 @@ int ctx_device(fmm_ctx* ctx) { return ctx->device; }
 int ctx_fail(fmm_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
 }  // namespace gb3
 
-#define TRY(expr)                                     \
-    do {                                              \
-        int _rc = (expr);                             \
-        if (_rc) return fail_cuda(ctx, _rc);          \
+// a failing step keeps its own message; otherwise the CUDA error text is recorded
+#define TRY(expr)                                                  \
+    do {                                                           \
+        int _rc = (expr);                                          \
+        if (_rc) return ctx->err[0] ? _rc : fail_cuda(ctx, _rc);   \
     } while (0)
 #define CU(expr) TRY(([&]() -> int { GB3_CUDA_TRY(expr); return 0; })())
 
@@ -285,10 +286,12 @@ static int run_walk(fmm_ctx* ctx, WalkParams wp, Buf& m2l, long long& m2l_cap, B
                     long long* n_m2l, long long* n_p2p, cudaStream_t s) {
     Cells c = cells_of(ctx);
     const int nc = ctx->ncells;
-    if (ctx->front_cap == 0) ctx->front_cap = std::max<long long>(1 << 16, 32LL * nc);
-    if (m2l_cap == 0) m2l_cap = std::max<long long>(1 << 16, 64LL * nc);
-    if (p2p_cap == 0) p2p_cap = std::max<long long>(1 << 16, 32LL * nc);
-    for (int attempt = 0; attempt < 8; ++attempt) {
+    // starting capacities scale with this tree (a previous, smaller evaluation may have
+    // left smaller ones); an overflow grows what overflowed and the walk is redone
+    ctx->front_cap = std::max<long long>(ctx->front_cap, std::max<long long>(1 << 16, 32LL * nc));
+    m2l_cap = std::max<long long>(m2l_cap, std::max<long long>(1 << 16, 64LL * nc));
+    p2p_cap = std::max<long long>(p2p_cap, std::max<long long>(1 << 16, 32LL * nc));
+    for (int attempt = 0; attempt < 24; ++attempt) {
         TRY(ensure(ctx->front0, sizeof(int2) * ctx->front_cap));
         TRY(ensure(ctx->front1, sizeof(int2) * ctx->front_cap));
         TRY(ensure(m2l, sizeof(int2) * m2l_cap));
@@ -332,7 +335,10 @@ static int run_walk(fmm_ctx* ctx, WalkParams wp, Buf& m2l, long long& m2l_cap, B
         if ((long long)ctx->h_counters[1] > m2l_cap) m2l_cap = std::max<long long>(2 * m2l_cap, 2 * (long long)ctx->h_counters[1]);
         if ((long long)ctx->h_counters[2] > p2p_cap) p2p_cap = std::max<long long>(2 * p2p_cap, 2 * (long long)ctx->h_counters[2]);
     }
-    return fail(ctx, FMM_E_OVERFLOW, "walk lists could not be grown enough");
+    char msg[200];
+    snprintf(msg, sizeof msg, "walk lists could not be grown enough (caps: front %lld, m2l %lld, p2p %lld)",
+             ctx->front_cap, m2l_cap, p2p_cap);
+    return fail(ctx, FMM_E_OVERFLOW, msg);
 }
 
 static int sort_and_segment(fmm_ctx* ctx, Buf& list, long long npairs, Buf& seg_start, Buf& seg_end, cudaStream_t s) {

@@ -331,3 +331,20 @@ def test_mixed_small_leaves(g, orc, leaf):
     assert np.all(np.isfinite(e))
     assert np.sqrt(np.mean(e ** 2)) < 1e-7
     ctx.close()
+
+
+def test_small_then_large_on_one_context(g):
+    """A context first used on a small system keeps working on a much larger ensemble:
+    the walk's list capacities follow the tree (regression: they once stayed at the
+    small system's size and the walk gave up growing them)."""
+    ctx = g.Context(p=14, eps=3.5e-7, leaf_size=80, p2p_c=4.0)
+    x, mu = inputs.plummer(2000, 5)
+    ctx.fmm_evaluate(_dev(x), _dev(mu))
+    systems = inputs.served_systems(8, inputs.BASE_SEED + 5)
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
+    xs = np.concatenate([s[0] for s in systems])
+    ms = np.concatenate([s[1] for s in systems])
+    psi, acc, st = ctx.fmm_evaluate_batch(off, _dev(xs), _dev(ms), 1.0, stats=True)
+    assert st["n"] == len(ms) and st["n_m2l"] > 0
+    assert np.all(np.isfinite(acc.cpu().numpy()))
+    ctx.close()
