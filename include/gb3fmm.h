@@ -77,6 +77,11 @@ typedef struct {
                              to the sink leaf's centre; 0 = from their FP32 high parts only */
     int    m2l_split;   /* mixed mode M2L: 1 = terms of order n+k <= 2 in FP64 and the others
                            in FP32 on scaled harmonics; 0 = every term in FP64        */
+    int    m2l_rot;     /* mixed mode M2L with m2l_split, 3 <= p <= 16: 1 = the FP32 terms through
+                           rotations into the frame of the interaction axis, the z-axis
+                           kernel eq. (A31) and the swap matrices of App. A.5 (O(p^3) per
+                           pair); 0 = eq. (3b) term by term (O(p^4)).  Same result up to
+                           FP32 rounding.                                               */
 } fmm_params;
 
 typedef struct {
@@ -96,7 +101,7 @@ typedef struct fmm_ctx fmm_ctx;
 
 /* Default parameters: p = 8, eps = 1e-7, (18a) with the low-order estimate,
  * leaf_size = 64, p2p_c = 8, mixed precision with two-float P2P positions and
- * the precision-split M2L.  Host pointer, filled in. */
+ * the precision-split, rotation-accelerated M2L.  Host pointer, filled in. */
 void fmm_default_params(fmm_params* out);
 
 /* Create a context on CUDA device `device` (the device becomes current for the

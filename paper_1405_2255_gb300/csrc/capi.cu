@@ -153,6 +153,7 @@ static int check_params(const fmm_params* p) {
     if (!(p->p2p_c >= 0)) return FMM_E_INVALID;
     if (p->precision != FMM_PREC_FP64 && p->precision != FMM_PREC_MIXED) return FMM_E_INVALID;
     if (p->scale_src != FMM_SCALE_ESTIMATE && p->scale_src != FMM_SCALE_CALLER) return FMM_E_INVALID;
+    if (p->m2l_rot != 0 && p->m2l_rot != 1) return FMM_E_INVALID;
     return 0;
 }
 
@@ -515,7 +516,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     if (split) {
         TRY(ensure(ctx->m2l_tmp, m2l_split_tmp_bytes(nc, prm.p, ctx->n_m2l)));
         launch_m2l_split(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc,
-                         c.sr, P<double>(ctx->M), prm.p, P<double>(ctx->F), s);
+                         c.sr, P<double>(ctx->M), prm.p, P<double>(ctx->F), prm.m2l_rot != 0, s);
     } else {
         TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc, prm.p)));
         launch_m2l(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc, c.sr,
@@ -604,6 +605,7 @@ void fmm_default_params(fmm_params* out) {
     out->scale_src = FMM_SCALE_ESTIMATE;
     out->p2p_two_float = 1;
     out->m2l_split = 1;
+    out->m2l_rot = 1;
 }
 
 int fmm_create(fmm_ctx** out, const fmm_params* params, int device) {

@@ -254,7 +254,7 @@ struct PairInfo {
     double x, y, z, rinv;
 };
 
-constexpr int kChunk = 32;  // M2L pairs per work item
+constexpr int kChunk = kM2LChunk;
 
 // ---------------------------------------------------------------- split M2L by rounds of equal n
 // Terms of order n + k <= 2 are summed in FP64 (spread over the lanes), the others
@@ -572,7 +572,7 @@ __global__ void k_m2l_reduce(const int* __restrict__ order, const int* __restric
 }
 
 void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells, const d4* cen,
-                      const double* M, int p, double* F, cudaStream_t s) {
+                      const double* M, int p, double* F, bool rot, cudaStream_t s) {
     if (ncells <= 0) return;
     if (p <= kJ64) {  // nothing to split
         launch_m2l(list, seg_start, seg_end, tmp, ncells, cen, M, p, F, s);
@@ -599,8 +599,12 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     k_sink_order<<<grid_for(ncells, 256), 256, 0, s>>>(flip ? k1 : k0, ncells, order, work + 1); note_launch();
     k_item_counts<<<grid_for(ncells, 256), 256, 0, s>>>(order, seg_start, seg_end, ncells, cnt); note_launch();
     scan_exclusive_i32(cnt, item_start, ncells, (int*)(work + 2), stmp, s);
-    k_prep_split<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mf, M64); note_launch();
-    m2l_rounds_launch<kRoundsBatch>(list, seg_start, seg_end, order, item_start, work, cen, Mf, M64, p, part, s);
+    if (rot && m2l_rot_supported(p)) {
+        launch_m2l_rot(list, seg_start, seg_end, order, item_start, work, cen, M, ncells, p, (float*)Mf, M64, part, s);
+    } else {
+        k_prep_split<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mf, M64); note_launch();
+        m2l_rounds_launch<kRoundsBatch>(list, seg_start, seg_end, order, item_start, work, cen, Mf, M64, p, part, s);
+    }
     k_m2l_reduce<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(order, item_start, cnt, work, ncells,
                                                                             ncoef(p), part, F);
     note_launch();

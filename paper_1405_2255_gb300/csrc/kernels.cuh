@@ -116,10 +116,23 @@ void launch_segments(const int2* list, long long npairs, int ncells, int* seg_st
 size_t m2l_tmp_bytes(int ncells, int p);
 void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells,
                 const d4* cen, const double* M, int p, double* F, cudaStream_t s);
-// mixed mode: orders <= 2 of Theta in FP64, the rest in FP32 on scaled harmonics
+// mixed mode: orders <= 2 of Theta in FP64, the rest in FP32 on scaled harmonics, either
+// directly (eq. 3b) or, when rot is set and m2l_rot_supported(p), through rotations into
+// the interaction's z frame (App. A.5, m2l_rot.cu)
 size_t m2l_split_tmp_bytes(int ncells, int p, long long npairs);
 void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells,
-                      const d4* cen, const double* M, int p, double* F, cudaStream_t s);
+                      const d4* cen, const double* M, int p, double* F, bool rot, cudaStream_t s);
+// M2L pairs per work item of the mixed-mode M2L: each sink's list is cut into chunks of
+// this many pairs from its start, summed separately and then added in chunk order
+constexpr int kM2LChunk = 32;
+constexpr int kRotMaxP = 16;  // largest order with a rotation-accelerated M2L
+bool m2l_rot_supported(int p);
+// sinks in `order` (work[1] of them), items from item_start, work[0] the item counter and
+// work[2] the number of items; Mt (ncells x (p+1)^2 floats) and M64 (ncells x 9) are scratch;
+// part receives one expansion per item
+void launch_m2l_rot(const int2* list, const int* seg_start, const int* seg_end, const int* order,
+                    const int* item_start, unsigned* work, const d4* cen, const double* M, int ncells, int p,
+                    float* Mt, cd* M64, double* part, cudaStream_t s);
 void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F,
                       cudaStream_t s);
 // L2P (eqs. 3a, 7) for every particle of every leaf: psi_far, acc_far (sorted order)

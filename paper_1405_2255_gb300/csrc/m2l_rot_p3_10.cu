@@ -1,0 +1,21 @@
+// m2l_rot_p3_10.cu -- instantiations of the rotation-accelerated M2L kernel for p = 3..10
+#include "m2l_rot.cuh"
+
+namespace gb3 {
+template void rot_launch<3>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
+                             const float*, const cd*, double*, cudaStream_t);
+template void rot_launch<4>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
+                             const float*, const cd*, double*, cudaStream_t);
+template void rot_launch<5>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
+                             const float*, const cd*, double*, cudaStream_t);
+template void rot_launch<6>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
+                             const float*, const cd*, double*, cudaStream_t);
+template void rot_launch<7>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
+                             const float*, const cd*, double*, cudaStream_t);
+template void rot_launch<8>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
+                             const float*, const cd*, double*, cudaStream_t);
+template void rot_launch<9>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
+                             const float*, const cd*, double*, cudaStream_t);
+template void rot_launch<10>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
+                             const float*, const cd*, double*, cudaStream_t);
+}  // namespace gb3

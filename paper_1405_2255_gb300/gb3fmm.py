@@ -28,7 +28,7 @@ FMM_SCALE_ESTIMATE, FMM_SCALE_CALLER = 0, 1
 class fmm_params(C.Structure):
     _fields_ = [("p", C.c_int), ("eps", C.c_double), ("mac", C.c_int), ("theta_crit", C.c_double),
                 ("leaf_size", C.c_int), ("p2p_c", C.c_double), ("precision", C.c_int), ("scale_src", C.c_int),
-                ("p2p_two_float", C.c_int), ("m2l_split", C.c_int)]
+                ("p2p_two_float", C.c_int), ("m2l_split", C.c_int), ("m2l_rot", C.c_int)]
 
 
 class fmm_stats(C.Structure):

@@ -348,3 +348,37 @@ def test_small_then_large_on_one_context(g):
     assert st["n"] == len(ms) and st["n_m2l"] > 0
     assert np.all(np.isfinite(acc.cpu().numpy()))
     ctx.close()
+
+
+@pytest.mark.parametrize("p", [3, 5, 8, 12, 14, 16])
+def test_m2l_rot_matches_direct(g, orc, p):
+    """The rotation-accelerated M2L (App. A.5: z rotations, swap matrices, eq. A31) gives
+    the direct eq. (3b) result up to FP32 rounding: same lists, same FP64 low orders, and
+    both against the oracle's FP64 FMM on those lists."""
+    x, mu = inputs.plummer(6000, inputs.BASE_SEED + 80 + p)
+    kw = dict(p=p, mac=g.FMM_MAC_THETA, theta_crit=0.6, leaf_size=24, p2p_c=0.0, precision=g.FMM_PREC_MIXED)
+    c_rot, c_dir = g.Context(m2l_rot=1, **kw), g.Context(m2l_rot=0, **kw)
+    _, a_rot, st = c_rot.fmm_evaluate(_dev(x), _dev(mu), stats=True)
+    _, a_dir = c_dir.fmm_evaluate(_dev(x), _dev(mu))
+    assert st["n_m2l"] > 5000
+    a_rot, a_dir = a_rot.cpu().numpy(), a_dir.cpu().numpy()
+    d = _rel(a_rot, a_dir)
+    assert np.sqrt(np.mean(d ** 2)) < 1e-7 and d.max() < 2e-6
+    run = orc.fmm(x, mu, p=p, mac=orc.MAC_THETA, theta_crit=0.6, leaf_size=24, p2p_c=0.0)
+    e_rot, e_dir = _rel(a_rot, run.acc), _rel(a_dir, run.acc)
+    assert np.sqrt(np.mean(e_rot ** 2)) < 1.5 * np.sqrt(np.mean(e_dir ** 2)) + 2e-8
+    assert e_rot.max() < 4e-6
+    c_rot.close()
+    c_dir.close()
+
+
+def test_m2l_rot_outside_range_falls_back(g):
+    """Orders without a rotation kernel (p > 16) take the direct FP32 M2L: identical results."""
+    x, mu = inputs.plummer(4000, inputs.BASE_SEED + 99)
+    kw = dict(p=17, mac=g.FMM_MAC_THETA, theta_crit=0.5, leaf_size=16, p2p_c=0.0, precision=g.FMM_PREC_MIXED)
+    c1, c0 = g.Context(m2l_rot=1, **kw), g.Context(m2l_rot=0, **kw)
+    _, a1 = c1.fmm_evaluate(_dev(x), _dev(mu))
+    _, a0 = c0.fmm_evaluate(_dev(x), _dev(mu))
+    assert np.array_equal(a1.cpu().numpy(), a0.cpu().numpy())
+    c1.close()
+    c0.close()
