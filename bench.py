@@ -38,9 +38,9 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--p", type=int, default=14)
-    ap.add_argument("--eps", type=float, default=3.5e-7)
+    ap.add_argument("--eps", type=float, default=3e-7)
     ap.add_argument("--leaf", type=int, default=80)
-    ap.add_argument("--c", type=float, default=4.0)
+    ap.add_argument("--c", type=float, default=1.0)
     ap.add_argument("--cpu-sample", type=int, default=50000)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-mode and direct-sum comparisons")
     ap.add_argument("--workload", default="plummer", choices=["plummer", "cusp", "ensemble", "serve"],
@@ -54,8 +54,8 @@ def parse():
     if a.workload == "cusp":
         if a.n == 1_000_000:
             a.n = 10_000_000
-        if a.eps == 3.5e-7:  # the cusp needs a smaller eps for the same rms error
-            a.eps = 2.8e-7
+        if a.eps == 3e-7:  # the cusp needs a smaller eps for the same rms error
+            a.eps = 2.5e-7
     return a
 
 
@@ -156,6 +156,26 @@ def m2l_flops(p):
     return 8 * sum((n + 1) * (p - n + 1) ** 2 for n in range(p + 1))
 
 
+def m2l_rot_flops(p):
+    """FP32 flops per pair of the rotation-accelerated M2L (App. A.5), 2 per multiply-add:
+    four z rotations (4 multiply-adds per m > 0 of each order), four swaps (one
+    multiply-add per entry of the swap matrices' parity pattern: cosine block n+m+l even,
+    sine block n+m+l odd; the restricted forward/backward swaps only the rows/columns
+    |m| <= min(n, p-n)), the z-axis kernel eq. (A31) over n + k >= 3, and the scaling of
+    the kept rotated multipoles and of the results."""
+    def swap(n, lim_rows, lim_cols):
+        c = sum(1 for m in range(n + 1) for l in range(n + 1) if (n + m + l) % 2 == 0 and m <= lim_rows and l <= lim_cols)
+        c += sum(1 for m in range(1, n + 1) for l in range(1, n + 1) if (n + m + l) % 2 and m <= lim_rows and l <= lim_cols)
+        return c
+    fma = 0
+    for n in range(p + 1):
+        L = min(n, p - n)
+        fma += 4 * 4 * n + 2 * swap(n, n, n) + swap(n, L, n) + swap(n, n, L) + (2 * L + 1) + (2 * n + 1)
+        for m in range(L + 1):
+            fma += (2 if m else 1) * sum(1 for k in range(max(m, 3 - n), p - n + 1))
+    return 2 * fma
+
+
 def oracle_run(n, p, eps, leaf, c, seed, model="plummer"):
     import oracle
     from paper_1405_2255_gb300 import inputs
@@ -210,8 +230,10 @@ def roofline(g, a, prec, phase, full):
     src = ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz" if mixed
            else "nominal FP64 rate of the part (1.25 TFLOP/s)")
     if t_m2l >= t_p2p:
-        achieved = full["n_m2l"] * m2l_flops(a.p) / t_m2l / 1e12
-        kern = "k_m2l_rounds (eq. 3b, orders > 2 in FP32)" if mixed else "k_m2l (eq. 3b, FP64)"
+        rot = mixed and 3 <= a.p <= 16
+        achieved = full["n_m2l"] * (m2l_rot_flops(a.p) if rot else m2l_flops(a.p)) / t_m2l / 1e12
+        kern = ("k_m2l_rot (App. A.5 rotations and eq. A31, orders > 2 in FP32)" if rot
+                else "k_m2l_rounds (eq. 3b, orders > 2 in FP32)" if mixed else "k_m2l (eq. 3b, FP64)")
     else:
         achieved = 20.0 * full["p2p_interactions"] / t_p2p / 1e12
         kern = "k_p2p_mixed (eq. 1, FP32 two-float)" if mixed else "k_p2p_fp64 (eq. 1)"

@@ -77,11 +77,12 @@ typedef struct {
                              to the sink leaf's centre; 0 = from their FP32 high parts only */
     int    m2l_split;   /* mixed mode M2L: 1 = terms of order n+k <= 2 in FP64 and the others
                            in FP32 on scaled harmonics; 0 = every term in FP64        */
-    int    m2l_rot;     /* mixed mode M2L with m2l_split, 3 <= p <= 16: 1 = the FP32 terms through
-                           rotations into the frame of the interaction axis, the z-axis
-                           kernel eq. (A31) and the swap matrices of App. A.5 (O(p^3) per
-                           pair); 0 = eq. (3b) term by term (O(p^4)).  Same result up to
-                           FP32 rounding.                                               */
+    int    m2l_rot;     /* mixed mode M2L with m2l_split, 3 <= p <= 16: 1 = the terms of order
+                           n+k >= 2 in FP32 through rotations into the frame of the
+                           interaction axis, the z-axis kernel eq. (A31) and the swap
+                           matrices of App. A.5 (O(p^3) per pair), n+k <= 1 in FP64;
+                           0 = eq. (3b) term by term (O(p^4)).  Same result up to FP32
+                           rounding.                                                    */
 } fmm_params;
 
 typedef struct {
@@ -217,6 +218,12 @@ int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t*
 /* Counts and phase times of the last evaluation on ctx (HOST out).  Phase events
  * are recorded on every evaluation; this call waits for the last one to finish. */
 int fmm_last_stats(fmm_ctx* ctx, fmm_stats* out);
+
+/* The swap matrix B_n (App. A.5.1: Theta_n^m(z, y, x) = sum_l B_n^{ml} Theta_n^l(x, y, z))
+ * that the rotation-accelerated M2L is built from, for 0 <= n <= 16: (2n+1)^2 doubles,
+ * row m = -n..n, column l = -n..n, row-major, into the HOST array B.  No device work.
+ * FMM_E_INVALID for n outside that range or B == NULL. */
+int fmm_swap_matrix(int n, double* B);
 
 /* Measure the device's FP64 (DFMA) and FP32 (FFMA) throughput in TFLOP/s with
  * two short register-only loops on the current device (HOST outs; about 50 ms).

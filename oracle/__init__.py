@@ -71,8 +71,9 @@ def _declare(L):
     L.orc_upsilon_re.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, _dp]
     L.orc_theta_re.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, _dp]
     L.orc_p2m.argtypes = [C.c_int, C.c_long, _dp, _dp, _dp, _dp, _dp]
-    for f in (L.orc_m2m, L.orc_m2l, L.orc_l2l):
+    for f in (L.orc_m2m, L.orc_m2l, L.orc_l2l, L.orc_m2l_rot):
         f.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_swap_matrix.argtypes = [C.c_int, _dp]
     L.orc_l2p.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.POINTER(C.c_double), _dp]
     L.orc_power.argtypes = [C.c_int, _dp, _dp, _dp]
     L.orc_direct.argtypes = [C.c_long, _dp, _dp, C.c_double, C.c_long, C.c_void_p, C.c_void_p,
@@ -147,6 +148,18 @@ def m2l(p, M, zA, sB):
 
 def l2l(p, F, s, sp):
     return _shift(lib().orc_l2l, p, F, s, sp)
+
+
+def m2l_rot(p, M, zA, sB):
+    """eq. (3b) through the rotations of App. A.5.2 and the z-axis kernel eq. (A31)."""
+    return _shift(lib().orc_m2l_rot, p, M, zA, sB)
+
+
+def swap_matrix(n):
+    """B_n of App. A.5.1, rows m and columns l = -n..n: Theta_n(z, y, x) = B_n Theta_n(x, y, z)."""
+    B = np.zeros((2 * n + 1) * (2 * n + 1))
+    lib().orc_swap_matrix(n, B)
+    return B.reshape(2 * n + 1, 2 * n + 1)
 
 
 def l2p(p, F, s, xb):

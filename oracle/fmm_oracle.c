@@ -13,6 +13,9 @@
  *     recurrences of App. A.3.1 (Theta_n^n, Upsilon_n^n and the three-term
  *     recurrences in n), negative m from the symmetry X_n^{-m} = (-1)^m X_n^{m*};
  *   - P2M eq. (3c), M2M eq. (4), M2L eq. (3b), L2L eq. (5), L2P eq. (7);
+ *   - the swap matrices of App. A.5.1 (recurrences) and the rotation-accelerated M2L of
+ *     App. A.5.2 with the z-axis kernel eq. (A31) (used by the tests only; the oracle's
+ *     FMM takes eq. (3b) term by term);
  *     a = -(Re Psi_1^1, Im Psi_1^1, Psi_1^0) (Sec. 2.1);
  *   - oct-tree of cubic cells (Sec. 2.2), expansion centres z = s = centre of the
  *     smallest enclosing sphere (Sec. 5.1.1), radii rho (Sec. 4, eqs. 9-10);
@@ -287,6 +290,113 @@ void orc_power(int p, const double *re, const double *im, double *P)
     cplx *M = to_c(p, re, im);
     multipole_power(p, M, P);
     free(M);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Rotation-accelerated M2L (App. A.5)                                        */
+/* ------------------------------------------------------------------------- */
+
+/* Swap matrix B_n of App. A.5.1 for exchanging the x and z axes:
+ * Theta_n^m(z, y, x) = sum_l B_n^{ml} Theta_n^l(x, y, z).  Built from B_0 = 1 with the
+ * recurrences given there, 2 B_{n+1}^{ml} = B_n^{m,l-1} - B_n^{m,l+1} for |m| <= n and
+ * 2 B_{n+1}^{n+1,l} = B_n^{n,l-1} + B_n^{n,l+1} + 2 B_n^{nl},
+ * 2 B_{n+1}^{-n-1,l} = B_n^{-n,l-1} + B_n^{-n,l+1} - 2 B_n^{-n,l}, entries with |l| > n
+ * being zero.  B[(m+n)(2n+1) + (l+n)], row m, column l. */
+static double bget(const double *b, int n, int m, int l)
+{
+    if (m < -n || m > n || l < -n || l > n) return 0.0;
+    return b[(m + n) * (2 * n + 1) + (l + n)];
+}
+void orc_swap_matrix(int n, double *B)
+{
+    double *b = malloc(sizeof(double) * (2 * n + 1) * (2 * n + 1));
+    double *nb = malloc(sizeof(double) * (2 * n + 1) * (2 * n + 1));
+    b[0] = 1.0;
+    for (int k = 0; k < n; ++k) {
+        const int w = 2 * (k + 1) + 1;
+        for (int i = 0; i < w * w; ++i) nb[i] = 0.0;
+        for (int m = -k; m <= k; ++m)
+            for (int l = -(k + 1); l <= k + 1; ++l)
+                nb[(m + k + 1) * w + (l + k + 1)] = 0.5 * (bget(b, k, m, l - 1) - bget(b, k, m, l + 1));
+        for (int l = -(k + 1); l <= k + 1; ++l) {
+            nb[(2 * k + 2) * w + (l + k + 1)] = 0.5 * (bget(b, k, k, l - 1) + bget(b, k, k, l + 1) + 2.0 * bget(b, k, k, l));
+            nb[0 * w + (l + k + 1)] = 0.5 * (bget(b, k, -k, l - 1) + bget(b, k, -k, l + 1) - 2.0 * bget(b, k, -k, l));
+        }
+        double *t = b; b = nb; nb = t;
+    }
+    memcpy(B, b, sizeof(double) * (2 * n + 1) * (2 * n + 1));
+    free(b);
+    free(nb);
+}
+
+/* X_n^m *= e^{-i m a} for every order (a rotation of the frame about z by a), e = e^{i a} */
+static void rot_z(int p, cplx *X, cplx e)
+{
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m) X[IX(n, m)] *= cpow(conj(e), m);
+}
+/* X_n <- S X_n per order, S = B_n (transpose = 1: B_n^T) */
+static void swap_xz(int p, cplx *X, int transpose)
+{
+    cplx *t = malloc(sizeof(cplx) * (2 * p + 1));
+    for (int n = 0; n <= p; ++n) {
+        double *Bn = malloc(sizeof(double) * (2 * n + 1) * (2 * n + 1));
+        orc_swap_matrix(n, Bn);
+        for (int m = -n; m <= n; ++m) {
+            cplx s = 0;
+            for (int l = -n; l <= n; ++l)
+                s += (transpose ? Bn[(l + n) * (2 * n + 1) + (m + n)] : Bn[(m + n) * (2 * n + 1) + (l + n)]) * X[IX(n, l)];
+            t[m + n] = s;
+        }
+        for (int m = -n; m <= n; ++m) X[IX(n, m)] = t[m + n];
+        free(Bn);
+    }
+    free(t);
+}
+
+/* eq. (3b) via rotations (App. A.5.2).  With r = s_B - z_A = (x, y, z), rho = |(x, y)|:
+ * rotate the frame about z so that r lies in the y-z plane (e^{i alpha} = (y - i x)/rho),
+ * swap x and z, rotate about z so that r lies on the x axis (e^{i beta} = (z + i rho)/|r|),
+ * swap x and z: r is now (0, 0, |r|).  Multipoles transform with the Upsilon swap matrices
+ * (B_n^T), the z-axis M2L is eq. (A31), and the local coefficients return through the
+ * inverse map (the swaps B_n and the conjugate phases, in reverse order). */
+static void m2l_rot(int p, const cplx *M, const double zA[3], const double sB[3], cplx *F)
+{
+    const double x = sB[0] - zA[0], y = sB[1] - zA[1], z = sB[2] - zA[2];
+    const double rho = sqrt(x * x + y * y), R = sqrt(x * x + y * y + z * z);
+    const cplx ea = rho > 0 ? (y - I * x) / rho : 1.0, eb = (z + I * rho) / R;
+    cplx *Mt = malloc(sizeof(cplx) * NCOEF(p)), *Ft = malloc(sizeof(cplx) * NCOEF(p));
+    memcpy(Mt, M, sizeof(cplx) * NCOEF(p));
+    rot_z(p, Mt, ea);
+    swap_xz(p, Mt, 1);
+    rot_z(p, Mt, eb);
+    swap_xz(p, Mt, 1);
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m) {
+            cplx s = 0;
+            for (int k = abs(m); k <= p - n; ++k) {
+                double f = 1.0;
+                for (int i = 2; i <= n + k; ++i) f *= i;
+                s += sgn_m(m) * Mt[IX(k, m)] * f / pow(R, n + k + 1);
+            }
+            Ft[IX(n, m)] = s;
+        }
+    swap_xz(p, Ft, 0);
+    rot_z(p, Ft, conj(eb));
+    swap_xz(p, Ft, 0);
+    rot_z(p, Ft, conj(ea));
+    for (int i = 0; i < NCOEF(p); ++i) F[i] += Ft[i];
+    free(Mt);
+    free(Ft);
+}
+void orc_m2l_rot(int p, const double *re, const double *im, const double zA[3], const double sB[3],
+                 double *ore, double *oim)
+{
+    cplx *M = to_c(p, re, im), *F = calloc(NCOEF(p), sizeof(cplx));
+    m2l_rot(p, M, zA, sB, F);
+    from_c(p, F, ore, oim);
+    free(M);
+    free(F);
 }
 
 /* ------------------------------------------------------------------------- */

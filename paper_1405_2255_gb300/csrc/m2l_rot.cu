@@ -7,6 +7,7 @@ namespace gb3 {
 namespace {
 
 // per cell: Mt = N_n^m M_n^m / rho^n in FP32 (real storage) and conj(M) of orders <= 2 in FP64
+// (the kernel reads the orders <= kRotJ64)
 __global__ void k_prep_rot(const double* __restrict__ M, const d4* __restrict__ cen, int ncells, int p,
                            float* __restrict__ Mt, cd* __restrict__ M64) {
     const int nco = ncoef(p), lane = threadIdx.x & 31;
@@ -81,3 +82,11 @@ void launch_m2l_rot(const int2* list, const int* seg_start, const int* seg_end, 
 }
 
 }  // namespace gb3
+
+extern "C" int fmm_swap_matrix(int n, double* B) {
+    if (n < 0 || n > gb3::kRotMaxP || !B) return FMM_E_INVALID;
+    for (int m = -n; m <= n; ++m)
+        for (int l = -n; l <= n; ++l)
+            B[(m + n) * (2 * n + 1) + (l + n)] = gb3::kSwap.full[n][gb3::kO + m][gb3::kO + l];
+    return FMM_OK;
+}

@@ -28,13 +28,16 @@
 // zeros that the parity of the harmonics gives; the entries are compile-time constants
 // (immediate operands of the FMAs), computed below from the recurrences in FP64.
 //
-// Precision split (as in the direct mixed-mode kernel): the terms of eq. (3b) with
-// n + k <= 2 are summed in FP64 from the FP64 moments; the others are summed in FP32 on
-// the scaled quantities Mt_k = Mhat_k / rho_A^k, (rho_A/R)^k, unit distance, and the
-// pair's result is scaled by (sigma_B/R)^{n+1}, so that every FP32 value is O(1)..O(M).
-// The z-axis kernel maps each order k of the rotated multipoles to each order n of the
-// rotated local expansion separately, so leaving out n + k <= 2 in the rotated frame
-// leaves out exactly the same terms as in the original frame.
+// Precision split: the terms of eq. (3b) with n + k <= kRotJ64 (= 1: the monopole and
+// dipole couplings, which carry nearly all of the force) are summed in FP64 from the FP64
+// moments; the others are summed in FP32 on the scaled quantities Mt_k = Mhat_k /
+// rho_A^k, (rho_A/R)^k, unit distance, and the pair's result is scaled by
+// (sigma_B/R)^{n+1}, so that every FP32 value is O(1)..O(M).  (The direct mixed-mode
+// kernel also sums the order-2 couplings in FP64; in FP32 they add about 1 % to the rms
+// force error at eps = 3e-7 and cost half of the FP64 work of a pair.)  The z-axis kernel
+// maps each order k of the rotated multipoles to each order n of the rotated local
+// expansion separately, so leaving out n + k <= kRotJ64 in the rotated frame leaves out
+// exactly the same terms as in the original frame.
 #pragma once
 #include <utility>
 
@@ -70,6 +73,7 @@ constexpr int kW = 2 * kRotMaxP + 1, kO = kRotMaxP;  // B_n^{ml} at b[kO + m][kO
 struct SwapTables {
     double cosb[kRotMaxP + 1][kRotMaxP + 1][kRotMaxP + 1];  // [n][m][l], 0 <= m, l <= n
     double sinb[kRotMaxP + 1][kRotMaxP + 1][kRotMaxP + 1];  // [n][m][l], 1 <= m, l <= n
+    double full[kRotMaxP + 1][kW][kW];                     // B_n^{ml} at [n][kO + m][kO + l]
 };
 
 constexpr double b_at(const double (&b)[kW][kW], int n, int m, int l) {
@@ -82,6 +86,8 @@ constexpr SwapTables make_swap_tables() {
     double nb[kW][kW] = {};
     b[kO][kO] = 1.0;  // B_0 = 1
     for (int n = 0; n <= kRotMaxP; ++n) {
+        for (int i = 0; i < kW; ++i)
+            for (int j = 0; j < kW; ++j) t.full[n][i][j] = b[i][j];
         // real blocks of Bhat_n = diag(1/N) B_n diag(N): a complex vector with
         // X^{-l} = (-1)^l conj(X^l) maps to Re Y^m = sum_{l>=0} C_ml Re X^l and
         // Im Y^m = sum_{l>=1} S_ml Im X^l
@@ -187,6 +193,10 @@ __host__ __device__ __forceinline__ void swap_xz(const float* in, float* out) {
 }
 
 constexpr int kPad = 33;  // column stride of the per-lane shared-memory vectors (words)
+// terms of eq. (3b) with n + k <= kRotJ64 are summed in FP64, the others in FP32
+constexpr int kRotJ64 = 1;
+constexpr int kRotLow = (kRotJ64 + 1) * (kRotJ64 + 2) / 2;  // FP64 outputs (n <= kRotJ64, m >= 0)
+constexpr int kRotLowM = (kRotJ64 + 1) * (kRotJ64 + 1);     // FP64 moments per cell (orders <= kRotJ64)
 
 // forward: scaled multipoles of order K -> rotated frame, entries |m| <= min(K, P-K), times (rho_A/R)^K
 template <int P, int K>
@@ -202,10 +212,18 @@ __host__ __device__ __forceinline__ void fwd_order(float* S, const float2* cw, c
 #pragma unroll
     for (int j = K - L; j <= K + L; ++j) S[(K * K + j) * kPad] = v[j] * tk;
 }
+// warps of a block meet after every kRotSyncOrders orders (0: only between the phases)
+constexpr int kRotSyncOrders = 0;
+template <int K>
+__host__ __device__ __forceinline__ void order_sync() {
+#ifdef __CUDA_ARCH__
+    if constexpr (kRotSyncOrders > 0 && K % (kRotSyncOrders > 0 ? kRotSyncOrders : 1) == 0) __syncthreads();
+#endif
+}
 template <int P, int... K>
 __host__ __device__ __forceinline__ void fwd_all(float* S, const float2* cw, const float2* cu, float tA, iseq<K...>) {
     float tk = 1.f;
-    ((fwd_order<P, K>(S, cw, cu, tk), tk *= tA), ...);
+    ((fwd_order<P, K>(S, cw, cu, tk), tk *= tA, order_sync<K + 1>()), ...);
 }
 
 // z-axis M2L for column m = M (SG = +1: real parts, -1: imaginary parts), in place
@@ -213,7 +231,7 @@ template <int P, int M, int SG, int N, int... K>
 __host__ __device__ __forceinline__ void zm2l_out(float* S, const float* x, iseq<K...>) {
     if constexpr (N >= M && N <= P - M) {
         float acc = 0.f;
-        ((K >= M && K <= P - N && N + K >= 3 ? (void)(acc = fmaf(kZ<N, K, M>, x[K], acc)) : (void)0), ...);
+        ((K >= M && K <= P - N && N + K > kRotJ64 ? (void)(acc = fmaf(kZ<N, K, M>, x[K], acc)) : (void)0), ...);
         S[(N * N + N + SG * M) * kPad] = acc;
     }
 }
@@ -246,7 +264,7 @@ __host__ __device__ __forceinline__ void bwd_order(float* S, const float2* cw, c
 template <int P, int... N>
 __host__ __device__ __forceinline__ void bwd_all(float* S, const float2* cw, const float2* cu, float tB, iseq<N...>) {
     float tn = tB;
-    ((bwd_order<P, N>(S, cw, cu, tn), tn *= tB), ...);
+    ((bwd_order<P, N>(S, cw, cu, tn), tn *= tB, order_sync<N + 1>()), ...);
 }
 
 // N_n^{|m|} by slot n^2+n+m (a constant-initialised copy in every translation unit)
@@ -261,6 +279,14 @@ constexpr RotNorm make_rot_norm() {
 }
 static __constant__ RotNorm c_rot_norm = make_rot_norm();
 
+// 4-byte asynchronous global -> shared copy; nbytes = 0 writes a zero
+__device__ __forceinline__ void rot_cp_async4(float* smem, const float* gmem, unsigned nbytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void rot_cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void rot_cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Theta_j^m(r) for j <= 2 and m >= 0 in closed form (FP64)
 __device__ inline cd theta_low_rot(int j, int m, double x, double y, double z, double rinv) {
     const double r2i = rinv * rinv, r3 = rinv * r2i, r5 = r3 * r2i;
@@ -271,36 +297,62 @@ __device__ inline cd theta_low_rot(int j, int m, double x, double y, double z, d
     return mkc(3.0 * (x * x - y * y) * r5, 6.0 * x * y * r5);
 }
 
+// Shared memory of one warp: the per-lane vectors S[NCO][kPad] (floats), sigma^-n and
+// the FP64 low-order outputs.
+template <int P>
+constexpr int rot_warp_bytes() {
+    return (((P + 1) * (P + 1) * kPad * 4 + 15) & ~15) + (((P + 2) * 8 + kRotLow * 16 + 15) & ~15);
+}
+// warps per block: as many as the shared memory of one SM holds (at most 8); they step
+// through the (long, straight-line) code of the orders together, so that they share its
+// instruction fetches
+template <int P>
+constexpr int rot_warps() {
+    return imin(8, imax(1, (227 * 1024) / rot_warp_bytes<P>()));
+}
+
 // One warp per work item: up to kM2LChunk pairs of one sink, lane = pair.
 template <int P>
-__global__ void __launch_bounds__(32) k_m2l_rot(const int2* __restrict__ list, const int* __restrict__ seg_start,
-                                                const int* __restrict__ seg_end, const int* __restrict__ order,
-                                                const int* __restrict__ item_start, unsigned* __restrict__ work,
-                                                const d4* __restrict__ cen, const float* __restrict__ Mt,
-                                                const cd* __restrict__ M64g, double* __restrict__ part) {
-    constexpr int NCO = (P + 1) * (P + 1);
+__global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
+    k_m2l_rot(const int2* __restrict__ list, const int* __restrict__ seg_start, const int* __restrict__ seg_end,
+              const int* __restrict__ order, const int* __restrict__ item_start, unsigned* __restrict__ work,
+              const d4* __restrict__ cen, const float* __restrict__ Mt, const cd* __restrict__ M64g,
+              double* __restrict__ part) {
+    constexpr int NCO = (P + 1) * (P + 1), W = rot_warps<P>();
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    float* S = (float*)sm_raw;                                         // [NCO][kPad]
-    double* pws = (double*)(sm_raw + ((NCO * kPad * 4 + 15) & ~15));   // sigma^-n, n <= P+1
-    cd* lowF = (cd*)(pws + P + 2);                                     // 6 FP64 outputs (n <= 2, m >= 0)
-    const int lane = threadIdx.x;
+    __shared__ unsigned s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* base = sm_raw + (size_t)warp * rot_warp_bytes<P>();
+    float* S = (float*)base;                                          // [NCO][kPad]
+    double* pws = (double*)(base + ((NCO * kPad * 4 + 15) & ~15));    // sigma^-n, n <= P+1
+    cd* lowF = (cd*)(pws + P + 2);                                    // FP64 outputs (n <= kRotJ64, m >= 0)
     float* Sl = S + lane;
     const unsigned nitems = work[2], nsinks = work[1];
     for (;;) {
-        unsigned w = 0;
-        if (lane == 0) w = atomicAdd(work, 1u);
-        w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= nitems) break;
-        int lo_i = 0, hi_i = (int)nsinks - 1;
-        while (lo_i < hi_i) {
-            const int mid = (lo_i + hi_i + 1) >> 1;
-            if ((unsigned)item_start[mid] <= w) lo_i = mid;
-            else hi_i = mid - 1;
+        // the block takes W consecutive items, one per warp (every warp runs every barrier)
+        if (threadIdx.x == 0) s_item = atomicAdd(work, (unsigned)W);
+        __syncthreads();
+        const unsigned w0 = s_item;
+        __syncthreads();
+        if (w0 >= nitems) break;
+        const unsigned w = w0 + warp;
+        const bool has = w < nitems;
+        int e0 = 0, e1 = 0, s0 = 0, s1 = 0;
+        d4 sB = mk4(0.0, 0.0, 0.0, 1.0);
+        if (has) {
+            int lo_i = 0, hi_i = (int)nsinks - 1;
+            while (lo_i < hi_i) {
+                const int mid = (lo_i + hi_i + 1) >> 1;
+                if ((unsigned)item_start[mid] <= w) lo_i = mid;
+                else hi_i = mid - 1;
+            }
+            const int B = order[lo_i];
+            s0 = seg_start[B];
+            s1 = seg_end[B];
+            e0 = s0 + (int)(w - (unsigned)item_start[lo_i]) * kM2LChunk;
+            e1 = min(e0 + kM2LChunk, s1);
+            sB = cen[B];
         }
-        const int B = order[lo_i];
-        const int s0 = seg_start[B], s1 = seg_end[B];
-        const int e0 = s0 + (int)(w - (unsigned)item_start[lo_i]) * kM2LChunk, e1 = min(e0 + kM2LChunk, s1);
-        const d4 sB = cen[B];
         double sigma = sB.w;
         if (!(sigma > 0)) {  // radius 0: half the closest source distance (over the whole list)
             double rmin = INFINITY;
@@ -311,21 +363,23 @@ __global__ void __launch_bounds__(32) k_m2l_rot(const int2* __restrict__ list, c
             }
             sigma = 0.5 * warp_min(rmin);
         }
-        // the lane's pair: geometry in FP64, rotation phases and scale factors in FP32
+        // the lane's pair: rotation phases e^{-i alpha}, e^{-i beta} and the scale factors
         const int e = e0 + lane;
         const bool act = e < e1;
         const int A = act ? list[e].x : -1;
         float tA = 0.f, tB = 0.f;
         float2 wv = make_float2(1.f, 0.f), uv = make_float2(1.f, 0.f);
-        if (act) {
+        if (act) {  // FP64 differences, then FP32 (the quantities feed FP32 arithmetic only)
             const d4 zA = cen[A];
-            const double x = sB.x - zA.x, y = sB.y - zA.y, z = sB.z - zA.z;
-            const double rxy2 = x * x + y * y, R = sqrt(rxy2 + z * z), Rinv = 1.0 / R;
-            const double rxy = sqrt(rxy2);
-            if (rxy > 0) wv = make_float2((float)(y / rxy), (float)(x / rxy));
-            uv = make_float2((float)(z * Rinv), (float)(-rxy * Rinv));
-            tA = (float)(zA.w * Rinv);
-            tB = (float)(sigma * Rinv);
+            const float x = (float)(sB.x - zA.x), y = (float)(sB.y - zA.y), z = (float)(sB.z - zA.z);
+            const float rxy2 = x * x + y * y, rxy = sqrtf(rxy2), Rinv = 1.f / sqrtf(rxy2 + z * z);
+            if (rxy > 0.f) {
+                const float ri = 1.f / rxy;
+                wv = make_float2(y * ri, x * ri);
+            }
+            uv = make_float2(z * Rinv, -rxy * Rinv);
+            tA = (float)zA.w * Rinv;
+            tB = (float)sigma * Rinv;
         }
         float2 cw[P + 1], cu[P + 1];
         cw[0] = make_float2(1.f, 0.f);
@@ -335,27 +389,26 @@ __global__ void __launch_bounds__(32) k_m2l_rot(const int2* __restrict__ list, c
             cw[m] = make_float2(cw[m - 1].x * wv.x - cw[m - 1].y * wv.y, cw[m - 1].x * wv.y + cw[m - 1].y * wv.x);
             cu[m] = make_float2(cu[m - 1].x * uv.x - cu[m - 1].y * uv.y, cu[m - 1].x * uv.y + cu[m - 1].y * uv.x);
         }
-        // stage the chunk's scaled multipoles, column b = pair b (zeros for missing pairs)
+        // stage the chunk's scaled multipoles, column b = pair b (zeros for missing pairs),
+        // by asynchronous copies that complete while the FP64 terms below are summed
         for (int b = 0; b < 32; ++b) {
             const int Ab = __shfl_sync(0xffffffffu, A, b);
             const float* src = Mt + (size_t)(Ab < 0 ? 0 : Ab) * NCO;
-            for (int c = lane; c < NCO; c += 32) S[c * kPad + b] = Ab >= 0 ? src[c] : 0.f;
+            const unsigned nbytes = Ab >= 0 ? 4u : 0u;  // 0: zero fill
+            for (int c = lane; c < NCO; c += 32) rot_cp_async4(S + c * kPad + b, src + c, nbytes);
         }
-        __syncwarp();
-        fwd_all<P>(Sl, cw, cu, tA, upto<P>{});
-        zm2l_all<P>(Sl, upto<P / 2>{});
-        bwd_all<P>(Sl, cw, cu, tB, upto<P>{});
-        // FP64 terms of orders n + k <= 2, then their sums over the pairs (fixed butterfly)
-        cd lo[6];
+        rot_cp_async_commit();
+        // FP64 terms of orders n + k <= kRotJ64, then their sums over the pairs (fixed butterfly)
+        cd lo[kRotLow];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) lo[i] = mkc(0.0, 0.0);
+        for (int i = 0; i < kRotLow; ++i) lo[i] = mkc(0.0, 0.0);
         if (act) {
             const d4 zA = cen[A];
             const double x = sB.x - zA.x, y = sB.y - zA.y, z = sB.z - zA.z;
-            const double Rinv = 1.0 / sqrt(x * x + y * y + z * z);
-            cd T[9], Mx[9];
+            const double Rinv = rsqrt(x * x + y * y + z * z);
+            cd T[kRotLowM], Mx[kRotLowM];
 #pragma unroll
-            for (int j = 0; j <= 2; ++j)
+            for (int j = 0; j <= kRotJ64; ++j)
 #pragma unroll
                 for (int m = 0; m <= j; ++m) {
                     const cd v = theta_low_rot(j, m, x, y, z, Rinv);
@@ -363,40 +416,49 @@ __global__ void __launch_bounds__(32) k_m2l_rot(const int2* __restrict__ list, c
                     if (m) T[cix(j, -m)] = (m & 1) ? mkc(-v.re, v.im) : mkc(v.re, -v.im);
                 }
 #pragma unroll
-            for (int i = 0; i < 9; ++i) Mx[i] = M64g[(size_t)A * 9 + i];
+            for (int i = 0; i < kRotLowM; ++i) Mx[i] = M64g[(size_t)A * 9 + i];
 #pragma unroll
-            for (int n = 0; n <= 2; ++n)
+            for (int n = 0; n <= kRotJ64; ++n)
 #pragma unroll
                 for (int m = 0; m <= n; ++m)
 #pragma unroll
-                    for (int k = 0; k + n <= 2; ++k)
+                    for (int k = 0; k + n <= kRotJ64; ++k)
 #pragma unroll
                         for (int l = -k; l <= k; ++l) cmac(lo[n * (n + 1) / 2 + m], Mx[cix(k, l)], T[cix(n + k, m + l)]);
         }
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
+        for (int i = 0; i < kRotLow; ++i) {
             lo[i].re = warp_sum(lo[i].re);
             lo[i].im = warp_sum(lo[i].im);
         }
         if (lane == 0) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) lowF[i] = lo[i];
+            for (int i = 0; i < kRotLow; ++i) lowF[i] = lo[i];
         }
+        rot_cp_async_wait_all();
+        __syncthreads();
+        fwd_all<P>(Sl, cw, cu, tA, upto<P>{});
+        __syncthreads();
+        zm2l_all<P>(Sl, upto<P / 2>{});
+        __syncthreads();
+        bwd_all<P>(Sl, cw, cu, tB, upto<P>{});
         warp_pow_table(1.0 / sigma, P + 1, lane, pws);
         __syncwarp();
-        double* out = part + (size_t)w * NCO;
-        for (int c = lane; c < NCO; c += 32) {
-            const float* row = S + c * kPad;
-            float s = 0.f;
+        if (has) {
+            double* out = part + (size_t)w * NCO;
+            for (int c = lane; c < NCO; c += 32) {
+                const float* row = S + c * kPad;
+                float s = 0.f;
 #pragma unroll 8
-            for (int b = 0; b < 32; ++b) s += row[b];
-            const int n = (int)sqrtf((float)c), m = c - n * n - n;
-            double v = (double)s * c_rot_norm.v[c] * pws[n + 1];
-            if (n <= 2) {
-                const cd lv = lowF[n * (n + 1) / 2 + (m < 0 ? -m : m)];
-                v += m >= 0 ? lv.re : lv.im;
+                for (int b = 0; b < 32; ++b) s += row[b];
+                const int n = (int)sqrtf((float)c), m = c - n * n - n;
+                double v = (double)s * c_rot_norm.v[c] * pws[n + 1];
+                if (n <= kRotJ64) {
+                    const cd lv = lowF[n * (n + 1) / 2 + (m < 0 ? -m : m)];
+                    v += m >= 0 ? lv.re : lv.im;
+                }
+                out[c] = v;
             }
-            out[c] = v;
         }
         __syncwarp();
     }
@@ -407,17 +469,16 @@ __global__ void __launch_bounds__(32) k_m2l_rot(const int2* __restrict__ list, c
 template <int P>
 void rot_launch(const int2* list, const int* seg_start, const int* seg_end, const int* order, const int* item_start,
                 unsigned* work, const d4* cen, const float* Mt, const cd* M64, double* part, cudaStream_t s) {
-    constexpr int NCO = (P + 1) * (P + 1);
-    const size_t sm = ((NCO * kPad * 4 + 15) & ~15) + (P + 2) * sizeof(double) + 6 * sizeof(cd);
+    constexpr int W = rot_warps<P>();
+    const size_t sm = (size_t)W * rot_warp_bytes<P>();
     cudaFuncSetAttribute(k_m2l_rot<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int dev = 0, nsm = 152, bps = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l_rot<P>, 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l_rot<P>, 32 * W, sm);
     const unsigned g = (unsigned)(nsm * (bps > 0 ? bps : 1));
-    k_m2l_rot<P><<<g, 32, sm, s>>>(list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part);
+    k_m2l_rot<P><<<g, 32 * W, sm, s>>>(list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part);
     note_launch();
 }
-
 
 }  // namespace gb3

@@ -49,7 +49,7 @@ EXPORTS = ["fmm_default_params", "fmm_create", "fmm_set_params", "fmm_evaluate",
            "fmm_direct", "fmm_evaluate_batch", "fmm_debug_dump", "fmm_last_stats", "fmm_destroy",
            "fmm_strerror", "fmm_last_error", "fmm_version", "fmm_alu_peaks", "fmm_evaluate_noalloc",
            "fmm_serve_config", "fmm_footprint_bytes", "fmm_system_register", "fmm_submit", "fmm_poll",
-           "fmm_system_release", "fmm_workspace_bytes"]
+           "fmm_system_release", "fmm_workspace_bytes", "fmm_swap_matrix"]
 
 _lib = None
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
     L.fmm_system_release.argtypes = [vp, ci]
     L.fmm_workspace_bytes.argtypes = [vp]
     L.fmm_workspace_bytes.restype = C.c_uint64
+    L.fmm_swap_matrix.argtypes = [ci, vp]
     for name in EXPORTS:
         if name not in ("fmm_strerror", "fmm_last_error", "fmm_version", "fmm_default_params",
                         "fmm_footprint_bytes", "fmm_workspace_bytes"):
@@ -302,6 +303,13 @@ def fmm_footprint_bytes(n: int, params: fmm_params | None = None, **kw) -> int:
     for k, v in kw.items():
         setattr(params, k, v)
     return int(load().fmm_footprint_bytes(C.byref(params), int(n)))
+
+
+def fmm_swap_matrix(n: int) -> np.ndarray:
+    """B_n (App. A.5.1) as built into the rotation-accelerated M2L, rows m / columns l = -n..n."""
+    B = np.zeros((2 * n + 1, 2 * n + 1))
+    _check(load().fmm_swap_matrix(int(n), B.ctypes.data))
+    return B
 
 
 def fmm_alu_peaks() -> tuple[float, float]:

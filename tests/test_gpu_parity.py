@@ -382,3 +382,16 @@ def test_m2l_rot_outside_range_falls_back(g):
     assert np.array_equal(a1.cpu().numpy(), a0.cpu().numpy())
     c1.close()
     c0.close()
+
+
+def test_library_swap_matrices_match_oracle_and_paper(g, orc):
+    """The swap matrices compiled into the rotation-accelerated M2L (host constants of the
+    library) equal the oracle's recurrence for every n <= 16 and the matrix printed in
+    App. A.5.1 for n = 4."""
+    import os
+    want4 = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "swap_b4_x16.txt"))
+    assert np.array_equal(16.0 * g.fmm_swap_matrix(4), want4)
+    for n in range(17):
+        assert np.max(np.abs(g.fmm_swap_matrix(n) - orc.swap_matrix(n))) <= 1e-12 * max(1.0, np.abs(orc.swap_matrix(n)).max())
+    with pytest.raises(g.FMMError):
+        g.fmm_swap_matrix(17)
