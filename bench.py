@@ -37,10 +37,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--p", type=int, default=14)
-    ap.add_argument("--eps", type=float, default=3e-7)
-    ap.add_argument("--leaf", type=int, default=80)
-    ap.add_argument("--c", type=float, default=1.0)
+    ap.add_argument("--p", type=int, default=None, help="expansion order (default: per workload, below)")
+    ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--leaf", type=int, default=None)
+    ap.add_argument("--c", type=float, default=None)
     ap.add_argument("--cpu-sample", type=int, default=50000)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-mode and direct-sum comparisons")
     ap.add_argument("--workload", default="plummer", choices=["plummer", "cusp", "ensemble", "serve"],
@@ -51,11 +51,16 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="choose (p, eps, leaf, p2p_c) for rms 1e-7 on the workload first (untimed)")
     a = ap.parse_args()
-    if a.workload == "cusp":
-        if a.n == 1_000_000:
-            a.n = 10_000_000
-        if a.eps == 3e-7:  # the cusp needs a smaller eps for the same rms error
-            a.eps = 2.5e-7
+    if a.workload == "cusp" and a.n == 1_000_000:
+        a.n = 10_000_000
+    # (p, eps, leaf, p2p_c) per workload from the autotuner at rms 1e-7 (eps with a margin):
+    # the single large systems take leaf 80; ensembles of small systems leaf 48, where
+    # large leaves let accepted pairs with theta near 1 dominate the error
+    dflt = {"plummer": (14, 3e-7, 80, 1.0), "cusp": (14, 2.6e-7, 80, 1.0),
+            "ensemble": (14, 3.6e-7, 48, 1.0), "serve": (14, 3.6e-7, 48, 1.0)}[a.workload]
+    for k, v in zip(("p", "eps", "leaf", "c"), dflt):
+        if getattr(a, k) is None:
+            setattr(a, k, v)
     return a
 
 
