@@ -150,6 +150,20 @@ int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, doubl
                int64_t nsinks, const int64_t* sinks, double* psi, double* acc, double* f,
                void* stream);
 
+/* Forces for a subset of the particles (Sec. 7.1: block time steps).  All n particles
+ * act as sources; active (DEVICE, n bytes, caller order) marks the sinks: psi[i] and
+ * acc[i] are written for active[i] != 0 only and left untouched otherwise.  The tree and
+ * the upward pass cover all particles; the walk drops every cell pair whose sink cell
+ * holds no active particle, so M2L, P2P, L2L and L2P run for the active part of the tree
+ * only.  The MAC scale of a sink cell (eqs. 18a,b) is the minimum over its ACTIVE
+ * particles, and the low-order estimate of Sec. 5.3.2 is evaluated for the active sinks:
+ * the error criterion concerns the forces being computed.  With every particle active
+ * the result equals fmm_evaluate's bit for bit.  Other arguments and errors as for
+ * fmm_evaluate; FMM_E_INVALID also for active == NULL with n > 0. */
+int fmm_evaluate_active(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G,
+                        const double* scale, const unsigned char* active, double* psi, double* acc,
+                        void* stream, fmm_stats* stats);
+
 /* Many independent systems in one call (the batched ensemble).  System s holds
  * particles [offsets[s], offsets[s+1]) of x/mu/psi/acc (device arrays laid out as
  * for fmm_evaluate); offsets is a HOST int64 array of nsys+1 non-decreasing entries

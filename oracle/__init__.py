@@ -83,6 +83,8 @@ def _declare(L):
     L.orc_meb_balls.argtypes = [C.c_int, _dp, _dp, _dp, C.POINTER(C.c_double)]
     L.orc_fmm.argtypes = [C.c_long, _dp, _dp, C.c_double, C.POINTER(Params), C.c_void_p]
     L.orc_fmm.restype = C.c_void_p
+    L.orc_fmm_active.argtypes = [C.c_long, _dp, _dp, C.c_double, C.POINTER(Params), C.c_void_p, C.c_void_p]
+    L.orc_fmm_active.restype = C.c_void_p
     L.orc_run_free.argtypes = [C.c_void_p]
     L.orc_run_outputs.argtypes = [C.c_void_p, _dp, _dp]
     L.orc_run_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
@@ -224,8 +226,9 @@ class Run:
 
 
 def fmm(x, mu, G=1.0, p=6, eps=1e-7, mac=MAC_A, theta_crit=0.5, leaf_size=32, p2p_c=1.0,
-        scale=None, keep=True):
-    """Run the oracle FMM; raises ValueError on invalid input."""
+        scale=None, keep=True, active=None):
+    """Run the oracle FMM; raises ValueError on invalid input.  active (bool/uint8 [n],
+    caller order): forces for that subset only (Sec. 7.1), NaN for the others."""
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     prm = Params(p, eps, mac, theta_crit, leaf_size, p2p_c, 1 if scale is not None else 0)
@@ -233,7 +236,9 @@ def fmm(x, mu, G=1.0, p=6, eps=1e-7, mac=MAC_A, theta_crit=0.5, leaf_size=32, p2
     if scale is not None:
         sc = np.ascontiguousarray(scale, dtype=np.float64)
     L = lib()
-    h = L.orc_fmm(len(mu), x, mu, G, C.byref(prm), sc.ctypes.data if sc is not None else None)
+    act = None if active is None else np.ascontiguousarray(np.asarray(active) != 0, dtype=np.uint8)
+    h = L.orc_fmm_active(len(mu), x, mu, G, C.byref(prm), sc.ctypes.data if sc is not None else None,
+                         act.ctypes.data if act is not None else None)
     if not h:
         raise ValueError("oracle rejected the input")
     try:

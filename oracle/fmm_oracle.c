@@ -697,12 +697,14 @@ typedef struct {
     double s[3], rho, mass;  /* centre z = s (smallest enclosing sphere), radius, mass */
     double com[3], rho_com;  /* centre of mass and its radius (low-order estimator) */
     double minscale;         /* min over the cell's sinks of the acceleration scale */
+    long nactive;            /* active particles in the cell (Sec. 7.1; all when no subset) */
 } cell_t;
 
 typedef struct {
     long n;
     double *xs, *mus;     /* sorted positions [n][3] and masses */
     long *perm;           /* perm[i] = original index of sorted particle i */
+    unsigned char *act;   /* act[i]: sorted particle i is an active sink (Sec. 7.1) */
     uint64_t *keys;
     cell_t *cells;
     long ncells, cap;
@@ -818,7 +820,7 @@ static void build_tree(tree_t *t, long n, const double *x, const double *mu, int
 
 static void free_tree(tree_t *t)
 {
-    free(t->xs); free(t->mus); free(t->perm); free(t->keys); free(t->cells);
+    free(t->xs); free(t->mus); free(t->perm); free(t->act); free(t->keys); free(t->cells);
     memset(t, 0, sizeof(*t));
 }
 
@@ -908,6 +910,7 @@ static int accept(const walk_t *w, long A, long B)
 static void walk(walk_t *w, long A, long B)
 {
     const cell_t *a = &w->t->cells[A], *b = &w->t->cells[B];
+    if (!b->nactive) return;  /* Sec. 7.1: only sink cells holding an active particle */
     if ((double)a->count * (double)b->count < w->p2p_thresh) { push(&w->p2p, A, B); return; }
     if (A == B) {
         if (a->leaf) { push(&w->p2p, A, B); return; }
@@ -1041,7 +1044,8 @@ static void min_scale(tree_t *t, long ci, const double *scale)
     cell_t *c = &t->cells[ci];
     double m = INFINITY;
     if (c->leaf) {
-        for (long i = c->first; i < c->first + c->count; ++i) if (scale[i] < m) m = scale[i];
+        for (long i = c->first; i < c->first + c->count; ++i)
+            if (t->act[i] && scale[i] < m) m = scale[i];  /* over the active sinks */
     } else {
         for (long j = 0; j < c->nchild; ++j) {
             min_scale(t, c->child + j, scale);
@@ -1061,8 +1065,13 @@ static int depth_of(const tree_t *t)
 void orc_run_free(orc_run *run);
 
 /* The whole FMM (Sec. 2.2.2): returns NULL on invalid input. */
-orc_run *orc_fmm(long n, const double *x, const double *mu, double G, const orc_params *prm,
-                 const double *scale_in /* caller order, may be NULL */)
+/* Sec. 7.1: active (caller order, may be NULL = all) marks the sinks whose forces are
+ * computed; all particles are sources.  Sink cells without an active particle take part
+ * in no interaction; the MAC scale of a cell is the minimum over its active particles;
+ * psi and acc of inactive particles are NaN. */
+orc_run *orc_fmm_active(long n, const double *x, const double *mu, double G, const orc_params *prm,
+                        const double *scale_in /* caller order, may be NULL */,
+                        const unsigned char *active /* caller order, may be NULL */)
 {
     if (n < 0 || !prm || prm->p < 1 || prm->p > 20 || prm->leaf_size < 1) return NULL;
     if (prm->mac != MAC_THETA && !(prm->eps > 0)) return NULL;
@@ -1081,6 +1090,13 @@ orc_run *orc_fmm(long n, const double *x, const double *mu, double G, const orc_
     build_tree(t, n, x, mu, prm->leaf_size);
     cell_geometry(t, 0);
     long nc = t->ncells;
+    t->act = malloc(n);
+    for (long i = 0; i < n; ++i) t->act[i] = active ? (active[t->perm[i]] != 0) : 1;
+    for (long ci = 0; ci < nc; ++ci) {
+        cell_t *c = &t->cells[ci];
+        c->nactive = 0;
+        for (long i = c->first; i < c->first + c->count; ++i) c->nactive += t->act[i];
+    }
     run->st.ncells = nc;
     for (long i = 0; i < nc; ++i) run->st.nleaves += t->cells[i].leaf;
     run->st.depth = depth_of(t);
@@ -1146,9 +1162,14 @@ orc_run *orc_fmm(long n, const double *x, const double *mu, double G, const orc_
                 l2l(p, &F[ci * nco], c->s, t->cells[c->child + j].s, &F[(c->child + j) * nco]);
         } else {
             for (long i = c->first; i < c->first + c->count; ++i) {
+                long o = t->perm[i];
+                if (!t->act[i]) {
+                    run->psi[o] = NAN;
+                    for (int d = 0; d < 3; ++d) run->acc[3 * o + d] = NAN;
+                    continue;
+                }
                 double psi_l, a[3];
                 l2p(p, &F[ci * nco], c->s, &t->xs[3 * i], &psi_l, a);
-                long o = t->perm[i];
                 run->psi[o] = G * (psi_l + ps[i]);
                 for (int d = 0; d < 3; ++d) run->acc[3 * o + d] = G * (a[d] + ac[3 * i + d]);
             }
@@ -1156,6 +1177,12 @@ orc_run *orc_fmm(long n, const double *x, const double *mu, double G, const orc_
     }
     free(ps); free(ac); free(M); free(F); free(P); free(w.binom);
     return run;
+}
+
+orc_run *orc_fmm(long n, const double *x, const double *mu, double G, const orc_params *prm,
+                 const double *scale_in /* caller order, may be NULL */)
+{
+    return orc_fmm_active(n, x, mu, G, prm, scale_in, NULL);
 }
 
 void orc_run_free(orc_run *run)

@@ -90,6 +90,9 @@ struct fmm_ctx {
     // on the device, roots (first, count) of the non-empty systems
     Buf sys_off, sys_G, sys_roots, skey, skey_alt, spos, spos_alt;
     int nsys = 0, nroots = 1;
+    // force evaluation for a subset (Sec. 7.1): per sorted particle and per cell activity
+    Buf pact, act, act_i, act_scan;
+    bool active_mode = false;
     std::vector<Buf*> bufs() {
         return {&hx, &hmu, &hpsi, &hacc, &bounds, &status, &counters, &coin, &dtotal, &keys, &keys_alt, &idx,
                 &idx_alt, &rtmp, &xm, &perm, &xhi, &xlo, &first, &count, &child, &nchild, &parent, &level, &sr,
@@ -97,7 +100,7 @@ struct fmm_ctx {
                 &leaf_pos, &rad_tmp, &M, &F, &Pw, &binom, &M1, &F1, &Ff, &front0, &front1, &m2l, &p2p,
                 &sort_tmp, &m2l_tmp, &p2p_tmp, &seg_start, &seg_end, &est_m2l, &est_p2p, &m2l_seg_start,
                 &m2l_seg_end, &psi_far, &acc_far, &psi_near, &acc_near, &scale_sorted, &sys_off, &sys_G,
-                &sys_roots, &skey, &skey_alt, &spos, &spos_alt};
+                &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan};
     }
     // tree shape of the last evaluation
     std::vector<int> lev_start;
@@ -141,6 +144,10 @@ static Cells cells_of(fmm_ctx* ctx) {
     c.cr = P<d4>(ctx->cr);
     c.mass = P<double>(ctx->mass);
     c.minscale = P<double>(ctx->minscale);
+    if (ctx->active_mode) {
+        c.act = P<unsigned char>(ctx->act);
+        c.pact = P<unsigned char>(ctx->pact);
+    }
     return c;
 }
 
@@ -426,8 +433,10 @@ static int phase_times(fmm_ctx* ctx) {
 
 // ------------------------------------------------------------------ one evaluation
 static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* mu, double G, const double* scale,
-                           double* psi, double* acc, cudaStream_t s, fmm_stats* stats) {
+                           double* psi, double* acc, cudaStream_t s, fmm_stats* stats,
+                           const unsigned char* active = nullptr) {
     const fmm_params& prm = ctx->prm;
+    ctx->active_mode = false;
     if (check_params(&prm)) return fail(ctx, FMM_E_INVALID, "invalid parameters");
     memset(&ctx->last, 0, sizeof ctx->last);
     ctx->last.n = n;
@@ -450,6 +459,16 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     CU(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), s));
     CU(cudaMemsetAsync(ctx->coin.p, 0, sizeof(unsigned long long), s));
     TRY(build_tree(ctx, n, x, mu, s));
+    if (active) {  // Sec. 7.1: only sink cells holding an active particle are evaluated
+        TRY(ensure(ctx->pact, (size_t)n));
+        TRY(ensure(ctx->act, (size_t)ctx->ncells));
+        TRY(ensure(ctx->act_i, sizeof(int) * ((size_t)n + 1)));
+        TRY(ensure(ctx->act_scan, sizeof(int) * ((size_t)n + scan_tmp_ints(n))));
+        launch_active_flags(active, P<int>(ctx->perm), n, P<int>(ctx->first), P<int>(ctx->count), ctx->ncells,
+                            P<unsigned char>(ctx->pact), P<unsigned char>(ctx->act), P<int>(ctx->act_i),
+                            P<int>(ctx->act_scan), P<int>(ctx->act_scan) + n, s);
+        ctx->active_mode = true;
+    }
     if (timing) CU(cudaEventRecord(ctx->ev[EV_TREE], s));
     const int nc = ctx->ncells, nco = ncoef(prm.p);
     const int nlev = (int)ctx->lev_start.size() - 1;
@@ -555,7 +574,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
                    P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
     launch_finish(P<double>(ctx->psi_far), P<double>(ctx->acc_far), P<double>(ctx->psi_near), P<double>(ctx->acc_near),
                   P<int>(ctx->perm), n, G, psi, acc, s, sys_off, ctx->nsys ? P<double>(ctx->sys_G) : nullptr,
-                  ctx->nsys);
+                  ctx->nsys, ctx->active_mode ? P<unsigned char>(ctx->pact) : nullptr);
     if (timing) {
         CU(cudaEventRecord(ctx->ev[EV_DOWN], s));
         CU(cudaEventRecord(ctx->ev[EV_END], s));
@@ -662,6 +681,17 @@ int fmm_evaluate(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, dou
     if (!std::isfinite(G)) return fail(ctx, FMM_E_INVALID, "G is not finite");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, FMM_E_CUDA, "cudaSetDevice failed");
     return evaluate_device(ctx, (int)n, x, mu, G, scale, psi, acc, (cudaStream_t)stream, stats);
+}
+
+int fmm_evaluate_active(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, const double* scale,
+                        const unsigned char* active, double* psi, double* acc, void* stream, fmm_stats* stats) {
+    if (!ctx) return FMM_E_INVALID;
+    ctx->err[0] = 0;
+    if (n < 0 || n > 0x7fffffffLL) return fail(ctx, FMM_E_INVALID, "n out of range");
+    if (n > 0 && (!x || !mu || !psi || !acc || !active)) return fail(ctx, FMM_E_INVALID, "NULL buffer");
+    if (!std::isfinite(G)) return fail(ctx, FMM_E_INVALID, "G is not finite");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, FMM_E_CUDA, "cudaSetDevice failed");
+    return evaluate_device(ctx, (int)n, x, mu, G, scale, psi, acc, (cudaStream_t)stream, stats, active);
 }
 
 int fmm_evaluate_host(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, double* psi, double* acc,

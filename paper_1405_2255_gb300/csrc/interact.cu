@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(128) k_l2l(Cells c, const d4* __restrict__ cen
     cd* X = csm + (size_t)wid * 2 * nco;
     cd* Y = X + nco;
     int cell = lev_begin + blockIdx.x * wpb + wid;
-    if (cell >= lev_end) return;
+    if (cell >= lev_end || !cell_active(c, cell)) return;
     int par = c.parent[cell];
     const d4 s = cen[par], sp = cen[cell];
     if (lane <= p) upsilon_column(p, lane, s.x - sp.x, s.y - sp.y, s.z - sp.z, X, true);
@@ -661,6 +661,7 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p(const d4* __restrict__ xm, 
     const int nco = ncoef(p);
     for (int t = blockIdx.x; t < nleaves; t += gridDim.x) {
         const int cell = leaves[t];
+        if (!cell_active(c, cell)) continue;  // block-uniform
         __syncthreads();
         expand_real(p, F + (size_t)cell * nco, Fc, false, threadIdx.x, blockDim.x);
         __syncthreads();
@@ -742,6 +743,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_fp64(const d4* __restric
     d4* tile = tile_all[wid];
     for (int t = blockIdx.x * kP2PWarps + wid; t < nleaves; t += gridDim.x * kP2PWarps) {
         const int leaf = leaves[t];
+        if (!cell_active(c, leaf)) continue;
         const int first = c.first[leaf], count = c.count[leaf];
         for (int s0 = 0; s0 < count; s0 += 32) {
             const int i = first + s0 + lane;
@@ -1042,6 +1044,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float* __
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= (unsigned)nleaves) break;
         const int leaf = order[w];
+        if (!cell_active(c, leaf)) continue;
         const int first = c.first[leaf], count = c.count[leaf];
         for (int s0 = 0; s0 < count; s0 += 32) {
             const int chunk = min(32, count - s0);
@@ -1336,8 +1339,9 @@ void launch_norm_scale(const double* /*psi_far*/, const double* acc_far, const d
 __global__ void k_finish(const double* __restrict__ pf, const double* __restrict__ af, const double* __restrict__ pn,
                          const double* __restrict__ an, const int* __restrict__ perm, int n, double G,
                          double* __restrict__ psi, double* __restrict__ acc, const int* __restrict__ off,
-                         const double* __restrict__ Gsys, int nsys) {
+                         const double* __restrict__ Gsys, int nsys, const unsigned char* __restrict__ pact) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (pact && !pact[i]) continue;  // outputs of inactive particles are left as they are
         int o = perm[i];
         if (Gsys) {  // the system of sorted particle i (systems keep their blocks when sorted)
             int lo = 0, hi = nsys - 1;
@@ -1355,10 +1359,10 @@ __global__ void k_finish(const double* __restrict__ pf, const double* __restrict
 }
 void launch_finish(const double* psi_far, const double* acc_far, const double* psi_near, const double* acc_near,
                    const int* perm, int n, double G, double* psi, double* acc, cudaStream_t s, const int* off,
-                   const double* Gsys, int nsys) {
+                   const double* Gsys, int nsys, const unsigned char* pact) {
     if (n > 0)
         k_finish<<<grid_for(n, 256), 256, 0, s>>>(psi_far, acc_far, psi_near, acc_near, perm, n, G, psi, acc, off,
-                                                  Gsys, nsys);
+                                                  Gsys, nsys, pact);
     note_launch();
 }
 

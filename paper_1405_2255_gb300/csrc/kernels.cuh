@@ -25,7 +25,13 @@ struct Cells {
     d4* cr;      // centre of mass and radius about it (low-order estimate)
     double* mass;
     double* minscale; // min over the cell's sinks of the MAC scale (eqs. 18a,b)
+    // force evaluation for a subset of the particles (Sec. 7.1): act[cell] != 0 when the
+    // cell holds an active particle, pact[i] != 0 for an active sorted particle i; both
+    // nullptr when every particle is active
+    const unsigned char* act = nullptr;
+    const unsigned char* pact = nullptr;
 };
+__device__ __forceinline__ bool cell_active(const Cells& c, int cell) { return !c.act || c.act[cell]; }
 
 // ---------------------------------------------------------------- tree (tree.cu)
 // A1: bounding box + validation; bounds[6] = dbl_key of (min x,y,z, max x,y,z)
@@ -178,7 +184,14 @@ void launch_norm_scale(const double* psi_far, const double* acc_far, const doubl
 // (ensemble: Gsys[k] for the caller particles [off[k], off[k+1]) instead of G)
 void launch_finish(const double* psi_far, const double* acc_far, const double* psi_near,
                    const double* acc_near, const int* perm, int n, double G, double* psi, double* acc,
-                   cudaStream_t s, const int* off = nullptr, const double* Gsys = nullptr, int nsys = 0);
+                   cudaStream_t s, const int* off = nullptr, const double* Gsys = nullptr, int nsys = 0,
+                   const unsigned char* pact = nullptr);
+// Sec. 7.1: pact[i] = active[perm[i]] != 0 (sorted order) and act[cell] = the cell holds an
+// active particle (from a prefix sum of pact over the cells' particle ranges); ai holds
+// n + 1 ints, scan n ints, scan_tmp scan_tmp_ints(n) ints
+void launch_active_flags(const unsigned char* active, const int* perm, int n, const int* first, const int* count,
+                         int ncells, unsigned char* pact, unsigned char* act, int* ai, int* scan, int* scan_tmp,
+                         cudaStream_t s);
 
 // ---------------------------------------------------------------- peaks (peaks.cu)
 int alu_peaks(double* fp64_tflops, double* fp32_tflops);

@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32) k_l2p_split(const d4* __rest
     const int t = blockIdx.x * kSplitWarps + wid;
     if (t >= nleaves) return;
     const int cell = leaves[t];
+    if (!cell_active(c, cell)) return;
     const d4 s = cen[cell];
     const double rho = s.w;
     const double* Fr = F + (size_t)cell * nco;
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(128) k_l2l_split(Cells c, const d4* __restrict
     cd* Y64 = (cd*)(Fh + nco);
     cd* F64 = Y64 + 9;
     const int cell = lev_begin + blockIdx.x * 4 + wid;
-    if (cell >= lev_end) return;
+    if (cell >= lev_end || !cell_active(c, cell)) return;
     const int par = c.parent[cell];
     const d4 s = cen[par], sp = cen[cell];
     const double rho = s.w;

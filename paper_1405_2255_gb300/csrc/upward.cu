@@ -199,7 +199,8 @@ __global__ void k_minscale_leaves(const double* __restrict__ sc, Cells c, const 
     if (t >= nleaves) return;
     int cell = leaves[t];
     double m = INFINITY;
-    for (int i = c.first[cell], e = c.first[cell] + c.count[cell]; i < e; ++i) m = fmin(m, sc[i]);
+    for (int i = c.first[cell], e = c.first[cell] + c.count[cell]; i < e; ++i)
+        if (!c.pact || c.pact[i]) m = fmin(m, sc[i]);  // over the active sinks only (Sec. 7.1)
     c.minscale[cell] = m;
 }
 void launch_minscale_leaves(const double* scale_sorted, Cells c, const int* leaves, int nleaves, cudaStream_t s) {
@@ -226,4 +227,36 @@ void launch_scale_from_caller(const double* scale, const int* perm, int n, doubl
     if (n > 0) k_scale_from_caller<<<grid_for(n, 256), 256, 0, s>>>(scale, perm, n, scale_sorted); note_launch();
 }
 
+}  // namespace gb3
+
+namespace gb3 {
+// ---------------------------------------------------------------- active subsets (Sec. 7.1)
+__global__ void k_active_sorted(const unsigned char* __restrict__ active, const int* __restrict__ perm, int n,
+                                unsigned char* __restrict__ pact, int* __restrict__ ai) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned char a = active[perm[i]] != 0;
+        pact[i] = a;
+        ai[i] = a;
+    }
+}
+__global__ void k_active_cells(const int* __restrict__ first, const int* __restrict__ count, int ncells,
+                               const int* __restrict__ scan, const int* __restrict__ total, int n,
+                               unsigned char* __restrict__ act) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        const int f = first[c], e = f + count[c];
+        const int hi = e < n ? scan[e] : *total;
+        act[c] = hi - scan[f] > 0;
+    }
+}
+void launch_active_flags(const unsigned char* active, const int* perm, int n, const int* first, const int* count,
+                         int ncells, unsigned char* pact, unsigned char* act, int* ai, int* scan, int* scan_tmp,
+                         cudaStream_t s) {
+    if (n <= 0) return;
+    k_active_sorted<<<grid_for(n, 256), 256, 0, s>>>(active, perm, n, pact, ai);
+    note_launch();
+    int* total = ai + n;  // ai holds n + 1 ints
+    scan_exclusive_i32(ai, scan, n, total, scan_tmp, s);
+    k_active_cells<<<grid_for(ncells, 256), 256, 0, s>>>(first, count, ncells, scan, total, n, act);
+    note_launch();
+}
 }  // namespace gb3

@@ -43,7 +43,7 @@ __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in
     for (long long base = (long long)blockIdx.x * blockDim.x; base < nfront; base += stride) {
         long long i = base + threadIdx.x;
         int act = kActNone, A = -1, B = -1, nchA = 0, nchB = 0, chA = 0, chB = 0;
-        if (i < nfront) {
+        if (i < nfront && cell_active(c, front_in[i].y)) {  // a sink without active particles has no work
             int2 pr = front_in[i];
             A = pr.x;
             B = pr.y;

@@ -49,7 +49,8 @@ EXPORTS = ["fmm_default_params", "fmm_create", "fmm_set_params", "fmm_evaluate",
            "fmm_direct", "fmm_evaluate_batch", "fmm_debug_dump", "fmm_last_stats", "fmm_destroy",
            "fmm_strerror", "fmm_last_error", "fmm_version", "fmm_alu_peaks", "fmm_evaluate_noalloc",
            "fmm_serve_config", "fmm_footprint_bytes", "fmm_system_register", "fmm_submit", "fmm_poll",
-           "fmm_system_release", "fmm_workspace_bytes", "fmm_swap_matrix"]
+           "fmm_system_release", "fmm_workspace_bytes", "fmm_swap_matrix",
+           "fmm_evaluate_active"]
 
 _lib = None
 
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH):
     L.fmm_workspace_bytes.argtypes = [vp]
     L.fmm_workspace_bytes.restype = C.c_uint64
     L.fmm_swap_matrix.argtypes = [ci, vp]
+    L.fmm_evaluate_active.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, vp, vp, C.POINTER(fmm_stats)]
     for name in EXPORTS:
         if name not in ("fmm_strerror", "fmm_last_error", "fmm_version", "fmm_default_params",
                         "fmm_footprint_bytes", "fmm_workspace_bytes"):
@@ -124,7 +126,7 @@ def _ptr(t):
         return None
     import torch
     assert t.is_cuda and t.is_contiguous(), "device buffers must be contiguous CUDA tensors"
-    assert t.dtype in (torch.float64, torch.int64), t.dtype
+    assert t.dtype in (torch.float64, torch.int64, torch.uint8), t.dtype
     return t.data_ptr()
 
 
@@ -176,6 +178,22 @@ class Context:
         st = fmm_stats() if stats else None
         rc = self.L.fmm_evaluate(self.h, n, _ptr(x), _ptr(mu), float(G), _ptr(scale), _ptr(psi), _ptr(acc),
                                  _stream(stream), C.byref(st) if st is not None else None)
+        _check(rc, self.h)
+        return (psi, acc, st.as_dict()) if stats else (psi, acc)
+
+    def fmm_evaluate_active(self, x, mu, active, G=1.0, psi=None, acc=None, scale=None, stream=None, stats=False):
+        """Forces for the active subset (Sec. 7.1): active is a [n] uint8/bool CUDA tensor; psi and
+        acc (allocated here if None) are written for the active particles only."""
+        import torch
+        n = mu.shape[0]
+        if psi is None:
+            psi = torch.full((n,), float("nan"), dtype=torch.float64, device=mu.device)
+        if acc is None:
+            acc = torch.full((n, 3), float("nan"), dtype=torch.float64, device=mu.device)
+        a = active if active.dtype == torch.uint8 else active.to(torch.uint8)
+        st = fmm_stats() if stats else None
+        rc = self.L.fmm_evaluate_active(self.h, n, _ptr(x), _ptr(mu), float(G), _ptr(scale), _ptr(a), _ptr(psi),
+                                        _ptr(acc), _stream(stream), C.byref(st) if st is not None else None)
         _check(rc, self.h)
         return (psi, acc, st.as_dict()) if stats else (psi, acc)
 

@@ -1,0 +1,113 @@
+"""GPU force evaluation for a subset of the particles (Sec. 7.1, fmm_evaluate_active)
+against the oracle's subset run and against the library's own full evaluation."""
+import numpy as np
+import pytest
+
+from paper_1405_2255_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PARITY_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_2255_gb300 import build
+    build.build()
+    from paper_1405_2255_gb300 import gb3fmm
+    gb3fmm.load()
+    return gb3fmm
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def _rel(a, ref):
+    return np.linalg.norm(a - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+
+
+def _subsets(x, seed):
+    rng = np.random.default_rng(seed)
+    r = np.linalg.norm(x, axis=1)
+    return {"central": r < np.median(r) * 0.5, "sparse": rng.random(len(r)) < 0.02,
+            "one": np.arange(len(r)) == 17, "none": np.zeros(len(r), bool)}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_all_active_equals_full(g, prec):
+    x, mu = inputs.plummer(20000, inputs.BASE_SEED + 111)
+    p = g.FMM_PREC_FP64 if prec == "fp64" else g.FMM_PREC_MIXED
+    ctx = g.Context(p=8, eps=1e-7, leaf_size=32, p2p_c=2.0, precision=p)
+    psi, acc = ctx.fmm_evaluate(_dev(x), _dev(mu))
+    import torch
+    psi_a, acc_a = ctx.fmm_evaluate_active(_dev(x), _dev(mu), torch.ones(20000, dtype=torch.uint8, device="cuda:0"))
+    assert torch.equal(psi, psi_a) and torch.equal(acc, acc_a)
+    ctx.close()
+
+
+@pytest.mark.parametrize("which", ["central", "sparse", "one"])
+def test_fp64_subset_matches_oracle(g, orc, which):
+    """FP64 mode: the subset run against the oracle's subset run element by element."""
+    x, mu = inputs.plummer(6000, inputs.BASE_SEED + 112)
+    act = _subsets(x, 5)[which]
+    kw = dict(p=6, eps=1e-7, leaf_size=16, p2p_c=1.0)
+    ctx = g.Context(precision=g.FMM_PREC_FP64, **kw)
+    psi, acc, st = ctx.fmm_evaluate_active(_dev(x), _dev(mu), _dev(act.astype(np.uint8)), stats=True)
+    run = orc.fmm(x, mu, active=act, **kw)
+    psi, acc = psi.cpu().numpy(), acc.cpu().numpy()
+    assert st["n_m2l"] == run.stats["n_m2l"] and st["n_p2p"] == run.stats["n_p2p"]
+    assert np.max(_rel(acc[act], run.acc[act])) <= PARITY_TOL
+    assert np.max(np.abs(psi[act] - run.psi[act]) / np.abs(run.psi[act])) <= PARITY_TOL
+    # the outputs of inactive particles are not written (NaN from the wrapper stays)
+    assert np.isnan(acc[~act]).all() and np.isnan(psi[~act]).all()
+    ctx.close()
+
+
+def test_empty_subset_writes_nothing(g):
+    import torch
+    x, mu = inputs.plummer(3000, inputs.BASE_SEED + 113)
+    ctx = g.Context()
+    psi, acc, st = ctx.fmm_evaluate_active(_dev(x), _dev(mu), torch.zeros(3000, dtype=torch.uint8, device="cuda:0"),
+                                           stats=True)
+    assert torch.isnan(psi).all() and torch.isnan(acc).all()
+    assert st["n_m2l"] == 0 and st["n_p2p"] == 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_geometric_mac_subset_equals_full(g, prec):
+    """With the geometric criterion the active particles get exactly the interactions of the
+    full run: identical results bit for bit."""
+    x, mu = inputs.plummer(30000, inputs.BASE_SEED + 114)
+    act = _subsets(x, 6)["central"] | _subsets(x, 7)["sparse"]
+    p = g.FMM_PREC_FP64 if prec == "fp64" else g.FMM_PREC_MIXED
+    ctx = g.Context(p=10, mac=g.FMM_MAC_THETA, theta_crit=0.55, leaf_size=32, p2p_c=1.0, precision=p)
+    psi, acc = ctx.fmm_evaluate(_dev(x), _dev(mu))
+    psi_a, acc_a, st = ctx.fmm_evaluate_active(_dev(x), _dev(mu), _dev(act.astype(np.uint8)), stats=True)
+    a, aa = acc.cpu().numpy(), acc_a.cpu().numpy()
+    assert np.array_equal(aa[act], a[act]) and np.array_equal(psi_a.cpu().numpy()[act], psi.cpu().numpy()[act])
+    ctx.close()
+
+
+def test_mixed_subset_accuracy(g):
+    """Mixed mode, central subset of a Plummer sphere: accuracy against the FP64 direct sum."""
+    import torch
+    n = 200000
+    x, mu = inputs.plummer(n, inputs.BASE_SEED + 115)
+    act = np.linalg.norm(x, axis=1) < 0.3
+    ctx = g.Context(p=12, eps=2e-7, leaf_size=48, p2p_c=1.0, precision=g.FMM_PREC_MIXED)
+    xt, mt = _dev(x), _dev(mu)
+    _, acc_full, st_full = ctx.fmm_evaluate(xt, mt, stats=True)
+    _, acc, st = ctx.fmm_evaluate_active(xt, mt, _dev(act.astype(np.uint8)), stats=True)
+    idx = np.flatnonzero(act)[::max(1, int(act.sum()) // 2000)]
+    _, a_t = ctx.fmm_direct(xt, mt, 1.0, sinks=torch.from_numpy(idx).to("cuda:0"))
+    e = _rel(acc.cpu().numpy()[idx], a_t.cpu().numpy())
+    ef = _rel(acc_full.cpu().numpy()[idx], a_t.cpu().numpy())
+    assert np.sqrt(np.mean(e ** 2)) < 2e-7 and np.sqrt(np.mean(e ** 2)) < 1.5 * np.sqrt(np.mean(ef ** 2)) + 1e-8
+    assert st["n_p2p"] < 0.5 * st_full["n_p2p"]
+    ctx.close()

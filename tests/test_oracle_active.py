@@ -1,0 +1,51 @@
+"""Pins of the force evaluation for a subset of the particles (Sec. 7.1) in the oracle."""
+import numpy as np
+
+from paper_1405_2255_gb300 import inputs
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def test_all_active_is_the_full_evaluation(orc):
+    x, mu = inputs.plummer(2500, 301)
+    full = orc.fmm(x, mu, p=6, eps=1e-6, leaf_size=24)
+    sub = orc.fmm(x, mu, p=6, eps=1e-6, leaf_size=24, active=np.ones(2500, bool))
+    assert np.array_equal(full.acc, sub.acc) and np.array_equal(full.psi, sub.psi)
+    assert np.array_equal(full.m2l, sub.m2l) and np.array_equal(full.p2p, sub.p2p)
+
+
+def test_geometric_mac_subset_equals_full(orc):
+    """With the geometric criterion the decisions do not depend on the sinks' scale, so the
+    active particles get exactly the interactions, in the same order, as in the full run."""
+    x, mu = inputs.plummer(3000, 302)
+    act = np.linalg.norm(x, axis=1) < 0.6
+    kw = dict(p=5, mac=orc.MAC_THETA, theta_crit=0.5, leaf_size=16, p2p_c=0.0)
+    full = orc.fmm(x, mu, **kw)
+    sub = orc.fmm(x, mu, active=act, **kw)
+    assert np.array_equal(sub.acc[act], full.acc[act]) and np.array_equal(sub.psi[act], full.psi[act])
+    assert np.isnan(sub.acc[~act]).all() and np.isnan(sub.psi[~act]).all()
+    # every interaction of the subset run has a sink holding an active particle, and the
+    # subset run keeps exactly the full run's interactions of those sinks
+    ci = sub.cells_int
+    sorted_act = act[sub.perm]
+    nact = np.array([sorted_act[f:f + c].sum() for f, c in zip(ci[:, 2], ci[:, 3])])
+    for lst_s, lst_f in ((sub.m2l, full.m2l), (sub.p2p, full.p2p)):
+        assert (nact[lst_s[:, 1]] > 0).all()
+        keep = nact[lst_f[:, 1]] > 0
+        assert np.array_equal(lst_s, lst_f[keep])
+
+
+def test_subset_accuracy_and_work(orc):
+    """The criterion on the active sinks' own scale keeps their errors at the level of the
+    full run, with far fewer interactions when the subset is a central sphere."""
+    x, mu = inputs.plummer(4000, 303)
+    act = np.linalg.norm(x, axis=1) < 0.4
+    full = orc.fmm(x, mu, p=6, eps=1e-6, leaf_size=24)
+    sub = orc.fmm(x, mu, p=6, eps=1e-6, leaf_size=24, active=act)
+    _, a_t, _, _ = orc.direct(x, mu)
+    e_sub, e_full = _rel(sub.acc[act], a_t[act]), _rel(full.acc[act], a_t[act])
+    assert np.sqrt(np.mean(e_sub ** 2)) < 2 * np.sqrt(np.mean(e_full ** 2)) + 1e-8
+    assert np.sqrt(np.mean(e_sub ** 2)) < 1e-6
+    assert sub.stats["n_p2p"] < full.stats["n_p2p"] and sub.stats["n_m2l"] < full.stats["n_m2l"]
