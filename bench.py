@@ -43,21 +43,23 @@ def parse():
     ap.add_argument("--c", type=float, default=None)
     ap.add_argument("--cpu-sample", type=int, default=50000)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-mode and direct-sum comparisons")
-    ap.add_argument("--workload", default="plummer", choices=["plummer", "cusp", "ensemble", "serve"],
+    ap.add_argument("--workload", default="plummer", choices=["plummer", "cusp", "ensemble", "serve", "active"],
                     help="plummer: one N=1e6 sphere (default); cusp: gamma=1.5 model with a central point mass; "
                          "ensemble: 256 spheres of 1e3..1e5 in one forest; serve: 64 systems of 1e4..2e6 "
-                         "served at 0.8 of capacity (Poisson arrivals)")
+                         "served at 0.8 of capacity (Poisson arrivals); active: forces for the innermost "
+                         "N_a of a Plummer sphere of 1e7 (Sec. 7.1), N_a = 1e3..1e7")
     ap.add_argument("--requests", type=int, default=384, help="serve: requests in the open-loop run")
     ap.add_argument("--autotune", action="store_true",
                     help="choose (p, eps, leaf, p2p_c) for rms 1e-7 on the workload first (untimed)")
     a = ap.parse_args()
-    if a.workload == "cusp" and a.n == 1_000_000:
+    if a.workload in ("cusp", "active") and a.n == 1_000_000:
         a.n = 10_000_000
     # (p, eps, leaf, p2p_c) per workload from the autotuner at rms 1e-7 (eps with a margin):
     # the single large systems take leaf 80; ensembles of small systems leaf 48, where
     # large leaves let accepted pairs with theta near 1 dominate the error
     dflt = {"plummer": (14, 3e-7, 80, 1.0), "cusp": (14, 2.6e-7, 80, 1.0),
-            "ensemble": (14, 3.6e-7, 48, 1.0), "serve": (14, 3.6e-7, 48, 1.0)}[a.workload]
+            "ensemble": (14, 3.6e-7, 48, 1.0), "serve": (14, 2.2e-7, 48, 1.0),
+            "active": (14, 3e-7, 80, 1.0)}[a.workload]
     for k, v in zip(("p", "eps", "leaf", "c"), dflt):
         if getattr(a, k) is None:
             setattr(a, k, v)
@@ -479,6 +481,76 @@ def run_serve(a, g, dev, local, rank, world, prec):
     ctx.close()
 
 
+def run_active(a, g, dev, local, rank, world, prec):
+    """Sec. 7.1: forces for the innermost N_a particles of a Plummer sphere of N (the
+    paper's Fig. 14 experiment), N_a = N/10^k; all N particles are sources.  The headline
+    value is active particle-forces/s at N_a = N/100; the sweep gives ms per step for
+    every N_a (tree and upward pass over all N, walk and interactions for the active part)."""
+    import torch
+    from paper_1405_2255_gb300 import inputs
+    x, mu = inputs.plummer(a.n, inputs.BASE_SEED + 2 + 7919 * rank)
+    xt, mt = torch.from_numpy(x).to(dev), torch.from_numpy(mu).to(dev)
+    order = np.argsort(np.linalg.norm(x, axis=1), kind="stable")
+    psi = torch.empty(a.n, dtype=torch.float64, device=dev)
+    acc = torch.empty((a.n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = g.Context(p=a.p, eps=a.eps, leaf_size=a.leaf, p2p_c=a.c, precision=prec, device=local)
+    stream = torch.cuda.current_stream(dev)
+    sweep, head = {}, None
+    na_list = sorted({int(a.n // 10 ** k) for k in range(0, 5)} | {1000})
+    rng = np.random.default_rng(rank)
+    for na in na_list:
+        act = np.zeros(a.n, dtype=np.uint8)
+        act[order[:na]] = 1
+        at = torch.from_numpy(act).to(dev)
+        for _ in range(max(a.warmup, 3)):
+            ctx.fmm_evaluate_active(xt, mt, at, psi=psi, acc=acc)
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        phase, launches = [], 0
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local) as clk:
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record(stream)
+                ctx.fmm_evaluate_active(xt, mt, at, psi=psi, acc=acc)
+                e1.record(stream)
+                st = ctx.fmm_last_stats()
+                phase.append(st)
+                launches += int(st["launches"])
+            torch.cuda.synchronize(dev)
+        ms = max_over_ranks(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]), world, dev)
+        idx = np.sort(rng.choice(order[:na], min(na, 2048), replace=False))
+        e = sampled_error(ctx, xt, mt, acc, idx, dev)
+        sweep[na] = {"ms": ms, "rms_rel_err": float(np.sqrt(np.mean(e ** 2))),
+                     "phase_ms": {k: float(np.mean([s_[k] for s_ in phase])) for k in
+                                  ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total")},
+                     "n_m2l": int(phase[-1]["n_m2l"]), "n_p2p": int(phase[-1]["n_p2p"])}
+        if na == a.n // 100:
+            head = (ms, launches / a.steps, clk.summary(), st)
+    ms, launches, clocks, st = head
+    na = a.n // 100
+    value = job_value(na, world, ms * 1e-3)
+    if rank == 0:
+        cfg = {"workload": f"active_innermost_n{a.n}", "n": a.n, "n_active": na,
+               "model": "truncated Plummer sphere R_t=30, equal masses; the innermost N_a particles active",
+               "p": a.p, "eps": a.eps, "mac": "18a (low-order a estimate over the active sinks)",
+               "leaf_size": a.leaf, "p2p_c": a.c, "precision": a.precision,
+               "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas",
+               "rms_rel_err": sweep[na]["rms_rel_err"], "err_sinks": min(na, 2048),
+               "phase_ms": sweep[na]["phase_ms"], "sweep_by_n_active": {str(k): v for k, v in sweep.items()}}
+        line = {"metric": "active particle-forces/s (Sec. 7.1 subset evaluation)", "value": value, "unit": UNIT,
+                "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if prec == g.FMM_PREC_MIXED else "f64", "data": "synthetic", "config": cfg,
+                "e2e": None, "roofline": None, "cpu_baseline": None, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def config_of(a):
     if a.workload == "cusp":
         return {"workload": f"cusp_n{a.n}", "n": a.n,
@@ -510,6 +582,8 @@ def main():
         return run_ensemble(a, g, dev, local, rank, world, prec)
     if a.workload == "serve":
         return run_serve(a, g, dev, local, rank, world, prec)
+    if a.workload == "active":
+        return run_active(a, g, dev, local, rank, world, prec)
     if a.workload == "cusp":
         x, mu = inputs.dehnen(a.n, inputs.BASE_SEED + 3 + 7919 * rank)
     else:
