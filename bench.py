@@ -523,12 +523,25 @@ def run_active(a, g, dev, local, rank, world, prec):
                 launches += int(st["launches"])
             torch.cuda.synchronize(dev)
         ms = max_over_ranks(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]), world, dev)
+        # the same step on the re-cycled tree of the previous step (Sec. 7.1's other measure;
+        # unchanged positions here, so this times the refresh of radii, masses and centres of mass)
+        ev_r = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        phase_r = []
+        for e0, e1 in ev_r:
+            flush.zero_()
+            e0.record(stream)
+            ctx.fmm_evaluate_active(xt, mt, at, psi=psi, acc=acc, reuse_tree=True)
+            e1.record(stream)
+            phase_r.append(ctx.fmm_last_stats())
+        torch.cuda.synchronize(dev)
+        ms_r = max_over_ranks(np.mean([e0.elapsed_time(e1) for e0, e1 in ev_r]), world, dev)
         idx = np.sort(rng.choice(order[:na], min(na, 2048), replace=False))
         e = sampled_error(ctx, xt, mt, acc, idx, dev)
         sweep[na] = {"ms": ms, "rms_rel_err": float(np.sqrt(np.mean(e ** 2))),
                      "phase_ms": {k: float(np.mean([s_[k] for s_ in phase])) for k in
                                   ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total")},
-                     "n_m2l": int(phase[-1]["n_m2l"]), "n_p2p": int(phase[-1]["n_p2p"])}
+                     "n_m2l": int(phase[-1]["n_m2l"]), "n_p2p": int(phase[-1]["n_p2p"]),
+                     "reused_tree_ms": ms_r, "reused_tree_t_tree": float(np.mean([s_["t_tree"] for s_ in phase_r]))}
         if na == a.n // 100:
             head = (ms, launches / a.steps, clk.summary(), st)
     ms, launches, clocks, st = head

@@ -158,11 +158,21 @@ int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, doubl
  * only.  The MAC scale of a sink cell (eqs. 18a,b) is the minimum over its ACTIVE
  * particles, and the low-order estimate of Sec. 5.3.2 is evaluated for the active sinks:
  * the error criterion concerns the forces being computed.  With every particle active
- * the result equals fmm_evaluate's bit for bit.  Other arguments and errors as for
- * fmm_evaluate; FMM_E_INVALID also for active == NULL with n > 0. */
+ * the result equals fmm_evaluate's bit for bit.
+ * reuse_tree = 1 re-cycles the tree of the previous evaluation on ctx (the other
+ * measure Sec. 7.1 names): it must have been a completed single-system evaluation
+ * (fmm_evaluate, fmm_evaluate_host or fmm_evaluate_active) of the same n particles in the
+ * same caller order.  The particle order, the cells and their expansion centres are
+ * kept; the positions and masses are gathered in that order and the radii, masses and
+ * centres of mass are recomputed exactly, so the MAC holds for the new positions (cells
+ * need not be the key cubes of the new positions); multipoles, walk and everything after
+ * them are recomputed.  With unchanged positions the result equals a fresh evaluation's
+ * bit for bit.  reuse_tree = 0 builds the tree anew.  Other arguments and errors as for
+ * fmm_evaluate; FMM_E_INVALID also for active == NULL with n > 0 or for reuse_tree = 1
+ * without such a previous evaluation. */
 int fmm_evaluate_active(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G,
-                        const double* scale, const unsigned char* active, double* psi, double* acc,
-                        void* stream, fmm_stats* stats);
+                        const double* scale, const unsigned char* active, int reuse_tree, double* psi,
+                        double* acc, void* stream, fmm_stats* stats);
 
 /* Many independent systems in one call (the batched ensemble).  System s holds
  * particles [offsets[s], offsets[s+1]) of x/mu/psi/acc (device arrays laid out as

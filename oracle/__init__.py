@@ -85,6 +85,9 @@ def _declare(L):
     L.orc_fmm.restype = C.c_void_p
     L.orc_fmm_active.argtypes = [C.c_long, _dp, _dp, C.c_double, C.POINTER(Params), C.c_void_p, C.c_void_p]
     L.orc_fmm_active.restype = C.c_void_p
+    L.orc_fmm_reuse.argtypes = [C.c_void_p, C.c_long, _dp, _dp, C.c_double, C.POINTER(Params), C.c_void_p,
+                                C.c_void_p]
+    L.orc_fmm_reuse.restype = C.c_void_p
     L.orc_run_free.argtypes = [C.c_void_p]
     L.orc_run_outputs.argtypes = [C.c_void_p, _dp, _dp]
     L.orc_run_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
@@ -232,34 +235,62 @@ def fmm(x, mu, G=1.0, p=6, eps=1e-7, mac=MAC_A, theta_crit=0.5, leaf_size=32, p2
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     prm = Params(p, eps, mac, theta_crit, leaf_size, p2p_c, 1 if scale is not None else 0)
-    sc = None
-    if scale is not None:
-        sc = np.ascontiguousarray(scale, dtype=np.float64)
-    L = lib()
+    sc = None if scale is None else np.ascontiguousarray(scale, dtype=np.float64)
     act = None if active is None else np.ascontiguousarray(np.asarray(active) != 0, dtype=np.uint8)
+    L = lib()
     h = L.orc_fmm_active(len(mu), x, mu, G, C.byref(prm), sc.ctypes.data if sc is not None else None,
                          act.ctypes.data if act is not None else None)
     if not h:
         raise ValueError("oracle rejected the input")
     try:
-        n = len(mu)
-        psi, acc = np.zeros(max(n, 1)), np.zeros((max(n, 1), 3))
-        L.orc_run_outputs(h, psi, acc)
-        st = Stats()
-        L.orc_run_stats(h, C.byref(st))
-        stats = {k: getattr(st, k) for k, _ in Stats._fields_}
-        if keep and n > 0:
-            nc = L.orc_run_ncells(h)
-            ci, cd = np.zeros((nc, 5), dtype=np.int64), np.zeros((nc, 6))
-            L.orc_run_cells(h, ci, cd)
-            m2 = np.zeros((max(st.n_m2l, 1), 2), dtype=np.int64)
-            pp = np.zeros((max(st.n_p2p, 1), 2), dtype=np.int64)
-            L.orc_run_lists(h, m2, pp)
-            perm = np.zeros(n, dtype=np.int64)
-            L.orc_run_perm(h, perm)
-            scl = np.zeros(n)
-            L.orc_run_scale(h, scl)
-            return Run(psi[:n], acc[:n], stats, ci, cd, m2[:st.n_m2l], pp[:st.n_p2p], perm, scl)
-        return Run(psi[:n], acc[:n], stats, None, None, None, None, None, None)
+        return _collect(L, h, len(mu), keep)
     finally:
         L.orc_run_free(h)
+
+
+def fmm_reused(x0, mu0, x, mu, G=1.0, p=6, eps=1e-7, mac=MAC_A, theta_crit=0.5, leaf_size=32, p2p_c=1.0,
+               active=None, keep=True):
+    """Sec. 7.1's re-cycled tree: build the tree for (x0, mu0), then evaluate (x, mu), the
+    same particles in the same order, on that tree (order, cells and centres kept; radii,
+    masses and centres of mass recomputed)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1, 3)
+    mu0 = np.ascontiguousarray(mu0, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    prm = Params(p, eps, mac, theta_crit, leaf_size, p2p_c, 0)
+    act = None if active is None else np.ascontiguousarray(np.asarray(active) != 0, dtype=np.uint8)
+    L = lib()
+    h0 = L.orc_fmm_active(len(mu0), x0, mu0, G, C.byref(prm), None, None)
+    if not h0:
+        raise ValueError("oracle rejected the first input")
+    try:
+        h = L.orc_fmm_reuse(h0, len(mu), x, mu, G, C.byref(prm), None, act.ctypes.data if act is not None else None)
+        if not h:
+            raise ValueError("oracle rejected the second input")
+        try:
+            return _collect(L, h, len(mu), keep)
+        finally:
+            L.orc_run_free(h)
+    finally:
+        L.orc_run_free(h0)
+
+
+def _collect(L, h, n, keep):
+    psi, acc = np.zeros(max(n, 1)), np.zeros((max(n, 1), 3))
+    L.orc_run_outputs(h, psi, acc)
+    st = Stats()
+    L.orc_run_stats(h, C.byref(st))
+    stats = {k: getattr(st, k) for k, _ in Stats._fields_}
+    if keep and n > 0:
+        nc = L.orc_run_ncells(h)
+        ci, cd = np.zeros((nc, 5), dtype=np.int64), np.zeros((nc, 6))
+        L.orc_run_cells(h, ci, cd)
+        m2 = np.zeros((max(st.n_m2l, 1), 2), dtype=np.int64)
+        pp = np.zeros((max(st.n_p2p, 1), 2), dtype=np.int64)
+        L.orc_run_lists(h, m2, pp)
+        perm = np.zeros(n, dtype=np.int64)
+        L.orc_run_perm(h, perm)
+        scl = np.zeros(n)
+        L.orc_run_scale(h, scl)
+        return Run(psi[:n], acc[:n], stats, ci, cd, m2[:st.n_m2l], pp[:st.n_p2p], perm, scl)
+    return Run(psi[:n], acc[:n], stats, None, None, None, None, None, None)

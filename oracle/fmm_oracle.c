@@ -825,14 +825,18 @@ static void free_tree(tree_t *t)
 }
 
 /* centres and radii, bottom-up (reading R-ses), plus mass and centre of mass */
-static void cell_geometry(tree_t *t, long ci)
+/* keep_centre: a re-cycled tree (Sec. 7.1) keeps the centres s and recomputes the radii,
+ * masses and centres of mass for the particles' current positions */
+static void cell_geometry_k(tree_t *t, long ci, int keep_centre)
 {
     cell_t *c = &t->cells[ci];
     if (!c->leaf)
-        for (long j = 0; j < c->nchild; ++j) cell_geometry(t, c->child + j);
+        for (long j = 0; j < c->nchild; ++j) cell_geometry_k(t, c->child + j, keep_centre);
     c = &t->cells[ci];
     const double *X = &t->xs[3 * c->first];
-    if (c->leaf) {
+    if (keep_centre) {
+        /* s stays */
+    } else if (c->leaf) {
         orc_meb_points((int)c->count, X, c->s, &c->rho);
     } else {
         double cen[8 * 3], rad[8];
@@ -862,6 +866,7 @@ static void cell_geometry(tree_t *t, long ci)
     }
     c->rho_com = rc;
 }
+static void cell_geometry(tree_t *t, long ci) { cell_geometry_k(t, ci, 0); }
 
 /* ------------------------------------------------------------------------- */
 /* Dual tree walk (Sec. 2.2.2) and acceptance criteria (eqs. 9, 15-18)        */
@@ -1064,6 +1069,8 @@ static int depth_of(const tree_t *t)
 
 void orc_run_free(orc_run *run);
 
+static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, const unsigned char *active);
+
 /* The whole FMM (Sec. 2.2.2): returns NULL on invalid input. */
 /* Sec. 7.1: active (caller order, may be NULL = all) marks the sinks whose forces are
  * computed; all particles are sources.  Sink cells without an active particle take part
@@ -1085,11 +1092,22 @@ orc_run *orc_fmm_active(long n, const double *x, const double *mu, double G, con
     run->psi = calloc(n > 0 ? n : 1, sizeof(double));
     run->acc = calloc(3 * (n > 0 ? n : 1), sizeof(double));
     if (n == 0) return run;
-    int p = prm->p, nco = NCOEF(p);
     tree_t *t = &run->t;
     build_tree(t, n, x, mu, prm->leaf_size);
     cell_geometry(t, 0);
+    evaluate_on_tree(run, G, scale_in, active);
+    return run;
+}
+
+/* everything after the tree and its geometry (shared by fresh and re-cycled trees) */
+static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, const unsigned char *active)
+{
+    const orc_params *prm = &run->prm;
+    tree_t *t = &run->t;
+    const long n = t->n;
+    int p = prm->p, nco = NCOEF(p);
     long nc = t->ncells;
+    free(t->act);
     t->act = malloc(n);
     for (long i = 0; i < n; ++i) t->act[i] = active ? (active[t->perm[i]] != 0) : 1;
     for (long ci = 0; ci < nc; ++ci) {
@@ -1176,6 +1194,46 @@ orc_run *orc_fmm_active(long n, const double *x, const double *mu, double G, con
         }
     }
     free(ps); free(ac); free(M); free(F); free(P); free(w.binom);
+}
+
+/* Sec. 7.1's re-cycled tree: the particle order, cells and centres of the run prev (the same
+ * n particles in the same caller order) for new positions x and masses mu; radii, masses
+ * and centres of mass are recomputed, then the evaluation proceeds as usual */
+orc_run *orc_fmm_reuse(const orc_run *prev, long n, const double *x, const double *mu, double G,
+                       const orc_params *prm, const double *scale_in, const unsigned char *active)
+{
+    if (!prev || prev->t.n != n || n <= 0 || !prm || prm->p < 1 || prm->p > 20) return NULL;
+    if (prm->mac != MAC_THETA && !(prm->eps > 0)) return NULL;
+    for (long i = 0; i < n; ++i) {
+        if (!isfinite(x[3 * i]) || !isfinite(x[3 * i + 1]) || !isfinite(x[3 * i + 2]) ||
+            !isfinite(mu[i]) || mu[i] < 0)
+            return NULL;
+    }
+    orc_run *run = calloc(1, sizeof(orc_run));
+    run->prm = *prm;
+    run->psi = calloc(n, sizeof(double));
+    run->acc = calloc(3 * n, sizeof(double));
+    tree_t *t = &run->t;
+    const tree_t *o = &prev->t;
+    t->n = n;
+    t->leaf_size = o->leaf_size;
+    t->ncells = t->cap = o->ncells;
+    for (int k = 0; k < 3; ++k) t->lo[k] = o->lo[k];
+    t->side = o->side;
+    t->cells = malloc(sizeof(cell_t) * o->ncells);
+    memcpy(t->cells, o->cells, sizeof(cell_t) * o->ncells);
+    t->perm = malloc(sizeof(long) * n);
+    memcpy(t->perm, o->perm, sizeof(long) * n);
+    t->keys = NULL;
+    t->xs = malloc(sizeof(double) * 3 * n);
+    t->mus = malloc(sizeof(double) * n);
+    for (long i = 0; i < n; ++i) {
+        const long j = t->perm[i];
+        for (int k = 0; k < 3; ++k) t->xs[3 * i + k] = x[3 * j + k];
+        t->mus[i] = mu[j];
+    }
+    cell_geometry_k(t, 0, 1);
+    evaluate_on_tree(run, G, scale_in, active);
     return run;
 }
 

@@ -93,6 +93,9 @@ struct fmm_ctx {
     // force evaluation for a subset (Sec. 7.1): per sorted particle and per cell activity
     Buf pact, act, act_i, act_scan;
     bool active_mode = false;
+    // the tree of the last evaluation can be reused (Sec. 7.1) when it was a single system
+    // of tree_n particles that completed
+    int tree_n = -1;
     std::vector<Buf*> bufs() {
         return {&hx, &hmu, &hpsi, &hacc, &bounds, &status, &counters, &coin, &dtotal, &keys, &keys_alt, &idx,
                 &idx_alt, &rtmp, &xm, &perm, &xhi, &xlo, &first, &count, &child, &nchild, &parent, &level, &sr,
@@ -190,6 +193,26 @@ __global__ void k_leaf_flags(const int* __restrict__ nchild, int nc, int* __rest
 __global__ void k_leaf_compact(const int* __restrict__ flag, const int* __restrict__ pos, int nc, int* __restrict__ leaves) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
         if (flag[i]) leaves[pos[i]] = i;
+}
+
+// Sec. 7.1's re-cycled tree: the previous evaluation's particle order, cells and centres
+// stay; positions and masses are gathered in that order and the radii, masses and
+// centres of mass are recomputed, so the MAC sees the true extent of every cell
+static int refresh_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cudaStream_t s) {
+    launch_bounds(x, mu, n, P<unsigned long long>(ctx->bounds), P<unsigned>(ctx->status), s);
+    launch_gather(x, mu, P<int>(ctx->perm), n, P<d4>(ctx->xm), P<int>(ctx->perm), s);
+    unsigned st = 0;
+    CU(cudaMemcpyAsync(&ctx->h_int[0], ctx->status.p, sizeof st, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    memcpy(&st, &ctx->h_int[0], sizeof st);
+    if (st & kStatInvalid) return fail(ctx, FMM_E_INVALID, "non-finite position or mass, or negative mass");
+    Cells c = cells_of(ctx);
+    const int nlev = (int)ctx->lev_start.size() - 1;
+    launch_leaf_geometry(P<d4>(ctx->xm), c, P<int>(ctx->leaves), ctx->nleaves, P<unsigned>(ctx->status), s, true);
+    for (int L = nlev - 1; L >= 0; --L)
+        launch_internal_geometry(P<d4>(ctx->xm), c, ctx->lev_start[L], ctx->lev_start[L + 1], n,
+                                 P<unsigned long long>(ctx->rad_tmp), P<unsigned>(ctx->status), s, true);
+    return 0;
 }
 
 static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cudaStream_t s) {
@@ -434,9 +457,14 @@ static int phase_times(fmm_ctx* ctx) {
 // ------------------------------------------------------------------ one evaluation
 static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* mu, double G, const double* scale,
                            double* psi, double* acc, cudaStream_t s, fmm_stats* stats,
-                           const unsigned char* active = nullptr) {
+                           const unsigned char* active = nullptr, bool reuse_tree = false) {
     const fmm_params& prm = ctx->prm;
     ctx->active_mode = false;
+    if (reuse_tree && (ctx->tree_n != n || ctx->nsys != 0 || n == 0))
+        return fail(ctx, FMM_E_INVALID, "no tree of this system to reuse (the last evaluation on this context "
+                                        "was not a completed single system of n particles)");
+    const int tree_n = ctx->tree_n, tree_nc = ctx->ncells, tree_nl = ctx->nleaves;
+    ctx->tree_n = -1;  // valid again once this evaluation has completed
     if (check_params(&prm)) return fail(ctx, FMM_E_INVALID, "invalid parameters");
     memset(&ctx->last, 0, sizeof ctx->last);
     ctx->last.n = n;
@@ -458,7 +486,14 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     if (timing) CU(cudaEventRecord(ctx->ev[EV_START], s));
     CU(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), s));
     CU(cudaMemsetAsync(ctx->coin.p, 0, sizeof(unsigned long long), s));
-    TRY(build_tree(ctx, n, x, mu, s));
+    if (reuse_tree) {
+        if (tree_nc <= 0 || tree_n != n) return fail(ctx, FMM_E_INVALID, "no tree to reuse");
+        ctx->ncells = tree_nc;
+        ctx->nleaves = tree_nl;
+        TRY(refresh_tree(ctx, n, x, mu, s));
+    } else {
+        TRY(build_tree(ctx, n, x, mu, s));
+    }
     if (active) {  // Sec. 7.1: only sink cells holding an active particle are evaluated
         TRY(ensure(ctx->pact, (size_t)n));
         TRY(ensure(ctx->act, (size_t)ctx->ncells));
@@ -590,6 +625,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     ctx->last.depth = nlev - 1;
     ctx->last.launches = launches_so_far() - launches0;
     ctx->timed = timing;
+    ctx->tree_n = ctx->nsys == 0 ? n : -1;
     if (stats) {
         CU(cudaStreamSynchronize(s));
         unsigned long long coin = 0;
@@ -684,14 +720,17 @@ int fmm_evaluate(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, dou
 }
 
 int fmm_evaluate_active(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, const double* scale,
-                        const unsigned char* active, double* psi, double* acc, void* stream, fmm_stats* stats) {
+                        const unsigned char* active, int reuse_tree, double* psi, double* acc, void* stream,
+                        fmm_stats* stats) {
     if (!ctx) return FMM_E_INVALID;
     ctx->err[0] = 0;
     if (n < 0 || n > 0x7fffffffLL) return fail(ctx, FMM_E_INVALID, "n out of range");
     if (n > 0 && (!x || !mu || !psi || !acc || !active)) return fail(ctx, FMM_E_INVALID, "NULL buffer");
     if (!std::isfinite(G)) return fail(ctx, FMM_E_INVALID, "G is not finite");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, FMM_E_CUDA, "cudaSetDevice failed");
-    return evaluate_device(ctx, (int)n, x, mu, G, scale, psi, acc, (cudaStream_t)stream, stats, active);
+    if (reuse_tree != 0 && reuse_tree != 1) return fail(ctx, FMM_E_INVALID, "reuse_tree must be 0 or 1");
+    return evaluate_device(ctx, (int)n, x, mu, G, scale, psi, acc, (cudaStream_t)stream, stats, active,
+                           reuse_tree != 0);
 }
 
 int fmm_evaluate_host(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, double* psi, double* acc,

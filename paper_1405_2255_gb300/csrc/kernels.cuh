@@ -68,10 +68,13 @@ void launch_split_level(const uint64_t* keys, Cells c, int lev_begin, int lev_en
 // A4: geometry.  Leaves: smallest enclosing ball of the particles, rho, mass,
 // centre of mass.  Internal cells of one level: smallest ball of the daughter balls,
 // mass and centre of mass from the daughters, then the exact radii over particles.
+// keep_centre: a reused tree (Sec. 7.1) keeps the cells' centres s and recomputes the
+// radii, masses and centres of mass for the particles' new positions
 void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves, unsigned* status,
-                          cudaStream_t s);
+                          cudaStream_t s, bool keep_centre = false);
 void launch_internal_geometry(const d4* xm, Cells c, int lev_begin, int lev_end, int n,
-                              unsigned long long* rad_tmp, unsigned* status, cudaStream_t s);
+                              unsigned long long* rad_tmp, unsigned* status, cudaStream_t s,
+                              bool keep_centre = false);
 
 // ---------------------------------------------------------------- upward (upward.cu)
 // P2M (eq. 3c) at leaves about centre cen (sr or cr), M2M (eq. 4) for the internal

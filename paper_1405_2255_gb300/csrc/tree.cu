@@ -715,7 +715,7 @@ __device__ void meb_points_mtf_warp(float (*L)[3], int n, float c[3], float& rad
 constexpr int kGeoWarps = 4;
 __global__ void __launch_bounds__(kGeoWarps * 32) k_leaf_geometry(const d4* __restrict__ xm, Cells c,
                                                                  const int* __restrict__ leaves, int nleaves,
-                                                                 unsigned* status) {
+                                                                 unsigned* status, bool keep_centre) {
     __shared__ float pbuf[kGeoWarps][kMebBuf][3];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int t = blockIdx.x * kGeoWarps + wid;
@@ -723,6 +723,11 @@ __global__ void __launch_bounds__(kGeoWarps * 32) k_leaf_geometry(const d4* __re
     const int cell = leaves[t];
     const int first = c.first[cell], count = c.count[cell];
     const d4* X = xm + first;
+    double s[3];
+    if (keep_centre) {  // a reused tree keeps its centres; radii, masses and centres of mass are new
+        const d4 v = c.sr[cell];
+        s[0] = v.x; s[1] = v.y; s[2] = v.z;
+    } else {
     LeafPts P;
     P.buf = pbuf[wid];
     P.X = X;
@@ -758,7 +763,10 @@ __global__ void __launch_bounds__(kGeoWarps * 32) k_leaf_geometry(const d4* __re
     float cf[3], radf;
     if (count <= kMebBuf) meb_points_mtf_warp(pbuf[wid], count, cf, radf, lane);
     else meb_points_warp(P, count, cf, radf, lane);
-    double s[3] = {P.o[0] + (double)cf[0], P.o[1] + (double)cf[1], P.o[2] + (double)cf[2]};
+    s[0] = P.o[0] + (double)cf[0];
+    s[1] = P.o[1] + (double)cf[1];
+    s[2] = P.o[2] + (double)cf[2];
+    }
     // radii as the square root of the largest squared distance (sqrt is monotonic and
     // correctly rounded, so this equals the largest distance)
     double r2max = 0, m = 0, mx[3] = {0, 0, 0};
@@ -794,10 +802,10 @@ __global__ void __launch_bounds__(kGeoWarps * 32) k_leaf_geometry(const d4* __re
 }
 
 void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves, unsigned* status,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool keep_centre) {
     if (nleaves > 0) {
         k_leaf_geometry<<<(nleaves + kGeoWarps - 1) / kGeoWarps, kGeoWarps * 32, 0, s>>>(xm, c, leaves, nleaves,
-                                                                                       status);
+                                                                                       status, keep_centre);
         note_launch();
     }
 }
@@ -957,11 +965,32 @@ __global__ void k_internal_radii_finish(Cells c, int lev_begin, int lev_end,
     c.cr[cell].w = sqrt(e2);
 }
 
+// a reused tree: the centres stay, mass and centre of mass from the daughters
+__global__ void k_internal_keep(Cells c, int lev_begin, int lev_end) {
+    const int cell = lev_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= lev_end) return;
+    const int nch = c.nchild[cell];
+    if (nch == 0) return;
+    const int ch = c.child[cell];
+    double m = 0, mx[3] = {0, 0, 0};
+    for (int i = 0; i < nch; ++i) {
+        const double md = c.mass[ch + i];
+        const d4 cm = c.cr[ch + i];
+        m += md;
+        mx[0] += md * cm.x; mx[1] += md * cm.y; mx[2] += md * cm.z;
+    }
+    const d4 s = c.sr[cell];
+    c.cr[cell] = mk4(m > 0 ? mx[0] / m : s.x, m > 0 ? mx[1] / m : s.y, m > 0 ? mx[2] / m : s.z, 0.0);
+    c.mass[cell] = m;
+}
+
 void launch_internal_geometry(const d4* xm, Cells c, int lev_begin, int lev_end, int n,
-                              unsigned long long* rad_tmp, unsigned* status, cudaStream_t s) {
+                              unsigned long long* rad_tmp, unsigned* status, cudaStream_t s, bool keep_centre) {
     int ncl = lev_end - lev_begin;
     if (ncl <= 0) return;
-    k_internal_meb<<<(unsigned)ncl, kMebWarps * 32, 0, s>>>(c, lev_begin, lev_end, status); note_launch();
+    if (keep_centre) k_internal_keep<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end);
+    else k_internal_meb<<<(unsigned)ncl, kMebWarps * 32, 0, s>>>(c, lev_begin, lev_end, status);
+    note_launch();
     cudaMemsetAsync(rad_tmp, 0, sizeof(unsigned long long) * 2 * ncl, s);
     k_internal_radii<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xm, c, lev_begin, lev_end, rad_tmp); note_launch();
     k_internal_radii_finish<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, rad_tmp); note_launch();

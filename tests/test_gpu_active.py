@@ -111,3 +111,55 @@ def test_mixed_subset_accuracy(g):
     assert np.sqrt(np.mean(e ** 2)) < 2e-7 and np.sqrt(np.mean(e ** 2)) < 1.5 * np.sqrt(np.mean(ef ** 2)) + 1e-8
     assert st["n_p2p"] < 0.5 * st_full["n_p2p"]
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_reused_tree_unchanged_positions_equals_fresh(g, prec):
+    import torch
+    x, mu = inputs.plummer(20000, inputs.BASE_SEED + 116)
+    p = g.FMM_PREC_FP64 if prec == "fp64" else g.FMM_PREC_MIXED
+    ctx = g.Context(p=8, eps=1e-7, leaf_size=32, p2p_c=2.0, precision=p)
+    xt, mt = _dev(x), _dev(mu)
+    psi, acc = ctx.fmm_evaluate(xt, mt)
+    ones = torch.ones(20000, dtype=torch.uint8, device="cuda:0")
+    psi_r, acc_r = ctx.fmm_evaluate_active(xt, mt, ones, reuse_tree=True)
+    assert torch.equal(psi, psi_r) and torch.equal(acc, acc_r)
+    ctx.close()
+
+
+@pytest.mark.parametrize("which", ["all", "central"])
+def test_fp64_reused_tree_matches_oracle(g, orc, which):
+    """FP64 mode after a drift of the particles: the re-cycled tree against the oracle's."""
+    import torch
+    x, mu = inputs.plummer(6000, inputs.BASE_SEED + 117)
+    rng = np.random.default_rng(9)
+    x1 = x + rng.normal(size=x.shape) * 0.02
+    act = np.ones(6000, bool) if which == "all" else np.linalg.norm(x1, axis=1) < 0.7
+    kw = dict(p=6, eps=1e-7, leaf_size=16, p2p_c=1.0)
+    ctx = g.Context(precision=g.FMM_PREC_FP64, **kw)
+    ctx.fmm_evaluate(_dev(x), _dev(mu))
+    psi, acc, st = ctx.fmm_evaluate_active(_dev(x1), _dev(mu), _dev(act.astype(np.uint8)), reuse_tree=True,
+                                           stats=True)
+    run = orc.fmm_reused(x, mu, x1, mu, active=act, **kw)
+    assert st["n_m2l"] == run.stats["n_m2l"] and st["n_p2p"] == run.stats["n_p2p"]
+    acc = acc.cpu().numpy()
+    assert np.max(_rel(acc[act], run.acc[act])) <= PARITY_TOL
+    ctx.close()
+
+
+def test_reuse_needs_a_previous_single_system(g):
+    import torch
+    x, mu = inputs.plummer(3000, inputs.BASE_SEED + 118)
+    ones = torch.ones(3000, dtype=torch.uint8, device="cuda:0")
+    ctx = g.Context()
+    with pytest.raises(g.FMMError):  # nothing evaluated yet
+        ctx.fmm_evaluate_active(_dev(x), _dev(mu), ones, reuse_tree=True)
+    ctx.fmm_evaluate(_dev(x[:2000]), _dev(mu[:2000]))
+    with pytest.raises(g.FMMError):  # another n
+        ctx.fmm_evaluate_active(_dev(x), _dev(mu), ones, reuse_tree=True)
+    ctx.fmm_evaluate_batch(np.array([0, 1500, 3000]), _dev(x), _dev(mu), np.ones(2))
+    with pytest.raises(g.FMMError):  # the last evaluation was a forest
+        ctx.fmm_evaluate_active(_dev(x), _dev(mu), ones, reuse_tree=True)
+    ctx.fmm_evaluate(_dev(x), _dev(mu))
+    ctx.fmm_evaluate_active(_dev(x), _dev(mu), ones, reuse_tree=True)
+    ctx.close()

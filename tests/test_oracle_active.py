@@ -49,3 +49,29 @@ def test_subset_accuracy_and_work(orc):
     assert np.sqrt(np.mean(e_sub ** 2)) < 2 * np.sqrt(np.mean(e_full ** 2)) + 1e-8
     assert np.sqrt(np.mean(e_sub ** 2)) < 1e-6
     assert sub.stats["n_p2p"] < full.stats["n_p2p"] and sub.stats["n_m2l"] < full.stats["n_m2l"]
+
+
+def test_reused_tree_with_unchanged_positions_is_the_fresh_run(orc):
+    x, mu = inputs.plummer(2500, 304)
+    fresh = orc.fmm(x, mu, p=6, eps=1e-6, leaf_size=24)
+    reuse = orc.fmm_reused(x, mu, x, mu, p=6, eps=1e-6, leaf_size=24)
+    assert np.array_equal(fresh.acc, reuse.acc) and np.array_equal(fresh.m2l, reuse.m2l)
+    assert np.array_equal(fresh.cells_dbl, reuse.cells_dbl)
+
+
+def test_reused_tree_after_a_drift(orc):
+    """After the particles moved, the re-cycled tree keeps its cells and centres but its
+    radii enclose the new positions exactly, and the forces keep the fresh tree's accuracy."""
+    x, mu = inputs.plummer(3000, 305)
+    rng = np.random.default_rng(3)
+    x1 = x + rng.normal(size=x.shape) * 0.02
+    reuse = orc.fmm_reused(x, mu, x1, mu, p=6, eps=1e-6, leaf_size=24)
+    fresh = orc.fmm(x1, mu, p=6, eps=1e-6, leaf_size=24)
+    xs = x1[reuse.perm]
+    for (lev, leaf, f, c, nch), (sx, sy, sz, rho, m, _) in zip(reuse.cells_int, reuse.cells_dbl):
+        d = np.linalg.norm(xs[f:f + c] - np.array([sx, sy, sz]), axis=1)
+        assert d.max() == rho
+        assert np.isclose(m, mu[reuse.perm][f:f + c].sum(), rtol=1e-14)
+    _, a_t, _, _ = orc.direct(x1, mu)
+    e_r, e_f = _rel(reuse.acc, a_t), _rel(fresh.acc, a_t)
+    assert np.sqrt(np.mean(e_r ** 2)) < 2 * np.sqrt(np.mean(e_f ** 2))
