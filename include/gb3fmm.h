@@ -150,15 +150,20 @@ int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, doubl
                int64_t nsinks, const int64_t* sinks, double* psi, double* acc, double* f,
                void* stream);
 
-/* Forces for a subset of the particles (Sec. 7.1: block time steps).  All n particles
- * act as sources; active (DEVICE, n bytes, caller order) marks the sinks: psi[i] and
- * acc[i] are written for active[i] != 0 only and left untouched otherwise.  The tree and
+/* The general evaluation: forces for a subset of the particles, individual accuracy
+ * parameters and a re-cycled tree, each optional.
+ * Subset (Sec. 7.1: block time steps).  All n particles act as sources; active (DEVICE,
+ * n bytes, caller order, NULL = all) marks the sinks: psi[i] and acc[i] are written for
+ * active[i] != 0 only and left untouched otherwise.  The tree and
  * the upward pass cover all particles; the walk drops every cell pair whose sink cell
  * holds no active particle, so M2L, P2P, L2L and L2P run for the active part of the tree
  * only.  The MAC scale of a sink cell (eqs. 18a,b) is the minimum over its ACTIVE
  * particles, and the low-order estimate of Sec. 5.3.2 is evaluated for the active sinks:
  * the error criterion concerns the forces being computed.  With every particle active
  * the result equals fmm_evaluate's bit for bit.
+ * Individual accuracy (Sec. 7, opening): eps_b (DEVICE, n doubles > 0, caller order, NULL = the
+ * global eps) replaces eps min_{b in B} a_b in (18a) (f_b in 18b) by min_{b in B} eps_b a_b;
+ * ignored by the geometric criterion.  eps_b[i] = eps for all i gives the global result.
  * reuse_tree = 1 re-cycles the tree of the previous evaluation on ctx (the other
  * measure Sec. 7.1 names): it must have been a completed single-system evaluation
  * (fmm_evaluate, fmm_evaluate_host or fmm_evaluate_active) of the same n particles in the
@@ -168,11 +173,11 @@ int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, doubl
  * need not be the key cubes of the new positions); multipoles, walk and everything after
  * them are recomputed.  With unchanged positions the result equals a fresh evaluation's
  * bit for bit.  reuse_tree = 0 builds the tree anew.  Other arguments and errors as for
- * fmm_evaluate; FMM_E_INVALID also for active == NULL with n > 0 or for reuse_tree = 1
- * without such a previous evaluation. */
+ * fmm_evaluate; FMM_E_INVALID also for a non-positive or non-finite eps_b or for
+ * reuse_tree = 1 without such a previous evaluation. */
 int fmm_evaluate_active(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G,
-                        const double* scale, const unsigned char* active, int reuse_tree, double* psi,
-                        double* acc, void* stream, fmm_stats* stats);
+                        const double* scale, const unsigned char* active, const double* eps_b, int reuse_tree,
+                        double* psi, double* acc, void* stream, fmm_stats* stats);
 
 /* Many independent systems in one call (the batched ensemble).  System s holds
  * particles [offsets[s], offsets[s+1]) of x/mu/psi/acc (device arrays laid out as

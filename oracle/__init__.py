@@ -83,10 +83,11 @@ def _declare(L):
     L.orc_meb_balls.argtypes = [C.c_int, _dp, _dp, _dp, C.POINTER(C.c_double)]
     L.orc_fmm.argtypes = [C.c_long, _dp, _dp, C.c_double, C.POINTER(Params), C.c_void_p]
     L.orc_fmm.restype = C.c_void_p
-    L.orc_fmm_active.argtypes = [C.c_long, _dp, _dp, C.c_double, C.POINTER(Params), C.c_void_p, C.c_void_p]
+    L.orc_fmm_active.argtypes = [C.c_long, _dp, _dp, C.c_double, C.POINTER(Params), C.c_void_p, C.c_void_p,
+                                 C.c_void_p]
     L.orc_fmm_active.restype = C.c_void_p
     L.orc_fmm_reuse.argtypes = [C.c_void_p, C.c_long, _dp, _dp, C.c_double, C.POINTER(Params), C.c_void_p,
-                                C.c_void_p]
+                                C.c_void_p, C.c_void_p]
     L.orc_fmm_reuse.restype = C.c_void_p
     L.orc_run_free.argtypes = [C.c_void_p]
     L.orc_run_outputs.argtypes = [C.c_void_p, _dp, _dp]
@@ -229,17 +230,19 @@ class Run:
 
 
 def fmm(x, mu, G=1.0, p=6, eps=1e-7, mac=MAC_A, theta_crit=0.5, leaf_size=32, p2p_c=1.0,
-        scale=None, keep=True, active=None):
+        scale=None, keep=True, active=None, eps_b=None):
     """Run the oracle FMM; raises ValueError on invalid input.  active (bool/uint8 [n],
-    caller order): forces for that subset only (Sec. 7.1), NaN for the others."""
+    caller order): forces for that subset only (Sec. 7.1), NaN for the others; eps_b [n]:
+    individual accuracy parameters (Sec. 7, opening)."""
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     prm = Params(p, eps, mac, theta_crit, leaf_size, p2p_c, 1 if scale is not None else 0)
     sc = None if scale is None else np.ascontiguousarray(scale, dtype=np.float64)
     act = None if active is None else np.ascontiguousarray(np.asarray(active) != 0, dtype=np.uint8)
     L = lib()
+    eb = None if eps_b is None else np.ascontiguousarray(eps_b, dtype=np.float64)
     h = L.orc_fmm_active(len(mu), x, mu, G, C.byref(prm), sc.ctypes.data if sc is not None else None,
-                         act.ctypes.data if act is not None else None)
+                         act.ctypes.data if act is not None else None, eb.ctypes.data if eb is not None else None)
     if not h:
         raise ValueError("oracle rejected the input")
     try:
@@ -260,11 +263,12 @@ def fmm_reused(x0, mu0, x, mu, G=1.0, p=6, eps=1e-7, mac=MAC_A, theta_crit=0.5, 
     prm = Params(p, eps, mac, theta_crit, leaf_size, p2p_c, 0)
     act = None if active is None else np.ascontiguousarray(np.asarray(active) != 0, dtype=np.uint8)
     L = lib()
-    h0 = L.orc_fmm_active(len(mu0), x0, mu0, G, C.byref(prm), None, None)
+    h0 = L.orc_fmm_active(len(mu0), x0, mu0, G, C.byref(prm), None, None, None)
     if not h0:
         raise ValueError("oracle rejected the first input")
     try:
-        h = L.orc_fmm_reuse(h0, len(mu), x, mu, G, C.byref(prm), None, act.ctypes.data if act is not None else None)
+        h = L.orc_fmm_reuse(h0, len(mu), x, mu, G, C.byref(prm), None, act.ctypes.data if act is not None else None,
+                            None)
         if not h:
             raise ValueError("oracle rejected the second input")
         try:

@@ -1069,7 +1069,8 @@ static int depth_of(const tree_t *t)
 
 void orc_run_free(orc_run *run);
 
-static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, const unsigned char *active);
+static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, const unsigned char *active,
+                             const double *eps_b);
 
 /* The whole FMM (Sec. 2.2.2): returns NULL on invalid input. */
 /* Sec. 7.1: active (caller order, may be NULL = all) marks the sinks whose forces are
@@ -1078,7 +1079,8 @@ static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, con
  * psi and acc of inactive particles are NaN. */
 orc_run *orc_fmm_active(long n, const double *x, const double *mu, double G, const orc_params *prm,
                         const double *scale_in /* caller order, may be NULL */,
-                        const unsigned char *active /* caller order, may be NULL */)
+                        const unsigned char *active /* caller order, may be NULL */,
+                        const double *eps_b /* caller order, may be NULL */)
 {
     if (n < 0 || !prm || prm->p < 1 || prm->p > 20 || prm->leaf_size < 1) return NULL;
     if (prm->mac != MAC_THETA && !(prm->eps > 0)) return NULL;
@@ -1095,12 +1097,13 @@ orc_run *orc_fmm_active(long n, const double *x, const double *mu, double G, con
     tree_t *t = &run->t;
     build_tree(t, n, x, mu, prm->leaf_size);
     cell_geometry(t, 0);
-    evaluate_on_tree(run, G, scale_in, active);
+    evaluate_on_tree(run, G, scale_in, active, eps_b);
     return run;
 }
 
 /* everything after the tree and its geometry (shared by fresh and re-cycled trees) */
-static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, const unsigned char *active)
+static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, const unsigned char *active,
+                             const double *eps_b)
 {
     const orc_params *prm = &run->prm;
     tree_t *t = &run->t;
@@ -1127,6 +1130,10 @@ static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, con
         } else {
             estimate_scale(run, prm->mac == MAC_F, run->scale_sorted);
         }
+        /* individual accuracy parameters (Sec. 7, opening): the criterion's right-hand side
+         * becomes min_{b in B} eps_b a_b, i.e. eps times the minimum of (eps_b / eps) a_b */
+        if (eps_b)
+            for (long i = 0; i < n; ++i) run->scale_sorted[i] *= eps_b[t->perm[i]] / prm->eps;
         min_scale(t, 0, run->scale_sorted);
     }
 
@@ -1200,7 +1207,8 @@ static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, con
  * n particles in the same caller order) for new positions x and masses mu; radii, masses
  * and centres of mass are recomputed, then the evaluation proceeds as usual */
 orc_run *orc_fmm_reuse(const orc_run *prev, long n, const double *x, const double *mu, double G,
-                       const orc_params *prm, const double *scale_in, const unsigned char *active)
+                       const orc_params *prm, const double *scale_in, const unsigned char *active,
+                       const double *eps_b)
 {
     if (!prev || prev->t.n != n || n <= 0 || !prm || prm->p < 1 || prm->p > 20) return NULL;
     if (prm->mac != MAC_THETA && !(prm->eps > 0)) return NULL;
@@ -1233,14 +1241,14 @@ orc_run *orc_fmm_reuse(const orc_run *prev, long n, const double *x, const doubl
         t->mus[i] = mu[j];
     }
     cell_geometry_k(t, 0, 1);
-    evaluate_on_tree(run, G, scale_in, active);
+    evaluate_on_tree(run, G, scale_in, active, eps_b);
     return run;
 }
 
 orc_run *orc_fmm(long n, const double *x, const double *mu, double G, const orc_params *prm,
                  const double *scale_in /* caller order, may be NULL */)
 {
-    return orc_fmm_active(n, x, mu, G, prm, scale_in, NULL);
+    return orc_fmm_active(n, x, mu, G, prm, scale_in, NULL, NULL);
 }
 
 void orc_run_free(orc_run *run)

@@ -457,7 +457,8 @@ static int phase_times(fmm_ctx* ctx) {
 // ------------------------------------------------------------------ one evaluation
 static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* mu, double G, const double* scale,
                            double* psi, double* acc, cudaStream_t s, fmm_stats* stats,
-                           const unsigned char* active = nullptr, bool reuse_tree = false) {
+                           const unsigned char* active = nullptr, bool reuse_tree = false,
+                           const double* eps_b = nullptr) {
     const fmm_params& prm = ctx->prm;
     ctx->active_mode = false;
     if (reuse_tree && (ctx->tree_n != n || ctx->nsys != 0 || n == 0))
@@ -525,6 +526,15 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
             launch_scale_from_caller(scale, P<int>(ctx->perm), n, P<double>(ctx->scale_sorted), s);
         else
             TRY(estimate_scale(ctx, s));
+        if (eps_b) {  // Sec. 7, opening: min over the sinks of eps_b a_b in place of eps min a_b
+            launch_scale_eps(eps_b, P<int>(ctx->perm), n, prm.eps, P<double>(ctx->scale_sorted),
+                             P<unsigned>(ctx->status), s);
+            unsigned st = 0;
+            CU(cudaMemcpyAsync(&ctx->h_int[0], ctx->status.p, sizeof st, cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            memcpy(&st, &ctx->h_int[0], sizeof st);
+            if (st & kStatInvalid) return fail(ctx, FMM_E_INVALID, "eps_b must be positive and finite");
+        }
         launch_minscale_leaves(P<double>(ctx->scale_sorted), c, P<int>(ctx->leaves), ctx->nleaves, s);
         for (int L = nlev - 1; L >= 0; --L) launch_minscale_level(c, ctx->lev_start[L], ctx->lev_start[L + 1], s);
     }
@@ -720,17 +730,17 @@ int fmm_evaluate(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, dou
 }
 
 int fmm_evaluate_active(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, const double* scale,
-                        const unsigned char* active, int reuse_tree, double* psi, double* acc, void* stream,
-                        fmm_stats* stats) {
+                        const unsigned char* active, const double* eps_b, int reuse_tree, double* psi, double* acc,
+                        void* stream, fmm_stats* stats) {
     if (!ctx) return FMM_E_INVALID;
     ctx->err[0] = 0;
     if (n < 0 || n > 0x7fffffffLL) return fail(ctx, FMM_E_INVALID, "n out of range");
-    if (n > 0 && (!x || !mu || !psi || !acc || !active)) return fail(ctx, FMM_E_INVALID, "NULL buffer");
+    if (n > 0 && (!x || !mu || !psi || !acc)) return fail(ctx, FMM_E_INVALID, "NULL buffer");
     if (!std::isfinite(G)) return fail(ctx, FMM_E_INVALID, "G is not finite");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, FMM_E_CUDA, "cudaSetDevice failed");
     if (reuse_tree != 0 && reuse_tree != 1) return fail(ctx, FMM_E_INVALID, "reuse_tree must be 0 or 1");
     return evaluate_device(ctx, (int)n, x, mu, G, scale, psi, acc, (cudaStream_t)stream, stats, active,
-                           reuse_tree != 0);
+                           reuse_tree != 0, eps_b);
 }
 
 int fmm_evaluate_host(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, double* psi, double* acc,

@@ -192,6 +192,9 @@ void launch_finish(const double* psi_far, const double* acc_far, const double* p
 // Sec. 7.1: pact[i] = active[perm[i]] != 0 (sorted order) and act[cell] = the cell holds an
 // active particle (from a prefix sum of pact over the cells' particle ranges); ai holds
 // n + 1 ints, scan n ints, scan_tmp scan_tmp_ints(n) ints
+// individual accuracy parameters (Sec. 7, opening): scale_sorted[i] *= eps_b[perm[i]] / eps
+void launch_scale_eps(const double* eps_b, const int* perm, int n, double eps, double* scale_sorted, unsigned* status,
+                      cudaStream_t s);
 void launch_active_flags(const unsigned char* active, const int* perm, int n, const int* first, const int* count,
                          int ncells, unsigned char* pact, unsigned char* act, int* ai, int* scan, int* scan_tmp,
                          cudaStream_t s);

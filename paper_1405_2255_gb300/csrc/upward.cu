@@ -260,3 +260,21 @@ void launch_active_flags(const unsigned char* active, const int* perm, int n, co
     note_launch();
 }
 }  // namespace gb3
+
+namespace gb3 {
+// ---------------------------------------------------------------- individual accuracy (Sec. 7, opening)
+// scale_sorted[i] *= eps_b[perm[i]] / eps, so that eps * min_B(scale) = min_B(eps_b a_b);
+// a non-positive or non-finite eps_b sets kStatInvalid
+__global__ void k_scale_eps(const double* __restrict__ eps_b, const int* __restrict__ perm, int n, double eps,
+                            double* __restrict__ scale_sorted, unsigned* __restrict__ status) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double e = eps_b[perm[i]];
+        if (!(e > 0) || !isfinite(e)) atomicOr(status, kStatInvalid);
+        scale_sorted[i] *= e / eps;
+    }
+}
+void launch_scale_eps(const double* eps_b, const int* perm, int n, double eps, double* scale_sorted, unsigned* status,
+                      cudaStream_t s) {
+    if (n > 0) k_scale_eps<<<grid_for(n, 256), 256, 0, s>>>(eps_b, perm, n, eps, scale_sorted, status); note_launch();
+}
+}  // namespace gb3

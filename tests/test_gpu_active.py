@@ -163,3 +163,31 @@ def test_reuse_needs_a_previous_single_system(g):
     ctx.fmm_evaluate(_dev(x), _dev(mu))
     ctx.fmm_evaluate_active(_dev(x), _dev(mu), ones, reuse_tree=True)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_individual_eps(g, orc, prec):
+    """Sec. 7, opening: eps_b = eps is the global run bit for bit; a tighter eps_b for the inner
+    particles matches the oracle (FP64) and lowers their errors (mixed)."""
+    import torch
+    x, mu = inputs.plummer(8000, inputs.BASE_SEED + 119)
+    p = g.FMM_PREC_FP64 if prec == "fp64" else g.FMM_PREC_MIXED
+    kw = dict(p=6, eps=1e-5, leaf_size=16, p2p_c=1.0)
+    ctx = g.Context(precision=p, **kw)
+    xt, mt = _dev(x), _dev(mu)
+    _, acc = ctx.fmm_evaluate(xt, mt)
+    _, acc_same = ctx.fmm_evaluate_active(xt, mt, eps_b=torch.full((8000,), 1e-5, dtype=torch.float64, device="cuda:0"))
+    assert torch.equal(acc, acc_same)
+    inner = np.linalg.norm(x, axis=1) < 0.5
+    eb = np.where(inner, 1e-8, 1e-5)
+    _, acc_t, st = ctx.fmm_evaluate_active(xt, mt, eps_b=_dev(eb), stats=True)
+    run = orc.fmm(x, mu, eps_b=eb, **kw)
+    if prec == "fp64":
+        assert st["n_m2l"] == run.stats["n_m2l"] and st["n_p2p"] == run.stats["n_p2p"]
+        assert np.max(_rel(acc_t.cpu().numpy(), run.acc)) <= PARITY_TOL
+    _, a_t, _, _ = orc.direct(x, mu)
+    e0, e1 = _rel(acc.cpu().numpy(), a_t), _rel(acc_t.cpu().numpy(), a_t)
+    assert np.sqrt(np.mean(e1[inner] ** 2)) < 0.2 * np.sqrt(np.mean(e0[inner] ** 2))
+    with pytest.raises(g.FMMError):
+        ctx.fmm_evaluate_active(xt, mt, eps_b=torch.zeros(8000, dtype=torch.float64, device="cuda:0"))
+    ctx.close()

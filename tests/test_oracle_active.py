@@ -75,3 +75,20 @@ def test_reused_tree_after_a_drift(orc):
     _, a_t, _, _ = orc.direct(x1, mu)
     e_r, e_f = _rel(reuse.acc, a_t), _rel(fresh.acc, a_t)
     assert np.sqrt(np.mean(e_r ** 2)) < 2 * np.sqrt(np.mean(e_f ** 2))
+
+
+def test_individual_eps(orc):
+    """Sec. 7, opening: eps_b = eps everywhere is the global run; tightening eps_b for a group of
+    particles lowers their errors and keeps the rest as it was."""
+    x, mu = inputs.plummer(3000, 306)
+    kw = dict(p=5, eps=1e-5, leaf_size=24)
+    ref = orc.fmm(x, mu, **kw)
+    same = orc.fmm(x, mu, eps_b=np.full(3000, 1e-5), **kw)
+    assert np.array_equal(ref.acc, same.acc)
+    inner = np.linalg.norm(x, axis=1) < 0.5
+    eb = np.where(inner, 1e-8, 1e-5)
+    tight = orc.fmm(x, mu, eps_b=eb, **kw)
+    _, a_t, _, _ = orc.direct(x, mu)
+    e_ref, e_t = _rel(ref.acc, a_t), _rel(tight.acc, a_t)
+    assert np.sqrt(np.mean(e_t[inner] ** 2)) < 0.1 * np.sqrt(np.mean(e_ref[inner] ** 2))
+    assert tight.stats["n_p2p"] + tight.stats["n_m2l"] > ref.stats["n_p2p"] + ref.stats["n_m2l"]
