@@ -195,12 +195,29 @@ static void l2l(int p, const cplx *F, const double s[3], const double sp[3], cpl
 
 /* eqs. (3a), (7): Psi_n^m(x_b) = sum_{k<=p-n} sum_l Upsilon_k^{l*}(s_B - x_b) F_{n+k}^{m+l}(s_B),
  * returns Psi = Psi_0^0 and a = -(Re Psi_1^1, Im Psi_1^1, Psi_1^0). */
-static void l2p(int p, const cplx *F, const double s[3], const double xb[3], double *psi, double a[3])
+/* tidal tensor of Sec. 7.4 from Psi_2^m: T = (xx, xy, xz, yy, yz, zz).  Reading R-tidal:
+ * the paper prints T_xy = -Im{Psi_2^2}/2; with the harmonics of App. A.3 (the same that give
+ * a = -(Re Psi_1^1, Im Psi_1^1, Psi_1^0)) Psi_2^2 = (d_x + i d_y)^2 Psi, so Im Psi_2^2 = 2 T_xy
+ * and T_xy = +Im{Psi_2^2}/2; the other five entries are as printed. */
+static void tidal_from_psi2(const cplx *Psi, double T[6])
+{
+    const cplx p20 = Psi[IX(2, 0)], p21 = Psi[IX(2, 1)], p22 = Psi[IX(2, 2)];
+    T[0] = -0.5 * creal(p20) + 0.5 * creal(p22);
+    T[1] = 0.5 * cimag(p22);
+    T[2] = creal(p21);
+    T[3] = -0.5 * creal(p20) - 0.5 * creal(p22);
+    T[4] = cimag(p21);
+    T[5] = creal(p20);
+}
+
+/* eq. (7) for n <= 1 (n <= 2 with T != NULL: the tidal tensor of Sec. 7.4) */
+static void l2p_t(int p, const cplx *F, const double s[3], const double xb[3], double *psi, double a[3], double *T)
 {
     cplx *Y = malloc(sizeof(cplx) * NCOEF(p));
     orc_upsilon(p, s[0] - xb[0], s[1] - xb[1], s[2] - xb[2], Y);
-    cplx Psi[4] = {0, 0, 0, 0}; /* (0,0), (1,-1), (1,0), (1,1) */
-    for (int n = 0; n <= 1 && n <= p; ++n)
+    cplx Psi[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}; /* (n, m) for n <= 2 at IX(n, m) */
+    const int nmax = T ? 2 : 1;
+    for (int n = 0; n <= nmax && n <= p; ++n)
         for (int m = -n; m <= n; ++m) {
             cplx acc = 0;
             for (int k = 0; k <= p - n; ++k)
@@ -219,7 +236,15 @@ static void l2p(int p, const cplx *F, const double s[3], const double xb[3], dou
     } else {
         a[0] = a[1] = a[2] = 0.0;
     }
+    if (T) {
+        if (p >= 2) tidal_from_psi2(Psi, T);
+        else for (int k = 0; k < 6; ++k) T[k] = 0.0;
+    }
     free(Y);
+}
+static void l2p(int p, const cplx *F, const double s[3], const double xb[3], double *psi, double a[3])
+{
+    l2p_t(p, F, s, xb, psi, a, NULL);
 }
 
 /* eq. (14): P_n^2 = sum_m (n-m)! (n+m)! |M_n^m|^2 */
@@ -441,6 +466,28 @@ long orc_direct(long n, const double *x, const double *mu, double G, long ns, co
         if (f) f[i] = G * nval(&Fs);
     }
     return coincident;
+}
+
+/* the tidal tensor T = grad grad Psi of eq. (1) at the sinks (Sec. 7.4), directly:
+ * T_b = sum_a G mu_a (3 d d^T - r^2 I) / r^5 with d = x_b - x_a, as (xx, xy, xz, yy, yz, zz) */
+void orc_direct_tidal(long n, const double *x, const double *mu, double G, long ns, const long *sinks, double *T)
+{
+    long nsink = sinks ? ns : n;
+    for (long i = 0; i < nsink; ++i) {
+        long b = sinks ? sinks[i] : i;
+        nsum S[6] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        for (long a = 0; a < n; ++a) {
+            if (a == b) continue;
+            double d[3] = {x[3 * b] - x[3 * a], x[3 * b + 1] - x[3 * a + 1], x[3 * b + 2] - x[3 * a + 2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2), q5 = mu[a] / (r2 * r2 * r);
+            int k = 0;
+            for (int u = 0; u < 3; ++u)
+                for (int v = u; v < 3; ++v) nadd(&S[k++], q5 * (3.0 * d[u] * d[v] - (u == v ? r2 : 0.0)));
+        }
+        for (int k = 0; k < 6; ++k) T[6 * i + k] = G * nval(&S[k]);
+    }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -957,6 +1004,27 @@ static void p2p_pair(const tree_t *t, long A, long B, double *psi, double *acc, 
     }
 }
 
+/* the near-field part of the tidal tensor over a cell pair: T_i += mu_j (3 d d^T - r^2 I)/r^5 */
+static void p2p_tidal_pair(const tree_t *t, long A, long B, double *T)
+{
+    const cell_t *a = &t->cells[A], *b = &t->cells[B];
+    for (long i = b->first; i < b->first + b->count; ++i) {
+        double S[6] = {0, 0, 0, 0, 0, 0};
+        for (long j = a->first; j < a->first + a->count; ++j) {
+            if (i == j) continue;
+            double d[3] = {t->xs[3 * i] - t->xs[3 * j], t->xs[3 * i + 1] - t->xs[3 * j + 1],
+                           t->xs[3 * i + 2] - t->xs[3 * j + 2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2), q5 = t->mus[j] / (r2 * r2 * r);
+            int k = 0;
+            for (int u = 0; u < 3; ++u)
+                for (int v = u; v < 3; ++v) S[k++] += q5 * (3.0 * d[u] * d[v] - (u == v ? r2 : 0.0));
+        }
+        for (int k = 0; k < 6; ++k) T[6 * i + k] += S[k];
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Whole evaluation                                                           */
 /* ------------------------------------------------------------------------- */
@@ -969,6 +1037,7 @@ typedef struct {
     int leaf_size;
     double p2p_c;     /* direct summation when N_A N_B < p2p_c p^3 */
     int scale_src;    /* 0: low-order FMM estimate, 1: caller-supplied per-particle scale */
+    int want_tidal;   /* 1: also the tidal tensor of Sec. 7.4 */
 } orc_params;
 
 typedef struct {
@@ -982,6 +1051,7 @@ typedef struct {
     plist m2l, p2p;
     double *scale_sorted; /* per sorted particle: the scale used in the MAC */
     double *psi, *acc;    /* caller order, G applied */
+    double *tidal;        /* caller order [n][6] (xx, xy, xz, yy, yz, zz), G applied; NULL unless asked */
     orc_stats st;
 } orc_run;
 
@@ -1176,6 +1246,13 @@ static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, con
         p2p_pair(t, A, B, ps, ac, &coin, 0);
         inter += t->cells[A].count * t->cells[B].count - (A == B ? t->cells[A].count : 0);
     }
+    double *tn = NULL;
+    if (prm->want_tidal) {
+        tn = calloc(6 * n, sizeof(double));
+        for (long i = 0; i < w.p2p.n; ++i) p2p_tidal_pair(t, w.p2p.v[i].a, w.p2p.v[i].b, tn);
+        free(run->tidal);
+        run->tidal = calloc(6 * n, sizeof(double));
+    }
     run->st.p2p_interactions = inter;
     run->st.coincident = coin;
 
@@ -1191,16 +1268,18 @@ static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, con
                 if (!t->act[i]) {
                     run->psi[o] = NAN;
                     for (int d = 0; d < 3; ++d) run->acc[3 * o + d] = NAN;
+                    if (tn) for (int d = 0; d < 6; ++d) run->tidal[6 * o + d] = NAN;
                     continue;
                 }
-                double psi_l, a[3];
-                l2p(p, &F[ci * nco], c->s, &t->xs[3 * i], &psi_l, a);
+                double psi_l, a[3], Tf[6];
+                l2p_t(p, &F[ci * nco], c->s, &t->xs[3 * i], &psi_l, a, tn ? Tf : NULL);
+                if (tn) for (int d = 0; d < 6; ++d) run->tidal[6 * o + d] = G * (Tf[d] + tn[6 * i + d]);
                 run->psi[o] = G * (psi_l + ps[i]);
                 for (int d = 0; d < 3; ++d) run->acc[3 * o + d] = G * (a[d] + ac[3 * i + d]);
             }
         }
     }
-    free(ps); free(ac); free(M); free(F); free(P); free(w.binom);
+    free(ps); free(ac); free(M); free(F); free(P); free(w.binom); free(tn);
 }
 
 /* Sec. 7.1's re-cycled tree: the particle order, cells and centres of the run prev (the same
@@ -1256,11 +1335,17 @@ void orc_run_free(orc_run *run)
     if (!run) return;
     free_tree(&run->t);
     free(run->m2l.v); free(run->p2p.v);
-    free(run->scale_sorted); free(run->psi); free(run->acc);
+    free(run->scale_sorted); free(run->psi); free(run->acc); free(run->tidal);
     free(run);
 }
 
 /* accessors used by the Python test wrapper */
+int orc_run_tidal(const orc_run *run, double *T)
+{
+    if (!run->tidal) return 0;
+    memcpy(T, run->tidal, sizeof(double) * 6 * run->t.n);
+    return 1;
+}
 void orc_run_outputs(const orc_run *run, double *psi, double *acc)
 {
     memcpy(psi, run->psi, sizeof(double) * run->t.n);
