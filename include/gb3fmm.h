@@ -174,10 +174,17 @@ int fmm_direct(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, doubl
  * them are recomputed.  With unchanged positions the result equals a fresh evaluation's
  * bit for bit.  reuse_tree = 0 builds the tree anew.  Other arguments and errors as for
  * fmm_evaluate; FMM_E_INVALID also for a non-positive or non-finite eps_b or for
- * reuse_tree = 1 without such a previous evaluation. */
+ * reuse_tree = 1 without such a previous evaluation.
+ * Tidal tensor (Sec. 7.4): tidal (DEVICE, [n][6] doubles, caller order, NULL = not computed)
+ * receives T = grad grad Psi as (xx, xy, xz, yy, yz, zz), G applied, for the active particles:
+ * the far part from the local expansion's Psi_2^m at the particle (T_xy = +Im Psi_2^2 / 2
+ * with this library's harmonics; the paper prints the opposite sign), the near part as the
+ * direct Hessian over the same sources as the particle's P2P (mixed mode: FP32 terms on
+ * two-float positions with two-float sums; FP64 mode: FP64).  T is one order of the
+ * expansion less accurate than a. */
 int fmm_evaluate_active(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G,
                         const double* scale, const unsigned char* active, const double* eps_b, int reuse_tree,
-                        double* psi, double* acc, void* stream, fmm_stats* stats);
+                        double* psi, double* acc, double* tidal, void* stream, fmm_stats* stats);
 
 /* Many independent systems in one call (the batched ensemble).  System s holds
  * particles [offsets[s], offsets[s+1]) of x/mu/psi/acc (device arrays laid out as

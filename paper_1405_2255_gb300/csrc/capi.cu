@@ -93,6 +93,7 @@ struct fmm_ctx {
     // force evaluation for a subset (Sec. 7.1): per sorted particle and per cell activity
     Buf pact, act, act_i, act_scan;
     bool active_mode = false;
+    Buf tid_far, tid_near;  // tidal tensor parts (Sec. 7.4), sorted order
     // the tree of the last evaluation can be reused (Sec. 7.1) when it was a single system
     // of tree_n particles that completed
     int tree_n = -1;
@@ -103,7 +104,7 @@ struct fmm_ctx {
                 &leaf_pos, &rad_tmp, &M, &F, &Pw, &binom, &M1, &F1, &Ff, &front0, &front1, &m2l, &p2p,
                 &sort_tmp, &m2l_tmp, &p2p_tmp, &seg_start, &seg_end, &est_m2l, &est_p2p, &m2l_seg_start,
                 &m2l_seg_end, &psi_far, &acc_far, &psi_near, &acc_near, &scale_sorted, &sys_off, &sys_G,
-                &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan};
+                &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan, &tid_far, &tid_near};
     }
     // tree shape of the last evaluation
     std::vector<int> lev_start;
@@ -458,7 +459,7 @@ static int phase_times(fmm_ctx* ctx) {
 static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* mu, double G, const double* scale,
                            double* psi, double* acc, cudaStream_t s, fmm_stats* stats,
                            const unsigned char* active = nullptr, bool reuse_tree = false,
-                           const double* eps_b = nullptr) {
+                           const double* eps_b = nullptr, double* tidal = nullptr) {
     const fmm_params& prm = ctx->prm;
     ctx->active_mode = false;
     if (reuse_tree && (ctx->tree_n != n || ctx->nsys != 0 || n == 0))
@@ -604,6 +605,12 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     const int* sys_off = ctx->nsys ? P<int>(ctx->sys_off) : nullptr;
     launch_coincident(P<d4>(ctx->xm), P<uint64_t>(ctx->keys), n, P<unsigned long long>(ctx->coin), s, sys_off,
                       ctx->nsys);
+    if (tidal) {  // Sec. 7.4: the near part over the same sources as the P2P
+        TRY(ensure(ctx->tid_near, sizeof(double) * 6 * (size_t)n));
+        launch_p2p_tidal(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), n, prm.precision == FMM_PREC_MIXED,
+                         c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves),
+                         ctx->nleaves, P<double>(ctx->tid_near), s);
+    }
     if (timing) CU(cudaEventRecord(ctx->ev[EV_P2P], s));
 
     // A11-A12: L2L, L2P, combine and scatter
@@ -620,6 +627,13 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     launch_finish(P<double>(ctx->psi_far), P<double>(ctx->acc_far), P<double>(ctx->psi_near), P<double>(ctx->acc_near),
                   P<int>(ctx->perm), n, G, psi, acc, s, sys_off, ctx->nsys ? P<double>(ctx->sys_G) : nullptr,
                   ctx->nsys, ctx->active_mode ? P<unsigned char>(ctx->pact) : nullptr);
+    if (tidal) {  // Sec. 7.4: the far part from Psi_2^m of the local expansions
+        TRY(ensure(ctx->tid_far, sizeof(double) * 6 * (size_t)n));
+        launch_l2p_tidal(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->F),
+                         P<double>(ctx->tid_far), s);
+        launch_finish_tidal(P<double>(ctx->tid_far), P<double>(ctx->tid_near), P<int>(ctx->perm), n, G,
+                            ctx->active_mode ? P<unsigned char>(ctx->pact) : nullptr, tidal, s);
+    }
     if (timing) {
         CU(cudaEventRecord(ctx->ev[EV_DOWN], s));
         CU(cudaEventRecord(ctx->ev[EV_END], s));
@@ -731,7 +745,7 @@ int fmm_evaluate(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, dou
 
 int fmm_evaluate_active(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, const double* scale,
                         const unsigned char* active, const double* eps_b, int reuse_tree, double* psi, double* acc,
-                        void* stream, fmm_stats* stats) {
+                        double* tidal, void* stream, fmm_stats* stats) {
     if (!ctx) return FMM_E_INVALID;
     ctx->err[0] = 0;
     if (n < 0 || n > 0x7fffffffLL) return fail(ctx, FMM_E_INVALID, "n out of range");
@@ -740,7 +754,7 @@ int fmm_evaluate_active(fmm_ctx* ctx, int64_t n, const double* x, const double* 
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, FMM_E_CUDA, "cudaSetDevice failed");
     if (reuse_tree != 0 && reuse_tree != 1) return fail(ctx, FMM_E_INVALID, "reuse_tree must be 0 or 1");
     return evaluate_device(ctx, (int)n, x, mu, G, scale, psi, acc, (cudaStream_t)stream, stats, active,
-                           reuse_tree != 0, eps_b);
+                           reuse_tree != 0, eps_b, tidal);
 }
 
 int fmm_evaluate_host(fmm_ctx* ctx, int64_t n, const double* x, const double* mu, double G, double* psi, double* acc,

@@ -135,6 +135,32 @@ __device__ inline double warp_min(double v) {
     return v;
 }
 
+// ---------------------------------------------------------------- two-float sums
+// (hi, lo) with hi + lo the sum to about 2^-48 relative: TwoSum (Knuth) of the running sum
+// and each FP32 partial, in explicit round-to-nearest operations
+struct ff {
+    float hi, lo;
+};
+__device__ inline ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff{s, e};
+}
+__device__ inline void ff_add_shfl(ff& a, int o) {
+    float h = __shfl_xor_sync(0xffffffffu, a.hi, o), l = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    ff s = two_sum(a.hi, h);
+    float lo = __fadd_rn(__fadd_rn(a.lo, l), s.lo);
+    a.hi = __fadd_rn(s.hi, lo);
+    a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
+}
+__device__ inline void ff_acc(ff& a, float v) {
+    ff s = two_sum(a.hi, v);
+    float lo = __fadd_rn(a.lo, s.lo);
+    a.hi = __fadd_rn(s.hi, lo);
+    a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
+}
+
 // order-preserving map of a double to uint64 (for atomicMin/atomicMax on doubles)
 __device__ inline unsigned long long dbl_key(double d) {
     unsigned long long u = (unsigned long long)__double_as_longlong(d);

@@ -824,29 +824,6 @@ void launch_split_positions(const d4* xm, int n, float* hi, float* lo, cudaStrea
     if (n > 0) k_split_positions<<<grid_for(n, 256), 256, 0, s>>>(xm, n, hi, lo); note_launch();
 }
 
-struct ff {
-    float hi, lo;
-};
-__device__ inline ff two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return ff{s, e};
-}
-__device__ inline void ff_add_shfl(ff& a, int o) {
-    float h = __shfl_xor_sync(0xffffffffu, a.hi, o), l = __shfl_xor_sync(0xffffffffu, a.lo, o);
-    ff s = two_sum(a.hi, h);
-    float lo = __fadd_rn(__fadd_rn(a.lo, l), s.lo);
-    a.hi = __fadd_rn(s.hi, lo);
-    a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
-}
-__device__ inline void ff_acc(ff& a, float v) {
-    ff s = two_sum(a.hi, v);
-    float lo = __fadd_rn(a.lo, s.lo);
-    a.hi = __fadd_rn(s.hi, lo);
-    a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
-}
-
 // The mixed kernel streams the sink's sources through warp-private tiles filled from
 // consecutive source cells (so small cells do not leave a tile half empty).  dx =
 // (hi_a - hi_b) + (lo_a - lo_b) carries one FP32 rounding relative to |dx| itself, so

@@ -192,6 +192,16 @@ void launch_finish(const double* psi_far, const double* acc_far, const double* p
 // Sec. 7.1: pact[i] = active[perm[i]] != 0 (sorted order) and act[cell] = the cell holds an
 // active particle (from a prefix sum of pact over the cells' particle ranges); ai holds
 // n + 1 ints, scan n ints, scan_tmp scan_tmp_ints(n) ints
+// tidal tensor (Sec. 7.4, tidal.cu): far part from Psi_2^m at the particles (sorted order,
+// [n][6]), near part over the P2P lists (fp32: two-float positions hi/lo), and the
+// combination G (far + near) scattered to the caller's order (active particles only)
+void launch_l2p_tidal(const d4* xm, Cells c, const d4* cen, const int* leaves, int nleaves, int p, const double* F,
+                      double* T, cudaStream_t s);
+void launch_p2p_tidal(const d4* xm, const float* hi, const float* lo, int n, bool fp32, Cells c, const int2* list,
+                      const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* T,
+                      cudaStream_t s);
+void launch_finish_tidal(const double* Tf, const double* Tn, const int* perm, int n, double G,
+                         const unsigned char* pact, double* T, cudaStream_t s);
 // individual accuracy parameters (Sec. 7, opening): scale_sorted[i] *= eps_b[perm[i]] / eps
 void launch_scale_eps(const double* eps_b, const int* perm, int n, double eps, double* scale_sorted, unsigned* status,
                       cudaStream_t s);

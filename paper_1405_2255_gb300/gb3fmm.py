@@ -93,7 +93,7 @@ def load(path: str = LIB_PATH):
     L.fmm_workspace_bytes.argtypes = [vp]
     L.fmm_workspace_bytes.restype = C.c_uint64
     L.fmm_swap_matrix.argtypes = [ci, vp]
-    L.fmm_evaluate_active.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, ci, vp, vp, vp, C.POINTER(fmm_stats)]
+    L.fmm_evaluate_active.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, ci, vp, vp, vp, vp, C.POINTER(fmm_stats)]
     for name in EXPORTS:
         if name not in ("fmm_strerror", "fmm_last_error", "fmm_version", "fmm_default_params",
                         "fmm_footprint_bytes", "fmm_workspace_bytes"):
@@ -182,11 +182,12 @@ class Context:
         return (psi, acc, st.as_dict()) if stats else (psi, acc)
 
     def fmm_evaluate_active(self, x, mu, active=None, G=1.0, psi=None, acc=None, scale=None, stream=None,
-                            stats=False, reuse_tree=False, eps_b=None):
+                            stats=False, reuse_tree=False, eps_b=None, tidal=None):
         """Forces for the active subset (Sec. 7.1): active is a [n] uint8/bool CUDA tensor or None
         (all); psi and acc (allocated here if None) are written for the active particles only.
         reuse_tree: keep the previous evaluation's tree (order, cells, centres) for the new
-        positions.  eps_b: [n] float64 CUDA tensor of individual accuracy parameters (Sec. 7, opening)."""
+        positions.  eps_b: [n] float64 CUDA tensor of individual accuracy parameters (Sec. 7, opening).
+        tidal: True or a [n,6] float64 CUDA tensor: also the tidal tensor (Sec. 7.4), returned last."""
         import torch
         n = mu.shape[0]
         if psi is None:
@@ -194,12 +195,17 @@ class Context:
         if acc is None:
             acc = torch.full((n, 3), float("nan"), dtype=torch.float64, device=mu.device)
         a = None if active is None else (active if active.dtype == torch.uint8 else active.to(torch.uint8))
+        T = None
+        if tidal is not None and tidal is not False:
+            T = tidal if isinstance(tidal, torch.Tensor) else torch.full((n, 6), float("nan"), dtype=torch.float64,
+                                                                         device=mu.device)
         st = fmm_stats() if stats else None
         rc = self.L.fmm_evaluate_active(self.h, n, _ptr(x), _ptr(mu), float(G), _ptr(scale), _ptr(a), _ptr(eps_b),
-                                        1 if reuse_tree else 0, _ptr(psi), _ptr(acc), _stream(stream),
+                                        1 if reuse_tree else 0, _ptr(psi), _ptr(acc), _ptr(T), _stream(stream),
                                         C.byref(st) if st is not None else None)
         _check(rc, self.h)
-        return (psi, acc, st.as_dict()) if stats else (psi, acc)
+        out = (psi, acc) + ((T,) if T is not None else ())
+        return out + (st.as_dict(),) if stats else out
 
     def fmm_evaluate_host(self, x: np.ndarray, mu: np.ndarray, G=1.0, psi=None, acc=None, stream=None, stats=False):
         """Host numpy in and out (the end-to-end call: copies inside)."""

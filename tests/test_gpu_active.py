@@ -191,3 +191,37 @@ def test_individual_eps(g, orc, prec):
     with pytest.raises(g.FMMError):
         ctx.fmm_evaluate_active(xt, mt, eps_b=torch.zeros(8000, dtype=torch.float64, device="cuda:0"))
     ctx.close()
+
+
+def _frob_rel(T, R):
+    return np.linalg.norm(T - R, axis=1) / np.linalg.norm(R, axis=1)
+
+
+@pytest.mark.parametrize("sub", [False, True])
+def test_fp64_tidal_matches_oracle(g, orc, sub):
+    """Sec. 7.4 in FP64 mode: the tidal tensor against the oracle's FMM tidal tensor."""
+    x, mu = inputs.plummer(6000, inputs.BASE_SEED + 120)
+    act = (np.linalg.norm(x, axis=1) < 0.8) if sub else np.ones(6000, bool)
+    kw = dict(p=7, eps=1e-7, leaf_size=16, p2p_c=1.0)
+    ctx = g.Context(precision=g.FMM_PREC_FP64, **kw)
+    psi, acc, T = ctx.fmm_evaluate_active(_dev(x), _dev(mu), _dev(act.astype(np.uint8)), G=1.5, tidal=True)
+    run = orc.fmm(x, mu, G=1.5, active=act, tidal=True, **kw)
+    T = T.cpu().numpy()
+    assert np.max(_frob_rel(T[act], run.tidal[act])) <= PARITY_TOL
+    assert np.isnan(T[~act]).all()
+    ctx.close()
+
+
+def test_mixed_tidal_accuracy(g, orc):
+    """Mixed mode: the tidal tensor against the direct Hessian; trace-free to rounding."""
+    x, mu = inputs.plummer(20000, inputs.BASE_SEED + 121)
+    ctx = g.Context(p=10, eps=1e-7, leaf_size=32, p2p_c=1.0, precision=g.FMM_PREC_MIXED)
+    _, acc, T = ctx.fmm_evaluate_active(_dev(x), _dev(mu), tidal=True)
+    sinks = np.arange(0, 20000, 13)
+    Td = orc.direct_tidal(x, mu, sinks=sinks)
+    T = T.cpu().numpy()
+    e = _frob_rel(T[sinks], Td)
+    assert np.sqrt(np.mean(e ** 2)) < 1e-5 and np.percentile(e, 99) < 1e-4
+    tr = np.abs(T[:, 0] + T[:, 3] + T[:, 5]) / np.linalg.norm(T, axis=1)
+    assert np.percentile(tr, 99) < 1e-4
+    ctx.close()
