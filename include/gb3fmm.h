@@ -83,6 +83,11 @@ typedef struct {
                            matrices of App. A.5 (O(p^3) per pair), n+k <= 1 in FP64;
                            0 = eq. (3b) term by term (O(p^4)).  Same result up to FP32
                            rounding.                                                    */
+    int    adaptive_p;  /* 1: every accepted M2L interaction takes the lowest order q in
+                           [min(3, p), p] whose error estimate E~ (eq. 17 with order q)
+                           meets the criterion (18a,b) (Sec. 7, opening); its M2L computes
+                           F_n for n <= q from M_k, k <= q - n.  0: every interaction at p.
+                           Only with FMM_MAC_A / FMM_MAC_F; fmm_evaluate_noalloc ignores it. */
 } fmm_params;
 
 typedef struct {
@@ -250,6 +255,10 @@ uint64_t fmm_workspace_bytes(fmm_ctx* ctx);
  * pointer may be NULL; counts are in the last stats. */
 int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t* m2l,
                    int64_t* p2p, int64_t* perm, double* scale_sorted);
+
+/* The expansion order of every M2L interaction of the last evaluation, in the order of
+ * fmm_debug_dump's m2l list (HOST out, n_m2l ints): the pair's q with adaptive_p, else p. */
+int fmm_debug_m2l_orders(fmm_ctx* ctx, int32_t* q);
 
 /* Counts and phase times of the last evaluation on ctx (HOST out).  Phase events
  * are recorded on every evaluation; this call waits for the last one to finish. */

@@ -54,7 +54,8 @@ def lib():
 
 class Params(C.Structure):
     _fields_ = [("p", C.c_int), ("eps", C.c_double), ("mac", C.c_int), ("theta_crit", C.c_double),
-                ("leaf_size", C.c_int), ("p2p_c", C.c_double), ("scale_src", C.c_int), ("want_tidal", C.c_int)]
+                ("leaf_size", C.c_int), ("p2p_c", C.c_double), ("scale_src", C.c_int), ("want_tidal", C.c_int),
+                ("adaptive_p", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -77,6 +78,7 @@ def _declare(L):
     L.orc_direct_tidal.argtypes = [C.c_long, _dp, _dp, C.c_double, C.c_long, C.c_void_p, C.c_void_p]
     L.orc_run_tidal.argtypes = [C.c_void_p, _dp]
     L.orc_run_tidal.restype = C.c_int
+    L.orc_run_m2l_orders.argtypes = [C.c_void_p, C.c_void_p]
     L.orc_l2p.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.POINTER(C.c_double), _dp]
     L.orc_power.argtypes = [C.c_int, _dp, _dp, _dp]
     L.orc_direct.argtypes = [C.c_long, _dp, _dp, C.c_double, C.c_long, C.c_void_p, C.c_void_p,
@@ -231,16 +233,18 @@ class Run:
     perm: np.ndarray
     scale: np.ndarray       # per sorted particle
     tidal: np.ndarray = None  # [n,6] (xx, xy, xz, yy, yz, zz) when asked for
+    m2l_q: np.ndarray = None  # order of each M2L interaction (same order as m2l)
 
 
 def fmm(x, mu, G=1.0, p=6, eps=1e-7, mac=MAC_A, theta_crit=0.5, leaf_size=32, p2p_c=1.0,
-        scale=None, keep=True, active=None, eps_b=None, tidal=False):
+        scale=None, keep=True, active=None, eps_b=None, tidal=False, adaptive_p=False):
     """Run the oracle FMM; raises ValueError on invalid input.  active (bool/uint8 [n],
     caller order): forces for that subset only (Sec. 7.1), NaN for the others; eps_b [n]:
     individual accuracy parameters (Sec. 7, opening)."""
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
     mu = np.ascontiguousarray(mu, dtype=np.float64)
-    prm = Params(p, eps, mac, theta_crit, leaf_size, p2p_c, 1 if scale is not None else 0, 1 if tidal else 0)
+    prm = Params(p, eps, mac, theta_crit, leaf_size, p2p_c, 1 if scale is not None else 0, 1 if tidal else 0,
+                 1 if adaptive_p else 0)
     sc = None if scale is None else np.ascontiguousarray(scale, dtype=np.float64)
     act = None if active is None else np.ascontiguousarray(np.asarray(active) != 0, dtype=np.uint8)
     L = lib()
@@ -264,7 +268,7 @@ def fmm_reused(x0, mu0, x, mu, G=1.0, p=6, eps=1e-7, mac=MAC_A, theta_crit=0.5, 
     mu0 = np.ascontiguousarray(mu0, dtype=np.float64)
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
     mu = np.ascontiguousarray(mu, dtype=np.float64)
-    prm = Params(p, eps, mac, theta_crit, leaf_size, p2p_c, 0, 0)
+    prm = Params(p, eps, mac, theta_crit, leaf_size, p2p_c, 0, 0, 0)
     act = None if active is None else np.ascontiguousarray(np.asarray(active) != 0, dtype=np.uint8)
     L = lib()
     h0 = L.orc_fmm_active(len(mu0), x0, mu0, G, C.byref(prm), None, None, None)
@@ -302,7 +306,9 @@ def _collect(L, h, n, keep):
         L.orc_run_perm(h, perm)
         scl = np.zeros(n)
         L.orc_run_scale(h, scl)
-        return Run(psi[:n], acc[:n], stats, ci, cd, m2[:st.n_m2l], pp[:st.n_p2p], perm, scl, tid)
+        q = np.zeros(max(st.n_m2l, 1), dtype=np.int32)
+        L.orc_run_m2l_orders(h, q.ctypes.data)
+        return Run(psi[:n], acc[:n], stats, ci, cd, m2[:st.n_m2l], pp[:st.n_p2p], perm, scl, tid, q[:st.n_m2l])
     return Run(psi[:n], acc[:n], stats, None, None, None, None, None, None, tid)
 
 

@@ -919,13 +919,14 @@ static void cell_geometry(tree_t *t, long ci) { cell_geometry_k(t, ci, 0); }
 /* Dual tree walk (Sec. 2.2.2) and acceptance criteria (eqs. 9, 15-18)        */
 /* ------------------------------------------------------------------------- */
 
-typedef struct { long a, b; } pair_t;
+typedef struct { long a, b; int q; } pair_t;  /* q: the M2L interaction's expansion order */
 typedef struct { pair_t *v; long n, cap; } plist;
-static void push(plist *l, long a, long b)
+static void push_q(plist *l, long a, long b, int q)
 {
     if (l->n == l->cap) { l->cap = l->cap ? 2 * l->cap : 4096; l->v = realloc(l->v, sizeof(pair_t) * l->cap); }
-    l->v[l->n].a = a; l->v[l->n].b = b; ++l->n;
+    l->v[l->n].a = a; l->v[l->n].b = b; l->v[l->n].q = q; ++l->n;
 }
+static void push(plist *l, long a, long b) { push_q(l, a, b, 0); }
 
 enum { MAC_A = 0, MAC_F = 1, MAC_THETA = 2, MAC_EST = 3 };
 
@@ -935,9 +936,26 @@ typedef struct {
     double eps, theta_crit, p2p_thresh;
     const double *P;      /* multipole power [ncells][p+1] (MAC_A/MAC_F) */
     double *binom;        /* C(p, k) */
+    int adaptive;         /* per-interaction order (Sec. 7, opening) */
     plist m2l, p2p;
 } walk_t;
 
+/* E~_{A->B} M_A / r^2 of order q, eqs. (15)-(17), without the division by M_A */
+static double mac_lhs(const walk_t *w, const double *P, double r, double ra, double rb, int q)
+{
+    double sum = 0, cqk = 1.0;  /* C(q, k) */
+    for (int k = 0; k <= q; ++k) {
+        sum += cqk * (P[k] / pow(r, k)) * pow(rb / r, q - k);
+        cqk = cqk * (q - k) / (k + 1);
+    }
+    double mx = ra > rb ? ra : rb;
+    double fac = (ra + rb > 0) ? 8.0 * mx / (ra + rb) : 8.0;
+    (void)w;
+    return fac * sum / (r * r);
+}
+
+/* 0: not accepted; else the order of the accepted M2L interaction: p, or with the adaptive
+ * walk the lowest q in [min(3, p), p] whose estimate of order q passes as well */
 static int accept(const walk_t *w, long A, long B)
 {
     const cell_t *a = &w->t->cells[A], *b = &w->t->cells[B];
@@ -945,9 +963,9 @@ static int accept(const walk_t *w, long A, long B)
     double ra = w->use_com ? a->rho_com : a->rho, rb = w->use_com ? b->rho_com : b->rho;
     double r = dist3(sb, za);
     double theta = (ra + rb) / r;           /* eq. (9) */
-    if (w->mac == MAC_THETA) return theta < w->theta_crit;
+    if (w->mac == MAC_THETA) return theta < w->theta_crit ? w->p : 0;
     if (!(theta < 1.0)) return 0;
-    if (w->mac == MAC_EST) return 1;
+    if (w->mac == MAC_EST) return w->p > 0 ? w->p : 1;
     /* E~_{A->B} M_A / r^2, eqs. (15)-(17), without the division by M_A */
     const double *P = &w->P[(long)A * (w->p + 1)];
     double sum = 0;
@@ -956,7 +974,12 @@ static int accept(const walk_t *w, long A, long B)
     double mx = ra > rb ? ra : rb;
     double fac = (ra + rb > 0) ? 8.0 * mx / (ra + rb) : 8.0;
     double lhs = fac * sum / (r * r);
-    return lhs < w->eps * b->minscale;      /* eqs. (18a) / (18b) */
+    const double rhs = w->eps * b->minscale;
+    if (!(lhs < rhs)) return 0;             /* eqs. (18a) / (18b) */
+    if (w->adaptive)
+        for (int q = w->p < 3 ? w->p : 3; q < w->p; ++q)
+            if (mac_lhs(w, P, r, ra, rb, q) < rhs) return q;
+    return w->p;
 }
 
 static void walk(walk_t *w, long A, long B)
@@ -970,7 +993,8 @@ static void walk(walk_t *w, long A, long B)
             for (long j = 0; j < a->nchild; ++j) walk(w, a->child + i, a->child + j);
         return;
     }
-    if (accept(w, A, B)) { push(&w->m2l, A, B); return; }
+    int q = accept(w, A, B);
+    if (q) { push_q(&w->m2l, A, B, q); return; }
     if (a->leaf && b->leaf) { push(&w->p2p, A, B); return; }
     double ra = w->use_com ? a->rho_com : a->rho, rb = w->use_com ? b->rho_com : b->rho;
     int split_a = (ra >= rb);
@@ -1038,6 +1062,7 @@ typedef struct {
     double p2p_c;     /* direct summation when N_A N_B < p2p_c p^3 */
     int scale_src;    /* 0: low-order FMM estimate, 1: caller-supplied per-particle scale */
     int want_tidal;   /* 1: also the tidal tensor of Sec. 7.4 */
+    int adaptive_p;   /* 1: per-interaction order (Sec. 7, opening) */
 } orc_params;
 
 typedef struct {
@@ -1223,6 +1248,7 @@ static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, con
     /* dual tree walk */
     walk_t w = {0};
     w.t = t; w.p = p; w.mac = prm->mac; w.use_com = 0;
+    w.adaptive = prm->adaptive_p && prm->mac != MAC_THETA;
     w.eps = prm->eps; w.theta_crit = prm->theta_crit;
     w.p2p_thresh = prm->p2p_c * pow((double)p, 3);
     w.P = P;
@@ -1235,9 +1261,9 @@ static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, con
     run->st.n_p2p = w.p2p.n;
 
     /* interactions */
-    for (long i = 0; i < w.m2l.n; ++i) {
+    for (long i = 0; i < w.m2l.n; ++i) {  /* each at its own order q <= p (F_n, n <= q; M_k, k <= q - n) */
         long A = w.m2l.v[i].a, B = w.m2l.v[i].b;
-        m2l(p, &M[A * nco], t->cells[A].s, t->cells[B].s, &F[B * nco]);
+        m2l(w.m2l.v[i].q, &M[A * nco], t->cells[A].s, t->cells[B].s, &F[B * nco]);
     }
     double *ps = calloc(n, sizeof(double)), *ac = calloc(3 * n, sizeof(double));
     long coin = 0, inter = 0;
@@ -1369,6 +1395,10 @@ void orc_run_lists(const orc_run *run, long *m2l /* [n_m2l][2] */, long *p2p /* 
 {
     for (long i = 0; i < run->m2l.n; ++i) { m2l[2 * i] = run->m2l.v[i].a; m2l[2 * i + 1] = run->m2l.v[i].b; }
     for (long i = 0; i < run->p2p.n; ++i) { p2p[2 * i] = run->p2p.v[i].a; p2p[2 * i + 1] = run->p2p.v[i].b; }
+}
+void orc_run_m2l_orders(const orc_run *run, int *q)
+{
+    for (long i = 0; i < run->m2l.n; ++i) q[i] = run->m2l.v[i].q;
 }
 void orc_run_perm(const orc_run *run, long *perm) { memcpy(perm, run->t.perm, sizeof(long) * run->t.n); }
 void orc_run_scale(const orc_run *run, double *scale_sorted)

@@ -74,7 +74,7 @@ struct fmm_ctx {
     Buf first, count, child, nchild, parent, level, sr, cr, mass, minscale;
     Buf split_nchild, split_oct, split_offs, scan_tmp, leaves, leaf_flag, leaf_pos, rad_tmp;
     // expansions
-    Buf M, F, Pw, binom, M1, F1, Ff;
+    Buf M, F, Pw, binom, pascal, M1, F1, Ff;
     // walk
     Buf front0, front1, m2l, p2p, sort_tmp, m2l_tmp, p2p_tmp, seg_start, seg_end, est_m2l, est_p2p, m2l_seg_start, m2l_seg_end;
     long long front_cap = 0, m2l_cap = 0, p2p_cap = 0, est_m2l_cap = 0, est_p2p_cap = 0;
@@ -101,7 +101,7 @@ struct fmm_ctx {
         return {&hx, &hmu, &hpsi, &hacc, &bounds, &status, &counters, &coin, &dtotal, &keys, &keys_alt, &idx,
                 &idx_alt, &rtmp, &xm, &perm, &xhi, &xlo, &first, &count, &child, &nchild, &parent, &level, &sr,
                 &cr, &mass, &minscale, &split_nchild, &split_oct, &split_offs, &scan_tmp, &leaves, &leaf_flag,
-                &leaf_pos, &rad_tmp, &M, &F, &Pw, &binom, &M1, &F1, &Ff, &front0, &front1, &m2l, &p2p,
+                &leaf_pos, &rad_tmp, &M, &F, &Pw, &binom, &pascal, &M1, &F1, &Ff, &front0, &front1, &m2l, &p2p,
                 &sort_tmp, &m2l_tmp, &p2p_tmp, &seg_start, &seg_end, &est_m2l, &est_p2p, &m2l_seg_start,
                 &m2l_seg_end, &psi_far, &acc_far, &psi_near, &acc_near, &scale_sorted, &sys_off, &sys_G,
                 &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan, &tid_far, &tid_near};
@@ -165,6 +165,7 @@ static int check_params(const fmm_params* p) {
     if (p->precision != FMM_PREC_FP64 && p->precision != FMM_PREC_MIXED) return FMM_E_INVALID;
     if (p->scale_src != FMM_SCALE_ESTIMATE && p->scale_src != FMM_SCALE_CALLER) return FMM_E_INVALID;
     if (p->m2l_rot != 0 && p->m2l_rot != 1) return FMM_E_INVALID;
+    if (p->adaptive_p != 0 && p->adaptive_p != 1) return FMM_E_INVALID;
     return 0;
 }
 
@@ -373,11 +374,12 @@ static int run_walk(fmm_ctx* ctx, WalkParams wp, Buf& m2l, long long& m2l_cap, B
     return fail(ctx, FMM_E_OVERFLOW, msg);
 }
 
-static int sort_and_segment(fmm_ctx* ctx, Buf& list, long long npairs, Buf& seg_start, Buf& seg_end, cudaStream_t s) {
+static int sort_and_segment(fmm_ctx* ctx, Buf& list, long long npairs, Buf& seg_start, Buf& seg_end, cudaStream_t s,
+                            bool wide = false) {
     TRY(ensure(ctx->sort_tmp, list_sort_tmp_bytes(npairs)));
     TRY(ensure(seg_start, sizeof(int) * ctx->ncells));
     TRY(ensure(seg_end, sizeof(int) * ctx->ncells));
-    sort_pairs_by_sink(P<int2>(list), npairs, ctx->ncells, ctx->sort_tmp.p, s);
+    sort_pairs_by_sink(P<int2>(list), npairs, ctx->ncells, ctx->sort_tmp.p, s, wide);
     launch_segments(P<int2>(list), npairs, ctx->ncells, P<int>(seg_start), P<int>(seg_end), s);
     return 0;
 }
@@ -572,8 +574,22 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     wp.P = P<double>(ctx->Pw);
     wp.binom = P<double>(ctx->binom);
     wp.use_com = 0;
+    wp.adaptive = prm.adaptive_p && prm.mac != FMM_MAC_THETA;
+    wp.p_lo = prm.p < 3 ? prm.p : 3;
+    wp.pascal = nullptr;
+    if (wp.adaptive) {
+        TRY(ensure(ctx->pascal, sizeof(double) * (kMaxP + 1) * (kMaxP + 1)));
+        double pt[(kMaxP + 1) * (kMaxP + 1)] = {};
+        for (int q = 0; q <= kMaxP; ++q) {
+            pt[q * (kMaxP + 1)] = 1.0;
+            for (int k = 1; k <= q; ++k) pt[q * (kMaxP + 1) + k] = pt[q * (kMaxP + 1) + k - 1] * (q - k + 1) / k;
+        }
+        CU(cudaMemcpyAsync(ctx->pascal.p, pt, sizeof pt, cudaMemcpyHostToDevice, s));
+        CU(cudaStreamSynchronize(s));  // pt lives on this stack frame
+        wp.pascal = P<double>(ctx->pascal);
+    }
     TRY(run_walk(ctx, wp, ctx->m2l, ctx->m2l_cap, ctx->p2p, ctx->p2p_cap, &ctx->n_m2l, &ctx->n_p2p, s));
-    TRY(sort_and_segment(ctx, ctx->m2l, ctx->n_m2l, ctx->m2l_seg_start, ctx->m2l_seg_end, s));
+    TRY(sort_and_segment(ctx, ctx->m2l, ctx->n_m2l, ctx->m2l_seg_start, ctx->m2l_seg_end, s, wp.adaptive != 0));
     if (timing) CU(cudaEventRecord(ctx->ev[EV_WALK], s));
 
     // A9: M2L
@@ -581,7 +597,8 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     if (split) {
         TRY(ensure(ctx->m2l_tmp, m2l_split_tmp_bytes(nc, prm.p, ctx->n_m2l)));
         launch_m2l_split(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc,
-                         c.sr, P<double>(ctx->M), prm.p, P<double>(ctx->F), prm.m2l_rot != 0, s);
+                         c.sr, P<double>(ctx->M), prm.p, P<double>(ctx->F), prm.m2l_rot != 0, s, wp.adaptive != 0,
+                         ctx->n_m2l);
     } else {
         TRY(ensure(ctx->m2l_tmp, m2l_tmp_bytes(nc, prm.p)));
         launch_m2l(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc, c.sr,
@@ -685,6 +702,7 @@ void fmm_default_params(fmm_params* out) {
     out->p2p_two_float = 1;
     out->m2l_split = 1;
     out->m2l_rot = 1;
+    out->adaptive_p = 0;
 }
 
 int fmm_create(fmm_ctx** out, const fmm_params* params, int device) {
@@ -838,6 +856,17 @@ int fmm_evaluate_batch(fmm_ctx* ctx, int nsys, const int64_t* offsets, const dou
     return 0;
 }
 
+int fmm_debug_m2l_orders(fmm_ctx* ctx, int32_t* q) {
+    if (!ctx || !q) return FMM_E_INVALID;
+    const long long cnt = ctx->n_m2l;
+    if (cnt <= 0) return 0;
+    CU(cudaDeviceSynchronize());
+    std::vector<int2> v(cnt);
+    CU(cudaMemcpy(v.data(), ctx->m2l.p, sizeof(int2) * cnt, cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < cnt; ++i) q[i] = m2l_order(v[i].x, ctx->prm.p);
+    return 0;
+}
+
 int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t* m2l, int64_t* p2p, int64_t* perm,
                    double* scale_sorted) {
     if (!ctx) return FMM_E_INVALID;
@@ -879,7 +908,7 @@ int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t*
         std::vector<int2> v(cnt);
         GB3_CUDA_TRY(cudaMemcpy(v.data(), b.p, sizeof(int2) * cnt, cudaMemcpyDeviceToHost));
         for (long long i = 0; i < cnt; ++i) {
-            out[2 * i] = v[i].x;
+            out[2 * i] = m2l_src(v[i].x);
             out[2 * i + 1] = v[i].y;
         }
         return 0;

@@ -58,24 +58,25 @@ __global__ void __launch_bounds__(64) k_m2l(const int2* __restrict__ list, const
             const int nb = min(NB, e1 - eb);
             // conj(M) of the batch
             for (int b = 0; b < nb; ++b) {
-                const cd* src = Mc + (size_t)list[eb + b].x * nco;
+                const cd* src = Mc + (size_t)m2l_src(list[eb + b].x) * nco;
                 for (int i = lane; i < nco; i += 32) Mb[b * nco + i] = src[i];
             }
             // Theta of the batch
             {
                 const int b = lane / LPP, sub = lane % LPP;
                 if (b < nb) {
-                    const d4 zA = cen[list[eb + b].x];
+                    const d4 zA = cen[m2l_src(list[eb + b].x)];
                     const double x = sB.x - zA.x, y = sB.y - zA.y, z = sB.z - zA.z;
                     for (int m = sub; m <= p; m += LPP) theta_column(p, m, x, y, z, T + b * nco);
                 }
             }
             __syncwarp();
             for (int b = 0; b < nb; ++b) {
+                const int pb = m2l_order(list[eb + b].x, p);  // the pair's order (adaptive walk) or p
 #pragma unroll
                 for (int q = 0; q < MAXQ; ++q)
-                    if (q < cnt)
-                        acc[q] = acc[q] + contract(p, sched.n[lane][q], sched.m[lane][q], Mb + b * nco, T + b * nco);
+                    if (q < cnt && sched.n[lane][q] <= pb)
+                        acc[q] = acc[q] + contract(pb, sched.n[lane][q], sched.m[lane][q], Mb + b * nco, T + b * nco);
             }
             __syncwarp();
         }
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
         if (!(sigma > 0)) {  // radius 0: half the closest source distance (over the whole list)
             double rmin = INFINITY;
             for (int e = s0 + lane; e < s1; e += 32) {
-                const d4 zA = cen[list[e].x];
+                const d4 zA = cen[m2l_src(list[e].x)];
                 const double dx = sB.x - zA.x, dy = sB.y - zA.y, dz = sB.z - zA.z;
                 rmin = fmin(rmin, sqrt(dx * dx + dy * dy + dz * dz));
             }
@@ -407,11 +408,13 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
         for (int eb = e0; eb < e1; eb += kRB) {
             const int nb = min(kRB, e1 - eb);
             if (lane < nb) {
-                const d4 zA = cen[list[eb + lane].x];
+                const int xe = list[eb + lane].x;
+                const d4 zA = cen[m2l_src(xe)];
                 const double x = sB.x - zA.x, y = sB.y - zA.y, z = sB.z - zA.z;
                 const double rinv = rsqrt(x * x + y * y + z * z);
                 pi[lane] = PairInfo{x, y, z, rinv};
-                unit[lane] = make_float4((float)(x * rinv), (float)(y * rinv), (float)(z * rinv), 0.f);
+                // .w: the pair's order (adaptive walk) or p
+                unit[lane] = make_float4((float)(x * rinv), (float)(y * rinv), (float)(z * rinv), (float)m2l_order(xe, p));
                 const float ta = (float)(zA.w * rinv), tb = (float)(sigma * rinv);
                 float a = 1.f, b = 1.f;
                 for (int k = 0; k <= p + 1; ++k) {
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
             __syncwarp();
             // scaled FP32 moments and FP64 low orders of the batch's sources
             for (int b = 0; b < nb; ++b) {
-                const int A = list[eb + b].x;
+                const int A = m2l_src(list[eb + b].x);
                 const float2* src = Mf + (size_t)A * nco;
                 const float* ta = thA + b * (kMaxP + 2);
                 for (int i = lane; i < nco; i += 32) {
@@ -470,8 +473,9 @@ __global__ void __launch_bounds__(32, 16) k_m2l_rounds(const int2* __restrict__ 
                     const int b = act ? u / (n + 1) : 0, m = act ? u % (n + 1) : 0;
                     const float2* X = Mh + b * nco;
                     const float2* Y = Th + b * nco;
+                    const int kmax = (int)unit[b].w - n;  // k <= q - n for a pair of order q
                     float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
-                    for (int k = kmin; k <= p - n; ++k)
+                    for (int k = kmin; k <= kmax; ++k)
                         m2l_row(k, X + k * k, Y + (n + k) * (n + k) + n + m, a0, a1, a2, a3);
                     if (act) {
                         const float sc = thB[b * (kMaxP + 2) + n + 1];
@@ -542,7 +546,8 @@ size_t m2l_split_tmp_bytes(int ncells, int p, long long npairs) {
     size_t n = (size_t)(ncells > 0 ? ncells : 1);
     size_t items = (size_t)(npairs / kChunk) + n + 1;
     return m2l_tmp_bytes(ncells, p) + n * (size_t)ncoef(p) * sizeof(float2) + n * kN64 * sizeof(cd) +
-           2 * n * sizeof(int) + scan_tmp_ints(n) * sizeof(int) + items * (size_t)ncoef(p) * sizeof(double) + 2048;
+           2 * n * sizeof(int) + scan_tmp_ints(n) * sizeof(int) + items * (size_t)ncoef(p) * sizeof(double) +
+           m2l_rot_group_bytes((long long)items) + 4096;
 }
 
 // chunks per sorted sink
@@ -556,23 +561,27 @@ __global__ void k_item_counts(const int* __restrict__ order, const int* __restri
 }
 
 // F_B = sum of its chunks' partial expansions, in chunk order
+// item_q (nullable): the order of item w's partial expansion (its coefficients of higher
+// order are not written and count as zero)
 __global__ void k_m2l_reduce(const int* __restrict__ order, const int* __restrict__ item_start,
                              const int* __restrict__ cnt, const unsigned* __restrict__ work, int ncells, int nco,
-                             const double* __restrict__ part, double* __restrict__ F) {
+                             const double* __restrict__ part, double* __restrict__ F, const int* __restrict__ item_q) {
     const unsigned nsinks = work[1];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)ncells * nco;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t / nco), j = (int)(t % nco);
         if ((unsigned)i >= nsinks) continue;
         const int a = item_start[i], b = a + cnt[i];
+        const int nj = (int)sqrtf((float)j);
         double v = 0.0;
-        for (int w = a; w < b; ++w) v += part[(size_t)w * nco + j];
+        for (int w = a; w < b; ++w)
+            if (!item_q || nj <= item_q[w]) v += part[(size_t)w * nco + j];
         F[(size_t)order[i] * nco + j] = v;
     }
 }
 
 void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells, const d4* cen,
-                      const double* M, int p, double* F, bool rot, cudaStream_t s) {
+                      const double* M, int p, double* F, bool rot, cudaStream_t s, bool adaptive, long long npairs) {
     if (ncells <= 0) return;
     if (p <= kJ64) {  // nothing to split
         launch_m2l(list, seg_start, seg_end, tmp, ncells, cen, M, p, F, s);
@@ -593,6 +602,9 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     int* item_start = cnt + ncells;
     int* stmp = item_start + ncells;
     double* part = (double*)(((uintptr_t)(stmp + scan_tmp_ints(ncells)) + 255) & ~(uintptr_t)255);
+    const long long items_cap = npairs / kChunk + ncells + 1;
+    void* gtmp = (void*)(((uintptr_t)(part + (size_t)items_cap * ncoef(p)) + 255) & ~(uintptr_t)255);
+    const int* item_q = nullptr;
     cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
     k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
     int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 0, 56, s);
@@ -600,13 +612,14 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     k_item_counts<<<grid_for(ncells, 256), 256, 0, s>>>(order, seg_start, seg_end, ncells, cnt); note_launch();
     scan_exclusive_i32(cnt, item_start, ncells, (int*)(work + 2), stmp, s);
     if (rot && m2l_rot_supported(p)) {
-        launch_m2l_rot(list, seg_start, seg_end, order, item_start, work, cen, M, ncells, p, (float*)Mf, M64, part, s);
+        item_q = launch_m2l_rot(list, seg_start, seg_end, order, item_start, work, cen, M, ncells, p, (float*)Mf, M64,
+                                part, adaptive, gtmp, items_cap, s);
     } else {
         k_prep_split<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mf, M64); note_launch();
         m2l_rounds_launch<kRoundsBatch>(list, seg_start, seg_end, order, item_start, work, cen, Mf, M64, p, part, s);
     }
     k_m2l_reduce<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(order, item_start, cnt, work, ncells,
-                                                                            ncoef(p), part, F);
+                                                                            ncoef(p), part, F, item_q);
     note_launch();
 }
 

@@ -99,7 +99,21 @@ struct WalkParams {
     const double* P;    // multipole power [nc][p+1]
     const double* binom;// device C(p,k)
     int use_com;        // radii/centres from cr (estimator) instead of sr
+    // per-interaction order (Sec. 7, opening): an accepted pair takes the lowest q in
+    // [p_lo, p] for which the criterion holds with E~ of order q; pascal[q * (kMaxP + 1) + k]
+    // = C(q, k)
+    int adaptive, p_lo;
+    const double* pascal;
 };
+// M2L list entries of an adaptive-order walk carry the pair's order q in the top bits of
+// the source index: x = source | (q << kM2LOrderShift); q = 0 stands for the global p
+constexpr int kM2LOrderShift = 27;
+constexpr int kM2LSrcMask = (1 << kM2LOrderShift) - 1;
+__host__ __device__ inline int m2l_src(int x) { return x & kM2LSrcMask; }
+__host__ __device__ inline int m2l_order(int x, int p) {
+    const int q = (int)((unsigned)x >> kM2LOrderShift);
+    return q ? q : p;
+}
 constexpr int kMacEstimate = 3;  // theta < 1 only (low-order estimate, Sec. 5.3.2)
 
 struct WalkBuffers {
@@ -117,7 +131,8 @@ void launch_walk_step(Cells c, WalkParams wp, const int2* front_in, long long nf
                       WalkBuffers wb, cudaStream_t s);
 // sort a pair list by (sink, source), then mark per-sink segments [seg_start, seg_end)
 size_t list_sort_tmp_bytes(long long npairs);
-void sort_pairs_by_sink(int2* list, long long npairs, int ncells, void* tmp, cudaStream_t s);
+// wide: the first entries use all 32 bits (an adaptive-order M2L list)
+void sort_pairs_by_sink(int2* list, long long npairs, int ncells, void* tmp, cudaStream_t s, bool wide = false);
 void launch_segments(const int2* list, long long npairs, int ncells, int* seg_start, int* seg_end,
                      cudaStream_t s);
 
@@ -129,8 +144,11 @@ void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void
 // directly (eq. 3b) or, when rot is set and m2l_rot_supported(p), through rotations into
 // the interaction's z frame (App. A.5, m2l_rot.cu)
 size_t m2l_split_tmp_bytes(int ncells, int p, long long npairs);
+// adaptive: the list comes from an adaptive-order walk (pairs carry their orders);
+// npairs: the list's length (bounds the work items)
 void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end, void* tmp, int ncells,
-                      const d4* cen, const double* M, int p, double* F, bool rot, cudaStream_t s);
+                      const d4* cen, const double* M, int p, double* F, bool rot, cudaStream_t s,
+                      bool adaptive = false, long long npairs = 0);
 // M2L pairs per work item of the mixed-mode M2L: each sink's list is cut into chunks of
 // this many pairs from its start, summed separately and then added in chunk order
 constexpr int kM2LChunk = 32;
@@ -139,9 +157,14 @@ bool m2l_rot_supported(int p);
 // sinks in `order` (work[1] of them), items from item_start, work[0] the item counter and
 // work[2] the number of items; Mt (ncells x (p+1)^2 floats) and M64 (ncells x 9) are scratch;
 // part receives one expansion per item
-void launch_m2l_rot(const int2* list, const int* seg_start, const int* seg_end, const int* order,
-                    const int* item_start, unsigned* work, const d4* cen, const double* M, int ncells, int p,
-                    float* Mt, cd* M64, double* part, cudaStream_t s);
+// adaptive: the items are grouped by the largest order of their pairs and each group runs
+// the kernel of that order (gtmp: m2l_rot_group_bytes(items_cap) bytes); returns the
+// per-item orders (device, nullptr without adaptive) for the reduction
+const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg_end, const int* order,
+                          const int* item_start, unsigned* work, const d4* cen, const double* M, int ncells, int p,
+                          float* Mt, cd* M64, double* part, bool adaptive, void* gtmp, long long items_cap,
+                          cudaStream_t s);
+size_t m2l_rot_group_bytes(long long items_cap);
 void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F,
                       cudaStream_t s);
 // L2P (eqs. 3a, 7) for every particle of every leaf: psi_far, acc_far (sorted order)

@@ -35,52 +35,154 @@ __global__ void k_prep_rot(const double* __restrict__ M, const d4* __restrict__ 
 
 }  // namespace
 
-extern template void rot_launch<3>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<4>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<5>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<6>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<7>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<8>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<9>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<10>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<11>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<12>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<13>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<14>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<15>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
-extern template void rot_launch<16>(const int2*, const int*, const int*, const int*, const int*, unsigned*, const d4*,
-                             const float*, const cd*, double*, cudaStream_t);
+extern template void rot_launch<3>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<4>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<5>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<6>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<7>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<8>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<9>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<10>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<11>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<12>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<13>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<14>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<15>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<16>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
+                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
+                                       unsigned*, int, int, cudaStream_t);
 
 bool m2l_rot_supported(int p) { return p >= 3 && p <= kRotMaxP; }
 
-void launch_m2l_rot(const int2* list, const int* seg_start, const int* seg_end, const int* order,
-                    const int* item_start, unsigned* work, const d4* cen, const double* M, int ncells, int p,
-                    float* Mt, cd* M64, double* part, cudaStream_t s) {
-    k_prep_rot<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mt, M64);
-    note_launch();
-#define GB3_ROT(PP) \
-    case PP: rot_launch<PP>(list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part, s); break;
-    switch (p) {
-        GB3_ROT(3) GB3_ROT(4) GB3_ROT(5) GB3_ROT(6) GB3_ROT(7) GB3_ROT(8) GB3_ROT(9) GB3_ROT(10) GB3_ROT(11)
-        GB3_ROT(12) GB3_ROT(13) GB3_ROT(14) GB3_ROT(15) GB3_ROT(16)
-        default: break;
+namespace {
+// item w (of the sorted sinks' chunks): the largest order of its pairs; key = (q << 32) | w
+__global__ void k_item_qmax(const int2* __restrict__ list, const int* __restrict__ seg_start,
+                            const int* __restrict__ seg_end, const int* __restrict__ order,
+                            const int* __restrict__ item_start, const unsigned* __restrict__ work, int p,
+                            uint64_t* __restrict__ keys, int* __restrict__ vals, int* __restrict__ item_q,
+                            unsigned* __restrict__ qcount, unsigned cap) {
+    const unsigned nitems = work[2], nsinks = work[1];
+    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < cap; w += gridDim.x * blockDim.x) {
+        if (w >= nitems) {  // unused slots sort last
+            keys[w] = ~0ull;
+            vals[w] = 0;
+            continue;
+        }
+        int lo_i = 0, hi_i = (int)nsinks - 1;
+        while (lo_i < hi_i) {
+            const int mid = (lo_i + hi_i + 1) >> 1;
+            if ((unsigned)item_start[mid] <= w) lo_i = mid;
+            else hi_i = mid - 1;
+        }
+        const int B = order[lo_i];
+        const int e0 = seg_start[B] + (int)(w - (unsigned)item_start[lo_i]) * kM2LChunk;
+        const int e1 = min(e0 + kM2LChunk, seg_end[B]);
+        int q = 0;
+        for (int e = e0; e < e1; ++e) q = max(q, m2l_order(list[e].x, p));
+        item_q[w] = q;
+        keys[w] = ((uint64_t)(unsigned)q << 32) | w;
+        vals[w] = 0;
+        atomicAdd(&qcount[q], 1u);
     }
-#undef GB3_ROT
+}
+// goff[q] = number of items of order < q (q = 0 .. kMaxP + 1); ilist[k] = item of sorted key k
+__global__ void k_item_groups(const unsigned* __restrict__ qcount, unsigned* __restrict__ goff,
+                              const uint64_t* __restrict__ keys, const unsigned* __restrict__ work,
+                              int* __restrict__ ilist) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned a = 0;
+        for (int q = 0; q <= kMaxP + 1; ++q) {
+            goff[q] = a;
+            if (q <= kMaxP) a += qcount[q];
+        }
+    }
+    const unsigned nitems = work[2];
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < nitems; k += gridDim.x * blockDim.x)
+        ilist[k] = (int)(keys[k] & 0xffffffffu);
+}
+}  // namespace
+
+size_t m2l_rot_group_bytes(long long items_cap) {
+    const size_t n = (size_t)(items_cap > 0 ? items_cap : 1);
+    return n * (2 * sizeof(uint64_t) + 4 * sizeof(int)) + radix_tmp_ints((long long)n) * sizeof(int) +
+           4 * (kMaxP + 2) * sizeof(unsigned) + 1024;
 }
 
+const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg_end, const int* order,
+                          const int* item_start, unsigned* work, const d4* cen, const double* M, int ncells, int p,
+                          float* Mt, cd* M64, double* part, bool adaptive, void* gtmp, long long items_cap,
+                          cudaStream_t s) {
+    k_prep_rot<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mt, M64);
+    note_launch();
+    const int nco = ncoef(p);
+#define GB3_ROT(PP)                                                                                      \
+    case PP:                                                                                             \
+        rot_launch<PP>(list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part, il, go, gq, ctr, \
+                       nco, adapt, s);                                                                   \
+        break;
+    auto launch_p = [&](int q, const int* il, const unsigned* go, int gq, unsigned* ctr, int adapt) {
+        switch (q) {
+            GB3_ROT(3) GB3_ROT(4) GB3_ROT(5) GB3_ROT(6) GB3_ROT(7) GB3_ROT(8) GB3_ROT(9) GB3_ROT(10) GB3_ROT(11)
+            GB3_ROT(12) GB3_ROT(13) GB3_ROT(14) GB3_ROT(15) GB3_ROT(16)
+            default: break;
+        }
+    };
+#undef GB3_ROT
+    if (!adaptive) {
+        // every item at p: the whole item range, counted by work[0]; the item count is on the
+        // device (work[2]), so the kernel reads it there
+        launch_p(p, nullptr, nullptr, 0, work, 0);
+        return nullptr;
+    }
+    // group the items by the largest order of their pairs; each group runs its own kernel
+    const size_t cap = (size_t)(items_cap > 0 ? items_cap : 1);
+    uint64_t* k0 = (uint64_t*)gtmp;
+    uint64_t* k1 = k0 + cap;
+    int* v0 = (int*)(k1 + cap);
+    int* v1 = v0 + cap;
+    int* item_q = v1 + cap;
+    int* ilist = item_q + cap;
+    unsigned* qcount = (unsigned*)(ilist + cap);
+    unsigned* goff = qcount + (kMaxP + 2);
+    unsigned* ctr = goff + (kMaxP + 2);
+    int* rtmp = (int*)(ctr + (kMaxP + 2));
+    cudaMemsetAsync(qcount, 0, 3 * (kMaxP + 2) * sizeof(unsigned), s);
+    k_item_qmax<<<grid_for(items_cap, 256), 256, 0, s>>>(list, seg_start, seg_end, order, item_start, work, p, k0, v0,
+                                                          item_q, qcount, (unsigned)cap);
+    note_launch();
+    // the items are at most items_cap; keys past work[2] are never read
+    const int flip = radix_sort_pairs_bits(k0, v0, k1, v1, items_cap, rtmp, 32, 40, s);
+    k_item_groups<<<grid_for(items_cap, 256), 256, 0, s>>>(qcount, goff, flip ? k1 : k0, work, ilist);
+    note_launch();
+    for (int q = (p < 3 ? p : 3); q <= p; ++q) launch_p(q, ilist, goff, q, ctr + q, 1);
+    return item_q;
+}
 }  // namespace gb3
 
 extern "C" int fmm_swap_matrix(int n, double* B) {

@@ -226,24 +226,28 @@ __host__ __device__ __forceinline__ void fwd_all(float* S, const float2* cw, con
     ((fwd_order<P, K>(S, cw, cu, tk), tk *= tA, order_sync<K + 1>()), ...);
 }
 
-// z-axis M2L for column m = M (SG = +1: real parts, -1: imaginary parts), in place
-template <int P, int M, int SG, int N, int... K>
-__host__ __device__ __forceinline__ void zm2l_out(float* S, const float* x, iseq<K...>) {
+// z-axis M2L for column m = M (SG = +1: real parts, -1: imaginary parts), in place.
+// MASK: the lane's pair has its own order q <= P (adaptive walk): only terms n + k <= q
+template <int P, int M, int SG, bool MASK, int N, int... K>
+__host__ __device__ __forceinline__ void zm2l_out(float* S, const float* x, int q, iseq<K...>) {
     if constexpr (N >= M && N <= P - M) {
         float acc = 0.f;
-        ((K >= M && K <= P - N && N + K > kRotJ64 ? (void)(acc = fmaf(kZ<N, K, M>, x[K], acc)) : (void)0), ...);
+        ((K >= M && K <= P - N && N + K > kRotJ64
+              ? (void)(acc = fmaf(kZ<N, K, M>, (!MASK || N + K <= q) ? x[K] : 0.f, acc))
+              : (void)0),
+         ...);
         S[(N * N + N + SG * M) * kPad] = acc;
     }
 }
-template <int P, int M, int SG, int... I>
-__host__ __device__ __forceinline__ void zm2l_col(float* S, iseq<I...>) {
+template <int P, int M, int SG, bool MASK, int... I>
+__host__ __device__ __forceinline__ void zm2l_col(float* S, int q, iseq<I...>) {
     float x[P + 1];
     ((I >= M && I <= P - M ? (void)(x[I] = S[(I * I + I + SG * M) * kPad]) : (void)0), ...);
-    (zm2l_out<P, M, SG, I>(S, x, upto<P>{}), ...);
+    (zm2l_out<P, M, SG, MASK, I>(S, x, q, upto<P>{}), ...);
 }
-template <int P, int... M>
-__host__ __device__ __forceinline__ void zm2l_all(float* S, iseq<M...>) {
-    ((zm2l_col<P, M, 1>(S, upto<P>{}), (M >= 1 ? zm2l_col<P, M, -1>(S, upto<P>{}) : (void)0)), ...);
+template <int P, bool MASK, int... M>
+__host__ __device__ __forceinline__ void zm2l_all(float* S, int q, iseq<M...>) {
+    ((zm2l_col<P, M, 1, MASK>(S, q, upto<P>{}), (M >= 1 ? zm2l_col<P, M, -1, MASK>(S, q, upto<P>{}) : (void)0)), ...);
 }
 
 // backward: rotated local coefficients of order N (entries |m| <= min(N, P-N)) -> original
@@ -311,13 +315,18 @@ constexpr int rot_warps() {
     return imin(8, imax(1, (227 * 1024) / rot_warp_bytes<P>()));
 }
 
-// One warp per work item: up to kM2LChunk pairs of one sink, lane = pair.
+// One warp per work item: up to kM2LChunk pairs of one sink, lane = pair.  The items are
+// ilist[goff[gq] .. goff[gq + 1]) (ilist == nullptr: 0 .. work[2]), taken from *counter;
+// item w's partial expansion goes to part + w * nco_out, nco_out = (p+1)^2 of the global order
+// p >= P, which is also the row length of Mt.  adapt: the pairs carry their own
+// orders q <= P (adaptive walk) and each lane keeps only the terms n + k <= q of its pair.
 template <int P>
 __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
     k_m2l_rot(const int2* __restrict__ list, const int* __restrict__ seg_start, const int* __restrict__ seg_end,
               const int* __restrict__ order, const int* __restrict__ item_start, unsigned* __restrict__ work,
               const d4* __restrict__ cen, const float* __restrict__ Mt, const cd* __restrict__ M64g,
-              double* __restrict__ part) {
+              double* __restrict__ part, const int* __restrict__ ilist, const unsigned* __restrict__ goff, int gq,
+              unsigned* __restrict__ counter, int nco_out, int adapt) {
     constexpr int NCO = (P + 1) * (P + 1), W = rot_warps<P>();
     extern __shared__ __align__(16) unsigned char sm_raw[];
     __shared__ unsigned s_item;
@@ -327,16 +336,17 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
     double* pws = (double*)(base + ((NCO * kPad * 4 + 15) & ~15));    // sigma^-n, n <= P+1
     cd* lowF = (cd*)(pws + P + 2);                                    // FP64 outputs (n <= kRotJ64, m >= 0)
     float* Sl = S + lane;
-    const unsigned nitems = work[2], nsinks = work[1];
+    const unsigned nsinks = work[1];
+    const unsigned lbase = ilist ? goff[gq] : 0u, nlist = ilist ? goff[gq + 1] - goff[gq] : work[2];
     for (;;) {
-        // the block takes W consecutive items, one per warp (every warp runs every barrier)
-        if (threadIdx.x == 0) s_item = atomicAdd(work, (unsigned)W);
+        // the block takes W consecutive list entries, one per warp (every warp runs every barrier)
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, (unsigned)W);
         __syncthreads();
         const unsigned w0 = s_item;
         __syncthreads();
-        if (w0 >= nitems) break;
-        const unsigned w = w0 + warp;
-        const bool has = w < nitems;
+        if (w0 >= nlist) break;
+        const bool has = w0 + warp < nlist;
+        const unsigned w = has ? (ilist ? (unsigned)ilist[lbase + w0 + warp] : w0 + warp) : 0u;
         int e0 = 0, e1 = 0, s0 = 0, s1 = 0;
         d4 sB = mk4(0.0, 0.0, 0.0, 1.0);
         if (has) {
@@ -357,7 +367,7 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
         if (!(sigma > 0)) {  // radius 0: half the closest source distance (over the whole list)
             double rmin = INFINITY;
             for (int e = s0 + lane; e < s1; e += 32) {
-                const d4 zA = cen[list[e].x];
+                const d4 zA = cen[m2l_src(list[e].x)];
                 const double dx = sB.x - zA.x, dy = sB.y - zA.y, dz = sB.z - zA.z;
                 rmin = fmin(rmin, sqrt(dx * dx + dy * dy + dz * dz));
             }
@@ -366,7 +376,9 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
         // the lane's pair: rotation phases e^{-i alpha}, e^{-i beta} and the scale factors
         const int e = e0 + lane;
         const bool act = e < e1;
-        const int A = act ? list[e].x : -1;
+        const int xe = act ? list[e].x : 0;
+        const int A = act ? m2l_src(xe) : -1;
+        const int qlane = act ? m2l_order(xe, P) : P;
         float tA = 0.f, tB = 0.f;
         float2 wv = make_float2(1.f, 0.f), uv = make_float2(1.f, 0.f);
         if (act) {  // FP64 differences, then FP32 (the quantities feed FP32 arithmetic only)
@@ -393,7 +405,7 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
         // by asynchronous copies that complete while the FP64 terms below are summed
         for (int b = 0; b < 32; ++b) {
             const int Ab = __shfl_sync(0xffffffffu, A, b);
-            const float* src = Mt + (size_t)(Ab < 0 ? 0 : Ab) * NCO;
+            const float* src = Mt + (size_t)(Ab < 0 ? 0 : Ab) * nco_out;  // rows of the global order
             const unsigned nbytes = Ab >= 0 ? 4u : 0u;  // 0: zero fill
             for (int c = lane; c < NCO; c += 32) rot_cp_async4(S + c * kPad + b, src + c, nbytes);
         }
@@ -439,13 +451,14 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
         __syncthreads();
         fwd_all<P>(Sl, cw, cu, tA, upto<P>{});
         __syncthreads();
-        zm2l_all<P>(Sl, upto<P / 2>{});
+        if (adapt) zm2l_all<P, true>(Sl, qlane, upto<P / 2>{});
+        else zm2l_all<P, false>(Sl, P, upto<P / 2>{});
         __syncthreads();
         bwd_all<P>(Sl, cw, cu, tB, upto<P>{});
         warp_pow_table(1.0 / sigma, P + 1, lane, pws);
         __syncwarp();
         if (has) {
-            double* out = part + (size_t)w * NCO;
+            double* out = part + (size_t)w * nco_out;
             for (int c = lane; c < NCO; c += 32) {
                 const float* row = S + c * kPad;
                 float s = 0.f;
@@ -468,7 +481,8 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
 
 template <int P>
 void rot_launch(const int2* list, const int* seg_start, const int* seg_end, const int* order, const int* item_start,
-                unsigned* work, const d4* cen, const float* Mt, const cd* M64, double* part, cudaStream_t s) {
+                unsigned* work, const d4* cen, const float* Mt, const cd* M64, double* part, const int* ilist,
+                const unsigned* goff, int gq, unsigned* counter, int nco_out, int adapt, cudaStream_t s) {
     constexpr int W = rot_warps<P>();
     const size_t sm = (size_t)W * rot_warp_bytes<P>();
     cudaFuncSetAttribute(k_m2l_rot<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -477,7 +491,8 @@ void rot_launch(const int2* list, const int* seg_start, const int* seg_end, cons
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l_rot<P>, 32 * W, sm);
     const unsigned g = (unsigned)(nsm * (bps > 0 ? bps : 1));
-    k_m2l_rot<P><<<g, 32 * W, sm, s>>>(list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part);
+    k_m2l_rot<P><<<g, 32 * W, sm, s>>>(list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part, ilist,
+                                       goff, gq, counter, nco_out, adapt);
     note_launch();
 }
 

@@ -329,6 +329,9 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     wp.P = Pw;
     wp.binom = binom;
     wp.use_com = 0;
+    wp.adaptive = 0;  // this path keeps every interaction at p
+    wp.p_lo = p;
+    wp.pascal = nullptr;
     long long nm = 0, np = 0;
     int rc = walk_na(r, wp, m2l, kListCap, p2p, kListCap, &nm, &np);
     if (rc) return rc;
@@ -338,7 +341,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     // A9-A12
     NA_CU(cudaMemsetAsync(F, 0, sizeof(double) * nco * (size_t)nc, s));
     if (split)
-        launch_m2l_split(m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.sr, M, p, F, prm.m2l_rot != 0, s);
+        launch_m2l_split(m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.sr, M, p, F, prm.m2l_rot != 0, s, false, nm);
     else
         launch_m2l(m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.sr, M, p, F, s);
     sort_pairs_by_sink(p2p, np, nc, r.sort_tmp, s);

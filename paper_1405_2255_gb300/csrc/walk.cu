@@ -79,7 +79,23 @@ __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in
                     double mx = ra > rb ? ra : rb;
                     double fac = (ra + rb > 0) ? 8.0 * mx / (ra + rb) : 8.0;
                     double lhs = fac * h / (r * r);
-                    accept = lhs < wp.eps * c.minscale[B];  // eqs. (18a,b)
+                    const double rhs = wp.eps * c.minscale[B];
+                    accept = lhs < rhs;  // eqs. (18a,b)
+                    if (accept && wp.adaptive) {
+                        // the lowest order q whose E~ (eq. 17 with q for p) passes as well
+                        for (int q = wp.p_lo; q < wp.p; ++q) {
+                            const double* C = wp.pascal + q * (kMaxP + 1);
+                            double hq = 0.0, rq = 1.0;
+                            for (int k = 0; k <= q; ++k) {
+                                hq = hq * u + C[k] * (P[k] * rq);
+                                rq *= rinv;
+                            }
+                            if (fac * hq / (r * r) < rhs) {
+                                A |= q << kM2LOrderShift;
+                                break;
+                            }
+                        }
+                    }
                 }
                 if (accept) act = kActM2L;
                 else if (!nchA && !nchB) act = kActP2P;
@@ -131,16 +147,17 @@ static int bits_for(long long v) {
     return b;
 }
 
-__global__ void k_pack_pairs(const int2* __restrict__ list, long long n, int sb, uint64_t* __restrict__ keys,
+// key = (sink << xb) | first entry: the first entry takes the low xb bits
+__global__ void k_pack_pairs(const int2* __restrict__ list, long long n, int xb, uint64_t* __restrict__ keys,
                              int* __restrict__ idx) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         int2 v = list[i];
-        keys[i] = ((uint64_t)(unsigned)v.y << sb) | (uint64_t)(unsigned)v.x;
+        keys[i] = ((uint64_t)(unsigned)v.y << xb) | (uint64_t)(unsigned)v.x;
         idx[i] = 0;
     }
 }
 __global__ void k_unpack_pairs(const uint64_t* __restrict__ keys, long long n, int sb, int2* __restrict__ list) {
-    const uint64_t mask = (1ull << sb) - 1;
+    const uint64_t mask = sb >= 32 ? 0xffffffffull : (1ull << sb) - 1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         uint64_t k = keys[i];
         list[i] = make_int2((int)(k & mask), (int)(k >> sb));
@@ -152,7 +169,7 @@ size_t list_sort_tmp_bytes(long long npairs) {
     return n * (2 * sizeof(uint64_t) + 2 * sizeof(int)) + radix_tmp_ints(n) * sizeof(int) + 256;
 }
 
-void sort_pairs_by_sink(int2* list, long long npairs, int ncells, void* tmp, cudaStream_t s) {
+void sort_pairs_by_sink(int2* list, long long npairs, int ncells, void* tmp, cudaStream_t s, bool wide) {
     if (npairs <= 1) return;
     int sb = bits_for(ncells);
     uint64_t* k0 = (uint64_t*)tmp;
@@ -160,11 +177,12 @@ void sort_pairs_by_sink(int2* list, long long npairs, int ncells, void* tmp, cud
     int* i0 = (int*)(k1 + npairs);
     int* i1 = i0 + npairs;
     int* rtmp = i1 + npairs;
+    const int xb = wide ? 32 : sb;
     unsigned g = grid_for(npairs, 256);
-    k_pack_pairs<<<g, 256, 0, s>>>(list, npairs, sb, k0, i0); note_launch();
-    int end_bit = 2 * sb;
+    k_pack_pairs<<<g, 256, 0, s>>>(list, npairs, xb, k0, i0); note_launch();
+    int end_bit = xb + sb;
     int flip = radix_sort_pairs_bits(k0, i0, k1, i1, npairs, rtmp, 0, end_bit, s);
-    k_unpack_pairs<<<g, 256, 0, s>>>(flip ? k1 : k0, npairs, sb, list); note_launch();
+    k_unpack_pairs<<<g, 256, 0, s>>>(flip ? k1 : k0, npairs, xb, list); note_launch();
 }
 
 __global__ void k_segments(const int2* __restrict__ list, long long n, int* __restrict__ seg_start,

@@ -28,7 +28,8 @@ FMM_SCALE_ESTIMATE, FMM_SCALE_CALLER = 0, 1
 class fmm_params(C.Structure):
     _fields_ = [("p", C.c_int), ("eps", C.c_double), ("mac", C.c_int), ("theta_crit", C.c_double),
                 ("leaf_size", C.c_int), ("p2p_c", C.c_double), ("precision", C.c_int), ("scale_src", C.c_int),
-                ("p2p_two_float", C.c_int), ("m2l_split", C.c_int), ("m2l_rot", C.c_int)]
+                ("p2p_two_float", C.c_int), ("m2l_split", C.c_int), ("m2l_rot", C.c_int),
+                ("adaptive_p", C.c_int)]
 
 
 class fmm_stats(C.Structure):
@@ -50,7 +51,7 @@ EXPORTS = ["fmm_default_params", "fmm_create", "fmm_set_params", "fmm_evaluate",
            "fmm_strerror", "fmm_last_error", "fmm_version", "fmm_alu_peaks", "fmm_evaluate_noalloc",
            "fmm_serve_config", "fmm_footprint_bytes", "fmm_system_register", "fmm_submit", "fmm_poll",
            "fmm_system_release", "fmm_workspace_bytes", "fmm_swap_matrix",
-           "fmm_evaluate_active"]
+           "fmm_evaluate_active", "fmm_debug_m2l_orders"]
 
 _lib = None
 
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
     L.fmm_workspace_bytes.argtypes = [vp]
     L.fmm_workspace_bytes.restype = C.c_uint64
     L.fmm_swap_matrix.argtypes = [ci, vp]
+    L.fmm_debug_m2l_orders.argtypes = [vp, vp]
     L.fmm_evaluate_active.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, ci, vp, vp, vp, vp, C.POINTER(fmm_stats)]
     for name in EXPORTS:
         if name not in ("fmm_strerror", "fmm_last_error", "fmm_version", "fmm_default_params",
@@ -285,6 +287,13 @@ class Context:
         st = fmm_stats()
         _check(self.L.fmm_last_stats(self.h, C.byref(st)), self.h)
         return st.as_dict()
+
+    def fmm_debug_m2l_orders(self) -> np.ndarray:
+        """Order of every M2L interaction of the last evaluation (fmm_debug_dump's order)."""
+        st = self.fmm_last_stats()
+        q = np.zeros(max(int(st["n_m2l"]), 1), dtype=np.int32)
+        _check(self.L.fmm_debug_m2l_orders(self.h, q.ctypes.data), self.h)
+        return q[:int(st["n_m2l"])]
 
     def fmm_debug_dump(self) -> dict:
         st = self.fmm_last_stats()

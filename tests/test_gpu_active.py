@@ -225,3 +225,31 @@ def test_mixed_tidal_accuracy(g, orc):
     tr = np.abs(T[:, 0] + T[:, 3] + T[:, 5]) / np.linalg.norm(T, axis=1)
     assert np.percentile(tr, 99) < 1e-4
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,rot", [("fp64", 1), ("mixed", 1), ("mixed", 0)])
+def test_adaptive_order_matches_oracle(g, orc, prec, rot):
+    """Sec. 7, opening, on the GPU: the same lists and per-pair orders as the oracle; FP64
+    mode to 1e-10, the mixed kernels (rotated: grouped by order; direct: per-pair truncation)
+    to the FP32 level against the oracle's FP64 run on those lists."""
+    x, mu = inputs.plummer(8000, inputs.BASE_SEED + 122)
+    kw = dict(p=11, eps=3e-7, leaf_size=24, p2p_c=1.0)
+    p = g.FMM_PREC_FP64 if prec == "fp64" else g.FMM_PREC_MIXED
+    ctx = g.Context(precision=p, m2l_rot=rot, adaptive_p=1, **kw)
+    _, acc = ctx.fmm_evaluate(_dev(x), _dev(mu))
+    d = ctx.fmm_debug_dump()
+    q = ctx.fmm_debug_m2l_orders()
+    run = orc.fmm(x, mu, adaptive_p=True, **kw)
+    # cells are numbered differently on the two sides: identify them by (first, count, level)
+    idg = [tuple(r) for r in d["cells_int"][:, [2, 3, 0]]]
+    ido = [tuple(r) for r in run.cells_int[:, [2, 3, 0]]]
+    key_g = sorted((idg[a_], idg[b_], int(q_)) for a_, b_, q_ in zip(d["m2l"][:, 0], d["m2l"][:, 1], q))
+    key_o = sorted((ido[a_], ido[b_], int(q_)) for a_, b_, q_ in zip(run.m2l[:, 0], run.m2l[:, 1], run.m2l_q))
+    assert key_g == key_o
+    acc = acc.cpu().numpy()
+    e = _rel(acc, run.acc)
+    if prec == "fp64":
+        assert e.max() <= PARITY_TOL
+    else:
+        assert np.sqrt(np.mean(e ** 2)) < 1e-7 and e.max() < 2e-6
+    ctx.close()

@@ -92,3 +92,21 @@ def test_individual_eps(orc):
     e_ref, e_t = _rel(ref.acc, a_t), _rel(tight.acc, a_t)
     assert np.sqrt(np.mean(e_t[inner] ** 2)) < 0.1 * np.sqrt(np.mean(e_ref[inner] ** 2))
     assert tight.stats["n_p2p"] + tight.stats["n_m2l"] > ref.stats["n_p2p"] + ref.stats["n_m2l"]
+
+
+def test_adaptive_order(orc):
+    """Sec. 7, opening: the adaptive walk keeps the lists and gives every accepted pair the
+    lowest order in [3, p] that passes; its forces keep the accuracy of the criterion."""
+    x, mu = inputs.plummer(4000, 307)
+    kw = dict(p=10, eps=3e-7, leaf_size=24, p2p_c=1.0)
+    fix = orc.fmm(x, mu, **kw)
+    ada = orc.fmm(x, mu, adaptive_p=True, **kw)
+    assert np.array_equal(fix.m2l, ada.m2l) and np.array_equal(fix.p2p, ada.p2p)
+    assert (fix.m2l_q == 10).all()
+    assert ada.m2l_q.min() >= 3 and ada.m2l_q.max() <= 10 and (ada.m2l_q < 10).any()
+    _, a_t, _, _ = orc.direct(x, mu)
+    e_f, e_a = _rel(fix.acc, a_t), _rel(ada.acc, a_t)
+    assert np.sqrt(np.mean(e_a ** 2)) < 2 * np.sqrt(np.mean(e_f ** 2))
+    # the geometric criterion has no order to adapt
+    geo = orc.fmm(x, mu, p=8, mac=orc.MAC_THETA, theta_crit=0.5, leaf_size=24, adaptive_p=True)
+    assert (geo.m2l_q == 8).all()
