@@ -682,6 +682,17 @@ def main():
         # GPU FP64 direct summation, timed on the sampled sinks and scaled to N sinks
         extras["fp64_direct_value"] = a.n / (t_direct * a.n / ns)
         extras["direct_sample_sinks"] = ns
+        # the same step with the tidal tensor (Sec. 7.4) as an extra output
+        Tt = torch.empty((a.n, 6), dtype=torch.float64, device=dev)
+        ctx.fmm_evaluate_active(xt, mt, psi=psi, acc=acc, tidal=Tt)
+        torch.cuda.synchronize(dev)
+        flush.zero_()
+        e0.record(stream)
+        ctx.fmm_evaluate_active(xt, mt, psi=psi, acc=acc, tidal=Tt)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        extras["with_tidal_ms"] = e0.elapsed_time(e1)
+        del Tt
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside)
     xh = torch.from_numpy(x).pin_memory().numpy()

@@ -63,9 +63,11 @@ def _time_ms(ctx, x, mu, psi, acc, reps=3):
 
 
 def tune(x, mu, target_rms=1e-7, ps=(8, 10, 12, 14, 16), leaves=(32, 48, 64, 96), cs=(1.0, 2.0, 4.0, 8.0),
-         nsinks=4096, seed=0, precision=None, eps0=2e-7, max_steps=4, margin=0.97, log=None) -> TuneResult:
+         nsinks=4096, seed=0, precision=None, eps0=2e-7, max_steps=4, margin=0.97, log=None,
+         fixed=None) -> TuneResult:
     """x [n,3], mu [n]: float64 CUDA tensors.  Returns the fastest candidate whose
-    measured rms relative error is at most target_rms."""
+    measured rms relative error is at most target_rms.  fixed: further fmm_params fields
+    held for every candidate (e.g. {"adaptive_p": 1})."""
     import torch
     from . import gb3fmm as g
     t0 = time.perf_counter()
@@ -85,7 +87,7 @@ def tune(x, mu, target_rms=1e-7, ps=(8, 10, 12, 14, 16), leaves=(32, 48, 64, 96)
             for c in cs:
                 cand = Candidate(p, leaf, c)
                 ctx = g.Context(p=p, eps=eps0, leaf_size=leaf, p2p_c=c, precision=prec,
-                                device=x.device.index or 0)
+                                device=x.device.index or 0, **(fixed or {}))
                 eps, hist = eps0, []
                 for _ in range(max_steps):
                     ctx.set_params(eps=eps)
