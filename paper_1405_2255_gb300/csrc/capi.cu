@@ -338,32 +338,35 @@ static int run_walk(fmm_ctx* ctx, WalkParams wp, Buf& m2l, long long& m2l_cap, B
         wb.p2p = P<int2>(p2p);
         wb.p2p_cap = p2p_cap;
         wb.counters = P<unsigned long long>(ctx->counters);
-        launch_walk_roots(wb.front[0], ctx->nroots, s);
-        CU(cudaMemsetAsync(wb.counters, 0, 4 * sizeof(unsigned long long), s));
-        long long nfront = ctx->nroots;
+        // counters: [0], [4] the frontier lengths (ping-pong), [1] M2L, [2] P2P, [3] overflow,
+        // [5] the largest frontier demand.  Every step of a pair descends one cell level on
+        // at least one side, so 2 * levels steps end the walk; the steps read their frontier
+        // lengths on the device and the host waits once, after the last one.
+        CU(cudaMemsetAsync(wb.counters, 0, 8 * sizeof(unsigned long long), s));
+        launch_walk_roots(wb.front[0], ctx->nroots, s, wb.counters);
+        const int nlev = (int)ctx->lev_start.size() - 1;
+        const int steps = 2 * nlev + 1;
         int cur = 0;
-        bool overflow = false;
-        long long need_front = 0;
-        while (nfront > 0) {
-            CU(cudaMemsetAsync(wb.counters, 0, sizeof(unsigned long long), s));
-            launch_walk_step(c, wp, wb.front[cur], nfront, wb.front[cur ^ 1], wb, s);
-            CU(cudaMemcpyAsync(ctx->h_counters, wb.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-            CU(cudaStreamSynchronize(s));
-            need_front = std::max<long long>(need_front, (long long)ctx->h_counters[0]);
-            if (ctx->h_counters[3]) {
-                overflow = true;
-                break;
-            }
-            nfront = (long long)ctx->h_counters[0];
+        for (int k = 0; k < steps; ++k) {
+            unsigned long long* in_cnt = wb.counters + (k & 1 ? 4 : 0);
+            unsigned long long* out_cnt = wb.counters + (k & 1 ? 0 : 4);
+            CU(cudaMemsetAsync(out_cnt, 0, sizeof(unsigned long long), s));
+            launch_walk_step_dev(c, wp, wb.front[cur], in_cnt, wb.front[cur ^ 1], wb, out_cnt, s);
             cur ^= 1;
         }
+        CU(cudaMemcpyAsync(ctx->h_counters, wb.counters, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        const long long left = (long long)ctx->h_counters[(steps - 1) & 1 ? 0 : 4];
+        const long long need_front = std::max<long long>((long long)ctx->h_counters[5], left);
+        const bool overflow = ctx->h_counters[3] != 0;
+        if (!overflow && left != 0) return fail(ctx, FMM_E_CUDA, "the tree walk did not end within 2 x levels steps");
         if (!overflow) {
             *n_m2l = (long long)ctx->h_counters[1];
             *n_p2p = (long long)ctx->h_counters[2];
             return 0;
         }
         // grow what overflowed (the counters hold at least the demand seen so far) and redo the walk
-        if ((long long)ctx->h_counters[0] > ctx->front_cap || need_front > ctx->front_cap)
+        if (need_front > ctx->front_cap)
             ctx->front_cap = std::max<long long>(2 * ctx->front_cap, 2 * need_front);
         if ((long long)ctx->h_counters[1] > m2l_cap) m2l_cap = std::max<long long>(2 * m2l_cap, 2 * (long long)ctx->h_counters[1]);
         if ((long long)ctx->h_counters[2] > p2p_cap) p2p_cap = std::max<long long>(2 * p2p_cap, 2 * (long long)ctx->h_counters[2]);

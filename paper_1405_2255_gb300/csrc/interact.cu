@@ -148,7 +148,9 @@ void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void
     cd* Mc = (cd*)(((uintptr_t)(rtmp + radix_tmp_ints(ncells)) + 255) & ~(uintptr_t)255);
     cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
     k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
-    int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 0, 56, s);
+    // the low 32 bits are the sink's index, already in order: the stable passes over the
+    // length bits alone keep ties in index order
+    int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 32, 56, s);
     k_sink_order<<<grid_for(ncells, 256), 256, 0, s>>>(flip ? k1 : k0, ncells, order, work + 1); note_launch();
     k_expand_conj<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(M, ncells, p, Mc); note_launch();
     LaneSched sched = make_lane_sched(p, kSchedDown);
@@ -607,7 +609,9 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     const int* item_q = nullptr;
     cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
     k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
-    int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 0, 56, s);
+    // the low 32 bits are the sink's index, already in order: the stable passes over the
+    // length bits alone keep ties in index order
+    int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 32, 56, s);
     k_sink_order<<<grid_for(ncells, 256), 256, 0, s>>>(flip ? k1 : k0, ncells, order, work + 1); note_launch();
     k_item_counts<<<grid_for(ncells, 256), 256, 0, s>>>(order, seg_start, seg_end, ncells, cnt); note_launch();
     scan_exclusive_i32(cnt, item_start, ncells, (int*)(work + 2), stmp, s);
@@ -1187,7 +1191,8 @@ void launch_p2p_mixed(const d4* /*xm*/, const float* hi, const float* lo, int n,
     cudaMemsetAsync(counter, 0, 4 * sizeof(unsigned), s);
     k_p2p_work<<<grid_for(nleaves, 128), 128, 0, s>>>(c, list, seg_start, seg_end, leaves, nleaves, k0, v0);
     note_launch();
-    const int flip = radix_sort_pairs_bits(k0, v0, k1, v1, nleaves, rtmp, 0, 64, s);
+    // the low 32 bits are the position in leaves[], already in order: sort the work bits only
+    const int flip = radix_sort_pairs_bits(k0, v0, k1, v1, nleaves, rtmp, 32, 64, s);
     k_p2p_order<<<grid_for(nleaves, 256), 256, 0, s>>>(flip ? k1 : k0, leaves, nleaves, order);
     note_launch();
     int dev = 0, nsm = 152, bps = 1;

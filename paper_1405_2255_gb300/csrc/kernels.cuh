@@ -126,9 +126,17 @@ struct WalkBuffers {
     unsigned long long* counters;  // [0] next frontier, [1] m2l, [2] p2p, [3] overflow flag
 };
 // the first frontier: (r, r) for the roots r = 0 .. nroots-1
-void launch_walk_roots(int2* front, int nroots, cudaStream_t s);
+// count (nullable): receives nroots, the first frontier's length on the device
+void launch_walk_roots(int2* front, int nroots, cudaStream_t s, unsigned long long* count = nullptr);
+// one breadth-first step over a frontier of nfront pairs (host value); the next frontier is
+// counted in wb.counters[0]
 void launch_walk_step(Cells c, WalkParams wp, const int2* front_in, long long nfront, int2* front_out,
                       WalkBuffers wb, cudaStream_t s);
+// the same with the frontier's length read on the device from *nfront_dev (no host round
+// trip between steps); the next frontier is counted in *out_cnt and wb.counters[5] keeps
+// the largest frontier demand seen
+void launch_walk_step_dev(Cells c, WalkParams wp, const int2* front_in, const unsigned long long* nfront_dev,
+                          int2* front_out, WalkBuffers wb, unsigned long long* out_cnt, cudaStream_t s);
 // sort a pair list by (sink, source), then mark per-sink segments [seg_start, seg_end)
 size_t list_sort_tmp_bytes(long long npairs);
 // wide: the first entries use all 32 bits (an adaptive-order M2L list)

@@ -37,8 +37,18 @@ __device__ inline long long warp_reserve(unsigned mine, unsigned long long* coun
 
 enum : int { kActNone = 0, kActM2L, kActP2P, kActSelf, kActSplitA, kActSplitB };
 
+// nfront_dev (nullable): the frontier's length on the device (read here, capped at the
+// buffer's capacity), else nfront; the next frontier is counted in *out_cnt
 __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in, long long nfront,
-                       int2* __restrict__ front_out, WalkBuffers wb) {
+                       const unsigned long long* __restrict__ nfront_dev, int2* __restrict__ front_out, WalkBuffers wb,
+                       unsigned long long* __restrict__ out_cnt) {
+    if (nfront_dev) {
+        const unsigned long long nd = *nfront_dev;
+        if (blockIdx.x == 0 && threadIdx.x == 0 && nd) atomicMax(&wb.counters[5], nd);  // demand seen
+        // after an overflow the frontier may have holes: no further steps (the walk is redone)
+        if (*(volatile const unsigned long long*)&wb.counters[3]) return;
+        nfront = (long long)nd < wb.front_cap ? (long long)nd : wb.front_cap;
+    }
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < nfront; base += stride) {
         long long i = base + threadIdx.x;
@@ -111,7 +121,7 @@ __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in
         unsigned nf = act == kActSelf ? nchA * nchA : act == kActSplitA ? nchA : act == kActSplitB ? nchB : 0;
         long long om = warp_reserve(nm, &wb.counters[1], wb.m2l_cap, &wb.counters[3]);
         long long op = warp_reserve(np, &wb.counters[2], wb.p2p_cap, &wb.counters[3]);
-        long long of = warp_reserve(nf, &wb.counters[0], wb.front_cap, &wb.counters[3]);
+        long long of = warp_reserve(nf, out_cnt, wb.front_cap, &wb.counters[3]);
         if (nm && om >= 0) wb.m2l[om] = make_int2(A, B);
         if (np && op >= 0) wb.p2p[op] = make_int2(A, B);
         if (nf && of >= 0) {
@@ -127,17 +137,25 @@ __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in
     }
 }
 
-__global__ void k_walk_roots(int2* front, int nroots) {
+__global__ void k_walk_roots(int2* front, int nroots, unsigned long long* count) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nroots; r += gridDim.x * blockDim.x) front[r] = make_int2(r, r);
+    if (count && blockIdx.x == 0 && threadIdx.x == 0) *count = (unsigned long long)nroots;
 }
-void launch_walk_roots(int2* front, int nroots, cudaStream_t s) {
-    if (nroots > 0) k_walk_roots<<<grid_for(nroots, 256), 256, 0, s>>>(front, nroots); note_launch();
+void launch_walk_roots(int2* front, int nroots, cudaStream_t s, unsigned long long* count) {
+    if (nroots > 0) k_walk_roots<<<grid_for(nroots, 256), 256, 0, s>>>(front, nroots, count); note_launch();
 }
 
 void launch_walk_step(Cells c, WalkParams wp, const int2* front_in, long long nfront, int2* front_out,
                       WalkBuffers wb, cudaStream_t s) {
     if (nfront <= 0) return;
-    k_walk<<<grid_for(nfront, 256, 152 * 16), 256, 0, s>>>(c, wp, front_in, nfront, front_out, wb); note_launch();
+    k_walk<<<grid_for(nfront, 256, 152 * 16), 256, 0, s>>>(c, wp, front_in, nfront, nullptr, front_out, wb,
+                                                             &wb.counters[0]);
+    note_launch();
+}
+void launch_walk_step_dev(Cells c, WalkParams wp, const int2* front_in, const unsigned long long* nfront_dev,
+                          int2* front_out, WalkBuffers wb, unsigned long long* out_cnt, cudaStream_t s) {
+    k_walk<<<152 * 8, 256, 0, s>>>(c, wp, front_in, 0, nfront_dev, front_out, wb, out_cnt);
+    note_launch();
 }
 
 // ---------------------------------------------------------------- list sort

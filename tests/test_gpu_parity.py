@@ -395,3 +395,20 @@ def test_library_swap_matrices_match_oracle_and_paper(g, orc):
         assert np.max(np.abs(g.fmm_swap_matrix(n) - orc.swap_matrix(n))) <= 1e-12 * max(1.0, np.abs(orc.swap_matrix(n)).max())
     with pytest.raises(g.FMMError):
         g.fmm_swap_matrix(17)
+
+
+def test_walk_lists_grow_after_an_overflow(g, orc):
+    """A context whose lists were sized by a tiny system meets a large one: the walk overflows,
+    grows the lists and is redone; the result equals a fresh context's."""
+    import torch
+    xs, ms = inputs.plummer(200, inputs.BASE_SEED + 130)
+    x, mu = inputs.plummer(60000, inputs.BASE_SEED + 131)
+    kw = dict(p=6, eps=1e-6, leaf_size=8, p2p_c=0.5)
+    c1 = g.Context(**kw)
+    c1.fmm_evaluate(_dev(xs), _dev(ms))
+    _, a1 = c1.fmm_evaluate(_dev(x), _dev(mu))
+    c2 = g.Context(**kw)
+    _, a2 = c2.fmm_evaluate(_dev(x), _dev(mu))
+    assert torch.equal(a1, a2)
+    c1.close()
+    c2.close()
