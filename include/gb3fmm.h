@@ -73,8 +73,11 @@ typedef struct {
     double p2p_c;       /* a pair (A,B) is summed directly when N_A N_B < p2p_c p^3     */
     int    precision;   /* FMM_PREC_*                                                  */
     int    scale_src;   /* FMM_SCALE_*                                                 */
-    int    p2p_two_float; /* mixed P2P: 1 = dx from two-float positions (hi + lo) relative
-                             to the sink leaf's centre; 0 = from their FP32 high parts only */
+    int    p2p_two_float; /* mixed P2P: 1 = dx = (h_a - h_b) + (l_a - l_b) from two-float
+                             positions (hi + lo) per pair; 2 = every source is turned once per
+                             tile into an FP32 offset from the sink leaf's centre,
+                             (h - c_h) + (l - c_l), and dx is one FP32 difference of offsets;
+                             0 = from the FP32 high parts only                           */
     int    m2l_split;   /* mixed mode M2L: 1 = terms of order n+k <= 2 in FP64 and the others
                            in FP32 on scaled harmonics; 0 = every term in FP64        */
     int    m2l_rot;     /* mixed mode M2L with m2l_split, 3 <= p <= 16: 1 = the terms of order

@@ -166,6 +166,7 @@ static int check_params(const fmm_params* p) {
     if (p->scale_src != FMM_SCALE_ESTIMATE && p->scale_src != FMM_SCALE_CALLER) return FMM_E_INVALID;
     if (p->m2l_rot != 0 && p->m2l_rot != 1) return FMM_E_INVALID;
     if (p->adaptive_p != 0 && p->adaptive_p != 1) return FMM_E_INVALID;
+    if (p->p2p_two_float < 0 || p->p2p_two_float > 2) return FMM_E_INVALID;
     return 0;
 }
 
@@ -431,7 +432,7 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
         TRY(ensure(ctx->p2p_tmp, p2p_tmp_bytes(ctx->nleaves)));
         launch_p2p_mixed(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), ctx->n, c, P<int2>(ctx->est_p2p),
                          P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
-                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), false, ctx->p2p_tmp.p, s);
+                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), 0, ctx->p2p_tmp.p, s);
     }
     else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->est_p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
@@ -616,7 +617,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         TRY(ensure(ctx->p2p_tmp, p2p_tmp_bytes(ctx->nleaves)));
         launch_p2p_mixed(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), ctx->n, c, P<int2>(ctx->p2p),
                          P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
-                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), prm.p2p_two_float != 0,
+                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), prm.p2p_two_float,
                          ctx->p2p_tmp.p, s);
     }
     else

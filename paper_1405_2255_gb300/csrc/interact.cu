@@ -1019,7 +1019,11 @@ struct SrcCursor {
 
 // One warp per sink leaf, leaves taken in decreasing order of work from an atomic
 // counter; sources come from the P2P segments of the leaf and of its ancestors.
-template <bool TWO_FLOAT>
+// MODE 0: dx from the FP32 high parts; 1: from the two-float positions, (h_a - h_b) +
+// (l_a - l_b) per pair; 2: leaf-relative: every tile's sources are turned once into FP32
+// offsets from the sink leaf's centre c (two-float differences (h - c_h) + (l - c_l)),
+// so that a pair's dx is one FP32 difference of offsets
+template <int MODE>
 __global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float* __restrict__ hi,
                                                                  const float* __restrict__ lo, int n, Cells c,
                                                                  const int2* __restrict__ list,
@@ -1028,7 +1032,9 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float* __
                                                                  const int* __restrict__ order, int nleaves,
                                                                  unsigned* __restrict__ counter,
                                                                  double* __restrict__ psi, double* __restrict__ acc) {
-    constexpr int NA = TWO_FLOAT ? 7 : 4;  // arrays per tile
+    constexpr bool TWO_FLOAT = MODE == 1;  // two-float dx in the pair loop
+    constexpr bool LOADLO = MODE >= 1;     // the tiles carry the low parts
+    constexpr int NA = LOADLO ? 7 : 4;     // arrays per tile
     __shared__ __align__(16) float tiles[kP2PWarps][2][NA * kP2PTile];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t nn = (size_t)n;
@@ -1052,11 +1058,22 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float* __
                 bhx = hi[i];
                 bhy = hi[nn + i];
                 bhz = hi[2 * nn + i];
-                if (TWO_FLOAT) {
+                if (LOADLO) {
                     blx = lo[i];
                     bly = lo[nn + i];
                     blz = lo[2 * nn + i];
                 }
+            }
+            // MODE 2: the leaf centre as two floats, the sink as its offset from it
+            float chx = 0, chy = 0, chz = 0, clx = 0, cly = 0, clz = 0;
+            if (MODE == 2) {
+                const d4 sc = c.sr[leaf];
+                chx = (float)sc.x; chy = (float)sc.y; chz = (float)sc.z;
+                clx = (float)(sc.x - (double)chx); cly = (float)(sc.y - (double)chy); clz = (float)(sc.z - (double)chz);
+                bhx = __fadd_rn(__fsub_rn(bhx, chx), __fsub_rn(blx, clx));
+                bhy = __fadd_rn(__fsub_rn(bhy, chy), __fsub_rn(bly, cly));
+                bhz = __fadd_rn(__fsub_rn(bhz, chz), __fsub_rn(blz, clz));
+                blx = bly = blz = 0.f;
             }
             const SinkPk b{f2_pack(bhx, bhx), f2_pack(bhy, bhy), f2_pack(bhz, bhz),
                            f2_pack(blx, blx), f2_pack(bly, bly), f2_pack(blz, blz)};
@@ -1068,24 +1085,34 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float* __
             const int T = 32 * R;  // sources per tile: eight groups of four for every replica
             int bb = 0;
             bool guard = false, guard_next = false;
-            int nt = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, hi, lo, nn, first, lane, T, tiles[wid][0],
-                                         guard);
+            int nt = cur.fill<LOADLO>(c, list, seg_start, seg_end, hi, lo, nn, first, lane, T, tiles[wid][0],
+                                      guard);
             cp_async_commit();
             while (nt > 0) {
                 // issue the next tile, then wait for the current one
-                const int nx = cur.fill<TWO_FLOAT>(c, list, seg_start, seg_end, hi, lo, nn, first, lane, T,
-                                                   tiles[wid][bb ^ 1], guard_next);
+                const int nx = cur.fill<LOADLO>(c, list, seg_start, seg_end, hi, lo, nn, first, lane, T,
+                                                tiles[wid][bb ^ 1], guard_next);
                 cp_async_commit();
                 cp_async_wait1();
                 float* tile = tiles[wid][bb];
                 const int ng = (nt + 3) >> 2;
+                if (MODE == 2) {  // offsets from the leaf centre, in place of the high parts
+                    __syncwarp();
+                    for (int j = lane; j < nt; j += 32) {
+                        tile[j] = __fadd_rn(__fsub_rn(tile[j], chx), __fsub_rn(tile[4 * kP2PTile + j], clx));
+                        tile[kP2PTile + j] =
+                            __fadd_rn(__fsub_rn(tile[kP2PTile + j], chy), __fsub_rn(tile[5 * kP2PTile + j], cly));
+                        tile[2 * kP2PTile + j] =
+                            __fadd_rn(__fsub_rn(tile[2 * kP2PTile + j], chz), __fsub_rn(tile[6 * kP2PTile + j], clz));
+                    }
+                }
                 if (lane < 4 * ng - nt) {  // pad to whole groups: massless, far away
                     float* t = tile + nt + lane;
                     t[0] = 1e15f;
                     t[kP2PTile] = 1e15f;
                     t[2 * kP2PTile] = 1e15f;
                     t[3 * kP2PTile] = 0.f;
-                    if (TWO_FLOAT) t[4 * kP2PTile] = t[5 * kP2PTile] = t[6 * kP2PTile] = 0.f;
+                    if (LOADLO) t[4 * kP2PTile] = t[5 * kP2PTile] = t[6 * kP2PTile] = 0.f;
                 }
                 __syncwarp();
                 if (guard) p2p_tile_r<TWO_FLOAT, true>(tile, ng, rep, R, b, a);
@@ -1179,7 +1206,7 @@ size_t p2p_tmp_bytes(int nleaves) {
 
 void launch_p2p_mixed(const d4* /*xm*/, const float* hi, const float* lo, int n, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* psi,
-                      double* acc, bool two_float, void* tmp, cudaStream_t s) {
+                      double* acc, int mode, void* tmp, cudaStream_t s) {
     if (nleaves <= 0) return;
     uint64_t* k0 = (uint64_t*)tmp;
     uint64_t* k1 = k0 + nleaves;
@@ -1198,16 +1225,14 @@ void launch_p2p_mixed(const d4* /*xm*/, const float* hi, const float* lo, int n,
     int dev = 0, nsm = 152, bps = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (two_float) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_p2p_mixed<true>, kP2PWarps * 32, 0);
-        k_p2p_mixed<true><<<nsm * (bps > 0 ? bps : 1), kP2PWarps * 32, 0, s>>>(hi, lo, n, c, list, seg_start, seg_end,
-                                                                             order, nleaves, counter, psi, acc);
-    } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_p2p_mixed<false>, kP2PWarps * 32, 0);
-        k_p2p_mixed<false><<<nsm * (bps > 0 ? bps : 1), kP2PWarps * 32, 0, s>>>(hi, lo, n, c, list, seg_start,
-                                                                              seg_end, order, nleaves, counter, psi,
-                                                                              acc);
-    }
+    auto go = [&](auto kern) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kP2PWarps * 32, 0);
+        kern<<<nsm * (bps > 0 ? bps : 1), kP2PWarps * 32, 0, s>>>(hi, lo, n, c, list, seg_start, seg_end, order,
+                                                                   nleaves, counter, psi, acc);
+    };
+    if (mode == 2) go(k_p2p_mixed<2>);
+    else if (mode == 1) go(k_p2p_mixed<1>);
+    else go(k_p2p_mixed<0>);
     note_launch();
 }
 

@@ -189,11 +189,12 @@ void launch_l2l_split(Cells c, const d4* cen, int lev_begin, int lev_end, int p,
 // its own P2P segment and those of its ancestors' segments.
 void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_start,
                      const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc, cudaStream_t s);
-// two_float: dx from two-float leaf-relative positions; otherwise from their FP32 high parts
+// mode (fmm_params.p2p_two_float): 0 dx from the FP32 high parts, 1 from the two-float
+// positions, 2 from FP32 offsets to the sink leaf's centre formed in two-float per tile
 size_t p2p_tmp_bytes(int nleaves);
 void launch_p2p_mixed(const d4* xm, const float* hi, const float* lo, int n, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves,
-                      double* psi, double* acc, bool two_float, void* tmp, cudaStream_t s);
+                      double* psi, double* acc, int mode, void* tmp, cudaStream_t s);
 // ordered pairs of distinct particles at distance 0 (sorted keys and positions); with
 // an ensemble (off != nullptr) only pairs inside one system count
 void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s,

@@ -296,7 +296,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
             launch_l2p(r.xm, r.c, r.c.cr, r.leaves, r.nleaves, 1, F1, psi_far, acc_far, s);
             if (prm.precision == FMM_PREC_MIXED)
                 launch_p2p_mixed(r.xm, xhi, xlo, n, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near,
-                                 acc_near, false, p2p_tmp, s);
+                                 acc_near, 0, p2p_tmp, s);
             else
                 launch_p2p_fp64(r.xm, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
             launch_norm_scale(nullptr, acc_far, acc_near, n, scale, s);
@@ -348,7 +348,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     launch_segments(p2p, np, nc, seg_start, seg_end, s);
     if (prm.precision == FMM_PREC_MIXED)
         launch_p2p_mixed(r.xm, xhi, xlo, n, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near,
-                         prm.p2p_two_float != 0, p2p_tmp, s);
+                         prm.p2p_two_float, p2p_tmp, s);
     else
         launch_p2p_fp64(r.xm, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
     for (int L = 1; L < nl; ++L) {
