@@ -76,6 +76,7 @@ struct fmm_ctx {
     // expansions
     Buf M, F, Pw, binom, pascal, M1, F1, Ff;
     // walk
+    Buf walkf;  // single-precision view of the cells for the walk's acceptance test
     Buf front0, front1, m2l, p2p, sort_tmp, m2l_tmp, p2p_tmp, seg_start, seg_end, est_m2l, est_p2p, m2l_seg_start, m2l_seg_end;
     long long front_cap = 0, m2l_cap = 0, p2p_cap = 0, est_m2l_cap = 0, est_p2p_cap = 0;
     // per particle results (sorted order)
@@ -104,7 +105,7 @@ struct fmm_ctx {
                 &leaf_pos, &rad_tmp, &M, &F, &Pw, &binom, &pascal, &M1, &F1, &Ff, &front0, &front1, &m2l, &p2p,
                 &sort_tmp, &m2l_tmp, &p2p_tmp, &seg_start, &seg_end, &est_m2l, &est_p2p, &m2l_seg_start,
                 &m2l_seg_end, &psi_far, &acc_far, &psi_near, &acc_near, &scale_sorted, &sys_off, &sys_G,
-                &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan, &tid_far, &tid_near};
+                &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan, &tid_far, &tid_near, &walkf};
     }
     // tree shape of the last evaluation
     std::vector<int> lev_start;
@@ -400,6 +401,9 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     wp.mac = kMacEstimate;
     wp.p2p_thresh = ctx->prm.p2p_c * (double)wp.p * wp.p * wp.p;  // the estimate's own order (reading R-p2p)
     wp.use_com = 1;
+    TRY(ensure(ctx->walkf, sizeof(float4) * 2 * (size_t)nc));
+    wp.fc = P<float4>(ctx->walkf);
+    launch_walk_prep(c, c.cr, nullptr, 0, 0.0, nc, P<float4>(ctx->walkf), nullptr, s);
     TRY(run_walk(ctx, wp, ctx->est_m2l, ctx->est_m2l_cap, ctx->est_p2p, ctx->est_p2p_cap, &ctx->n_est_m2l,
                  &ctx->n_est_p2p, s));
     TRY(sort_and_segment(ctx, ctx->est_m2l, ctx->n_est_m2l, ctx->m2l_seg_start, ctx->m2l_seg_end, s));
@@ -570,6 +574,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
 
     // A8: dual tree walk
     WalkParams wp;
+    memset(&wp, 0, sizeof wp);
     wp.p = prm.p;
     wp.mac = prm.mac;
     wp.eps = prm.eps;
@@ -591,6 +596,14 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         CU(cudaMemcpyAsync(ctx->pascal.p, pt, sizeof pt, cudaMemcpyHostToDevice, s));
         CU(cudaStreamSynchronize(s));  // pt lives on this stack frame
         wp.pascal = P<double>(ctx->pascal);
+    }
+    if (prm.mac != FMM_MAC_THETA && !wp.adaptive) {
+        const int fs = walk_fstride(prm.p);
+        TRY(ensure(ctx->walkf, sizeof(float) * (8 + (size_t)fs) * nc));
+        wp.fc = P<float4>(ctx->walkf);
+        wp.fP = (float*)(wp.fc + 2 * (size_t)nc);
+        wp.fstride = fs;
+        launch_walk_prep(c, c.sr, wp.P, prm.p, prm.eps, nc, P<float4>(ctx->walkf), P<float>(ctx->walkf) + 8 * (size_t)nc, s);
     }
     TRY(run_walk(ctx, wp, ctx->m2l, ctx->m2l_cap, ctx->p2p, ctx->p2p_cap, &ctx->n_m2l, &ctx->n_p2p, s));
     TRY(sort_and_segment(ctx, ctx->m2l, ctx->n_m2l, ctx->m2l_seg_start, ctx->m2l_seg_end, s, wp.adaptive != 0));

@@ -893,6 +893,15 @@ struct AccPk {
     f2 ps, ax, ay, az;
 };
 
+// 1/sqrt(r2) by the hardware approximation with subnormal inputs flushed to zero (an
+// r2 below 2^-126 would be a pair closer than 1e-19 in the positions' units); the
+// non-flushing form spends extra instructions per pair on rescaling such inputs
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // two sources (x, y, z, w high parts; x, y, z low parts as packed pairs) against the sink
 template <bool TWO_FLOAT, bool GUARD>
 __device__ __forceinline__ void p2p_pair2(f2 X, f2 Y, f2 Z, f2 W, f2 XL, f2 YL, f2 ZL, const SinkPk& b, AccPk& a) {
@@ -905,7 +914,7 @@ __device__ __forceinline__ void p2p_pair2(f2 X, f2 Y, f2 Z, f2 W, f2 XL, f2 YL, 
     const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
     float r2a, r2b;
     f2_unpack(r2, r2a, r2b);
-    float ia = rsqrtf(r2a), ib = rsqrtf(r2b);
+    float ia = rsqrt_ftz(r2a), ib = rsqrt_ftz(r2b);
     if (GUARD) {
         ia = r2a > 0.f ? ia : 0.f;
         ib = r2b > 0.f ? ib : 0.f;

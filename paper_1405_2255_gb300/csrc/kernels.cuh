@@ -104,7 +104,20 @@ struct WalkParams {
     // = C(q, k)
     int adaptive, p_lo;
     const double* pascal;
+    // single-precision view of the cells for the acceptance test (nullable, then every
+    // decision is taken in FP64): fc[2 c] = centre high parts and rho, fc[2 c + 1] = centre
+    // low parts and P_0; fP[c * fstride + k] = P_k / (P_0 rho^k) for k <= p and, at k = p + 1,
+    // eps * minscale.  A decision within a margin of its threshold is taken in FP64.
+    const float4* fc;
+    const float* fP;
+    int fstride;
 };
+// row stride of fP for order p (P_0..P_p, eps * minscale, padded to float4)
+inline int walk_fstride(int p) { return (p + 2 + 3) & ~3; }
+// fill the single-precision view: centres from cen (sr, or cr for the estimator); with P
+// (nullable) also the normalised powers and eps * minscale
+void launch_walk_prep(Cells c, const d4* cen, const double* P, int p, double eps, int nc, float4* fc, float* fP,
+                      cudaStream_t s);
 // M2L list entries of an adaptive-order walk carry the pair's order q in the top bits of
 // the source index: x = source | (q << kM2LOrderShift); q = 0 stands for the global p
 constexpr int kM2LOrderShift = 27;

@@ -262,6 +262,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     double* M1 = A.take<double>(4 * (size_t)nc);
     double* F1 = A.take<double>(4 * (size_t)nc);
     double* Ff = A.take<double>(nc);
+    float4* walkf = A.take<float4>((size_t)(2 + walk_fstride(p) / 4) * nc);
     void* m2l_tmp = A.take<unsigned char>(m2l_split_tmp_bytes(nc, p > 1 ? p : 1, kListCap));
     void* p2p_tmp = A.take<unsigned char>(p2p_tmp_bytes(r.nleaves));
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the expansions and lists");
@@ -276,6 +277,8 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
         ew.mac = kMacEstimate;
         ew.p2p_thresh = prm.p2p_c * (double)ew.p * ew.p * ew.p;  // the estimate's own order
         ew.use_com = 1;
+        ew.fc = walkf;
+        launch_walk_prep(r.c, r.c.cr, nullptr, 0, 0.0, nc, walkf, nullptr, s);
         long long nm = 0, np = 0;
         int rc = walk_na(r, ew, est_m2l, kEstCap, est_p2p, kEstCap, &nm, &np);
         if (rc) return rc;
@@ -321,6 +324,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
 
     // A8: dual tree walk
     WalkParams wp;
+    memset(&wp, 0, sizeof wp);
     wp.p = p;
     wp.mac = prm.mac;
     wp.eps = prm.eps;
@@ -332,6 +336,12 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     wp.adaptive = 0;  // this path keeps every interaction at p
     wp.p_lo = p;
     wp.pascal = nullptr;
+    if (prm.mac != FMM_MAC_THETA) {
+        wp.fc = walkf;
+        wp.fP = (const float*)(walkf + 2 * (size_t)nc);
+        wp.fstride = walk_fstride(p);
+        launch_walk_prep(r.c, r.c.sr, Pw, p, prm.eps, nc, walkf, (float*)(walkf + 2 * (size_t)nc), s);
+    }
     long long nm = 0, np = 0;
     int rc = walk_na(r, wp, m2l, kListCap, p2p, kListCap, &nm, &np);
     if (rc) return rc;

@@ -413,37 +413,59 @@ void launch_split_level(const uint64_t* keys, Cells c, int lev_begin, int lev_en
 constexpr float kMebSing = 1e-6f;  // singular support set (relative to the Gram scale)
 constexpr float kMebIn = 1e-5f;    // inside tolerance, relative to the radius
 
-__device__ bool solve_small_dev(int k, float A[3][3], float b0[3], float b1[3], float x0[3], float x1[3]) {
-    float M[3][5];
+// Gaussian elimination with partial pivoting of the K x K system A x = b0, b1 (K
+// fixed at compile time so that the arrays stay in registers; the row swap is a
+// select per candidate row, the arithmetic and its order as in the plain form)
+template <int K>
+__device__ __forceinline__ bool solve_small_k(const float (&A)[3][3], const float (&b0)[3], const float (&b1)[3],
+                                              float (&x0)[3], float (&x1)[3]) {
+    float M[K][K + 2];
     float scale = 0;
-    for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j)
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int j = 0; j < K; ++j)
             if (fabsf(A[i][j]) > scale) scale = fabsf(A[i][j]);
     if (scale == 0) return false;
-    for (int i = 0; i < k; ++i) {
-        for (int j = 0; j < k; ++j) M[i][j] = A[i][j];
-        M[i][k] = b0[i];
-        M[i][k + 1] = b1[i];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) M[i][j] = A[i][j];
+        M[i][K] = b0[i];
+        M[i][K + 1] = b1[i];
     }
-    for (int col = 0; col < k; ++col) {
+#pragma unroll
+    for (int col = 0; col < K; ++col) {
         int piv = col;
-        for (int r = col + 1; r < k; ++r)
-            if (fabsf(M[r][col]) > fabsf(M[piv][col])) piv = r;
-        if (fabsf(M[piv][col]) <= kMebSing * scale) return false;
-        if (piv != col)
-            for (int j = 0; j < k + 2; ++j) {
-                float t = M[col][j];
-                M[col][j] = M[piv][j];
-                M[piv][j] = t;
+        float pv = fabsf(M[col][col]);
+#pragma unroll
+        for (int r = col + 1; r < K; ++r)
+            if (fabsf(M[r][col]) > pv) {
+                piv = r;
+                pv = fabsf(M[r][col]);
             }
-        for (int r = col + 1; r < k; ++r) {
-            float fct = M[r][col] / M[col][col];
-            for (int j = col; j < k + 2; ++j) M[r][j] -= fct * M[col][j];
+        if (pv <= kMebSing * scale) return false;
+#pragma unroll
+        for (int r = col + 1; r < K; ++r)
+            if (piv == r)
+#pragma unroll
+                for (int j = 0; j < K + 2; ++j) {
+                    const float t = M[col][j];
+                    M[col][j] = M[r][j];
+                    M[r][j] = t;
+                }
+#pragma unroll
+        for (int r = col + 1; r < K; ++r) {
+            const float fct = M[r][col] / M[col][col];
+#pragma unroll
+            for (int j = col; j < K + 2; ++j) M[r][j] -= fct * M[col][j];
         }
     }
-    for (int r = k - 1; r >= 0; --r) {
-        float s0 = M[r][k], s1 = M[r][k + 1];
-        for (int j = r + 1; j < k; ++j) {
+#pragma unroll
+    for (int r = K - 1; r >= 0; --r) {
+        float s0 = M[r][K], s1 = M[r][K + 1];
+#pragma unroll
+        for (int j = r + 1; j < K; ++j) {
             s0 -= M[r][j] * x0[j];
             s1 -= M[r][j] * x1[j];
         }
@@ -453,24 +475,32 @@ __device__ bool solve_small_dev(int k, float A[3][3], float b0[3], float b1[3], 
     return true;
 }
 
-__device__ bool support_ball_dev(int k, const float (*c)[3], const float* r, float oc[3], float& orad) {
-    if (k == 1) {
+// support_ball for a support set of NS = 1..4 balls (size fixed at compile time)
+template <int NS>
+__device__ __forceinline__ bool support_ball_k(const float (*c)[3], const float* r, float oc[3], float& orad) {
+    if (NS == 1) {
         oc[0] = c[0][0]; oc[1] = c[0][1]; oc[2] = c[0][2];
         orad = r[0];
         return true;
     }
-    int q = k - 1;
+    constexpr int q = NS > 1 ? NS - 1 : 1;
     float D[3][3], G[3][3], a[3], b[3], la[3], lb[3];
+#pragma unroll
     for (int j = 0; j < q; ++j)
+#pragma unroll
         for (int d = 0; d < 3; ++d) D[j][d] = c[j + 1][d] - c[0][d];
+#pragma unroll
     for (int i = 0; i < q; ++i) {
+#pragma unroll
         for (int j = 0; j < q; ++j) G[i][j] = D[i][0] * D[j][0] + D[i][1] * D[j][1] + D[i][2] * D[j][2];
         a[i] = 0.5f * (G[i][i] - r[i + 1] * r[i + 1] + r[0] * r[0]);
         b[i] = r[i + 1] - r[0];
     }
-    if (!solve_small_dev(q, G, a, b, la, lb)) return false;
+    if (!solve_small_k<q>(G, a, b, la, lb)) return false;
     float A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+#pragma unroll
     for (int j = 0; j < q; ++j)
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
             A[d] += la[j] * D[j][d];
             B[d] += lb[j] * D[j][d];
@@ -479,7 +509,8 @@ __device__ bool support_ball_dev(int k, const float (*c)[3], const float* r, flo
     float qb = A[0] * B[0] + A[1] * B[1] + A[2] * B[2] + r[0];
     float qc = A[0] * A[0] + A[1] * A[1] + A[2] * A[2] - r[0] * r[0];
     float rmax = r[0];
-    for (int i = 1; i < k; ++i)
+#pragma unroll
+    for (int i = 1; i < NS; ++i)
         if (r[i] > rmax) rmax = r[i];
     float R;
     if (fabsf(qa) < 1e-6f) {
@@ -500,9 +531,21 @@ __device__ bool support_ball_dev(int k, const float (*c)[3], const float* r, flo
         else return false;
     }
     if (!(R >= 0) || R < rmax - kMebSing * rmax) return false;
+#pragma unroll
     for (int d = 0; d < 3; ++d) oc[d] = c[0][d] + A[d] + R * B[d];
     orad = R;
     return true;
+}
+
+// the smallest ball whose boundary touches each of k <= 4 balls (c_i, r_i) from
+// inside (k at run time)
+__device__ __noinline__ bool support_ball_dev(int k, const float (*c)[3], const float* r, float oc[3], float& orad) {
+    switch (k) {
+        case 1: return support_ball_k<1>(c, r, oc, orad);
+        case 2: return support_ball_k<2>(c, r, oc, orad);
+        case 3: return support_ball_k<3>(c, r, oc, orad);
+        default: return support_ball_k<4>(c, r, oc, orad);
+    }
 }
 
 __device__ inline float dist3f_dev(const float a[3], const float b[3]) {
@@ -510,38 +553,62 @@ __device__ inline float dist3f_dev(const float a[3], const float b[3]) {
     return sqrtf(dx * dx + dy * dy + dz * dz);
 }
 
-// Welzl's b_md(empty, R): the smallest ball with the support points on its boundary
-__device__ void trivial_ball_dev(int nr, const float (*R)[3], float c[3], float& rad) {
+// Welzl's b_md(empty, R): the smallest ball with the support points on its boundary.
+// When the nr points admit no ball through all of them (a degenerate set), the
+// smallest ball through a subset that still contains the others
+struct Pts4 {
+    float p[4][3];
+};
+struct Ball4 {
+    float c[3], r;
+};
+__device__ __noinline__ Ball4 trivial_ball_subsets(int nr, Pts4 R, Ball4 cur) {
     const float zr[4] = {0, 0, 0, 0};
-    if (nr == 0) {
-        c[0] = c[1] = c[2] = 0;
-        rad = -1.0f;
-        return;
-    }
-    if (support_ball_dev(nr, R, zr, c, rad)) return;
     float best = -1;
     for (int mask = 1; mask < (1 << nr); ++mask) {
         float sub[4][3];
         int k = 0;
         for (int i = 0; i < nr; ++i)
             if (mask & (1 << i)) {
-                for (int d = 0; d < 3; ++d) sub[k][d] = R[i][d];
+                for (int d = 0; d < 3; ++d) sub[k][d] = R.p[i][d];
                 ++k;
             }
         float cc[3], rr;
         if (!support_ball_dev(k, sub, zr, cc, rr)) continue;
         bool ok = true;
         for (int i = 0; i < nr; ++i)
-            if (dist3f_dev(R[i], cc) > rr * (1.0f + kMebIn)) {
+            if (dist3f_dev(R.p[i], cc) > rr * (1.0f + kMebIn)) {
                 ok = false;
                 break;
             }
         if (ok && (best < 0 || rr < best)) {
             best = rr;
-            c[0] = cc[0]; c[1] = cc[1]; c[2] = cc[2];
-            rad = rr;
+            cur.c[0] = cc[0]; cur.c[1] = cc[1]; cur.c[2] = cc[2];
+            cur.r = rr;
         }
     }
+    return cur;
+}
+template <int NR>
+__device__ __forceinline__ void trivial_ball_dev(const float (&R)[4][3], float (&c)[3], float& rad) {
+    const float zr[4] = {0, 0, 0, 0};
+    if (NR == 0) {
+        c[0] = c[1] = c[2] = 0;
+        rad = -1.0f;
+        return;
+    }
+    if (support_ball_k<NR == 0 ? 1 : NR>(R, zr, c, rad)) return;
+    Pts4 P;
+    Ball4 cur;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) P.p[i][d] = R[i][d];
+    cur.c[0] = c[0]; cur.c[1] = c[1]; cur.c[2] = c[2];
+    cur.r = rad;
+    cur = trivial_ball_subsets(NR, P, cur);
+    c[0] = cur.c[0]; c[1] = cur.c[1]; c[2] = cur.c[2];
+    rad = cur.r;
 }
 
 __device__ inline bool in_ball_dev(const float p[3], const float c[3], float rad) {
@@ -592,26 +659,26 @@ __device__ int first_outside(const LeafPts& P, int from, int to, const float c[3
     return -1;
 }
 
-__device__ void meb_points_warp(const LeafPts& P, int n, float c[3], float& rad, int lane) {
+__device__ __noinline__ void meb_points_warp(const LeafPts& P, int n, float c[3], float& rad, int lane) {
     float R[4][3];
     float c0[3], r0, c1[3], r1, c2[3], r2, c3[3], r3;
-    trivial_ball_dev(0, R, c0, r0);
+    trivial_ball_dev<0>(R, c0, r0);
     int i = first_outside(P, 0, n, c0, r0, lane);
     while (i >= 0) {
         P.get(i, R[0]);
-        trivial_ball_dev(1, R, c1, r1);
+        trivial_ball_dev<1>(R, c1, r1);
         int j = first_outside(P, 0, i, c1, r1, lane);
         while (j >= 0) {
             P.get(j, R[1]);
-            trivial_ball_dev(2, R, c2, r2);
+            trivial_ball_dev<2>(R, c2, r2);
             int k = first_outside(P, 0, j, c2, r2, lane);
             while (k >= 0) {
                 P.get(k, R[2]);
-                trivial_ball_dev(3, R, c3, r3);
+                trivial_ball_dev<3>(R, c3, r3);
                 int l = first_outside(P, 0, k, c3, r3, lane);
                 while (l >= 0) {
                     P.get(l, R[3]);
-                    trivial_ball_dev(4, R, c3, r3);
+                    trivial_ball_dev<4>(R, c3, r3);
                     l = first_outside(P, l + 1, k, c3, r3, lane);
                 }
                 for (int d = 0; d < 3; ++d) c2[d] = c3[d];
@@ -676,23 +743,23 @@ __device__ inline void cp3(float d[3], const float s[3]) {
 __device__ void meb_points_mtf_warp(float (*L)[3], int n, float c[3], float& rad, int lane) {
     float R[4][3];
     float c0[3], r0, c1[3], r1, c2[3], r2, c3[3], r3;
-    trivial_ball_dev(0, R, c0, r0);
+    trivial_ball_dev<0>(R, c0, r0);
     for (int i0 = first_outside_buf(L, 0, n, c0, r0, lane); i0 >= 0;
          i0 = first_outside_buf(L, i0 + 1, n, c0, r0, lane)) {
         cp3(R[0], L[i0]);
-        trivial_ball_dev(1, R, c1, r1);
+        trivial_ball_dev<1>(R, c1, r1);
         for (int i1 = first_outside_buf(L, 0, i0, c1, r1, lane); i1 >= 0;
              i1 = first_outside_buf(L, i1 + 1, i0, c1, r1, lane)) {
             cp3(R[1], L[i1]);
-            trivial_ball_dev(2, R, c2, r2);
+            trivial_ball_dev<2>(R, c2, r2);
             for (int i2 = first_outside_buf(L, 0, i1, c2, r2, lane); i2 >= 0;
                  i2 = first_outside_buf(L, i2 + 1, i1, c2, r2, lane)) {
                 cp3(R[2], L[i2]);
-                trivial_ball_dev(3, R, c3, r3);
+                trivial_ball_dev<3>(R, c3, r3);
                 for (int i3 = first_outside_buf(L, 0, i2, c3, r3, lane); i3 >= 0;
                      i3 = first_outside_buf(L, i3 + 1, i2, c3, r3, lane)) {
                     cp3(R[3], L[i3]);
-                    trivial_ball_dev(4, R, c3, r3);
+                    trivial_ball_dev<4>(R, c3, r3);
                     move_to_front(L, i3, lane);
                 }
                 cp3(c2, c3);
@@ -713,7 +780,7 @@ __device__ void meb_points_mtf_warp(float (*L)[3], int n, float c[3], float& rad
 
 // one warp per leaf: smallest enclosing ball, exact radius, mass, centre of mass
 constexpr int kGeoWarps = 4;
-__global__ void __launch_bounds__(kGeoWarps * 32) k_leaf_geometry(const d4* __restrict__ xm, Cells c,
+__global__ void __maxnreg__(168) k_leaf_geometry(const d4* __restrict__ xm, Cells c,
                                                                  const int* __restrict__ leaves, int nleaves,
                                                                  unsigned* status, bool keep_centre) {
     __shared__ float pbuf[kGeoWarps][kMebBuf][3];
@@ -827,34 +894,50 @@ __global__ void __launch_bounds__(kMebWarps * 32) k_internal_meb(Cells c, int le
     if (nch == 0) return;  // leaves are done
     const int ch = c.child[cell];
     const d4 o = c.sr[ch];
+    // the daughters' balls relative to the first one (registers: loops over all 8 slots)
     float cen[8][3], rad[8];
-    for (int i = 0; i < nch; ++i) {
-        d4 v = c.sr[ch + i];
-        cen[i][0] = (float)(v.x - o.x);
-        cen[i][1] = (float)(v.y - o.y);
-        cen[i][2] = (float)(v.z - o.z);
-        rad[i] = (float)v.w;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        cen[i][0] = cen[i][1] = cen[i][2] = rad[i] = 0.f;
+        if (i < nch) {
+            const d4 v = c.sr[ch + i];
+            cen[i][0] = (float)(v.x - o.x);
+            cen[i][1] = (float)(v.y - o.y);
+            cen[i][2] = (float)(v.z - o.z);
+            rad[i] = (float)v.w;
+        }
     }
     float best = -1, bc[3] = {0, 0, 0};
     int bmask = 1 << 30;
     const int mask = 1 + lane + 32 * wid;
     if (mask < (1 << nch) && __popc(mask) <= 4) {
-        float sc[4][3], sr[4];
+        // the k-th daughter of the mask into slot k of the support set
+        float sc[4][3] = {}, sr[4] = {};
         int k = 0;
-        for (int i = 0; i < nch; ++i)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
             if (mask & (1 << i)) {
-                for (int d = 0; d < 3; ++d) sc[k][d] = cen[i][d];
-                sr[k] = rad[i];
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (k == t) {
+                        sc[t][0] = cen[i][0]; sc[t][1] = cen[i][1]; sc[t][2] = cen[i][2];
+                        sr[t] = rad[i];
+                    }
                 ++k;
             }
         float cc[3], rr;
-        if (support_ball_dev(k, sc, sr, cc, rr)) {
+        bool found;
+        switch (k) {
+            case 1: found = support_ball_k<1>(sc, sr, cc, rr); break;
+            case 2: found = support_ball_k<2>(sc, sr, cc, rr); break;
+            case 3: found = support_ball_k<3>(sc, sr, cc, rr); break;
+            default: found = support_ball_k<4>(sc, sr, cc, rr); break;
+        }
+        if (found) {
             bool ok = true;
-            for (int i = 0; i < nch; ++i)
-                if (dist3f_dev(cen[i], cc) + rad[i] > rr * (1.0f + kMebIn)) {
-                    ok = false;
-                    break;
-                }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < nch && dist3f_dev(cen[i], cc) + rad[i] > rr * (1.0f + kMebIn)) ok = false;
             if (ok) {
                 best = rr;
                 bmask = mask;

@@ -37,6 +37,122 @@ __device__ inline long long warp_reserve(unsigned mine, unsigned long long* coun
 
 enum : int { kActNone = 0, kActM2L, kActP2P, kActSelf, kActSplitA, kActSplitB };
 
+// ---------------------------------------------------------------- single-precision pre-test
+// The decisions theta < 1 (eq. 9) and E~_{A->B} M_A / r^2 < eps minscale_B (eqs. 15-18)
+// are first taken in FP32 with bounds on the rounding error; a value within a margin of
+// its threshold, or outside the range in which the bounds hold, leaves the decision to
+// the FP64 form below, so every decision is the one FP64 takes.
+//  r: each centre difference is formed from two-float centres (high parts, then low
+//     parts) with an error of at most 2^-23 |d| + 2^-46 (|a| + |b|); requiring
+//     2^-24 sum|coordinates| < r keeps the relative error of r below 2^-19
+//  theta = (rho_A + rho_B) / r: relative error below 3e-6 (rsqrt.approx within 2^-22);
+//     margin 1e-5
+//  E~ M_A / r^2 = fac P_0 h / r^2 with h = sum_k C(p,k) Pn_k u_A^k u_B^(p-k), u = rho / r < 1
+//     and Pn_k = P_k / (P_0 rho_A^k) in [0, 1]: every factor of a term carries at most
+//     3e-6, so h is within (p + 3) 3e-6 < 6e-5 for p <= 16; margin 2e-4; an h below
+//     2^-90 (underflowed terms) is left to FP64
+constexpr float kThetaMargin = 1e-5f, kMacMargin = 2e-4f;
+
+struct PascalF {
+    float c[kMaxP + 1][kMaxP + 1];
+    constexpr PascalF() : c{} {
+        for (int q = 0; q <= kMaxP; ++q) {
+            c[q][0] = 1.f;
+            for (int k = 1; k <= q; ++k) c[q][k] = c[q - 1][k - 1] + (k < q ? c[q - 1][k] : 0.f);
+        }
+    }
+};
+// C(q, k) for q <= 20: integers below 2^24, exact in FP32
+static __constant__ PascalF c_pascalf = PascalF();
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// 1: accepted, 0: not accepted, -1: left to FP64
+__device__ __forceinline__ int accept_fp32(const WalkParams& wp, int A, int B) {
+    const float4 ah = wp.fc[2 * A], al = wp.fc[2 * A + 1];
+    const float4 bh = wp.fc[2 * B], bl = wp.fc[2 * B + 1];
+    const float dx = (bh.x - ah.x) + (bl.x - al.x);
+    const float dy = (bh.y - ah.y) + (bl.y - al.y);
+    const float dz = (bh.z - ah.z) + (bl.z - al.z);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float e = (fabsf(ah.x) + fabsf(ah.y) + fabsf(ah.z) + fabsf(bh.x) + fabsf(bh.y) + fabsf(bh.z)) * 0x1p-24f;
+    if (!(r2 >= 0x1p-100f) || !(e * e < r2)) return -1;
+    const float rinv = rsqrt_approx(r2);
+    const float ra = ah.w, rb = bh.w;
+    const float th = (ra + rb) * rinv;
+    if (th >= 1.0f + kThetaMargin) return 0;
+    if (!(th < 1.0f - kThetaMargin)) return -1;
+    if (wp.mac == kMacEstimate) return 1;
+    const float* Pn = wp.fP + (size_t)A * wp.fstride;
+    const float rhs = wp.fP[(size_t)B * wp.fstride + wp.p + 1];
+    const float ua = ra * rinv, ub = rb * rinv;
+    const float* C = c_pascalf.c[wp.p];
+    float h = 0.f, uak = 1.f;
+    for (int k = 0; k <= wp.p; ++k) {
+        h = h * ub + C[k] * (Pn[k] * uak);
+        uak *= ua;
+    }
+    if (!(h >= 0x1p-90f)) return -1;
+    const float mx = ra > rb ? ra : rb;
+    const float fac = (ra + rb > 0.f) ? 8.0f * mx / (ra + rb) : 8.0f;
+    const float lhs = fac * h * al.w * (rinv * rinv);
+    if (lhs < rhs * (1.0f - kMacMargin)) return 1;
+    if (lhs > rhs * (1.0f + kMacMargin)) return 0;
+    return -1;
+}
+
+// the single-precision view of one cell; a cell out of the bounds' range gets NaN radius
+// and P_0, which sends its pairs to FP64
+__global__ void k_walk_prep(Cells c, const d4* __restrict__ cen, const double* __restrict__ P, int p, double eps,
+                            int nc, float4* __restrict__ fc, float* __restrict__ fP, int fstride) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= nc) return;
+    const d4 v = cen[cell];
+    const double lim = 0x1p100;
+    bool ok = fabs(v.x) <= lim && fabs(v.y) <= lim && fabs(v.z) <= lim && v.w >= 0.0 && v.w <= lim;
+    const float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
+    const float lx = (float)(v.x - (double)hx), ly = (float)(v.y - (double)hy), lz = (float)(v.z - (double)hz);
+    float p0 = 0.f;
+    if (P) {
+        const double* Pc = P + (size_t)cell * (p + 1);
+        float* row = fP + (size_t)cell * fstride;
+        const double P0 = Pc[0];
+        bool okp = P0 >= 0x1p-100 && P0 <= lim;
+        const double rinv = v.w > 0.0 ? 1.0 / v.w : 0.0;
+        double sc = okp ? 1.0 / P0 : 0.0;
+        row[0] = 1.f;
+        for (int k = 1; k <= p; ++k) {
+            if (v.w > 0.0) {
+                sc *= rinv;
+                const double t = Pc[k] * sc;
+                okp = okp && t >= 0.0 && t <= 2.0;
+                row[k] = (float)t;
+            } else {
+                okp = okp && Pc[k] == 0.0;
+                row[k] = 0.f;
+            }
+        }
+        const double rhs = eps * c.minscale[cell];
+        row[p + 1] = (rhs >= 0x1p-100 && rhs <= lim) ? (float)rhs : __int_as_float(0x7fc00000);
+        p0 = okp ? (float)P0 : __int_as_float(0x7fc00000);
+    }
+    const float rho = ok ? (float)v.w : __int_as_float(0x7fc00000);
+    if (!ok) p0 = __int_as_float(0x7fc00000);
+    fc[2 * cell] = make_float4(hx, hy, hz, rho);
+    fc[2 * cell + 1] = make_float4(lx, ly, lz, p0);
+}
+
+void launch_walk_prep(Cells c, const d4* cen, const double* P, int p, double eps, int nc, float4* fc, float* fP,
+                      cudaStream_t s) {
+    if (nc <= 0) return;
+    k_walk_prep<<<(nc + 127) / 128, 128, 0, s>>>(c, cen, P, p, eps, nc, fc, fP, walk_fstride(p));
+    note_launch();
+}
+
 // nfront_dev (nullable): the frontier's length on the device (read here, capped at the
 // buffer's capacity), else nfront; the next frontier is counted in *out_cnt
 __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in, long long nfront,
@@ -49,6 +165,10 @@ __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in
         if (*(volatile const unsigned long long*)&wb.counters[3]) return;
         nfront = (long long)nd < wb.front_cap ? (long long)nd : wb.front_cap;
     }
+    // cnt_A cnt_B < p2p_thresh as integers: the product of two counts is exact in FP64
+    // below 2^53 and far above any threshold beyond it
+    const double tc = ceil(wp.p2p_thresh);
+    const long long thr = tc <= 0.0 ? 0LL : (tc >= 0x1p62 ? (1LL << 62) : (long long)tc);
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < nfront; base += stride) {
         long long i = base + threadIdx.x;
@@ -57,52 +177,55 @@ __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in
             int2 pr = front_in[i];
             A = pr.x;
             B = pr.y;
-            int cntA = c.count[A], cntB = c.count[B];
+            const long long cntA = c.count[A], cntB = c.count[B];
             nchA = c.nchild[A];
             nchB = c.nchild[B];
             chA = c.child[A];
             chB = c.child[B];
-            if ((double)cntA * (double)cntB < wp.p2p_thresh) {
+            if (cntA * cntB < thr) {
                 act = kActP2P;  // reading R-p2p: direct summation is preferable
             } else if (A == B) {
                 act = nchA ? kActSelf : kActP2P;
             } else {
-                d4 za = wp.use_com ? c.cr[A] : c.sr[A];
-                d4 sb = wp.use_com ? c.cr[B] : c.sr[B];
-                double ra = za.w, rb = sb.w;
-                double dx = sb.x - za.x, dy = sb.y - za.y, dz = sb.z - za.z;
-                double r = sqrt(dx * dx + dy * dy + dz * dz);
-                double theta = (ra + rb) / r;  // eq. (9)
-                bool accept;
-                if (wp.mac == FMM_MAC_THETA) accept = theta < wp.theta_crit;
-                else if (!(theta < 1.0)) accept = false;
-                else if (wp.mac == kMacEstimate) accept = true;
-                else {
-                    // E~_{A->B} M_A / r^2 (eqs. 15-17) without dividing by M_A:
-                    // 8 max/(rhoA+rhoB) * sum_k C(p,k) P_k rhoB^{p-k} / r^{p+2}
-                    const double* P = wp.P + (size_t)A * (wp.p + 1);
-                    double rinv = 1.0 / r, u = rb * rinv, rk = 1.0, h = 0.0;
-                    for (int k = 0; k <= wp.p; ++k) {
-                        h = h * u + wp.binom[k] * (P[k] * rk);
-                        rk *= rinv;
-                    }
-                    double mx = ra > rb ? ra : rb;
-                    double fac = (ra + rb > 0) ? 8.0 * mx / (ra + rb) : 8.0;
-                    double lhs = fac * h / (r * r);
-                    const double rhs = wp.eps * c.minscale[B];
-                    accept = lhs < rhs;  // eqs. (18a,b)
-                    if (accept && wp.adaptive) {
-                        // the lowest order q whose E~ (eq. 17 with q for p) passes as well
-                        for (int q = wp.p_lo; q < wp.p; ++q) {
-                            const double* C = wp.pascal + q * (kMaxP + 1);
-                            double hq = 0.0, rq = 1.0;
-                            for (int k = 0; k <= q; ++k) {
-                                hq = hq * u + C[k] * (P[k] * rq);
-                                rq *= rinv;
-                            }
-                            if (fac * hq / (r * r) < rhs) {
-                                A |= q << kM2LOrderShift;
-                                break;
+                const d4* cen = wp.use_com ? c.cr : c.sr;
+                const int dec = (wp.fc && !wp.adaptive && wp.mac != FMM_MAC_THETA) ? accept_fp32(wp, A, B) : -1;
+                bool accept = dec == 1;
+                if (dec < 0) {
+                    const d4 za = cen[A], sb = cen[B];
+                    double ra = za.w, rb = sb.w;
+                    double dx = sb.x - za.x, dy = sb.y - za.y, dz = sb.z - za.z;
+                    double r = sqrt(dx * dx + dy * dy + dz * dz);
+                    double theta = (ra + rb) / r;  // eq. (9)
+                    if (wp.mac == FMM_MAC_THETA) accept = theta < wp.theta_crit;
+                    else if (!(theta < 1.0)) accept = false;
+                    else if (wp.mac == kMacEstimate) accept = true;
+                    else {
+                        // E~_{A->B} M_A / r^2 (eqs. 15-17) without dividing by M_A:
+                        // 8 max/(rhoA+rhoB) * sum_k C(p,k) P_k rhoB^{p-k} / r^{p+2}
+                        const double* P = wp.P + (size_t)A * (wp.p + 1);
+                        double rinv = 1.0 / r, u = rb * rinv, rk = 1.0, h = 0.0;
+                        for (int k = 0; k <= wp.p; ++k) {
+                            h = h * u + wp.binom[k] * (P[k] * rk);
+                            rk *= rinv;
+                        }
+                        double mx = ra > rb ? ra : rb;
+                        double fac = (ra + rb > 0) ? 8.0 * mx / (ra + rb) : 8.0;
+                        double lhs = fac * h / (r * r);
+                        const double rhs = wp.eps * c.minscale[B];
+                        accept = lhs < rhs;  // eqs. (18a,b)
+                        if (accept && wp.adaptive) {
+                            // the lowest order q whose E~ (eq. 17 with q for p) passes as well
+                            for (int q = wp.p_lo; q < wp.p; ++q) {
+                                const double* C = wp.pascal + q * (kMaxP + 1);
+                                double hq = 0.0, rq = 1.0;
+                                for (int k = 0; k <= q; ++k) {
+                                    hq = hq * u + C[k] * (P[k] * rq);
+                                    rq *= rinv;
+                                }
+                                if (fac * hq / (r * r) < rhs) {
+                                    A |= q << kM2LOrderShift;
+                                    break;
+                                }
                             }
                         }
                     }
@@ -110,7 +233,11 @@ __global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in
                 if (accept) act = kActM2L;
                 else if (!nchA && !nchB) act = kActP2P;
                 else {
-                    bool split_a = ra >= rb;
+                    // rounding to FP32 keeps the order of distinct radii except for ties
+                    bool split_a;
+                    const float fa = dec >= 0 ? wp.fc[2 * A].w : 0.f, fb = dec >= 0 ? wp.fc[2 * B].w : 0.f;
+                    if (dec >= 0 && fa != fb) split_a = fa > fb;
+                    else split_a = cen[A].w >= cen[B].w;
                     if (!nchA) split_a = false;
                     if (!nchB) split_a = true;
                     act = split_a ? kActSplitA : kActSplitB;
