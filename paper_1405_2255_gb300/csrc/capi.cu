@@ -426,13 +426,11 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     const int pe = 1, nco = ncoef(pe);
     TRY(ensure(ctx->F1, sizeof(double) * nco * (size_t)nc));
     // multipoles about the centres of mass: the masses and centres of the geometry pass
+    const bool mixed = ctx->prm.precision == FMM_PREC_MIXED;
     launch_est_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), nc, c,
-                   P<double>(ctx->F1), s);
-    for (int L = 1; L < nlev; ++L) launch_l2l_level(c, c.cr, ctx->lev_start[L], ctx->lev_start[L + 1], pe, P<double>(ctx->F1), s);
-    launch_l2p(P<d4>(ctx->xm), c, c.cr, P<int>(ctx->leaves), ctx->nleaves, pe, P<double>(ctx->F1),
-               P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
-    if (ctx->prm.precision == FMM_PREC_MIXED)
-    {
+                   P<double>(ctx->F1), s, mixed ? P<float4>(ctx->walkf) : nullptr);
+    // (the p = 1 L2L is folded into launch_est_scale)
+    if (mixed) {
         TRY(ensure(ctx->p2p_tmp, p2p_tmp_bytes(ctx->nleaves)));
         launch_p2p_mixed(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), ctx->n, c, P<int2>(ctx->est_p2p),
                          P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
@@ -441,7 +439,7 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->est_p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
                         P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
-    launch_norm_scale(nullptr, P<double>(ctx->acc_far), P<double>(ctx->acc_near), n, scale, s);
+    launch_est_scale(c, P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->F1), P<double>(ctx->acc_near), scale, s);
     return 0;
 }
 

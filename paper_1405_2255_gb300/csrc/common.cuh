@@ -154,6 +154,14 @@ __device__ inline void ff_add_shfl(ff& a, int o) {
     a.hi = __fadd_rn(s.hi, lo);
     a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
 }
+// a += the (hi, lo) of lane src
+__device__ inline void ff_add_lane(ff& a, int src) {
+    float h = __shfl_sync(0xffffffffu, a.hi, src), l = __shfl_sync(0xffffffffu, a.lo, src);
+    ff s = two_sum(a.hi, h);
+    float lo = __fadd_rn(__fadd_rn(a.lo, l), s.lo);
+    a.hi = __fadd_rn(s.hi, lo);
+    a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
+}
 __device__ inline void ff_acc(ff& a, float v) {
     ff s = two_sum(a.hi, v);
     float lo = __fadd_rn(a.lo, s.lo);

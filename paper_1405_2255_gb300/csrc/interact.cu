@@ -962,6 +962,7 @@ __device__ __forceinline__ void p2p_tile_r(const float* __restrict__ T, int ng, 
                                            AccPk& a) {
     if (R == 1) p2p_tile<TWO_FLOAT, GUARD, 1>(T, ng, r0, b, a);
     else if (R == 2) p2p_tile<TWO_FLOAT, GUARD, 2>(T, ng, r0, b, a);
+    else if (R == 3) p2p_tile<TWO_FLOAT, GUARD, 3>(T, ng, r0, b, a);
     else p2p_tile<TWO_FLOAT, GUARD, 4>(T, ng, r0, b, a);
 }
 
@@ -1055,12 +1056,16 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float* __
         const int leaf = order[w];
         if (!cell_active(c, leaf)) continue;
         const int first = c.first[leaf], count = c.count[leaf];
+        // chunks of up to 32 sinks, one pass over the sources each (every pass walks the
+        // source cells again); a chunk of S sinks takes R = 32 / S replicas (up to 4), which
+        // take the groups of a tile in turn
         for (int s0 = 0; s0 < count; s0 += 32) {
             const int chunk = min(32, count - s0);
-            const int R = chunk <= 8 ? 4 : (chunk <= 16 ? 2 : 1);
-            const int S = 32 / R;
-            const int sink = lane % S, rep = lane / S;
-            const bool active = sink < chunk;
+            const int R = chunk <= 8 ? 4 : (chunk <= 10 ? 3 : (chunk <= 16 ? 2 : 1));
+            const int S = R == 3 ? 10 : 32 / R;
+            // lanes past S * R repeat replica 0's work; their sums are not used
+            const int sink = lane % S, rep = lane / S < R ? lane / S : 0;
+            const bool active = sink < chunk && lane < S * R;
             const int i = first + s0 + sink;
             float bhx = 0, bhy = 0, bhz = 0, blx = 0, bly = 0, blz = 0;
             if (active) {
@@ -1138,11 +1143,17 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float* __
                 nt = nx;
                 guard = guard_next;
             }
-            // add the replicas' partial sums (lanes sink, sink + S, ...)
-            for (int o = S; o < 32; o <<= 1) {
-                ff_add_shfl(aps, o); ff_add_shfl(aax, o); ff_add_shfl(aay, o); ff_add_shfl(aaz, o);
+            // add the replicas' partial sums (lanes sink + S, sink + 2 S, ... into lane sink);
+            // only lanes below S accumulate, so every lane read still holds its own sum
+            for (int j = 1; j < R; ++j) {
+                const int src = min(lane + j * S, 31);
+                ff tps = aps, tax = aax, tay = aay, taz = aaz;
+                ff_add_lane(tps, src); ff_add_lane(tax, src); ff_add_lane(tay, src); ff_add_lane(taz, src);
+                if (lane < S) {
+                    aps = tps; aax = tax; aay = tay; aaz = taz;
+                }
             }
-            if (active && rep == 0) {
+            if (active && lane < S) {
                 psi[i] = (double)aps.hi + (double)aps.lo;
                 acc[3 * (size_t)i] = (double)aax.hi + (double)aax.lo;
                 acc[3 * (size_t)i + 1] = (double)aay.hi + (double)aay.lo;
@@ -1288,9 +1299,113 @@ __global__ void k_est_m2l(const int2* __restrict__ list, const int* __restrict__
     F1[4 * (size_t)B + 2] = fz;
     F1[4 * (size_t)B + 3] = fx;
 }
+// The same sums in single precision (mixed mode, where the estimate's P2P is FP32 too):
+// one warp per sink cell, lanes over its sources, two-float centre differences from the
+// walk's single-precision view (fc[2 c] = high parts and rho, fc[2 c + 1] = low parts
+// and M); a pair with a cell outside that view's range (NaN rho) is summed in FP64.
+// Lane partial sums are added in a fixed butterfly order.
+__global__ void k_est_m2l_f32(const int2* __restrict__ list, const int* __restrict__ seg_start,
+                              const int* __restrict__ seg_end, int ncells, Cells c, const float4* __restrict__ fc,
+                              double* __restrict__ F1) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int B = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; B < ncells; B += nw) {
+        const int e0 = seg_start[B], e1 = seg_end[B];
+        if (e0 >= e1) {
+            if (lane < 4) F1[4 * (size_t)B + lane] = 0.0;
+            continue;
+        }
+        const float4 bh = fc[2 * B], bl = fc[2 * B + 1];
+        float f0 = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const int A = list[e].x;
+            const float4 ah = fc[2 * A], al = fc[2 * A + 1];
+            if (ah.w == ah.w && bh.w == bh.w) {
+                const float x = (bh.x - ah.x) + (bl.x - al.x);
+                const float y = (bh.y - ah.y) + (bl.y - al.y);
+                const float z = (bh.z - ah.z) + (bl.z - al.z);
+                const float rinv = rsqrt_ftz(x * x + y * y + z * z);
+                const float q = al.w * rinv, q3 = q * rinv * rinv;
+                f0 += q;
+                fx += q3 * x;
+                fy += q3 * y;
+                fz += q3 * z;
+            } else {
+                const d4 sb = c.cr[B], za = c.cr[A];
+                const double x = sb.x - za.x, y = sb.y - za.y, z = sb.z - za.z;
+                const double rinv = 1.0 / sqrt(x * x + y * y + z * z);
+                const double q = c.mass[A] * rinv, q3 = q * rinv * rinv;
+                f0 += (float)q;
+                fx += (float)(q3 * x);
+                fy += (float)(q3 * y);
+                fz += (float)(q3 * z);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            f0 += __shfl_xor_sync(0xffffffffu, f0, o);
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (lane == 0) {
+            F1[4 * (size_t)B] = f0;
+            F1[4 * (size_t)B + 1] = fy;
+            F1[4 * (size_t)B + 2] = fz;
+            F1[4 * (size_t)B + 3] = fx;
+        }
+    }
+}
 void launch_est_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* F1,
-                    cudaStream_t s) {
-    if (ncells > 0) k_est_m2l<<<(ncells + 127) / 128, 128, 0, s>>>(list, seg_start, seg_end, ncells, c, F1); note_launch();
+                    cudaStream_t s, const float4* fc) {
+    if (ncells <= 0) return;
+    if (fc) {
+        const long long warps = ncells;
+        const unsigned g = (unsigned)std::min<long long>((warps + 7) / 8, 152LL * 16);
+        k_est_m2l_f32<<<g, 256, 0, s>>>(list, seg_start, seg_end, ncells, c, fc, F1);
+    } else {
+        k_est_m2l<<<(ncells + 127) / 128, 128, 0, s>>>(list, seg_start, seg_end, ncells, c, F1);
+    }
+    note_launch();
+}
+
+// The estimate's far field at p = 1.  L2L (eq. 5) at p = 1 passes F_1^m down unchanged
+// (only the k = 0 term, Upsilon_0^0 = 1, reaches n = 1), so a leaf's F_1 is its own M2L
+// result plus its parent's F_1, which is added here along the ancestor chain, root first,
+// in the order of the level-by-level pass.  L2P (eq. 7) at p = 1 gives the same
+// acceleration at every particle of the leaf, a = -(Re F_1^1, Im F_1^1, F_1^0); the scale
+// is |a_far + a_near| of each particle.  One warp per leaf.
+__global__ void k_est_scale(Cells c, const int* __restrict__ leaves, int nleaves, const double* __restrict__ F1,
+                            const double* __restrict__ an, double* __restrict__ scale) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nleaves; t += nw) {
+        const int cell = leaves[t];
+        if (!cell_active(c, cell)) continue;
+        int chain[24], depth = 0;  // at most 22 levels: 21 key bits per axis below the root
+        for (int a = cell; a >= 0 && depth < 24; a = c.parent[a]) chain[depth++] = a;
+        double f1 = 0.0, f2 = 0.0, f3 = 0.0;
+        for (int k = depth - 1; k >= 0; --k) {
+            const double* f = F1 + 4 * (size_t)chain[k];
+            f1 = f[1] + f1;
+            f2 = f[2] + f2;
+            f3 = f[3] + f3;
+        }
+        const double ax = -f3, ay = -f1, az = -f2;
+        const int first = c.first[cell], count = c.count[cell];
+        for (int j = lane; j < count; j += 32) {
+            const size_t i = (size_t)first + j;
+            const double x = ax + an[3 * i], y = ay + an[3 * i + 1], z = az + an[3 * i + 2];
+            scale[i] = sqrt(x * x + y * y + z * z);
+        }
+    }
+}
+void launch_est_scale(Cells c, const int* leaves, int nleaves, const double* F1, const double* acc_near,
+                      double* scale, cudaStream_t s) {
+    if (nleaves <= 0) return;
+    const unsigned g = (unsigned)std::min<long long>(((long long)nleaves + 7) / 8, 152LL * 16);
+    k_est_scale<<<g, 256, 0, s>>>(c, leaves, nleaves, F1, acc_near, scale);
+    note_launch();
 }
 void launch_f_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* Ff,
                   cudaStream_t s) {

@@ -115,7 +115,7 @@ struct WalkParams {
 // row stride of fP for order p (P_0..P_p, eps * minscale, padded to float4)
 inline int walk_fstride(int p) { return (p + 2 + 3) & ~3; }
 // fill the single-precision view: centres from cen (sr, or cr for the estimator); with P
-// (nullable) also the normalised powers and eps * minscale
+// (nullable) also the normalised powers and eps * minscale, without it the masses
 void launch_walk_prep(Cells c, const d4* cen, const double* P, int p, double eps, int nc, float4* fc, float* fP,
                       cudaStream_t s);
 // M2L list entries of an adaptive-order walk carry the pair's order q in the top bits of
@@ -224,7 +224,10 @@ void launch_f_p2p(const d4* xm, Cells c, const int2* list, const int* seg_start,
 // p = 1 M2L of the acceleration estimate from the monopoles about the centres of mass
 // (the dipole vanishes there) into F1[nc][4]
 void launch_est_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* F1,
-                    cudaStream_t s);
+                    cudaStream_t s, const float4* fc = nullptr);
+// the estimate's far field at p = 1 plus its near field, as the scale |a| per sorted particle
+void launch_est_scale(Cells c, const int* leaves, int nleaves, const double* F1, const double* acc_near,
+                      double* scale, cudaStream_t s);
 // |far + near| of the p = 1 estimate into the per-particle scale
 void launch_norm_scale(const double* psi_far, const double* acc_far, const double* acc_near, int n,
                        double* scale, cudaStream_t s);

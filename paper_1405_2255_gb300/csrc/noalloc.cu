@@ -295,14 +295,13 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
             launch_p2m(r.xm, r.c, r.c.cr, r.leaves, r.nleaves, 1, M1, s);
             for (int L = nl - 1; L >= 0; --L) launch_m2m_level(r.c, r.c.cr, r.lev[L], r.lev[L + 1], 1, M1, s);
             launch_m2l(est_m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.cr, M1, 1, F1, s);
-            for (int L = 1; L < nl; ++L) launch_l2l_level(r.c, r.c.cr, r.lev[L], r.lev[L + 1], 1, F1, s);
-            launch_l2p(r.xm, r.c, r.c.cr, r.leaves, r.nleaves, 1, F1, psi_far, acc_far, s);
+            // (the p = 1 L2L is folded into launch_est_scale)
             if (prm.precision == FMM_PREC_MIXED)
                 launch_p2p_mixed(r.xm, xhi, xlo, n, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near,
                                  acc_near, 0, p2p_tmp, s);
             else
                 launch_p2p_fp64(r.xm, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
-            launch_norm_scale(nullptr, acc_far, acc_near, n, scale, s);
+            launch_est_scale(r.c, r.leaves, r.nleaves, F1, acc_near, scale, s);
         }
         launch_minscale_leaves(scale, r.c, r.leaves, r.nleaves, s);
         for (int L = nl - 1; L >= 0; --L) launch_minscale_level(r.c, r.lev[L], r.lev[L + 1], s);

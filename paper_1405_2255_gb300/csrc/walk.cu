@@ -106,7 +106,8 @@ __device__ __forceinline__ int accept_fp32(const WalkParams& wp, int A, int B) {
 }
 
 // the single-precision view of one cell; a cell out of the bounds' range gets NaN radius
-// and P_0, which sends its pairs to FP64
+// and P_0, which sends its pairs to FP64.  Without P (the estimator's walk) the P_0 slot
+// holds the cell's mass instead
 __global__ void k_walk_prep(Cells c, const d4* __restrict__ cen, const double* __restrict__ P, int p, double eps,
                             int nc, float4* __restrict__ fc, float* __restrict__ fP, int fstride) {
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,6 +140,11 @@ __global__ void k_walk_prep(Cells c, const d4* __restrict__ cen, const double* _
         const double rhs = eps * c.minscale[cell];
         row[p + 1] = (rhs >= 0x1p-100 && rhs <= lim) ? (float)rhs : __int_as_float(0x7fc00000);
         p0 = okp ? (float)P0 : __int_as_float(0x7fc00000);
+    }
+    else {  // the estimator's view: the cell's mass in the P_0 slot
+        const double m = c.mass[cell];
+        ok = ok && (m == 0.0 || (m >= 0x1p-100 && m <= lim));
+        p0 = (float)m;
     }
     const float rho = ok ? (float)v.w : __int_as_float(0x7fc00000);
     if (!ok) p0 = __int_as_float(0x7fc00000);
