@@ -222,7 +222,7 @@ def reference_arm(a, rank, world):
 # the same workload and parameters (summaries and commands under profiles/); None for
 # any other configuration or once the kernel has changed since the capture
 MEASURED_TRAFFIC = {
-    ("plummer", 1000000, 14, 3e-7, 80, 1.0, "mixed"): {"k_p2p_mixed": 94.14e6, "k_m2l_rot": 200.56e6},
+    ("plummer", 1000000, 14, 3e-7, 80, 1.0, "mixed"): {"k_p2p_mixed": 94.43e6, "k_m2l_rot": 198.87e6},
 }
 
 
