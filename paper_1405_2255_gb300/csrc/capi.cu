@@ -199,6 +199,15 @@ __global__ void k_leaf_compact(const int* __restrict__ flag, const int* __restri
         if (flag[i]) leaves[pos[i]] = i;
 }
 
+// the two-float copies of the sorted positions and masses (the internal radii's
+// single-precision bounds, the mixed-mode kernels)
+static int split_positions(fmm_ctx* ctx, int n, cudaStream_t s) {
+    TRY(ensure(ctx->xhi, sizeof(float4) * (size_t)n));
+    TRY(ensure(ctx->xlo, sizeof(float4) * (size_t)n));
+    launch_split_positions(P<d4>(ctx->xm), n, P<float>(ctx->xhi), P<float>(ctx->xlo), s);
+    return 0;
+}
+
 // Sec. 7.1's re-cycled tree: the previous evaluation's particle order, cells and centres
 // stay; positions and masses are gathered in that order and the radii, masses and
 // centres of mass are recomputed, so the MAC sees the true extent of every cell
@@ -212,10 +221,12 @@ static int refresh_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, 
     if (st & kStatInvalid) return fail(ctx, FMM_E_INVALID, "non-finite position or mass, or negative mass");
     Cells c = cells_of(ctx);
     const int nlev = (int)ctx->lev_start.size() - 1;
+    TRY(split_positions(ctx, n, s));
     launch_leaf_geometry(P<d4>(ctx->xm), c, P<int>(ctx->leaves), ctx->nleaves, P<unsigned>(ctx->status), s, true);
     for (int L = nlev - 1; L >= 0; --L)
-        launch_internal_geometry(P<d4>(ctx->xm), c, ctx->lev_start[L], ctx->lev_start[L + 1], n,
-                                 P<unsigned long long>(ctx->rad_tmp), P<unsigned>(ctx->status), s, true);
+        launch_internal_geometry(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), c, ctx->lev_start[L],
+                                 ctx->lev_start[L + 1], n, P<unsigned long long>(ctx->rad_tmp),
+                                 P<unsigned>(ctx->status), s, true);
     return 0;
 }
 
@@ -308,11 +319,13 @@ static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cu
     int nlev = (int)ctx->lev_start.size() - 1;
     int maxlev_cells = 0;
     for (int L = 0; L < nlev; ++L) maxlev_cells = std::max(maxlev_cells, ctx->lev_start[L + 1] - ctx->lev_start[L]);
-    TRY(ensure(ctx->rad_tmp, sizeof(unsigned long long) * 2 * (size_t)maxlev_cells));
+    TRY(ensure(ctx->rad_tmp, sizeof(unsigned long long) * rad_tmp_u64_per_cell() * (size_t)maxlev_cells));
+    TRY(split_positions(ctx, n, s));
     launch_leaf_geometry(P<d4>(ctx->xm), c, P<int>(ctx->leaves), ctx->nleaves, P<unsigned>(ctx->status), s);
     for (int L = nlev - 1; L >= 0; --L)
-        launch_internal_geometry(P<d4>(ctx->xm), c, ctx->lev_start[L], ctx->lev_start[L + 1], n,
-                                 P<unsigned long long>(ctx->rad_tmp), P<unsigned>(ctx->status), s);
+        launch_internal_geometry(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), c, ctx->lev_start[L],
+                                 ctx->lev_start[L + 1], n, P<unsigned long long>(ctx->rad_tmp),
+                                 P<unsigned>(ctx->status), s);
     return 0;
 }
 
@@ -523,11 +536,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     TRY(ensure(ctx->psi_near, sizeof(double) * n));
     TRY(ensure(ctx->acc_near, sizeof(double) * 3 * (size_t)n));
     TRY(ensure(ctx->scale_sorted, sizeof(double) * n));
-    if (prm.precision == FMM_PREC_MIXED) {
-        TRY(ensure(ctx->xhi, sizeof(float4) * n));
-        TRY(ensure(ctx->xlo, sizeof(float4) * n));
-        launch_split_positions(P<d4>(ctx->xm), n, P<float>(ctx->xhi), P<float>(ctx->xlo), s);
-    }
+    // (the two-float positions were made with the tree)
 
     // A7: acceleration scale for the MAC and its per-cell minimum
     if (prm.mac != FMM_MAC_THETA) {

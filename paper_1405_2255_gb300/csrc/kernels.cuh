@@ -72,9 +72,12 @@ void launch_split_level(const uint64_t* keys, Cells c, int lev_begin, int lev_en
 // radii, masses and centres of mass for the particles' new positions
 void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves, unsigned* status,
                           cudaStream_t s, bool keep_centre = false);
-void launch_internal_geometry(const d4* xm, Cells c, int lev_begin, int lev_end, int n,
-                              unsigned long long* rad_tmp, unsigned* status, cudaStream_t s,
+// xhi/xlo: the two-float positions (launch_split_positions); rad_tmp: rad_tmp_u64_per_cell()
+// words per cell of the largest level
+void launch_internal_geometry(const d4* xm, const float* xhi, const float* xlo, Cells c, int lev_begin, int lev_end,
+                              int n, unsigned long long* rad_tmp, unsigned* status, cudaStream_t s,
                               bool keep_centre = false);
+size_t rad_tmp_u64_per_cell();
 
 // ---------------------------------------------------------------- upward (upward.cu)
 // P2M (eq. 3c) at leaves about centre cen (sr or cr), M2M (eq. 4) for the internal

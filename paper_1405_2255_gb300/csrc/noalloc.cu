@@ -219,7 +219,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     int* leaf_flag = A.take<int>(nc);
     int* leaf_pos = A.take<int>(nc);
     r.leaves = A.take<int>(nc);
-    unsigned long long* rad_tmp = A.take<unsigned long long>(2 * (size_t)nc);
+    unsigned long long* rad_tmp = A.take<unsigned long long>(rad_tmp_u64_per_cell() * (size_t)nc);
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the tree");
     k_leaf_flags_na<<<grid_for(nc, 256), 256, 0, s>>>(r.c.nchild, nc, leaf_flag);
     note_launch();
@@ -231,9 +231,14 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     NA_CU(cudaMemcpyAsync(&st, r.status, sizeof st, cudaMemcpyDeviceToHost, s));
     NA_CU(cudaStreamSynchronize(s));
     if (st & kStatInvalid) return fail_na(r, FMM_E_INVALID, "non-finite position or mass, or negative mass");
+    // two-float positions: the internal radii's single-precision bounds and the mixed P2P
+    float* xhi = (float*)A.take<float4>(n);  // 4n floats: X | Y | Z | W
+    float* xlo = (float*)A.take<float4>(n);  // 3n floats used: XL | YL | ZL
+    if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the tree");
+    launch_split_positions(r.xm, n, xhi, xlo, s);
     launch_leaf_geometry(r.xm, r.c, r.leaves, r.nleaves, r.status, s);
     for (int L = nl - 1; L >= 0; --L)
-        launch_internal_geometry(r.xm, r.c, r.lev[L], r.lev[L + 1], n, rad_tmp, r.status, s);
+        launch_internal_geometry(r.xm, xhi, xlo, r.c, r.lev[L], r.lev[L + 1], n, rad_tmp, r.status, s);
 
     // per-particle results and lists
     double* psi_far = A.take<double>(n);
@@ -241,8 +246,6 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     double* psi_near = A.take<double>(n);
     double* acc_near = A.take<double>(3 * (size_t)n);
     double* scale = A.take<double>(n);
-    float* xhi = (float*)A.take<float4>(n);  // 4n floats: X | Y | Z | W
-    float* xlo = (float*)A.take<float4>(n);  // 3n floats used: XL | YL | ZL
     r.front0 = A.take<int2>(kFrontCap);
     r.front1 = A.take<int2>(kFrontCap);
     int2* m2l = A.take<int2>(kListCap);
@@ -266,7 +269,6 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     void* m2l_tmp = A.take<unsigned char>(m2l_split_tmp_bytes(nc, p > 1 ? p : 1, kListCap));
     void* p2p_tmp = A.take<unsigned char>(p2p_tmp_bytes(r.nleaves));
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the expansions and lists");
-    if (prm.precision == FMM_PREC_MIXED) launch_split_positions(r.xm, n, xhi, xlo, s);
 
     // A7: scale estimate and its per-cell minimum
     if (prm.mac != FMM_MAC_THETA) {

@@ -877,6 +877,29 @@ void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves,
     }
 }
 
+// tmp layout per cell of the level (ncl cells): keys[2 ncl] (u64), lb[2 ncl] (float),
+// cen[12 ncl] (float: s hi, s lo, com hi, com lo)
+struct RadTmp {
+    unsigned long long* key;
+    float* lb;
+    float* cen;
+    __host__ __device__ RadTmp(unsigned long long* t, int ncl)
+        : key(t), lb((float*)(t + 2 * (size_t)ncl)), cen((float*)(t + 3 * (size_t)ncl)) {}
+};
+size_t rad_tmp_u64_per_cell() { return 9; }
+
+__device__ inline void write_cen_f(const RadTmp& R, int k, const double s[3], const double m[3]) {
+    float* q = R.cen + 12 * (size_t)k;
+    for (int d = 0; d < 3; ++d) {
+        const float h = (float)s[d];
+        q[d] = h;
+        q[3 + d] = (float)(s[d] - (double)h);
+        const float hm = (float)m[d];
+        q[6 + d] = hm;
+        q[9 + d] = (float)(m[d] - (double)hm);
+    }
+}
+
 // Internal cells of one level: smallest ball enclosing the daughter balls (s_d, rho_d),
 // as the smallest support ball (over all subsets of 1..4 daughters, enumerated by
 // mask) that contains every daughter ball; single precision relative to the first
@@ -886,7 +909,7 @@ void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves,
 // valid ball (ties: the smaller mask)
 constexpr int kMebWarps = 8;
 __global__ void __launch_bounds__(kMebWarps * 32) k_internal_meb(Cells c, int lev_begin, int lev_end,
-                                                                 unsigned* status) {
+                                                                 unsigned* status, unsigned long long* tmp) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int cell = lev_begin + blockIdx.x;
     if (cell >= lev_end) return;
@@ -992,48 +1015,118 @@ __global__ void __launch_bounds__(kMebWarps * 32) k_internal_meb(Cells c, int le
         c.sr[cell] = mk4(s[0], s[1], s[2], 0.0);
         c.cr[cell] = mk4(com[0], com[1], com[2], 0.0);
         c.mass[cell] = m;
+        write_cen_f(RadTmp(tmp, lev_end - lev_begin), cell - lev_begin, s, com);
     }
 }
 
-// exact radii of the internal cells of one level: max over their particles of
-// |x - s| and |x - com|; particle-parallel with a warp max per run of equal cells
-__global__ void k_internal_radii(const d4* __restrict__ xm, Cells c, int lev_begin, int lev_end,
-                                 unsigned long long* __restrict__ rad_tmp) {
-    // the level's cells cover particles [pbeg, pend) (cells of a level are in key order)
+// Exact radii of the internal cells of one level: max over their particles of |x - s|
+// and |x - com| (Sec. 4), taken in FP64, but only for the particles that can attain the
+// maximum.  A first pass bounds every distance in FP32 from the two-float positions and
+// the two-float centres: the difference of two-float values carries at most 2^-23 |d| +
+// 2^-46 (|x| + |s|) per coordinate, so with d_f the FP32 distance
+//   d_f (1 - 2^-20) - E <= d <= d_f (1 + 2^-20) + E,  E = 2^-44 sum_c (|x_c| + |s_c|)
+// (the FP32 square and square root stay inside the relative margin; below the coordinate
+// range 2^-18 an underflowed square would escape E and above 2^60 it would overflow, so
+// there every particle is a candidate).  The per-cell maximum LB of the lower bounds is
+// at most the largest distance, so the particle attaining it has an upper bound >= LB;
+// the second pass takes the FP64 distance of every particle whose upper bound reaches LB,
+// and the maximum over those is the maximum over all, bit for bit.
+// the level's cells cover particles [pbeg, pend) (cells of a level are in key order); the
+// last cell with first <= i
+__device__ inline int level_cell_of(const Cells& c, int lev_begin, int lev_end, int i) {
+    int lo = lev_begin, hi = lev_end - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (c.first[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return (i >= c.first[lo] && i < c.first[lo] + c.count[lo] && c.nchild[lo] > 0) ? lo : -1;
+}
+
+// FP32 bounds of the distance of particle i from a two-float centre q (hi[3], lo[3])
+__device__ inline void dist_bounds_f(const float* __restrict__ xhi, const float* __restrict__ xlo, size_t n,
+                                     int i, const float* q, float& lb, float& ub) {
+    float d2 = 0.f, mag = 0.f;
+    for (int d = 0; d < 3; ++d) {
+        const float xh = xhi[d * n + i];
+        const float dd = __fadd_rn(__fsub_rn(xh, q[d]), __fsub_rn(xlo[d * n + i], q[3 + d]));
+        d2 = __fmaf_rn(dd, dd, d2);
+        mag = __fadd_rn(mag, __fadd_rn(fabsf(xh), fabsf(q[d])));
+    }
+    if (!(mag >= 0x1p-18f && mag <= 0x1p60f)) {
+        lb = 0.f;
+        ub = __int_as_float(0x7f800000);
+        return;
+    }
+    const float df = sqrtf(d2), E = mag * 0x1p-44f;
+    lb = fmaxf(0.f, df * (1.0f - 0x1p-20f) - E);
+    ub = df * (1.0f + 0x1p-20f) + E;
+}
+
+__global__ void k_internal_radii_lb(const float* __restrict__ xhi, const float* __restrict__ xlo, int n, Cells c,
+                                    int lev_begin, int lev_end, unsigned long long* __restrict__ tmp) {
+    const RadTmp R(tmp, lev_end - lev_begin);
     const int pbeg = c.first[lev_begin];
     const int pend = c.first[lev_end - 1] + c.count[lev_end - 1];
     for (int i0 = blockIdx.x * blockDim.x; i0 < pend - pbeg; i0 += gridDim.x * blockDim.x) {
-        int i = pbeg + i0 + threadIdx.x;
+        const int i = pbeg + i0 + threadIdx.x;
         int cell = -1;
-        double d2 = 0, e2 = 0;
+        float l0 = 0.f, l1 = 0.f;
         if (i < pend) {
-            int lo = lev_begin, hi = lev_end - 1;  // last cell with first <= i
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (c.first[mid] <= i) lo = mid;
-                else hi = mid - 1;
-            }
-            if (i >= c.first[lo] && i < c.first[lo] + c.count[lo] && c.nchild[lo] > 0) {
-                cell = lo;
-                d4 p = xm[i];
-                d4 s = c.sr[cell], m = c.cr[cell];
-                double dx = p.x - s.x, dy = p.y - s.y, dz = p.z - s.z;
-                d2 = dx * dx + dy * dy + dz * dz;
-                double ex = p.x - m.x, ey = p.y - m.y, ez = p.z - m.z;
-                e2 = ex * ex + ey * ey + ez * ez;
+            cell = level_cell_of(c, lev_begin, lev_end, i);
+            if (cell >= 0) {
+                const float* q = R.cen + 12 * (size_t)(cell - lev_begin);
+                float u;
+                dist_bounds_f(xhi, xlo, (size_t)n, i, q, l0, u);
+                dist_bounds_f(xhi, xlo, (size_t)n, i, q + 6, l1, u);
             }
         }
-        int c0 = __shfl_sync(0xffffffffu, cell, 0);
+        // non-negative floats order as their bit patterns
+        const int c0 = __shfl_sync(0xffffffffu, cell, 0);
         if (__all_sync(0xffffffffu, cell == c0)) {
-            d2 = warp_max(d2);
-            e2 = warp_max(e2);
+            for (int o = 16; o > 0; o >>= 1) {
+                l0 = fmaxf(l0, __shfl_xor_sync(0xffffffffu, l0, o));
+                l1 = fmaxf(l1, __shfl_xor_sync(0xffffffffu, l1, o));
+            }
             if ((threadIdx.x & 31) == 0 && c0 >= 0) {
-                atomicMax(&rad_tmp[2 * (c0 - lev_begin)], dbl_key(d2));
-                atomicMax(&rad_tmp[2 * (c0 - lev_begin) + 1], dbl_key(e2));
+                atomicMax((int*)&R.lb[2 * (c0 - lev_begin)], __float_as_int(l0));
+                atomicMax((int*)&R.lb[2 * (c0 - lev_begin) + 1], __float_as_int(l1));
             }
         } else if (cell >= 0) {
-            atomicMax(&rad_tmp[2 * (cell - lev_begin)], dbl_key(d2));
-            atomicMax(&rad_tmp[2 * (cell - lev_begin) + 1], dbl_key(e2));
+            atomicMax((int*)&R.lb[2 * (cell - lev_begin)], __float_as_int(l0));
+            atomicMax((int*)&R.lb[2 * (cell - lev_begin) + 1], __float_as_int(l1));
+        }
+    }
+}
+
+__global__ void k_internal_radii(const d4* __restrict__ xm, const float* __restrict__ xhi,
+                                 const float* __restrict__ xlo, int n, Cells c, int lev_begin, int lev_end,
+                                 unsigned long long* __restrict__ tmp) {
+    const RadTmp R(tmp, lev_end - lev_begin);
+    const int pbeg = c.first[lev_begin];
+    const int pend = c.first[lev_end - 1] + c.count[lev_end - 1];
+    for (int i0 = blockIdx.x * blockDim.x; i0 < pend - pbeg; i0 += gridDim.x * blockDim.x) {
+        const int i = pbeg + i0 + threadIdx.x;
+        if (i >= pend) continue;
+        const int cell = level_cell_of(c, lev_begin, lev_end, i);
+        if (cell < 0) continue;
+        const int k = cell - lev_begin;
+        const float* q = R.cen + 12 * (size_t)k;
+        float l, u0, u1;
+        dist_bounds_f(xhi, xlo, (size_t)n, i, q, l, u0);
+        dist_bounds_f(xhi, xlo, (size_t)n, i, q + 6, l, u1);
+        const bool want0 = u0 >= R.lb[2 * k], want1 = u1 >= R.lb[2 * k + 1];
+        if (!want0 && !want1) continue;
+        const d4 p = xm[i];
+        if (want0) {
+            const d4 sc = c.sr[cell];
+            const double dx = p.x - sc.x, dy = p.y - sc.y, dz = p.z - sc.z;
+            atomicMax(&R.key[2 * k], dbl_key(dx * dx + dy * dy + dz * dz));
+        }
+        if (want1) {
+            const d4 m = c.cr[cell];
+            const double ex = p.x - m.x, ey = p.y - m.y, ez = p.z - m.z;
+            atomicMax(&R.key[2 * k + 1], dbl_key(ex * ex + ey * ey + ez * ez));
         }
     }
 }
@@ -1049,7 +1142,7 @@ __global__ void k_internal_radii_finish(Cells c, int lev_begin, int lev_end,
 }
 
 // a reused tree: the centres stay, mass and centre of mass from the daughters
-__global__ void k_internal_keep(Cells c, int lev_begin, int lev_end) {
+__global__ void k_internal_keep(Cells c, int lev_begin, int lev_end, unsigned long long* tmp) {
     const int cell = lev_begin + blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= lev_end) return;
     const int nch = c.nchild[cell];
@@ -1063,19 +1156,26 @@ __global__ void k_internal_keep(Cells c, int lev_begin, int lev_end) {
         mx[0] += md * cm.x; mx[1] += md * cm.y; mx[2] += md * cm.z;
     }
     const d4 s = c.sr[cell];
-    c.cr[cell] = mk4(m > 0 ? mx[0] / m : s.x, m > 0 ? mx[1] / m : s.y, m > 0 ? mx[2] / m : s.z, 0.0);
+    const double com[3] = {m > 0 ? mx[0] / m : s.x, m > 0 ? mx[1] / m : s.y, m > 0 ? mx[2] / m : s.z};
+    c.cr[cell] = mk4(com[0], com[1], com[2], 0.0);
     c.mass[cell] = m;
+    const double sv[3] = {s.x, s.y, s.z};
+    write_cen_f(RadTmp(tmp, lev_end - lev_begin), cell - lev_begin, sv, com);
 }
 
-void launch_internal_geometry(const d4* xm, Cells c, int lev_begin, int lev_end, int n,
-                              unsigned long long* rad_tmp, unsigned* status, cudaStream_t s, bool keep_centre) {
+void launch_internal_geometry(const d4* xm, const float* xhi, const float* xlo, Cells c, int lev_begin, int lev_end,
+                              int n, unsigned long long* rad_tmp, unsigned* status, cudaStream_t s, bool keep_centre) {
     int ncl = lev_end - lev_begin;
     if (ncl <= 0) return;
-    if (keep_centre) k_internal_keep<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end);
-    else k_internal_meb<<<(unsigned)ncl, kMebWarps * 32, 0, s>>>(c, lev_begin, lev_end, status);
+    // bounds and keys start at 0 (every distance is >= 0)
+    cudaMemsetAsync(rad_tmp, 0, sizeof(unsigned long long) * 3 * (size_t)ncl, s);
+    if (keep_centre) k_internal_keep<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end, rad_tmp);
+    else k_internal_meb<<<(unsigned)ncl, kMebWarps * 32, 0, s>>>(c, lev_begin, lev_end, status, rad_tmp);
     note_launch();
-    cudaMemsetAsync(rad_tmp, 0, sizeof(unsigned long long) * 2 * ncl, s);
-    k_internal_radii<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xm, c, lev_begin, lev_end, rad_tmp); note_launch();
+    k_internal_radii_lb<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xhi, xlo, n, c, lev_begin, lev_end, rad_tmp);
+    note_launch();
+    k_internal_radii<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xm, xhi, xlo, n, c, lev_begin, lev_end, rad_tmp);
+    note_launch();
     k_internal_radii_finish<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, rad_tmp); note_launch();
 }
 

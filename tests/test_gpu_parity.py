@@ -104,6 +104,23 @@ def test_fmm_fp64_matches_oracle(g, orc, case):
     assert np.max(np.abs(psi - run.psi) / run.psi) <= PARITY_TOL
 
 
+@pytest.mark.parametrize("shift,mscale", [(1e5, 1.0), (0.0, 1e-38), (0.0, 1e36), (3e3, 1e-20)])
+def test_walk_single_precision_view_extremes(g, orc, shift, mscale):
+    """The walk takes its acceptance test in FP32 from a single-precision view of the cells and
+    leaves to FP64 every decision within its error margins or outside the FP32 range. Far from
+    the origin the two-float centre differences lose their bound for close cells; masses far
+    outside the FP32 range put P_0 and eps * minscale out of it. Trees, lists and forces stay
+    those of the oracle."""
+    x, mu = inputs.config_input(1)
+    x = x + shift
+    mu = mu * mscale
+    psi, acc, st, dump, run = _run_both(g, orc, x, mu, eps=1e-6)
+    flips, nm, npp = _compare_structure(dump, run)
+    assert flips == 0 and nm > 0 and npp > 0
+    assert np.max(_rel(acc, run.acc)) <= PARITY_TOL
+    assert np.max(np.abs(psi - run.psi) / run.psi) <= PARITY_TOL
+
+
 def test_estimate_scale_matches_oracle(g, orc):
     x, mu = inputs.config_input(1)
     for mac in (0, 1):
