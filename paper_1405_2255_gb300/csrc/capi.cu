@@ -72,7 +72,7 @@ struct fmm_ctx {
     Buf keys, keys_alt, idx, idx_alt, rtmp, xm, perm, xhi, xlo;
     // cells
     Buf first, count, child, nchild, parent, level, sr, cr, mass, minscale;
-    Buf split_nchild, split_oct, split_offs, scan_tmp, leaves, leaf_flag, leaf_pos, rad_tmp;
+    Buf split_nchild, split_oct, split_offs, scan_tmp, leaves, leaf_flag, leaf_pos, rad_tmp, owner;
     // expansions
     Buf M, F, Pw, binom, pascal, M1, F1, Ff;
     // walk
@@ -105,7 +105,7 @@ struct fmm_ctx {
                 &leaf_pos, &rad_tmp, &M, &F, &Pw, &binom, &pascal, &M1, &F1, &Ff, &front0, &front1, &m2l, &p2p,
                 &sort_tmp, &m2l_tmp, &p2p_tmp, &seg_start, &seg_end, &est_m2l, &est_p2p, &m2l_seg_start,
                 &m2l_seg_end, &psi_far, &acc_far, &psi_near, &acc_near, &scale_sorted, &sys_off, &sys_G,
-                &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan, &tid_far, &tid_near, &walkf};
+                &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan, &tid_far, &tid_near, &walkf, &owner};
     }
     // tree shape of the last evaluation
     std::vector<int> lev_start;
@@ -222,10 +222,12 @@ static int refresh_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, 
     Cells c = cells_of(ctx);
     const int nlev = (int)ctx->lev_start.size() - 1;
     TRY(split_positions(ctx, n, s));
+    TRY(ensure(ctx->owner, sizeof(int) * (size_t)n));
     launch_leaf_geometry(P<d4>(ctx->xm), c, P<int>(ctx->leaves), ctx->nleaves, P<unsigned>(ctx->status), s, true);
+    launch_leaf_owner(c, P<int>(ctx->leaves), ctx->nleaves, P<int>(ctx->owner), s);
     for (int L = nlev - 1; L >= 0; --L)
         launch_internal_geometry(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), c, ctx->lev_start[L],
-                                 ctx->lev_start[L + 1], n, P<unsigned long long>(ctx->rad_tmp),
+                                 ctx->lev_start[L + 1], n, P<int>(ctx->owner), P<unsigned long long>(ctx->rad_tmp),
                                  P<unsigned>(ctx->status), s, true);
     return 0;
 }
@@ -321,10 +323,12 @@ static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cu
     for (int L = 0; L < nlev; ++L) maxlev_cells = std::max(maxlev_cells, ctx->lev_start[L + 1] - ctx->lev_start[L]);
     TRY(ensure(ctx->rad_tmp, sizeof(unsigned long long) * rad_tmp_u64_per_cell() * (size_t)maxlev_cells));
     TRY(split_positions(ctx, n, s));
+    TRY(ensure(ctx->owner, sizeof(int) * (size_t)n));
     launch_leaf_geometry(P<d4>(ctx->xm), c, P<int>(ctx->leaves), ctx->nleaves, P<unsigned>(ctx->status), s);
+    launch_leaf_owner(c, P<int>(ctx->leaves), ctx->nleaves, P<int>(ctx->owner), s);
     for (int L = nlev - 1; L >= 0; --L)
         launch_internal_geometry(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), c, ctx->lev_start[L],
-                                 ctx->lev_start[L + 1], n, P<unsigned long long>(ctx->rad_tmp),
+                                 ctx->lev_start[L + 1], n, P<int>(ctx->owner), P<unsigned long long>(ctx->rad_tmp),
                                  P<unsigned>(ctx->status), s);
     return 0;
 }

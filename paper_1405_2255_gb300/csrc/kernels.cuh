@@ -72,11 +72,13 @@ void launch_split_level(const uint64_t* keys, Cells c, int lev_begin, int lev_en
 // radii, masses and centres of mass for the particles' new positions
 void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves, unsigned* status,
                           cudaStream_t s, bool keep_centre = false);
-// xhi/xlo: the two-float positions (launch_split_positions); rad_tmp: rad_tmp_u64_per_cell()
-// words per cell of the largest level
+// xhi/xlo: the two-float positions (launch_split_positions); owner: per particle, set by
+// launch_leaf_owner before the deepest level and moved up as the levels are processed
+// bottom-up; rad_tmp: rad_tmp_u64_per_cell() words per cell of the largest level
 void launch_internal_geometry(const d4* xm, const float* xhi, const float* xlo, Cells c, int lev_begin, int lev_end,
-                              int n, unsigned long long* rad_tmp, unsigned* status, cudaStream_t s,
+                              int n, int* owner, unsigned long long* rad_tmp, unsigned* status, cudaStream_t s,
                               bool keep_centre = false);
+void launch_leaf_owner(Cells c, const int* leaves, int nleaves, int* owner, cudaStream_t s);
 size_t rad_tmp_u64_per_cell();
 
 // ---------------------------------------------------------------- upward (upward.cu)

@@ -235,10 +235,13 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     float* xhi = (float*)A.take<float4>(n);  // 4n floats: X | Y | Z | W
     float* xlo = (float*)A.take<float4>(n);  // 3n floats used: XL | YL | ZL
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the tree");
+    int* owner = A.take<int>(n);
+    if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the tree");
     launch_split_positions(r.xm, n, xhi, xlo, s);
     launch_leaf_geometry(r.xm, r.c, r.leaves, r.nleaves, r.status, s);
+    launch_leaf_owner(r.c, r.leaves, r.nleaves, owner, s);
     for (int L = nl - 1; L >= 0; --L)
-        launch_internal_geometry(r.xm, xhi, xlo, r.c, r.lev[L], r.lev[L + 1], n, rad_tmp, r.status, s);
+        launch_internal_geometry(r.xm, xhi, xlo, r.c, r.lev[L], r.lev[L + 1], n, owner, rad_tmp, r.status, s);
 
     // per-particle results and lists
     double* psi_far = A.take<double>(n);

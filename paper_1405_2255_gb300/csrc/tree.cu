@@ -1031,16 +1031,32 @@ __global__ void __launch_bounds__(kMebWarps * 32) k_internal_meb(Cells c, int le
 // at most the largest distance, so the particle attaining it has an upper bound >= LB;
 // the second pass takes the FP64 distance of every particle whose upper bound reaches LB,
 // and the maximum over those is the maximum over all, bit for bit.
-// the level's cells cover particles [pbeg, pend) (cells of a level are in key order); the
-// last cell with first <= i
-__device__ inline int level_cell_of(const Cells& c, int lev_begin, int lev_end, int i) {
-    int lo = lev_begin, hi = lev_end - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (c.first[mid] <= i) lo = mid;
-        else hi = mid - 1;
+// owner[i]: the particle's ancestor at the level processed last (its leaf to begin with).
+// The levels are processed bottom-up, so at level L the owner moves up one cell when it
+// lies below L; the particle belongs to an internal cell of level L iff its owner is one.
+__global__ void k_leaf_owner(Cells c, const int* __restrict__ leaves, int nleaves, int* __restrict__ owner) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nleaves; t += gridDim.x * blockDim.x) {
+        const int leaf = leaves[t];
+        for (int i = c.first[leaf], e = c.first[leaf] + c.count[leaf]; i < e; ++i) owner[i] = leaf;
     }
-    return (i >= c.first[lo] && i < c.first[lo] + c.count[lo] && c.nchild[lo] > 0) ? lo : -1;
+}
+void launch_leaf_owner(Cells c, const int* leaves, int nleaves, int* owner, cudaStream_t s) {
+    if (nleaves > 0) {
+        k_leaf_owner<<<grid_for(nleaves, 128), 128, 0, s>>>(c, leaves, nleaves, owner);
+        note_launch();
+    }
+}
+__device__ inline int level_cell_up(const Cells& c, int L, int* __restrict__ owner, int i) {
+    int a = owner[i];
+    if (c.level[a] > L) {
+        a = c.parent[a];
+        owner[i] = a;
+    }
+    return (c.level[a] == L && c.nchild[a] > 0) ? a : -1;
+}
+__device__ inline int level_cell_now(const Cells& c, int L, const int* __restrict__ owner, int i) {
+    const int a = owner[i];
+    return (c.level[a] == L && c.nchild[a] > 0) ? a : -1;
 }
 
 // FP32 bounds of the distance of particle i from a two-float centre q (hi[3], lo[3])
@@ -1064,8 +1080,10 @@ __device__ inline void dist_bounds_f(const float* __restrict__ xhi, const float*
 }
 
 __global__ void k_internal_radii_lb(const float* __restrict__ xhi, const float* __restrict__ xlo, int n, Cells c,
-                                    int lev_begin, int lev_end, unsigned long long* __restrict__ tmp) {
+                                    int lev_begin, int lev_end, int* __restrict__ owner,
+                                    unsigned long long* __restrict__ tmp) {
     const RadTmp R(tmp, lev_end - lev_begin);
+    const int L = c.level[lev_begin];
     const int pbeg = c.first[lev_begin];
     const int pend = c.first[lev_end - 1] + c.count[lev_end - 1];
     for (int i0 = blockIdx.x * blockDim.x; i0 < pend - pbeg; i0 += gridDim.x * blockDim.x) {
@@ -1073,7 +1091,7 @@ __global__ void k_internal_radii_lb(const float* __restrict__ xhi, const float* 
         int cell = -1;
         float l0 = 0.f, l1 = 0.f;
         if (i < pend) {
-            cell = level_cell_of(c, lev_begin, lev_end, i);
+            cell = level_cell_up(c, L, owner, i);
             if (cell >= 0) {
                 const float* q = R.cen + 12 * (size_t)(cell - lev_begin);
                 float u;
@@ -1101,14 +1119,15 @@ __global__ void k_internal_radii_lb(const float* __restrict__ xhi, const float* 
 
 __global__ void k_internal_radii(const d4* __restrict__ xm, const float* __restrict__ xhi,
                                  const float* __restrict__ xlo, int n, Cells c, int lev_begin, int lev_end,
-                                 unsigned long long* __restrict__ tmp) {
+                                 const int* __restrict__ owner, unsigned long long* __restrict__ tmp) {
     const RadTmp R(tmp, lev_end - lev_begin);
+    const int L = c.level[lev_begin];
     const int pbeg = c.first[lev_begin];
     const int pend = c.first[lev_end - 1] + c.count[lev_end - 1];
     for (int i0 = blockIdx.x * blockDim.x; i0 < pend - pbeg; i0 += gridDim.x * blockDim.x) {
         const int i = pbeg + i0 + threadIdx.x;
         if (i >= pend) continue;
-        const int cell = level_cell_of(c, lev_begin, lev_end, i);
+        const int cell = level_cell_now(c, L, owner, i);
         if (cell < 0) continue;
         const int k = cell - lev_begin;
         const float* q = R.cen + 12 * (size_t)k;
@@ -1164,7 +1183,8 @@ __global__ void k_internal_keep(Cells c, int lev_begin, int lev_end, unsigned lo
 }
 
 void launch_internal_geometry(const d4* xm, const float* xhi, const float* xlo, Cells c, int lev_begin, int lev_end,
-                              int n, unsigned long long* rad_tmp, unsigned* status, cudaStream_t s, bool keep_centre) {
+                              int n, int* owner, unsigned long long* rad_tmp, unsigned* status, cudaStream_t s,
+                              bool keep_centre) {
     int ncl = lev_end - lev_begin;
     if (ncl <= 0) return;
     // bounds and keys start at 0 (every distance is >= 0)
@@ -1172,9 +1192,11 @@ void launch_internal_geometry(const d4* xm, const float* xhi, const float* xlo, 
     if (keep_centre) k_internal_keep<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end, rad_tmp);
     else k_internal_meb<<<(unsigned)ncl, kMebWarps * 32, 0, s>>>(c, lev_begin, lev_end, status, rad_tmp);
     note_launch();
-    k_internal_radii_lb<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xhi, xlo, n, c, lev_begin, lev_end, rad_tmp);
+    k_internal_radii_lb<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xhi, xlo, n, c, lev_begin, lev_end, owner,
+                                                                     rad_tmp);
     note_launch();
-    k_internal_radii<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xm, xhi, xlo, n, c, lev_begin, lev_end, rad_tmp);
+    k_internal_radii<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xm, xhi, xlo, n, c, lev_begin, lev_end, owner,
+                                                                  rad_tmp);
     note_launch();
     k_internal_radii_finish<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, rad_tmp); note_launch();
 }
