@@ -77,6 +77,7 @@ struct fmm_ctx {
     Buf M, F, Pw, binom, pascal, M1, F1, Ff;
     // walk
     Buf walkf;  // single-precision view of the cells for the walk's acceptance test
+    Buf units;  // int[2]: the working units of the tree in use (launch_work_units)
     Buf front0, front1, m2l, p2p, sort_tmp, m2l_tmp, p2p_tmp, seg_start, seg_end, est_m2l, est_p2p, m2l_seg_start, m2l_seg_end;
     long long front_cap = 0, m2l_cap = 0, p2p_cap = 0, est_m2l_cap = 0, est_p2p_cap = 0;
     // per particle results (sorted order)
@@ -105,7 +106,7 @@ struct fmm_ctx {
                 &leaf_pos, &rad_tmp, &M, &F, &Pw, &binom, &pascal, &M1, &F1, &Ff, &front0, &front1, &m2l, &p2p,
                 &sort_tmp, &m2l_tmp, &p2p_tmp, &seg_start, &seg_end, &est_m2l, &est_p2p, &m2l_seg_start,
                 &m2l_seg_end, &psi_far, &acc_far, &psi_near, &acc_near, &scale_sorted, &sys_off, &sys_G,
-                &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan, &tid_far, &tid_near, &walkf, &owner};
+                &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan, &tid_far, &tid_near, &walkf, &owner, &units};
     }
     // tree shape of the last evaluation
     std::vector<int> lev_start;
@@ -213,7 +214,8 @@ static int split_positions(fmm_ctx* ctx, int n, cudaStream_t s) {
 // centres of mass are recomputed, so the MAC sees the true extent of every cell
 static int refresh_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cudaStream_t s) {
     launch_bounds(x, mu, n, P<unsigned long long>(ctx->bounds), P<unsigned>(ctx->status), s);
-    launch_gather(x, mu, P<int>(ctx->perm), n, P<d4>(ctx->xm), P<int>(ctx->perm), s);
+    // the tree's centres are in the working units it was built in: keep them
+    launch_gather(x, mu, P<int>(ctx->perm), n, P<d4>(ctx->xm), P<int>(ctx->perm), s, P<int>(ctx->units));
     unsigned st = 0;
     CU(cudaMemcpyAsync(&ctx->h_int[0], ctx->status.p, sizeof st, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -249,7 +251,7 @@ static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cu
                          n, P<int>(ctx->rtmp), s);
     } else {
         // forest: per-system bounds and keys, sort by key, then (stably) by system
-        TRY(ensure(ctx->bounds, sizeof(unsigned long long) * 6 * (size_t)nsys));
+        TRY(ensure(ctx->bounds, sizeof(unsigned long long) * (6 * (size_t)nsys + 1)));
         TRY(ensure(ctx->skey, sizeof(uint64_t) * n));
         TRY(ensure(ctx->skey_alt, sizeof(uint64_t) * n));
         TRY(ensure(ctx->spos, sizeof(int) * n));
@@ -265,7 +267,11 @@ static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cu
         std::swap(ctx->keys, ctx->keys_alt);
         std::swap(ctx->idx, ctx->idx_alt);
     }
-    launch_gather(x, mu, P<int>(ctx->idx), n, P<d4>(ctx->xm), P<int>(ctx->perm), s);
+    // working units: mixed precision rescales positions and masses by powers of two (exact)
+    TRY(ensure(ctx->units, 2 * sizeof(int)));
+    if (ctx->prm.precision == FMM_PREC_MIXED) launch_work_units(P<unsigned long long>(ctx->bounds), nsys, P<int>(ctx->units), s);
+    else CU(cudaMemsetAsync(ctx->units.p, 0, 2 * sizeof(int), s));
+    launch_gather(x, mu, P<int>(ctx->idx), n, P<d4>(ctx->xm), P<int>(ctx->perm), s, P<int>(ctx->units));
 
     // cell capacity: leaves <= n, internal cells hold > leaf particles, <= 21 levels
     const int nroots = ctx->nroots;
@@ -545,7 +551,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     // A7: acceleration scale for the MAC and its per-cell minimum
     if (prm.mac != FMM_MAC_THETA) {
         if (prm.scale_src == FMM_SCALE_CALLER)
-            launch_scale_from_caller(scale, P<int>(ctx->perm), n, P<double>(ctx->scale_sorted), s);
+            launch_scale_from_caller(scale, P<int>(ctx->perm), n, P<double>(ctx->scale_sorted), s, P<int>(ctx->units));
         else
             TRY(estimate_scale(ctx, s));
         if (eps_b) {  // Sec. 7, opening: min over the sinks of eps_b a_b in place of eps min a_b
@@ -671,13 +677,13 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
                    P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
     launch_finish(P<double>(ctx->psi_far), P<double>(ctx->acc_far), P<double>(ctx->psi_near), P<double>(ctx->acc_near),
                   P<int>(ctx->perm), n, G, psi, acc, s, sys_off, ctx->nsys ? P<double>(ctx->sys_G) : nullptr,
-                  ctx->nsys, ctx->active_mode ? P<unsigned char>(ctx->pact) : nullptr);
+                  ctx->nsys, ctx->active_mode ? P<unsigned char>(ctx->pact) : nullptr, P<int>(ctx->units));
     if (tidal) {  // Sec. 7.4: the far part from Psi_2^m of the local expansions
         TRY(ensure(ctx->tid_far, sizeof(double) * 6 * (size_t)n));
         launch_l2p_tidal(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->F),
                          P<double>(ctx->tid_far), s);
         launch_finish_tidal(P<double>(ctx->tid_far), P<double>(ctx->tid_near), P<int>(ctx->perm), n, G,
-                            ctx->active_mode ? P<unsigned char>(ctx->pact) : nullptr, tidal, s);
+                            ctx->active_mode ? P<unsigned char>(ctx->pact) : nullptr, tidal, s, P<int>(ctx->units));
     }
     if (timing) {
         CU(cudaEventRecord(ctx->ev[EV_DOWN], s));
@@ -750,7 +756,7 @@ int fmm_create(fmm_ctx** out, const fmm_params* params, int device) {
     ctx->device = device;
     memset(&ctx->last, 0, sizeof ctx->last);
     int rc = 0;
-    if (!rc) rc = ensure(ctx->bounds, 6 * sizeof(unsigned long long));
+    if (!rc) rc = ensure(ctx->bounds, 8 * sizeof(unsigned long long));
     if (!rc) rc = ensure(ctx->status, 16);
     if (!rc) rc = ensure(ctx->counters, 8 * sizeof(unsigned long long));
     if (!rc) rc = ensure(ctx->coin, 16);
@@ -900,6 +906,9 @@ int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t*
     if (!ctx) return FMM_E_INVALID;
     const int nc = ctx->ncells, n = ctx->n;
     CU(cudaDeviceSynchronize());
+    // the caller's units: lengths 2^e0, masses 2^e1, scales (accelerations) 2^(e1 - 2 e0)
+    int e[2] = {0, 0};
+    if (ctx->units.p) CU(cudaMemcpy(e, ctx->units.p, sizeof e, cudaMemcpyDeviceToHost));
     if (cells_int || cells_dbl) {
         std::vector<int> lv(nc), fi(nc), co(nc), nch(nc);
         std::vector<d4> sr(nc);
@@ -922,12 +931,12 @@ int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t*
                 cells_int[5 * i + 4] = nch[i];
             }
             if (cells_dbl) {
-                cells_dbl[6 * i] = sr[i].x;
-                cells_dbl[6 * i + 1] = sr[i].y;
-                cells_dbl[6 * i + 2] = sr[i].z;
-                cells_dbl[6 * i + 3] = sr[i].w;
-                cells_dbl[6 * i + 4] = ms[i];
-                cells_dbl[6 * i + 5] = mn[i];
+                cells_dbl[6 * i] = std::ldexp(sr[i].x, e[0]);
+                cells_dbl[6 * i + 1] = std::ldexp(sr[i].y, e[0]);
+                cells_dbl[6 * i + 2] = std::ldexp(sr[i].z, e[0]);
+                cells_dbl[6 * i + 3] = std::ldexp(sr[i].w, e[0]);
+                cells_dbl[6 * i + 4] = std::ldexp(ms[i], e[1]);
+                cells_dbl[6 * i + 5] = std::ldexp(mn[i], e[1] - 2 * e[0]);
             }
         }
     }
@@ -948,7 +957,10 @@ int fmm_debug_dump(fmm_ctx* ctx, int64_t* cells_int, double* cells_dbl, int64_t*
         CU(cudaMemcpy(pv.data(), ctx->perm.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
         for (int i = 0; i < n; ++i) perm[i] = pv[i];
     }
-    if (scale_sorted && n && ctx->scale_sorted.p) CU(cudaMemcpy(scale_sorted, ctx->scale_sorted.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (scale_sorted && n && ctx->scale_sorted.p) {
+        CU(cudaMemcpy(scale_sorted, ctx->scale_sorted.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; ++i) scale_sorted[i] = std::ldexp(scale_sorted[i], e[1] - 2 * e[0]);
+    }
     return 0;
 }
 

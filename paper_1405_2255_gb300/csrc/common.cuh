@@ -169,6 +169,12 @@ __device__ inline void ff_acc(ff& a, float v) {
     a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
 }
 
+// 2^k as a double for |k| <= 1022, from its bits (exact)
+__device__ inline double pow2i(int k) {
+    k = k < -1022 ? -1022 : (k > 1023 ? 1023 : k);
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
 // order-preserving map of a double to uint64 (for atomicMin/atomicMax on doubles)
 __device__ inline unsigned long long dbl_key(double d) {
     unsigned long long u = (unsigned long long)__double_as_longlong(d);

@@ -1483,7 +1483,10 @@ void launch_norm_scale(const double* /*psi_far*/, const double* acc_far, const d
 __global__ void k_finish(const double* __restrict__ pf, const double* __restrict__ af, const double* __restrict__ pn,
                          const double* __restrict__ an, const int* __restrict__ perm, int n, double G,
                          double* __restrict__ psi, double* __restrict__ acc, const int* __restrict__ off,
-                         const double* __restrict__ Gsys, int nsys, const unsigned char* __restrict__ pact) {
+                         const double* __restrict__ Gsys, int nsys, const unsigned char* __restrict__ pact,
+                         const int* __restrict__ e) {
+    // back from the working units: Psi ~ mu / x, a ~ mu / x^2 (exact powers of two)
+    const int kp = e ? e[1] - e[0] : 0, ka = e ? e[1] - 2 * e[0] : 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (pact && !pact[i]) continue;  // outputs of inactive particles are left as they are
         int o = perm[i];
@@ -1496,17 +1499,18 @@ __global__ void k_finish(const double* __restrict__ pf, const double* __restrict
             }
             G = Gsys[lo];
         }
-        psi[o] = G * (pf[i] + pn[i]);
+        psi[o] = ldexp(G * (pf[i] + pn[i]), kp);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) acc[3 * (size_t)o + d] = G * (af[3 * (size_t)i + d] + an[3 * (size_t)i + d]);
+        for (int d = 0; d < 3; ++d)
+            acc[3 * (size_t)o + d] = ldexp(G * (af[3 * (size_t)i + d] + an[3 * (size_t)i + d]), ka);
     }
 }
 void launch_finish(const double* psi_far, const double* acc_far, const double* psi_near, const double* acc_near,
                    const int* perm, int n, double G, double* psi, double* acc, cudaStream_t s, const int* off,
-                   const double* Gsys, int nsys, const unsigned char* pact) {
+                   const double* Gsys, int nsys, const unsigned char* pact, const int* e) {
     if (n > 0)
         k_finish<<<grid_for(n, 256), 256, 0, s>>>(psi_far, acc_far, psi_near, acc_near, perm, n, G, psi, acc, off,
-                                                  Gsys, nsys, pact);
+                                                  Gsys, nsys, pact, e);
     note_launch();
 }
 

@@ -46,8 +46,13 @@ int radix_sort_pairs_bits(uint64_t* keys, int* idx, uint64_t* keys_alt, int* idx
                           int begin_bit, int end_bit, cudaStream_t s);
 void radix_sort_pairs(uint64_t* keys, int* idx, uint64_t* keys_alt, int* idx_alt, int n, int* tmp,
                       cudaStream_t s);
+// e (nullable, device): positions enter scaled by 2^-e[0], masses by 2^-e[1] (launch_work_units)
 void launch_gather(const double* x, const double* mu, const int* idx, int n, d4* xm, int* perm,
-                   cudaStream_t s);
+                   cudaStream_t s, const int* e = nullptr);
+// working units of the mixed-precision path: e[0] = floor(log2 extent), e[1] = floor(log2 max mass)
+// from the bounds of launch_bounds (nsys = 0; the largest mass in bounds[6]) or
+// launch_bounds_sys (the largest mass in bounds[6 nsys])
+void launch_work_units(const unsigned long long* bounds, int nsys, int* e, cudaStream_t s);
 // A1-A2 for an ensemble of nsys systems, system k = caller particles [off[k], off[k+1])
 // (off on the device): per-system bounds (bounds[6k..6k+5]) and keys in the system's
 // own root cube; then a stable sort of the key-sorted (keys, idx) by system into
@@ -94,7 +99,7 @@ void launch_minscale_leaves(const double* scale_sorted, Cells c, const int* leav
                             cudaStream_t s);
 void launch_minscale_level(Cells c, int lev_begin, int lev_end, cudaStream_t s);
 void launch_scale_from_caller(const double* scale, const int* perm, int n, double* scale_sorted,
-                              cudaStream_t s);
+                              cudaStream_t s, const int* e = nullptr);
 
 // ---------------------------------------------------------------- walk (walk.cu)
 struct WalkParams {
@@ -238,10 +243,12 @@ void launch_norm_scale(const double* psi_far, const double* acc_far, const doubl
                        double* scale, cudaStream_t s);
 // combine far + near, multiply by G and scatter to the caller's order (A12)
 // (ensemble: Gsys[k] for the caller particles [off[k], off[k+1]) instead of G)
+// e (nullable): the working units (launch_work_units); psi is scaled back by 2^(e1 - e0), a by
+// 2^(e1 - 2 e0)
 void launch_finish(const double* psi_far, const double* acc_far, const double* psi_near,
                    const double* acc_near, const int* perm, int n, double G, double* psi, double* acc,
                    cudaStream_t s, const int* off = nullptr, const double* Gsys = nullptr, int nsys = 0,
-                   const unsigned char* pact = nullptr);
+                   const unsigned char* pact = nullptr, const int* e = nullptr);
 // Sec. 7.1: pact[i] = active[perm[i]] != 0 (sorted order) and act[cell] = the cell holds an
 // active particle (from a prefix sum of pact over the cells' particle ranges); ai holds
 // n + 1 ints, scan n ints, scan_tmp scan_tmp_ints(n) ints
@@ -254,7 +261,7 @@ void launch_p2p_tidal(const d4* xm, const float* hi, const float* lo, int n, boo
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* T,
                       cudaStream_t s);
 void launch_finish_tidal(const double* Tf, const double* Tn, const int* perm, int n, double G,
-                         const unsigned char* pact, double* T, cudaStream_t s);
+                         const unsigned char* pact, double* T, cudaStream_t s, const int* e = nullptr);
 // individual accuracy parameters (Sec. 7, opening): scale_sorted[i] *= eps_b[perm[i]] / eps
 void launch_scale_eps(const double* eps_b, const int* perm, int n, double eps, double* scale_sorted, unsigned* status,
                       cudaStream_t s);

@@ -204,16 +204,18 @@ void launch_p2p_tidal(const d4* xm, const float* hi, const float* lo, int n, boo
 // T_caller = G (far + near), active particles only
 __global__ void k_finish_tidal(const double* __restrict__ Tf, const double* __restrict__ Tn,
                                const int* __restrict__ perm, int n, double G, const unsigned char* __restrict__ pact,
-                               double* __restrict__ T) {
+                               double* __restrict__ T, const int* __restrict__ e) {
+    const int kt = e ? e[1] - 3 * e[0] : 0;  // the tidal tensor ~ mu / x^3 in the working units
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (pact && !pact[i]) continue;
         const int o = perm[i];
-        for (int k = 0; k < 6; ++k) T[6 * (size_t)o + k] = G * (Tf[6 * (size_t)i + k] + Tn[6 * (size_t)i + k]);
+        for (int k = 0; k < 6; ++k)
+            T[6 * (size_t)o + k] = ldexp(G * (Tf[6 * (size_t)i + k] + Tn[6 * (size_t)i + k]), kt);
     }
 }
 void launch_finish_tidal(const double* Tf, const double* Tn, const int* perm, int n, double G,
-                         const unsigned char* pact, double* T, cudaStream_t s) {
-    if (n > 0) k_finish_tidal<<<grid_for(n, 256), 256, 0, s>>>(Tf, Tn, perm, n, G, pact, T); note_launch();
+                         const unsigned char* pact, double* T, cudaStream_t s, const int* e) {
+    if (n > 0) k_finish_tidal<<<grid_for(n, 256), 256, 0, s>>>(Tf, Tn, perm, n, G, pact, T, e); note_launch();
 }
 
 }  // namespace gb3

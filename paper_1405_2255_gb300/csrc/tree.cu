@@ -13,17 +13,19 @@ namespace gb3 {
 __global__ void k_bounds_init(unsigned long long* b) {
     int i = threadIdx.x;
     if (i < 3) b[i] = ~0ull;
-    else if (i < 6) b[i] = 0ull;
+    else if (i < 7) b[i] = 0ull;  // [6]: the largest mass
 }
 
 __global__ void k_bounds(const double* __restrict__ x, const double* __restrict__ mu, int n,
                          unsigned long long* bounds, unsigned* status) {
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double mmax = 0.0;
     bool bad = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double v[3] = {x[3 * (long long)i], x[3 * (long long)i + 1], x[3 * (long long)i + 2]};
         double m = mu[i];
         bad |= !(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(m) && m >= 0.0);
+        mmax = fmax(mmax, m);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             lo[d] = fmin(lo[d], v[d]);
@@ -35,6 +37,7 @@ __global__ void k_bounds(const double* __restrict__ x, const double* __restrict_
         lo[d] = warp_min(lo[d]);
         hi[d] = warp_max(hi[d]);
     }
+    mmax = warp_max(mmax);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatInvalid);
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
@@ -44,6 +47,7 @@ __global__ void k_bounds(const double* __restrict__ x, const double* __restrict_
                 atomicMax(&bounds[3 + d], dbl_key(hi[d]));
             }
         }
+        if (mmax > 0.0 && isfinite(mmax)) atomicMax(&bounds[6], dbl_key(mmax));
     }
 }
 
@@ -123,8 +127,8 @@ __device__ inline int system_of(const int* __restrict__ off, int nsys, int i) {
 }
 
 __global__ void k_bounds_init_sys(unsigned long long* b, int nsys) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 6 * nsys; i += gridDim.x * blockDim.x)
-        b[i] = (i % 6) < 3 ? ~0ull : 0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= 6 * nsys; i += gridDim.x * blockDim.x)
+        b[i] = (i < 6 * nsys && (i % 6) < 3) ? ~0ull : 0ull;  // [6 nsys]: the largest mass
 }
 
 __global__ void k_bounds_sys(const double* __restrict__ x, const double* __restrict__ mu, int n,
@@ -133,6 +137,7 @@ __global__ void k_bounds_sys(const double* __restrict__ x, const double* __restr
     for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
         const int i = i0 + threadIdx.x;
         double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        double mmax = 0.0;
         int k = -1;
         bool bad = false;
         if (i < n) {
@@ -142,8 +147,11 @@ __global__ void k_bounds_sys(const double* __restrict__ x, const double* __restr
             bad = !(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(m) && m >= 0.0);
 #pragma unroll
             for (int d = 0; d < 3; ++d) lo[d] = hi[d] = v[d];
+            if (m > 0.0 && isfinite(m)) mmax = m;
         }
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStatInvalid);
+        mmax = warp_max(mmax);
+        if (lane == 0 && mmax > 0.0) atomicMax(&bounds[6 * nsys], dbl_key(mmax));
         const int k0 = __shfl_sync(0xffffffffu, k, 0);
         if (__all_sync(0xffffffffu, k == k0)) {  // the whole warp in one system: reduce first
 #pragma unroll
@@ -167,7 +175,7 @@ __global__ void k_bounds_sys(const double* __restrict__ x, const double* __restr
 
 void launch_bounds_sys(const double* x, const double* mu, int n, const int* off, int nsys,
                        unsigned long long* bounds, unsigned* status, cudaStream_t s) {
-    k_bounds_init_sys<<<grid_for(6LL * nsys, 256), 256, 0, s>>>(bounds, nsys); note_launch();
+    k_bounds_init_sys<<<grid_for(6LL * nsys + 1, 256), 256, 0, s>>>(bounds, nsys); note_launch();
     if (n > 0) k_bounds_sys<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, mu, n, off, nsys, bounds, status); note_launch();
 }
 
@@ -317,18 +325,44 @@ void radix_sort_pairs(uint64_t* keys, int* idx, uint64_t* keys_alt, int* idx_alt
     radix_sort_pairs_bits(keys, idx, keys_alt, idx_alt, n, tmp, 0, 64, s);
 }
 
+// e (nullable): the working units, positions times 2^-e[0] and masses times 2^-e[1]
 __global__ void k_gather(const double* __restrict__ x, const double* __restrict__ mu, const int* __restrict__ idx,
-                         int n, d4* __restrict__ xm, int* __restrict__ perm) {
+                         int n, d4* __restrict__ xm, int* __restrict__ perm, const int* __restrict__ e) {
+    const double fx = e ? pow2i(-e[0]) : 1.0, fm = e ? pow2i(-e[1]) : 1.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int j = idx[i];
-        xm[i] = mk4(x[3 * (long long)j], x[3 * (long long)j + 1], x[3 * (long long)j + 2], mu[j]);
+        xm[i] = mk4(x[3 * (long long)j] * fx, x[3 * (long long)j + 1] * fx, x[3 * (long long)j + 2] * fx, mu[j] * fm);
         perm[i] = j;
     }
 }
 
 void launch_gather(const double* x, const double* mu, const int* idx, int n, d4* xm, int* perm,
-                   cudaStream_t s) {
-    if (n > 0) k_gather<<<grid_for(n, 256), 256, 0, s>>>(x, mu, idx, n, xm, perm); note_launch();
+                   cudaStream_t s, const int* e) {
+    if (n > 0) k_gather<<<grid_for(n, 256), 256, 0, s>>>(x, mu, idx, n, xm, perm, e); note_launch();
+}
+
+// The mixed-precision path works in units in which the system's extent and its largest mass
+// lie in [1, 2): positions and masses are scaled by powers of two (exact), so the FP32
+// parts (pair terms, high expansion orders, estimate) stay in range whatever the caller's
+// units, and the outputs are scaled back exactly.  One thread; e[0], e[1]: the exponents.
+__global__ void k_work_units(const unsigned long long* __restrict__ b, int nsys, int* __restrict__ e) {
+    if (blockIdx.x || threadIdx.x) return;
+    const int ns = nsys > 0 ? nsys : 1;
+    double ext = 0.0;
+    for (int k = 0; k < ns; ++k)
+        for (int d = 0; d < 3; ++d) {
+            const double lo = key_dbl(b[6 * k + d]), hi = key_dbl(b[6 * k + 3 + d]);
+            if (hi >= lo) ext = fmax(ext, hi - lo);
+        }
+    const double mmax = key_dbl(b[6 * ns]);
+    const bool use_m = b[6 * ns] != 0ull && mmax > 0.0 && isfinite(mmax);
+    int el = (ext > 0.0 && isfinite(ext)) ? ilogb(ext) : 0, em = use_m ? ilogb(mmax) : 0;
+    e[0] = max(-1000, min(1000, el));
+    e[1] = max(-1000, min(1000, em));
+}
+void launch_work_units(const unsigned long long* bounds, int nsys, int* e, cudaStream_t s) {
+    k_work_units<<<1, 32, 0, s>>>(bounds, nsys, e);
+    note_launch();
 }
 
 // ------------------------------------------------------------------ A3 oct-tree

@@ -219,12 +219,16 @@ void launch_minscale_level(Cells c, int lev_begin, int lev_end, cudaStream_t s) 
     int ncl = lev_end - lev_begin;
     if (ncl > 0) k_minscale_level<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end); note_launch();
 }
+// the caller's scale (an acceleration, ~ mu / x^2) in the working units (e nullable)
 __global__ void k_scale_from_caller(const double* __restrict__ scale, const int* __restrict__ perm, int n,
-                                    double* __restrict__ out) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = scale[perm[i]];
+                                    double* __restrict__ out, const int* __restrict__ e) {
+    const int ks = e ? 2 * e[0] - e[1] : 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = ldexp(scale[perm[i]], ks);
 }
-void launch_scale_from_caller(const double* scale, const int* perm, int n, double* scale_sorted, cudaStream_t s) {
-    if (n > 0) k_scale_from_caller<<<grid_for(n, 256), 256, 0, s>>>(scale, perm, n, scale_sorted); note_launch();
+void launch_scale_from_caller(const double* scale, const int* perm, int n, double* scale_sorted, cudaStream_t s,
+                              const int* e) {
+    if (n > 0) k_scale_from_caller<<<grid_for(n, 256), 256, 0, s>>>(scale, perm, n, scale_sorted, e); note_launch();
 }
 
 }  // namespace gb3

@@ -121,6 +121,23 @@ def test_walk_single_precision_view_extremes(g, orc, shift, mscale):
     assert np.max(np.abs(psi - run.psi) / run.psi) <= PARITY_TOL
 
 
+@pytest.mark.parametrize("ex,em", [(70, 100), (-60, -90), (0, 0)])
+def test_mixed_mode_any_units(g, ex, em):
+    """Mixed precision works in units in which the extent and the largest mass are of order
+    one (powers of two, exact): a system in other units (here positions x 2^ex and masses
+    x 2^em, far outside the FP32 range for |ex|, |em| >= 60) gives Psi x 2^(em - ex) and
+    a x 2^(em - 2 ex), bit for bit."""
+    x, mu = inputs.plummer(20000, inputs.BASE_SEED + 140)
+    ctx = g.Context(p=10, eps=1e-6, leaf_size=32, precision=g.FMM_PREC_MIXED)
+    psi0, acc0 = ctx.fmm_evaluate(_dev(x), _dev(mu))
+    psi1, acc1 = ctx.fmm_evaluate(_dev(np.ldexp(x, ex)), _dev(np.ldexp(mu, em)))
+    p0, a0 = psi0.cpu().numpy(), acc0.cpu().numpy()
+    assert np.all(np.isfinite(a0)) and np.all(p0 > 0)
+    assert np.array_equal(psi1.cpu().numpy(), np.ldexp(p0, em - ex))
+    assert np.array_equal(acc1.cpu().numpy(), np.ldexp(a0, em - 2 * ex))
+    ctx.close()
+
+
 def test_estimate_scale_matches_oracle(g, orc):
     x, mu = inputs.config_input(1)
     for mac in (0, 1):
