@@ -1466,19 +1466,6 @@ void launch_f_p2p(const d4* xm, Cells c, const int2* list, const int* seg_start,
     note_launch();
 }
 
-__global__ void k_norm_scale(const double* __restrict__ af, const double* __restrict__ an, int n,
-                             double* __restrict__ scale) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double x = af[3 * (size_t)i] + an[3 * (size_t)i], y = af[3 * (size_t)i + 1] + an[3 * (size_t)i + 1],
-               z = af[3 * (size_t)i + 2] + an[3 * (size_t)i + 2];
-        scale[i] = sqrt(x * x + y * y + z * z);
-    }
-}
-void launch_norm_scale(const double* /*psi_far*/, const double* acc_far, const double* acc_near, int n, double* scale,
-                       cudaStream_t s) {
-    if (n > 0) k_norm_scale<<<grid_for(n, 256), 256, 0, s>>>(acc_far, acc_near, n, scale); note_launch();
-}
-
 // ---------------------------------------------------------------- finish (A12)
 __global__ void k_finish(const double* __restrict__ pf, const double* __restrict__ af, const double* __restrict__ pn,
                          const double* __restrict__ an, const int* __restrict__ perm, int n, double G,

@@ -238,9 +238,6 @@ void launch_est_m2l(const int2* list, const int* seg_start, const int* seg_end, 
 // the estimate's far field at p = 1 plus its near field, as the scale |a| per sorted particle
 void launch_est_scale(Cells c, const int* leaves, int nleaves, const double* F1, const double* acc_near,
                       double* scale, cudaStream_t s);
-// |far + near| of the p = 1 estimate into the per-particle scale
-void launch_norm_scale(const double* psi_far, const double* acc_far, const double* acc_near, int n,
-                       double* scale, cudaStream_t s);
 // combine far + near, multiply by G and scatter to the caller's order (A12)
 // (ensemble: Gsys[k] for the caller particles [off[k], off[k+1]) instead of G)
 // e (nullable): the working units (launch_work_units); psi is scaled back by 2^(e1 - e0), a by
