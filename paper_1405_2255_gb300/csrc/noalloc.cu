@@ -191,10 +191,15 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     int* scan_tmp = A.take<int>(scan_tmp_ints(cap));
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the particle arrays");
     NA_CU(cudaMemsetAsync(r.status, 0, sizeof(unsigned), s));
+    // working units of the mixed path (positions and masses scaled by powers of two)
+    int* units = A.take<int>(2);
+    if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the particle arrays");
     launch_bounds(x, mu, n, bounds, r.status, s);
+    if (prm.precision == FMM_PREC_MIXED) launch_work_units(bounds, 0, units, s);
+    else NA_CU(cudaMemsetAsync(units, 0, 2 * sizeof(int), s));
     launch_keys(x, n, bounds, r.keys, idx, s);
     radix_sort_pairs(r.keys, idx, keys_alt, idx_alt, n, rtmp, s);
-    launch_gather(x, mu, idx, n, r.xm, r.perm, s);
+    launch_gather(x, mu, idx, n, r.xm, r.perm, s, units);
     k_root_na<<<1, 1, 0, s>>>(r.c, n);
     note_launch();
     // top-down levels
@@ -371,7 +376,8 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     }
     if (split) launch_l2p_split(r.xm, r.c, r.c.sr, r.leaves, r.nleaves, p, F, psi_far, acc_far, s);
     else launch_l2p(r.xm, r.c, r.c.sr, r.leaves, r.nleaves, p, F, psi_far, acc_far, s);
-    launch_finish(psi_far, acc_far, psi_near, acc_near, r.perm, n, G, psi, acc, s);
+    launch_finish(psi_far, acc_far, psi_near, acc_near, r.perm, n, G, psi, acc, s, nullptr, nullptr, 0, nullptr,
+                  units);
     NA_CU(cudaGetLastError());
     return 0;
 }

@@ -57,6 +57,24 @@ def test_noalloc_matches_evaluate_on_two_calls(g, precision):
     ctx.close()
 
 
+def test_noalloc_mixed_any_units(g):
+    """The working units of the mixed path here too: positions x 2^70 and masses x 2^100
+    give Psi x 2^30 and a x 2^-40, bit for bit."""
+    import torch
+    prm = dict(p=8, eps=1e-6, leaf_size=32, p2p_c=4.0, precision=1)
+    x, mu = inputs.plummer(4000, inputs.BASE_SEED + 13)
+    out = []
+    for ex, em in ((0, 0), (70, 100)):
+        psi = torch.empty(len(mu), dtype=torch.float64, device="cuda:0")
+        acc = torch.empty((len(mu), 3), dtype=torch.float64, device="cuda:0")
+        g.fmm_evaluate_noalloc(_dev(np.ldexp(x, ex)), _dev(np.ldexp(mu, em)), 1.0, psi=psi, acc=acc, **prm)
+        torch.cuda.synchronize()
+        out.append((psi.cpu().numpy(), acc.cpu().numpy()))
+    assert np.all(np.isfinite(out[0][1]))
+    assert np.array_equal(out[1][0], np.ldexp(out[0][0], 30))
+    assert np.array_equal(out[1][1], np.ldexp(out[0][1], -40))
+
+
 def test_noalloc_rejects_too_many_particles(g):
     x, mu = inputs.plummer(8193, 3)
     with pytest.raises(g.FMMError) as e:
