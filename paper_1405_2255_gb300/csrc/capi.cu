@@ -1005,15 +1005,16 @@ int64_t fmm_footprint_bytes(const fmm_params* prm, int64_t n) {
     if (n < 0 || check_params(prm)) return -1;
     const double leaf = prm->leaf_size, P = (prm->p + 1.0) * (prm->p + 1.0), nd = (double)n;
     // particle arrays (sorted copies, keys, two-float positions, near/far results,
-    // ensemble sort keys, a serving slot's staging)
-    const double particles = 1.25 * 264.0 * nd;
+    // ensemble sort keys, owning cells of the radii pass, a serving slot's staging)
+    const double particles = 1.25 * 268.0 * nd;
     // cell arrays sized by the cell capacity n + 21 n / (leaf + 1)
     const double cap = nd + 21.0 * std::floor(nd / (leaf + 1.0)) + 64.0;
     const double cellcap = 1.25 * 104.0 * cap;
     // per cell built: M, F, their FP32/FP64 split copies and M2L scratch, power,
-    // the low-order estimate and per-cell scratch; then the lists
+    // the low-order estimate, the walk's single-precision view (<= 128 B), the radii
+    // scratch (72 B) and per-cell scratch; then the lists
     const double cells = kCellsPerLeafN * nd / leaf + 64.0;
-    const double per_cell = 1.25 * 48.0 * P + 2000.0 + kM2LPerCell * (kPairBytes + 1.25 * 8.0 * P / 32.0) +
+    const double per_cell = 1.25 * 48.0 * P + 2200.0 + kM2LPerCell * (kPairBytes + 1.25 * 8.0 * P / 32.0) +
                             (kP2PPerCell + kEstPerCell) * kPairBytes;
     return (int64_t)(particles + cellcap + per_cell * cells) + (int64_t)(16 << 20);
 }
