@@ -56,9 +56,14 @@ extern "C" {
 
 /* arithmetic of the path */
 #define FMM_PREC_FP64   0  /* every step in IEEE FP64                                   */
-#define FMM_PREC_MIXED  1  /* P2P in FP32 on two-float leaf-relative positions with
-                              compensated accumulation; M2L terms of order > 2 in FP32
-                              (m2l_split); everything else FP64                       */
+#define FMM_PREC_MIXED  1  /* P2P in FP32 on two-float positions with compensated
+                              accumulation; expansion terms of order > 2 (> 1 in the
+                              rotated M2L) in FP32 on radius-scaled harmonics
+                              (m2l_split, m2l_rot); the acceleration estimate's M2L in
+                              FP32; everything else FP64.  Computed in units in which
+                              the extent and the largest mass are of order one (exact
+                              powers of two), so the results do not depend on the
+                              caller's units                                          */
 
 /* source of the acceleration scale used by (18a)/(18b) */
 #define FMM_SCALE_ESTIMATE 0  /* low-order FMM estimate (Sec. 5.3.2)                  */
