@@ -13,6 +13,11 @@ Parity status per function (the pins live in tests/test_oracle_*.py):
   M2L/L2L/L2P   pinned: against direct summation (converges as p grows), strict
                 bound eq. (12), L2L exactness, L2P gradient vs finite differences.
   MEB           pinned: brute force over support sets on small point sets.
+  estimate E~   pinned: eq. (17) equals 4 theta^p (equal radii) and 8 (rho/r)^p (one radius
+                zero) for a point-mass source, where E = theta^p exactly (Sec. 4.2); a spread
+                source lies strictly between the point-mass and all-at-the-centre values;
+                Sec. 4's single-interaction statistics (relative errors above E~ <= 2 %,
+                absolute <= 10 %, overestimates by > 10x <= 2 %, eq. 12 always).
   walk / FMM    pinned: reduction to direct summation (eps -> 0), N <= leaf size,
                 whole-FMM error vs brute force, Plummer closed form, momentum.
   direct sum    pinned: two-body and symmetric closed forms, Plummer closed form.
@@ -103,6 +108,10 @@ def _declare(L):
     L.orc_run_lists.argtypes = [C.c_void_p, _lp, _lp]
     L.orc_run_perm.argtypes = [C.c_void_p, _lp]
     L.orc_run_scale.argtypes = [C.c_void_p, _dp]
+    L.orc_mac_lhs.argtypes = [C.c_int, _dp, C.c_double, C.c_double, C.c_double]
+    L.orc_mac_lhs.restype = C.c_double
+    L.orc_interaction_errors.argtypes = [C.c_void_p, C.c_long, C.c_long, C.c_int, _dp]
+    L.orc_interaction_errors.restype = C.c_int
 
 
 def _c3(v):
@@ -186,6 +195,45 @@ def power(p, M):
     P = np.zeros(p + 1)
     lib().orc_power(p, mr, mi, P)
     return P
+
+
+def error_estimate(P, r, rho_a, rho_b, mass, q=None):
+    """E~_{A->B} of eq. (17) from the source cell's multipole powers P_0..P_q (eq. 14), the
+    distance r = |s_B - z_A|, the radii rho_A, rho_B and the mass M_A: the quantity the
+    oracle's walk compares, divided by M_A / r^2."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    q = len(P) - 1 if q is None else q
+    return lib().orc_mac_lhs(q, P, float(r), float(rho_a), float(rho_b)) * r * r / mass
+
+
+def interaction_errors(x, mu, p, theta_crit=0.7, leaf_size=32, p2p_c=1.0, sample=None, seed=0):
+    """Sec. 4's single-interaction experiment: the cell pairs (A, B) that a walk with the
+    geometric criterion theta < theta_crit (eq. 9) accepts, minus those with
+    N_A N_B < p2p_c p^3, each evaluated alone at order p against direct summation.
+    Returns an array [pairs, 4]: max delta a r^2 / M_A, max delta a / a, E~ (eq. 17), theta."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    prm = Params(p, 1.0, MAC_THETA, theta_crit, leaf_size, p2p_c, 0, 0, 0)
+    L = lib()
+    h = L.orc_fmm_active(len(mu), x, mu, 1.0, C.byref(prm), None, None, None)
+    if not h:
+        raise ValueError("oracle rejected the input")
+    try:
+        st = Stats()
+        L.orc_run_stats(h, C.byref(st))
+        m2 = np.zeros((max(st.n_m2l, 1), 2), dtype=np.int64)
+        pp = np.zeros((max(st.n_p2p, 1), 2), dtype=np.int64)
+        L.orc_run_lists(h, m2, pp)
+        m2 = m2[:st.n_m2l]
+        if sample is not None and sample < len(m2):
+            m2 = m2[np.sort(np.random.default_rng(seed).choice(len(m2), sample, replace=False))]
+        out, row = [], np.zeros(4)
+        for a, b in m2:
+            if L.orc_interaction_errors(h, int(a), int(b), p, row):
+                out.append(row.copy())
+        return np.array(out).reshape(-1, 4)
+    finally:
+        L.orc_run_free(h)
 
 
 def direct(x, mu, G=1.0, sinks=None):

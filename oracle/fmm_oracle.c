@@ -935,22 +935,23 @@ typedef struct {
     int p, mac, use_com;
     double eps, theta_crit, p2p_thresh;
     const double *P;      /* multipole power [ncells][p+1] (MAC_A/MAC_F) */
-    double *binom;        /* C(p, k) */
     int adaptive;         /* per-interaction order (Sec. 7, opening) */
     plist m2l, p2p;
 } walk_t;
 
-/* E~_{A->B} M_A / r^2 of order q, eqs. (15)-(17), without the division by M_A */
-static double mac_lhs(const walk_t *w, const double *P, double r, double ra, double rb, int q)
+/* E~_{A->B} M_A / r^2 of order q, eqs. (15)-(17), without the division by M_A:
+ * M_A E_{A->B} = sum_k C(q,k) P_k rho_B^{q-k} / r^q (eq. 15; P_k of eq. 14 for the source
+ * cell A, P_0 = M_A), times 8 max(rho_A, rho_B) / (rho_A + rho_B) (eq. 17), over r^2.
+ * The one function behind every acceptance decision of the oracle's walk. */
+double orc_mac_lhs(int q, const double *P, double r, double ra, double rb)
 {
-    double sum = 0, cqk = 1.0;  /* C(q, k) */
+    double sum = 0, cqk = 1.0;  /* C(q, k), exact integers for q <= 20 */
     for (int k = 0; k <= q; ++k) {
         sum += cqk * (P[k] / pow(r, k)) * pow(rb / r, q - k);
         cqk = cqk * (q - k) / (k + 1);
     }
     double mx = ra > rb ? ra : rb;
     double fac = (ra + rb > 0) ? 8.0 * mx / (ra + rb) : 8.0;
-    (void)w;
     return fac * sum / (r * r);
 }
 
@@ -968,17 +969,12 @@ static int accept(const walk_t *w, long A, long B)
     if (w->mac == MAC_EST) return w->p > 0 ? w->p : 1;
     /* E~_{A->B} M_A / r^2, eqs. (15)-(17), without the division by M_A */
     const double *P = &w->P[(long)A * (w->p + 1)];
-    double sum = 0;
-    for (int k = 0; k <= w->p; ++k)
-        sum += w->binom[k] * (P[k] / pow(r, k)) * pow(rb / r, w->p - k);
-    double mx = ra > rb ? ra : rb;
-    double fac = (ra + rb > 0) ? 8.0 * mx / (ra + rb) : 8.0;
-    double lhs = fac * sum / (r * r);
+    const double lhs = orc_mac_lhs(w->p, P, r, ra, rb);
     const double rhs = w->eps * b->minscale;
     if (!(lhs < rhs)) return 0;             /* eqs. (18a) / (18b) */
     if (w->adaptive)
         for (int q = w->p < 3 ? w->p : 3; q < w->p; ++q)
-            if (mac_lhs(w, P, r, ra, rb, q) < rhs) return q;
+            if (orc_mac_lhs(q, P, r, ra, rb) < rhs) return q;
     return w->p;
 }
 
@@ -1252,8 +1248,6 @@ static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, con
     w.eps = prm->eps; w.theta_crit = prm->theta_crit;
     w.p2p_thresh = prm->p2p_c * pow((double)p, 3);
     w.P = P;
-    w.binom = malloc(sizeof(double) * (p + 1));
-    for (int k = 0; k <= p; ++k) w.binom[k] = round(tgamma(p + 1.0) / (tgamma(k + 1.0) * tgamma(p - k + 1.0)));
     walk(&w, 0, 0);
     run->m2l = w.m2l;
     run->p2p = w.p2p;
@@ -1305,7 +1299,7 @@ static void evaluate_on_tree(orc_run *run, double G, const double *scale_in, con
             }
         }
     }
-    free(ps); free(ac); free(M); free(F); free(P); free(w.binom); free(tn);
+    free(ps); free(ac); free(M); free(F); free(P); free(tn);
 }
 
 /* Sec. 7.1's re-cycled tree: the particle order, cells and centres of the run prev (the same
@@ -1399,6 +1393,51 @@ void orc_run_lists(const orc_run *run, long *m2l /* [n_m2l][2] */, long *p2p /* 
 void orc_run_m2l_orders(const orc_run *run, int *q)
 {
     for (long i = 0; i < run->m2l.n; ++i) q[i] = run->m2l.v[i].q;
+}
+/* The single-interaction experiment of Sec. 4 (its Figs. 2-3): the particles of sink cell B
+ * receive the interaction of source cell A through the chain P2M (eq. 3c, about z_A = s_A),
+ * M2L (eq. 3b, to s_B) and L2P (eqs. 3a, 7) at order p, and the FP64 direct sum of A's
+ * particles (eq. 1) is the truth.  out[0] = max over b in B of delta a_b r^2 / M_A;
+ * out[1] = max over b of delta a_b / |a_b|, a_b the true acceleration due to A;
+ * out[2] = E~_{A->B} of eq. (17) (from orc_mac_lhs, times r^2 / M_A); out[3] = theta of
+ * eq. (9) with rho_z = rho_s = rho.  Returns 0 when A or B is not a cell of the run, A has
+ * no mass, or A = B. */
+int orc_interaction_errors(const orc_run *run, long A, long B, int p, double *out)
+{
+    const tree_t *t = &run->t;
+    if (A < 0 || B < 0 || A >= t->ncells || B >= t->ncells || A == B || p < 1 || p > 20) return 0;
+    const cell_t *a = &t->cells[A], *b = &t->cells[B];
+    if (!(a->mass > 0)) return 0;
+    const int nco = NCOEF(p);
+    cplx *M = calloc(nco, sizeof(cplx)), *F = calloc(nco, sizeof(cplx));
+    double *P = calloc(p + 1, sizeof(double));
+    p2m(p, a->count, &t->xs[3 * a->first], &t->mus[a->first], a->s, M);
+    multipole_power(p, M, P);
+    m2l(p, M, a->s, b->s, F);
+    const double r = dist3(b->s, a->s);
+    double e_abs = 0, e_rel = 0;
+    for (long i = b->first; i < b->first + b->count; ++i) {
+        const double *xb = &t->xs[3 * i];
+        double psi_l, af[3], at[3] = {0, 0, 0};
+        l2p(p, F, b->s, xb, &psi_l, af);
+        for (long j = a->first; j < a->first + a->count; ++j) {
+            const double d[3] = {t->xs[3 * j] - xb[0], t->xs[3 * j + 1] - xb[1], t->xs[3 * j + 2] - xb[2]};
+            const double rr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            const double q = t->mus[j] / (rr * rr * rr);
+            for (int k = 0; k < 3; ++k) at[k] += q * d[k];
+        }
+        const double da = sqrt((af[0] - at[0]) * (af[0] - at[0]) + (af[1] - at[1]) * (af[1] - at[1]) +
+                               (af[2] - at[2]) * (af[2] - at[2]));
+        const double an = sqrt(at[0] * at[0] + at[1] * at[1] + at[2] * at[2]);
+        if (da * r * r / a->mass > e_abs) e_abs = da * r * r / a->mass;
+        if (an > 0 && da / an > e_rel) e_rel = da / an;
+    }
+    out[0] = e_abs;
+    out[1] = e_rel;
+    out[2] = orc_mac_lhs(p, P, r, a->rho, b->rho) * r * r / a->mass;
+    out[3] = (a->rho + b->rho) / r;
+    free(M); free(F); free(P);
+    return 1;
 }
 void orc_run_perm(const orc_run *run, long *perm) { memcpy(perm, run->t.perm, sizeof(long) * run->t.n); }
 void orc_run_scale(const orc_run *run, double *scale_sorted)

@@ -141,18 +141,21 @@ def test_geometric_mac_error_falls_with_p(orc, plummer4k):
 
 
 def test_low_order_estimate_accuracy(orc, plummer4k):
-    """The p = 1 (a) and p = 0 (f) low-order estimates are rough (~15 % rms, Sec. 5.3.2)."""
+    """The p = 1 (a) and p = 0 (f) low-order estimates have rms relative errors of ~15 %
+    (Sec. 5.3.2): within [5 %, 30 %] and without a bias beyond a few per cent."""
     x, mu, psi, acc, f = plummer4k
     run = orc.fmm(x, mu, p=6, eps=1e-6, leaf_size=16)
     a_est = np.empty(len(mu))
     a_est[run.perm] = run.scale
     e = a_est / np.linalg.norm(acc, axis=1) - 1
-    assert np.sqrt(np.mean(e ** 2)) < 0.5
+    assert 0.05 <= np.sqrt(np.mean(e ** 2)) <= 0.3
+    assert abs(np.mean(e)) < 0.05
     run = orc.fmm(x, mu, p=6, eps=1e-6, mac=orc.MAC_F, leaf_size=16)
     f_est = np.empty(len(mu))
     f_est[run.perm] = run.scale
     e = f_est / f - 1
-    assert np.sqrt(np.mean(e ** 2)) < 0.5
+    assert 0.05 <= np.sqrt(np.mean(e ** 2)) <= 0.3
+    assert abs(np.mean(e)) < 0.05
 
 
 def test_momentum(orc, plummer4k):
