@@ -284,24 +284,30 @@ int fmm_swap_matrix(int n, double* B);
 int fmm_alu_peaks(double* fp64_tflops, double* fp32_tflops);
 
 /* fmm_evaluate for small systems without allocating any device memory.
- * (The paper has no counterpart: this is a service of the library.)  Callers that
- * cannot allocate -- code running while a stream is captured into a CUDA graph,
- * simulation codes whose device memory is owned by their own pool, plugins that
- * may not grow the process's footprint -- evaluate systems of up to 8192
- * particles here.  All scratch memory comes from one fixed 32 MiB array in
- * device global memory that every GPU loading the library holds until the
- * process exits; nothing calls cudaMalloc, cudaFree or any other device
- * allocator.  On its first call on a device the entry point looks up that array's
- * device address (cudaGetSymbolAddress, with the device current); make that first
- * call before any stream capture.  All calls share the array and it keeps the last
- * call's contents (what must start at zero is cleared on every call); calls whose
- * work overlaps on the GPU race on it and give wrong results, so serialise them.
+ * (The paper has no counterpart: this is a service of the library.)  Some callers
+ * cannot allocate: simulation codes whose device memory belongs to their own pool
+ * allocator (a cudaMalloc behind the pool's back breaks its accounting and can
+ * fail once the pool holds the memory), and plugins that may not grow the host
+ * process's device footprint.  They evaluate systems of up to 8192 particles
+ * here.  All scratch memory comes from one fixed 32 MiB array in device global
+ * memory that every GPU loading the library holds until the process exits;
+ * nothing calls cudaMalloc, cudaFree or any other device allocator.  On its first
+ * call on a device the entry point looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (what must start at zero is cleared on every call); calls whose work
+ * overlaps on the GPU race on it and give wrong results, so serialise them.  The
+ * call waits for its stream several times (the tree's level sizes and the walk's
+ * frontier lengths are read on the host).
  *   n       0 <= n <= 8192, else FMM_E_INVALID
  *   x, mu   device, [n][3] and [n] FP64 (as fmm_evaluate)
- *   params  host; p <= 10, leaf_size >= 16, scale_src = FMM_SCALE_ESTIMATE
+ *   params  host; p <= 10, 24 <= leaf_size <= 4096, scale_src = FMM_SCALE_ESTIMATE
  *   psi/acc device outputs (as fmm_evaluate)
- *   stream  cudaStream_t or NULL; the call synchronises it a few times
+ *   stream  cudaStream_t or NULL
  *   errbuf  host, may be NULL: receives a one-line description of a failure
+ * The M2L and P2P lists hold at most 196,608 cell pairs each: parameters that need
+ * longer lists (at n near 8192: eps below ~1e-8, or p2p_c below ~2 with eps near
+ * 1e-7) return FMM_E_OVERFLOW.
  * Returns 0, FMM_E_INVALID, FMM_E_OVERFLOW (an interaction list or the tree does
  * not fit in the array) or FMM_E_CUDA. */
 int fmm_evaluate_noalloc(int64_t n, const double* x, const double* mu, double G, const fmm_params* params,

@@ -14,6 +14,25 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     return FMM_E_CUDA;
 }
 
+// SM count per device, queried on first use (0 = not yet known)
+static int g_sm_count[64] = {0};
+int sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 148;  // a query that fails only sizes grid-stride loops
+    }
+    int n = __atomic_load_n(&g_sm_count[dev], __ATOMIC_RELAXED);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            return 148;
+        }
+        __atomic_store_n(&g_sm_count[dev], n, __ATOMIC_RELAXED);
+    }
+    return n;
+}
+
 thread_local long long g_launches = 0;
 void note_launch() { ++g_launches; }
 long long launches_so_far() { return g_launches; }

@@ -105,8 +105,13 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 void note_launch();
 long long launches_so_far();
 
-inline unsigned grid_for(long long n, int block, long long cap = 152LL * 64) {
+// streaming multiprocessors of the current device (queried once per device)
+int sm_count();
+
+// blocks for n items of `block` threads, at most per_sm blocks per SM (grid-stride loops)
+inline unsigned grid_for(long long n, int block, int per_sm = 64) {
     long long g = (n + block - 1) / block;
+    const long long cap = (long long)sm_count() * per_sm;
     if (g < 1) g = 1;
     if (g > cap) g = cap;
     return (unsigned)g;

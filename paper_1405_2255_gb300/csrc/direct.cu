@@ -6,6 +6,7 @@ namespace gb3 {
 
 constexpr int kDirThreads = 128;
 
+template <bool WANT_F>
 __global__ void __launch_bounds__(kDirThreads) k_direct(const double* __restrict__ x, const double* __restrict__ mu,
                                                         int n, double G, const int64_t* __restrict__ sinks,
                                                         int nsinks, double* __restrict__ psi,
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(kDirThreads) k_direct(const double* __restrict
                         const double qm = q.w * rinv;
                         const double q3 = qm * rinv * rinv;
                         ps += qm;
-                        fs += q.w * rinv * rinv;
+                        if (WANT_F) fs += q.w * rinv * rinv;
                         ax = fma(q3, dx, ax);
                         ay = fma(q3, dy, ay);
                         az = fma(q3, dz, az);
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(kDirThreads) k_direct(const double* __restrict
             acc[3 * (long long)t] = G * ax;
             acc[3 * (long long)t + 1] = G * ay;
             acc[3 * (long long)t + 2] = G * az;
-            if (f) f[t] = G * fs;
+            if (WANT_F) f[t] = G * fs;
         }
     }
 }
@@ -53,8 +54,10 @@ __global__ void __launch_bounds__(kDirThreads) k_direct(const double* __restrict
 void launch_direct(const double* x, const double* mu, int n, double G, const int64_t* sinks, int nsinks,
                    double* psi, double* acc, double* f, cudaStream_t s) {
     if (nsinks <= 0) return;
-    unsigned g = grid_for(nsinks, kDirThreads, 152 * 32);
-    k_direct<<<g, kDirThreads, 0, s>>>(x, mu, n, G, sinks, nsinks, psi, acc, f); note_launch();
+    unsigned g = grid_for(nsinks, kDirThreads, 32);
+    if (f) k_direct<true><<<g, kDirThreads, 0, s>>>(x, mu, n, G, sinks, nsinks, psi, acc, f);
+    else k_direct<false><<<g, kDirThreads, 0, s>>>(x, mu, n, G, sinks, nsinks, psi, acc, f);
+    note_launch();
 }
 
 }  // namespace gb3

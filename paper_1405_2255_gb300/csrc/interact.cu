@@ -737,7 +737,7 @@ void launch_l2p(const d4* xm, Cells c, const d4* cen, const int* leaves, int nle
                 double* psi, double* acc, cudaStream_t s) {
     if (nleaves <= 0) return;
     size_t sm = (size_t)ncoef(p) * sizeof(cd);
-    unsigned g = nleaves < 152 * 64 ? nleaves : 152 * 64;
+    unsigned g = (unsigned)std::min<long long>(nleaves, (long long)sm_count() * 64);
     k_l2p<<<g, kL2PThreads, sm, s>>>(xm, c, cen, leaves, nleaves, p, F, psi, acc); note_launch();
 }
 
@@ -806,7 +806,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_fp64(const d4* __restric
 
 static unsigned p2p_grid(int nleaves) {
     long long g = ((long long)nleaves + kP2PWarps - 1) / kP2PWarps;
-    return (unsigned)(g < 152 * 48 ? g : 152 * 48);
+    return (unsigned)std::min<long long>(g, (long long)sm_count() * 48);
 }
 
 void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_start, const int* seg_end,
@@ -1361,7 +1361,7 @@ void launch_est_m2l(const int2* list, const int* seg_start, const int* seg_end, 
     if (ncells <= 0) return;
     if (fc) {
         const long long warps = ncells;
-        const unsigned g = (unsigned)std::min<long long>((warps + 7) / 8, 152LL * 16);
+        const unsigned g = (unsigned)std::min<long long>((warps + 7) / 8, (long long)sm_count() * 16);
         k_est_m2l_f32<<<g, 256, 0, s>>>(list, seg_start, seg_end, ncells, c, fc, F1);
     } else {
         k_est_m2l<<<(ncells + 127) / 128, 128, 0, s>>>(list, seg_start, seg_end, ncells, c, F1);
@@ -1403,7 +1403,7 @@ __global__ void k_est_scale(Cells c, const int* __restrict__ leaves, int nleaves
 void launch_est_scale(Cells c, const int* leaves, int nleaves, const double* F1, const double* acc_near,
                       double* scale, cudaStream_t s) {
     if (nleaves <= 0) return;
-    const unsigned g = (unsigned)std::min<long long>(((long long)nleaves + 7) / 8, 152LL * 16);
+    const unsigned g = (unsigned)std::min<long long>(((long long)nleaves + 7) / 8, (long long)sm_count() * 16);
     k_est_scale<<<g, 256, 0, s>>>(c, leaves, nleaves, F1, acc_near, scale);
     note_launch();
 }

@@ -2,11 +2,11 @@
 // small systems, with every piece of scratch memory taken from one fixed array
 // in device global memory instead of from cudaMalloc.
 //
-// Some callers cannot allocate device memory: code running while a stream is
-// being captured into a CUDA graph (allocation calls are not capturable),
-// simulation codes whose memory is owned by their own pool allocator, and
-// plugins that are not allowed to grow the process's device footprint.  This
-// entry point lets them evaluate systems of up to kNoAllocMaxN particles.
+// Some callers cannot allocate device memory: simulation codes whose memory is
+// owned by their own pool allocator, and plugins that are not allowed to grow the
+// process's device footprint.  This entry point lets them evaluate systems of up
+// to kNoAllocMaxN particles.  It waits for its stream several times (level sizes
+// and frontier lengths are read on the host), like fmm_evaluate.
 //
 // The scratch array is a file-scope __device__ variable: every GPU that loads
 // the library holds it (kNoAllocBytes) until the process exits.  Host code cannot
@@ -270,7 +270,6 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     double* F = A.take<double>((size_t)nco * nc);
     double* Pw = A.take<double>((size_t)(p + 1) * nc);
     double* binom = A.take<double>(kMaxP + 1);
-    double* M1 = A.take<double>(4 * (size_t)nc);
     double* F1 = A.take<double>(4 * (size_t)nc);
     double* Ff = A.take<double>(nc);
     float4* walkf = A.take<float4>((size_t)(2 + walk_fstride(p) / 4) * nc);
@@ -301,10 +300,10 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
             for (int L = 1; L < nl; ++L) launch_f_down_level(r.c, r.lev[L], r.lev[L + 1], Ff, s);
             launch_f_p2p(r.xm, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, Ff, scale, s);
         } else {
-            NA_CU(cudaMemsetAsync(F1, 0, sizeof(double) * 4 * (size_t)nc, s));
-            launch_p2m(r.xm, r.c, r.c.cr, r.leaves, r.nleaves, 1, M1, s);
-            for (int L = nl - 1; L >= 0; --L) launch_m2m_level(r.c, r.c.cr, r.lev[L], r.lev[L + 1], 1, M1, s);
-            launch_m2l(est_m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.cr, M1, 1, F1, s);
+            // the estimate's monopole M2L about the centres of mass, as fmm_evaluate takes it
+            // (FP32 from the walk's single-precision view in mixed mode)
+            launch_est_m2l(est_m2l, m2l_seg_start, m2l_seg_end, nc, r.c, F1, s,
+                           prm.precision == FMM_PREC_MIXED ? walkf : nullptr);
             // (the p = 1 L2L is folded into launch_est_scale)
             if (prm.precision == FMM_PREC_MIXED)
                 launch_p2p_mixed(r.xm, xhi, xlo, n, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near,
@@ -400,8 +399,8 @@ extern "C" int fmm_evaluate_noalloc(int64_t n, const double* x, const double* mu
     if (prm.mac != FMM_MAC_THETA && !(prm.eps > 0)) return report(fail_na(r, FMM_E_INVALID, "eps must be > 0"));
     if (prm.mac == FMM_MAC_THETA && !(prm.theta_crit > 0 && prm.theta_crit < 1))
         return report(fail_na(r, FMM_E_INVALID, "theta_crit must be in (0,1)"));
-    if (prm.leaf_size < 16 || prm.leaf_size > 4096)
-        return report(fail_na(r, FMM_E_INVALID, "leaf_size must be in [16, 4096] here"));
+    if (prm.leaf_size < 24 || prm.leaf_size > 4096)
+        return report(fail_na(r, FMM_E_INVALID, "leaf_size must be in [24, 4096] here"));
     if (prm.precision != FMM_PREC_FP64 && prm.precision != FMM_PREC_MIXED)
         return report(fail_na(r, FMM_E_INVALID, "unknown precision"));
     if (prm.scale_src != FMM_SCALE_ESTIMATE)

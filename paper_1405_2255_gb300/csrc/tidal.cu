@@ -77,7 +77,7 @@ void launch_l2p_tidal(const d4* xm, Cells c, const d4* cen, const int* leaves, i
                       double* T, cudaStream_t s) {
     if (nleaves <= 0) return;  // (p < 2: the loops are empty and T_far = 0)
     const size_t sm = sizeof(cd) * (size_t)ncoef(p);
-    const unsigned g = (unsigned)(nleaves < 152 * 16 ? nleaves : 152 * 16);
+    const unsigned g = (unsigned)std::min<long long>(nleaves, (long long)sm_count() * 16);
     k_l2p_tidal<<<g, kTidThreads, sm, s>>>(xm, c, cen, leaves, nleaves, p, F, T);
     note_launch();
 }
@@ -193,7 +193,7 @@ void launch_p2p_tidal(const d4* xm, const float* hi, const float* lo, int n, boo
                       cudaStream_t s) {
     if (nleaves <= 0) return;
     long long g = ((long long)nleaves + kTidWarps - 1) / kTidWarps;
-    if (g > 152 * 32) g = 152 * 32;
+    if (g > (long long)sm_count() * 32) g = (long long)sm_count() * 32;
     if (fp32) k_p2p_tidal<true><<<(unsigned)g, kTidWarps * 32, 0, s>>>(xm, hi, lo, n, c, list, seg_start, seg_end,
                                                                       leaves, nleaves, T);
     else k_p2p_tidal<false><<<(unsigned)g, kTidWarps * 32, 0, s>>>(xm, hi, lo, n, c, list, seg_start, seg_end, leaves,

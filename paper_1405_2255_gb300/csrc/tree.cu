@@ -54,7 +54,7 @@ __global__ void k_bounds(const double* __restrict__ x, const double* __restrict_
 void launch_bounds(const double* x, const double* mu, int n, unsigned long long* bounds, unsigned* status,
                    cudaStream_t s) {
     k_bounds_init<<<1, 32, 0, s>>>(bounds); note_launch();
-    if (n > 0) k_bounds<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, mu, n, bounds, status); note_launch();
+    if (n > 0) k_bounds<<<grid_for(n, 256, 8), 256, 0, s>>>(x, mu, n, bounds, status); note_launch();
 }
 
 // ------------------------------------------------------------------ A2 keys
@@ -176,7 +176,7 @@ __global__ void k_bounds_sys(const double* __restrict__ x, const double* __restr
 void launch_bounds_sys(const double* x, const double* mu, int n, const int* off, int nsys,
                        unsigned long long* bounds, unsigned* status, cudaStream_t s) {
     k_bounds_init_sys<<<grid_for(6LL * nsys + 1, 256), 256, 0, s>>>(bounds, nsys); note_launch();
-    if (n > 0) k_bounds_sys<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(x, mu, n, off, nsys, bounds, status); note_launch();
+    if (n > 0) k_bounds_sys<<<grid_for(n, 256, 8), 256, 0, s>>>(x, mu, n, off, nsys, bounds, status); note_launch();
 }
 
 __global__ void k_keys_sys(const double* __restrict__ x, int n, const int* __restrict__ off, int nsys,
@@ -1226,10 +1226,10 @@ void launch_internal_geometry(const d4* xm, const float* xhi, const float* xlo, 
     if (keep_centre) k_internal_keep<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end, rad_tmp);
     else k_internal_meb<<<(unsigned)ncl, kMebWarps * 32, 0, s>>>(c, lev_begin, lev_end, status, rad_tmp);
     note_launch();
-    k_internal_radii_lb<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xhi, xlo, n, c, lev_begin, lev_end, owner,
+    k_internal_radii_lb<<<grid_for(n, 256, 16), 256, 0, s>>>(xhi, xlo, n, c, lev_begin, lev_end, owner,
                                                                      rad_tmp);
     note_launch();
-    k_internal_radii<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(xm, xhi, xlo, n, c, lev_begin, lev_end, owner,
+    k_internal_radii<<<grid_for(n, 256, 16), 256, 0, s>>>(xm, xhi, xlo, n, c, lev_begin, lev_end, owner,
                                                                   rad_tmp);
     note_launch();
     k_internal_radii_finish<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, rad_tmp); note_launch();

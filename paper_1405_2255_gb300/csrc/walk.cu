@@ -281,13 +281,13 @@ void launch_walk_roots(int2* front, int nroots, cudaStream_t s, unsigned long lo
 void launch_walk_step(Cells c, WalkParams wp, const int2* front_in, long long nfront, int2* front_out,
                       WalkBuffers wb, cudaStream_t s) {
     if (nfront <= 0) return;
-    k_walk<<<grid_for(nfront, 256, 152 * 16), 256, 0, s>>>(c, wp, front_in, nfront, nullptr, front_out, wb,
+    k_walk<<<grid_for(nfront, 256, 16), 256, 0, s>>>(c, wp, front_in, nfront, nullptr, front_out, wb,
                                                              &wb.counters[0]);
     note_launch();
 }
 void launch_walk_step_dev(Cells c, WalkParams wp, const int2* front_in, const unsigned long long* nfront_dev,
                           int2* front_out, WalkBuffers wb, unsigned long long* out_cnt, cudaStream_t s) {
-    k_walk<<<152 * 8, 256, 0, s>>>(c, wp, front_in, 0, nfront_dev, front_out, wb, out_cnt);
+    k_walk<<<sm_count() * 8, 256, 0, s>>>(c, wp, front_in, 0, nfront_dev, front_out, wb, out_cnt);
     note_launch();
 }
 

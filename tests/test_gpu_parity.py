@@ -104,6 +104,20 @@ def test_fmm_fp64_matches_oracle(g, orc, case):
     assert np.max(np.abs(psi - run.psi) / run.psi) <= PARITY_TOL
 
 
+def test_fmm_fp64_matches_oracle_at_benchmark_parameters(g, orc):
+    """Plummer N = 2e5 from the benchmark's generator at the benchmark's parameters (p = 14,
+    eps = 3e-7, leaf 80, p2p_c 1) in FP64 mode: tree, lists and forces equal the oracle's.
+    This reaches the order-14 FP64 M2L, sinks whose lists span many work items and lists
+    larger than a fresh context's first capacity."""
+    x, mu = inputs.plummer(200000, inputs.BASE_SEED + 2)
+    psi, acc, st, dump, run = _run_both(g, orc, x, mu, p=14, eps=3e-7, leaf_size=80, p2p_c=1.0)
+    flips, nm, npp = _compare_structure(dump, run)
+    assert flips == 0 and nm > 100000 and npp > 100000
+    assert st["n_m2l"] == run.stats["n_m2l"] and st["p2p_interactions"] == run.stats["p2p_interactions"]
+    assert np.max(_rel(acc, run.acc)) <= PARITY_TOL
+    assert np.max(np.abs(psi - run.psi) / run.psi) <= PARITY_TOL
+
+
 @pytest.mark.parametrize("shift,mscale", [(1e5, 1.0), (0.0, 1e-38), (0.0, 1e36), (3e3, 1e-20)])
 def test_walk_single_precision_view_extremes(g, orc, shift, mscale):
     """The walk takes its acceptance test in FP32 from a single-precision view of the cells and
@@ -384,13 +398,15 @@ def test_small_then_large_on_one_context(g):
     ctx.close()
 
 
-@pytest.mark.parametrize("p", [3, 5, 8, 12, 14, 16])
-def test_m2l_rot_matches_direct(g, orc, p):
+@pytest.mark.parametrize("p,leaf,n", [(3, 24, 6000), (5, 24, 6000), (8, 24, 6000), (12, 24, 6000), (14, 24, 6000),
+                                      (16, 24, 6000), (14, 80, 40000)])
+def test_m2l_rot_matches_direct(g, orc, p, leaf, n):
     """The rotation-accelerated M2L (App. A.5: z rotations, swap matrices, eq. A31) gives
     the direct eq. (3b) result up to FP32 rounding: same lists, same FP64 low orders, and
-    both against the oracle's FP64 FMM on those lists."""
-    x, mu = inputs.plummer(6000, inputs.BASE_SEED + 80 + p)
-    kw = dict(p=p, mac=g.FMM_MAC_THETA, theta_crit=0.6, leaf_size=24, p2p_c=0.0, precision=g.FMM_PREC_MIXED)
+    both against the oracle's FP64 FMM on those lists (p = 14 also at the benchmark's leaf
+    size 80)."""
+    x, mu = inputs.plummer(n, inputs.BASE_SEED + 80 + p + (leaf if leaf != 24 else 0))
+    kw = dict(p=p, mac=g.FMM_MAC_THETA, theta_crit=0.6, leaf_size=leaf, p2p_c=0.0, precision=g.FMM_PREC_MIXED)
     c_rot, c_dir = g.Context(m2l_rot=1, **kw), g.Context(m2l_rot=0, **kw)
     _, a_rot, st = c_rot.fmm_evaluate(_dev(x), _dev(mu), stats=True)
     _, a_dir = c_dir.fmm_evaluate(_dev(x), _dev(mu))
@@ -398,7 +414,7 @@ def test_m2l_rot_matches_direct(g, orc, p):
     a_rot, a_dir = a_rot.cpu().numpy(), a_dir.cpu().numpy()
     d = _rel(a_rot, a_dir)
     assert np.sqrt(np.mean(d ** 2)) < 1e-7 and d.max() < 2e-6
-    run = orc.fmm(x, mu, p=p, mac=orc.MAC_THETA, theta_crit=0.6, leaf_size=24, p2p_c=0.0)
+    run = orc.fmm(x, mu, p=p, mac=orc.MAC_THETA, theta_crit=0.6, leaf_size=leaf, p2p_c=0.0)
     e_rot, e_dir = _rel(a_rot, run.acc), _rel(a_dir, run.acc)
     assert np.sqrt(np.mean(e_rot ** 2)) < 1.5 * np.sqrt(np.mean(e_dir ** 2)) + 2e-8
     assert e_rot.max() < 4e-6

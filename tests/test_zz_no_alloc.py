@@ -1,8 +1,9 @@
 """The allocation-free entry point fmm_evaluate_noalloc, called through the C ABI.
 
-Callers that cannot allocate device memory (inside a CUDA graph capture, under a
-foreign pool allocator) evaluate small systems with it; the library takes all its
-scratch from one fixed array in device memory.  This file is collected last so
+Callers that cannot allocate device memory (simulation codes whose device memory
+belongs to their own pool allocator, plugins that may not grow the process's
+footprint) evaluate small systems with it; the library takes all its scratch from
+one fixed array in device memory.  This file is collected last so
 that a run stopping at the first failure has run every other test first; it also
 passes when run alone in a fresh process.
 """
@@ -73,6 +74,33 @@ def test_noalloc_mixed_any_units(g):
     assert np.all(np.isfinite(out[0][1]))
     assert np.array_equal(out[1][0], np.ldexp(out[0][0], 30))
     assert np.array_equal(out[1][1], np.ldexp(out[0][1], -40))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("model", ["plummer", "cusp"])
+def test_noalloc_at_its_documented_limits(g, precision, model):
+    """The largest documented case fits the fixed array: n = 8192, p = 10, leaf_size = 24
+    (eps 1e-7, p2p_c 2), both precisions, with the same result as fmm_evaluate."""
+    import torch
+    prm = dict(p=10, eps=1e-7, leaf_size=24, p2p_c=2.0, precision=precision)
+    x, mu = (inputs.plummer if model == "plummer" else inputs.dehnen)(8192, inputs.BASE_SEED + 14)
+    xd, md = _dev(x), _dev(mu)
+    ctx = g.Context(**prm)
+    psi_ref, acc_ref = ctx.fmm_evaluate(xd, md, 1.0)
+    psi = torch.empty(8192, dtype=torch.float64, device="cuda:0")
+    acc = torch.empty((8192, 3), dtype=torch.float64, device="cuda:0")
+    g.fmm_evaluate_noalloc(xd, md, 1.0, psi=psi, acc=acc, **prm)
+    torch.cuda.synchronize()
+    assert np.max(_rel(acc.cpu().numpy(), acc_ref.cpu().numpy())) <= TOL
+    ctx.close()
+
+
+def test_noalloc_reports_list_overflow(g):
+    """Lists longer than the fixed capacity end in FMM_E_OVERFLOW, not in a wrong result."""
+    x, mu = inputs.plummer(8192, inputs.BASE_SEED + 15)
+    with pytest.raises(g.FMMError) as e:
+        g.fmm_evaluate_noalloc(_dev(x), _dev(mu), 1.0, p=10, eps=1e-9, leaf_size=24, p2p_c=0.0)
+    assert e.value.code == g.FMM_E_OVERFLOW
 
 
 def test_noalloc_rejects_too_many_particles(g):
