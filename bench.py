@@ -29,7 +29,7 @@ UNIT = "particle-forces/s"
 L2_FLUSH_BYTES = 256 << 20
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -51,30 +51,50 @@ def parse():
     ap.add_argument("--requests", type=int, default=384, help="serve: requests in the open-loop run")
     ap.add_argument("--autotune", action="store_true",
                     help="choose (p, eps, leaf, p2p_c) for rms 1e-7 on the workload first (untimed)")
-    a = ap.parse_args()
+    ap.add_argument("--no-configs", action="store_true",
+                    help="plummer: skip the sub-records of the cusp, ensemble and served-stream workloads")
+    a = ap.parse_args(argv)
     if a.workload in ("cusp", "active") and a.n == 1_000_000:
         a.n = 10_000_000
-    # (p, eps, leaf, p2p_c) per workload from the autotuner at rms 1e-7 (eps with a margin):
-    # the single large systems take leaf 80; ensembles of small systems leaf 48, where
-    # large leaves let accepted pairs with theta near 1 dominate the error
-    dflt = {"plummer": (14, 3e-7, 80, 1.0), "cusp": (14, 2.6e-7, 80, 1.0),
-            "ensemble": (14, 3.6e-7, 48, 1.0), "serve": (14, 2.2e-7, 48, 1.0),
-            "active": (14, 3e-7, 80, 1.0)}[a.workload]
-    for k, v in zip(("p", "eps", "leaf", "c"), dflt):
+    for k, v in zip(("p", "eps", "leaf", "c"), PARAMS[a.workload]):
         if getattr(a, k) is None:
             setattr(a, k, v)
     return a
+
+
+# (p, eps, leaf, p2p_c) per workload from the autotuner at rms 1e-7 (eps with a margin; the
+# Plummer sphere's on 10^5 sampled sinks, the truth sample of the bench, whose rms includes
+# the few particles near the centre where |a| -> 0): the single large systems take leaf 80;
+# ensembles of small systems leaf 48, where large leaves let accepted pairs with theta near 1
+# dominate the error
+PARAMS = {"plummer": (14, 2.3e-7, 80, 1.0), "cusp": (14, 2.6e-7, 80, 1.0),
+          "ensemble": (14, 3.6e-7, 48, 1.0), "serve": (14, 2.0e-7, 48, 1.0),
+          "active": (14, 2.3e-7, 80, 1.0)}
 
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-# ALU peaks derived from the unit counts and the maximum SM clock: 152 SMs x 128 FP32
-# lanes x 2 flops (FFMA) x 2070 MHz; FP64 is the part's nominal 1.25 TFLOP/s
-SM_COUNT, SM_MAX_MHZ = 152, 2070.0
-FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# ALU peaks derived from the unit counts and the maximum SM clock: SMs x 128 FP32 lanes x
+# 2 flops (FFMA) x the maximum SM clock (the SM count and clock are read from the device);
+# FP64 is the part's nominal 1.25 TFLOP/s
 FP64_PEAK_TFLOPS = 1.25
+
+
+def fp32_peak(dev=None):
+    """(TFLOP/s, SM count, max SM MHz) of the FP32 FMA pipes of the device."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = 2070.0
+    try:
+        q = subprocess.run(["nvidia-smi", f"--id={torch.cuda.current_device() if dev is None else dev.index}",
+                            "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                           capture_output=True, text=True, timeout=20)
+        mhz = float(q.stdout.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        pass
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
 
 
 def max_over_ranks(v, world, device=None):
@@ -221,9 +241,7 @@ def reference_arm(a, rank, world):
 # DRAM bytes (read + write) per launch of the dominant kernels, from one ncu capture of
 # the same workload and parameters (summaries and commands under profiles/); None for
 # any other configuration or once the kernel has changed since the capture
-MEASURED_TRAFFIC = {
-    ("plummer", 1000000, 14, 3e-7, 80, 1.0, "mixed"): {"k_p2p_mixed": 94.43e6, "k_m2l_rot": 198.87e6},
-}
+MEASURED_TRAFFIC = {}
 
 
 def roofline(g, a, prec, phase, full):
@@ -233,8 +251,9 @@ def roofline(g, a, prec, phase, full):
     t_p2p = float(np.mean([s["t_p2p"] for s in phase])) * 1e-3
     loop64, loop32 = g.fmm_alu_peaks()
     mixed = prec == g.FMM_PREC_MIXED
-    pk, loop = (FP32_PEAK_TFLOPS, loop32) if mixed else (FP64_PEAK_TFLOPS, loop64)
-    src = ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz" if mixed
+    p32, sms, mhz = fp32_peak()
+    pk, loop = (p32, loop32) if mixed else (FP64_PEAK_TFLOPS, loop64)
+    src = (f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz" if mixed
            else "nominal FP64 rate of the part (1.25 TFLOP/s)")
     if t_m2l >= t_p2p:
         rot = mixed and 3 <= a.p <= 16
@@ -274,11 +293,29 @@ def cpu_sample_line(a, model="plummer"):
                       f"recipe and parameters, one evaluation ({tcpu:.1f} s)"}
 
 
-def run_ensemble(a, g, dev, local, rank, world, prec):
+def event_ms(fn, stream, warm=3, reps=10, flush=None):
+    """Median CUDA-event time (ms, on stream) of fn() over reps runs after warm untimed runs;
+    flush (a tensor larger than L2) is overwritten before every timed run."""
+    import torch
+    for _ in range(warm):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in ev:
+        if flush is not None:
+            flush.zero_()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return float(np.median([e0.elapsed_time(e1) for e0, e1 in ev]))
+
+
+def ensemble_record(a, g, dev, local, rank, world, prec, steps, warmup, emit_line):
     """256 Plummer spheres of N log-uniform in [1e3, 1e5] with Kroupa-like masses,
     evaluated together as one forest per step (fmm_evaluate_batch)."""
     import torch
     from paper_1405_2255_gb300 import inputs
+    p, eps, leaf, c = (a.p, a.eps, a.leaf, a.c) if a.workload == "ensemble" else PARAMS["ensemble"]
     systems = inputs.ensemble(256, inputs.BASE_SEED + 4 + 7919 * rank)
     sizes = np.array([len(m) for _, m in systems])
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
@@ -290,20 +327,20 @@ def run_ensemble(a, g, dev, local, rank, world, prec):
     acc = torch.empty((ntot, 3), dtype=torch.float64, device=dev)
     G = np.ones(len(systems))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    ctx = g.Context(p=a.p, eps=a.eps, leaf_size=a.leaf, p2p_c=a.c, precision=prec, device=local)
+    ctx = g.Context(p=p, eps=eps, leaf_size=leaf, p2p_c=c, precision=prec, device=local)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(max(a.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         ctx.fmm_evaluate_batch(off, xt, mt, G, psi=psi, acc=acc)
     torch.cuda.synchronize(dev)
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     phase, launches = [], 0
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
-        for k in range(a.steps):
+        for k in range(steps):
             flush.zero_()
             ev0[k].record(stream)
             ctx.fmm_evaluate_batch(off, xt, mt, G, psi=psi, acc=acc)
@@ -315,7 +352,6 @@ def run_ensemble(a, g, dev, local, rank, world, prec):
     ms_step = max_over_ranks(np.mean([e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1)]), world, dev)
     value = job_value(ntot, world, ms_step * 1e-3)
     _, _, full = ctx.fmm_evaluate_batch(off, xt, mt, G, psi=psi, acc=acc, stats=True)
-    roof = roofline(g, a, prec, phase, full)
     # accuracy: 16 sinks of every system against the FP64 direct sum over that system
     rng = np.random.default_rng(rank)
     errs = []
@@ -325,6 +361,17 @@ def run_ensemble(a, g, dev, local, rank, world, prec):
         idx = np.sort(rng.choice(n, min(n, 16), replace=False))
         errs.append(sampled_error(ctx, xt[sl], mt[sl], acc[sl], idx, dev))
     e = np.concatenate(errs)
+    rec = {"workload": "ensemble256_plummer_kroupa", "value": value, "unit": UNIT, "ms_per_step": ms_step,
+           "steps": steps, "systems": len(systems), "n_total": ntot,
+           "n_range": [int(sizes.min()), int(sizes.max())], "p": p, "eps": eps, "leaf_size": leaf, "p2p_c": c,
+           "rms_rel_err": float(np.sqrt(np.mean(e ** 2))), "p999_rel_err": float(np.percentile(e, 99.9)),
+           "err_sinks": int(len(e)), "launches_per_step": launches / steps,
+           "phase_ms": {k: float(np.mean([s_[k] for s_ in phase])) for k in
+                        ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total")}}
+    if not emit_line:
+        ctx.close()
+        return rec
+    roof = roofline(g, a, prec, phase, full)
     extras = {}
     if not a.no_extras and rank == 0:
         # the same systems one call each (no forest)
@@ -340,7 +387,7 @@ def run_ensemble(a, g, dev, local, rank, world, prec):
     ah = torch.empty((ntot, 3), dtype=torch.float64).pin_memory()
     ph = torch.empty(ntot, dtype=torch.float64).pin_memory()
     te = []
-    for k in range(a.steps + 1):
+    for k in range(steps + 1):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -356,17 +403,15 @@ def run_ensemble(a, g, dev, local, rank, world, prec):
     cpu = cpu_sample_line(a) if rank == 0 and world == 1 else None
     if rank == 0:
         cfg = {"workload": "ensemble256_plummer_kroupa", "systems": len(systems), "n_total": ntot,
-               "n_range": [int(sizes.min()), int(sizes.max())],
+               "n_range": rec["n_range"],
                "model": "256 truncated Plummer spheres, N log-uniform in [1e3, 1e5], Kroupa-like masses",
-               "p": a.p, "eps": a.eps, "mac": "18a (low-order a estimate)", "leaf_size": a.leaf, "p2p_c": a.c,
+               "p": p, "eps": eps, "mac": "18a (low-order a estimate)", "leaf_size": leaf, "p2p_c": c,
                "precision": a.precision, "l2": "flushed between steps (256 MiB write)",
                "parallelism": "one forest per call; replicas across GPUs",
-               "rms_rel_err": float(np.sqrt(np.mean(e ** 2))), "p999_rel_err": float(np.percentile(e, 99.9)),
-               "err_sinks": int(len(e)),
-               "phase_ms": {k: float(np.mean([s[k] for s in phase])) for k in
-                            ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total")}}
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-                "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "rms_rel_err": rec["rms_rel_err"], "p999_rel_err": rec["p999_rel_err"],
+               "err_sinks": rec["err_sinks"], "phase_ms": rec["phase_ms"]}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+                "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64" if prec == g.FMM_PREC_MIXED else "f64",
                 "data": "synthetic", "config": cfg,
                 "e2e": {"value": job_value(ntot, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": 32 * ntot,
@@ -375,23 +420,31 @@ def run_ensemble(a, g, dev, local, rank, world, prec):
         line.update(extras)
         print(json.dumps(line), flush=True)
     ctx.close()
+    return rec
 
 
-def run_serve(a, g, dev, local, rank, world, prec):
+def run_ensemble(a, g, dev, local, rank, world, prec):
+    ensemble_record(a, g, dev, local, rank, world, prec, a.steps, a.warmup, True)
+
+
+def serve_record(a, g, dev, local, rank, world, prec, nreq, warmup, cap_rounds):
     """64 concurrent simulations (half Plummer, half gamma = 1.5 cusps, N log-uniform in
     [1e4, 2e6]) served by the request loop.  Capacity is measured closed-loop (all
     systems submitted at once); then requests arrive as a Poisson process at 0.8 of
     that capacity, each system taking the next request once its previous result is
-    back, and latency is counted from arrival to completion."""
+    back, and latency is counted from arrival to completion.  Returns the record and
+    the clock summary."""
     import torch
     from paper_1405_2255_gb300 import inputs
+    p, eps, leaf, c = (a.p, a.eps, a.leaf, a.c) if a.workload == "serve" else PARAMS["serve"]
     systems = inputs.served_systems(64, inputs.BASE_SEED + 5 + 7919 * rank)
     sizes = np.array([len(m) for _, m in systems])
     dx = [torch.from_numpy(x).to(dev) for x, _ in systems]
     dm = [torch.from_numpy(m).to(dev) for _, m in systems]
+    del systems
     dp = [torch.empty(n, dtype=torch.float64, device=dev) for n in sizes]
     da = [torch.empty((n, 3), dtype=torch.float64, device=dev) for n in sizes]
-    ctx = g.Context(p=a.p, eps=a.eps, leaf_size=a.leaf, p2p_c=a.c, precision=prec, device=local)
+    ctx = g.Context(p=p, eps=eps, leaf_size=leaf, p2p_c=c, precision=prec, device=local)
     ctx.fmm_serve_config(0, 2)
     ids = [ctx.fmm_system_register(int(n)) for n in sizes]
     torch.cuda.synchronize(dev)
@@ -403,17 +456,16 @@ def run_serve(a, g, dev, local, rank, world, prec):
             ctx.fmm_poll(t, -1)
         return time.perf_counter() - t0
 
-    for _ in range(max(a.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         closed_loop()
-    caps = [closed_loop() for _ in range(max(a.steps, 1))]
+    caps = [closed_loop() for _ in range(max(cap_rounds, 1))]
     t_cap = float(np.median(caps))
     capacity = float(sizes.sum()) / t_cap
     # open loop: aggregate Poisson arrivals at 0.8 capacity, systems in turn
-    nreq = a.requests
     rate = 0.8 * capacity / float(sizes.mean())
     arrivals = inputs.poisson_arrivals(nreq, rate, inputs.BASE_SEED + 5 + 31 * rank)
-    order = np.arange(nreq) % len(systems)
-    backlog = [[] for _ in systems]
+    order = np.arange(nreq) % len(sizes)
+    backlog = [[] for _ in sizes]
     inflight = {}
     lat, done_n = [], 0
     nxt = 0
@@ -425,7 +477,7 @@ def run_serve(a, g, dev, local, rank, world, prec):
                 k = int(order[nxt])
                 backlog[k].append(arrivals[nxt])
                 nxt += 1
-            for k in range(len(systems)):
+            for k in range(len(sizes)):
                 if backlog[k] and k not in inflight:
                     t_arr = backlog[k].pop(0)
                     ts = time.perf_counter() - t0
@@ -439,14 +491,14 @@ def run_serve(a, g, dev, local, rank, world, prec):
                     del inflight[k]
             time.sleep(2e-4)
         elapsed = time.perf_counter() - t0
-    value = done_n / elapsed
     lat_ms = 1e3 * np.array(lat)
+    ctx.close()
     # the results of the last requests against each system alone, and their accuracy
-    alone = g.Context(p=a.p, eps=a.eps, leaf_size=a.leaf, p2p_c=a.c, precision=prec, device=local)
+    alone = g.Context(p=p, eps=eps, leaf_size=leaf, p2p_c=c, precision=prec, device=local)
     same = 0
     errs = []
     rng = np.random.default_rng(rank)
-    for k in range(len(systems)):
+    for k in range(len(sizes)):
         p1, a1 = alone.fmm_evaluate(dx[k], dm[k], 1.0)
         same += int(torch.equal(a1, da[k]) and torch.equal(p1, dp[k]))
         idx = np.sort(rng.choice(int(sizes[k]), 64, replace=False))
@@ -455,30 +507,36 @@ def run_serve(a, g, dev, local, rank, world, prec):
         errs.append(sampled_error(alone, dx[k], dm[k], da[k], np.unique(idx), dev))
     e = np.concatenate(errs)
     alone.close()
-    cpu = cpu_sample_line(a) if rank == 0 and world == 1 else None
     value = sum_over_ranks(done_n, world, dev) / max_over_ranks(elapsed, world, dev)
+    rec = {"workload": "serve64_plummer_cusp", "value": value, "unit": UNIT, "systems": len(sizes),
+           "n_total": int(sizes.sum()), "n_range": [int(sizes.min()), int(sizes.max())], "p": p, "eps": eps,
+           "leaf_size": leaf, "p2p_c": c, "slots": 2, "requests": nreq, "load": 0.8,
+           "capacity_pf_s": capacity, "closed_loop_ms": 1e3 * t_cap,
+           "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                          "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
+           "results_equal_alone": f"{same}/{len(sizes)}",
+           "rms_rel_err": float(np.sqrt(np.mean(e ** 2))), "p999_rel_err": float(np.percentile(e, 99.9)),
+           "err_sinks": int(len(e))}
+    return rec, clk.summary()
+
+
+def run_serve(a, g, dev, local, rank, world, prec):
+    rec, clocks = serve_record(a, g, dev, local, rank, world, prec, a.requests, a.warmup, a.steps)
+    cpu = cpu_sample_line(a) if rank == 0 and world == 1 else None
     if rank == 0:
-        cfg = {"workload": "serve64_plummer_cusp", "systems": len(systems), "n_total": int(sizes.sum()),
-               "n_range": [int(sizes.min()), int(sizes.max())],
-               "model": "32 truncated Plummer spheres + 32 gamma=1.5 cusps with 1% central point mass, "
-                        "N log-uniform in [1e4, 2e6]",
-               "p": a.p, "eps": a.eps, "mac": "18a (low-order a estimate)", "leaf_size": a.leaf, "p2p_c": a.c,
-               "precision": a.precision, "slots": 2, "requests": nreq, "load": 0.8,
-               "capacity_pf_s": capacity, "closed_loop_ms": 1e3 * t_cap,
-               "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
-                              "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
-               "results_equal_alone": f"{same}/{len(systems)}",
-               "rms_rel_err": float(np.sqrt(np.mean(e ** 2))), "p999_rel_err": float(np.percentile(e, 99.9)),
-               "err_sinks": int(len(e)), "l2": "inputs larger than L2 (19M particles resident)",
-               "parallelism": "2 slots with continuous batching; replicas across GPUs"}
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": nreq,
-                "warmup": a.warmup, "ms_per_step": float(lat_ms.mean()), "higher_is_better": True,
+        cfg = dict(rec)
+        cfg.update({"model": "32 truncated Plummer spheres + 32 gamma=1.5 cusps with 1% central point mass, "
+                             "N log-uniform in [1e4, 2e6]", "mac": "18a (low-order a estimate)",
+                    "precision": a.precision, "l2": "inputs larger than L2 (19M particles resident)",
+                    "parallelism": "2 slots with continuous batching; replicas across GPUs"})
+        for k in ("value", "unit"):
+            cfg.pop(k)
+        line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": a.requests,
+                "warmup": a.warmup, "ms_per_step": rec["latency_ms"]["mean"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if prec == g.FMM_PREC_MIXED else "f64", "data": "synthetic", "config": cfg,
-                "e2e": None, "roofline": None, "cpu_baseline": cpu, "gpu_launches": None,
-                "clocks": clk.summary()}
+                "e2e": None, "roofline": None, "cpu_baseline": cpu, "gpu_launches": None, "clocks": clocks}
         print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def run_active(a, g, dev, local, rank, world, prec):
@@ -576,6 +634,84 @@ def config_of(a):
             "precision": a.precision, "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas"}
 
 
+# (p, eps, leaf, p2p_c) of the plain all-FP64 GPU FMM (precision = FP64) at rms 1e-7 on the
+# default workload: its own autotuner optimum over p 10..16, leaf 32..128, p2p_c 1..4 (truth on
+# 10^5 sampled sinks; eps with a margin)
+FP64_PARAMS = (16, 3.3e-7, 96, 1.0)
+
+
+def cusp_record(a, g, dev, local, rank, prec, steps, warmup):
+    """gamma = 1.5 Dehnen cusp of 1e7 particles with a 1 % central point mass."""
+    import torch
+    from paper_1405_2255_gb300 import inputs
+    p, eps, leaf, c = PARAMS["cusp"]
+    n = 10_000_000
+    x, mu = inputs.dehnen(n, inputs.BASE_SEED + 3 + 7919 * rank)
+    xt, mt = torch.from_numpy(x).to(dev), torch.from_numpy(mu).to(dev)
+    del x, mu
+    psi = torch.empty(n, dtype=torch.float64, device=dev)
+    acc = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    ctx = g.Context(p=p, eps=eps, leaf_size=leaf, p2p_c=c, precision=prec, device=local)
+    stream = torch.cuda.current_stream(dev)
+    ms = event_ms(lambda: ctx.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc), stream, max(warmup, 3), steps)
+    rng = np.random.default_rng(rank)
+    pick = rng.choice(n, 10000, replace=False)
+    pick[0] = 0  # the central point mass
+    e = sampled_error(ctx, xt, mt, acc, np.unique(pick), dev)
+    ctx.close()
+    return {"workload": f"cusp_n{n}", "value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "timing": f"median of {steps} after {max(warmup, 3)} warm-up (inputs larger than L2)",
+            "p": p, "eps": eps, "leaf_size": leaf, "p2p_c": c,
+            "rms_rel_err": float(np.sqrt(np.mean(e ** 2))), "p999_rel_err": float(np.percentile(e, 99.9)),
+            "err_sinks": int(len(e))}
+
+
+def crossover(g, dev, local, prec, flush):
+    """Sec. 6.4's comparison with direct summation: the mixed FMM against the GPU FP64 direct
+    sum for N = 1e4 .. 1e6 (Plummer spheres of the default generator).  At every N the FMM's
+    eps is set by the autotuner's secant steps so that the rms relative error over up to 32768
+    sinks (all of them for N <= 32768) is at most 1e-7 (p = 14, p2p_c = 1; leaf 48 below
+    N = 3e5, 80 from there on); the direct sum runs over all sinks up to N = 1e5 and over
+    32768 sampled sinks above (scaled to N)."""
+    import torch
+    from paper_1405_2255_gb300 import autotune, inputs
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for n in (10_000, 30_000, 100_000, 300_000, 1_000_000):
+        x, mu = inputs.plummer(n, inputs.BASE_SEED + 2)
+        xt, mt = torch.from_numpy(x).to(dev), torch.from_numpy(mu).to(dev)
+        p, eps, leaf, c = PARAMS["ensemble"] if n < 300_000 else PARAMS["plummer"]
+        tr = autotune.tune(xt, mt, target_rms=1e-7, ps=(p,), leaves=(leaf,), cs=(c,), nsinks=min(n, 32768),
+                           precision=prec, eps0=eps, margin=0.95)
+        eps = tr.best.eps
+        ctx = g.Context(p=p, eps=eps, leaf_size=leaf, p2p_c=c, precision=prec, device=local)
+        psi = torch.empty(n, dtype=torch.float64, device=dev)
+        acc = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        ms = event_ms(lambda: ctx.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc), stream, 3, 5, flush)
+        ns = n if n <= 100_000 else 32768
+        sinks = None if ns == n else torch.from_numpy(
+            np.sort(np.random.default_rng(n).choice(n, ns, replace=False)).astype(np.int64)).to(dev)
+        ms_d = event_ms(lambda: ctx.fmm_direct(xt, mt, 1.0, sinks=sinks), stream, 1, 3)
+        _, acc_t = ctx.fmm_direct(xt, mt, 1.0, sinks=sinks)
+        idx = torch.arange(n, device=dev) if sinks is None else sinks
+        e = (torch.linalg.norm(acc[idx] - acc_t, dim=1) / torch.linalg.norm(acc_t, dim=1)).cpu().numpy()
+        fmm_v, dir_v = n / (ms * 1e-3), ns / (ms_d * 1e-3)
+        rows.append({"n": n, "fmm_value": fmm_v, "fmm_ms": ms, "direct_value": dir_v,
+                     "direct_ms_scaled": ms_d * n / ns, "direct_sinks": ns, "fmm_over_direct": fmm_v / dir_v,
+                     "fmm_rms_rel_err": float(np.sqrt(np.mean(e ** 2))), "p": p, "eps": eps, "leaf_size": leaf})
+        ctx.close()
+        del xt, mt, psi, acc, acc_t
+    # the smallest N of the sweep from which on the FMM beats direct summation at every larger N
+    cross = None
+    for r in reversed(rows):
+        if r["fmm_over_direct"] > 1.0:
+            cross = r["n"]
+        else:
+            break
+    return {"rows": rows, "fmm_faster_from_n": cross,
+            "timing": "CUDA events; FMM median of 5 after 3 warm-ups (L2 flushed), direct median of 3 after 1"}
+
+
 def main():
     a = parse()
     rank, world, local = dist_env()
@@ -645,20 +781,21 @@ def main():
     ms = max_over_ranks(np.mean([e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1)]), world, dev)
     value = job_value(a.n, world, ms * 1e-3)
 
-    # accuracy of the timed configuration: GPU FP64 direct sum on sampled sinks
+    # accuracy of the timed configuration: GPU FP64 direct sum over all sources for a seeded
+    # sample of 10^5 sinks (fewer when N is smaller)
     rng = np.random.default_rng(rank)
-    ns = min(a.n, 4096)
+    ns = min(a.n, 100_000)
     pick = rng.choice(a.n, ns, replace=False)
     if a.workload == "cusp":
         pick[0] = 0  # the central point mass is always in the sample
     sinks = torch.from_numpy(np.sort(np.unique(pick)).astype(np.int64)).to(dev)
     ns = int(sinks.numel())
-    torch.cuda.synchronize(dev)
-    td0 = time.perf_counter()
     _, acc_t = ctx.fmm_direct(xt, mt, 1.0, sinks=sinks)
-    torch.cuda.synchronize(dev)
-    t_direct = time.perf_counter() - td0
-    e = (torch.linalg.norm(acc[sinks] - acc_t, dim=1) / torch.linalg.norm(acc_t, dim=1)).cpu().numpy()
+
+    def errors(acc_):
+        return (torch.linalg.norm(acc_[sinks] - acc_t, dim=1) / torch.linalg.norm(acc_t, dim=1)).cpu().numpy()
+
+    e = errors(acc)
     rms, p999 = float(np.sqrt(np.mean(e ** 2))), float(np.percentile(e, 99.9))
 
     # roofline of the dominant kernel (phase times averaged over the timed steps)
@@ -667,32 +804,77 @@ def main():
 
     extras = {}
     if not a.no_extras and rank == 0:
-        # the plain all-FP64 GPU FMM on the same input and parameters
-        c64 = g.Context(p=a.p, eps=a.eps, leaf_size=a.leaf, p2p_c=a.c, precision=g.FMM_PREC_FP64, device=local)
-        c64.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        e0.record(stream)
-        c64.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        extras["fp64_fmm_value"] = a.n / (e0.elapsed_time(e1) * 1e-3)
+        base = {}
+        # (i) the plain all-FP64 GPU FMM at its own tuned parameters, and at the mixed mode's
+        p64, eps64, leaf64, c64_ = FP64_PARAMS
+        c64 = g.Context(p=p64, eps=eps64, leaf_size=leaf64, p2p_c=c64_, precision=g.FMM_PREC_FP64, device=local)
+        ms64 = event_ms(lambda: c64.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc), stream, 3, 10, flush)
+        e64 = errors(acc)
+        c64.set_params(p=a.p, eps=a.eps, leaf_size=a.leaf, p2p_c=a.c)
+        ms64m = event_ms(lambda: c64.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc), stream, 1, 3, flush)
         c64.close()
-        # GPU FP64 direct summation, timed on the sampled sinks and scaled to N sinks
-        extras["fp64_direct_value"] = a.n / (t_direct * a.n / ns)
-        extras["direct_sample_sinks"] = ns
+        base["fp64_fmm"] = {"value": a.n / (ms64 * 1e-3), "ms": ms64, "p": p64, "eps": eps64,
+                            "leaf_size": leaf64, "p2p_c": c64_, "rms_rel_err": float(np.sqrt(np.mean(e64 ** 2))),
+                            "p999_rel_err": float(np.percentile(e64, 99.9)),
+                            "params_source": "autotuner with precision = FP64 at rms 1e-7 on this workload",
+                            "timing": "CUDA events, median of 10 after 3 warm-ups, L2 flushed",
+                            "at_mixed_params_ms": ms64m, "mixed_over_fp64": value / (a.n / (ms64 * 1e-3))}
+        # (ii) mixed mode with FP64 expansions (m2l_split = 0: FP32 only in P2P and the estimate),
+        # at the FP64 parameters and at the default ones
+        lit = g.Context(p=p64, eps=eps64, leaf_size=leaf64, p2p_c=c64_, precision=prec, m2l_split=0,
+                        device=local)
+        ms_l = event_ms(lambda: lit.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc), stream, 3, 5, flush)
+        e_l = errors(acc)
+        lit.set_params(p=a.p, eps=a.eps, leaf_size=a.leaf, p2p_c=a.c)
+        ms_l2 = event_ms(lambda: lit.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc), stream, 1, 3, flush)
+        e_l2 = errors(acc)
+        lit.close()
+        base["mixed_fp64_expansions"] = {
+            "what": "P2P and the scale estimate in FP32, P2M/M2M/M2L/L2L/L2P all in FP64 (m2l_split = 0)",
+            "value": a.n / (ms_l * 1e-3), "ms": ms_l, "p": p64, "eps": eps64, "leaf_size": leaf64,
+            "p2p_c": c64_, "rms_rel_err": float(np.sqrt(np.mean(e_l ** 2))),
+            "at_default_params": {"value": a.n / (ms_l2 * 1e-3), "ms": ms_l2,
+                                  "rms_rel_err": float(np.sqrt(np.mean(e_l2 ** 2)))}}
+        # (iii) GPU FP64 direct summation: 32768 sampled sinks (enough blocks for every SM), all
+        # sources, no f, scaled to N sinks
+        nd = min(a.n, 32768)
+        dsinks = sinks[torch.randperm(ns, generator=torch.Generator().manual_seed(1))[:nd].to(dev)]
+        ms_d = event_ms(lambda: ctx.fmm_direct(xt, mt, 1.0, sinks=dsinks), stream, 1, 3)
+        pairs = float(nd) * a.n
+        base["fp64_direct"] = {"value": nd / (ms_d * 1e-3), "sinks_timed": nd, "ms_sinks_timed": ms_d,
+                               "ms_scaled_to_n": ms_d * a.n / nd, "pairs_per_s": pairs / (ms_d * 1e-3),
+                               "fp64_tflops_at_20_per_pair": 20 * pairs / (ms_d * 1e-3) / 1e12,
+                               "timing": "CUDA events, median of 3 after 1 warm-up"}
+        base["mixed_over_direct"] = value / base["fp64_direct"]["value"]
+        if a.workload == "plummer" and a.n == 1_000_000:
+            base["crossover"] = crossover(g, dev, local, prec, flush)
+        extras["baselines"] = base
+        extras["fp64_fmm_value"] = base["fp64_fmm"]["value"]
+        extras["fp64_direct_value"] = base["fp64_direct"]["value"]
+        # the swap stage of the rotated M2L (App. A.5.1) on the tensor cores against the FMA
+        # immediates the M2L kernel uses (a dense small-matrix contraction of the M2L)
+        extras["m2l_swap_probe"] = g.fmm_swap_probe(1 << 20, 16)
         # the same step with the tidal tensor (Sec. 7.4) as an extra output
         Tt = torch.empty((a.n, 6), dtype=torch.float64, device=dev)
-        ctx.fmm_evaluate_active(xt, mt, psi=psi, acc=acc, tidal=Tt)
-        torch.cuda.synchronize(dev)
-        flush.zero_()
-        e0.record(stream)
-        ctx.fmm_evaluate_active(xt, mt, psi=psi, acc=acc, tidal=Tt)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        extras["with_tidal_ms"] = e0.elapsed_time(e1)
+        extras["with_tidal_ms"] = event_ms(lambda: ctx.fmm_evaluate_active(xt, mt, psi=psi, acc=acc, tidal=Tt),
+                                           stream, 1, 3, flush)
         del Tt
+        ctx.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc)
+    if not a.no_configs and world == 1 and a.workload == "plummer":
+        # the other workloads as compact sub-records (each with its own parameters)
+        cfgs = {}
+        for name, fn in (("cusp", lambda: cusp_record(a, g, dev, local, rank, prec, 5, 3)),
+                         ("ensemble", lambda: ensemble_record(a, g, dev, local, rank, world, prec, 10, 3, False)),
+                         ("serve", lambda: serve_record(a, g, dev, local, rank, world, prec, 192, 3, 3)[0])):
+            try:
+                cfgs[name] = fn()
+            except Exception as ex:  # a failing sub-record must not hide the headline
+                cfgs[name] = {"error": f"{type(ex).__name__}: {ex}"}
+            torch.cuda.empty_cache()
+        extras["configs"] = cfgs
+        if "latency_ms" in cfgs.get("serve", {}):
+            extras["p50_latency_ms"] = cfgs["serve"]["latency_ms"]["p50"]
+            extras["p99_latency_ms"] = cfgs["serve"]["latency_ms"]["p99"]
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside)
     xh = torch.from_numpy(x).pin_memory().numpy()
@@ -716,6 +898,7 @@ def main():
         if tuned:
             cfg["autotune"] = tuned
         cfg.update({"rms_rel_err": rms, "p999_rel_err": p999, "err_sinks": int(ns),
+                    "err_truth": "GPU FP64 direct sum over all sources for a seeded sample of sinks",
                     "phase_ms": {k: float(np.mean([s[k] for s in phase])) for k in
                                  ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total")},
                     "n_m2l": int(full["n_m2l"]), "n_p2p": int(full["n_p2p"]),

@@ -78,10 +78,13 @@ typedef struct {
     double p2p_c;       /* a pair (A,B) is summed directly when N_A N_B < p2p_c p^3     */
     int    precision;   /* FMM_PREC_*                                                  */
     int    scale_src;   /* FMM_SCALE_*                                                 */
-    int    p2p_two_float; /* mixed P2P: 1 = dx = (h_a - h_b) + (l_a - l_b) from two-float
-                             positions (hi + lo) per pair; 2 = every source is turned once per
-                             tile into an FP32 offset from the sink leaf's centre,
-                             (h - c_h) + (l - c_l), and dx is one FP32 difference of offsets;
+    int    p2p_two_float; /* mixed P2P, how dx = x_a - x_b is formed in FP32:
+                             1 = per source cell A of sink leaf B: if A may hold a source
+                             closer than rho_B to a sink (|s_A - s_B| < rho_A + 2 rho_B),
+                             dx = (h_a - h_b) + (l_a - l_b) from the two-float positions
+                             (hi + lo); otherwise from FP32 offsets to B's centre c,
+                             (h - c_h) + (l - c_l), formed once per staged tile (default);
+                             2 = offsets for every source; 3 = two-float for every source;
                              0 = from the FP32 high parts only                           */
     int    m2l_split;   /* mixed mode M2L: 1 = terms of order n+k <= 2 in FP64 and the others
                            in FP32 on scaled harmonics; 0 = every term in FP64        */
@@ -282,6 +285,16 @@ int fmm_swap_matrix(int n, double* B);
  * two short register-only loops on the current device (HOST outs; about 50 ms).
  * These are the roofline denominators of the ALU-bound kernels. */
 int fmm_alu_peaks(double* fp64_tflops, double* fp32_tflops);
+
+/* Measurement behind a design choice of the rotation-accelerated M2L (App. A.5; no
+ * counterpart in the paper's method): the swap stage (the matrices of App. A.5.1 applied to
+ * one vector per interaction pair, orders 0..14) timed on the current device for npairs
+ * random vectors, `reps` applications each (reps even, > 0), once as the FMA-immediate code
+ * the M2L kernel uses and once on the tensor cores (TF32 mma.sync, three products per entry
+ * for FP32 accuracy).  ms[0], ms[1] (HOST out): best kernel times of the two; *maxdiff
+ * (HOST out): the largest difference of their results after one more application.  Allocates
+ * and frees its own device buffers; FMM_E_INVALID for bad arguments. */
+int fmm_swap_probe(int npairs, int reps, double* ms, double* maxdiff);
 
 /* fmm_evaluate for small systems without allocating any device memory.
  * (The paper has no counterpart: this is a service of the library.)  Some callers

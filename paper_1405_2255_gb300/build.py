@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "--expt-relaxed-constexpr"]
 # decision quantities (keys, centres, radii) are computed without FMA contraction
 PER_FILE = {"tree.cu": ["--fmad=false"]}
-SOURCES = ["common.cu", "tree.cu", "upward.cu", "walk.cu", "interact.cu", "direct.cu", "split.cu", "peaks.cu", "capi.cu", "noalloc.cu", "serve.cu", "m2l_rot.cu", "tidal.cu",
+SOURCES = ["common.cu", "tree.cu", "upward.cu", "walk.cu", "interact.cu", "p2p.cu", "direct.cu", "split.cu", "peaks.cu", "swap_probe.cu", "capi.cu", "noalloc.cu", "serve.cu", "m2l_rot.cu", "tidal.cu",
            "m2l_rot_p3_10.cu", "m2l_rot_p11_13.cu", "m2l_rot_p14_15.cu", "m2l_rot_p16.cu"]
 
 

@@ -168,7 +168,7 @@ static int check_params(const fmm_params* p) {
     if (p->scale_src != FMM_SCALE_ESTIMATE && p->scale_src != FMM_SCALE_CALLER) return FMM_E_INVALID;
     if (p->m2l_rot != 0 && p->m2l_rot != 1) return FMM_E_INVALID;
     if (p->adaptive_p != 0 && p->adaptive_p != 1) return FMM_E_INVALID;
-    if (p->p2p_two_float < 0 || p->p2p_two_float > 2) return FMM_E_INVALID;
+    if (p->p2p_two_float < 0 || p->p2p_two_float > 3) return FMM_E_INVALID;
     return 0;
 }
 
@@ -402,14 +402,31 @@ static int run_walk(fmm_ctx* ctx, WalkParams wp, Buf& m2l, long long& m2l_cap, B
     return fail(ctx, FMM_E_OVERFLOW, msg);
 }
 
-static int sort_and_segment(fmm_ctx* ctx, Buf& list, long long npairs, Buf& seg_start, Buf& seg_end, cudaStream_t s,
-                            bool wide = false) {
-    TRY(ensure(ctx->sort_tmp, list_sort_tmp_bytes(npairs)));
+static int sort_and_segment(fmm_ctx* ctx, Buf& list, long long npairs, Buf& seg_start, Buf& seg_end,
+                            cudaStream_t s, bool wide = false) {
+    TRY(ensure(ctx->sort_tmp, list_sort_tmp_bytes(npairs, ctx->ncells)));
     TRY(ensure(seg_start, sizeof(int) * ctx->ncells));
     TRY(ensure(seg_end, sizeof(int) * ctx->ncells));
     sort_pairs_by_sink(P<int2>(list), npairs, ctx->ncells, ctx->sort_tmp.p, s, wide);
     launch_segments(P<int2>(list), npairs, ctx->ncells, P<int>(seg_start), P<int>(seg_end), s);
     return 0;
+}
+
+// mixed P2P over the segments in seg_start/seg_end of list: the work plan grows its scratch
+// once if the plan needs more than the context holds
+static int run_p2p_mixed(fmm_ctx* ctx, const int2* list, int mode, cudaStream_t s) {
+    Cells c = cells_of(ctx);
+    TRY(ensure(ctx->p2p_tmp, p2p_plan_fixed_bytes(ctx->nleaves)));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const size_t need = launch_p2p_mixed(P<float>(ctx->xhi), P<float>(ctx->xlo), ctx->n, c, list,
+                                             P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves),
+                                             ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), mode,
+                                             ctx->p2p_tmp.p, ctx->p2p_tmp.bytes, ctx->h_counters + 6, s);
+        if (need == ~(size_t)0) return fail(ctx, FMM_E_OVERFLOW, "P2P plan beyond 2^31 source ranges or n >= 2^29");
+        if (need <= ctx->p2p_tmp.bytes) return 0;
+        TRY(ensure(ctx->p2p_tmp, need));
+    }
+    return fail(ctx, FMM_E_CUDA, "P2P plan did not fit after growing its scratch");
 }
 
 // ------------------------------------------------------------------ the low-order scale (A7)
@@ -433,7 +450,7 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     // P2P segments of the estimate reuse seg_start/seg_end of the main lists (written later)
     TRY(ensure(ctx->seg_start, sizeof(int) * nc));
     TRY(ensure(ctx->seg_end, sizeof(int) * nc));
-    TRY(ensure(ctx->sort_tmp, list_sort_tmp_bytes(ctx->n_est_p2p)));
+    TRY(ensure(ctx->sort_tmp, list_sort_tmp_bytes(ctx->n_est_p2p, nc)));
     sort_pairs_by_sink(P<int2>(ctx->est_p2p), ctx->n_est_p2p, nc, ctx->sort_tmp.p, s);
     launch_segments(P<int2>(ctx->est_p2p), ctx->n_est_p2p, nc, P<int>(ctx->seg_start), P<int>(ctx->seg_end), s);
     double* scale = P<double>(ctx->scale_sorted);
@@ -453,12 +470,8 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     launch_est_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), nc, c,
                    P<double>(ctx->F1), s, mixed ? P<float4>(ctx->walkf) : nullptr);
     // (the p = 1 L2L is folded into launch_est_scale)
-    if (mixed) {
-        TRY(ensure(ctx->p2p_tmp, p2p_tmp_bytes(ctx->nleaves)));
-        launch_p2p_mixed(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), ctx->n, c, P<int2>(ctx->est_p2p),
-                         P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
-                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), 0, ctx->p2p_tmp.p, s);
-    }
+    if (mixed)
+        TRY(run_p2p_mixed(ctx, P<int2>(ctx->est_p2p), 0, s));
     else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->est_p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
                         P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
@@ -643,13 +656,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     // A10: P2P
     TRY(sort_and_segment(ctx, ctx->p2p, ctx->n_p2p, ctx->seg_start, ctx->seg_end, s));
     if (prm.precision == FMM_PREC_MIXED)
-    {
-        TRY(ensure(ctx->p2p_tmp, p2p_tmp_bytes(ctx->nleaves)));
-        launch_p2p_mixed(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), ctx->n, c, P<int2>(ctx->p2p),
-                         P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves), ctx->nleaves,
-                         P<double>(ctx->psi_near), P<double>(ctx->acc_near), prm.p2p_two_float,
-                         ctx->p2p_tmp.p, s);
-    }
+        TRY(run_p2p_mixed(ctx, P<int2>(ctx->p2p), prm.p2p_two_float, s));
     else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
                         P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
@@ -974,6 +981,10 @@ int fmm_last_stats(fmm_ctx* ctx, fmm_stats* out) {
 int fmm_alu_peaks(double* fp64_tflops, double* fp32_tflops) {
     if (!fp64_tflops || !fp32_tflops) return FMM_E_INVALID;
     return alu_peaks(fp64_tflops, fp32_tflops);
+}
+
+int fmm_swap_probe(int npairs, int reps, double* ms, double* maxdiff) {
+    return swap_probe(npairs, reps, ms, maxdiff);
 }
 
 uint64_t fmm_workspace_bytes(fmm_ctx* ctx) {

@@ -174,6 +174,15 @@ __device__ inline void ff_acc(ff& a, float v) {
     a.lo = __fsub_rn(lo, __fsub_rn(a.hi, s.hi));
 }
 
+// 1/sqrt(x) by the hardware approximation with subnormal inputs flushed to zero (an x below
+// 2^-126 would be a pair closer than 1e-19 in the working units); the non-flushing form spends
+// extra instructions per call on rescaling such inputs
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // 2^k as a double for |k| <= 1022, from its bits (exact)
 __device__ inline double pow2i(int k) {
     k = k < -1022 ? -1022 : (k > 1023 ? 1023 : k);

@@ -565,14 +565,18 @@ __global__ void k_item_counts(const int* __restrict__ order, const int* __restri
 // F_B = sum of its chunks' partial expansions, in chunk order
 // item_q (nullable): the order of item w's partial expansion (its coefficients of higher
 // order are not written and count as zero)
+// single: sinks of one item were written to F by the M2L kernel itself (and sinks without an
+// item hold the zeros F starts with), so only sinks of two or more items are summed here
 __global__ void k_m2l_reduce(const int* __restrict__ order, const int* __restrict__ item_start,
                              const int* __restrict__ cnt, const unsigned* __restrict__ work, int ncells, int nco,
-                             const double* __restrict__ part, double* __restrict__ F, const int* __restrict__ item_q) {
+                             const double* __restrict__ part, double* __restrict__ F, const int* __restrict__ item_q,
+                             bool single) {
     const unsigned nsinks = work[1];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)ncells * nco;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t / nco), j = (int)(t % nco);
         if ((unsigned)i >= nsinks) continue;
+        if (single && cnt[i] <= 1) continue;
         const int a = item_start[i], b = a + cnt[i];
         const int nj = (int)sqrtf((float)j);
         double v = 0.0;
@@ -607,6 +611,7 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     const long long items_cap = npairs / kChunk + ncells + 1;
     void* gtmp = (void*)(((uintptr_t)(part + (size_t)items_cap * ncoef(p)) + 255) & ~(uintptr_t)255);
     const int* item_q = nullptr;
+    bool single = false;
     cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
     k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
     // the low 32 bits are the sink's index, already in order: the stable passes over the
@@ -617,13 +622,14 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     scan_exclusive_i32(cnt, item_start, ncells, (int*)(work + 2), stmp, s);
     if (rot && m2l_rot_supported(p)) {
         item_q = launch_m2l_rot(list, seg_start, seg_end, order, item_start, work, cen, M, ncells, p, (float*)Mf, M64,
-                                part, adaptive, gtmp, items_cap, s);
+                                part, F, adaptive, gtmp, items_cap, s);
+        single = true;
     } else {
         k_prep_split<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mf, M64); note_launch();
         m2l_rounds_launch<kRoundsBatch>(list, seg_start, seg_end, order, item_start, work, cen, Mf, M64, p, part, s);
     }
     k_m2l_reduce<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(order, item_start, cnt, work, ncells,
-                                                                            ncoef(p), part, F, item_q);
+                                                                            ncoef(p), part, F, item_q, single);
     note_launch();
 }
 
@@ -841,328 +847,6 @@ void launch_split_positions(const d4* xm, int n, float* hi, float* lo, cudaStrea
     if (n > 0) k_split_positions<<<grid_for(n, 256), 256, 0, s>>>(xm, n, hi, lo); note_launch();
 }
 
-// The mixed kernel streams the sink's sources through warp-private tiles filled from
-// consecutive source cells (so small cells do not leave a tile half empty).  dx =
-// (hi_a - hi_b) + (lo_a - lo_b) carries one FP32 rounding relative to |dx| itself, so
-// no per-leaf change of origin is needed: a tile is filled by plain 4-byte copies
-// (cp.async) of the structure-of-arrays positions, double buffered so that the next
-// tile's loads overlap the current tile's pairs.  The pair terms run two sources at a
-// time in packed FP32 (f32x2) arithmetic, four sources per shared-memory load.  A chunk
-// of s <= 32 sinks is replicated R = 1, 2 or 4 times across the warp (lane = r * (32/R)
-// + sink), replica r taking every R-th group of four sources; the replicas' sums are
-// added at the end.  Tiles that hold a source cell containing the sink leaf skip the
-// r = 0 pairs (the sink itself and coincident particles); all other tiles need no
-// test, since particles of different leaves are never coincident.  A partial tile is
-// padded to a whole group with massless sources far away.  TWO_FLOAT = false uses the
-// high parts alone (the low-order scale estimate).
-typedef unsigned long long f2;  // two packed floats
-__device__ __forceinline__ f2 f2_pack(float a, float b) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(f2 v, float& a, float& b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
-    f2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
-// the sink of a lane, its coordinates duplicated in both halves
-struct SinkPk {
-    f2 hx, hy, hz, lx, ly, lz;
-};
-struct AccPk {
-    f2 ps, ax, ay, az;
-};
-
-// 1/sqrt(r2) by the hardware approximation with subnormal inputs flushed to zero (an
-// r2 below 2^-126 would be a pair closer than 1e-19 in the positions' units); the
-// non-flushing form spends extra instructions per pair on rescaling such inputs
-__device__ __forceinline__ float rsqrt_ftz(float x) {
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// two sources (x, y, z, w high parts; x, y, z low parts as packed pairs) against the sink
-template <bool TWO_FLOAT, bool GUARD>
-__device__ __forceinline__ void p2p_pair2(f2 X, f2 Y, f2 Z, f2 W, f2 XL, f2 YL, f2 ZL, const SinkPk& b, AccPk& a) {
-    f2 dx = f2_sub(X, b.hx), dy = f2_sub(Y, b.hy), dz = f2_sub(Z, b.hz);
-    if (TWO_FLOAT) {
-        dx = f2_add(dx, f2_sub(XL, b.lx));
-        dy = f2_add(dy, f2_sub(YL, b.ly));
-        dz = f2_add(dz, f2_sub(ZL, b.lz));
-    }
-    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
-    float r2a, r2b;
-    f2_unpack(r2, r2a, r2b);
-    float ia = rsqrt_ftz(r2a), ib = rsqrt_ftz(r2b);
-    if (GUARD) {
-        ia = r2a > 0.f ? ia : 0.f;
-        ib = r2b > 0.f ? ib : 0.f;
-    }
-    const f2 rinv = f2_pack(ia, ib);
-    const f2 qm = f2_mul(W, rinv);
-    const f2 q3 = f2_mul(qm, f2_mul(rinv, rinv));
-    a.ps = f2_add(a.ps, qm);
-    a.ax = f2_fma(q3, dx, a.ax);
-    a.ay = f2_fma(q3, dy, a.ay);
-    a.az = f2_fma(q3, dz, a.az);
-}
-
-// one group of four sources of the tile (index g) against the sink
-template <bool TWO_FLOAT, bool GUARD>
-__device__ __forceinline__ void p2p_group(const float* __restrict__ T, int g, const SinkPk& b, AccPk& a) {
-    const float4 X = ((const float4*)(T + 0 * kP2PTile))[g], Y = ((const float4*)(T + 1 * kP2PTile))[g],
-                 Z = ((const float4*)(T + 2 * kP2PTile))[g], W = ((const float4*)(T + 3 * kP2PTile))[g];
-    float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), YL = XL, ZL = XL;
-    if (TWO_FLOAT) {
-        XL = ((const float4*)(T + 4 * kP2PTile))[g];
-        YL = ((const float4*)(T + 5 * kP2PTile))[g];
-        ZL = ((const float4*)(T + 6 * kP2PTile))[g];
-    }
-    p2p_pair2<TWO_FLOAT, GUARD>(f2_pack(X.x, X.y), f2_pack(Y.x, Y.y), f2_pack(Z.x, Z.y), f2_pack(W.x, W.y),
-                                f2_pack(XL.x, XL.y), f2_pack(YL.x, YL.y), f2_pack(ZL.x, ZL.y), b, a);
-    p2p_pair2<TWO_FLOAT, GUARD>(f2_pack(X.z, X.w), f2_pack(Y.z, Y.w), f2_pack(Z.z, Z.w), f2_pack(W.z, W.w),
-                                f2_pack(XL.z, XL.w), f2_pack(YL.z, YL.w), f2_pack(ZL.z, ZL.w), b, a);
-}
-
-// replica r0 of R takes groups r0, r0 + R, ... of a tile of ng groups; a full tile
-// (8 groups per replica) has a trip count known at compile time
-template <bool TWO_FLOAT, bool GUARD, int R>
-__device__ __forceinline__ void p2p_tile(const float* __restrict__ T, int ng, int r0, const SinkPk& b, AccPk& a) {
-    if (ng == 8 * R) {
-#pragma unroll 2
-        for (int k = 0; k < 8; ++k) p2p_group<TWO_FLOAT, GUARD>(T, r0 + R * k, b, a);
-    } else {
-#pragma unroll 1
-        for (int g = r0; g < ng; g += R) p2p_group<TWO_FLOAT, GUARD>(T, g, b, a);
-    }
-}
-template <bool TWO_FLOAT, bool GUARD>
-__device__ __forceinline__ void p2p_tile_r(const float* __restrict__ T, int ng, int r0, int R, const SinkPk& b,
-                                           AccPk& a) {
-    if (R == 1) p2p_tile<TWO_FLOAT, GUARD, 1>(T, ng, r0, b, a);
-    else if (R == 2) p2p_tile<TWO_FLOAT, GUARD, 2>(T, ng, r0, b, a);
-    else if (R == 3) p2p_tile<TWO_FLOAT, GUARD, 3>(T, ng, r0, b, a);
-    else p2p_tile<TWO_FLOAT, GUARD, 4>(T, ng, r0, b, a);
-}
-
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// The sources of one sink leaf: the entries of its own P2P segment, then those of
-// each ancestor's segment; fill() copies the next <= T source particles into a tile
-// (structure of arrays: X, Y, Z, W[, XL, YL, ZL] at stride kP2PTile).
-struct SrcCursor {
-    int cell, e, e1, af, an, off;
-    bool contains;
-    __device__ void start(const int* seg_start, const int* seg_end, int leaf) {
-        cell = leaf;
-        e = seg_start[leaf];
-        e1 = seg_end[leaf];
-        af = an = off = 0;
-        contains = false;
-    }
-    template <bool TWO_FLOAT>
-    __device__ int fill(const Cells& c, const int2* __restrict__ list, const int* __restrict__ seg_start,
-                        const int* __restrict__ seg_end, const float* __restrict__ hi,
-                        const float* __restrict__ lo, size_t n, int first, int lane, int T, float* tile,
-                        bool& guard) {
-        int m = 0;
-        guard = false;
-        if (cell < 0) return 0;  // exhausted
-        while (m < T) {
-            if (off == an) {  // next source cell
-                while (e == e1) {
-                    cell = c.parent[cell];
-                    if (cell < 0) return m;
-                    e = seg_start[cell];
-                    e1 = seg_end[cell];
-                }
-                const int A = list[e++].x;
-                af = c.first[A];
-                an = c.count[A];
-                off = 0;
-                contains = af <= first && first < af + an;
-                continue;
-            }
-            const int k = min(T - m, an - off);
-            for (int q = lane; q < k; q += 32) {
-                const size_t j = (size_t)af + off + q;
-                float* t = tile + m + q;
-#pragma unroll
-                for (int d = 0; d < 4; ++d) cp_async4(t + d * kP2PTile, hi + d * n + j);
-                if (TWO_FLOAT)
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) cp_async4(t + (4 + d) * kP2PTile, lo + d * n + j);
-            }
-            guard |= contains;
-            m += k;
-            off += k;
-        }
-        return m;
-    }
-};
-
-// One warp per sink leaf, leaves taken in decreasing order of work from an atomic
-// counter; sources come from the P2P segments of the leaf and of its ancestors.
-// MODE 0: dx from the FP32 high parts; 1: from the two-float positions, (h_a - h_b) +
-// (l_a - l_b) per pair; 2: leaf-relative: every tile's sources are turned once into FP32
-// offsets from the sink leaf's centre c (two-float differences (h - c_h) + (l - c_l)),
-// so that a pair's dx is one FP32 difference of offsets
-template <int MODE>
-__global__ void __launch_bounds__(kP2PWarps * 32, 5) k_p2p_mixed(const float* __restrict__ hi,
-                                                                 const float* __restrict__ lo, int n, Cells c,
-                                                                 const int2* __restrict__ list,
-                                                                 const int* __restrict__ seg_start,
-                                                                 const int* __restrict__ seg_end,
-                                                                 const int* __restrict__ order, int nleaves,
-                                                                 unsigned* __restrict__ counter,
-                                                                 double* __restrict__ psi, double* __restrict__ acc) {
-    constexpr bool TWO_FLOAT = MODE == 1;  // two-float dx in the pair loop
-    constexpr bool LOADLO = MODE >= 1;     // the tiles carry the low parts
-    constexpr int NA = LOADLO ? 7 : 4;     // arrays per tile
-    __shared__ __align__(16) float tiles[kP2PWarps][2][NA * kP2PTile];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t nn = (size_t)n;
-    for (;;) {
-        unsigned w = 0;
-        if (lane == 0) w = atomicAdd(counter, 1u);
-        w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= (unsigned)nleaves) break;
-        const int leaf = order[w];
-        if (!cell_active(c, leaf)) continue;
-        const int first = c.first[leaf], count = c.count[leaf];
-        // chunks of up to 32 sinks, one pass over the sources each (every pass walks the
-        // source cells again); a chunk of S sinks takes R = 32 / S replicas (up to 4), which
-        // take the groups of a tile in turn
-        for (int s0 = 0; s0 < count; s0 += 32) {
-            const int chunk = min(32, count - s0);
-            const int R = chunk <= 8 ? 4 : (chunk <= 10 ? 3 : (chunk <= 16 ? 2 : 1));
-            const int S = R == 3 ? 10 : 32 / R;
-            // lanes past S * R repeat replica 0's work; their sums are not used
-            const int sink = lane % S, rep = lane / S < R ? lane / S : 0;
-            const bool active = sink < chunk && lane < S * R;
-            const int i = first + s0 + sink;
-            float bhx = 0, bhy = 0, bhz = 0, blx = 0, bly = 0, blz = 0;
-            if (active) {
-                bhx = hi[i];
-                bhy = hi[nn + i];
-                bhz = hi[2 * nn + i];
-                if (LOADLO) {
-                    blx = lo[i];
-                    bly = lo[nn + i];
-                    blz = lo[2 * nn + i];
-                }
-            }
-            // MODE 2: the leaf centre as two floats, the sink as its offset from it
-            float chx = 0, chy = 0, chz = 0, clx = 0, cly = 0, clz = 0;
-            if (MODE == 2) {
-                const d4 sc = c.sr[leaf];
-                chx = (float)sc.x; chy = (float)sc.y; chz = (float)sc.z;
-                clx = (float)(sc.x - (double)chx); cly = (float)(sc.y - (double)chy); clz = (float)(sc.z - (double)chz);
-                bhx = __fadd_rn(__fsub_rn(bhx, chx), __fsub_rn(blx, clx));
-                bhy = __fadd_rn(__fsub_rn(bhy, chy), __fsub_rn(bly, cly));
-                bhz = __fadd_rn(__fsub_rn(bhz, chz), __fsub_rn(blz, clz));
-                blx = bly = blz = 0.f;
-            }
-            const SinkPk b{f2_pack(bhx, bhx), f2_pack(bhy, bhy), f2_pack(bhz, bhz),
-                           f2_pack(blx, blx), f2_pack(bly, bly), f2_pack(blz, blz)};
-            const f2 zero = f2_pack(0.f, 0.f);
-            AccPk a{zero, zero, zero, zero};
-            ff aps = {0, 0}, aax = {0, 0}, aay = {0, 0}, aaz = {0, 0};
-            SrcCursor cur;
-            cur.start(seg_start, seg_end, leaf);
-            const int T = 32 * R;  // sources per tile: eight groups of four for every replica
-            int bb = 0;
-            bool guard = false, guard_next = false;
-            int nt = cur.fill<LOADLO>(c, list, seg_start, seg_end, hi, lo, nn, first, lane, T, tiles[wid][0],
-                                      guard);
-            cp_async_commit();
-            while (nt > 0) {
-                // issue the next tile, then wait for the current one
-                const int nx = cur.fill<LOADLO>(c, list, seg_start, seg_end, hi, lo, nn, first, lane, T,
-                                                tiles[wid][bb ^ 1], guard_next);
-                cp_async_commit();
-                cp_async_wait1();
-                float* tile = tiles[wid][bb];
-                const int ng = (nt + 3) >> 2;
-                if (MODE == 2) {  // offsets from the leaf centre, in place of the high parts
-                    __syncwarp();
-                    for (int j = lane; j < nt; j += 32) {
-                        tile[j] = __fadd_rn(__fsub_rn(tile[j], chx), __fsub_rn(tile[4 * kP2PTile + j], clx));
-                        tile[kP2PTile + j] =
-                            __fadd_rn(__fsub_rn(tile[kP2PTile + j], chy), __fsub_rn(tile[5 * kP2PTile + j], cly));
-                        tile[2 * kP2PTile + j] =
-                            __fadd_rn(__fsub_rn(tile[2 * kP2PTile + j], chz), __fsub_rn(tile[6 * kP2PTile + j], clz));
-                    }
-                }
-                if (lane < 4 * ng - nt) {  // pad to whole groups: massless, far away
-                    float* t = tile + nt + lane;
-                    t[0] = 1e15f;
-                    t[kP2PTile] = 1e15f;
-                    t[2 * kP2PTile] = 1e15f;
-                    t[3 * kP2PTile] = 0.f;
-                    if (LOADLO) t[4 * kP2PTile] = t[5 * kP2PTile] = t[6 * kP2PTile] = 0.f;
-                }
-                __syncwarp();
-                if (guard) p2p_tile_r<TWO_FLOAT, true>(tile, ng, rep, R, b, a);
-                else p2p_tile_r<TWO_FLOAT, false>(tile, ng, rep, R, b, a);
-                // fold the FP32 partials (<= 32 pairs per lane) into the two-float sums
-                float u0, u1;
-                f2_unpack(a.ps, u0, u1); ff_acc(aps, u0 + u1);
-                f2_unpack(a.ax, u0, u1); ff_acc(aax, u0 + u1);
-                f2_unpack(a.ay, u0, u1); ff_acc(aay, u0 + u1);
-                f2_unpack(a.az, u0, u1); ff_acc(aaz, u0 + u1);
-                a = AccPk{zero, zero, zero, zero};
-                __syncwarp();  // every lane is done with the tile before it is refilled
-                bb ^= 1;
-                nt = nx;
-                guard = guard_next;
-            }
-            // add the replicas' partial sums (lanes sink + S, sink + 2 S, ... into lane sink);
-            // only lanes below S accumulate, so every lane read still holds its own sum
-            for (int j = 1; j < R; ++j) {
-                const int src = min(lane + j * S, 31);
-                ff tps = aps, tax = aax, tay = aay, taz = aaz;
-                ff_add_lane(tps, src); ff_add_lane(tax, src); ff_add_lane(tay, src); ff_add_lane(taz, src);
-                if (lane < S) {
-                    aps = tps; aax = tax; aay = tay; aaz = taz;
-                }
-            }
-            if (active && lane < S) {
-                psi[i] = (double)aps.hi + (double)aps.lo;
-                acc[3 * (size_t)i] = (double)aax.hi + (double)aax.lo;
-                acc[3 * (size_t)i + 1] = (double)aay.hi + (double)aay.lo;
-                acc[3 * (size_t)i + 2] = (double)aaz.hi + (double)aaz.lo;
-            }
-        }
-    }
-}
-
 // number of ordered pairs (a != b) at distance 0: equal positions have equal keys,
 // so they sit next to each other in key order inside one leaf
 __global__ void k_coincident(const d4* __restrict__ xm, const uint64_t* __restrict__ keys, int n,
@@ -1195,65 +879,6 @@ void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long 
         k_coincident<<<grid_for(n, 256), 256, 0, s>>>(xm, keys, n, coincident, off, nsys);
         note_launch();
     }
-}
-
-// P2P work of a leaf: its sink chunks times the sources of its own and its ancestors'
-// segments; leaves are processed in decreasing order of it, taken from an atomic counter
-__global__ void k_p2p_work(Cells c, const int2* __restrict__ list, const int* __restrict__ seg_start,
-                           const int* __restrict__ seg_end, const int* __restrict__ leaves, int nleaves,
-                           uint64_t* __restrict__ keys, int* __restrict__ vals) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nleaves; t += gridDim.x * blockDim.x) {
-        const int leaf = leaves[t];
-        unsigned long long src = 0;
-        for (int cell = leaf; cell >= 0; cell = c.parent[cell])
-            for (int e = seg_start[cell]; e < seg_end[cell]; ++e) src += c.count[list[e].x];
-        unsigned long long work = src * (unsigned long long)((c.count[leaf] + 31) / 32);
-        const unsigned w32 = work > 0xffffffffull ? 0xffffffffu : (unsigned)work;
-        keys[t] = ((uint64_t)(0xffffffffu - w32) << 32) | (unsigned)t;
-        vals[t] = 0;
-    }
-}
-__global__ void k_p2p_order(const uint64_t* __restrict__ keys, const int* __restrict__ leaves, int nleaves,
-                            int* __restrict__ order) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nleaves; t += gridDim.x * blockDim.x)
-        order[t] = leaves[(int)(keys[t] & 0xffffffffu)];
-}
-
-size_t p2p_tmp_bytes(int nleaves) {
-    size_t n = (size_t)(nleaves > 0 ? nleaves : 1);
-    return n * (2 * sizeof(uint64_t) + 3 * sizeof(int)) + radix_tmp_ints(n) * sizeof(int) + 512;
-}
-
-void launch_p2p_mixed(const d4* /*xm*/, const float* hi, const float* lo, int n, Cells c, const int2* list,
-                      const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* psi,
-                      double* acc, int mode, void* tmp, cudaStream_t s) {
-    if (nleaves <= 0) return;
-    uint64_t* k0 = (uint64_t*)tmp;
-    uint64_t* k1 = k0 + nleaves;
-    int* v0 = (int*)(k1 + nleaves);
-    int* v1 = v0 + nleaves;
-    int* order = v1 + nleaves;
-    unsigned* counter = (unsigned*)(order + nleaves);
-    int* rtmp = (int*)(counter + 4);
-    cudaMemsetAsync(counter, 0, 4 * sizeof(unsigned), s);
-    k_p2p_work<<<grid_for(nleaves, 128), 128, 0, s>>>(c, list, seg_start, seg_end, leaves, nleaves, k0, v0);
-    note_launch();
-    // the low 32 bits are the position in leaves[], already in order: sort the work bits only
-    const int flip = radix_sort_pairs_bits(k0, v0, k1, v1, nleaves, rtmp, 32, 64, s);
-    k_p2p_order<<<grid_for(nleaves, 256), 256, 0, s>>>(flip ? k1 : k0, leaves, nleaves, order);
-    note_launch();
-    int dev = 0, nsm = 152, bps = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    auto go = [&](auto kern) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kP2PWarps * 32, 0);
-        kern<<<nsm * (bps > 0 ? bps : 1), kP2PWarps * 32, 0, s>>>(hi, lo, n, c, list, seg_start, seg_end, order,
-                                                                   nleaves, counter, psi, acc);
-    };
-    if (mode == 2) go(k_p2p_mixed<2>);
-    else if (mode == 1) go(k_p2p_mixed<1>);
-    else go(k_p2p_mixed<0>);
-    note_launch();
 }
 
 // ---------------------------------------------------------------- low-order f estimate

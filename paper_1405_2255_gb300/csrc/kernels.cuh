@@ -160,9 +160,10 @@ void launch_walk_step(Cells c, WalkParams wp, const int2* front_in, long long nf
 // the largest frontier demand seen
 void launch_walk_step_dev(Cells c, WalkParams wp, const int2* front_in, const unsigned long long* nfront_dev,
                           int2* front_out, WalkBuffers wb, unsigned long long* out_cnt, cudaStream_t s);
-// sort a pair list by (sink, source), then mark per-sink segments [seg_start, seg_end)
-size_t list_sort_tmp_bytes(long long npairs);
-// wide: the first entries use all 32 bits (an adaptive-order M2L list)
+// sort a pair list by (sink, first entry) -- the first entry taken as unsigned, so an adaptive
+// walk's M2L entries (wide: order bits above the source index) sort by (sink, order, source) --
+// then mark per-sink segments [seg_start, seg_end); tmp: list_sort_tmp_bytes(npairs, ncells)
+size_t list_sort_tmp_bytes(long long npairs, int ncells);
 void sort_pairs_by_sink(int2* list, long long npairs, int ncells, void* tmp, cudaStream_t s, bool wide = false);
 void launch_segments(const int2* list, long long npairs, int ncells, int* seg_start, int* seg_end,
                      cudaStream_t s);
@@ -187,14 +188,15 @@ constexpr int kRotMaxP = 16;  // largest order with a rotation-accelerated M2L
 bool m2l_rot_supported(int p);
 // sinks in `order` (work[1] of them), items from item_start, work[0] the item counter and
 // work[2] the number of items; Mt (ncells x (p+1)^2 floats) and M64 (ncells x 9) are scratch;
-// part receives one expansion per item
+// part receives one expansion per item, except that a sink whose list is a single item has
+// its expansion written to F (zeroed beforehand) directly
 // adaptive: the items are grouped by the largest order of their pairs and each group runs
 // the kernel of that order (gtmp: m2l_rot_group_bytes(items_cap) bytes); returns the
 // per-item orders (device, nullptr without adaptive) for the reduction
 const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg_end, const int* order,
                           const int* item_start, unsigned* work, const d4* cen, const double* M, int ncells, int p,
-                          float* Mt, cd* M64, double* part, bool adaptive, void* gtmp, long long items_cap,
-                          cudaStream_t s);
+                          float* Mt, cd* M64, double* part, double* F, bool adaptive, void* gtmp,
+                          long long items_cap, cudaStream_t s);
 size_t m2l_rot_group_bytes(long long items_cap);
 void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F,
                       cudaStream_t s);
@@ -212,12 +214,17 @@ void launch_l2l_split(Cells c, const d4* cen, int lev_begin, int lev_end, int p,
 // its own P2P segment and those of its ancestors' segments.
 void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_start,
                      const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc, cudaStream_t s);
-// mode (fmm_params.p2p_two_float): 0 dx from the FP32 high parts, 1 from the two-float
-// positions, 2 from FP32 offsets to the sink leaf's centre formed in two-float per tile
-size_t p2p_tmp_bytes(int nleaves);
-void launch_p2p_mixed(const d4* xm, const float* hi, const float* lo, int n, Cells c, const int2* list,
-                      const int* seg_start, const int* seg_end, const int* leaves, int nleaves,
-                      double* psi, double* acc, int mode, void* tmp, cudaStream_t s);
+// Mixed P2P (p2p.cu).  mode (fmm_params.p2p_two_float): 0 dx from the FP32 high parts (the
+// low-order estimate), 1 two-float dx for near source cells and FP32 offsets from the sink
+// leaf's centre for the others, 2 offsets for all, 3 two-float for all.  tmp holds the work
+// plan: at least p2p_plan_fixed_bytes(nleaves); the call plans, reads the plan's size on the
+// host (h_tot: 2 host words; the stream is synchronised once) and runs the P2P if tmp_bytes
+// holds it.  Returns the bytes the call needs: a value above tmp_bytes means nothing was
+// computed (call again with that much), ~0 a plan beyond 2^31 ranges or items or n >= 2^29.
+size_t p2p_plan_fixed_bytes(int nleaves);
+size_t launch_p2p_mixed(const float* hi, const float* lo, int n, Cells c, const int2* list, const int* seg_start,
+                        const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc, int mode,
+                        void* tmp, size_t tmp_bytes, unsigned long long* h_tot, cudaStream_t s);
 // ordered pairs of distinct particles at distance 0 (sorted keys and positions); with
 // an ensemble (off != nullptr) only pairs inside one system count
 void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s,
@@ -268,6 +275,9 @@ void launch_active_flags(const unsigned char* active, const int* perm, int n, co
 
 // ---------------------------------------------------------------- peaks (peaks.cu)
 int alu_peaks(double* fp64_tflops, double* fp32_tflops);
+// the swap stage of the rotated M2L at p = 14 as FMA immediates and as 3xTF32 mma.sync
+// (swap_probe.cu); ms[0], ms[1] their kernel times, *maxdiff the largest difference
+int swap_probe(int npairs, int reps, double* ms, double* maxdiff);
 
 // ---------------------------------------------------------------- direct (direct.cu)
 void launch_direct(const double* x, const double* mu, int n, double G, const int64_t* sinks, int nsinks,

@@ -35,48 +35,20 @@ __global__ void k_prep_rot(const double* __restrict__ M, const d4* __restrict__ 
 
 }  // namespace
 
-extern template void rot_launch<3>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<4>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<5>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<6>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<7>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<8>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<9>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<10>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<11>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<12>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<13>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<14>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<15>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
-extern template void rot_launch<16>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                       const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                       unsigned*, int, int, cudaStream_t);
+extern template void rot_launch<3>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<4>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<5>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<6>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<7>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<8>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<9>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<10>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<11>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<12>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<13>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<14>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<15>(const RotArgs&, cudaStream_t);
+extern template void rot_launch<16>(const RotArgs&, cudaStream_t);
 
 bool m2l_rot_supported(int p) { return p >= 3 && p <= kRotMaxP; }
 
@@ -136,15 +108,16 @@ size_t m2l_rot_group_bytes(long long items_cap) {
 
 const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg_end, const int* order,
                           const int* item_start, unsigned* work, const d4* cen, const double* M, int ncells, int p,
-                          float* Mt, cd* M64, double* part, bool adaptive, void* gtmp, long long items_cap,
-                          cudaStream_t s) {
+                          float* Mt, cd* M64, double* part, double* F, bool adaptive, void* gtmp,
+                          long long items_cap, cudaStream_t s) {
     k_prep_rot<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mt, M64);
     note_launch();
     const int nco = ncoef(p);
 #define GB3_ROT(PP)                                                                                      \
     case PP:                                                                                             \
-        rot_launch<PP>(list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part, il, go, gq, ctr, \
-                       nco, adapt, s);                                                                   \
+        rot_launch<PP>(RotArgs{list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part, F, il,  \
+                               go, gq, ctr, nco, adapt},                                                \
+                       s);                                                                               \
         break;
     auto launch_p = [&](int q, const int* il, const unsigned* go, int gq, unsigned* ctr, int adapt) {
         switch (q) {

@@ -44,8 +44,29 @@
 #include "kernels.cuh"
 
 namespace gb3 {
-namespace {
 
+// arguments of one launch of the rotated M2L kernel (see k_m2l_rot)
+struct RotArgs {
+    const int2* list;
+    const int* seg_start;
+    const int* seg_end;
+    const int* order;
+    const int* item_start;
+    unsigned* work;
+    const d4* cen;
+    const float* Mt;
+    const cd* M64;
+    double* part;
+    double* F;
+    const int* ilist;
+    const unsigned* goff;
+    int gq;
+    unsigned* counter;
+    int nco_out;
+    int adapt;
+};
+
+namespace {
 
 // ---------------------------------------------------------------- constant tables
 constexpr double rfact(int n) {
@@ -318,15 +339,25 @@ constexpr int rot_warps() {
 // One warp per work item: up to kM2LChunk pairs of one sink, lane = pair.  The items are
 // ilist[goff[gq] .. goff[gq + 1]) (ilist == nullptr: 0 .. work[2]), taken from *counter;
 // item w's partial expansion goes to part + w * nco_out, nco_out = (p+1)^2 of the global order
-// p >= P, which is also the row length of Mt.  adapt: the pairs carry their own
-// orders q <= P (adaptive walk) and each lane keeps only the terms n + k <= q of its pair.
+// p >= P, which is also the row length of Mt; a sink whose whole list is one item has its
+// expansion written to F + B * nco_out directly (F starts at zero; the reduction skips it).
+// adapt: the pairs carry their own orders q <= P (adaptive walk) and each lane keeps only
+// the terms n + k <= q of its pair.
 template <int P>
-__global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
-    k_m2l_rot(const int2* __restrict__ list, const int* __restrict__ seg_start, const int* __restrict__ seg_end,
-              const int* __restrict__ order, const int* __restrict__ item_start, unsigned* __restrict__ work,
-              const d4* __restrict__ cen, const float* __restrict__ Mt, const cd* __restrict__ M64g,
-              double* __restrict__ part, const int* __restrict__ ilist, const unsigned* __restrict__ goff, int gq,
-              unsigned* __restrict__ counter, int nco_out, int adapt) {
+__global__ void __launch_bounds__(32 * rot_warps<P>(), 1) k_m2l_rot(const RotArgs args) {
+    const int2* __restrict__ list = args.list;
+    const int* __restrict__ seg_start = args.seg_start;
+    const int* __restrict__ seg_end = args.seg_end;
+    const int* __restrict__ order = args.order;
+    const int* __restrict__ item_start = args.item_start;
+    const unsigned* __restrict__ work = args.work;
+    const d4* __restrict__ cen = args.cen;
+    const float* __restrict__ Mt = args.Mt;
+    const cd* __restrict__ M64g = args.M64;
+    const int* __restrict__ ilist = args.ilist;
+    const unsigned* __restrict__ goff = args.goff;
+    const int gq = args.gq, nco_out = args.nco_out, adapt = args.adapt;
+    unsigned* __restrict__ counter = args.counter;
     constexpr int NCO = (P + 1) * (P + 1), W = rot_warps<P>();
     extern __shared__ __align__(16) unsigned char sm_raw[];
     __shared__ unsigned s_item;
@@ -347,7 +378,7 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
         if (w0 >= nlist) break;
         const bool has = w0 + warp < nlist;
         const unsigned w = has ? (ilist ? (unsigned)ilist[lbase + w0 + warp] : w0 + warp) : 0u;
-        int e0 = 0, e1 = 0, s0 = 0, s1 = 0;
+        int e0 = 0, e1 = 0, s0 = 0, s1 = 0, B = 0;
         d4 sB = mk4(0.0, 0.0, 0.0, 1.0);
         if (has) {
             int lo_i = 0, hi_i = (int)nsinks - 1;
@@ -356,7 +387,7 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
                 if ((unsigned)item_start[mid] <= w) lo_i = mid;
                 else hi_i = mid - 1;
             }
-            const int B = order[lo_i];
+            B = order[lo_i];
             s0 = seg_start[B];
             s1 = seg_end[B];
             e0 = s0 + (int)(w - (unsigned)item_start[lo_i]) * kM2LChunk;
@@ -458,7 +489,7 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
         warp_pow_table(1.0 / sigma, P + 1, lane, pws);
         __syncwarp();
         if (has) {
-            double* out = part + (size_t)w * nco_out;
+            double* out = s1 - s0 <= kM2LChunk ? args.F + (size_t)B * nco_out : args.part + (size_t)w * nco_out;
             for (int c = lane; c < NCO; c += 32) {
                 const float* row = S + c * kPad;
                 float s = 0.f;
@@ -480,9 +511,7 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1)
 }  // namespace
 
 template <int P>
-void rot_launch(const int2* list, const int* seg_start, const int* seg_end, const int* order, const int* item_start,
-                unsigned* work, const d4* cen, const float* Mt, const cd* M64, double* part, const int* ilist,
-                const unsigned* goff, int gq, unsigned* counter, int nco_out, int adapt, cudaStream_t s) {
+void rot_launch(const RotArgs& args, cudaStream_t s) {
     constexpr int W = rot_warps<P>();
     const size_t sm = (size_t)W * rot_warp_bytes<P>();
     cudaFuncSetAttribute(k_m2l_rot<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -491,8 +520,7 @@ void rot_launch(const int2* list, const int* seg_start, const int* seg_end, cons
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_m2l_rot<P>, 32 * W, sm);
     const unsigned g = (unsigned)(nsm * (bps > 0 ? bps : 1));
-    k_m2l_rot<P><<<g, 32 * W, sm, s>>>(list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part, ilist,
-                                       goff, gq, counter, nco_out, adapt);
+    k_m2l_rot<P><<<g, 32 * W, sm, s>>>(args);
     note_launch();
 }
 

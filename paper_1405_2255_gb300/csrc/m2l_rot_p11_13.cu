@@ -2,13 +2,7 @@
 #include "m2l_rot.cuh"
 
 namespace gb3 {
-template void rot_launch<11>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
-template void rot_launch<12>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
-template void rot_launch<13>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
+template void rot_launch<11>(const RotArgs&, cudaStream_t);
+template void rot_launch<12>(const RotArgs&, cudaStream_t);
+template void rot_launch<13>(const RotArgs&, cudaStream_t);
 }  // namespace gb3

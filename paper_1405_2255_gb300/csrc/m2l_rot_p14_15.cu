@@ -2,10 +2,6 @@
 #include "m2l_rot.cuh"
 
 namespace gb3 {
-template void rot_launch<14>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
-template void rot_launch<15>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
+template void rot_launch<14>(const RotArgs&, cudaStream_t);
+template void rot_launch<15>(const RotArgs&, cudaStream_t);
 }  // namespace gb3

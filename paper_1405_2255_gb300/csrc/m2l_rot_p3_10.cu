@@ -2,28 +2,12 @@
 #include "m2l_rot.cuh"
 
 namespace gb3 {
-template void rot_launch<3>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
-template void rot_launch<4>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
-template void rot_launch<5>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
-template void rot_launch<6>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
-template void rot_launch<7>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
-template void rot_launch<8>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
-template void rot_launch<9>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
-template void rot_launch<10>(const int2*, const int*, const int*, const int*, const int*, unsigned*,
-                                const d4*, const float*, const cd*, double*, const int*, const unsigned*, int,
-                                unsigned*, int, int, cudaStream_t);
+template void rot_launch<3>(const RotArgs&, cudaStream_t);
+template void rot_launch<4>(const RotArgs&, cudaStream_t);
+template void rot_launch<5>(const RotArgs&, cudaStream_t);
+template void rot_launch<6>(const RotArgs&, cudaStream_t);
+template void rot_launch<7>(const RotArgs&, cudaStream_t);
+template void rot_launch<8>(const RotArgs&, cudaStream_t);
+template void rot_launch<9>(const RotArgs&, cudaStream_t);
+template void rot_launch<10>(const RotArgs&, cudaStream_t);
 }  // namespace gb3

@@ -113,6 +113,8 @@ struct Run {
     int* dtotal = nullptr;
     int2 *front0 = nullptr, *front1 = nullptr;
     void* sort_tmp = nullptr;
+    void* p2p_tmp = nullptr;
+    size_t p2p_tmp_bytes = 0;
 };
 
 int fail_na(Run& r, int code, const char* msg) {
@@ -158,6 +160,17 @@ int walk_na(Run& r, WalkParams wp, int2* m2l, long long m2l_cap, int2* p2p, long
     }
     *nm = (long long)h[1];
     *np = (long long)h[2];
+    return 0;
+}
+
+// mixed P2P with its work plan in the rest of the static array (shared with the list sorts)
+int p2p_na(Run& r, const float* xhi, const float* xlo, const int2* list, const int* seg_start, const int* seg_end,
+           double* psi, double* acc, int mode) {
+    unsigned long long h_tot[2] = {0, 0};
+    const size_t have = r.p2p_tmp_bytes;
+    const size_t need = launch_p2p_mixed(xhi, xlo, r.n, r.c, list, seg_start, seg_end, r.leaves, r.nleaves, psi, acc,
+                                         mode, r.p2p_tmp, have, h_tot, r.s);
+    if (need > have) return fail_na(r, FMM_E_OVERFLOW, "the P2P work plan exceeds the static scratch capacity");
     return 0;
 }
 
@@ -260,7 +273,6 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     int2* p2p = A.take<int2>(kListCap);
     int2* est_m2l = A.take<int2>(kEstCap);
     int2* est_p2p = A.take<int2>(kEstCap);
-    r.sort_tmp = A.take<unsigned char>(list_sort_tmp_bytes(kListCap));
     int* m2l_seg_start = A.take<int>(nc);
     int* m2l_seg_end = A.take<int>(nc);
     int* seg_start = A.take<int>(nc);
@@ -274,8 +286,15 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     double* Ff = A.take<double>(nc);
     float4* walkf = A.take<float4>((size_t)(2 + walk_fstride(p) / 4) * nc);
     void* m2l_tmp = A.take<unsigned char>(m2l_split_tmp_bytes(nc, p > 1 ? p : 1, kListCap));
-    void* p2p_tmp = A.take<unsigned char>(p2p_tmp_bytes(r.nleaves));
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the expansions and lists");
+    // the rest of the array serves the list sorts and, once a list is sorted, the mixed P2P's
+    // work plan (the two never overlap on the stream)
+    const size_t used = (A.used + 255) & ~(size_t)255;
+    r.p2p_tmp_bytes = used < kNoAllocBytes ? kNoAllocBytes - used : 0;
+    if (r.p2p_tmp_bytes < list_sort_tmp_bytes(kListCap, (int)cap))
+        return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the list sorts");
+    r.p2p_tmp = A.take<unsigned char>(r.p2p_tmp_bytes);
+    r.sort_tmp = r.p2p_tmp;
 
     // A7: scale estimate and its per-cell minimum
     if (prm.mac != FMM_MAC_THETA) {
@@ -305,10 +324,10 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
             launch_est_m2l(est_m2l, m2l_seg_start, m2l_seg_end, nc, r.c, F1, s,
                            prm.precision == FMM_PREC_MIXED ? walkf : nullptr);
             // (the p = 1 L2L is folded into launch_est_scale)
-            if (prm.precision == FMM_PREC_MIXED)
-                launch_p2p_mixed(r.xm, xhi, xlo, n, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near,
-                                 acc_near, 0, p2p_tmp, s);
-            else
+            if (prm.precision == FMM_PREC_MIXED) {
+                rc = p2p_na(r, xhi, xlo, est_p2p, seg_start, seg_end, psi_near, acc_near, 0);
+                if (rc) return rc;
+            } else
                 launch_p2p_fp64(r.xm, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
             launch_est_scale(r.c, r.leaves, r.nleaves, F1, acc_near, scale, s);
         }
@@ -364,10 +383,10 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
         launch_m2l(m2l, m2l_seg_start, m2l_seg_end, m2l_tmp, nc, r.c.sr, M, p, F, s);
     sort_pairs_by_sink(p2p, np, nc, r.sort_tmp, s);
     launch_segments(p2p, np, nc, seg_start, seg_end, s);
-    if (prm.precision == FMM_PREC_MIXED)
-        launch_p2p_mixed(r.xm, xhi, xlo, n, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near,
-                         prm.p2p_two_float, p2p_tmp, s);
-    else
+    if (prm.precision == FMM_PREC_MIXED) {
+        rc = p2p_na(r, xhi, xlo, p2p, seg_start, seg_end, psi_near, acc_near, prm.p2p_two_float);
+        if (rc) return rc;
+    } else
         launch_p2p_fp64(r.xm, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
     for (int L = 1; L < nl; ++L) {
         if (split) launch_l2l_split(r.c, r.c.sr, r.lev[L], r.lev[L + 1], p, F, s);

@@ -1,0 +1,592 @@
+// p2p.cu -- the mixed-precision P2P of eq. (1): for every sink leaf B, Psi_b += mu_a / r and
+// a_b += mu_a (x_a - x_b) / r^3 over the particles a of its source cells (its own P2P segment
+// and those of its ancestors), a != b and r > 0 (coincident pairs skipped).
+//
+// Pair terms are FP32; each lane's FP32 sums over one tile (at most 128 pairs) are added to
+// two-float accumulators (TwoSum), so the sum over a sink's thousands of sources is compensated.
+// What a pair needs in FP32 is an accurate difference dx = x_a - x_b.  Two forms:
+//   near: dx = (h_a - h_b) + (l_a - l_b) from the two-float positions (hi = fl32(x),
+//         lo = fl32(x - hi)), one FP32 rounding relative to |dx| itself however close the pair;
+//   far:  every source of a tile is turned once into its FP32 offset from the sink leaf's centre
+//         c, o_a = (h_a - c_h) + (l_a - c_l), the sink likewise, and dx = o_a - o_b: one FP32
+//         operation per coordinate and pair instead of three.  o_a and o_b carry absolute errors
+//         of about 2^-24 |o|, so dx is relatively accurate to about 2^-24 (1 + 2 rho_B / |dx|).
+// A source cell A is near when some pair of A x B could be closer than rho_B (the sink leaf's
+// radius): |s_A - s_B| < rho_A + 2 rho_B.  Far pairs are then at least rho_B apart and their dx
+// is good to about 3 x 2^-24, the same order as the rsqrt.approx of every pair.
+//
+// Work plan, built once per evaluation (k_p2p_count, k_p2p_emit): per leaf, its sources as
+// particle ranges with their class (consecutive source cells of one class whose particles are
+// contiguous are merged), in a region sized by its number of source cells, near ranges from the
+// front and far ones from the back; and the work items (leaf, sink chunk).  A leaf of c sinks
+// is cut into k chunks of S = ceil(c / k) sinks, each chunk replicated R <= 4 times across a
+// warp (lane = replica * S + sink; replica r takes every R-th group of four sources of a tile),
+// with (k, R) the choice that keeps the most lanes busy.  Every item streams its leaf's ranges
+// through double-buffered structure-of-arrays tiles of 128 sources (96 for three replicas;
+// 4-byte cp.async copies); a tile holds one class.  Items run in decreasing order of their
+// length (source particles / R) from an atomic counter.
+#include <climits>
+
+#include "kernels.cuh"
+
+namespace gb3 {
+
+constexpr int kP2PWarpsM = 4;        // warps per block
+constexpr int kP2PTileM = 128;       // sources per staged tile at the largest replica count (4 x 32)
+constexpr int kRangeCountBits = 29;  // a range record holds count | near << 30 | guard << 29
+constexpr int kRangeMax = (1 << kRangeCountBits) - 1;
+
+typedef unsigned long long f2;  // two packed floats
+__device__ __forceinline__ f2 f2_pack(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// the sink of a lane, its coordinates duplicated in both halves
+struct SinkPk {
+    f2 hx, hy, hz, lx, ly, lz;
+};
+struct AccPk {
+    f2 ps, ax, ay, az;
+};
+
+// two sources against the sink; TWO_FLOAT: dx from the two-float parts, else from X, Y, Z alone
+// (FP32 offsets, or the high parts for the low-order estimate); GUARD: skip r = 0
+template <bool TWO_FLOAT, bool GUARD>
+__device__ __forceinline__ void pair2(f2 X, f2 Y, f2 Z, f2 W, f2 XL, f2 YL, f2 ZL, const SinkPk& b, AccPk& a) {
+    f2 dx = f2_sub(X, b.hx), dy = f2_sub(Y, b.hy), dz = f2_sub(Z, b.hz);
+    if (TWO_FLOAT) {
+        dx = f2_add(dx, f2_sub(XL, b.lx));
+        dy = f2_add(dy, f2_sub(YL, b.ly));
+        dz = f2_add(dz, f2_sub(ZL, b.lz));
+    }
+    const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+    float r2a, r2b;
+    f2_unpack(r2, r2a, r2b);
+    float ia = rsqrt_ftz(r2a), ib = rsqrt_ftz(r2b);
+    if (GUARD) {
+        ia = r2a > 0.f ? ia : 0.f;
+        ib = r2b > 0.f ? ib : 0.f;
+    }
+    const f2 rinv = f2_pack(ia, ib);
+    const f2 qm = f2_mul(W, rinv);
+    const f2 q3 = f2_mul(qm, f2_mul(rinv, rinv));
+    a.ps = f2_add(a.ps, qm);
+    a.ax = f2_fma(q3, dx, a.ax);
+    a.ay = f2_fma(q3, dy, a.ay);
+    a.az = f2_fma(q3, dz, a.az);
+}
+
+// one group of four sources of the tile (index g) against the sink
+template <bool TWO_FLOAT, bool GUARD>
+__device__ __forceinline__ void group4(const float* __restrict__ T, int g, const SinkPk& b, AccPk& a) {
+    const float4 X = ((const float4*)(T + 0 * kP2PTileM))[g], Y = ((const float4*)(T + 1 * kP2PTileM))[g],
+                 Z = ((const float4*)(T + 2 * kP2PTileM))[g], W = ((const float4*)(T + 3 * kP2PTileM))[g];
+    float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), YL = XL, ZL = XL;
+    if (TWO_FLOAT) {
+        XL = ((const float4*)(T + 4 * kP2PTileM))[g];
+        YL = ((const float4*)(T + 5 * kP2PTileM))[g];
+        ZL = ((const float4*)(T + 6 * kP2PTileM))[g];
+    }
+    pair2<TWO_FLOAT, GUARD>(f2_pack(X.x, X.y), f2_pack(Y.x, Y.y), f2_pack(Z.x, Z.y), f2_pack(W.x, W.y),
+                            f2_pack(XL.x, XL.y), f2_pack(YL.x, YL.y), f2_pack(ZL.x, ZL.y), b, a);
+    pair2<TWO_FLOAT, GUARD>(f2_pack(X.z, X.w), f2_pack(Y.z, Y.w), f2_pack(Z.z, Z.w), f2_pack(W.z, W.w),
+                            f2_pack(XL.z, XL.w), f2_pack(YL.z, YL.w), f2_pack(ZL.z, ZL.w), b, a);
+}
+
+// sources per full tile for R replicas: 128, or 96 for three (eight groups of four each)
+__host__ __device__ constexpr int p2p_tile(int R) { return R == 3 ? 96 : kP2PTileM; }
+
+// replica r0 of R takes groups r0, r0 + R, ... of a tile of ng groups; a full tile has a trip
+// count known at compile time
+template <bool TWO_FLOAT, bool GUARD, int R>
+__device__ __forceinline__ void tile_r(const float* __restrict__ T, int ng, int r0, const SinkPk& b, AccPk& a) {
+    constexpr int NG = p2p_tile(R) / 4;
+    if (ng == NG) {
+#pragma unroll 2
+        for (int k = 0; k < NG / R; ++k) group4<TWO_FLOAT, GUARD>(T, r0 + R * k, b, a);
+    } else {
+#pragma unroll 1
+        for (int g = r0; g < ng; g += R) group4<TWO_FLOAT, GUARD>(T, g, b, a);
+    }
+}
+template <bool TWO_FLOAT, bool GUARD>
+__device__ __forceinline__ void tile_any(const float* __restrict__ T, int ng, int r0, int R, const SinkPk& b,
+                                         AccPk& a) {
+    if (R == 1) tile_r<TWO_FLOAT, GUARD, 1>(T, ng, r0, b, a);
+    else if (R == 2) tile_r<TWO_FLOAT, GUARD, 2>(T, ng, r0, b, a);
+    else if (R == 3) tile_r<TWO_FLOAT, GUARD, 3>(T, ng, r0, b, a);
+    else tile_r<TWO_FLOAT, GUARD, 4>(T, ng, r0, b, a);
+}
+
+// s.hi += v with the rounding error of that addition (TwoSum) kept in s.lo; s.lo is not
+// renormalised against s.hi (its own rounding, u |s.lo|, stays far below u |s.hi|)
+__device__ __forceinline__ void acc2(ff& s, float v) {
+    const ff t = two_sum(s.hi, v);
+    s.hi = t.hi;
+    s.lo = __fadd_rn(s.lo, t.lo);
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// (k chunks, R replicas) for a leaf of c sinks: the most busy lanes, c R / (32 k), fewest chunks
+// on ties; R <= 4 (a tile holds 32 R sources)
+__host__ __device__ inline void p2p_chunking(int c, int& k, int& R) {
+    k = 1;
+    R = 1;
+    if (c <= 0) return;
+    const int kmin = (c + 31) / 32;
+    float best = -1.f;
+    for (int kk = kmin; kk < kmin + 16; ++kk) {
+        const int S = (c + kk - 1) / kk;
+        const int RR = 32 / S < 4 ? 32 / S : 4;
+        const float u = (float)c * (float)RR / (32.f * (float)kk);
+        if (u > best + 1e-6f) {
+            best = u;
+            k = kk;
+            R = RR;
+        }
+        if (S <= 8) break;  // already four replicas; more chunks only add passes
+    }
+    k = (c + (c + k - 1) / k - 1) / ((c + k - 1) / k);  // no empty chunk: k = ceil(c / S)
+}
+
+// class of source cell A for sink leaf B (see the file comment); mode 1 only
+__device__ inline bool p2p_near(const d4& a, const d4& b) {
+    const double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    const double lim = a.w + 2.0 * b.w;
+    return dx * dx + dy * dy + dz * dz < lim * lim;
+}
+
+// per leaf index t (one warp each): the number of its source cells (the ranges it can need at
+// most: its own and its ancestors' segment lengths) and the sort key of its items, descending
+// in the length of an item (source particles / R)
+__global__ void k_p2p_count(Cells c, const int2* __restrict__ list, const int* __restrict__ seg_start,
+                            const int* __restrict__ seg_end, const int* __restrict__ leaves, int nleaves,
+                            int* __restrict__ nb, uint64_t* __restrict__ keys, unsigned long long* __restrict__ tot) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long my = 0;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nleaves; t += nw) {
+        const int leaf = leaves[t];
+        long long e = 0, src = 0;
+        for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
+            const int s0 = seg_start[cell], s1 = seg_end[cell];
+            e += s1 - s0;
+            for (int i = s0 + lane; i < s1; i += 32) src += c.count[list[i].x];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) src += __shfl_xor_sync(0xffffffffu, src, o);
+        if (lane == 0) {
+            nb[t] = (int)e;
+            my += (unsigned long long)e;
+            int k, R;
+            p2p_chunking(c.count[leaf], k, R);
+            const unsigned long long len = (unsigned long long)src / (unsigned long long)R + 1;
+            const unsigned w32 = !cell_active(c, leaf) ? 0u : (len > 0xfffffffeull ? 0xfffffffeu : (unsigned)len);
+            keys[t] = ((uint64_t)(0xffffffffu - w32) << 32) | (unsigned)t;
+        }
+    }
+    if (lane == 0 && my) atomicAdd(&tot[0], my);
+}
+
+// items per position of the sorted order (0 for a leaf without active particles)
+__global__ void k_p2p_nitems(const uint64_t* __restrict__ keys, const int* __restrict__ leaves, int nleaves, Cells c,
+                             int* __restrict__ order, int* __restrict__ nit, unsigned long long* __restrict__ tot) {
+    unsigned long long my = 0;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nleaves; q += gridDim.x * blockDim.x) {
+        const int t = (int)(keys[q] & 0xffffffffu);
+        order[q] = t;
+        const int leaf = leaves[t];
+        int k = 0, R;
+        if (cell_active(c, leaf)) p2p_chunking(c.count[leaf], k, R);
+        nit[q] = k;
+        my += (unsigned long long)k;
+    }
+    if (my) atomicAdd(&tot[1], my);
+}
+
+// Walks the sources of leaf B (its own segment, then each ancestor's) and merges them into
+// ranges per class; emit(near, first, count, guard) receives every finished range in order.
+template <class Emit>
+__device__ void p2p_ranges_of(const Cells& c, const int2* __restrict__ list, const int* __restrict__ seg_start,
+                              const int* __restrict__ seg_end, int leaf, int mode, int lane, Emit emit) {
+    const d4 sb = c.sr[leaf];
+    const long long b0 = c.first[leaf], b1 = b0 + c.count[leaf];
+    auto overlaps = [&](long long f, long long m) { return f < b1 && b0 < f + m; };
+    int cf[2] = {0, 0}, cn[2] = {0, 0};
+    bool cg[2] = {false, false};
+    for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
+        const int s0 = seg_start[cell], s1 = seg_end[cell];
+        for (int e0 = s0; e0 < s1; e0 += 32) {
+            int af = 0, an = 0, kk = 0;
+            if (e0 + lane < s1) {
+                const int A = list[e0 + lane].x;
+                af = c.first[A];
+                an = c.count[A];
+                kk = mode == 1 ? (p2p_near(c.sr[A], sb) ? 1 : 0) : (mode == 3 ? 1 : 0);
+            }
+            const int m = min(32, s1 - e0);
+            for (int q = 0; q < m; ++q) {
+                const int f = __shfl_sync(0xffffffffu, af, q), n = __shfl_sync(0xffffffffu, an, q);
+                const int k = __shfl_sync(0xffffffffu, kk, q);
+                if (n <= 0) continue;
+                if (cn[k] > 0 && cf[k] + cn[k] == f && (long long)cn[k] + n <= kRangeMax) {
+                    cn[k] += n;
+                    cg[k] = cg[k] || overlaps(f, n);
+                    continue;
+                }
+                if (cn[k] > 0) emit(k, cf[k], cn[k], cg[k]);
+                cf[k] = f;
+                cn[k] = n;
+                cg[k] = overlaps(f, n);
+            }
+        }
+    }
+    for (int k = 1; k >= 0; --k)
+        if (cn[k] > 0) emit(k, cf[k], cn[k], cg[k]);
+}
+
+__global__ void k_p2p_emit(Cells c, const int2* __restrict__ list, const int* __restrict__ seg_start,
+                           const int* __restrict__ seg_end, const int* __restrict__ leaves, int nleaves, int mode,
+                           const int* __restrict__ order, const int* __restrict__ roff, const int* __restrict__ nb,
+                           int* __restrict__ nnear, int* __restrict__ nfar, const int* __restrict__ ioff,
+                           const int* __restrict__ nit, int2* __restrict__ ranges, int2* __restrict__ items) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nleaves; q += nw) {
+        const int t = order[q];
+        for (int j = lane; j < nit[q]; j += 32) items[ioff[q] + j] = make_int2(t, j);
+        const int leaf = leaves[t];
+        const int r0 = roff[t], r1 = r0 + nb[t];
+        int cnt[2] = {0, 0};
+        p2p_ranges_of(c, list, seg_start, seg_end, leaf, mode, lane,
+                      [&](int k, int f, int m, bool g) {
+                          const int pos = k ? r0 + cnt[1] : r1 - 1 - cnt[0];
+                          if (lane == 0) ranges[pos] = make_int2(f, m | (k << 30) | ((g ? 1 : 0) << kRangeCountBits));
+                          ++cnt[k];
+                      });
+        if (lane == 0) {
+            nnear[t] = cnt[1];
+            nfar[t] = cnt[0];
+        }
+    }
+}
+
+// The ranges of one item as a stream of tiles.  A tile takes sources from consecutive ranges
+// of one class; fill() returns the number of sources copied (0 when the stream is exhausted)
+// and the tile's class and guard flag.
+struct RangeStream {
+    int e, e_end;      // next range, end of the current segment
+    int f0, f1;        // the second segment (the far ranges)
+    int af, an, off;   // the current range and the position in it
+    bool near, guard;  // its class and guard flag
+    __device__ void start(int r0, int r1, int s0, int s1) {
+        e = r0;
+        e_end = r1;
+        f0 = s0;
+        f1 = s1;
+        af = an = off = 0;
+        near = guard = false;
+    }
+    template <bool LOADLO>
+    __device__ int fill(const int2* __restrict__ ranges, const float* __restrict__ hi, const float* __restrict__ lo,
+                        size_t n, int lane, int T, float* tile, bool& tile_near, bool& tile_guard) {
+        int m = 0;
+        tile_guard = false;
+        tile_near = near;
+        while (m < T) {
+            if (off == an) {  // next range
+                if (e >= e_end) {
+                    if (f0 >= f1) break;
+                    e = f0;  // on to the second segment
+                    e_end = f1;
+                    f0 = f1;
+                    continue;
+                }
+                const int2 r = ranges[e];
+                const bool nr = (r.y >> 30) & 1;
+                if (m > 0 && nr != tile_near) break;  // a tile holds one class
+                ++e;
+                af = r.x;
+                an = r.y & kRangeMax;
+                off = 0;
+                near = nr;
+                guard = (r.y >> kRangeCountBits) & 1;
+                tile_near = nr;
+                continue;
+            }
+            const int k = min(T - m, an - off);
+            for (int q = lane; q < k; q += 32) {
+                const size_t j = (size_t)af + off + q;
+                float* t = tile + m + q;
+#pragma unroll
+                for (int d = 0; d < 4; ++d) cp_async4(t + d * kP2PTileM, hi + d * n + j);
+                if (LOADLO)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) cp_async4(t + (4 + d) * kP2PTileM, lo + d * n + j);
+            }
+            tile_guard = tile_guard || guard;
+            m += k;
+            off += k;
+        }
+        return m;
+    }
+};
+
+// MODE 0: dx from the FP32 high parts (the low-order estimate); 1: near ranges two-float,
+// far ranges FP32 offsets from the leaf centre; 2: offsets for every range; 3: two-float for
+// every range
+template <int MODE>
+__global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
+    k_p2p_mixed(const float* __restrict__ hi, const float* __restrict__ lo, int n, Cells c,
+                const int* __restrict__ leaves, const int2* __restrict__ ranges, const int* __restrict__ roff,
+                const int* __restrict__ nb, const int* __restrict__ nnear, const int* __restrict__ nfar,
+                const int2* __restrict__ items, int nitems, unsigned* __restrict__ counter,
+                double* __restrict__ psi, double* __restrict__ acc) {
+    constexpr bool LOADLO = MODE >= 1;  // the tiles carry the low parts
+    constexpr bool CENTRE = MODE == 1 || MODE == 2;
+    constexpr int NA = LOADLO ? 7 : 4;  // arrays per tile
+    __shared__ __align__(16) float tiles[kP2PWarpsM][2][NA * kP2PTileM];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t nn = (size_t)n;
+    const f2 zero = f2_pack(0.f, 0.f);
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(counter, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= (unsigned)nitems) break;
+        const int2 it = items[w];
+        const int t = it.x, leaf = leaves[t];
+        const int first = c.first[leaf], count = c.count[leaf];
+        int k, R;
+        p2p_chunking(count, k, R);
+        const int S = (count + k - 1) / k;
+        const int s0 = it.y * S, chunk = min(S, count - s0);
+        // lanes past S * R repeat replica 0's work; their sums are not used
+        const int sink = lane % S, rep = lane / S < R ? lane / S : 0;
+        const bool active = sink < chunk && lane < S * R;
+        const int i = first + s0 + (sink < chunk ? sink : 0);
+        const float bhx = hi[i], bhy = hi[nn + i], bhz = hi[2 * nn + i];
+        float blx = 0.f, bly = 0.f, blz = 0.f;
+        if (LOADLO) {
+            blx = lo[i];
+            bly = lo[nn + i];
+            blz = lo[2 * nn + i];
+        }
+        const SinkPk b2{f2_pack(bhx, bhx), f2_pack(bhy, bhy), f2_pack(bhz, bhz),
+                        f2_pack(blx, blx), f2_pack(bly, bly), f2_pack(blz, blz)};
+        // the leaf centre as two floats, the sink as its FP32 offset from it
+        float chx = 0.f, chy = 0.f, chz = 0.f, clx = 0.f, cly = 0.f, clz = 0.f;
+        SinkPk bo = b2;
+        if (CENTRE) {
+            const d4 sc = c.sr[leaf];
+            chx = (float)sc.x;
+            chy = (float)sc.y;
+            chz = (float)sc.z;
+            clx = (float)(sc.x - (double)chx);
+            cly = (float)(sc.y - (double)chy);
+            clz = (float)(sc.z - (double)chz);
+            const float ox = __fadd_rn(__fsub_rn(bhx, chx), __fsub_rn(blx, clx));
+            const float oy = __fadd_rn(__fsub_rn(bhy, chy), __fsub_rn(bly, cly));
+            const float oz = __fadd_rn(__fsub_rn(bhz, chz), __fsub_rn(blz, clz));
+            bo = SinkPk{f2_pack(ox, ox), f2_pack(oy, oy), f2_pack(oz, oz), zero, zero, zero};
+        }
+        AccPk a{zero, zero, zero, zero};
+        ff aps = {0, 0}, aax = {0, 0}, aay = {0, 0}, aaz = {0, 0};
+        RangeStream cur;
+        {
+            const int r0 = roff[t], r1 = r0 + nb[t];
+            cur.start(r0, r0 + nnear[t], r1 - nfar[t], r1);
+        }
+        const int T = p2p_tile(R);  // sources per tile, shared by the replicas
+        int bb = 0;
+        bool near = false, guard = false, near_next = false, guard_next = false;
+        int nt = cur.fill<LOADLO>(ranges, hi, lo, nn, lane, T, tiles[wid][0], near, guard);
+        cp_async_commit();
+        while (nt > 0) {
+            // issue the next tile, then wait for the current one
+            const int nx = cur.fill<LOADLO>(ranges, hi, lo, nn, lane, T, tiles[wid][bb ^ 1], near_next, guard_next);
+            cp_async_commit();
+            cp_async_wait1();
+            float* tile = tiles[wid][bb];
+            const int ng = (nt + 3) >> 2;
+            const bool two = MODE == 3 || (MODE == 1 && near);
+            if (CENTRE && !two) {  // offsets from the leaf centre, in place of the high parts
+                __syncwarp();
+                for (int j = lane; j < nt; j += 32) {
+                    tile[j] = __fadd_rn(__fsub_rn(tile[j], chx), __fsub_rn(tile[4 * kP2PTileM + j], clx));
+                    tile[kP2PTileM + j] =
+                        __fadd_rn(__fsub_rn(tile[kP2PTileM + j], chy), __fsub_rn(tile[5 * kP2PTileM + j], cly));
+                    tile[2 * kP2PTileM + j] =
+                        __fadd_rn(__fsub_rn(tile[2 * kP2PTileM + j], chz), __fsub_rn(tile[6 * kP2PTileM + j], clz));
+                }
+            }
+            if (lane < 4 * ng - nt) {  // pad to whole groups: massless, far away
+                float* p = tile + nt + lane;
+                p[0] = 1e15f;
+                p[kP2PTileM] = 1e15f;
+                p[2 * kP2PTileM] = 1e15f;
+                p[3 * kP2PTileM] = 0.f;
+                if (LOADLO) p[4 * kP2PTileM] = p[5 * kP2PTileM] = p[6 * kP2PTileM] = 0.f;
+            }
+            __syncwarp();
+            if (two) {
+                if (guard) tile_any<true, true>(tile, ng, rep, R, b2, a);
+                else tile_any<true, false>(tile, ng, rep, R, b2, a);
+            } else if (CENTRE) {
+                if (guard) tile_any<false, true>(tile, ng, rep, R, bo, a);
+                else tile_any<false, false>(tile, ng, rep, R, bo, a);
+            } else {
+                if (guard) tile_any<false, true>(tile, ng, rep, R, b2, a);
+                else tile_any<false, false>(tile, ng, rep, R, b2, a);
+            }
+            // fold the FP32 partials (<= 128 pairs per lane) into the two-float sums
+            float u0, u1;
+            f2_unpack(a.ps, u0, u1); acc2(aps, u0 + u1);
+            f2_unpack(a.ax, u0, u1); acc2(aax, u0 + u1);
+            f2_unpack(a.ay, u0, u1); acc2(aay, u0 + u1);
+            f2_unpack(a.az, u0, u1); acc2(aaz, u0 + u1);
+            a = AccPk{zero, zero, zero, zero};
+            __syncwarp();  // every lane is done with the tile before it is refilled
+            bb ^= 1;
+            nt = nx;
+            near = near_next;
+            guard = guard_next;
+        }
+        // add the replicas' partial sums (lanes sink + S, sink + 2 S, ... into lane sink);
+        // only lanes below S accumulate, so every lane read still holds its own sum
+        for (int j = 1; j < R; ++j) {
+            const int src = min(lane + j * S, 31);
+            ff tps = aps, tax = aax, tay = aay, taz = aaz;
+            ff_add_lane(tps, src); ff_add_lane(tax, src); ff_add_lane(tay, src); ff_add_lane(taz, src);
+            if (lane < S) {
+                aps = tps; aax = tax; aay = tay; aaz = taz;
+            }
+        }
+        if (active && lane < S) {
+            psi[i] = (double)aps.hi + (double)aps.lo;
+            acc[3 * (size_t)i] = (double)aax.hi + (double)aax.lo;
+            acc[3 * (size_t)i + 1] = (double)aay.hi + (double)aay.lo;
+            acc[3 * (size_t)i + 2] = (double)aaz.hi + (double)aaz.lo;
+        }
+    }
+}
+
+namespace {
+// layout of the fixed part of the scratch (depends on the number of leaves only)
+struct PlanLayout {
+    uint64_t *k0, *k1;
+    int *order, *nb, *roff, *nnear, *nfar, *nit, *ioff, *stmp, *rtmp;
+    unsigned long long* tot;  // [0] ranges, [1] items
+    unsigned* counter;
+    size_t bytes;
+};
+PlanLayout plan_layout(void* base, int nleaves) {
+    PlanLayout L;
+    const size_t nl = (size_t)(nleaves > 0 ? nleaves : 1);
+    unsigned char* p = (unsigned char*)base;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        unsigned char* r = p ? p + off : nullptr;
+        off += bytes;
+        return r;
+    };
+    L.k0 = (uint64_t*)take(nl * 8);
+    L.k1 = (uint64_t*)take(nl * 8);
+    L.order = (int*)take(nl * 4);
+    L.nb = (int*)take(nl * 4);
+    L.roff = (int*)take((nl + 1) * 4);
+    L.nnear = (int*)take(nl * 4);
+    L.nfar = (int*)take(nl * 4);
+    L.nit = (int*)take(nl * 4);
+    L.ioff = (int*)take((nl + 1) * 4);
+    L.stmp = (int*)take(scan_tmp_ints((long long)nl + 1) * 4);
+    L.rtmp = (int*)take(radix_tmp_ints((long long)nl) * 4);
+    L.tot = (unsigned long long*)take(4 * 8);
+    L.counter = (unsigned*)take(4 * 4);
+    L.bytes = (off + 255) & ~(size_t)255;
+    return L;
+}
+}  // namespace
+
+size_t p2p_plan_fixed_bytes(int nleaves) { return plan_layout(nullptr, nleaves).bytes; }
+
+size_t launch_p2p_mixed(const float* hi, const float* lo, int n, Cells c, const int2* list, const int* seg_start,
+                        const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc, int mode,
+                        void* tmp, size_t tmp_bytes, unsigned long long* h_tot, cudaStream_t s) {
+    if (nleaves <= 0) return 0;
+    if (n > kRangeMax) return ~(size_t)0;  // no range is ever cut: a leaf's region holds its source cells
+    PlanLayout L = plan_layout(tmp, nleaves);
+    if (tmp_bytes < L.bytes) return L.bytes;
+    cudaMemsetAsync(L.tot, 0, 4 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(L.counter, 0, 4 * sizeof(unsigned), s);
+    k_p2p_count<<<grid_for((long long)nleaves * 32, 128, 16), 128, 0, s>>>(c, list, seg_start, seg_end, leaves,
+                                                                           nleaves, L.nb, L.k0, L.tot);
+    note_launch();
+    scan_exclusive_i32(L.nb, L.roff, nleaves, L.roff + nleaves, L.stmp, s);
+    // the low 32 bits are the leaf index, already in order: sort the length bits only
+    const int flip = radix_sort_pairs_bits(L.k0, nullptr, L.k1, nullptr, nleaves, L.rtmp, 32, 64, s);
+    k_p2p_nitems<<<grid_for(nleaves, 256), 256, 0, s>>>(flip ? L.k1 : L.k0, leaves, nleaves, c, L.order, L.nit,
+                                                         L.tot);
+    note_launch();
+    scan_exclusive_i32(L.nit, L.ioff, nleaves, L.ioff + nleaves, L.stmp, s);
+    cudaMemcpyAsync(h_tot, L.tot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    const unsigned long long nranges = h_tot[0], nitems = h_tot[1];
+    if (nranges > (unsigned long long)INT_MAX || nitems > (unsigned long long)INT_MAX) return ~(size_t)0;
+    size_t need = L.bytes + ((nranges * sizeof(int2) + 255) & ~255ull) + nitems * sizeof(int2) + 256;
+    if (tmp_bytes < need) return need;
+    int2* ranges = (int2*)((unsigned char*)tmp + L.bytes);
+    int2* items = (int2*)((unsigned char*)ranges + ((nranges * sizeof(int2) + 255) & ~255ull));
+    const unsigned g = grid_for((long long)nleaves * 32, 128, 16);  // one warp per leaf
+    k_p2p_emit<<<g, 128, 0, s>>>(c, list, seg_start, seg_end, leaves, nleaves, mode, L.order, L.roff, L.nb, L.nnear,
+                                 L.nfar, L.ioff, L.nit, ranges, items);
+    note_launch();
+    if (nitems == 0) return need;
+    int bps = 1;
+    auto go = [&](auto kern) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kP2PWarpsM * 32, 0);
+        kern<<<sm_count() * (bps > 0 ? bps : 1), kP2PWarpsM * 32, 0, s>>>(hi, lo, n, c, leaves, ranges, L.roff, L.nb,
+                                                                         L.nnear, L.nfar, items, (int)nitems,
+                                                                         L.counter, psi, acc);
+    };
+    if (mode == 1) go(k_p2p_mixed<1>);
+    else if (mode == 2) go(k_p2p_mixed<2>);
+    else if (mode == 3) go(k_p2p_mixed<3>);
+    else go(k_p2p_mixed<0>);
+    note_launch();
+    return need;
+}
+
+}  // namespace gb3

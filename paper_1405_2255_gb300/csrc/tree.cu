@@ -226,7 +226,7 @@ int sort_by_system(const uint64_t* keys, const int* idx, int n, const int* off, 
 
 // ------------------------------------------------------------------ A2 radix sort
 // Stable LSD radix sort of (key, index) pairs, 8 bits per pass, 8 passes over the
-// 63 key bits.  Per pass: a digit histogram per tile, a device-wide exclusive scan
+// 63 key bits (index arrays nullptr: the keys alone).  Per pass: a digit histogram per tile, a device-wide exclusive scan
 // in digit-major order, and a stable scatter that ranks equal digits inside the
 // tile in item order with warp match masks.
 constexpr int kRsThreads = 256;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* __res
         long long i = base + r * kRsThreads + threadIdx.x;
         bool valid = i < n;
         uint64_t key = valid ? kin[i] : 0;
-        int val = valid ? vin[i] : 0;
+        int val = (valid && vin) ? vin[i] : 0;
         int d = valid ? (int)((key >> shift) & 255) : 256;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int rank = __popc(peers & ((1u << lane) - 1));
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* __res
         if (valid) {
             int dst = wc[w][d] + rank;
             kout[dst] = key;
-            vout[dst] = val;
+            if (vout) vout[dst] = val;
         }
         __syncthreads();
     }

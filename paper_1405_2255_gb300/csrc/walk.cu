@@ -298,42 +298,40 @@ static int bits_for(long long v) {
     return b;
 }
 
-// key = (sink << xb) | first entry: the first entry takes the low xb bits
-__global__ void k_pack_pairs(const int2* __restrict__ list, long long n, int xb, uint64_t* __restrict__ keys,
-                             int* __restrict__ idx) {
+// key = (sink << xb) | first entry: the first entry (taken as unsigned) in the low xb bits
+__global__ void k_pack_pairs(const int2* __restrict__ list, long long n, int xb, uint64_t* __restrict__ keys) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int2 v = list[i];
+        const int2 v = list[i];
         keys[i] = ((uint64_t)(unsigned)v.y << xb) | (uint64_t)(unsigned)v.x;
-        idx[i] = 0;
     }
 }
-__global__ void k_unpack_pairs(const uint64_t* __restrict__ keys, long long n, int sb, int2* __restrict__ list) {
-    const uint64_t mask = sb >= 32 ? 0xffffffffull : (1ull << sb) - 1;
+__global__ void k_unpack_pairs(const uint64_t* __restrict__ keys, long long n, int xb, int2* __restrict__ list) {
+    const uint64_t mask = xb >= 32 ? 0xffffffffull : (1ull << xb) - 1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        uint64_t k = keys[i];
-        list[i] = make_int2((int)(k & mask), (int)(k >> sb));
+        const uint64_t k = keys[i];
+        list[i] = make_int2((int)(unsigned)(k & mask), (int)(k >> xb));
     }
 }
 
-size_t list_sort_tmp_bytes(long long npairs) {
-    size_t n = (size_t)(npairs > 0 ? npairs : 1);
-    return n * (2 * sizeof(uint64_t) + 2 * sizeof(int)) + radix_tmp_ints(n) * sizeof(int) + 256;
+size_t list_sort_tmp_bytes(long long npairs, int /*ncells*/) {
+    const size_t n = (size_t)(npairs > 0 ? npairs : 1);
+    return n * 2 * sizeof(uint64_t) + radix_tmp_ints((long long)n) * sizeof(int) + 256;
 }
 
+// LSD radix passes over the keys alone (8 bits per pass over the xb + sb bits in use)
 void sort_pairs_by_sink(int2* list, long long npairs, int ncells, void* tmp, cudaStream_t s, bool wide) {
     if (npairs <= 1) return;
-    int sb = bits_for(ncells);
+    const int sb = bits_for(ncells);
+    const int xb = wide ? 32 : sb;
     uint64_t* k0 = (uint64_t*)tmp;
     uint64_t* k1 = k0 + npairs;
-    int* i0 = (int*)(k1 + npairs);
-    int* i1 = i0 + npairs;
-    int* rtmp = i1 + npairs;
-    const int xb = wide ? 32 : sb;
-    unsigned g = grid_for(npairs, 256);
-    k_pack_pairs<<<g, 256, 0, s>>>(list, npairs, xb, k0, i0); note_launch();
-    int end_bit = xb + sb;
-    int flip = radix_sort_pairs_bits(k0, i0, k1, i1, npairs, rtmp, 0, end_bit, s);
-    k_unpack_pairs<<<g, 256, 0, s>>>(flip ? k1 : k0, npairs, xb, list); note_launch();
+    int* rtmp = (int*)(k1 + npairs);
+    const unsigned g = grid_for(npairs, 256);
+    k_pack_pairs<<<g, 256, 0, s>>>(list, npairs, xb, k0);
+    note_launch();
+    const int flip = radix_sort_pairs_bits(k0, nullptr, k1, nullptr, npairs, rtmp, 0, xb + sb, s);
+    k_unpack_pairs<<<g, 256, 0, s>>>(flip ? k1 : k0, npairs, xb, list);
+    note_launch();
 }
 
 __global__ void k_segments(const int2* __restrict__ list, long long n, int* __restrict__ seg_start,

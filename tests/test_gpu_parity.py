@@ -239,6 +239,35 @@ def test_mixed_precision_accuracy(g, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("shift", [0.0, 3e4])
+def test_mixed_p2p_dx_forms(g, orc, shift):
+    """The mixed P2P's forms of dx (p2p_two_float): two-float for near source cells and
+    leaf-centre offsets for the far ones (1, default), offsets for all (2), two-float for all
+    (3).  Against FP64 direct summation 1 and 3 meet the accuracy target, also far from the
+    origin, and 1 stays within FP32 rounding of 3; 2 loses accuracy on close pairs (their
+    offsets from the leaf centre are rounded relative to the leaf's size, not to their
+    distance) and is only bounded."""
+    x, mu = inputs.plummer(20000, inputs.BASE_SEED + 150)
+    x = x + shift
+    sinks = np.arange(0, 20000, 5)
+    _, a_t, _, _ = orc.direct(x, mu, sinks=sinks)
+    out, rms = {}, {}
+    for mode in (1, 2, 3):
+        ctx = g.Context(p=10, eps=1e-7, leaf_size=48, p2p_c=1.0, precision=g.FMM_PREC_MIXED, p2p_two_float=mode)
+        _, acc = ctx.fmm_evaluate(_dev(x), _dev(mu))
+        out[mode] = acc.cpu().numpy()
+        e = _rel(out[mode][sinks], a_t)
+        rms[mode] = np.sqrt(np.mean(e ** 2))
+        assert rms[mode] < (1e-7 if mode != 2 else 3e-7), (mode, rms)
+        assert np.all(np.isfinite(out[mode]))
+        ctx.close()
+    # the split's extra rounding (far dx good to a few 2^-24, like the pair's rsqrt.approx)
+    # adds in quadrature to the FMM's own error
+    assert rms[1] <= 1.1 * rms[3] + 5e-9, rms
+    d = _rel(out[1], out[3])
+    assert np.sqrt(np.mean(d ** 2)) < 5e-8 and d.max() < 2e-6, (np.sqrt(np.mean(d ** 2)), d.max())
+
+
 def test_host_entry_matches_device_entry(g):
     x, mu = inputs.plummer(3000, 9)
     ctx = g.Context(p=5, eps=1e-6, precision=g.FMM_PREC_FP64)
@@ -445,6 +474,14 @@ def test_library_swap_matrices_match_oracle_and_paper(g, orc):
         assert np.max(np.abs(g.fmm_swap_matrix(n) - orc.swap_matrix(n))) <= 1e-12 * max(1.0, np.abs(orc.swap_matrix(n)).max())
     with pytest.raises(g.FMMError):
         g.fmm_swap_matrix(17)
+
+
+def test_swap_probe_paths_agree(g):
+    """The tensor-core form of the swap stage (3xTF32 mma.sync on the parity blocks of the swap
+    matrices) computes what the FMA-immediate form computes, to FP32 rounding."""
+    r = g.fmm_swap_probe(4096, 2)
+    assert r["fma_ms"] > 0 and r["mma_ms"] > 0
+    assert r["maxdiff"] < 1e-4
 
 
 def test_walk_lists_grow_after_an_overflow(g, orc):
