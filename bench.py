@@ -49,6 +49,7 @@ def parse(argv=None):
                          "served at 0.8 of capacity (Poisson arrivals); active: forces for the innermost "
                          "N_a of a Plummer sphere of 1e7 (Sec. 7.1), N_a = 1e3..1e7")
     ap.add_argument("--requests", type=int, default=384, help="serve: requests in the open-loop run")
+    ap.add_argument("--slots", type=int, default=2, help="serve: concurrent slots of the request loop")
     ap.add_argument("--autotune", action="store_true",
                     help="choose (p, eps, leaf, p2p_c) for rms 1e-7 on the workload first (untimed)")
     ap.add_argument("--no-configs", action="store_true",
@@ -241,7 +242,9 @@ def reference_arm(a, rank, world):
 # DRAM bytes (read + write) per launch of the dominant kernels, from one ncu capture of
 # the same workload and parameters (summaries and commands under profiles/); None for
 # any other configuration or once the kernel has changed since the capture
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("plummer", 1000000, 14, 2.3e-7, 80, 1.0, "mixed"): {"k_p2p_mixed": 74.05e6, "k_m2l_rot": 204.41e6},
+}
 
 
 def roofline(g, a, prec, phase, full):
@@ -445,7 +448,8 @@ def serve_record(a, g, dev, local, rank, world, prec, nreq, warmup, cap_rounds):
     dp = [torch.empty(n, dtype=torch.float64, device=dev) for n in sizes]
     da = [torch.empty((n, 3), dtype=torch.float64, device=dev) for n in sizes]
     ctx = g.Context(p=p, eps=eps, leaf_size=leaf, p2p_c=c, precision=prec, device=local)
-    ctx.fmm_serve_config(0, 2)
+    slots = getattr(a, "slots", 2)
+    ctx.fmm_serve_config(0, slots)
     ids = [ctx.fmm_system_register(int(n)) for n in sizes]
     torch.cuda.synchronize(dev)
 
@@ -510,7 +514,7 @@ def serve_record(a, g, dev, local, rank, world, prec, nreq, warmup, cap_rounds):
     value = sum_over_ranks(done_n, world, dev) / max_over_ranks(elapsed, world, dev)
     rec = {"workload": "serve64_plummer_cusp", "value": value, "unit": UNIT, "systems": len(sizes),
            "n_total": int(sizes.sum()), "n_range": [int(sizes.min()), int(sizes.max())], "p": p, "eps": eps,
-           "leaf_size": leaf, "p2p_c": c, "slots": 2, "requests": nreq, "load": 0.8,
+           "leaf_size": leaf, "p2p_c": c, "slots": slots, "requests": nreq, "load": 0.8,
            "capacity_pf_s": capacity, "closed_loop_ms": 1e3 * t_cap,
            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
                           "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
@@ -528,7 +532,7 @@ def run_serve(a, g, dev, local, rank, world, prec):
         cfg.update({"model": "32 truncated Plummer spheres + 32 gamma=1.5 cusps with 1% central point mass, "
                              "N log-uniform in [1e4, 2e6]", "mac": "18a (low-order a estimate)",
                     "precision": a.precision, "l2": "inputs larger than L2 (19M particles resident)",
-                    "parallelism": "2 slots with continuous batching; replicas across GPUs"})
+                    "parallelism": f"{rec['slots']} slots with continuous batching; replicas across GPUs"})
         for k in ("value", "unit"):
             cfg.pop(k)
         line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": a.requests,
@@ -669,10 +673,10 @@ def cusp_record(a, g, dev, local, rank, prec, steps, warmup):
 def crossover(g, dev, local, prec, flush):
     """Sec. 6.4's comparison with direct summation: the mixed FMM against the GPU FP64 direct
     sum for N = 1e4 .. 1e6 (Plummer spheres of the default generator).  At every N the FMM's
-    eps is set by the autotuner's secant steps so that the rms relative error over up to 32768
-    sinks (all of them for N <= 32768) is at most 1e-7 (p = 14, p2p_c = 1; leaf 48 below
-    N = 3e5, 80 from there on); the direct sum runs over all sinks up to N = 1e5 and over
-    32768 sampled sinks above (scaled to N)."""
+    eps is set by the autotuner's secant steps so that the rms relative error is at most 1e-7
+    over all sinks up to N = 1e5 and over 32768 sampled sinks above (p = 14, p2p_c = 1; leaf 48
+    below N = 3e5, 80 from there on); the direct sum runs over the same sinks (its time scaled
+    to N sinks)."""
     import torch
     from paper_1405_2255_gb300 import autotune, inputs
     stream = torch.cuda.current_stream(dev)
@@ -681,16 +685,19 @@ def crossover(g, dev, local, prec, flush):
         x, mu = inputs.plummer(n, inputs.BASE_SEED + 2)
         xt, mt = torch.from_numpy(x).to(dev), torch.from_numpy(mu).to(dev)
         p, eps, leaf, c = PARAMS["ensemble"] if n < 300_000 else PARAMS["plummer"]
-        tr = autotune.tune(xt, mt, target_rms=1e-7, ps=(p,), leaves=(leaf,), cs=(c,), nsinks=min(n, 32768),
+        # the tuner's truth sample (all sinks up to N = 1e5, else 32768 drawn with seed 0) is also
+        # the sample the row's rms is checked on
+        ntr = n if n <= 100_000 else 32768
+        tr = autotune.tune(xt, mt, target_rms=1e-7, ps=(p,), leaves=(leaf,), cs=(c,), nsinks=ntr,
                            precision=prec, eps0=eps, margin=0.95)
         eps = tr.best.eps
         ctx = g.Context(p=p, eps=eps, leaf_size=leaf, p2p_c=c, precision=prec, device=local)
         psi = torch.empty(n, dtype=torch.float64, device=dev)
         acc = torch.empty((n, 3), dtype=torch.float64, device=dev)
         ms = event_ms(lambda: ctx.fmm_evaluate(xt, mt, 1.0, psi=psi, acc=acc), stream, 3, 5, flush)
-        ns = n if n <= 100_000 else 32768
+        ns = ntr
         sinks = None if ns == n else torch.from_numpy(
-            np.sort(np.random.default_rng(n).choice(n, ns, replace=False)).astype(np.int64)).to(dev)
+            np.sort(np.random.default_rng(0).choice(n, ns, replace=False)).astype(np.int64)).to(dev)
         ms_d = event_ms(lambda: ctx.fmm_direct(xt, mt, 1.0, sinks=sinks), stream, 1, 3)
         _, acc_t = ctx.fmm_direct(xt, mt, 1.0, sinks=sinks)
         idx = torch.arange(n, device=dev) if sinks is None else sinks
