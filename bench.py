@@ -268,10 +268,14 @@ def roofline(g, a, prec, phase, full):
         kern = "k_p2p_mixed (eq. 1, FP32 two-float)" if mixed else "k_p2p_fp64 (eq. 1)"
     key = (a.workload, a.n, a.p, a.eps, a.leaf, a.c, a.precision)
     traffic = MEASURED_TRAFFIC.get(key, {}).get(kern.split(" ")[0])
+    pair_ceiling = 20.0 * g.fmm_pair_peak(20) / 1e3 if mixed else None  # TFLOP/s, 20 flops per pair
     return {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
             "frac": achieved / pk, "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
             "peak_source": src,
             "peak_loop_measured": loop, "frac_of_loop": achieved / loop,
+            "pair_arithmetic_ceiling": pair_ceiling,
+            "pair_arithmetic_ceiling_note": "the P2P pair arithmetic alone (fmm_pair_peak, 20 warps per SM): "
+                                            "13 FP32 operations and one rsqrt per pair, no staging",
             "phase_share": {"m2l": t_m2l / (float(np.mean([s["t_total"] for s in phase])) * 1e-3),
                             "p2p": t_p2p / (float(np.mean([s["t_total"] for s in phase])) * 1e-3)}}
 

@@ -983,6 +983,8 @@ int fmm_alu_peaks(double* fp64_tflops, double* fp32_tflops) {
     return alu_peaks(fp64_tflops, fp32_tflops);
 }
 
+int fmm_pair_peak(int warps_per_sm, double* gpairs_s) { return pair_peak(warps_per_sm, gpairs_s); }
+
 int fmm_swap_probe(int npairs, int reps, double* ms, double* maxdiff) {
     return swap_probe(npairs, reps, ms, maxdiff);
 }

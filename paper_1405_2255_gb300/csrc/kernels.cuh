@@ -275,6 +275,8 @@ void launch_active_flags(const unsigned char* active, const int* perm, int n, co
 
 // ---------------------------------------------------------------- peaks (peaks.cu)
 int alu_peaks(double* fp64_tflops, double* fp32_tflops);
+// the mixed P2P's pair arithmetic alone (peaks.cu), in 10^9 pairs per second
+int pair_peak(int warps_per_sm, double* gpairs_s);
 // the swap stage of the rotated M2L at p = 14 as FMA immediates and as 3xTF32 mma.sync
 // (swap_probe.cu); ms[0], ms[1] their kernel times, *maxdiff the largest difference
 int swap_probe(int npairs, int reps, double* ms, double* maxdiff);

@@ -235,70 +235,101 @@ __global__ void k_p2p_nitems(const uint64_t* __restrict__ keys, const int* __res
     if (my) atomicAdd(&tot[1], my);
 }
 
-// Walks the sources of leaf B (its own segment, then each ancestor's) and merges them into
-// ranges per class; emit(near, first, count, guard) receives every finished range in order.
-template <class Emit>
-__device__ void p2p_ranges_of(const Cells& c, const int2* __restrict__ list, const int* __restrict__ seg_start,
-                              const int* __restrict__ seg_end, int leaf, int mode, int lane, Emit emit) {
-    const d4 sb = c.sr[leaf];
-    const long long b0 = c.first[leaf], b1 = b0 + c.count[leaf];
-    auto overlaps = [&](long long f, long long m) { return f < b1 && b0 < f + m; };
-    int cf[2] = {0, 0}, cn[2] = {0, 0};
-    bool cg[2] = {false, false};
-    for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
-        const int s0 = seg_start[cell], s1 = seg_end[cell];
-        for (int e0 = s0; e0 < s1; e0 += 32) {
-            int af = 0, an = 0, kk = 0;
-            if (e0 + lane < s1) {
-                const int A = list[e0 + lane].x;
-                af = c.first[A];
-                an = c.count[A];
-                kk = mode == 1 ? (p2p_near(c.sr[A], sb) ? 1 : 0) : (mode == 3 ? 1 : 0);
-            }
-            const int m = min(32, s1 - e0);
-            for (int q = 0; q < m; ++q) {
-                const int f = __shfl_sync(0xffffffffu, af, q), n = __shfl_sync(0xffffffffu, an, q);
-                const int k = __shfl_sync(0xffffffffu, kk, q);
-                if (n <= 0) continue;
-                if (cn[k] > 0 && cf[k] + cn[k] == f && (long long)cn[k] + n <= kRangeMax) {
-                    cn[k] += n;
-                    cg[k] = cg[k] || overlaps(f, n);
-                    continue;
-                }
-                if (cn[k] > 0) emit(k, cf[k], cn[k], cg[k]);
-                cf[k] = f;
-                cn[k] = n;
-                cg[k] = overlaps(f, n);
-            }
-        }
-    }
-    for (int k = 1; k >= 0; --k)
-        if (cn[k] > 0) emit(k, cf[k], cn[k], cg[k]);
-}
-
-__global__ void k_p2p_emit(Cells c, const int2* __restrict__ list, const int* __restrict__ seg_start,
-                           const int* __restrict__ seg_end, const int* __restrict__ leaves, int nleaves, int mode,
-                           const int* __restrict__ order, const int* __restrict__ roff, const int* __restrict__ nb,
-                           int* __restrict__ nnear, int* __restrict__ nfar, const int* __restrict__ ioff,
-                           const int* __restrict__ nit, int2* __restrict__ ranges, int2* __restrict__ items) {
-    const int lane = threadIdx.x & 31;
+// ranges of leaf index t into its region [roff[t], roff[t] + nb[t]): near ones from the front,
+// far ones from the back (in reverse order), their numbers into nnear[t], nfar[t]; items
+// (t, chunk) of sorted position q.  One warp per position.  The sources (the leaf's own
+// segment, then each ancestor's) are merged per class in stream order: an entry joins the open
+// range of its class when its particles follow that range's directly.  The lanes take 32 entries
+// at a time; each finds its class predecessor (the closest lower lane of its class, else the
+// open range carried from the earlier entries), the entries that do not join start a run, a
+// run's count and guard flag are summed in shared memory, and every run but the last of its
+// class is written out; the last stays open.  This is the result of the sequential pass.
+constexpr int kEmitWarps = 4;
+__global__ void __launch_bounds__(kEmitWarps * 32)
+    k_p2p_emit(Cells c, const int2* __restrict__ list, const int* __restrict__ seg_start,
+               const int* __restrict__ seg_end, const int* __restrict__ leaves, int nleaves, int mode,
+               const int* __restrict__ order, const int* __restrict__ roff, const int* __restrict__ nb,
+               int* __restrict__ nnear, int* __restrict__ nfar, const int* __restrict__ ioff,
+               const int* __restrict__ nit, int2* __restrict__ ranges, int2* __restrict__ items) {
+    __shared__ int rsum_all[kEmitWarps][33], rg_all[kEmitWarps][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int* rsum = rsum_all[wid];  // [0]: the open range carried in; [1 + L]: the run starting at lane L
+    int* rg = rg_all[wid];
+    const unsigned below = (1u << lane) - 1u, upto = below | (1u << lane);
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nleaves; q += nw) {
         const int t = order[q];
         for (int j = lane; j < nit[q]; j += 32) items[ioff[q] + j] = make_int2(t, j);
         const int leaf = leaves[t];
+        const d4 sb = c.sr[leaf];
+        const long long b0 = c.first[leaf], b1 = b0 + c.count[leaf];
         const int r0 = roff[t], r1 = r0 + nb[t];
-        int cnt[2] = {0, 0};
-        p2p_ranges_of(c, list, seg_start, seg_end, leaf, mode, lane,
-                      [&](int k, int f, int m, bool g) {
-                          const int pos = k ? r0 + cnt[1] : r1 - 1 - cnt[0];
-                          if (lane == 0) ranges[pos] = make_int2(f, m | (k << 30) | ((g ? 1 : 0) << kRangeCountBits));
-                          ++cnt[k];
-                      });
+        int cf[2] = {0, 0}, cn[2] = {0, 0}, cnt[2] = {0, 0};  // open range and records written per class
+        bool cg[2] = {false, false};
+        auto put = [&](int k, int idx, int f, int n, bool g) {
+            ranges[k ? r0 + idx : r1 - 1 - idx] = make_int2(f, n | (k << 30) | ((g ? 1 : 0) << kRangeCountBits));
+        };
+        for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
+            const int s0 = seg_start[cell], s1 = seg_end[cell];
+            for (int e0 = s0; e0 < s1; e0 += 32) {
+                int f = 0, n = 0, kk = -1;
+                if (e0 + lane < s1) {
+                    const int A = list[e0 + lane].x;
+                    f = c.first[A];
+                    n = c.count[A];
+                    kk = mode == 1 ? (p2p_near(c.sr[A], sb) ? 1 : 0) : (mode == 3 ? 1 : 0);
+                    if (n <= 0) kk = -1;
+                }
+                const bool g = kk >= 0 && f < b1 && b0 < (long long)f + n;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const unsigned M = __ballot_sync(0xffffffffu, kk == k);
+                    if (!M) continue;
+                    const unsigned pm = M & below;
+                    const int P = pm ? 31 - __clz(pm) : lane;
+                    const int pf = __shfl_sync(0xffffffffu, f, P), pn = __shfl_sync(0xffffffffu, n, P);
+                    const long long pe = pm ? (long long)pf + pn : (cn[k] > 0 ? (long long)cf[k] + cn[k] : -1);
+                    const bool mine = kk == k;
+                    const unsigned S = __ballot_sync(0xffffffffu, mine && pe != f);
+                    const unsigned sm = S & upto;
+                    const int rs = sm ? 31 - __clz(sm) : -1;  // the run this lane belongs to
+                    rsum[lane] = 0;
+                    rg[lane] = 0;
+                    if (lane == 0) rsum[32] = rg[32] = 0;
+                    __syncwarp();
+                    if (mine) {
+                        atomicAdd(&rsum[rs + 1], n);
+                        if (g) atomicOr(&rg[rs + 1], 1);
+                    }
+                    __syncwarp();
+                    if (!S) {  // every entry joins the open range
+                        cn[k] += rsum[0];
+                        cg[k] = cg[k] || rg[0];
+                    } else {
+                        int base = cnt[k];
+                        if (cn[k] > 0) {  // the open range closes at the first start
+                            if (lane == 0) put(k, base, cf[k], cn[k] + rsum[0], cg[k] || rg[0]);
+                            ++base;
+                        }
+                        const int last = 31 - __clz(S);
+                        if (((S >> lane) & 1) && lane != last)
+                            put(k, base + __popc(S & below), f, rsum[lane + 1], rg[lane + 1] != 0);
+                        cnt[k] = base + __popc(S) - 1;
+                        cf[k] = __shfl_sync(0xffffffffu, f, last);
+                        cn[k] = rsum[last + 1];
+                        cg[k] = rg[last + 1] != 0;
+                    }
+                    __syncwarp();
+                }
+            }
+        }
         if (lane == 0) {
+            for (int k = 1; k >= 0; --k)
+                if (cn[k] > 0) put(k, cnt[k]++, cf[k], cn[k], cg[k]);
             nnear[t] = cnt[1];
             nfar[t] = cnt[0];
         }
+        __syncwarp();
     }
 }
 
@@ -569,8 +600,8 @@ size_t launch_p2p_mixed(const float* hi, const float* lo, int n, Cells c, const 
     if (tmp_bytes < need) return need;
     int2* ranges = (int2*)((unsigned char*)tmp + L.bytes);
     int2* items = (int2*)((unsigned char*)ranges + ((nranges * sizeof(int2) + 255) & ~255ull));
-    const unsigned g = grid_for((long long)nleaves * 32, 128, 16);  // one warp per leaf
-    k_p2p_emit<<<g, 128, 0, s>>>(c, list, seg_start, seg_end, leaves, nleaves, mode, L.order, L.roff, L.nb, L.nnear,
+    const unsigned g = grid_for((long long)nleaves * 32, kEmitWarps * 32, 16);  // one warp per leaf
+    k_p2p_emit<<<g, kEmitWarps * 32, 0, s>>>(c, list, seg_start, seg_end, leaves, nleaves, mode, L.order, L.roff, L.nb, L.nnear,
                                  L.nfar, L.ioff, L.nit, ranges, items);
     note_launch();
     if (nitems == 0) return need;

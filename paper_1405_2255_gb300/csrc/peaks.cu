@@ -71,4 +71,107 @@ int alu_peaks(double* fp64_tflops, double* fp32_tflops) {
     return 0;
 }
 
+// The pair arithmetic of the mixed P2P alone (its far form: dx from FP32 offsets, packed f32x2
+// operations, rsqrt.approx.ftz), sources from a shared-memory table, one sink per lane, no tile
+// staging, list walking or idle lanes: the rate the P2P kernel's arithmetic can reach on this
+// device.  Gpairs/s over iters passes of 1024 sources per thread.
+typedef unsigned long long pf2;
+__device__ __forceinline__ pf2 pp_pack(float a, float b) {
+    pf2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void pp_unpack(pf2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ pf2 pp_sub(pf2 a, pf2 b) {
+    pf2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ pf2 pp_add(pf2 a, pf2 b) {
+    pf2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ pf2 pp_mul(pf2 a, pf2 b) {
+    pf2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ pf2 pp_fma(pf2 a, pf2 b, pf2 c) {
+    pf2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+__global__ void __launch_bounds__(128) k_peak_pairs(float* out, int iters) {
+    __shared__ float4 src[4][256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        src[0][i] = make_float4(i * 1e-3f, 1 + i * 1e-3f, 2 + i * 1e-3f, 3 + i * 1e-3f);
+        src[1][i] = src[0][i];
+        src[2][i] = src[0][i];
+        src[3][i] = make_float4(1e-6f, 1e-6f, 1e-6f, 1e-6f);
+    }
+    __syncthreads();
+    const float bx = threadIdx.x * 0.01f + 0.5f, by = 0.3f, bz = -0.2f;
+    const pf2 hx = pp_pack(bx, bx), hy = pp_pack(by, by), hz = pp_pack(bz, bz);
+    pf2 ps = 0, ax = 0, ay = 0, az = 0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll 2
+        for (int g = 0; g < 256; ++g) {
+            const ulonglong2 X = ((const ulonglong2*)src[0])[g], Y = ((const ulonglong2*)src[1])[g],
+                             Z = ((const ulonglong2*)src[2])[g], W = ((const ulonglong2*)src[3])[g];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const pf2 dx = pp_sub(h ? X.y : X.x, hx), dy = pp_sub(h ? Y.y : Y.x, hy), dz = pp_sub(h ? Z.y : Z.x, hz);
+                const pf2 r2 = pp_fma(dx, dx, pp_fma(dy, dy, pp_mul(dz, dz)));
+                float a, b;
+                pp_unpack(r2, a, b);
+                const pf2 ri = pp_pack(rsqrt_ftz(a), rsqrt_ftz(b));
+                const pf2 qm = pp_mul(h ? W.y : W.x, ri), q3 = pp_mul(qm, pp_mul(ri, ri));
+                ps = pp_add(ps, qm);
+                ax = pp_fma(q3, dx, ax);
+                ay = pp_fma(q3, dy, ay);
+                az = pp_fma(q3, dz, az);
+            }
+        }
+    }
+    float a, b, s = 0.f;
+    pp_unpack(ps, a, b); s += a + b;
+    pp_unpack(ax, a, b); s += a + b;
+    pp_unpack(ay, a, b); s += a + b;
+    pp_unpack(az, a, b); s += a + b;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+int pair_peak(int warps_per_sm, double* gpairs_s) {
+    if (warps_per_sm < 4 || warps_per_sm > 32 || !gpairs_s) return FMM_E_INVALID;
+    int dev, nsm;
+    GB3_CUDA_TRY(cudaGetDevice(&dev));
+    GB3_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 128, blocks = nsm * warps_per_sm / 4, iters = 64;
+    float* d = nullptr;
+    GB3_CUDA_TRY(cudaMalloc(&d, (size_t)threads * blocks * sizeof(float)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f, ms = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0);
+        k_peak_pairs<<<blocks, threads>>>(d, iters);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaError_t err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d);
+    if (err != cudaSuccess) return cuda_fail(err, "pair probe", __FILE__, __LINE__);
+    *gpairs_s = (double)blocks * threads * iters * 1024.0 / (best * 1e-3) / 1e9;
+    return 0;
+}
+
 }  // namespace gb3

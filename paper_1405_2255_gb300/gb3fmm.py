@@ -51,7 +51,7 @@ EXPORTS = ["fmm_default_params", "fmm_create", "fmm_set_params", "fmm_evaluate",
            "fmm_strerror", "fmm_last_error", "fmm_version", "fmm_alu_peaks", "fmm_evaluate_noalloc",
            "fmm_serve_config", "fmm_footprint_bytes", "fmm_system_register", "fmm_submit", "fmm_poll",
            "fmm_system_release", "fmm_workspace_bytes", "fmm_swap_matrix",
-           "fmm_evaluate_active", "fmm_debug_m2l_orders", "fmm_swap_probe"]
+           "fmm_evaluate_active", "fmm_debug_m2l_orders", "fmm_swap_probe", "fmm_pair_peak"]
 
 _lib = None
 
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
     L.fmm_swap_matrix.argtypes = [ci, vp]
     L.fmm_debug_m2l_orders.argtypes = [vp, vp]
     L.fmm_swap_probe.argtypes = [ci, ci, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.fmm_pair_peak.argtypes = [ci, C.POINTER(C.c_double)]
     L.fmm_evaluate_active.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, ci, vp, vp, vp, vp, C.POINTER(fmm_stats)]
     for name in EXPORTS:
         if name not in ("fmm_strerror", "fmm_last_error", "fmm_version", "fmm_default_params",
@@ -355,6 +356,13 @@ def fmm_alu_peaks() -> tuple[float, float]:
     a, b = C.c_double(), C.c_double()
     _check(load().fmm_alu_peaks(C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def fmm_pair_peak(warps_per_sm: int = 20) -> float:
+    """The mixed P2P's pair arithmetic alone, in 10^9 pairs per second."""
+    v = C.c_double()
+    _check(load().fmm_pair_peak(int(warps_per_sm), C.byref(v)))
+    return v.value
 
 
 def fmm_swap_probe(npairs: int = 1 << 20, reps: int = 16) -> dict:
