@@ -814,7 +814,7 @@ __device__ void meb_points_mtf_warp(float (*L)[3], int n, float c[3], float& rad
 
 // one warp per leaf: smallest enclosing ball, exact radius, mass, centre of mass
 constexpr int kGeoWarps = 4;
-__global__ void __maxnreg__(168) k_leaf_geometry(const d4* __restrict__ xm, Cells c,
+__global__ void __maxnreg__(128) k_leaf_geometry(const d4* __restrict__ xm, Cells c,
                                                                  const int* __restrict__ leaves, int nleaves,
                                                                  unsigned* status, bool keep_centre) {
     __shared__ float pbuf[kGeoWarps][kMebBuf][3];
