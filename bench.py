@@ -249,29 +249,40 @@ MEASURED_TRAFFIC = {
 
 def roofline(g, a, prec, phase, full):
     """Achieved vs peak of the dominant kernel: algorithmic flops of the run's own lists
-    over its CUDA-event phase time averaged over the timed steps."""
+    over that kernel's own launch duration (CUDA events recorded around the launch on its
+    stream) averaged over the timed steps; also over its whole phase (list sort, work plan,
+    reduction and kernel)."""
     t_m2l = float(np.mean([s["t_m2l"] for s in phase])) * 1e-3
     t_p2p = float(np.mean([s["t_p2p"] for s in phase])) * 1e-3
+    k_m2l = float(np.mean([s["t_m2l_kernel"] for s in phase])) * 1e-3
+    k_p2p = float(np.mean([s["t_p2p_kernel"] for s in phase])) * 1e-3
+    if k_m2l <= 0.0 or k_p2p <= 0.0:  # a path without the marked kernels: the phases
+        k_m2l, k_p2p = t_m2l, t_p2p
     loop64, loop32 = g.fmm_alu_peaks()
     mixed = prec == g.FMM_PREC_MIXED
     p32, sms, mhz = fp32_peak()
     pk, loop = (p32, loop32) if mixed else (FP64_PEAK_TFLOPS, loop64)
     src = (f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz" if mixed
            else "nominal FP64 rate of the part (1.25 TFLOP/s)")
-    if t_m2l >= t_p2p:
+    if k_m2l >= k_p2p:
         rot = mixed and 3 <= a.p <= 16
-        achieved = full["n_m2l"] * (m2l_rot_flops(a.p) if rot else m2l_flops(a.p)) / t_m2l / 1e12
+        work = full["n_m2l"] * (m2l_rot_flops(a.p) if rot else m2l_flops(a.p))
+        t_k, t_ph = k_m2l, t_m2l
         kern = ("k_m2l_rot (App. A.5 rotations and eq. A31, orders > 2 in FP32)" if rot
                 else "k_m2l_rounds (eq. 3b, orders > 2 in FP32)" if mixed else "k_m2l (eq. 3b, FP64)")
     else:
-        achieved = 20.0 * full["p2p_interactions"] / t_p2p / 1e12
+        work = 20.0 * full["p2p_interactions"]
+        t_k, t_ph = k_p2p, t_p2p
         kern = "k_p2p_mixed (eq. 1, FP32 two-float)" if mixed else "k_p2p_fp64 (eq. 1)"
+    achieved = work / t_k / 1e12
     key = (a.workload, a.n, a.p, a.eps, a.leaf, a.c, a.precision)
     traffic = MEASURED_TRAFFIC.get(key, {}).get(kern.split(" ")[0])
     pair_ceiling = 20.0 * g.fmm_pair_peak(20) / 1e3 if mixed else None  # TFLOP/s, 20 flops per pair
     return {"kernel": kern, "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
             "frac": achieved / pk, "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
             "peak_source": src,
+            "kernel_ms": 1e3 * t_k, "timing": "CUDA events around the kernel's launches, mean over the timed steps",
+            "phase_ms": 1e3 * t_ph, "achieved_phase": work / t_ph / 1e12, "frac_phase": work / t_ph / 1e12 / pk,
             "peak_loop_measured": loop, "frac_of_loop": achieved / loop,
             "pair_arithmetic_ceiling": pair_ceiling,
             "pair_arithmetic_ceiling_note": "the P2P pair arithmetic alone (fmm_pair_peak, 20 warps per SM): "
@@ -374,7 +385,7 @@ def ensemble_record(a, g, dev, local, rank, world, prec, steps, warmup, emit_lin
            "rms_rel_err": float(np.sqrt(np.mean(e ** 2))), "p999_rel_err": float(np.percentile(e, 99.9)),
            "err_sinks": int(len(e)), "launches_per_step": launches / steps,
            "phase_ms": {k: float(np.mean([s_[k] for s_ in phase])) for k in
-                        ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total")}}
+                        ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total", "t_m2l_kernel", "t_p2p_kernel")}}
     if not emit_line:
         ctx.close()
         return rec
@@ -605,7 +616,7 @@ def run_active(a, g, dev, local, rank, world, prec):
         e = sampled_error(ctx, xt, mt, acc, idx, dev)
         sweep[na] = {"ms": ms, "rms_rel_err": float(np.sqrt(np.mean(e ** 2))),
                      "phase_ms": {k: float(np.mean([s_[k] for s_ in phase])) for k in
-                                  ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total")},
+                                  ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total", "t_m2l_kernel", "t_p2p_kernel")},
                      "n_m2l": int(phase[-1]["n_m2l"]), "n_p2p": int(phase[-1]["n_p2p"]),
                      "reused_tree_ms": ms_r, "reused_tree_t_tree": float(np.mean([s_["t_tree"] for s_ in phase_r]))}
         if na == a.n // 100:
@@ -911,7 +922,7 @@ def main():
         cfg.update({"rms_rel_err": rms, "p999_rel_err": p999, "err_sinks": int(ns),
                     "err_truth": "GPU FP64 direct sum over all sources for a seeded sample of sinks",
                     "phase_ms": {k: float(np.mean([s[k] for s in phase])) for k in
-                                 ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total")},
+                                 ("t_tree", "t_estimate", "t_up", "t_walk", "t_m2l", "t_p2p", "t_down", "t_total", "t_m2l_kernel", "t_p2p_kernel")},
                     "n_m2l": int(full["n_m2l"]), "n_p2p": int(full["n_p2p"]),
                     "p2p_interactions": int(full["p2p_interactions"]), "ncells": int(full["ncells"])})
         line = {

@@ -112,6 +112,11 @@ typedef struct {
     float   t_tree, t_estimate, t_up, t_walk, t_m2l, t_p2p, t_down, t_total;
     /* number of kernels the library launched for the evaluation */
     int64_t launches;
+    /* device time in milliseconds of the main M2L kernel(s) of the rotated precision-split
+       path and of the main mixed-precision P2P kernel alone (CUDA events recorded right
+       before and after the launch; the phases above also hold their list sorts, work
+       plans and reductions); 0 where that kernel did not run */
+    float   t_m2l_kernel, t_p2p_kernel;
 } fmm_stats;
 
 typedef struct fmm_ctx fmm_ctx;

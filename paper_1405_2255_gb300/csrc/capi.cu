@@ -56,7 +56,7 @@ T* P(Buf& b) {
     return (T*)b.p;
 }
 
-enum { EV_START, EV_TREE, EV_EST, EV_UP, EV_WALK, EV_M2L, EV_P2P, EV_DOWN, EV_END, EV_N };
+enum { EV_START, EV_TREE, EV_EST, EV_UP, EV_WALK, EV_M2L, EV_P2P, EV_DOWN, EV_END, EV_M2LK0, EV_M2LK1, EV_P2PK0, EV_P2PK1, EV_N };
 
 }  // namespace
 
@@ -69,7 +69,7 @@ struct fmm_ctx {
     Buf hx, hmu, hpsi, hacc;
     // particles and sort
     Buf bounds, status, counters, coin, dtotal;
-    Buf keys, keys_alt, idx, idx_alt, rtmp, xm, perm, xhi, xlo;
+    Buf keys, keys_alt, idx, idx_alt, rtmp, xm, perm, xp;
     // cells
     Buf first, count, child, nchild, parent, level, sr, cr, mass, minscale;
     Buf split_nchild, split_oct, split_offs, scan_tmp, leaves, leaf_flag, leaf_pos, rad_tmp, owner;
@@ -87,6 +87,7 @@ struct fmm_ctx {
     cudaEvent_t ev[EV_N];
     bool ev_ok = false;
     bool timed = false;  // the events of the last evaluation were recorded
+    bool marked_m2l = false, marked_p2p = false;  // ... and those around its main kernels
     gb3::Serve* serve = nullptr;  // the serving loop (serve.cu), created on first use
     // ensemble of the current evaluation (nsys = 0: one system): system offsets and G
     // on the device, roots (first, count) of the non-empty systems
@@ -101,7 +102,7 @@ struct fmm_ctx {
     int tree_n = -1;
     std::vector<Buf*> bufs() {
         return {&hx, &hmu, &hpsi, &hacc, &bounds, &status, &counters, &coin, &dtotal, &keys, &keys_alt, &idx,
-                &idx_alt, &rtmp, &xm, &perm, &xhi, &xlo, &first, &count, &child, &nchild, &parent, &level, &sr,
+                &idx_alt, &rtmp, &xm, &perm, &xp, &first, &count, &child, &nchild, &parent, &level, &sr,
                 &cr, &mass, &minscale, &split_nchild, &split_oct, &split_offs, &scan_tmp, &leaves, &leaf_flag,
                 &leaf_pos, &rad_tmp, &M, &F, &Pw, &binom, &pascal, &M1, &F1, &Ff, &front0, &front1, &m2l, &p2p,
                 &sort_tmp, &m2l_tmp, &p2p_tmp, &seg_start, &seg_end, &est_m2l, &est_p2p, &m2l_seg_start,
@@ -200,12 +201,11 @@ __global__ void k_leaf_compact(const int* __restrict__ flag, const int* __restri
         if (flag[i]) leaves[pos[i]] = i;
 }
 
-// the two-float copies of the sorted positions and masses (the internal radii's
+// the two-float records of the sorted positions and masses (the internal radii's
 // single-precision bounds, the mixed-mode kernels)
 static int split_positions(fmm_ctx* ctx, int n, cudaStream_t s) {
-    TRY(ensure(ctx->xhi, sizeof(float4) * (size_t)n));
-    TRY(ensure(ctx->xlo, sizeof(float4) * (size_t)n));
-    launch_split_positions(P<d4>(ctx->xm), n, P<float>(ctx->xhi), P<float>(ctx->xlo), s);
+    TRY(ensure(ctx->xp, 2 * sizeof(float4) * (size_t)n));
+    launch_split_positions(P<d4>(ctx->xm), n, P<float4>(ctx->xp), s);
     return 0;
 }
 
@@ -228,7 +228,7 @@ static int refresh_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, 
     launch_leaf_geometry(P<d4>(ctx->xm), c, P<int>(ctx->leaves), ctx->nleaves, P<unsigned>(ctx->status), s, true);
     launch_leaf_owner(c, P<int>(ctx->leaves), ctx->nleaves, P<int>(ctx->owner), s);
     for (int L = nlev - 1; L >= 0; --L)
-        launch_internal_geometry(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), c, ctx->lev_start[L],
+        launch_internal_geometry(P<d4>(ctx->xm), P<float4>(ctx->xp), c, ctx->lev_start[L],
                                  ctx->lev_start[L + 1], n, P<int>(ctx->owner), P<unsigned long long>(ctx->rad_tmp),
                                  P<unsigned>(ctx->status), s, true);
     return 0;
@@ -333,7 +333,7 @@ static int build_tree(fmm_ctx* ctx, int n, const double* x, const double* mu, cu
     launch_leaf_geometry(P<d4>(ctx->xm), c, P<int>(ctx->leaves), ctx->nleaves, P<unsigned>(ctx->status), s);
     launch_leaf_owner(c, P<int>(ctx->leaves), ctx->nleaves, P<int>(ctx->owner), s);
     for (int L = nlev - 1; L >= 0; --L)
-        launch_internal_geometry(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), c, ctx->lev_start[L],
+        launch_internal_geometry(P<d4>(ctx->xm), P<float4>(ctx->xp), c, ctx->lev_start[L],
                                  ctx->lev_start[L + 1], n, P<int>(ctx->owner), P<unsigned long long>(ctx->rad_tmp),
                                  P<unsigned>(ctx->status), s);
     return 0;
@@ -418,7 +418,7 @@ static int run_p2p_mixed(fmm_ctx* ctx, const int2* list, int mode, cudaStream_t 
     Cells c = cells_of(ctx);
     TRY(ensure(ctx->p2p_tmp, p2p_plan_fixed_bytes(ctx->nleaves)));
     for (int attempt = 0; attempt < 2; ++attempt) {
-        const size_t need = launch_p2p_mixed(P<float>(ctx->xhi), P<float>(ctx->xlo), ctx->n, c, list,
+        const size_t need = launch_p2p_mixed(P<float4>(ctx->xp), ctx->n, c, list,
                                              P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves),
                                              ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), mode,
                                              ctx->p2p_tmp.p, ctx->p2p_tmp.bytes, ctx->h_counters + 6, s);
@@ -496,6 +496,17 @@ static int phase_times(fmm_ctx* ctx) {
     ctx->last.t_p2p = el(EV_M2L, EV_P2P);
     ctx->last.t_down = el(EV_P2P, EV_DOWN);
     ctx->last.t_total = el(EV_START, EV_END);
+    // the main kernels' own times; 0 when the kernel did not run (no marks recorded)
+    auto kel = [&](int a, int b) {
+        float k = 0.f;
+        if (cudaEventElapsedTime(&k, ctx->ev[a], ctx->ev[b]) != cudaSuccess) {
+            cudaGetLastError();
+            k = 0.f;
+        }
+        return k;
+    };
+    ctx->last.t_m2l_kernel = ctx->marked_m2l ? kel(EV_M2LK0, EV_M2LK1) : 0.f;
+    ctx->last.t_p2p_kernel = ctx->marked_p2p ? kel(EV_P2PK0, EV_P2PK1) : 0.f;
     return 0;
 }
 
@@ -529,6 +540,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     const bool timing = ctx->ev_ok;
     const long long launches0 = launches_so_far();
     ctx->timed = false;
+    ctx->marked_m2l = ctx->marked_p2p = false;
     if (timing) CU(cudaEventRecord(ctx->ev[EV_START], s));
     CU(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), s));
     CU(cudaMemsetAsync(ctx->coin.p, 0, sizeof(unsigned long long), s));
@@ -643,6 +655,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     CU(cudaMemsetAsync(ctx->F.p, 0, sizeof(double) * nco * (size_t)nc, s));
     if (split) {
         TRY(ensure(ctx->m2l_tmp, m2l_split_tmp_bytes(nc, prm.p, ctx->n_m2l)));
+        kernel_marks(timing ? &ctx->ev[EV_M2LK0] : nullptr);
         launch_m2l_split(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc,
                          c.sr, P<double>(ctx->M), prm.p, P<double>(ctx->F), prm.m2l_rot != 0, s, wp.adaptive != 0,
                          ctx->n_m2l);
@@ -651,13 +664,19 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         launch_m2l(P<int2>(ctx->m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), ctx->m2l_tmp.p, nc, c.sr,
                    P<double>(ctx->M), prm.p, P<double>(ctx->F), s);
     }
+    ctx->marked_m2l = marks_recorded();
+    kernel_marks(nullptr);
     if (timing) CU(cudaEventRecord(ctx->ev[EV_M2L], s));
 
     // A10: P2P
     TRY(sort_and_segment(ctx, ctx->p2p, ctx->n_p2p, ctx->seg_start, ctx->seg_end, s));
-    if (prm.precision == FMM_PREC_MIXED)
-        TRY(run_p2p_mixed(ctx, P<int2>(ctx->p2p), prm.p2p_two_float, s));
-    else
+    if (prm.precision == FMM_PREC_MIXED) {
+        kernel_marks(timing ? &ctx->ev[EV_P2PK0] : nullptr);
+        const int rc = run_p2p_mixed(ctx, P<int2>(ctx->p2p), prm.p2p_two_float, s);
+        ctx->marked_p2p = marks_recorded();
+        kernel_marks(nullptr);
+        TRY(rc);
+    } else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
                         P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
     const int* sys_off = ctx->nsys ? P<int>(ctx->sys_off) : nullptr;
@@ -665,7 +684,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
                       ctx->nsys);
     if (tidal) {  // Sec. 7.4: the near part over the same sources as the P2P
         TRY(ensure(ctx->tid_near, sizeof(double) * 6 * (size_t)n));
-        launch_p2p_tidal(P<d4>(ctx->xm), P<float>(ctx->xhi), P<float>(ctx->xlo), n, prm.precision == FMM_PREC_MIXED,
+        launch_p2p_tidal(P<d4>(ctx->xm), P<float4>(ctx->xp), n, prm.precision == FMM_PREC_MIXED,
                          c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves),
                          ctx->nleaves, P<double>(ctx->tid_near), s);
     }

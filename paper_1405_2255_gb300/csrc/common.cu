@@ -37,6 +37,20 @@ thread_local long long g_launches = 0;
 void note_launch() { ++g_launches; }
 long long launches_so_far() { return g_launches; }
 
+thread_local cudaEvent_t* g_marks = nullptr;
+thread_local int g_marks_hit = 0;
+void kernel_marks(cudaEvent_t* ev) {
+    g_marks = ev;
+    g_marks_hit = 0;
+}
+void mark_begin(cudaStream_t s) {
+    if (g_marks && cudaEventRecord(g_marks[0], s) == cudaSuccess) g_marks_hit |= 1;
+}
+void mark_end(cudaStream_t s) {
+    if (g_marks && cudaEventRecord(g_marks[1], s) == cudaSuccess) g_marks_hit |= 2;
+}
+bool marks_recorded() { return g_marks_hit == 3; }
+
 // ---------------------------------------------------------------- scan
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;

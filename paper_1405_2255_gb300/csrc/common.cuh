@@ -105,6 +105,14 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 void note_launch();
 long long launches_so_far();
 
+// kernel marks: while a pair of events is set for this host thread, the launchers of the
+// main P2P and M2L kernels record the first event right before the kernel and the second
+// right after it, so that the kernel's own device time can be read; nullptr turns it off
+void kernel_marks(cudaEvent_t* ev);
+void mark_begin(cudaStream_t s);
+void mark_end(cudaStream_t s);
+bool marks_recorded();  // both events were recorded since the last kernel_marks()
+
 // streaming multiprocessors of the current device (queried once per device)
 int sm_count();
 

@@ -828,23 +828,19 @@ void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_sta
 // dx = (hi_a - hi_b) + (lo_a - lo_b) keeps its relative accuracy even for close
 // pairs.  Pair terms are FP32; the FP32 sums of every ~32 pairs are added to
 // two-float accumulators (TwoSum), so the sum over tiles is compensated.
-// Layout (structure of arrays, n floats each): hi = [X | Y | Z | W] (high parts of the
-// position and the mass), lo = [XL | YL | ZL] (low parts).
-__global__ void k_split_positions(const d4* __restrict__ xm, int n, float* __restrict__ hi, float* __restrict__ lo) {
+// Layout: one 32-byte record per particle, xp[2i] = (high parts of the position, mass as
+// FP32), xp[2i + 1] = (low parts, 0), so that a range of particles is one contiguous block.
+__global__ void k_split_positions(const d4* __restrict__ xm, int n, float4* __restrict__ xp) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         d4 v = xm[i];
         const float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
-        hi[i] = hx;
-        hi[n + i] = hy;
-        hi[2 * (size_t)n + i] = hz;
-        hi[3 * (size_t)n + i] = (float)v.w;
-        lo[i] = (float)(v.x - (double)hx);
-        lo[n + i] = (float)(v.y - (double)hy);
-        lo[2 * (size_t)n + i] = (float)(v.z - (double)hz);
+        xp[2 * (size_t)i] = make_float4(hx, hy, hz, (float)v.w);
+        xp[2 * (size_t)i + 1] =
+            make_float4((float)(v.x - (double)hx), (float)(v.y - (double)hy), (float)(v.z - (double)hz), 0.f);
     }
 }
-void launch_split_positions(const d4* xm, int n, float* hi, float* lo, cudaStream_t s) {
-    if (n > 0) k_split_positions<<<grid_for(n, 256), 256, 0, s>>>(xm, n, hi, lo); note_launch();
+void launch_split_positions(const d4* xm, int n, float4* xp, cudaStream_t s) {
+    if (n > 0) k_split_positions<<<grid_for(n, 256), 256, 0, s>>>(xm, n, xp); note_launch();
 }
 
 // number of ordered pairs (a != b) at distance 0: equal positions have equal keys,

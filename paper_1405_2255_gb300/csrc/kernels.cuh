@@ -77,10 +77,10 @@ void launch_split_level(const uint64_t* keys, Cells c, int lev_begin, int lev_en
 // radii, masses and centres of mass for the particles' new positions
 void launch_leaf_geometry(const d4* xm, Cells c, const int* leaves, int nleaves, unsigned* status,
                           cudaStream_t s, bool keep_centre = false);
-// xhi/xlo: the two-float positions (launch_split_positions); owner: per particle, set by
+// xp: the two-float position records (launch_split_positions); owner: per particle, set by
 // launch_leaf_owner before the deepest level and moved up as the levels are processed
 // bottom-up; rad_tmp: rad_tmp_u64_per_cell() words per cell of the largest level
-void launch_internal_geometry(const d4* xm, const float* xhi, const float* xlo, Cells c, int lev_begin, int lev_end,
+void launch_internal_geometry(const d4* xm, const float4* xp, Cells c, int lev_begin, int lev_end,
                               int n, int* owner, unsigned long long* rad_tmp, unsigned* status, cudaStream_t s,
                               bool keep_centre = false);
 void launch_leaf_owner(Cells c, const int* leaves, int nleaves, int* owner, cudaStream_t s);
@@ -222,16 +222,16 @@ void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_sta
 // holds it.  Returns the bytes the call needs: a value above tmp_bytes means nothing was
 // computed (call again with that much), ~0 a plan beyond 2^31 ranges or items or n >= 2^29.
 size_t p2p_plan_fixed_bytes(int nleaves);
-size_t launch_p2p_mixed(const float* hi, const float* lo, int n, Cells c, const int2* list, const int* seg_start,
+size_t launch_p2p_mixed(const float4* xp, int n, Cells c, const int2* list, const int* seg_start,
                         const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc, int mode,
                         void* tmp, size_t tmp_bytes, unsigned long long* h_tot, cudaStream_t s);
 // ordered pairs of distinct particles at distance 0 (sorted keys and positions); with
 // an ensemble (off != nullptr) only pairs inside one system count
 void launch_coincident(const d4* xm, const uint64_t* keys, int n, unsigned long long* coincident, cudaStream_t s,
                        const int* off = nullptr, int nsys = 0);
-// two-float positions in structure-of-arrays form: hi = [X | Y | Z | W] (4n floats),
-// lo = [XL | YL | ZL] (3n floats)
-void launch_split_positions(const d4* xm, int n, float* hi, float* lo, cudaStream_t s);
+// two-float position records, 32 bytes per particle: xp[2i] = (hi x, hi y, hi z, mass),
+// xp[2i + 1] = (lo x, lo y, lo z, 0) with hi = fl32(x) and lo = fl32(x - hi)
+void launch_split_positions(const d4* xm, int n, float4* xp, cudaStream_t s);
 // low-order f estimate (p = 0, 1/r^2 kernel): M2L, pass-down, P2P, evaluation
 void launch_f_m2l(const int2* list, const int* seg_start, const int* seg_end, int ncells, Cells c, double* Ff,
                   cudaStream_t s);
@@ -257,11 +257,11 @@ void launch_finish(const double* psi_far, const double* acc_far, const double* p
 // active particle (from a prefix sum of pact over the cells' particle ranges); ai holds
 // n + 1 ints, scan n ints, scan_tmp scan_tmp_ints(n) ints
 // tidal tensor (Sec. 7.4, tidal.cu): far part from Psi_2^m at the particles (sorted order,
-// [n][6]), near part over the P2P lists (fp32: two-float positions hi/lo), and the
+// [n][6]), near part over the P2P lists (fp32: the two-float position records xp), and the
 // combination G (far + near) scattered to the caller's order (active particles only)
 void launch_l2p_tidal(const d4* xm, Cells c, const d4* cen, const int* leaves, int nleaves, int p, const double* F,
                       double* T, cudaStream_t s);
-void launch_p2p_tidal(const d4* xm, const float* hi, const float* lo, int n, bool fp32, Cells c, const int2* list,
+void launch_p2p_tidal(const d4* xm, const float4* xp, int n, bool fp32, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* T,
                       cudaStream_t s);
 void launch_finish_tidal(const double* Tf, const double* Tn, const int* perm, int n, double G,

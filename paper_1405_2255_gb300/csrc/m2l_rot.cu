@@ -130,7 +130,9 @@ const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg
     if (!adaptive) {
         // every item at p: the whole item range, counted by work[0]; the item count is on the
         // device (work[2]), so the kernel reads it there
+        mark_begin(s);
         launch_p(p, nullptr, nullptr, 0, work, 0);
+        mark_end(s);
         return nullptr;
     }
     // group the items by the largest order of their pairs; each group runs its own kernel
@@ -153,7 +155,9 @@ const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg
     const int flip = radix_sort_pairs_bits(k0, v0, k1, v1, items_cap, rtmp, 32, 40, s);
     k_item_groups<<<grid_for(items_cap, 256), 256, 0, s>>>(qcount, goff, flip ? k1 : k0, work, ilist);
     note_launch();
+    mark_begin(s);
     for (int q = (p < 3 ? p : 3); q <= p; ++q) launch_p(q, ilist, goff, q, ctr + q, 1);
+    mark_end(s);
     return item_q;
 }
 }  // namespace gb3

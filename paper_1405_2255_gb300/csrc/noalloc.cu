@@ -164,11 +164,11 @@ int walk_na(Run& r, WalkParams wp, int2* m2l, long long m2l_cap, int2* p2p, long
 }
 
 // mixed P2P with its work plan in the rest of the static array (shared with the list sorts)
-int p2p_na(Run& r, const float* xhi, const float* xlo, const int2* list, const int* seg_start, const int* seg_end,
+int p2p_na(Run& r, const float4* xp, const int2* list, const int* seg_start, const int* seg_end,
            double* psi, double* acc, int mode) {
     unsigned long long h_tot[2] = {0, 0};
     const size_t have = r.p2p_tmp_bytes;
-    const size_t need = launch_p2p_mixed(xhi, xlo, r.n, r.c, list, seg_start, seg_end, r.leaves, r.nleaves, psi, acc,
+    const size_t need = launch_p2p_mixed(xp, r.n, r.c, list, seg_start, seg_end, r.leaves, r.nleaves, psi, acc,
                                          mode, r.p2p_tmp, have, h_tot, r.s);
     if (need > have) return fail_na(r, FMM_E_OVERFLOW, "the P2P work plan exceeds the static scratch capacity");
     return 0;
@@ -250,16 +250,15 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     NA_CU(cudaStreamSynchronize(s));
     if (st & kStatInvalid) return fail_na(r, FMM_E_INVALID, "non-finite position or mass, or negative mass");
     // two-float positions: the internal radii's single-precision bounds and the mixed P2P
-    float* xhi = (float*)A.take<float4>(n);  // 4n floats: X | Y | Z | W
-    float* xlo = (float*)A.take<float4>(n);  // 3n floats used: XL | YL | ZL
+    float4* xp = A.take<float4>(2 * (size_t)n);  // two records per particle: hi and mass, lo
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the tree");
     int* owner = A.take<int>(n);
     if (!A.ok) return fail_na(r, FMM_E_OVERFLOW, "static scratch too small for the tree");
-    launch_split_positions(r.xm, n, xhi, xlo, s);
+    launch_split_positions(r.xm, n, xp, s);
     launch_leaf_geometry(r.xm, r.c, r.leaves, r.nleaves, r.status, s);
     launch_leaf_owner(r.c, r.leaves, r.nleaves, owner, s);
     for (int L = nl - 1; L >= 0; --L)
-        launch_internal_geometry(r.xm, xhi, xlo, r.c, r.lev[L], r.lev[L + 1], n, owner, rad_tmp, r.status, s);
+        launch_internal_geometry(r.xm, xp, r.c, r.lev[L], r.lev[L + 1], n, owner, rad_tmp, r.status, s);
 
     // per-particle results and lists
     double* psi_far = A.take<double>(n);
@@ -325,7 +324,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
                            prm.precision == FMM_PREC_MIXED ? walkf : nullptr);
             // (the p = 1 L2L is folded into launch_est_scale)
             if (prm.precision == FMM_PREC_MIXED) {
-                rc = p2p_na(r, xhi, xlo, est_p2p, seg_start, seg_end, psi_near, acc_near, 0);
+                rc = p2p_na(r, xp, est_p2p, seg_start, seg_end, psi_near, acc_near, 0);
                 if (rc) return rc;
             } else
                 launch_p2p_fp64(r.xm, r.c, est_p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);
@@ -384,7 +383,7 @@ int evaluate_na(Run& r, const fmm_params& prm, const double* x, const double* mu
     sort_pairs_by_sink(p2p, np, nc, r.sort_tmp, s);
     launch_segments(p2p, np, nc, seg_start, seg_end, s);
     if (prm.precision == FMM_PREC_MIXED) {
-        rc = p2p_na(r, xhi, xlo, p2p, seg_start, seg_end, psi_near, acc_near, prm.p2p_two_float);
+        rc = p2p_na(r, xp, p2p, seg_start, seg_end, psi_near, acc_near, prm.p2p_two_float);
         if (rc) return rc;
     } else
         launch_p2p_fp64(r.xm, r.c, p2p, seg_start, seg_end, r.leaves, r.nleaves, psi_near, acc_near, s);

@@ -151,12 +151,12 @@ __device__ __forceinline__ void acc2(ff& s, float v) {
     s.lo = __fadd_rn(s.lo, t.lo);
 }
 
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // (k chunks, R replicas) for a leaf of c sinks: the most busy lanes, c R / (32 k), fewest chunks
 // on ties; R <= 4 (a tile holds 32 R sources)
@@ -333,58 +333,66 @@ __global__ void __launch_bounds__(kEmitWarps * 32)
     }
 }
 
-// The ranges of one item as a stream of tiles.  A tile takes sources from consecutive ranges
-// of one class; fill() returns the number of sources copied (0 when the stream is exhausted)
-// and the tile's class and guard flag.
+// The ranges of one item as a stream of tiles.  The item's records (its near segment, then
+// its far segment) are read 32 at a time into a register window, lane j holding record
+// w0 + j, and the next window is loaded as soon as the current one is taken.  A tile takes
+// sources from consecutive ranges of one class; fill() copies their position records (two
+// float4 each, one with LOADLO false) into the raw tile and returns their number (0 when the
+// stream is exhausted) with the tile's class and guard flag.
 struct RangeStream {
-    int e, e_end;      // next range, end of the current segment
-    int f0, f1;        // the second segment (the far ranges)
-    int af, an, off;   // the current range and the position in it
-    bool near, guard;  // its class and guard flag
-    __device__ void start(int r0, int r1, int s0, int s1) {
-        e = r0;
-        e_end = r1;
-        f0 = s0;
-        f1 = s1;
+    int a0, na, b0, total;  // flattened record i: i < na ? a0 + i : b0 + i - na; total records
+    int pos, w0;            // next record, first record of the window
+    int2 win, nwin;         // the window and the one after it
+    int af, an, off;        // the current range and the position in it
+    bool near, guard;       // its class and guard flag
+    __device__ int2 load(const int2* __restrict__ ranges, int w, int lane) const {
+        const int i = w + lane;
+        return i < total ? ranges[i < na ? a0 + i : b0 + (i - na)] : make_int2(0, 0);
+    }
+    __device__ void start(const int2* __restrict__ ranges, int lane, int r0, int r1, int s0, int s1) {
+        a0 = r0;
+        na = r1 - r0;
+        b0 = s0;
+        total = na + (s1 - s0);
+        pos = w0 = 0;
+        win = load(ranges, 0, lane);
+        nwin = load(ranges, 32, lane);
         af = an = off = 0;
         near = guard = false;
     }
     template <bool LOADLO>
-    __device__ int fill(const int2* __restrict__ ranges, const float* __restrict__ hi, const float* __restrict__ lo,
-                        size_t n, int lane, int T, float* tile, bool& tile_near, bool& tile_guard) {
+    __device__ int fill(const int2* __restrict__ ranges, const float4* __restrict__ xp, int lane, int T,
+                        float4* raw, bool& tile_near, bool& tile_guard) {
         int m = 0;
         tile_guard = false;
         tile_near = near;
         while (m < T) {
             if (off == an) {  // next range
-                if (e >= e_end) {
-                    if (f0 >= f1) break;
-                    e = f0;  // on to the second segment
-                    e_end = f1;
-                    f0 = f1;
-                    continue;
+                if (pos >= total) break;
+                if (pos - w0 >= 32) {  // on to the prefetched window
+                    win = nwin;
+                    w0 += 32;
+                    nwin = load(ranges, w0 + 32, lane);
                 }
-                const int2 r = ranges[e];
-                const bool nr = (r.y >> 30) & 1;
+                const int rx = __shfl_sync(0xffffffffu, win.x, pos - w0);
+                const int ry = __shfl_sync(0xffffffffu, win.y, pos - w0);
+                const bool nr = (ry >> 30) & 1;
                 if (m > 0 && nr != tile_near) break;  // a tile holds one class
-                ++e;
-                af = r.x;
-                an = r.y & kRangeMax;
+                ++pos;
+                af = rx;
+                an = ry & kRangeMax;
                 off = 0;
                 near = nr;
-                guard = (r.y >> kRangeCountBits) & 1;
+                guard = (ry >> kRangeCountBits) & 1;
                 tile_near = nr;
                 continue;
             }
             const int k = min(T - m, an - off);
             for (int q = lane; q < k; q += 32) {
-                const size_t j = (size_t)af + off + q;
-                float* t = tile + m + q;
-#pragma unroll
-                for (int d = 0; d < 4; ++d) cp_async4(t + d * kP2PTileM, hi + d * n + j);
-                if (LOADLO)
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) cp_async4(t + (4 + d) * kP2PTileM, lo + d * n + j);
+                const float4* g = xp + 2 * ((size_t)af + off + q);
+                float4* t = raw + 2 * (m + q);
+                cp_async16(t, g);
+                if (LOADLO) cp_async16(t + 1, g + 1);
             }
             tile_guard = tile_guard || guard;
             m += k;
@@ -399,17 +407,21 @@ struct RangeStream {
 // every range
 template <int MODE>
 __global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
-    k_p2p_mixed(const float* __restrict__ hi, const float* __restrict__ lo, int n, Cells c,
+    k_p2p_mixed(const float4* __restrict__ xp, Cells c,
                 const int* __restrict__ leaves, const int2* __restrict__ ranges, const int* __restrict__ roff,
                 const int* __restrict__ nb, const int* __restrict__ nnear, const int* __restrict__ nfar,
                 const int2* __restrict__ items, int nitems, unsigned* __restrict__ counter,
                 double* __restrict__ psi, double* __restrict__ acc) {
     constexpr bool LOADLO = MODE >= 1;  // the tiles carry the low parts
     constexpr bool CENTRE = MODE == 1 || MODE == 2;
-    constexpr int NA = LOADLO ? 7 : 4;  // arrays per tile
-    __shared__ __align__(16) float tiles[kP2PWarpsM][2][NA * kP2PTileM];
+    constexpr int NA = LOADLO ? 7 : 4;  // arrays of the computed tile
+    // per warp: the raw position records of the tile in flight, and the tile being computed
+    // (structure of arrays X | Y | Z | W [| XL | YL | ZL], high parts or offsets)
+    __shared__ __align__(16) float4 raws[kP2PWarpsM][2 * kP2PTileM];
+    __shared__ __align__(16) float tiles[kP2PWarpsM][NA * kP2PTileM];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t nn = (size_t)n;
+    float4* raw = raws[wid];
+    float* tile = tiles[wid];
     const f2 zero = f2_pack(0.f, 0.f);
     for (;;) {
         unsigned w = 0;
@@ -427,12 +439,14 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
         const int sink = lane % S, rep = lane / S < R ? lane / S : 0;
         const bool active = sink < chunk && lane < S * R;
         const int i = first + s0 + (sink < chunk ? sink : 0);
-        const float bhx = hi[i], bhy = hi[nn + i], bhz = hi[2 * nn + i];
+        const float4 bh = xp[2 * (size_t)i];
+        const float bhx = bh.x, bhy = bh.y, bhz = bh.z;
         float blx = 0.f, bly = 0.f, blz = 0.f;
         if (LOADLO) {
-            blx = lo[i];
-            bly = lo[nn + i];
-            blz = lo[2 * nn + i];
+            const float4 bl = xp[2 * (size_t)i + 1];
+            blx = bl.x;
+            bly = bl.y;
+            blz = bl.z;
         }
         const SinkPk b2{f2_pack(bhx, bhx), f2_pack(bhy, bhy), f2_pack(bhz, bhz),
                         f2_pack(blx, blx), f2_pack(bly, bly), f2_pack(blz, blz)};
@@ -457,40 +471,58 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
         RangeStream cur;
         {
             const int r0 = roff[t], r1 = r0 + nb[t];
-            cur.start(r0, r0 + nnear[t], r1 - nfar[t], r1);
+            cur.start(ranges, lane, r0, r0 + nnear[t], r1 - nfar[t], r1);
         }
         const int T = p2p_tile(R);  // sources per tile, shared by the replicas
-        int bb = 0;
         bool near = false, guard = false, near_next = false, guard_next = false;
-        int nt = cur.fill<LOADLO>(ranges, hi, lo, nn, lane, T, tiles[wid][0], near, guard);
+        int nt = cur.fill<LOADLO>(ranges, xp, lane, T, raw, near, guard);
         cp_async_commit();
         while (nt > 0) {
-            // issue the next tile, then wait for the current one
-            const int nx = cur.fill<LOADLO>(ranges, hi, lo, nn, lane, T, tiles[wid][bb ^ 1], near_next, guard_next);
-            cp_async_commit();
-            cp_async_wait1();
-            float* tile = tiles[wid][bb];
+            cp_async_wait0();
+            __syncwarp();  // the raw tile has arrived; every lane is done with the previous tile
             const int ng = (nt + 3) >> 2;
             const bool two = MODE == 3 || (MODE == 1 && near);
-            if (CENTRE && !two) {  // offsets from the leaf centre, in place of the high parts
-                __syncwarp();
-                for (int j = lane; j < nt; j += 32) {
-                    tile[j] = __fadd_rn(__fsub_rn(tile[j], chx), __fsub_rn(tile[4 * kP2PTileM + j], clx));
-                    tile[kP2PTileM + j] =
-                        __fadd_rn(__fsub_rn(tile[kP2PTileM + j], chy), __fsub_rn(tile[5 * kP2PTileM + j], cly));
-                    tile[2 * kP2PTileM + j] =
-                        __fadd_rn(__fsub_rn(tile[2 * kP2PTileM + j], chz), __fsub_rn(tile[6 * kP2PTileM + j], clz));
+            // the computed tile: offsets from the leaf centre (far, CENTRE) or the parts as they
+            // are; padded to whole groups with massless sources far away
+            for (int j = lane; j < 4 * ng; j += 32) {
+                float x = 1e15f, y = 1e15f, z = 1e15f, w = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
+                if (j < nt) {
+                    const float4 h = raw[2 * j];
+                    w = h.w;
+                    if (LOADLO) {
+                        const float4 l = raw[2 * j + 1];
+                        if (CENTRE && !two) {
+                            x = __fadd_rn(__fsub_rn(h.x, chx), __fsub_rn(l.x, clx));
+                            y = __fadd_rn(__fsub_rn(h.y, chy), __fsub_rn(l.y, cly));
+                            z = __fadd_rn(__fsub_rn(h.z, chz), __fsub_rn(l.z, clz));
+                        } else {
+                            x = h.x;
+                            y = h.y;
+                            z = h.z;
+                            xl = l.x;
+                            yl = l.y;
+                            zl = l.z;
+                        }
+                    } else {
+                        x = h.x;
+                        y = h.y;
+                        z = h.z;
+                    }
+                }
+                tile[j] = x;
+                tile[kP2PTileM + j] = y;
+                tile[2 * kP2PTileM + j] = z;
+                tile[3 * kP2PTileM + j] = w;
+                if (LOADLO && two) {
+                    tile[4 * kP2PTileM + j] = xl;
+                    tile[5 * kP2PTileM + j] = yl;
+                    tile[6 * kP2PTileM + j] = zl;
                 }
             }
-            if (lane < 4 * ng - nt) {  // pad to whole groups: massless, far away
-                float* p = tile + nt + lane;
-                p[0] = 1e15f;
-                p[kP2PTileM] = 1e15f;
-                p[2 * kP2PTileM] = 1e15f;
-                p[3 * kP2PTileM] = 0.f;
-                if (LOADLO) p[4 * kP2PTileM] = p[5 * kP2PTileM] = p[6 * kP2PTileM] = 0.f;
-            }
-            __syncwarp();
+            __syncwarp();  // the computed tile is complete and the raw tile free
+            // the next tile's copies run while this one is computed
+            const int nx = cur.fill<LOADLO>(ranges, xp, lane, T, raw, near_next, guard_next);
+            cp_async_commit();
             if (two) {
                 if (guard) tile_any<true, true>(tile, ng, rep, R, b2, a);
                 else tile_any<true, false>(tile, ng, rep, R, b2, a);
@@ -508,8 +540,6 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
             f2_unpack(a.ay, u0, u1); acc2(aay, u0 + u1);
             f2_unpack(a.az, u0, u1); acc2(aaz, u0 + u1);
             a = AccPk{zero, zero, zero, zero};
-            __syncwarp();  // every lane is done with the tile before it is refilled
-            bb ^= 1;
             nt = nx;
             near = near_next;
             guard = guard_next;
@@ -573,7 +603,7 @@ PlanLayout plan_layout(void* base, int nleaves) {
 
 size_t p2p_plan_fixed_bytes(int nleaves) { return plan_layout(nullptr, nleaves).bytes; }
 
-size_t launch_p2p_mixed(const float* hi, const float* lo, int n, Cells c, const int2* list, const int* seg_start,
+size_t launch_p2p_mixed(const float4* xp, int n, Cells c, const int2* list, const int* seg_start,
                         const int* seg_end, const int* leaves, int nleaves, double* psi, double* acc, int mode,
                         void* tmp, size_t tmp_bytes, unsigned long long* h_tot, cudaStream_t s) {
     if (nleaves <= 0) return 0;
@@ -608,14 +638,16 @@ size_t launch_p2p_mixed(const float* hi, const float* lo, int n, Cells c, const 
     int bps = 1;
     auto go = [&](auto kern) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kP2PWarpsM * 32, 0);
-        kern<<<sm_count() * (bps > 0 ? bps : 1), kP2PWarpsM * 32, 0, s>>>(hi, lo, n, c, leaves, ranges, L.roff, L.nb,
+        kern<<<sm_count() * (bps > 0 ? bps : 1), kP2PWarpsM * 32, 0, s>>>(xp, c, leaves, ranges, L.roff, L.nb,
                                                                          L.nnear, L.nfar, items, (int)nitems,
                                                                          L.counter, psi, acc);
     };
+    mark_begin(s);
     if (mode == 1) go(k_p2p_mixed<1>);
     else if (mode == 2) go(k_p2p_mixed<2>);
     else if (mode == 3) go(k_p2p_mixed<3>);
     else go(k_p2p_mixed<0>);
+    mark_end(s);
     note_launch();
     return need;
 }

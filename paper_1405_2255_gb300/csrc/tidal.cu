@@ -84,12 +84,12 @@ void launch_l2p_tidal(const d4* xm, Cells c, const d4* cen, const int* leaves, i
 
 // near part: one warp per sink leaf, lane = sink (chunks of 32), the sources of the leaf's
 // own P2P segment and of its ancestors' segments through shared-memory tiles of 32.
-// FP32 = true: dx from the two-float positions (hi + lo), FP32 pair terms, two-float sums
+// FP32 = true: dx from the two-float position records (hi + lo), FP32 pair terms, two-float sums
 // folded per tile; false: FP64 throughout.
 constexpr int kTidWarps = 4;
 template <bool FP32>
-__global__ void __launch_bounds__(kTidWarps * 32) k_p2p_tidal(const d4* __restrict__ xm, const float* __restrict__ hi,
-                                                              const float* __restrict__ lo, int n, Cells c,
+__global__ void __launch_bounds__(kTidWarps * 32) k_p2p_tidal(const d4* __restrict__ xm, const float4* __restrict__ xp,
+                                                              int n, Cells c,
                                                               const int2* __restrict__ list,
                                                               const int* __restrict__ seg_start,
                                                               const int* __restrict__ seg_end,
@@ -98,7 +98,6 @@ __global__ void __launch_bounds__(kTidWarps * 32) k_p2p_tidal(const d4* __restri
     __shared__ d4 tile64[kTidWarps][32];
     __shared__ float tile32[kTidWarps][7][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t nn = (size_t)n;
     for (int t = blockIdx.x * kTidWarps + wid; t < nleaves; t += gridDim.x * kTidWarps) {
         const int leaf = leaves[t];
         if (!cell_active(c, leaf)) continue;
@@ -110,10 +109,13 @@ __global__ void __launch_bounds__(kTidWarps * 32) k_p2p_tidal(const d4* __restri
             float bh[3] = {0.f, 0.f, 0.f}, bl[3] = {0.f, 0.f, 0.f};
             if (act) {
                 if (FP32) {
-                    for (int d = 0; d < 3; ++d) {
-                        bh[d] = hi[d * nn + i];
-                        bl[d] = lo[d * nn + i];
-                    }
+                    const float4 h = xp[2 * (size_t)i], l = xp[2 * (size_t)i + 1];
+                    bh[0] = h.x;
+                    bh[1] = h.y;
+                    bh[2] = h.z;
+                    bl[0] = l.x;
+                    bl[1] = l.y;
+                    bl[2] = l.z;
                 } else {
                     xb = xm[i];
                 }
@@ -131,8 +133,14 @@ __global__ void __launch_bounds__(kTidWarps * 32) k_p2p_tidal(const d4* __restri
                         if (lane < nt) {
                             const int j = af + j0 + lane;
                             if (FP32) {
-                                for (int d = 0; d < 4; ++d) tile32[wid][d][lane] = hi[d * nn + j];
-                                for (int d = 0; d < 3; ++d) tile32[wid][4 + d][lane] = lo[d * nn + j];
+                                const float4 h = xp[2 * (size_t)j], l = xp[2 * (size_t)j + 1];
+                                tile32[wid][0][lane] = h.x;
+                                tile32[wid][1][lane] = h.y;
+                                tile32[wid][2][lane] = h.z;
+                                tile32[wid][3][lane] = h.w;
+                                tile32[wid][4][lane] = l.x;
+                                tile32[wid][5][lane] = l.y;
+                                tile32[wid][6][lane] = l.z;
                             } else {
                                 tile64[wid][lane] = xm[j];
                             }
@@ -188,15 +196,15 @@ __global__ void __launch_bounds__(kTidWarps * 32) k_p2p_tidal(const d4* __restri
     }
 }
 
-void launch_p2p_tidal(const d4* xm, const float* hi, const float* lo, int n, bool fp32, Cells c, const int2* list,
+void launch_p2p_tidal(const d4* xm, const float4* xp, int n, bool fp32, Cells c, const int2* list,
                       const int* seg_start, const int* seg_end, const int* leaves, int nleaves, double* T,
                       cudaStream_t s) {
     if (nleaves <= 0) return;
     long long g = ((long long)nleaves + kTidWarps - 1) / kTidWarps;
     if (g > (long long)sm_count() * 32) g = (long long)sm_count() * 32;
-    if (fp32) k_p2p_tidal<true><<<(unsigned)g, kTidWarps * 32, 0, s>>>(xm, hi, lo, n, c, list, seg_start, seg_end,
+    if (fp32) k_p2p_tidal<true><<<(unsigned)g, kTidWarps * 32, 0, s>>>(xm, xp, n, c, list, seg_start, seg_end,
                                                                       leaves, nleaves, T);
-    else k_p2p_tidal<false><<<(unsigned)g, kTidWarps * 32, 0, s>>>(xm, hi, lo, n, c, list, seg_start, seg_end, leaves,
+    else k_p2p_tidal<false><<<(unsigned)g, kTidWarps * 32, 0, s>>>(xm, xp, n, c, list, seg_start, seg_end, leaves,
                                                                    nleaves, T);
     note_launch();
 }

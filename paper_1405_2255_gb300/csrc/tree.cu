@@ -1094,12 +1094,13 @@ __device__ inline int level_cell_now(const Cells& c, int L, const int* __restric
 }
 
 // FP32 bounds of the distance of particle i from a two-float centre q (hi[3], lo[3])
-__device__ inline void dist_bounds_f(const float* __restrict__ xhi, const float* __restrict__ xlo, size_t n,
-                                     int i, const float* q, float& lb, float& ub) {
+__device__ inline void dist_bounds_f(const float4* __restrict__ xp, int i, const float* q, float& lb, float& ub) {
+    const float4 h = xp[2 * (size_t)i], l = xp[2 * (size_t)i + 1];
+    const float xhs[3] = {h.x, h.y, h.z}, xls[3] = {l.x, l.y, l.z};
     float d2 = 0.f, mag = 0.f;
     for (int d = 0; d < 3; ++d) {
-        const float xh = xhi[d * n + i];
-        const float dd = __fadd_rn(__fsub_rn(xh, q[d]), __fsub_rn(xlo[d * n + i], q[3 + d]));
+        const float xh = xhs[d];
+        const float dd = __fadd_rn(__fsub_rn(xh, q[d]), __fsub_rn(xls[d], q[3 + d]));
         d2 = __fmaf_rn(dd, dd, d2);
         mag = __fadd_rn(mag, __fadd_rn(fabsf(xh), fabsf(q[d])));
     }
@@ -1113,7 +1114,7 @@ __device__ inline void dist_bounds_f(const float* __restrict__ xhi, const float*
     ub = df * (1.0f + 0x1p-20f) + E;
 }
 
-__global__ void k_internal_radii_lb(const float* __restrict__ xhi, const float* __restrict__ xlo, int n, Cells c,
+__global__ void k_internal_radii_lb(const float4* __restrict__ xp, int n, Cells c,
                                     int lev_begin, int lev_end, int* __restrict__ owner,
                                     unsigned long long* __restrict__ tmp) {
     const RadTmp R(tmp, lev_end - lev_begin);
@@ -1129,8 +1130,8 @@ __global__ void k_internal_radii_lb(const float* __restrict__ xhi, const float* 
             if (cell >= 0) {
                 const float* q = R.cen + 12 * (size_t)(cell - lev_begin);
                 float u;
-                dist_bounds_f(xhi, xlo, (size_t)n, i, q, l0, u);
-                dist_bounds_f(xhi, xlo, (size_t)n, i, q + 6, l1, u);
+                dist_bounds_f(xp, i, q, l0, u);
+                dist_bounds_f(xp, i, q + 6, l1, u);
             }
         }
         // non-negative floats order as their bit patterns
@@ -1151,8 +1152,8 @@ __global__ void k_internal_radii_lb(const float* __restrict__ xhi, const float* 
     }
 }
 
-__global__ void k_internal_radii(const d4* __restrict__ xm, const float* __restrict__ xhi,
-                                 const float* __restrict__ xlo, int n, Cells c, int lev_begin, int lev_end,
+__global__ void k_internal_radii(const d4* __restrict__ xm, const float4* __restrict__ xp, int n, Cells c,
+                                 int lev_begin, int lev_end,
                                  const int* __restrict__ owner, unsigned long long* __restrict__ tmp) {
     const RadTmp R(tmp, lev_end - lev_begin);
     const int L = c.level[lev_begin];
@@ -1166,8 +1167,8 @@ __global__ void k_internal_radii(const d4* __restrict__ xm, const float* __restr
         const int k = cell - lev_begin;
         const float* q = R.cen + 12 * (size_t)k;
         float l, u0, u1;
-        dist_bounds_f(xhi, xlo, (size_t)n, i, q, l, u0);
-        dist_bounds_f(xhi, xlo, (size_t)n, i, q + 6, l, u1);
+        dist_bounds_f(xp, i, q, l, u0);
+        dist_bounds_f(xp, i, q + 6, l, u1);
         const bool want0 = u0 >= R.lb[2 * k], want1 = u1 >= R.lb[2 * k + 1];
         if (!want0 && !want1) continue;
         const d4 p = xm[i];
@@ -1216,7 +1217,7 @@ __global__ void k_internal_keep(Cells c, int lev_begin, int lev_end, unsigned lo
     write_cen_f(RadTmp(tmp, lev_end - lev_begin), cell - lev_begin, sv, com);
 }
 
-void launch_internal_geometry(const d4* xm, const float* xhi, const float* xlo, Cells c, int lev_begin, int lev_end,
+void launch_internal_geometry(const d4* xm, const float4* xp, Cells c, int lev_begin, int lev_end,
                               int n, int* owner, unsigned long long* rad_tmp, unsigned* status, cudaStream_t s,
                               bool keep_centre) {
     int ncl = lev_end - lev_begin;
@@ -1226,10 +1227,10 @@ void launch_internal_geometry(const d4* xm, const float* xhi, const float* xlo, 
     if (keep_centre) k_internal_keep<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end, rad_tmp);
     else k_internal_meb<<<(unsigned)ncl, kMebWarps * 32, 0, s>>>(c, lev_begin, lev_end, status, rad_tmp);
     note_launch();
-    k_internal_radii_lb<<<grid_for(n, 256, 16), 256, 0, s>>>(xhi, xlo, n, c, lev_begin, lev_end, owner,
+    k_internal_radii_lb<<<grid_for(n, 256, 16), 256, 0, s>>>(xp, n, c, lev_begin, lev_end, owner,
                                                                      rad_tmp);
     note_launch();
-    k_internal_radii<<<grid_for(n, 256, 16), 256, 0, s>>>(xm, xhi, xlo, n, c, lev_begin, lev_end, owner,
+    k_internal_radii<<<grid_for(n, 256, 16), 256, 0, s>>>(xm, xp, n, c, lev_begin, lev_end, owner,
                                                                   rad_tmp);
     note_launch();
     k_internal_radii_finish<<<(ncl + 255) / 256, 256, 0, s>>>(c, lev_begin, lev_end, rad_tmp); note_launch();

@@ -39,7 +39,7 @@ class fmm_stats(C.Structure):
                 ("eps", C.c_double), ("leaf_size", C.c_int),
                 ("t_tree", C.c_float), ("t_estimate", C.c_float), ("t_up", C.c_float), ("t_walk", C.c_float),
                 ("t_m2l", C.c_float), ("t_p2p", C.c_float), ("t_down", C.c_float), ("t_total", C.c_float),
-                ("launches", C.c_int64)]
+                ("launches", C.c_int64), ("t_m2l_kernel", C.c_float), ("t_p2p_kernel", C.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
