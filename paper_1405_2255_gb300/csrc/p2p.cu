@@ -18,13 +18,16 @@
 // Work plan, built once per evaluation (k_p2p_count, k_p2p_emit): per leaf, its sources as
 // particle ranges with their class (consecutive source cells of one class whose particles are
 // contiguous are merged), in a region sized by its number of source cells, near ranges from the
-// front and far ones from the back; and the work items (leaf, sink chunk).  A leaf of c sinks
-// is cut into k chunks of S = ceil(c / k) sinks, each chunk replicated R <= 4 times across a
-// warp (lane = replica * S + sink; replica r takes every R-th group of four sources of a tile),
-// with (k, R) the choice that keeps the most lanes busy.  Every item streams its leaf's ranges
-// through double-buffered structure-of-arrays tiles of 128 sources (96 for three replicas;
-// 4-byte cp.async copies); a tile holds one class.  Items run in decreasing order of their
-// length (source particles / R) from an atomic counter.
+// front and far ones from the back; and the work items (leaf, sink chunk).  Every lane holds two
+// sinks, so that each source read from shared memory serves two pairs: a leaf of c sinks is cut
+// into k items of at most 2 S sinks (slot s of an item holds its sinks s and S + s), each item
+// replicated R <= 8 times across a warp (lane = replica * S + slot; replica r takes every R-th
+// group of four sources of a tile), with (k, R) the cheapest by a cost per item of the lanes'
+// pair work (2 / R per source) and the staging of its sources.  Every item streams its leaf's
+// ranges as tiles of up to 128 sources: 32-byte position records copied asynchronously into a
+// raw tile while the previous tile is computed, then converted into the structure-of-arrays
+// tile the pairs read (offsets from the leaf centre for far tiles); a tile holds one class.
+// Items run in decreasing order of their length (source particles / R) from an atomic counter.
 #include <climits>
 
 #include "kernels.cuh"
@@ -101,9 +104,10 @@ __device__ __forceinline__ void pair2(f2 X, f2 Y, f2 Z, f2 W, f2 XL, f2 YL, f2 Z
     a.az = f2_fma(q3, dz, a.az);
 }
 
-// one group of four sources of the tile (index g) against the sink
+// one group of four sources of the tile (index g) against the lane's two sinks
 template <bool TWO_FLOAT, bool GUARD>
-__device__ __forceinline__ void group4(const float* __restrict__ T, int g, const SinkPk& b, AccPk& a) {
+__device__ __forceinline__ void group4(const float* __restrict__ T, int g, const SinkPk& b0, const SinkPk& b1,
+                                       AccPk& a0, AccPk& a1) {
     const float4 X = ((const float4*)(T + 0 * kP2PTileM))[g], Y = ((const float4*)(T + 1 * kP2PTileM))[g],
                  Z = ((const float4*)(T + 2 * kP2PTileM))[g], W = ((const float4*)(T + 3 * kP2PTileM))[g];
     float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), YL = XL, ZL = XL;
@@ -112,35 +116,28 @@ __device__ __forceinline__ void group4(const float* __restrict__ T, int g, const
         YL = ((const float4*)(T + 5 * kP2PTileM))[g];
         ZL = ((const float4*)(T + 6 * kP2PTileM))[g];
     }
-    pair2<TWO_FLOAT, GUARD>(f2_pack(X.x, X.y), f2_pack(Y.x, Y.y), f2_pack(Z.x, Z.y), f2_pack(W.x, W.y),
-                            f2_pack(XL.x, XL.y), f2_pack(YL.x, YL.y), f2_pack(ZL.x, ZL.y), b, a);
-    pair2<TWO_FLOAT, GUARD>(f2_pack(X.z, X.w), f2_pack(Y.z, Y.w), f2_pack(Z.z, Z.w), f2_pack(W.z, W.w),
-                            f2_pack(XL.z, XL.w), f2_pack(YL.z, YL.w), f2_pack(ZL.z, ZL.w), b, a);
+    const f2 x01 = f2_pack(X.x, X.y), y01 = f2_pack(Y.x, Y.y), z01 = f2_pack(Z.x, Z.y), w01 = f2_pack(W.x, W.y);
+    const f2 x23 = f2_pack(X.z, X.w), y23 = f2_pack(Y.z, Y.w), z23 = f2_pack(Z.z, Z.w), w23 = f2_pack(W.z, W.w);
+    const f2 l01 = f2_pack(XL.x, XL.y), m01 = f2_pack(YL.x, YL.y), n01 = f2_pack(ZL.x, ZL.y);
+    const f2 l23 = f2_pack(XL.z, XL.w), m23 = f2_pack(YL.z, YL.w), n23 = f2_pack(ZL.z, ZL.w);
+    pair2<TWO_FLOAT, GUARD>(x01, y01, z01, w01, l01, m01, n01, b0, a0);
+    pair2<TWO_FLOAT, GUARD>(x01, y01, z01, w01, l01, m01, n01, b1, a1);
+    pair2<TWO_FLOAT, GUARD>(x23, y23, z23, w23, l23, m23, n23, b0, a0);
+    pair2<TWO_FLOAT, GUARD>(x23, y23, z23, w23, l23, m23, n23, b1, a1);
 }
 
-// sources per full tile for R replicas: 128, or 96 for three (eight groups of four each)
-__host__ __device__ constexpr int p2p_tile(int R) { return R == 3 ? 96 : kP2PTileM; }
+constexpr int kP2PRmax = 8;  // replicas of an item across a warp
+// groups of four per replica in a full tile, and sources per full tile: 4 R (32 / R) <= 128
+__host__ __device__ constexpr int p2p_groups(int R) { return 32 / R; }
+__host__ __device__ constexpr int p2p_tile(int R) { return 4 * R * (32 / R); }
 
-// replica r0 of R takes groups r0, r0 + R, ... of a tile of ng groups; a full tile has a trip
-// count known at compile time
-template <bool TWO_FLOAT, bool GUARD, int R>
-__device__ __forceinline__ void tile_r(const float* __restrict__ T, int ng, int r0, const SinkPk& b, AccPk& a) {
-    constexpr int NG = p2p_tile(R) / 4;
-    if (ng == NG) {
-#pragma unroll 2
-        for (int k = 0; k < NG / R; ++k) group4<TWO_FLOAT, GUARD>(T, r0 + R * k, b, a);
-    } else {
-#pragma unroll 1
-        for (int g = r0; g < ng; g += R) group4<TWO_FLOAT, GUARD>(T, g, b, a);
-    }
-}
+// replica r0 of R takes groups r0, r0 + R, ... of a tile of ng groups (one loop for every R,
+// so that the four forms of the pair code stay small enough for the instruction cache)
 template <bool TWO_FLOAT, bool GUARD>
-__device__ __forceinline__ void tile_any(const float* __restrict__ T, int ng, int r0, int R, const SinkPk& b,
-                                         AccPk& a) {
-    if (R == 1) tile_r<TWO_FLOAT, GUARD, 1>(T, ng, r0, b, a);
-    else if (R == 2) tile_r<TWO_FLOAT, GUARD, 2>(T, ng, r0, b, a);
-    else if (R == 3) tile_r<TWO_FLOAT, GUARD, 3>(T, ng, r0, b, a);
-    else tile_r<TWO_FLOAT, GUARD, 4>(T, ng, r0, b, a);
+__device__ __forceinline__ void tile_any(const float* __restrict__ T, int ng, int r0, int R, const SinkPk& b0,
+                                         const SinkPk& b1, AccPk& a0, AccPk& a1) {
+#pragma unroll 2
+    for (int g = r0; g < ng; g += R) group4<TWO_FLOAT, GUARD>(T, g, b0, b1, a0, a1);
 }
 
 // s.hi += v with the rounding error of that addition (TwoSum) kept in s.lo; s.lo is not
@@ -151,6 +148,21 @@ __device__ __forceinline__ void acc2(ff& s, float v) {
     s.lo = __fadd_rn(s.lo, t.lo);
 }
 
+// the FP32 partials of one sink folded into its two-float sums (4 per sink)
+__device__ __forceinline__ void fold(AccPk& a, ff* sum) {
+    float u0, u1;
+    f2_unpack(a.ps, u0, u1);
+    acc2(sum[0], u0 + u1);
+    f2_unpack(a.ax, u0, u1);
+    acc2(sum[1], u0 + u1);
+    f2_unpack(a.ay, u0, u1);
+    acc2(sum[2], u0 + u1);
+    f2_unpack(a.az, u0, u1);
+    acc2(sum[3], u0 + u1);
+    const f2 zero = f2_pack(0.f, 0.f);
+    a = AccPk{zero, zero, zero, zero};
+}
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -158,26 +170,26 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// (k chunks, R replicas) for a leaf of c sinks: the most busy lanes, c R / (32 k), fewest chunks
-// on ties; R <= 4 (a tile holds 32 R sources)
-__host__ __device__ inline void p2p_chunking(int c, int& k, int& R) {
-    k = 1;
-    R = 1;
+// (k items, R replicas, S slots) for a leaf of c sinks, two sinks per slot: the least cost
+// k (2 / R + 0.6) per source over k >= ceil(c / 64) (the lanes' pair work and the staging of
+// the sources, in units of a lane's pair), then k = ceil(c / (2 S)) so that no item is empty
+__host__ __device__ inline void p2p_chunking(int c, int& k, int& R, int& S) {
+    k = R = S = 1;
     if (c <= 0) return;
-    const int kmin = (c + 31) / 32;
-    float best = -1.f;
-    for (int kk = kmin; kk < kmin + 16; ++kk) {
-        const int S = (c + kk - 1) / kk;
-        const int RR = 32 / S < 4 ? 32 / S : 4;
-        const float u = (float)c * (float)RR / (32.f * (float)kk);
-        if (u > best + 1e-6f) {
-            best = u;
+    const int kmin = (c + 63) / 64;
+    float best = 3.0e38f;
+    for (int kk = kmin; kk < kmin + 12; ++kk) {
+        const int SS = (c + 2 * kk - 1) / (2 * kk);
+        const int RR = 32 / SS < kP2PRmax ? 32 / SS : kP2PRmax;
+        const float cost = (float)kk * (2.0f / (float)RR + 0.6f);
+        if (cost < best) {
+            best = cost;
             k = kk;
             R = RR;
+            S = SS;
         }
-        if (S <= 8) break;  // already four replicas; more chunks only add passes
     }
-    k = (c + (c + k - 1) / k - 1) / ((c + k - 1) / k);  // no empty chunk: k = ceil(c / S)
+    k = (c + 2 * S - 1) / (2 * S);
 }
 
 // class of source cell A for sink leaf B (see the file comment); mode 1 only
@@ -189,7 +201,7 @@ __device__ inline bool p2p_near(const d4& a, const d4& b) {
 
 // per leaf index t (one warp each): the number of its source cells (the ranges it can need at
 // most: its own and its ancestors' segment lengths) and the sort key of its items, descending
-// in the length of an item (source particles / R)
+// in the length of an item (2 source particles / R: a lane's pairs)
 __global__ void k_p2p_count(Cells c, const int2* __restrict__ list, const int* __restrict__ seg_start,
                             const int* __restrict__ seg_end, const int* __restrict__ leaves, int nleaves,
                             int* __restrict__ nb, uint64_t* __restrict__ keys, unsigned long long* __restrict__ tot) {
@@ -209,9 +221,9 @@ __global__ void k_p2p_count(Cells c, const int2* __restrict__ list, const int* _
         if (lane == 0) {
             nb[t] = (int)e;
             my += (unsigned long long)e;
-            int k, R;
-            p2p_chunking(c.count[leaf], k, R);
-            const unsigned long long len = (unsigned long long)src / (unsigned long long)R + 1;
+            int k, R, S;
+            p2p_chunking(c.count[leaf], k, R, S);
+            const unsigned long long len = 2ull * (unsigned long long)src / (unsigned long long)R + 1;
             const unsigned w32 = !cell_active(c, leaf) ? 0u : (len > 0xfffffffeull ? 0xfffffffeu : (unsigned)len);
             keys[t] = ((uint64_t)(0xffffffffu - w32) << 32) | (unsigned)t;
         }
@@ -227,8 +239,8 @@ __global__ void k_p2p_nitems(const uint64_t* __restrict__ keys, const int* __res
         const int t = (int)(keys[q] & 0xffffffffu);
         order[q] = t;
         const int leaf = leaves[t];
-        int k = 0, R;
-        if (cell_active(c, leaf)) p2p_chunking(c.count[leaf], k, R);
+        int k = 0, R, S;
+        if (cell_active(c, leaf)) p2p_chunking(c.count[leaf], k, R, S);
         nit[q] = k;
         my += (unsigned long long)k;
     }
@@ -406,7 +418,7 @@ struct RangeStream {
 // far ranges FP32 offsets from the leaf centre; 2: offsets for every range; 3: two-float for
 // every range
 template <int MODE>
-__global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
+__global__ void __launch_bounds__(kP2PWarpsM * 32, 4)
     k_p2p_mixed(const float4* __restrict__ xp, Cells c,
                 const int* __restrict__ leaves, const int2* __restrict__ ranges, const int* __restrict__ roff,
                 const int* __restrict__ nb, const int* __restrict__ nnear, const int* __restrict__ nfar,
@@ -431,28 +443,18 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
         const int2 it = items[w];
         const int t = it.x, leaf = leaves[t];
         const int first = c.first[leaf], count = c.count[leaf];
-        int k, R;
-        p2p_chunking(count, k, R);
-        const int S = (count + k - 1) / k;
-        const int s0 = it.y * S, chunk = min(S, count - s0);
-        // lanes past S * R repeat replica 0's work; their sums are not used
-        const int sink = lane % S, rep = lane / S < R ? lane / S : 0;
-        const bool active = sink < chunk && lane < S * R;
-        const int i = first + s0 + (sink < chunk ? sink : 0);
-        const float4 bh = xp[2 * (size_t)i];
-        const float bhx = bh.x, bhy = bh.y, bhz = bh.z;
-        float blx = 0.f, bly = 0.f, blz = 0.f;
-        if (LOADLO) {
-            const float4 bl = xp[2 * (size_t)i + 1];
-            blx = bl.x;
-            bly = bl.y;
-            blz = bl.z;
-        }
-        const SinkPk b2{f2_pack(bhx, bhx), f2_pack(bhy, bhy), f2_pack(bhz, bhz),
-                        f2_pack(blx, blx), f2_pack(bly, bly), f2_pack(blz, blz)};
-        // the leaf centre as two floats, the sink as its FP32 offset from it
+        int k, R, S;
+        p2p_chunking(count, k, R, S);
+        const int s0 = it.y * 2 * S, chunk = min(2 * S, count - s0);
+        // lanes past S * R repeat replica 0's work; their sums are not used.  The lane's sinks
+        // are s0 + slot and s0 + S + slot; a missing one repeats the item's first sink
+        const int slot = lane % S, rep = lane / S < R ? lane / S : 0;
+        const bool okA = lane < S * R && slot < chunk, okB = lane < S * R && S + slot < chunk;
+        const int iA = first + s0 + (slot < chunk ? slot : 0);
+        const int iB = first + s0 + (S + slot < chunk ? S + slot : 0);
+        // the leaf centre as two floats; the sinks as FP32 offsets from it (CENTRE) or their
+        // high parts
         float chx = 0.f, chy = 0.f, chz = 0.f, clx = 0.f, cly = 0.f, clz = 0.f;
-        SinkPk bo = b2;
         if (CENTRE) {
             const d4 sc = c.sr[leaf];
             chx = (float)sc.x;
@@ -461,13 +463,28 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
             clx = (float)(sc.x - (double)chx);
             cly = (float)(sc.y - (double)chy);
             clz = (float)(sc.z - (double)chz);
-            const float ox = __fadd_rn(__fsub_rn(bhx, chx), __fsub_rn(blx, clx));
-            const float oy = __fadd_rn(__fsub_rn(bhy, chy), __fsub_rn(bly, cly));
-            const float oz = __fadd_rn(__fsub_rn(bhz, chz), __fsub_rn(blz, clz));
-            bo = SinkPk{f2_pack(ox, ox), f2_pack(oy, oy), f2_pack(oz, oz), zero, zero, zero};
         }
-        AccPk a{zero, zero, zero, zero};
-        ff aps = {0, 0}, aax = {0, 0}, aay = {0, 0}, aaz = {0, 0};
+        auto far_sink = [&](int i) {
+            const float4 h = xp[2 * (size_t)i];
+            float ox = h.x, oy = h.y, oz = h.z;
+            if (CENTRE) {
+                const float4 l = xp[2 * (size_t)i + 1];
+                ox = __fadd_rn(__fsub_rn(h.x, chx), __fsub_rn(l.x, clx));
+                oy = __fadd_rn(__fsub_rn(h.y, chy), __fsub_rn(l.y, cly));
+                oz = __fadd_rn(__fsub_rn(h.z, chz), __fsub_rn(l.z, clz));
+            }
+            return SinkPk{f2_pack(ox, ox), f2_pack(oy, oy), f2_pack(oz, oz), zero, zero, zero};
+        };
+        auto near_sink = [&](int i) {
+            const float4 h = xp[2 * (size_t)i], l = xp[2 * (size_t)i + 1];
+            return SinkPk{f2_pack(h.x, h.x), f2_pack(h.y, h.y), f2_pack(h.z, h.z),
+                          f2_pack(l.x, l.x), f2_pack(l.y, l.y), f2_pack(l.z, l.z)};
+        };
+        const SinkPk fA = far_sink(iA), fB = far_sink(iB);
+        AccPk aA{zero, zero, zero, zero}, aB{zero, zero, zero, zero};
+        ff sA[4], sB[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sA[q] = sB[q] = ff{0.f, 0.f};
         RangeStream cur;
         {
             const int r0 = roff[t], r1 = r0 + nb[t];
@@ -485,10 +502,10 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
             // the computed tile: offsets from the leaf centre (far, CENTRE) or the parts as they
             // are; padded to whole groups with massless sources far away
             for (int j = lane; j < 4 * ng; j += 32) {
-                float x = 1e15f, y = 1e15f, z = 1e15f, w = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
+                float x = 1e15f, y = 1e15f, z = 1e15f, wm = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
                 if (j < nt) {
                     const float4 h = raw[2 * j];
-                    w = h.w;
+                    wm = h.w;
                     if (LOADLO) {
                         const float4 l = raw[2 * j + 1];
                         if (CENTRE && !two) {
@@ -512,7 +529,7 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
                 tile[j] = x;
                 tile[kP2PTileM + j] = y;
                 tile[2 * kP2PTileM + j] = z;
-                tile[3 * kP2PTileM + j] = w;
+                tile[3 * kP2PTileM + j] = wm;
                 if (LOADLO && two) {
                     tile[4 * kP2PTileM + j] = xl;
                     tile[5 * kP2PTileM + j] = yl;
@@ -523,42 +540,50 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 5)
             // the next tile's copies run while this one is computed
             const int nx = cur.fill<LOADLO>(ranges, xp, lane, T, raw, near_next, guard_next);
             cp_async_commit();
-            if (two) {
-                if (guard) tile_any<true, true>(tile, ng, rep, R, b2, a);
-                else tile_any<true, false>(tile, ng, rep, R, b2, a);
-            } else if (CENTRE) {
-                if (guard) tile_any<false, true>(tile, ng, rep, R, bo, a);
-                else tile_any<false, false>(tile, ng, rep, R, bo, a);
+            if (two) {  // the sinks' two-float parts, read again for this tile
+                const SinkPk nA = near_sink(iA), nB = near_sink(iB);
+                if (guard) tile_any<true, true>(tile, ng, rep, R, nA, nB, aA, aB);
+                else tile_any<true, false>(tile, ng, rep, R, nA, nB, aA, aB);
             } else {
-                if (guard) tile_any<false, true>(tile, ng, rep, R, b2, a);
-                else tile_any<false, false>(tile, ng, rep, R, b2, a);
+                if (guard) tile_any<false, true>(tile, ng, rep, R, fA, fB, aA, aB);
+                else tile_any<false, false>(tile, ng, rep, R, fA, fB, aA, aB);
             }
-            // fold the FP32 partials (<= 128 pairs per lane) into the two-float sums
-            float u0, u1;
-            f2_unpack(a.ps, u0, u1); acc2(aps, u0 + u1);
-            f2_unpack(a.ax, u0, u1); acc2(aax, u0 + u1);
-            f2_unpack(a.ay, u0, u1); acc2(aay, u0 + u1);
-            f2_unpack(a.az, u0, u1); acc2(aaz, u0 + u1);
-            a = AccPk{zero, zero, zero, zero};
+            // fold the FP32 partials (<= 128 pairs per sink) into the two-float sums
+            fold(aA, sA);
+            fold(aB, sB);
             nt = nx;
             near = near_next;
             guard = guard_next;
         }
-        // add the replicas' partial sums (lanes sink + S, sink + 2 S, ... into lane sink);
-        // only lanes below S accumulate, so every lane read still holds its own sum
-        for (int j = 1; j < R; ++j) {
-            const int src = min(lane + j * S, 31);
-            ff tps = aps, tax = aax, tay = aay, taz = aaz;
-            ff_add_lane(tps, src); ff_add_lane(tax, src); ff_add_lane(tay, src); ff_add_lane(taz, src);
-            if (lane < S) {
-                aps = tps; aax = tax; aay = tay; aaz = taz;
+        // add the replicas' partial sums into the lanes of replica 0 (a tree over the replicas:
+        // at step h, replica r takes replica r + h when r is a multiple of 2 h)
+        for (int h = 1; h < R; h *= 2) {
+            const int src = min(lane + h * S, 31);
+            const bool take = rep % (2 * h) == 0 && rep + h < R && lane < S * R;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ff ta = sA[q], tb = sB[q];
+                ff_add_lane(ta, src);
+                ff_add_lane(tb, src);
+                if (take) {
+                    sA[q] = ta;
+                    sB[q] = tb;
+                }
             }
         }
-        if (active && lane < S) {
-            psi[i] = (double)aps.hi + (double)aps.lo;
-            acc[3 * (size_t)i] = (double)aax.hi + (double)aax.lo;
-            acc[3 * (size_t)i + 1] = (double)aay.hi + (double)aay.lo;
-            acc[3 * (size_t)i + 2] = (double)aaz.hi + (double)aaz.lo;
+        if (lane < S) {
+            if (okA) {
+                psi[iA] = (double)sA[0].hi + (double)sA[0].lo;
+                acc[3 * (size_t)iA] = (double)sA[1].hi + (double)sA[1].lo;
+                acc[3 * (size_t)iA + 1] = (double)sA[2].hi + (double)sA[2].lo;
+                acc[3 * (size_t)iA + 2] = (double)sA[3].hi + (double)sA[3].lo;
+            }
+            if (okB) {
+                psi[iB] = (double)sB[0].hi + (double)sB[0].lo;
+                acc[3 * (size_t)iB] = (double)sB[1].hi + (double)sB[1].lo;
+                acc[3 * (size_t)iB + 1] = (double)sB[2].hi + (double)sB[2].lo;
+                acc[3 * (size_t)iB + 2] = (double)sB[3].hi + (double)sB[3].lo;
+            }
         }
     }
 }

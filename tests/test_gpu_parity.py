@@ -396,10 +396,10 @@ def test_autotune_meets_target(g):
     ctx.close()
 
 
-@pytest.mark.parametrize("leaf", [1, 3, 8, 20, 40])
+@pytest.mark.parametrize("leaf", [1, 3, 8, 20, 40, 80, 200])
 def test_mixed_small_leaves(g, orc, leaf):
-    """Mixed P2P with every chunk size a small leaf produces (1..40 sinks: replica counts
-    32..1) against the FP64 direct sum."""
+    """Mixed P2P with every item shape the leaves produce (1..200 sinks: one to eight
+    replicas, one to four items of up to 64 sinks, two per lane) against the FP64 direct sum."""
     x, mu = inputs.plummer(3000, inputs.BASE_SEED + 70 + leaf)
     ctx = g.Context(p=8, eps=1e-8, leaf_size=leaf, p2p_c=4.0, precision=g.FMM_PREC_MIXED)
     psi, acc = ctx.fmm_evaluate(_dev(x), _dev(mu))
