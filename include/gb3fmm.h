@@ -293,7 +293,7 @@ int fmm_alu_peaks(double* fp64_tflops, double* fp32_tflops);
 
 /* The rate of the mixed P2P's pair arithmetic alone (eq. 1 in its far form: dx from FP32
  * offsets, packed FP32 operations, the hardware rsqrt approximation), sources from shared
- * memory, one sink per lane, no staging, list walking or idle lanes, with warps_per_sm warps
+ * memory, two sinks per lane, no staging, list walking or idle lanes, with warps_per_sm warps
  * per SM (4..32) on the current device: the ceiling the P2P kernel's arithmetic is measured
  * against.  *gpairs_s (HOST out): 10^9 particle pairs per second.  About 10 ms; allocates and
  * frees a small device buffer. */

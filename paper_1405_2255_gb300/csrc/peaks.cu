@@ -105,9 +105,25 @@ __device__ __forceinline__ pf2 pp_fma(pf2 a, pf2 b, pf2 c) {
     return r;
 }
 
+// one far-form pair of eq. (1) for two packed sources against one sink
+__device__ __forceinline__ void peak_pair2(pf2 X, pf2 Y, pf2 Z, pf2 W, pf2 hx, pf2 hy, pf2 hz, pf2& ps, pf2& ax,
+                                           pf2& ay, pf2& az) {
+    const pf2 dx = pp_sub(X, hx), dy = pp_sub(Y, hy), dz = pp_sub(Z, hz);
+    const pf2 r2 = pp_fma(dx, dx, pp_fma(dy, dy, pp_mul(dz, dz)));
+    float a, b;
+    pp_unpack(r2, a, b);
+    const pf2 ri = pp_pack(rsqrt_ftz(a), rsqrt_ftz(b));
+    const pf2 qm = pp_mul(W, ri), q3 = pp_mul(qm, pp_mul(ri, ri));
+    ps = pp_add(ps, qm);
+    ax = pp_fma(q3, dx, ax);
+    ay = pp_fma(q3, dy, ay);
+    az = pp_fma(q3, dz, az);
+}
+// the P2P kernel's inner loop: groups of four sources from shared memory (structure of
+// arrays), two sinks per lane, each source pair packed against both
 __global__ void __launch_bounds__(128) k_peak_pairs(float* out, int iters) {
-    __shared__ float4 src[4][256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    __shared__ float4 src[4][128];
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) {
         src[0][i] = make_float4(i * 1e-3f, 1 + i * 1e-3f, 2 + i * 1e-3f, 3 + i * 1e-3f);
         src[1][i] = src[0][i];
         src[2][i] = src[0][i];
@@ -116,32 +132,26 @@ __global__ void __launch_bounds__(128) k_peak_pairs(float* out, int iters) {
     __syncthreads();
     const float bx = threadIdx.x * 0.01f + 0.5f, by = 0.3f, bz = -0.2f;
     const pf2 hx = pp_pack(bx, bx), hy = pp_pack(by, by), hz = pp_pack(bz, bz);
-    pf2 ps = 0, ax = 0, ay = 0, az = 0;
+    const pf2 gx = pp_pack(bx + 0.1f, bx + 0.1f), gy = pp_pack(by - 0.1f, by - 0.1f), gz = hz;
+    pf2 ps = 0, ax = 0, ay = 0, az = 0, qs = 0, bx2 = 0, by2 = 0, bz2 = 0;
     for (int it = 0; it < iters; ++it) {
 #pragma unroll 2
-        for (int g = 0; g < 256; ++g) {
+        for (int g = 0; g < 128; ++g) {
             const ulonglong2 X = ((const ulonglong2*)src[0])[g], Y = ((const ulonglong2*)src[1])[g],
                              Z = ((const ulonglong2*)src[2])[g], W = ((const ulonglong2*)src[3])[g];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const pf2 dx = pp_sub(h ? X.y : X.x, hx), dy = pp_sub(h ? Y.y : Y.x, hy), dz = pp_sub(h ? Z.y : Z.x, hz);
-                const pf2 r2 = pp_fma(dx, dx, pp_fma(dy, dy, pp_mul(dz, dz)));
-                float a, b;
-                pp_unpack(r2, a, b);
-                const pf2 ri = pp_pack(rsqrt_ftz(a), rsqrt_ftz(b));
-                const pf2 qm = pp_mul(h ? W.y : W.x, ri), q3 = pp_mul(qm, pp_mul(ri, ri));
-                ps = pp_add(ps, qm);
-                ax = pp_fma(q3, dx, ax);
-                ay = pp_fma(q3, dy, ay);
-                az = pp_fma(q3, dz, az);
+                const pf2 xx = h ? X.y : X.x, yy = h ? Y.y : Y.x, zz = h ? Z.y : Z.x, ww = h ? W.y : W.x;
+                peak_pair2(xx, yy, zz, ww, hx, hy, hz, ps, ax, ay, az);
+                peak_pair2(xx, yy, zz, ww, gx, gy, gz, qs, bx2, by2, bz2);
             }
         }
     }
     float a, b, s = 0.f;
-    pp_unpack(ps, a, b); s += a + b;
-    pp_unpack(ax, a, b); s += a + b;
-    pp_unpack(ay, a, b); s += a + b;
-    pp_unpack(az, a, b); s += a + b;
+    for (pf2 v : {ps, ax, ay, az, qs, bx2, by2, bz2}) {
+        pp_unpack(v, a, b);
+        s += a + b;
+    }
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 

@@ -358,7 +358,7 @@ def fmm_alu_peaks() -> tuple[float, float]:
     return a.value, b.value
 
 
-def fmm_pair_peak(warps_per_sm: int = 20) -> float:
+def fmm_pair_peak(warps_per_sm: int = 16) -> float:
     """The mixed P2P's pair arithmetic alone, in 10^9 pairs per second."""
     v = C.c_double()
     _check(load().fmm_pair_peak(int(warps_per_sm), C.byref(v)))
