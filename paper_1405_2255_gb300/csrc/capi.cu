@@ -56,7 +56,8 @@ T* P(Buf& b) {
     return (T*)b.p;
 }
 
-enum { EV_START, EV_TREE, EV_EST, EV_UP, EV_WALK, EV_M2L, EV_P2P, EV_DOWN, EV_END, EV_M2LK0, EV_M2LK1, EV_P2PK0, EV_P2PK1, EV_N };
+enum { EV_START, EV_TREE, EV_EST, EV_UP, EV_WALK, EV_M2L, EV_P2P, EV_DOWN, EV_END, EV_M2LK0, EV_M2LK1, EV_P2PK0, EV_P2PK1,
+       EV_JOINED, EV_N };
 
 }  // namespace
 
@@ -86,6 +87,10 @@ struct fmm_ctx {
     int* h_int = nullptr;                      // pinned
     cudaEvent_t ev[EV_N];
     bool ev_ok = false;
+    // the second stream of the upward pass, which runs beside the scale estimate, and the
+    // events that fork it from and join it to the caller's stream
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool timed = false;  // the events of the last evaluation were recorded
     bool marked_m2l = false, marked_p2p = false;  // ... and those around its main kernels
     gb3::Serve* serve = nullptr;  // the serving loop (serve.cu), created on first use
@@ -490,8 +495,8 @@ static int phase_times(fmm_ctx* ctx) {
     };
     ctx->last.t_tree = el(EV_START, EV_TREE);
     ctx->last.t_estimate = el(EV_TREE, EV_EST);
-    ctx->last.t_up = el(EV_EST, EV_UP);
-    ctx->last.t_walk = el(EV_UP, EV_WALK);
+    ctx->last.t_up = el(EV_TREE, EV_UP);  // beside the estimate, on the second stream
+    ctx->last.t_walk = el(EV_JOINED, EV_WALK);
     ctx->last.t_m2l = el(EV_WALK, EV_M2L);
     ctx->last.t_p2p = el(EV_M2L, EV_P2P);
     ctx->last.t_down = el(EV_P2P, EV_DOWN);
@@ -573,6 +578,41 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     TRY(ensure(ctx->scale_sorted, sizeof(double) * n));
     // (the two-float positions were made with the tree)
 
+    // A5-A6 (upward pass) and A7 (scale estimate) are independent: the upward pass is
+    // queued on the context's second stream, then the estimate, which waits on the host for
+    // its list sizes, runs on s; s waits for the upward pass before the walk
+    TRY(ensure(ctx->M, sizeof(double) * nco * (size_t)nc));
+    TRY(ensure(ctx->F, sizeof(double) * nco * (size_t)nc));
+    TRY(ensure(ctx->Pw, sizeof(double) * (prm.p + 1) * (size_t)nc));
+    TRY(ensure(ctx->binom, sizeof(double) * (kMaxP + 1)));
+    {
+        double bn[kMaxP + 1];
+        bn[0] = 1;
+        for (int k = 1; k <= prm.p; ++k) bn[k] = bn[k - 1] * (prm.p - k + 1) / k;
+        CU(cudaMemcpyAsync(ctx->binom.p, bn, sizeof(double) * (prm.p + 1), cudaMemcpyHostToDevice, s));
+    }
+    const bool split = prm.precision == FMM_PREC_MIXED && prm.m2l_split;
+    {
+        cudaStream_t u = ctx->s2;
+        CU(cudaEventRecord(ctx->ev_fork, s));
+        CU(cudaStreamWaitEvent(u, ctx->ev_fork, 0));
+        if (split) launch_p2m_split(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->M), u);
+        else launch_p2m(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->M), u);
+        for (int L = nlev - 1; L >= 0; --L) {
+            if (split) launch_m2m_split(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->M), u);
+            else launch_m2m_level(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->M), u);
+        }
+        launch_power(P<double>(ctx->M), nc, prm.p, P<double>(ctx->Pw), u);
+        if (timing) CU(cudaEventRecord(ctx->ev[EV_UP], u));
+        CU(cudaEventRecord(ctx->ev_join, u));
+    }
+    // every exit from here on (errors included) leaves s behind the upward pass
+    struct Join {
+        cudaStream_t s;
+        cudaEvent_t e;
+        ~Join() { cudaStreamWaitEvent(s, e, 0); }
+    } join{s, ctx->ev_join};
+
     // A7: acceleration scale for the MAC and its per-cell minimum
     if (prm.mac != FMM_MAC_THETA) {
         if (prm.scale_src == FMM_SCALE_CALLER)
@@ -592,27 +632,8 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         for (int L = nlev - 1; L >= 0; --L) launch_minscale_level(c, ctx->lev_start[L], ctx->lev_start[L + 1], s);
     }
     if (timing) CU(cudaEventRecord(ctx->ev[EV_EST], s));
-
-    // A5-A6: upward pass
-    TRY(ensure(ctx->M, sizeof(double) * nco * (size_t)nc));
-    TRY(ensure(ctx->F, sizeof(double) * nco * (size_t)nc));
-    TRY(ensure(ctx->Pw, sizeof(double) * (prm.p + 1) * (size_t)nc));
-    TRY(ensure(ctx->binom, sizeof(double) * (kMaxP + 1)));
-    {
-        double bn[kMaxP + 1];
-        bn[0] = 1;
-        for (int k = 1; k <= prm.p; ++k) bn[k] = bn[k - 1] * (prm.p - k + 1) / k;
-        CU(cudaMemcpyAsync(ctx->binom.p, bn, sizeof(double) * (prm.p + 1), cudaMemcpyHostToDevice, s));
-    }
-    const bool split = prm.precision == FMM_PREC_MIXED && prm.m2l_split;
-    if (split) launch_p2m_split(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->M), s);
-    else launch_p2m(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->M), s);
-    for (int L = nlev - 1; L >= 0; --L) {
-        if (split) launch_m2m_split(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->M), s);
-        else launch_m2m_level(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->M), s);
-    }
-    launch_power(P<double>(ctx->M), nc, prm.p, P<double>(ctx->Pw), s);
-    if (timing) CU(cudaEventRecord(ctx->ev[EV_UP], s));
+    CU(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_JOINED], s));
 
     // A8: dual tree walk
     WalkParams wp;
@@ -794,6 +815,10 @@ int fmm_create(fmm_ctx** out, const fmm_params* params, int device) {
         for (int i = 0; i < EV_N; ++i)
             if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) ctx->ev_ok = false;
     }
+    if (!rc && (cudaStreamCreateWithFlags(&ctx->s2, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess))
+        rc = FMM_E_CUDA;
     if (rc) {
         cudaGetLastError();
         fmm_destroy(ctx);
@@ -1060,6 +1085,10 @@ int fmm_destroy(fmm_ctx* ctx) {
     if (ctx->h_int) cudaFreeHost(ctx->h_int);
     if (ctx->ev_ok)
         for (int i = 0; i < EV_N; ++i) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->s2) cudaStreamSynchronize(ctx->s2);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->s2) cudaStreamDestroy(ctx->s2);
     delete ctx;
     return 0;
 }
