@@ -83,7 +83,7 @@ struct fmm_ctx {
     long long front_cap = 0, m2l_cap = 0, p2p_cap = 0, est_m2l_cap = 0, est_p2p_cap = 0;
     // per particle results (sorted order)
     Buf psi_far, acc_far, psi_near, acc_near, scale_sorted;
-    unsigned long long* h_counters = nullptr;  // pinned
+    unsigned long long* h_counters = nullptr;  // pinned, 16 words: the walk [0, 8), the P2P plan [8, 14)
     int* h_int = nullptr;                      // pinned
     cudaEvent_t ev[EV_N];
     bool ev_ok = false;
@@ -426,7 +426,7 @@ static int run_p2p_mixed(fmm_ctx* ctx, const int2* list, int mode, cudaStream_t 
         const size_t need = launch_p2p_mixed(P<float4>(ctx->xp), ctx->n, c, list,
                                              P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves),
                                              ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), mode,
-                                             ctx->p2p_tmp.p, ctx->p2p_tmp.bytes, ctx->h_counters + 6, s);
+                                             ctx->p2p_tmp.p, ctx->p2p_tmp.bytes, ctx->h_counters + 8, s);
         if (need == ~(size_t)0) return fail(ctx, FMM_E_OVERFLOW, "P2P plan beyond 2^31 source ranges or n >= 2^29");
         if (need <= ctx->p2p_tmp.bytes) return 0;
         TRY(ensure(ctx->p2p_tmp, need));
@@ -808,7 +808,7 @@ int fmm_create(fmm_ctx** out, const fmm_params* params, int device) {
     if (!rc) rc = ensure(ctx->counters, 8 * sizeof(unsigned long long));
     if (!rc) rc = ensure(ctx->coin, 16);
     if (!rc) rc = ensure(ctx->dtotal, 16);
-    if (!rc && cudaMallocHost((void**)&ctx->h_counters, 8 * sizeof(unsigned long long)) != cudaSuccess) rc = FMM_E_OOM;
+    if (!rc && cudaMallocHost((void**)&ctx->h_counters, 16 * sizeof(unsigned long long)) != cudaSuccess) rc = FMM_E_OOM;
     if (!rc && cudaMallocHost((void**)&ctx->h_int, 16 * sizeof(int)) != cudaSuccess) rc = FMM_E_OOM;
     if (!rc) {
         ctx->ev_ok = true;

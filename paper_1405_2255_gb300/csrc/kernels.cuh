@@ -218,7 +218,7 @@ void launch_p2p_fp64(const d4* xm, Cells c, const int2* list, const int* seg_sta
 // low-order estimate), 1 two-float dx for near source cells and FP32 offsets from the sink
 // leaf's centre for the others, 2 offsets for all, 3 two-float for all.  tmp holds the work
 // plan: at least p2p_plan_fixed_bytes(nleaves); the call plans, reads the plan's size on the
-// host (h_tot: 2 host words; the stream is synchronised once) and runs the P2P if tmp_bytes
+// host (h_tot: 6 host words; the stream is synchronised once) and runs the P2P if tmp_bytes
 // holds it.  Returns the bytes the call needs: a value above tmp_bytes means nothing was
 // computed (call again with that much), ~0 a plan beyond 2^31 ranges or items or n >= 2^29.
 size_t p2p_plan_fixed_bytes(int nleaves);

@@ -166,7 +166,7 @@ int walk_na(Run& r, WalkParams wp, int2* m2l, long long m2l_cap, int2* p2p, long
 // mixed P2P with its work plan in the rest of the static array (shared with the list sorts)
 int p2p_na(Run& r, const float4* xp, const int2* list, const int* seg_start, const int* seg_end,
            double* psi, double* acc, int mode) {
-    unsigned long long h_tot[2] = {0, 0};
+    unsigned long long h_tot[6] = {0, 0, 0, 0, 0, 0};
     const size_t have = r.p2p_tmp_bytes;
     const size_t need = launch_p2p_mixed(xp, r.n, r.c, list, seg_start, seg_end, r.leaves, r.nleaves, psi, acc,
                                          mode, r.p2p_tmp, have, h_tot, r.s);

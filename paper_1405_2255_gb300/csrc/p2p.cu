@@ -199,15 +199,24 @@ __device__ inline bool p2p_near(const d4& a, const d4& b) {
     return dx * dx + dy * dy + dz * dz < lim * lim;
 }
 
-// per leaf index t (one warp each): the number of its source cells (the ranges it can need at
-// most: its own and its ancestors' segment lengths) and the sort key of its items, descending
-// in the length of an item (2 source particles / R: a lane's pairs)
+// Long items are split: a leaf whose item would take a lane more than kP2PPieceSteps pair steps
+// (2 sources / R) has its stream of source cells cut into P = ceil(steps / kP2PPieceSteps) <=
+// kP2PMaxPieces pieces of about equal numbers of source cells, each with its own ranges, items
+// and FP64 partial sums, which k_p2p_reduce adds in piece order.  The split depends on the leaf
+// alone, so a system gives the same result in an ensemble as alone.
+constexpr int kP2PMaxPieces = 64;
+constexpr unsigned kP2PPieceSteps = 8192;
+
+// per leaf index t (one warp each): the number of its source cells nb[t] (the ranges it can need
+// at most: its own and its ancestors' segment lengths) and the length of its items (a lane's
+// pair steps, 2 source particles / R; 0 for a leaf without active particles); tot[0] += nb,
+// tot[2] += items x length (reported work)
 __global__ void k_p2p_count(Cells c, const int2* __restrict__ list, const int* __restrict__ seg_start,
                             const int* __restrict__ seg_end, const int* __restrict__ leaves, int nleaves,
-                            int* __restrict__ nb, uint64_t* __restrict__ keys, unsigned long long* __restrict__ tot) {
+                            int* __restrict__ nb, unsigned* __restrict__ len, unsigned long long* __restrict__ tot) {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    unsigned long long my = 0;
+    unsigned long long my = 0, work = 0;
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nleaves; t += nw) {
         const int leaf = leaves[t];
         long long e = 0, src = 0;
@@ -223,46 +232,88 @@ __global__ void k_p2p_count(Cells c, const int2* __restrict__ list, const int* _
             my += (unsigned long long)e;
             int k, R, S;
             p2p_chunking(c.count[leaf], k, R, S);
-            const unsigned long long len = 2ull * (unsigned long long)src / (unsigned long long)R + 1;
-            const unsigned w32 = !cell_active(c, leaf) ? 0u : (len > 0xfffffffeull ? 0xfffffffeu : (unsigned)len);
-            keys[t] = ((uint64_t)(0xffffffffu - w32) << 32) | (unsigned)t;
+            const unsigned long long l = 2ull * (unsigned long long)src / (unsigned long long)R + 1;
+            const unsigned w32 = !cell_active(c, leaf) ? 0u : (l > 0xfffffffeull ? 0xfffffffeu : (unsigned)l);
+            len[t] = w32;
+            if (w32) work += (unsigned long long)k * w32;
         }
     }
     if (lane == 0 && my) atomicAdd(&tot[0], my);
+    if (lane == 0 && work) atomicAdd(&tot[2], work);
 }
 
-// items per position of the sorted order (0 for a leaf without active particles)
+// per leaf index t: its pieces np[t] and its sort key, descending in the length of a piece's items
+__global__ void k_p2p_pieces(const unsigned* __restrict__ len, const int* __restrict__ nb, int nleaves,
+                             int* __restrict__ np, uint64_t* __restrict__ keys) {
+    const unsigned long long lmax = kP2PPieceSteps;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nleaves; t += gridDim.x * blockDim.x) {
+        const unsigned l = len[t];
+        int P = (int)(((unsigned long long)l + lmax - 1) / lmax);
+        const int cap = nb[t] < kP2PMaxPieces ? nb[t] : kP2PMaxPieces;
+        P = P < 1 ? 1 : (P > cap ? (cap > 0 ? cap : 1) : P);
+        np[t] = P;
+        const unsigned w32 = l ? (unsigned)(((unsigned long long)l + P - 1) / P) : 0u;
+        keys[t] = ((uint64_t)(0xffffffffu - w32) << 32) | (unsigned)t;
+    }
+}
+
+// per position q of the sorted order: items nit[q] (pieces x items per piece; 0 for a leaf
+// without active particles) and pieces npc[q]; tot[1] += items, tot[3] += pieces, tot[4] += the
+// partial sums of split leaves (pieces x sinks), tot[5] += split leaves
 __global__ void k_p2p_nitems(const uint64_t* __restrict__ keys, const int* __restrict__ leaves, int nleaves, Cells c,
-                             int* __restrict__ order, int* __restrict__ nit, unsigned long long* __restrict__ tot) {
-    unsigned long long my = 0;
+                             const int* __restrict__ np, int* __restrict__ order, int* __restrict__ nit,
+                             int* __restrict__ npc, unsigned long long* __restrict__ tot) {
+    unsigned long long my = 0, mp = 0, mpart = 0, msplit = 0;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nleaves; q += gridDim.x * blockDim.x) {
         const int t = (int)(keys[q] & 0xffffffffu);
         order[q] = t;
         const int leaf = leaves[t];
-        int k = 0, R, S;
-        if (cell_active(c, leaf)) p2p_chunking(c.count[leaf], k, R, S);
-        nit[q] = k;
-        my += (unsigned long long)k;
+        int k = 0, R, S, P = 0;
+        if (cell_active(c, leaf)) {
+            p2p_chunking(c.count[leaf], k, R, S);
+            P = np[t];
+        }
+        nit[q] = k * P;
+        npc[q] = P;
+        my += (unsigned long long)(k * P);
+        mp += (unsigned long long)P;
+        if (P > 1) {
+            mpart += (unsigned long long)P * (unsigned long long)c.count[leaf];
+            ++msplit;
+        }
     }
     if (my) atomicAdd(&tot[1], my);
+    if (mp) atomicAdd(&tot[3], mp);
+    if (mpart) atomicAdd(&tot[4], mpart);
+    if (msplit) atomicAdd(&tot[5], msplit);
 }
 
-// ranges of leaf index t into its region [roff[t], roff[t] + nb[t]): near ones from the front,
-// far ones from the back (in reverse order), their numbers into nnear[t], nfar[t]; items
-// (t, chunk) of sorted position q.  One warp per position.  The sources (the leaf's own
-// segment, then each ancestor's) are merged per class in stream order: an entry joins the open
-// range of its class when its particles follow that range's directly.  The lanes take 32 entries
-// at a time; each finds its class predecessor (the closest lower lane of its class, else the
-// open range carried from the earlier entries), the entries that do not join start a run, a
-// run's count and guard flag are summed in shared memory, and every run but the last of its
-// class is written out; the last stays open.  This is the result of the sequential pass.
+// per piece v: its leaf index, its region of ranges [r0, r1) (near ranges from the front, far
+// ones from the back), their numbers, and the first of its partial sums (-1: the piece is the
+// whole leaf and writes psi and acc directly)
+struct Pieces {
+    int *leaf, *r0, *r1, *nnear, *nfar, *part;
+};
+
+// ranges of the pieces of leaf index t (sorted position q); items (piece, chunk).  One warp per
+// position.  Piece j takes the source cells j e / P .. (j + 1) e / P - 1 of the leaf's stream
+// (its own segment, then each ancestor's; e cells in all) and owns that part of the leaf's region
+// [roff[t], roff[t] + e).  Within a piece the sources are merged per class in stream order: an
+// entry joins the open range of its class when its particles follow that range's directly.  The
+// lanes take up to 32 entries at a time; each finds its class predecessor (the closest lower
+// lane of its class, else the open range carried from the earlier entries), the entries that do
+// not join start a run, a run's count and guard flag are summed in shared memory, and every run
+// but the last of its class is written out; the last stays open until the piece ends.  This is
+// the result of the sequential pass.  A split leaf takes its partial-sum slots (P x sinks) and
+// an entry of the split list (t, first slot) from the counters tot[6], tot[7].
 constexpr int kEmitWarps = 4;
 __global__ void __launch_bounds__(kEmitWarps * 32)
     k_p2p_emit(Cells c, const int2* __restrict__ list, const int* __restrict__ seg_start,
                const int* __restrict__ seg_end, const int* __restrict__ leaves, int nleaves, int mode,
                const int* __restrict__ order, const int* __restrict__ roff, const int* __restrict__ nb,
-               int* __restrict__ nnear, int* __restrict__ nfar, const int* __restrict__ ioff,
-               const int* __restrict__ nit, int2* __restrict__ ranges, int2* __restrict__ items) {
+               const int* __restrict__ ioff, const int* __restrict__ nit, const int* __restrict__ voff,
+               const int* __restrict__ npc, Pieces pc, int2* __restrict__ ranges, int2* __restrict__ items,
+               int2* __restrict__ split, unsigned long long* __restrict__ tot) {
     __shared__ int rsum_all[kEmitWarps][33], rg_all[kEmitWarps][33];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int* rsum = rsum_all[wid];  // [0]: the open range carried in; [1 + L]: the run starting at lane L
@@ -270,36 +321,60 @@ __global__ void __launch_bounds__(kEmitWarps * 32)
     const unsigned below = (1u << lane) - 1u, upto = below | (1u << lane);
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nleaves; q += nw) {
+        const int P = npc[q];
+        if (P == 0) continue;  // no active particle: no items, no ranges
         const int t = order[q];
-        for (int j = lane; j < nit[q]; j += 32) items[ioff[q] + j] = make_int2(t, j);
+        const int kper = nit[q] / P;  // items per piece
         const int leaf = leaves[t];
+        const int count = c.count[leaf];
+        int pbase = -1;
+        if (P > 1 && lane == 0) {
+            pbase = (int)atomicAdd(&tot[6], (unsigned long long)P * (unsigned long long)count);
+            const int si = (int)atomicAdd(&tot[7], 1ull);
+            split[si] = make_int2(t, pbase);
+        }
+        pbase = __shfl_sync(0xffffffffu, pbase, 0);
+        for (int j = lane; j < nit[q]; j += 32) items[ioff[q] + j] = make_int2(voff[q] + j / kper, j % kper);
         const d4 sb = c.sr[leaf];
-        const long long b0 = c.first[leaf], b1 = b0 + c.count[leaf];
-        const int r0 = roff[t], r1 = r0 + nb[t];
-        int cf[2] = {0, 0}, cn[2] = {0, 0}, cnt[2] = {0, 0};  // open range and records written per class
-        bool cg[2] = {false, false};
-        auto put = [&](int k, int idx, int f, int n, bool g) {
-            ranges[k ? r0 + idx : r1 - 1 - idx] = make_int2(f, n | (k << 30) | ((g ? 1 : 0) << kRangeCountBits));
-        };
-        for (int cell = leaf; cell >= 0; cell = c.parent[cell]) {
-            const int s0 = seg_start[cell], s1 = seg_end[cell];
-            for (int e0 = s0; e0 < s1; e0 += 32) {
+        const long long b0 = c.first[leaf], b1 = b0 + count;
+        const long long e = nb[t];
+        // the cursor over the leaf's stream of source cells: cell, its list segment, position
+        int cell = leaf, s1 = seg_end[leaf], at = seg_start[leaf];
+        for (int pj = 0; pj < P; ++pj) {
+            const int v = voff[q] + pj;
+            const long long f0 = e * pj / P, f1 = e * (pj + 1) / P;
+            const int r0 = roff[t] + (int)f0, r1 = roff[t] + (int)f1;
+            int cf[2] = {0, 0}, cn[2] = {0, 0}, cnt[2] = {0, 0};  // open range and records written per class
+            bool cg[2] = {false, false};
+            auto put = [&](int k, int idx, int f, int n, bool g) {
+                ranges[k ? r0 + idx : r1 - 1 - idx] =
+                    make_int2(f, n | (k << 30) | ((g ? 1 : 0) << kRangeCountBits));
+            };
+            for (long long fi = f0; fi < f1;) {
+                while (at >= s1) {  // on to the next ancestor's segment
+                    cell = c.parent[cell];
+                    at = seg_start[cell];
+                    s1 = seg_end[cell];
+                }
+                const int m = (int)min((long long)min(32, s1 - at), f1 - fi);
                 int f = 0, n = 0, kk = -1;
-                if (e0 + lane < s1) {
-                    const int A = list[e0 + lane].x;
+                if (lane < m) {
+                    const int A = list[at + lane].x;
                     f = c.first[A];
                     n = c.count[A];
                     kk = mode == 1 ? (p2p_near(c.sr[A], sb) ? 1 : 0) : (mode == 3 ? 1 : 0);
                     if (n <= 0) kk = -1;
                 }
+                at += m;
+                fi += m;
                 const bool g = kk >= 0 && f < b1 && b0 < (long long)f + n;
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const unsigned M = __ballot_sync(0xffffffffu, kk == k);
                     if (!M) continue;
                     const unsigned pm = M & below;
-                    const int P = pm ? 31 - __clz(pm) : lane;
-                    const int pf = __shfl_sync(0xffffffffu, f, P), pn = __shfl_sync(0xffffffffu, n, P);
+                    const int pl = pm ? 31 - __clz(pm) : lane;
+                    const int pf = __shfl_sync(0xffffffffu, f, pl), pn = __shfl_sync(0xffffffffu, n, pl);
                     const long long pe = pm ? (long long)pf + pn : (cn[k] > 0 ? (long long)cf[k] + cn[k] : -1);
                     const bool mine = kk == k;
                     const unsigned S = __ballot_sync(0xffffffffu, mine && pe != f);
@@ -334,14 +409,45 @@ __global__ void __launch_bounds__(kEmitWarps * 32)
                     __syncwarp();
                 }
             }
+            if (lane == 0) {
+                for (int k = 1; k >= 0; --k)
+                    if (cn[k] > 0) put(k, cnt[k]++, cf[k], cn[k], cg[k]);
+                pc.leaf[v] = t;
+                pc.r0[v] = r0;
+                pc.r1[v] = r1;
+                pc.nnear[v] = cnt[1];
+                pc.nfar[v] = cnt[0];
+                pc.part[v] = P > 1 ? pbase + pj * count : -1;
+            }
+            __syncwarp();
         }
-        if (lane == 0) {
-            for (int k = 1; k >= 0; --k)
-                if (cn[k] > 0) put(k, cnt[k]++, cf[k], cn[k], cg[k]);
-            nnear[t] = cnt[1];
-            nfar[t] = cnt[0];
+    }
+}
+
+// the FP64 partial sums of the split leaves added in piece order into psi and acc: one warp per
+// entry (t, first slot) of the split list, lanes over the leaf's sinks
+__global__ void k_p2p_reduce(Cells c, const int* __restrict__ leaves, const int* __restrict__ np,
+                             const int2* __restrict__ split, int nsplit, const double* __restrict__ part,
+                             double* __restrict__ psi, double* __restrict__ acc) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nsplit; w += nw) {
+        const int2 sp = split[w];
+        const int leaf = leaves[sp.x], P = np[sp.x];
+        const int first = c.first[leaf], count = c.count[leaf];
+        for (int sk = lane; sk < count; sk += 32) {
+            double v[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int j = 0; j < P; ++j) {
+                const double* pp = part + 4 * ((size_t)sp.y + (size_t)j * count + sk);
+#pragma unroll
+                for (int d = 0; d < 4; ++d) v[d] += pp[d];
+            }
+            const size_t i = (size_t)first + sk;
+            psi[i] = v[0];
+            acc[3 * i] = v[1];
+            acc[3 * i + 1] = v[2];
+            acc[3 * i + 2] = v[3];
         }
-        __syncwarp();
     }
 }
 
@@ -419,11 +525,10 @@ struct RangeStream {
 // every range
 template <int MODE>
 __global__ void __launch_bounds__(kP2PWarpsM * 32, 4)
-    k_p2p_mixed(const float4* __restrict__ xp, Cells c,
-                const int* __restrict__ leaves, const int2* __restrict__ ranges, const int* __restrict__ roff,
-                const int* __restrict__ nb, const int* __restrict__ nnear, const int* __restrict__ nfar,
-                const int2* __restrict__ items, int nitems, unsigned* __restrict__ counter,
-                double* __restrict__ psi, double* __restrict__ acc) {
+    k_p2p_mixed(const float4* __restrict__ xp, Cells c, const int* __restrict__ leaves,
+                const int2* __restrict__ ranges, const Pieces pc, const int2* __restrict__ items, int nitems,
+                unsigned* __restrict__ counter, double* __restrict__ psi, double* __restrict__ acc,
+                double* __restrict__ part) {
     constexpr bool LOADLO = MODE >= 1;  // the tiles carry the low parts
     constexpr bool CENTRE = MODE == 1 || MODE == 2;
     constexpr int NA = LOADLO ? 7 : 4;  // arrays of the computed tile
@@ -441,7 +546,7 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 4)
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= (unsigned)nitems) break;
         const int2 it = items[w];
-        const int t = it.x, leaf = leaves[t];
+        const int v = it.x, t = pc.leaf[v], leaf = leaves[t];
         const int first = c.first[leaf], count = c.count[leaf];
         int k, R, S;
         p2p_chunking(count, k, R, S);
@@ -487,8 +592,8 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 4)
         for (int q = 0; q < 4; ++q) sA[q] = sB[q] = ff{0.f, 0.f};
         RangeStream cur;
         {
-            const int r0 = roff[t], r1 = r0 + nb[t];
-            cur.start(ranges, lane, r0, r0 + nnear[t], r1 - nfar[t], r1);
+            const int r0 = pc.r0[v], r1 = pc.r1[v];
+            cur.start(ranges, lane, r0, r0 + pc.nnear[v], r1 - pc.nfar[v], r1);
         }
         const int T = p2p_tile(R);  // sources per tile, shared by the replicas
         bool near = false, guard = false, near_next = false, guard_next = false;
@@ -571,19 +676,25 @@ __global__ void __launch_bounds__(kP2PWarpsM * 32, 4)
                 }
             }
         }
+        // a whole leaf writes psi and acc; a piece of a split leaf its partial-sum slots
+        const int pslot = pc.part[v];
+        auto out = [&](int i, const ff* sm) {
+            double* o4 = pslot >= 0 ? part + 4 * ((size_t)pslot + (size_t)(i - first)) : nullptr;
+            const double vv[4] = {(double)sm[0].hi + (double)sm[0].lo, (double)sm[1].hi + (double)sm[1].lo,
+                                  (double)sm[2].hi + (double)sm[2].lo, (double)sm[3].hi + (double)sm[3].lo};
+            if (o4) {
+#pragma unroll
+                for (int d = 0; d < 4; ++d) o4[d] = vv[d];
+            } else {
+                psi[i] = vv[0];
+                acc[3 * (size_t)i] = vv[1];
+                acc[3 * (size_t)i + 1] = vv[2];
+                acc[3 * (size_t)i + 2] = vv[3];
+            }
+        };
         if (lane < S) {
-            if (okA) {
-                psi[iA] = (double)sA[0].hi + (double)sA[0].lo;
-                acc[3 * (size_t)iA] = (double)sA[1].hi + (double)sA[1].lo;
-                acc[3 * (size_t)iA + 1] = (double)sA[2].hi + (double)sA[2].lo;
-                acc[3 * (size_t)iA + 2] = (double)sA[3].hi + (double)sA[3].lo;
-            }
-            if (okB) {
-                psi[iB] = (double)sB[0].hi + (double)sB[0].lo;
-                acc[3 * (size_t)iB] = (double)sB[1].hi + (double)sB[1].lo;
-                acc[3 * (size_t)iB + 1] = (double)sB[2].hi + (double)sB[2].lo;
-                acc[3 * (size_t)iB + 2] = (double)sB[3].hi + (double)sB[3].lo;
-            }
+            if (okA) out(iA, sA);
+            if (okB) out(iB, sB);
         }
     }
 }
@@ -592,8 +703,10 @@ namespace {
 // layout of the fixed part of the scratch (depends on the number of leaves only)
 struct PlanLayout {
     uint64_t *k0, *k1;
-    int *order, *nb, *roff, *nnear, *nfar, *nit, *ioff, *stmp, *rtmp;
-    unsigned long long* tot;  // [0] ranges, [1] items
+    unsigned* len;
+    int *order, *nb, *roff, *np, *npc, *voff, *nit, *ioff, *stmp, *rtmp;
+    unsigned long long* tot;  // [0] ranges, [1] items, [2] work, [3] pieces, [4] partial slots,
+                              // [5] split leaves, [6] [7] allocators of the emit
     unsigned* counter;
     size_t bytes;
 };
@@ -610,16 +723,18 @@ PlanLayout plan_layout(void* base, int nleaves) {
     };
     L.k0 = (uint64_t*)take(nl * 8);
     L.k1 = (uint64_t*)take(nl * 8);
+    L.len = (unsigned*)take(nl * 4);
     L.order = (int*)take(nl * 4);
     L.nb = (int*)take(nl * 4);
     L.roff = (int*)take((nl + 1) * 4);
-    L.nnear = (int*)take(nl * 4);
-    L.nfar = (int*)take(nl * 4);
+    L.np = (int*)take(nl * 4);
+    L.npc = (int*)take(nl * 4);
+    L.voff = (int*)take((nl + 1) * 4);
     L.nit = (int*)take(nl * 4);
     L.ioff = (int*)take((nl + 1) * 4);
     L.stmp = (int*)take(scan_tmp_ints((long long)nl + 1) * 4);
     L.rtmp = (int*)take(radix_tmp_ints((long long)nl) * 4);
-    L.tot = (unsigned long long*)take(4 * 8);
+    L.tot = (unsigned long long*)take(8 * 8);
     L.counter = (unsigned*)take(4 * 4);
     L.bytes = (off + 255) & ~(size_t)255;
     return L;
@@ -635,37 +750,56 @@ size_t launch_p2p_mixed(const float4* xp, int n, Cells c, const int2* list, cons
     if (n > kRangeMax) return ~(size_t)0;  // no range is ever cut: a leaf's region holds its source cells
     PlanLayout L = plan_layout(tmp, nleaves);
     if (tmp_bytes < L.bytes) return L.bytes;
-    cudaMemsetAsync(L.tot, 0, 4 * sizeof(unsigned long long), s);
+    int bps = 1;
+    auto kern_of = [&]() {
+        return mode == 1 ? k_p2p_mixed<1> : mode == 2 ? k_p2p_mixed<2> : mode == 3 ? k_p2p_mixed<3> : k_p2p_mixed<0>;
+    };
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern_of(), kP2PWarpsM * 32, 0);
+    if (bps < 1) bps = 1;
+    const int nblocks = sm_count() * bps;
+    cudaMemsetAsync(L.tot, 0, 8 * sizeof(unsigned long long), s);
     cudaMemsetAsync(L.counter, 0, 4 * sizeof(unsigned), s);
     k_p2p_count<<<grid_for((long long)nleaves * 32, 128, 16), 128, 0, s>>>(c, list, seg_start, seg_end, leaves,
-                                                                           nleaves, L.nb, L.k0, L.tot);
+                                                                           nleaves, L.nb, L.len, L.tot);
     note_launch();
     scan_exclusive_i32(L.nb, L.roff, nleaves, L.roff + nleaves, L.stmp, s);
+    k_p2p_pieces<<<grid_for(nleaves, 256), 256, 0, s>>>(L.len, L.nb, nleaves, L.np, L.k0);
+    note_launch();
     // the low 32 bits are the leaf index, already in order: sort the length bits only
     const int flip = radix_sort_pairs_bits(L.k0, nullptr, L.k1, nullptr, nleaves, L.rtmp, 32, 64, s);
-    k_p2p_nitems<<<grid_for(nleaves, 256), 256, 0, s>>>(flip ? L.k1 : L.k0, leaves, nleaves, c, L.order, L.nit,
-                                                         L.tot);
+    k_p2p_nitems<<<grid_for(nleaves, 256), 256, 0, s>>>(flip ? L.k1 : L.k0, leaves, nleaves, c, L.np, L.order,
+                                                         L.nit, L.npc, L.tot);
     note_launch();
     scan_exclusive_i32(L.nit, L.ioff, nleaves, L.ioff + nleaves, L.stmp, s);
-    cudaMemcpyAsync(h_tot, L.tot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    scan_exclusive_i32(L.npc, L.voff, nleaves, L.voff + nleaves, L.stmp, s);
+    cudaMemcpyAsync(h_tot, L.tot, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
-    const unsigned long long nranges = h_tot[0], nitems = h_tot[1];
-    if (nranges > (unsigned long long)INT_MAX || nitems > (unsigned long long)INT_MAX) return ~(size_t)0;
-    size_t need = L.bytes + ((nranges * sizeof(int2) + 255) & ~255ull) + nitems * sizeof(int2) + 256;
+    const unsigned long long nranges = h_tot[0], nitems = h_tot[1], npieces = h_tot[3], nslots = h_tot[4],
+                             nsplit = h_tot[5];
+    if (nranges > (unsigned long long)INT_MAX || nitems > (unsigned long long)INT_MAX ||
+        nslots > (unsigned long long)INT_MAX)
+        return ~(size_t)0;
+    auto a256 = [](unsigned long long b) { return (size_t)((b + 255) & ~255ull); };
+    const size_t o_ranges = L.bytes, o_items = o_ranges + a256(nranges * sizeof(int2)),
+                 o_pieces = o_items + a256(nitems * sizeof(int2)), o_split = o_pieces + a256(npieces * 6 * sizeof(int)),
+                 o_part = o_split + a256(nsplit * sizeof(int2)), need = o_part + a256(nslots * 4 * sizeof(double)) + 256;
     if (tmp_bytes < need) return need;
-    int2* ranges = (int2*)((unsigned char*)tmp + L.bytes);
-    int2* items = (int2*)((unsigned char*)ranges + ((nranges * sizeof(int2) + 255) & ~255ull));
+    unsigned char* b = (unsigned char*)tmp;
+    int2* ranges = (int2*)(b + o_ranges);
+    int2* items = (int2*)(b + o_items);
+    int* pv = (int*)(b + o_pieces);
+    const size_t npv = (size_t)npieces;
+    const Pieces pc{pv, pv + npv, pv + 2 * npv, pv + 3 * npv, pv + 4 * npv, pv + 5 * npv};
+    int2* split = (int2*)(b + o_split);
+    double* part = (double*)(b + o_part);
     const unsigned g = grid_for((long long)nleaves * 32, kEmitWarps * 32, 16);  // one warp per leaf
-    k_p2p_emit<<<g, kEmitWarps * 32, 0, s>>>(c, list, seg_start, seg_end, leaves, nleaves, mode, L.order, L.roff, L.nb, L.nnear,
-                                 L.nfar, L.ioff, L.nit, ranges, items);
+    k_p2p_emit<<<g, kEmitWarps * 32, 0, s>>>(c, list, seg_start, seg_end, leaves, nleaves, mode, L.order, L.roff,
+                                             L.nb, L.ioff, L.nit, L.voff, L.npc, pc, ranges, items, split, L.tot);
     note_launch();
     if (nitems == 0) return need;
-    int bps = 1;
     auto go = [&](auto kern) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kP2PWarpsM * 32, 0);
-        kern<<<sm_count() * (bps > 0 ? bps : 1), kP2PWarpsM * 32, 0, s>>>(xp, c, leaves, ranges, L.roff, L.nb,
-                                                                         L.nnear, L.nfar, items, (int)nitems,
-                                                                         L.counter, psi, acc);
+        kern<<<nblocks, kP2PWarpsM * 32, 0, s>>>(xp, c, leaves, ranges, pc, items, (int)nitems, L.counter, psi, acc,
+                                                 part);
     };
     mark_begin(s);
     if (mode == 1) go(k_p2p_mixed<1>);
@@ -674,6 +808,11 @@ size_t launch_p2p_mixed(const float4* xp, int n, Cells c, const int2* list, cons
     else go(k_p2p_mixed<0>);
     mark_end(s);
     note_launch();
+    if (nsplit > 0) {
+        k_p2p_reduce<<<grid_for((long long)nsplit * 32, 128, 16), 128, 0, s>>>(c, leaves, L.np, split, (int)nsplit,
+                                                                              part, psi, acc);
+        note_launch();
+    }
     return need;
 }
 
