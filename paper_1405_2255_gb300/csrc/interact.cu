@@ -621,9 +621,10 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     k_item_counts<<<grid_for(ncells, 256), 256, 0, s>>>(order, seg_start, seg_end, ncells, cnt); note_launch();
     scan_exclusive_i32(cnt, item_start, ncells, (int*)(work + 2), stmp, s);
     if (rot && m2l_rot_supported(p)) {
-        item_q = launch_m2l_rot(list, seg_start, seg_end, order, item_start, work, cen, M, ncells, p, (float*)Mf, M64,
-                                part, F, adaptive, gtmp, items_cap, s);
+        item_q = launch_m2l_rot(list, seg_start, seg_end, order, item_start, cnt, work, cen, M, ncells, p, (float*)Mf,
+                                M64, part, F, adaptive, gtmp, items_cap, s);
         single = true;
+        if (!adaptive) return;  // every sink's F was written once by the kernel
     } else {
         k_prep_split<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mf, M64); note_launch();
         m2l_rounds_launch<kRoundsBatch>(list, seg_start, seg_end, order, item_start, work, cen, Mf, M64, p, part, s);

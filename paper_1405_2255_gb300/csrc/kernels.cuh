@@ -186,16 +186,17 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
 constexpr int kM2LChunk = 32;
 constexpr int kRotMaxP = 16;  // largest order with a rotation-accelerated M2L
 bool m2l_rot_supported(int p);
-// sinks in `order` (work[1] of them), items from item_start, work[0] the item counter and
-// work[2] the number of items; Mt (ncells x (p+1)^2 floats) and M64 (ncells x 9) are scratch;
-// part receives one expansion per item, except that a sink whose list is a single item has
-// its expansion written to F (zeroed beforehand) directly
-// adaptive: the items are grouped by the largest order of their pairs and each group runs
-// the kernel of that order (gtmp: m2l_rot_group_bytes(items_cap) bytes); returns the
-// per-item orders (device, nullptr without adaptive) for the reduction
+// sinks in `order` (work[1] of them, cnt[i] items of sink position i from item_start[i]);
+// Mt (ncells x (p+1)^2 floats) and M64 (ncells x 9) are scratch.  Without adaptive, every
+// warp takes whole sinks (work[3] the sink counter) and writes each sink's F once; nothing
+// is left to reduce.  adaptive: the items are grouped by the largest order of their pairs and
+// each group runs the kernel of that order (gtmp: m2l_rot_group_bytes(items_cap) bytes; work[0]
+// the item counter, work[2] the number of items); part receives one expansion per item, except
+// that a sink whose list is a single item has its expansion written to F (zeroed beforehand)
+// directly; returns the per-item orders (device) for the reduction
 const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg_end, const int* order,
-                          const int* item_start, unsigned* work, const d4* cen, const double* M, int ncells, int p,
-                          float* Mt, cd* M64, double* part, double* F, bool adaptive, void* gtmp,
+                          const int* item_start, const int* cnt, unsigned* work, const d4* cen, const double* M,
+                          int ncells, int p, float* Mt, cd* M64, double* part, double* F, bool adaptive, void* gtmp,
                           long long items_cap, cudaStream_t s);
 size_t m2l_rot_group_bytes(long long items_cap);
 void launch_l2l_level(Cells c, const d4* cen, int lev_begin, int lev_end, int p, double* F,

@@ -107,8 +107,8 @@ size_t m2l_rot_group_bytes(long long items_cap) {
 }
 
 const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg_end, const int* order,
-                          const int* item_start, unsigned* work, const d4* cen, const double* M, int ncells, int p,
-                          float* Mt, cd* M64, double* part, double* F, bool adaptive, void* gtmp,
+                          const int* item_start, const int* cnt, unsigned* work, const d4* cen, const double* M,
+                          int ncells, int p, float* Mt, cd* M64, double* part, double* F, bool adaptive, void* gtmp,
                           long long items_cap, cudaStream_t s) {
     k_prep_rot<<<grid_for((long long)ncells * 32, 256), 256, 0, s>>>(M, cen, ncells, p, Mt, M64);
     note_launch();
@@ -116,10 +116,10 @@ const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg
 #define GB3_ROT(PP)                                                                                      \
     case PP:                                                                                             \
         rot_launch<PP>(RotArgs{list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part, F, il,  \
-                               go, gq, ctr, nco, adapt},                                                \
+                               go, gq, ctr, nco, adapt, by_sink ? cnt : nullptr, by_sink ? work + 3 : nullptr}, \
                        s);                                                                               \
         break;
-    auto launch_p = [&](int q, const int* il, const unsigned* go, int gq, unsigned* ctr, int adapt) {
+    auto launch_p = [&](int q, const int* il, const unsigned* go, int gq, unsigned* ctr, int adapt, bool by_sink) {
         switch (q) {
             GB3_ROT(3) GB3_ROT(4) GB3_ROT(5) GB3_ROT(6) GB3_ROT(7) GB3_ROT(8) GB3_ROT(9) GB3_ROT(10) GB3_ROT(11)
             GB3_ROT(12) GB3_ROT(13) GB3_ROT(14) GB3_ROT(15) GB3_ROT(16)
@@ -128,10 +128,10 @@ const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg
     };
 #undef GB3_ROT
     if (!adaptive) {
-        // every item at p: the whole item range, counted by work[0]; the item count is on the
-        // device (work[2]), so the kernel reads it there
+        // every pair at p: whole sinks, counted by work[3] (the sink count is on the device,
+        // work[1]); F is written once per sink and needs no reduction
         mark_begin(s);
-        launch_p(p, nullptr, nullptr, 0, work, 0);
+        launch_p(p, nullptr, nullptr, 0, work, 0, true);
         mark_end(s);
         return nullptr;
     }
@@ -156,7 +156,7 @@ const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg
     k_item_groups<<<grid_for(items_cap, 256), 256, 0, s>>>(qcount, goff, flip ? k1 : k0, work, ilist);
     note_launch();
     mark_begin(s);
-    for (int q = (p < 3 ? p : 3); q <= p; ++q) launch_p(q, ilist, goff, q, ctr + q, 1);
+    for (int q = (p < 3 ? p : 3); q <= p; ++q) launch_p(q, ilist, goff, q, ctr + q, 1, false);
     mark_end(s);
     return item_q;
 }

@@ -64,6 +64,10 @@ struct RotArgs {
     unsigned* counter;
     int nco_out;
     int adapt;
+    // by-sink mode (ilist == nullptr and cnt != nullptr): every warp takes whole sinks from
+    // *sink_counter (positions of the sorted order, cnt[i] items each) and writes F once per sink
+    const int* cnt;
+    unsigned* sink_counter;
 };
 
 namespace {
@@ -323,10 +327,14 @@ __device__ inline cd theta_low_rot(int j, int m, double x, double y, double z, d
 }
 
 // Shared memory of one warp: the per-lane vectors S[NCO][kPad] (floats), sigma^-n and
-// the FP64 low-order outputs.
+// the FP64 low-order outputs; then the sink's accumulated expansion (NCO doubles, by-sink mode).
+template <int P>
+constexpr int rot_warp_core_bytes() {
+    return (((P + 1) * (P + 1) * kPad * 4 + 15) & ~15) + (((P + 2) * 8 + kRotLow * 16 + 15) & ~15);
+}
 template <int P>
 constexpr int rot_warp_bytes() {
-    return (((P + 1) * (P + 1) * kPad * 4 + 15) & ~15) + (((P + 2) * 8 + kRotLow * 16 + 15) & ~15);
+    return rot_warp_core_bytes<P>() + (((P + 1) * (P + 1) * 8 + 15) & ~15);
 }
 // warps per block: as many as the shared memory of one SM holds (at most 8); they step
 // through the (long, straight-line) code of the orders together, so that they share its
@@ -336,13 +344,15 @@ constexpr int rot_warps() {
     return imin(8, imax(1, (227 * 1024) / rot_warp_bytes<P>()));
 }
 
-// One warp per work item: up to kM2LChunk pairs of one sink, lane = pair.  The items are
-// ilist[goff[gq] .. goff[gq + 1]) (ilist == nullptr: 0 .. work[2]), taken from *counter;
-// item w's partial expansion goes to part + w * nco_out, nco_out = (p+1)^2 of the global order
-// p >= P, which is also the row length of Mt; a sink whose whole list is one item has its
-// expansion written to F + B * nco_out directly (F starts at zero; the reduction skips it).
-// adapt: the pairs carry their own orders q <= P (adaptive walk) and each lane keeps only
-// the terms n + k <= q of its pair.
+// One warp per work item: up to kM2LChunk pairs of one sink, lane = pair.  By sink (cnt !=
+// nullptr, every pair at p): a warp takes a whole sink from *sink_counter (longest lists first)
+// and its items one after the other, adds their expansions in item order into its
+// shared-memory accumulator and writes F + B * nco_out once.  By item (the adaptive walk's
+// groups): the items are ilist[goff[gq] .. goff[gq + 1]) taken from *counter; item w's partial
+// expansion goes to part + w * nco_out, nco_out = (p+1)^2 of the global order p >= P, which is
+// also the row length of Mt (a sink whose whole list is one item has its expansion written to F
+// directly; F starts at zero).  adapt: the pairs carry their own orders q <= P (adaptive walk)
+// and each lane keeps only the terms n + k <= q of its pair.
 template <int P>
 __global__ void __launch_bounds__(32 * rot_warps<P>(), 1) k_m2l_rot(const RotArgs args) {
     const int2* __restrict__ list = args.list;
@@ -367,26 +377,64 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1) k_m2l_rot(const RotArg
     double* pws = (double*)(base + ((NCO * kPad * 4 + 15) & ~15));    // sigma^-n, n <= P+1
     cd* lowF = (cd*)(pws + P + 2);                                    // FP64 outputs (n <= kRotJ64, m >= 0)
     float* Sl = S + lane;
+    double* accF = (double*)(base + rot_warp_core_bytes<P>());  // the sink's expansion (by sink)
     const unsigned nsinks = work[1];
     const unsigned lbase = ilist ? goff[gq] : 0u, nlist = ilist ? goff[gq + 1] - goff[gq] : work[2];
+    const bool by_sink = !ilist && args.cnt;
+    int cur = -1, cur_it = 0, cur_end = 0;  // by sink: the warp's sink position and item cursor
+    bool done = false;
     for (;;) {
-        // the block takes W consecutive list entries, one per warp (every warp runs every barrier)
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, (unsigned)W);
-        __syncthreads();
-        const unsigned w0 = s_item;
-        __syncthreads();
-        if (w0 >= nlist) break;
-        const bool has = w0 + warp < nlist;
-        const unsigned w = has ? (ilist ? (unsigned)ilist[lbase + w0 + warp] : w0 + warp) : 0u;
+        bool has;
+        unsigned w;
+        int pos = 0;
+        if (by_sink) {
+            // the warp's sink is used up: write its expansion, take the next sink
+            while (!done && cur_it >= cur_end) {
+                if (cur >= 0) {
+                    double* o = args.F + (size_t)order[cur] * nco_out;
+                    for (int c = lane; c < NCO; c += 32) o[c] = accF[c];
+                }
+                unsigned nx = 0;
+                if (lane == 0) nx = atomicAdd(args.sink_counter, 1u);
+                nx = __shfl_sync(0xffffffffu, nx, 0);
+                if (nx >= nsinks) {
+                    done = true;
+                    cur = -1;
+                    break;
+                }
+                cur = (int)nx;
+                cur_it = item_start[cur];
+                cur_end = cur_it + args.cnt[cur];
+                for (int c = lane; c < NCO; c += 32) accF[c] = 0.0;
+                __syncwarp();
+            }
+            has = !done;
+            w = has ? (unsigned)cur_it : 0u;
+            pos = has ? cur : 0;
+            if (!__syncthreads_or(has)) break;  // every warp runs every barrier
+        } else {
+            // the block takes W consecutive list entries, one per warp (every warp runs every barrier)
+            if (threadIdx.x == 0) s_item = atomicAdd(counter, (unsigned)W);
+            __syncthreads();
+            const unsigned w0 = s_item;
+            __syncthreads();
+            if (w0 >= nlist) break;
+            has = w0 + warp < nlist;
+            w = has ? (ilist ? (unsigned)ilist[lbase + w0 + warp] : w0 + warp) : 0u;
+            if (has) {
+                int lo_i = 0, hi_i = (int)nsinks - 1;
+                while (lo_i < hi_i) {
+                    const int mid = (lo_i + hi_i + 1) >> 1;
+                    if ((unsigned)item_start[mid] <= w) lo_i = mid;
+                    else hi_i = mid - 1;
+                }
+                pos = lo_i;
+            }
+        }
         int e0 = 0, e1 = 0, s0 = 0, s1 = 0, B = 0;
         d4 sB = mk4(0.0, 0.0, 0.0, 1.0);
         if (has) {
-            int lo_i = 0, hi_i = (int)nsinks - 1;
-            while (lo_i < hi_i) {
-                const int mid = (lo_i + hi_i + 1) >> 1;
-                if ((unsigned)item_start[mid] <= w) lo_i = mid;
-                else hi_i = mid - 1;
-            }
+            const int lo_i = pos;
             B = order[lo_i];
             s0 = seg_start[B];
             s1 = seg_end[B];
@@ -489,7 +537,8 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1) k_m2l_rot(const RotArg
         warp_pow_table(1.0 / sigma, P + 1, lane, pws);
         __syncwarp();
         if (has) {
-            double* out = s1 - s0 <= kM2LChunk ? args.F + (size_t)B * nco_out : args.part + (size_t)w * nco_out;
+            double* out = by_sink ? accF
+                          : (s1 - s0 <= kM2LChunk ? args.F + (size_t)B * nco_out : args.part + (size_t)w * nco_out);
             for (int c = lane; c < NCO; c += 32) {
                 const float* row = S + c * kPad;
                 float s = 0.f;
@@ -501,8 +550,10 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1) k_m2l_rot(const RotArg
                     const cd lv = lowF[n * (n + 1) / 2 + (m < 0 ? -m : m)];
                     v += m >= 0 ? lv.re : lv.im;
                 }
-                out[c] = v;
+                if (by_sink) out[c] += v;
+                else out[c] = v;
             }
+            if (by_sink) ++cur_it;
         }
         __syncwarp();
     }

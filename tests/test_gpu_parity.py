@@ -410,6 +410,35 @@ def test_mixed_small_leaves(g, orc, leaf):
     ctx.close()
 
 
+def test_mixed_long_items_split(g, orc):
+    """Leaves whose P2P items are long have their source streams cut into pieces whose FP64
+    partial sums are added in piece order.  With p2p_c = 512 nearly every pair is P2P, so every
+    leaf of 16 sees about N sources (2 N / R > 8192 pair steps per lane at N = 40000): the
+    result matches the FP64 direct sum, and in an ensemble each system equals itself alone bit
+    for bit (the split depends on the leaf alone)."""
+    systems = [inputs.plummer(40000, inputs.BASE_SEED + 90), inputs.plummer(25000, inputs.BASE_SEED + 91)]
+    ctx = g.Context(p=8, eps=1e-8, leaf_size=16, p2p_c=512.0, precision=g.FMM_PREC_MIXED)
+    alone = []
+    for x, mu in systems:
+        psi, acc, st = ctx.fmm_evaluate(_dev(x), _dev(mu), stats=True)
+        assert st["p2p_interactions"] > 0.9 * len(mu) * (len(mu) - 1)
+        alone.append((psi.cpu().numpy(), acc.cpu().numpy()))
+    x, mu = systems[0]
+    idx = np.random.default_rng(7).choice(len(mu), 2000, replace=False)
+    p_t, a_t, _, _ = orc.direct(x, mu, sinks=idx)
+    e = _rel(alone[0][1][idx], a_t)
+    assert np.sqrt(np.mean(e ** 2)) < 1e-7
+    xs = np.concatenate([s[0] for s in systems])
+    ms = np.concatenate([s[1] for s in systems])
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
+    psi_b, acc_b = ctx.fmm_evaluate_batch(off, _dev(xs), _dev(ms), 1.0)
+    psi_b, acc_b = psi_b.cpu().numpy(), acc_b.cpu().numpy()
+    for i in range(len(systems)):
+        assert np.array_equal(acc_b[off[i]:off[i + 1]], alone[i][1]), i
+        assert np.array_equal(psi_b[off[i]:off[i + 1]], alone[i][0]), i
+    ctx.close()
+
+
 def test_small_then_large_on_one_context(g):
     """A context first used on a small system keeps working on a much larger ensemble:
     the walk's list capacities follow the tree (regression: they once stayed at the
