@@ -108,18 +108,17 @@ __device__ __forceinline__ void pair2(f2 X, f2 Y, f2 Z, f2 W, f2 XL, f2 YL, f2 Z
 template <bool TWO_FLOAT, bool GUARD>
 __device__ __forceinline__ void group4(const float* __restrict__ T, int g, const SinkPk& b0, const SinkPk& b1,
                                        AccPk& a0, AccPk& a1) {
-    const float4 X = ((const float4*)(T + 0 * kP2PTileM))[g], Y = ((const float4*)(T + 1 * kP2PTileM))[g],
-                 Z = ((const float4*)(T + 2 * kP2PTileM))[g], W = ((const float4*)(T + 3 * kP2PTileM))[g];
-    float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), YL = XL, ZL = XL;
+    // 16-byte loads straight into packed pairs (sources 0, 1 and 2, 3 of the group)
+    const ulonglong2 X = ((const ulonglong2*)(T + 0 * kP2PTileM))[g], Y = ((const ulonglong2*)(T + 1 * kP2PTileM))[g],
+                     Z = ((const ulonglong2*)(T + 2 * kP2PTileM))[g], W = ((const ulonglong2*)(T + 3 * kP2PTileM))[g];
+    ulonglong2 XL = make_ulonglong2(0ull, 0ull), YL = XL, ZL = XL;
     if (TWO_FLOAT) {
-        XL = ((const float4*)(T + 4 * kP2PTileM))[g];
-        YL = ((const float4*)(T + 5 * kP2PTileM))[g];
-        ZL = ((const float4*)(T + 6 * kP2PTileM))[g];
+        XL = ((const ulonglong2*)(T + 4 * kP2PTileM))[g];
+        YL = ((const ulonglong2*)(T + 5 * kP2PTileM))[g];
+        ZL = ((const ulonglong2*)(T + 6 * kP2PTileM))[g];
     }
-    const f2 x01 = f2_pack(X.x, X.y), y01 = f2_pack(Y.x, Y.y), z01 = f2_pack(Z.x, Z.y), w01 = f2_pack(W.x, W.y);
-    const f2 x23 = f2_pack(X.z, X.w), y23 = f2_pack(Y.z, Y.w), z23 = f2_pack(Z.z, Z.w), w23 = f2_pack(W.z, W.w);
-    const f2 l01 = f2_pack(XL.x, XL.y), m01 = f2_pack(YL.x, YL.y), n01 = f2_pack(ZL.x, ZL.y);
-    const f2 l23 = f2_pack(XL.z, XL.w), m23 = f2_pack(YL.z, YL.w), n23 = f2_pack(ZL.z, ZL.w);
+    const f2 x01 = X.x, y01 = Y.x, z01 = Z.x, w01 = W.x, x23 = X.y, y23 = Y.y, z23 = Z.y, w23 = W.y;
+    const f2 l01 = XL.x, m01 = YL.x, n01 = ZL.x, l23 = XL.y, m23 = YL.y, n23 = ZL.y;
     pair2<TWO_FLOAT, GUARD>(x01, y01, z01, w01, l01, m01, n01, b0, a0);
     pair2<TWO_FLOAT, GUARD>(x01, y01, z01, w01, l01, m01, n01, b1, a1);
     pair2<TWO_FLOAT, GUARD>(x23, y23, z23, w23, l23, m23, n23, b0, a0);
