@@ -27,9 +27,10 @@
  *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Device
  *     calls are asynchronous with respect to the host unless stated otherwise;
  *     inputs must stay valid until the stream has reached the call's end.  An
- *     evaluation forks part of its work (the upward pass) onto a stream of the
- *     context and joins it back into `stream` with events before it goes on, so
- *     everything the call does is ordered before work queued later on `stream`.
+ *     evaluation forks two independent parts of its work (the upward pass and the
+ *     scale estimate) onto two streams of the context (low and high priority) and
+ *     joins them back into `stream` with events before it goes on, so everything
+ *     the call does is ordered before work queued later on `stream`.
  *   - A context is not thread-safe: one host thread at a time per context.
  */
 #ifndef GB3FMM_H
@@ -111,10 +112,10 @@ typedef struct {
     int     depth, p;
     double  eps;
     int     leaf_size;
-    /* device time per phase in milliseconds (CUDA events).  The upward pass runs on a second
-       stream of the context beside the scale estimate: t_estimate and t_up both start at the
-       end of the tree phase and overlap; t_walk starts once both are done.  The phases are
-       otherwise consecutive on the call's stream and t_total spans the whole evaluation. */
+    /* device time per phase in milliseconds (CUDA events).  The upward pass and the scale
+       estimate run side by side on two streams of the context: t_estimate and t_up both start
+       at the end of the tree phase and overlap; t_walk starts once both are done.  The phases
+       are otherwise consecutive on the call's stream and t_total spans the whole evaluation. */
     float   t_tree, t_estimate, t_up, t_walk, t_m2l, t_p2p, t_down, t_total;
     /* number of kernels the library launched for the evaluation */
     int64_t launches;

@@ -87,10 +87,11 @@ struct fmm_ctx {
     int* h_int = nullptr;                      // pinned
     cudaEvent_t ev[EV_N];
     bool ev_ok = false;
-    // the second stream of the upward pass, which runs beside the scale estimate, and the
-    // events that fork it from and join it to the caller's stream
-    cudaStream_t s2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the streams of the upward pass (lowest priority) and of the scale estimate (highest: it
+    // is the longer branch and waits on the host between its kernels), which run side by side,
+    // and the events that fork them from and join them to the caller's stream
+    cudaStream_t s2 = nullptr, s_hi = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_est = nullptr;
     bool timed = false;  // the events of the last evaluation were recorded
     bool marked_m2l = false, marked_p2p = false;  // ... and those around its main kernels
     gb3::Serve* serve = nullptr;  // the serving loop (serve.cu), created on first use
@@ -606,14 +607,22 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         if (timing) CU(cudaEventRecord(ctx->ev[EV_UP], u));
         CU(cudaEventRecord(ctx->ev_join, u));
     }
-    // every exit from here on (errors included) leaves s behind the upward pass
+    // every exit from here on (errors included) leaves s behind the upward pass and the estimate
     struct Join {
-        cudaStream_t s;
-        cudaEvent_t e;
-        ~Join() { cudaStreamWaitEvent(s, e, 0); }
-    } join{s, ctx->ev_join};
+        cudaStream_t s, se;
+        cudaEvent_t e, ee;
+        ~Join() {
+            cudaEventRecord(ee, se);
+            cudaStreamWaitEvent(s, ee, 0);
+            cudaStreamWaitEvent(s, e, 0);
+        }
+    } join{s, ctx->s_hi, ctx->ev_join, ctx->ev_join_est};
 
-    // A7: acceleration scale for the MAC and its per-cell minimum
+    // A7: acceleration scale for the MAC and its per-cell minimum, on its own stream
+    {
+    cudaStream_t s0 = s;  // the caller's stream; s is the estimate's in this block
+    CU(cudaStreamWaitEvent(ctx->s_hi, ctx->ev_fork, 0));
+    s = ctx->s_hi;
     if (prm.mac != FMM_MAC_THETA) {
         if (prm.scale_src == FMM_SCALE_CALLER)
             launch_scale_from_caller(scale, P<int>(ctx->perm), n, P<double>(ctx->scale_sorted), s, P<int>(ctx->units));
@@ -632,6 +641,10 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         for (int L = nlev - 1; L >= 0; --L) launch_minscale_level(c, ctx->lev_start[L], ctx->lev_start[L + 1], s);
     }
     if (timing) CU(cudaEventRecord(ctx->ev[EV_EST], s));
+    CU(cudaEventRecord(ctx->ev_join_est, s));
+    s = s0;
+    }
+    CU(cudaStreamWaitEvent(s, ctx->ev_join_est, 0));
     CU(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     if (timing) CU(cudaEventRecord(ctx->ev[EV_JOINED], s));
 
@@ -815,9 +828,13 @@ int fmm_create(fmm_ctx** out, const fmm_params* params, int device) {
         for (int i = 0; i < EV_N; ++i)
             if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) ctx->ev_ok = false;
     }
-    if (!rc && (cudaStreamCreateWithFlags(&ctx->s2, cudaStreamNonBlocking) != cudaSuccess ||
+    int prio_least = 0, prio_greatest = 0;
+    if (!rc && cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) rc = FMM_E_CUDA;
+    if (!rc && (cudaStreamCreateWithPriority(&ctx->s2, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+                cudaStreamCreateWithPriority(&ctx->s_hi, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
                 cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess))
+                cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->ev_join_est, cudaEventDisableTiming) != cudaSuccess))
         rc = FMM_E_CUDA;
     if (rc) {
         cudaGetLastError();
@@ -1086,9 +1103,12 @@ int fmm_destroy(fmm_ctx* ctx) {
     if (ctx->ev_ok)
         for (int i = 0; i < EV_N; ++i) cudaEventDestroy(ctx->ev[i]);
     if (ctx->s2) cudaStreamSynchronize(ctx->s2);
+    if (ctx->s_hi) cudaStreamSynchronize(ctx->s_hi);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_join_est) cudaEventDestroy(ctx->ev_join_est);
     if (ctx->s2) cudaStreamDestroy(ctx->s2);
+    if (ctx->s_hi) cudaStreamDestroy(ctx->s_hi);
     delete ctx;
     return 0;
 }
