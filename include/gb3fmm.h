@@ -27,10 +27,11 @@
  *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Device
  *     calls are asynchronous with respect to the host unless stated otherwise;
  *     inputs must stay valid until the stream has reached the call's end.  An
- *     evaluation forks two independent parts of its work (the upward pass and the
- *     scale estimate) onto two streams of the context (low and high priority) and
- *     joins them back into `stream` with events before it goes on, so everything
- *     the call does is ordered before work queued later on `stream`.
+ *     evaluation forks independent parts of its work onto two streams of the
+ *     context (the upward pass beside the scale estimate, later the P2P beside the
+ *     M2L and downward pass) and joins them back into `stream` with events before
+ *     it goes on, so everything the call does is ordered before work queued later
+ *     on `stream`.
  *   - A context is not thread-safe: one host thread at a time per context.
  */
 #ifndef GB3FMM_H
@@ -112,10 +113,11 @@ typedef struct {
     int     depth, p;
     double  eps;
     int     leaf_size;
-    /* device time per phase in milliseconds (CUDA events).  The upward pass and the scale
-       estimate run side by side on two streams of the context: t_estimate and t_up both start
-       at the end of the tree phase and overlap; t_walk starts once both are done.  The phases
-       are otherwise consecutive on the call's stream and t_total spans the whole evaluation. */
+    /* device time per phase in milliseconds (CUDA events).  Two pairs of phases run side by
+       side on two streams of the context: t_estimate and t_up both start at the end of the tree
+       phase; t_walk starts once both are done; t_m2l and t_p2p both start at the end of the
+       walk, t_down where t_m2l ends (on the M2L's stream); t_total spans the whole evaluation
+       (the phases overlap, so they add up to more than it). */
     float   t_tree, t_estimate, t_up, t_walk, t_m2l, t_p2p, t_down, t_total;
     /* number of kernels the library launched for the evaluation */
     int64_t launches;

@@ -87,9 +87,10 @@ struct fmm_ctx {
     int* h_int = nullptr;                      // pinned
     cudaEvent_t ev[EV_N];
     bool ev_ok = false;
-    // the streams of the upward pass (lowest priority) and of the scale estimate (highest: it
-    // is the longer branch and waits on the host between its kernels), which run side by side,
-    // and the events that fork them from and join them to the caller's stream
+    // two streams of the context, lowest and highest priority: the upward pass runs on the first
+    // beside the scale estimate on the second (the longer branch, which waits on the host
+    // between its kernels); later the P2P runs on the first beside the M2L and the downward pass
+    // on the second.  Events fork them from and join them to the caller's stream.
     cudaStream_t s2 = nullptr, s_hi = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_est = nullptr;
     bool timed = false;  // the events of the last evaluation were recorded
@@ -498,9 +499,9 @@ static int phase_times(fmm_ctx* ctx) {
     ctx->last.t_estimate = el(EV_TREE, EV_EST);
     ctx->last.t_up = el(EV_TREE, EV_UP);  // beside the estimate, on the second stream
     ctx->last.t_walk = el(EV_JOINED, EV_WALK);
-    ctx->last.t_m2l = el(EV_WALK, EV_M2L);
-    ctx->last.t_p2p = el(EV_M2L, EV_P2P);
-    ctx->last.t_down = el(EV_P2P, EV_DOWN);
+    ctx->last.t_m2l = el(EV_WALK, EV_M2L);   // M2L, then the downward pass, on one stream
+    ctx->last.t_p2p = el(EV_WALK, EV_P2P);   // beside them on the other
+    ctx->last.t_down = el(EV_M2L, EV_DOWN);
     ctx->last.t_total = el(EV_START, EV_END);
     // the main kernels' own times; 0 when the kernel did not run (no marks recorded)
     auto kel = [&](int a, int b) {
@@ -607,16 +608,17 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         if (timing) CU(cudaEventRecord(ctx->ev[EV_UP], u));
         CU(cudaEventRecord(ctx->ev_join, u));
     }
-    // every exit from here on (errors included) leaves s behind the upward pass and the estimate
+    // every exit from here on (errors included) leaves s behind all the work of both streams
     struct Join {
-        cudaStream_t s, se;
+        cudaStream_t s, s2, se;
         cudaEvent_t e, ee;
         ~Join() {
+            cudaEventRecord(e, s2);
             cudaEventRecord(ee, se);
-            cudaStreamWaitEvent(s, ee, 0);
             cudaStreamWaitEvent(s, e, 0);
+            cudaStreamWaitEvent(s, ee, 0);
         }
-    } join{s, ctx->s_hi, ctx->ev_join, ctx->ev_join_est};
+    } join{s, ctx->s2, ctx->s_hi, ctx->ev_join, ctx->ev_join_est};
 
     // A7: acceleration scale for the MAC and its per-cell minimum, on its own stream
     {
@@ -685,6 +687,14 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     TRY(sort_and_segment(ctx, ctx->m2l, ctx->n_m2l, ctx->m2l_seg_start, ctx->m2l_seg_end, s, wp.adaptive != 0));
     if (timing) CU(cudaEventRecord(ctx->ev[EV_WALK], s));
 
+    // A9 M2L with A11 L2L and L2P (on the high-priority stream) and A10 P2P (on the low-priority
+    // stream; it waits on the host for its work plan, which runs beside the M2L kernel) are
+    // independent; s waits for both
+    CU(cudaEventRecord(ctx->ev_fork, s));
+    {
+    cudaStream_t s0 = s;
+    s = ctx->s_hi;
+    CU(cudaStreamWaitEvent(s, ctx->ev_fork, 0));
     // A9: M2L
     CU(cudaMemsetAsync(ctx->F.p, 0, sizeof(double) * nco * (size_t)nc, s));
     if (split) {
@@ -701,30 +711,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     ctx->marked_m2l = marks_recorded();
     kernel_marks(nullptr);
     if (timing) CU(cudaEventRecord(ctx->ev[EV_M2L], s));
-
-    // A10: P2P
-    TRY(sort_and_segment(ctx, ctx->p2p, ctx->n_p2p, ctx->seg_start, ctx->seg_end, s));
-    if (prm.precision == FMM_PREC_MIXED) {
-        kernel_marks(timing ? &ctx->ev[EV_P2PK0] : nullptr);
-        const int rc = run_p2p_mixed(ctx, P<int2>(ctx->p2p), prm.p2p_two_float, s);
-        ctx->marked_p2p = marks_recorded();
-        kernel_marks(nullptr);
-        TRY(rc);
-    } else
-        launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
-                        P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
-    const int* sys_off = ctx->nsys ? P<int>(ctx->sys_off) : nullptr;
-    launch_coincident(P<d4>(ctx->xm), P<uint64_t>(ctx->keys), n, P<unsigned long long>(ctx->coin), s, sys_off,
-                      ctx->nsys);
-    if (tidal) {  // Sec. 7.4: the near part over the same sources as the P2P
-        TRY(ensure(ctx->tid_near, sizeof(double) * 6 * (size_t)n));
-        launch_p2p_tidal(P<d4>(ctx->xm), P<float4>(ctx->xp), n, prm.precision == FMM_PREC_MIXED,
-                         c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves),
-                         ctx->nleaves, P<double>(ctx->tid_near), s);
-    }
-    if (timing) CU(cudaEventRecord(ctx->ev[EV_P2P], s));
-
-    // A11-A12: L2L, L2P, combine and scatter
+    // A11-A12: L2L, L2P
     for (int L = 1; L < nlev; ++L) {
         if (split) launch_l2l_split(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->F), s);
         else launch_l2l_level(c, c.sr, ctx->lev_start[L], ctx->lev_start[L + 1], prm.p, P<double>(ctx->F), s);
@@ -735,6 +722,37 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     else
         launch_l2p(P<d4>(ctx->xm), c, c.sr, P<int>(ctx->leaves), ctx->nleaves, prm.p, P<double>(ctx->F),
                    P<double>(ctx->psi_far), P<double>(ctx->acc_far), s);
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_DOWN], s));
+    CU(cudaEventRecord(ctx->ev_join, s));
+
+    // A10: P2P
+    s = ctx->s2;
+    CU(cudaStreamWaitEvent(s, ctx->ev_fork, 0));
+    TRY(sort_and_segment(ctx, ctx->p2p, ctx->n_p2p, ctx->seg_start, ctx->seg_end, s));
+    if (prm.precision == FMM_PREC_MIXED) {
+        kernel_marks(timing ? &ctx->ev[EV_P2PK0] : nullptr);
+        const int rc = run_p2p_mixed(ctx, P<int2>(ctx->p2p), prm.p2p_two_float, s);
+        ctx->marked_p2p = marks_recorded();
+        kernel_marks(nullptr);
+        TRY(rc);
+    } else
+        launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
+                        P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
+    launch_coincident(P<d4>(ctx->xm), P<uint64_t>(ctx->keys), n, P<unsigned long long>(ctx->coin), s,
+                      ctx->nsys ? P<int>(ctx->sys_off) : nullptr, ctx->nsys);
+    if (tidal) {  // Sec. 7.4: the near part over the same sources as the P2P
+        TRY(ensure(ctx->tid_near, sizeof(double) * 6 * (size_t)n));
+        launch_p2p_tidal(P<d4>(ctx->xm), P<float4>(ctx->xp), n, prm.precision == FMM_PREC_MIXED,
+                         c, P<int2>(ctx->p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end), P<int>(ctx->leaves),
+                         ctx->nleaves, P<double>(ctx->tid_near), s);
+    }
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_P2P], s));
+    CU(cudaEventRecord(ctx->ev_join_est, s));
+    s = s0;
+    }
+    CU(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+    CU(cudaStreamWaitEvent(s, ctx->ev_join_est, 0));
+    const int* sys_off = ctx->nsys ? P<int>(ctx->sys_off) : nullptr;
     launch_finish(P<double>(ctx->psi_far), P<double>(ctx->acc_far), P<double>(ctx->psi_near), P<double>(ctx->acc_near),
                   P<int>(ctx->perm), n, G, psi, acc, s, sys_off, ctx->nsys ? P<double>(ctx->sys_G) : nullptr,
                   ctx->nsys, ctx->active_mode ? P<unsigned char>(ctx->pact) : nullptr, P<int>(ctx->units));
@@ -745,10 +763,7 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
         launch_finish_tidal(P<double>(ctx->tid_far), P<double>(ctx->tid_near), P<int>(ctx->perm), n, G,
                             ctx->active_mode ? P<unsigned char>(ctx->pact) : nullptr, tidal, s, P<int>(ctx->units));
     }
-    if (timing) {
-        CU(cudaEventRecord(ctx->ev[EV_DOWN], s));
-        CU(cudaEventRecord(ctx->ev[EV_END], s));
-    }
+    if (timing) CU(cudaEventRecord(ctx->ev[EV_END], s));
     CU(cudaGetLastError());
 
     ctx->last.ncells = nc;
