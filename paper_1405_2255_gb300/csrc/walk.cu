@@ -161,7 +161,9 @@ void launch_walk_prep(Cells c, const d4* cen, const double* P, int p, double eps
 
 // nfront_dev (nullable): the frontier's length on the device (read here, capped at the
 // buffer's capacity), else nfront; the next frontier is counted in *out_cnt
-__global__ void k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in, long long nfront,
+// 32 registers (a few spills) so that the launch of 8 blocks per SM is one wave: the steps are
+// bound by the latency of the cell gathers
+__global__ void __launch_bounds__(256, 8) k_walk(Cells c, WalkParams wp, const int2* __restrict__ front_in, long long nfront,
                        const unsigned long long* __restrict__ nfront_dev, int2* __restrict__ front_out, WalkBuffers wb,
                        unsigned long long* __restrict__ out_cnt) {
     if (nfront_dev) {
