@@ -288,8 +288,10 @@ def roofline(g, a, prec, phase, full):
             "pair_arithmetic_ceiling_note": "the P2P pair arithmetic alone (fmm_pair_peak, 16 warps per SM as "
                                             "the kernel): 13 FP32 operations and one rsqrt per pair, two sinks "
                                             "per lane, no staging or idle lanes",
-            "phase_share": {"m2l": t_m2l / (float(np.mean([s["t_total"] for s in phase])) * 1e-3),
-                            "p2p": t_p2p / (float(np.mean([s["t_total"] for s in phase])) * 1e-3)}}
+            "kernel_share": {"m2l": k_m2l / (float(np.mean([s["t_total"] for s in phase])) * 1e-3),
+                             "p2p": k_p2p / (float(np.mean([s["t_total"] for s in phase])) * 1e-3),
+                             "note": "each main kernel's own CUDA-event time over the step's (the M2L and the "
+                                     "P2P run side by side on two streams)"}}
 
 
 def sampled_error(ctx, xt, mt, acc, idx, dev, G=1.0):

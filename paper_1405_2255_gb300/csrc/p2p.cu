@@ -208,14 +208,13 @@ constexpr unsigned kP2PPieceSteps = 8192;
 
 // per leaf index t (one warp each): the number of its source cells nb[t] (the ranges it can need
 // at most: its own and its ancestors' segment lengths) and the length of its items (a lane's
-// pair steps, 2 source particles / R; 0 for a leaf without active particles); tot[0] += nb,
-// tot[2] += items x length (reported work)
+// pair steps, 2 source particles / R; 0 for a leaf without active particles); tot[0] += nb
 __global__ void k_p2p_count(Cells c, const int2* __restrict__ list, const int* __restrict__ seg_start,
                             const int* __restrict__ seg_end, const int* __restrict__ leaves, int nleaves,
                             int* __restrict__ nb, unsigned* __restrict__ len, unsigned long long* __restrict__ tot) {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    unsigned long long my = 0, work = 0;
+    unsigned long long my = 0;
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nleaves; t += nw) {
         const int leaf = leaves[t];
         long long e = 0, src = 0;
@@ -234,11 +233,9 @@ __global__ void k_p2p_count(Cells c, const int2* __restrict__ list, const int* _
             const unsigned long long l = 2ull * (unsigned long long)src / (unsigned long long)R + 1;
             const unsigned w32 = !cell_active(c, leaf) ? 0u : (l > 0xfffffffeull ? 0xfffffffeu : (unsigned)l);
             len[t] = w32;
-            if (w32) work += (unsigned long long)k * w32;
         }
     }
     if (lane == 0 && my) atomicAdd(&tot[0], my);
-    if (lane == 0 && work) atomicAdd(&tot[2], work);
 }
 
 // per leaf index t: its pieces np[t] and its sort key, descending in the length of a piece's items
@@ -704,8 +701,8 @@ struct PlanLayout {
     uint64_t *k0, *k1;
     unsigned* len;
     int *order, *nb, *roff, *np, *npc, *voff, *nit, *ioff, *stmp, *rtmp;
-    unsigned long long* tot;  // [0] ranges, [1] items, [2] work, [3] pieces, [4] partial slots,
-                              // [5] split leaves, [6] [7] allocators of the emit
+    unsigned long long* tot;  // [0] ranges, [1] items, [3] pieces, [4] partial slots, [5] split
+                              // leaves, [6] [7] allocators of the emit ([2] unused)
     unsigned* counter;
     size_t bytes;
 };
