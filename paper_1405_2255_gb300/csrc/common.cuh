@@ -113,6 +113,18 @@ void mark_begin(cudaStream_t s);
 void mark_end(cudaStream_t s);
 bool marks_recorded();  // both events were recorded since the last kernel_marks()
 
+// a length on a logarithmic scale of eight steps per octave, 0 for 0 and 1..255 otherwise:
+// sort keys of work lists ordered longest first (one 8-bit radix pass instead of one per byte
+// of the exact length; the order within a step stays that of the indices)
+__host__ __device__ inline unsigned qlen8(unsigned len) {
+    if (len == 0) return 0;
+    int lg = 31;
+    while (!(len >> lg)) --lg;                                 // floor(log2 len)
+    const unsigned frac = lg >= 3 ? (len >> (lg - 3)) & 7u : (len << (3 - lg)) & 7u;
+    const unsigned q = 1u + 8u * (unsigned)lg + frac;          // 1 .. 256
+    return q > 255u ? 255u : q;
+}
+
 // streaming multiprocessors of the current device (queried once per device)
 int sm_count();
 

@@ -92,12 +92,13 @@ __global__ void __launch_bounds__(64) k_m2l(const int2* __restrict__ list, const
     }
 }
 
-// sinks with a non-empty M2L segment, ordered by decreasing segment length
+// sinks with a non-empty M2L segment, ordered by decreasing segment length (eight steps per
+// octave, qlen8)
 __global__ void k_sink_keys(const int* __restrict__ seg_start, const int* __restrict__ seg_end, int ncells,
                             uint64_t* __restrict__ keys, int* __restrict__ vals) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += gridDim.x * blockDim.x) {
         unsigned len = (unsigned)(seg_end[i] - seg_start[i]);
-        keys[i] = ((uint64_t)(0xffffffu - min(len, 0xffffffu)) << 32) | (unsigned)i;
+        keys[i] = ((uint64_t)(255u - qlen8(len)) << 32) | (unsigned)i;
         vals[i] = len ? 1 : 0;
     }
 }
@@ -105,9 +106,9 @@ __global__ void k_sink_order(const uint64_t* __restrict__ keys, int ncells, int*
                              unsigned* __restrict__ nsinks) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += gridDim.x * blockDim.x) {
         uint64_t k = keys[i];
-        unsigned len = 0xffffffu - (unsigned)(k >> 32);
+        unsigned q = 255u - (unsigned)(k >> 32);  // 0: an empty list (sorted last)
         order[i] = (int)(k & 0xffffffffu);
-        if (len && (i == ncells - 1 || (0xffffffu - (unsigned)(keys[i + 1] >> 32)) == 0)) *nsinks = (unsigned)(i + 1);
+        if (q && (i == ncells - 1 || (255u - (unsigned)(keys[i + 1] >> 32)) == 0)) *nsinks = (unsigned)(i + 1);
     }
 }
 
@@ -148,9 +149,9 @@ void launch_m2l(const int2* list, const int* seg_start, const int* seg_end, void
     cd* Mc = (cd*)(((uintptr_t)(rtmp + radix_tmp_ints(ncells)) + 255) & ~(uintptr_t)255);
     cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
     k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
-    // the low 32 bits are the sink's index, already in order: the stable passes over the
-    // length bits alone keep ties in index order
-    int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 32, 56, s);
+    // the low 32 bits are the sink's index, already in order: the stable pass over the 8
+    // length bits alone keeps ties in index order
+    int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 32, 40, s);
     k_sink_order<<<grid_for(ncells, 256), 256, 0, s>>>(flip ? k1 : k0, ncells, order, work + 1); note_launch();
     k_expand_conj<<<grid_for((long long)ncells * ncoef(p), 256), 256, 0, s>>>(M, ncells, p, Mc); note_launch();
     LaneSched sched = make_lane_sched(p, kSchedDown);
@@ -614,9 +615,9 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     bool single = false;
     cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
     k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
-    // the low 32 bits are the sink's index, already in order: the stable passes over the
-    // length bits alone keep ties in index order
-    int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 32, 56, s);
+    // the low 32 bits are the sink's index, already in order: the stable pass over the 8
+    // length bits alone keeps ties in index order
+    int flip = radix_sort_pairs_bits(k0, v0, k1, v1, ncells, rtmp, 32, 40, s);
     k_sink_order<<<grid_for(ncells, 256), 256, 0, s>>>(flip ? k1 : k0, ncells, order, work + 1); note_launch();
     k_item_counts<<<grid_for(ncells, 256), 256, 0, s>>>(order, seg_start, seg_end, ncells, cnt); note_launch();
     scan_exclusive_i32(cnt, item_start, ncells, (int*)(work + 2), stmp, s);

@@ -249,7 +249,7 @@ __global__ void k_p2p_pieces(const unsigned* __restrict__ len, const int* __rest
         P = P < 1 ? 1 : (P > cap ? (cap > 0 ? cap : 1) : P);
         np[t] = P;
         const unsigned w32 = l ? (unsigned)(((unsigned long long)l + P - 1) / P) : 0u;
-        keys[t] = ((uint64_t)(0xffffffffu - w32) << 32) | (unsigned)t;
+        keys[t] = ((uint64_t)(255u - qlen8(w32)) << 32) | (unsigned)t;
     }
 }
 
@@ -761,8 +761,8 @@ size_t launch_p2p_mixed(const float4* xp, int n, Cells c, const int2* list, cons
     scan_exclusive_i32(L.nb, L.roff, nleaves, L.roff + nleaves, L.stmp, s);
     k_p2p_pieces<<<grid_for(nleaves, 256), 256, 0, s>>>(L.len, L.nb, nleaves, L.np, L.k0);
     note_launch();
-    // the low 32 bits are the leaf index, already in order: sort the length bits only
-    const int flip = radix_sort_pairs_bits(L.k0, nullptr, L.k1, nullptr, nleaves, L.rtmp, 32, 64, s);
+    // the low 32 bits are the leaf index, already in order: sort the 8 length bits only
+    const int flip = radix_sort_pairs_bits(L.k0, nullptr, L.k1, nullptr, nleaves, L.rtmp, 32, 40, s);
     k_p2p_nitems<<<grid_for(nleaves, 256), 256, 0, s>>>(flip ? L.k1 : L.k0, leaves, nleaves, c, L.np, L.order,
                                                          L.nit, L.npc, L.tot);
     note_launch();
