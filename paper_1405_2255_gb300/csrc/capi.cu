@@ -79,7 +79,8 @@ struct fmm_ctx {
     // walk
     Buf walkf;  // single-precision view of the cells for the walk's acceptance test
     Buf units;  // int[2]: the working units of the tree in use (launch_work_units)
-    Buf front0, front1, m2l, p2p, sort_tmp, m2l_tmp, p2p_tmp, seg_start, seg_end, est_m2l, est_p2p, m2l_seg_start, m2l_seg_end;
+    Buf front0, front1, m2l, p2p, sort_tmp, sort_tmp2, m2l_tmp, p2p_tmp, seg_start, seg_end, est_m2l, est_p2p,
+        m2l_seg_start, m2l_seg_end;
     long long front_cap = 0, m2l_cap = 0, p2p_cap = 0, est_m2l_cap = 0, est_p2p_cap = 0;
     // per particle results (sorted order)
     Buf psi_far, acc_far, psi_near, acc_near, scale_sorted;
@@ -93,6 +94,9 @@ struct fmm_ctx {
     // on the second.  Events fork them from and join them to the caller's stream.
     cudaStream_t s2 = nullptr, s_hi = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_est = nullptr;
+    // a third stream (highest priority): the estimate's M2L branch beside its P2P branch
+    cudaStream_t s3 = nullptr;
+    cudaEvent_t ev_est_fork = nullptr, ev_est_m2l = nullptr, ev_join3 = nullptr;
     bool timed = false;  // the events of the last evaluation were recorded
     bool marked_m2l = false, marked_p2p = false;  // ... and those around its main kernels
     gb3::Serve* serve = nullptr;  // the serving loop (serve.cu), created on first use
@@ -112,7 +116,7 @@ struct fmm_ctx {
                 &idx_alt, &rtmp, &xm, &perm, &xp, &first, &count, &child, &nchild, &parent, &level, &sr,
                 &cr, &mass, &minscale, &split_nchild, &split_oct, &split_offs, &scan_tmp, &leaves, &leaf_flag,
                 &leaf_pos, &rad_tmp, &M, &F, &Pw, &binom, &pascal, &M1, &F1, &Ff, &front0, &front1, &m2l, &p2p,
-                &sort_tmp, &m2l_tmp, &p2p_tmp, &seg_start, &seg_end, &est_m2l, &est_p2p, &m2l_seg_start,
+                &sort_tmp, &sort_tmp2, &m2l_tmp, &p2p_tmp, &seg_start, &seg_end, &est_m2l, &est_p2p, &m2l_seg_start,
                 &m2l_seg_end, &psi_far, &acc_far, &psi_near, &acc_near, &scale_sorted, &sys_off, &sys_G,
                 &sys_roots, &skey, &skey_alt, &spos, &spos_alt, &pact, &act, &act_i, &act_scan, &tid_far, &tid_near, &walkf, &owner, &units};
     }
@@ -410,11 +414,12 @@ static int run_walk(fmm_ctx* ctx, WalkParams wp, Buf& m2l, long long& m2l_cap, B
 }
 
 static int sort_and_segment(fmm_ctx* ctx, Buf& list, long long npairs, Buf& seg_start, Buf& seg_end,
-                            cudaStream_t s, bool wide = false) {
-    TRY(ensure(ctx->sort_tmp, list_sort_tmp_bytes(npairs, ctx->ncells)));
+                            cudaStream_t s, bool wide = false, Buf* tmp = nullptr) {
+    Buf& st = tmp ? *tmp : ctx->sort_tmp;
+    TRY(ensure(st, list_sort_tmp_bytes(npairs, ctx->ncells)));
     TRY(ensure(seg_start, sizeof(int) * ctx->ncells));
     TRY(ensure(seg_end, sizeof(int) * ctx->ncells));
-    sort_pairs_by_sink(P<int2>(list), npairs, ctx->ncells, ctx->sort_tmp.p, s, wide);
+    sort_pairs_by_sink(P<int2>(list), npairs, ctx->ncells, st.p, s, wide);
     launch_segments(P<int2>(list), npairs, ctx->ncells, P<int>(seg_start), P<int>(seg_end), s);
     return 0;
 }
@@ -453,7 +458,24 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
     launch_walk_prep(c, c.cr, nullptr, 0, 0.0, nc, P<float4>(ctx->walkf), nullptr, s);
     TRY(run_walk(ctx, wp, ctx->est_m2l, ctx->est_m2l_cap, ctx->est_p2p, ctx->est_p2p_cap, &ctx->n_est_m2l,
                  &ctx->n_est_p2p, s));
-    TRY(sort_and_segment(ctx, ctx->est_m2l, ctx->n_est_m2l, ctx->m2l_seg_start, ctx->m2l_seg_end, s));
+    // the M2L branch (list sort, M2L) on the third stream beside the P2P branch on s; both
+    // meet before the scale
+    const int pe = 1, nco = ncoef(pe);
+    if (!want_f) TRY(ensure(ctx->F1, sizeof(double) * nco * (size_t)nc));
+    const bool mixed = ctx->prm.precision == FMM_PREC_MIXED;
+    cudaStream_t sm = want_f ? s : ctx->s3;
+    if (!want_f) {
+        CU(cudaEventRecord(ctx->ev_est_fork, s));
+        CU(cudaStreamWaitEvent(sm, ctx->ev_est_fork, 0));
+    }
+    TRY(sort_and_segment(ctx, ctx->est_m2l, ctx->n_est_m2l, ctx->m2l_seg_start, ctx->m2l_seg_end, sm, false,
+                         &ctx->sort_tmp2));
+    if (!want_f) {
+        // multipoles about the centres of mass: the masses and centres of the geometry pass
+        launch_est_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), nc, c,
+                       P<double>(ctx->F1), sm, mixed ? P<float4>(ctx->walkf) : nullptr);
+        CU(cudaEventRecord(ctx->ev_est_m2l, sm));
+    }
     // P2P segments of the estimate reuse seg_start/seg_end of the main lists (written later)
     TRY(ensure(ctx->seg_start, sizeof(int) * nc));
     TRY(ensure(ctx->seg_end, sizeof(int) * nc));
@@ -470,18 +492,13 @@ static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
                      P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->Ff), scale, s);
         return 0;
     }
-    const int pe = 1, nco = ncoef(pe);
-    TRY(ensure(ctx->F1, sizeof(double) * nco * (size_t)nc));
-    // multipoles about the centres of mass: the masses and centres of the geometry pass
-    const bool mixed = ctx->prm.precision == FMM_PREC_MIXED;
-    launch_est_m2l(P<int2>(ctx->est_m2l), P<int>(ctx->m2l_seg_start), P<int>(ctx->m2l_seg_end), nc, c,
-                   P<double>(ctx->F1), s, mixed ? P<float4>(ctx->walkf) : nullptr);
     // (the p = 1 L2L is folded into launch_est_scale)
     if (mixed)
         TRY(run_p2p_mixed(ctx, P<int2>(ctx->est_p2p), 0, s));
     else
         launch_p2p_fp64(P<d4>(ctx->xm), c, P<int2>(ctx->est_p2p), P<int>(ctx->seg_start), P<int>(ctx->seg_end),
                         P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->psi_near), P<double>(ctx->acc_near), s);
+    CU(cudaStreamWaitEvent(s, ctx->ev_est_m2l, 0));
     launch_est_scale(c, P<int>(ctx->leaves), ctx->nleaves, P<double>(ctx->F1), P<double>(ctx->acc_near), scale, s);
     return 0;
 }
@@ -610,15 +627,17 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     }
     // every exit from here on (errors included) leaves s behind all the work of both streams
     struct Join {
-        cudaStream_t s, s2, se;
-        cudaEvent_t e, ee;
+        cudaStream_t s, s2, se, s3;
+        cudaEvent_t e, ee, e3;
         ~Join() {
             cudaEventRecord(e, s2);
             cudaEventRecord(ee, se);
+            cudaEventRecord(e3, s3);
             cudaStreamWaitEvent(s, e, 0);
             cudaStreamWaitEvent(s, ee, 0);
+            cudaStreamWaitEvent(s, e3, 0);
         }
-    } join{s, ctx->s2, ctx->s_hi, ctx->ev_join, ctx->ev_join_est};
+    } join{s, ctx->s2, ctx->s_hi, ctx->s3, ctx->ev_join, ctx->ev_join_est, ctx->ev_join3};
 
     // A7: acceleration scale for the MAC and its per-cell minimum, on its own stream
     {
@@ -849,7 +868,11 @@ int fmm_create(fmm_ctx** out, const fmm_params* params, int device) {
                 cudaStreamCreateWithPriority(&ctx->s_hi, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
                 cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&ctx->ev_join_est, cudaEventDisableTiming) != cudaSuccess))
+                cudaEventCreateWithFlags(&ctx->ev_join_est, cudaEventDisableTiming) != cudaSuccess ||
+                cudaStreamCreateWithPriority(&ctx->s3, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->ev_est_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->ev_est_m2l, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->ev_join3, cudaEventDisableTiming) != cudaSuccess))
         rc = FMM_E_CUDA;
     if (rc) {
         cudaGetLastError();
@@ -1119,11 +1142,16 @@ int fmm_destroy(fmm_ctx* ctx) {
         for (int i = 0; i < EV_N; ++i) cudaEventDestroy(ctx->ev[i]);
     if (ctx->s2) cudaStreamSynchronize(ctx->s2);
     if (ctx->s_hi) cudaStreamSynchronize(ctx->s_hi);
+    if (ctx->s3) cudaStreamSynchronize(ctx->s3);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->ev_join_est) cudaEventDestroy(ctx->ev_join_est);
+    if (ctx->ev_est_fork) cudaEventDestroy(ctx->ev_est_fork);
+    if (ctx->ev_est_m2l) cudaEventDestroy(ctx->ev_est_m2l);
+    if (ctx->ev_join3) cudaEventDestroy(ctx->ev_join3);
     if (ctx->s2) cudaStreamDestroy(ctx->s2);
     if (ctx->s_hi) cudaStreamDestroy(ctx->s_hi);
+    if (ctx->s3) cudaStreamDestroy(ctx->s3);
     delete ctx;
     return 0;
 }
