@@ -27,9 +27,10 @@
  *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Device
  *     calls are asynchronous with respect to the host unless stated otherwise;
  *     inputs must stay valid until the stream has reached the call's end.  An
- *     evaluation forks independent parts of its work onto two streams of the
- *     context (the upward pass beside the scale estimate, later the P2P beside the
- *     M2L and downward pass) and joins them back into `stream` with events before
+ *     evaluation forks independent parts of its work onto three streams of the
+ *     context (the upward pass beside the scale estimate, whose own M2L and P2P
+ *     branches run side by side; later the P2P beside the M2L and downward pass)
+ *     and joins them back into `stream` with events before
  *     it goes on, so everything the call does is ordered before work queued later
  *     on `stream`.
  *   - A context is not thread-safe: one host thread at a time per context.
