@@ -16,7 +16,8 @@ __global__ void k_bounds_init(unsigned long long* b) {
     else if (i < 7) b[i] = 0ull;  // [6]: the largest mass
 }
 
-__global__ void k_bounds(const double* __restrict__ x, const double* __restrict__ mu, int n,
+constexpr int kBoundsThreads = 256;
+__global__ void __launch_bounds__(kBoundsThreads) k_bounds(const double* __restrict__ x, const double* __restrict__ mu, int n,
                          unsigned long long* bounds, unsigned* status) {
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     double mmax = 0.0;
@@ -38,23 +39,45 @@ __global__ void k_bounds(const double* __restrict__ x, const double* __restrict_
         hi[d] = warp_max(hi[d]);
     }
     mmax = warp_max(mmax);
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatInvalid);
-    if ((threadIdx.x & 31) == 0) {
+    // then over the block's warps, so that each block (not each warp) does the atomics
+    __shared__ double sv[kBoundsThreads / 32][7];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool bbad = __syncthreads_or(bad);
+    if (lane == 0) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            if (lo[d] <= hi[d]) {
-                atomicMin(&bounds[d], dbl_key(lo[d]));
-                atomicMax(&bounds[3 + d], dbl_key(hi[d]));
-            }
+            sv[w][d] = lo[d];
+            sv[w][3 + d] = hi[d];
         }
-        if (mmax > 0.0 && isfinite(mmax)) atomicMax(&bounds[6], dbl_key(mmax));
+        sv[w][6] = mmax;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = warp_min(lane < nw ? sv[lane][d] : (double)INFINITY);
+            hi[d] = warp_max(lane < nw ? sv[lane][3 + d] : -(double)INFINITY);
+        }
+        mmax = warp_max(lane < nw ? sv[lane][6] : 0.0);
+        if (lane == 0) {
+            if (bbad) atomicOr(status, kStatInvalid);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (lo[d] <= hi[d]) {
+                    atomicMin(&bounds[d], dbl_key(lo[d]));
+                    atomicMax(&bounds[3 + d], dbl_key(hi[d]));
+                }
+            }
+            if (mmax > 0.0 && isfinite(mmax)) atomicMax(&bounds[6], dbl_key(mmax));
+        }
     }
 }
 
 void launch_bounds(const double* x, const double* mu, int n, unsigned long long* bounds, unsigned* status,
                    cudaStream_t s) {
     k_bounds_init<<<1, 32, 0, s>>>(bounds); note_launch();
-    if (n > 0) k_bounds<<<grid_for(n, 256, 8), 256, 0, s>>>(x, mu, n, bounds, status); note_launch();
+    if (n > 0) k_bounds<<<grid_for(n, kBoundsThreads, 8), kBoundsThreads, 0, s>>>(x, mu, n, bounds, status); note_launch();
 }
 
 // ------------------------------------------------------------------ A2 keys
@@ -1114,9 +1137,12 @@ __device__ inline void dist_bounds_f(const float4* __restrict__ xp, int i, const
     ub = df * (1.0f + 0x1p-20f) + E;
 }
 
-__global__ void k_internal_radii_lb(const float4* __restrict__ xp, int n, Cells c,
+constexpr int kRadThreads = 256;
+__global__ void __launch_bounds__(kRadThreads) k_internal_radii_lb(const float4* __restrict__ xp, int n, Cells c,
                                     int lev_begin, int lev_end, int* __restrict__ owner,
                                     unsigned long long* __restrict__ tmp) {
+    __shared__ int s_cell;
+    __shared__ float s_l[kRadThreads / 32][2];
     const RadTmp R(tmp, lev_end - lev_begin);
     const int L = c.level[lev_begin];
     const int pbeg = c.first[lev_begin];
@@ -1136,11 +1162,33 @@ __global__ void k_internal_radii_lb(const float4* __restrict__ xp, int n, Cells 
         }
         // non-negative floats order as their bit patterns
         const int c0 = __shfl_sync(0xffffffffu, cell, 0);
-        if (__all_sync(0xffffffffu, cell == c0)) {
+        const bool wsame = __all_sync(0xffffffffu, cell == c0);
+        if (wsame) {
             for (int o = 16; o > 0; o >>= 1) {
                 l0 = fmaxf(l0, __shfl_xor_sync(0xffffffffu, l0, o));
                 l1 = fmaxf(l1, __shfl_xor_sync(0xffffffffu, l1, o));
             }
+        }
+        // near the root every particle of a block shares its cell: one atomic per block
+        // (the max does not depend on the order it is taken in)
+        if (threadIdx.x == 0) s_cell = cell;
+        __syncthreads();
+        if (__syncthreads_and(wsame && c0 == s_cell)) {
+            if ((threadIdx.x & 31) == 0) {
+                s_l[threadIdx.x >> 5][0] = l0;
+                s_l[threadIdx.x >> 5][1] = l1;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && cell >= 0) {
+                for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+                    l0 = fmaxf(l0, s_l[k][0]);
+                    l1 = fmaxf(l1, s_l[k][1]);
+                }
+                atomicMax((int*)&R.lb[2 * (cell - lev_begin)], __float_as_int(l0));
+                atomicMax((int*)&R.lb[2 * (cell - lev_begin) + 1], __float_as_int(l1));
+            }
+            __syncthreads();
+        } else if (wsame) {
             if ((threadIdx.x & 31) == 0 && c0 >= 0) {
                 atomicMax((int*)&R.lb[2 * (c0 - lev_begin)], __float_as_int(l0));
                 atomicMax((int*)&R.lb[2 * (c0 - lev_begin) + 1], __float_as_int(l1));
@@ -1227,7 +1275,7 @@ void launch_internal_geometry(const d4* xm, const float4* xp, Cells c, int lev_b
     if (keep_centre) k_internal_keep<<<(ncl + 127) / 128, 128, 0, s>>>(c, lev_begin, lev_end, rad_tmp);
     else k_internal_meb<<<(unsigned)ncl, kMebWarps * 32, 0, s>>>(c, lev_begin, lev_end, status, rad_tmp);
     note_launch();
-    k_internal_radii_lb<<<grid_for(n, 256, 16), 256, 0, s>>>(xp, n, c, lev_begin, lev_end, owner,
+    k_internal_radii_lb<<<grid_for(n, kRadThreads, 16), kRadThreads, 0, s>>>(xp, n, c, lev_begin, lev_end, owner,
                                                                      rad_tmp);
     note_launch();
     k_internal_radii<<<grid_for(n, 256, 16), 256, 0, s>>>(xm, xp, n, c, lev_begin, lev_end, owner,
