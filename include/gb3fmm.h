@@ -115,7 +115,7 @@ typedef struct {
     double  eps;
     int     leaf_size;
     /* device time per phase in milliseconds (CUDA events).  Two pairs of phases run side by
-       side on two streams of the context: t_estimate and t_up both start at the end of the tree
+       side on the context's streams: t_estimate and t_up both start at the end of the tree
        phase; t_walk starts once both are done; t_m2l and t_p2p both start at the end of the
        walk, t_down where t_m2l ends (on the M2L's stream); t_total spans the whole evaluation
        (the phases overlap, so they add up to more than it). */

@@ -88,13 +88,13 @@ struct fmm_ctx {
     int* h_int = nullptr;                      // pinned
     cudaEvent_t ev[EV_N];
     bool ev_ok = false;
-    // two streams of the context, lowest and highest priority: the upward pass runs on the first
-    // beside the scale estimate on the second (the longer branch, which waits on the host
-    // between its kernels); later the P2P runs on the first beside the M2L and the downward pass
-    // on the second.  Events fork them from and join them to the caller's stream.
+    // three streams of the context: s2 (lowest priority) and s_hi, s3 (highest).  The upward
+    // pass runs on s2 beside the scale estimate on s_hi (which waits on the host between its
+    // kernels), whose M2L branch (list sort, M2L) runs on s3 beside its P2P branch; later the
+    // P2P runs on s2 beside the M2L and the downward pass on s_hi.  Events fork them from and
+    // join them to the caller's stream.
     cudaStream_t s2 = nullptr, s_hi = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_est = nullptr;
-    // a third stream (highest priority): the estimate's M2L branch beside its P2P branch
     cudaStream_t s3 = nullptr;
     cudaEvent_t ev_est_fork = nullptr, ev_est_m2l = nullptr, ev_join3 = nullptr;
     bool timed = false;  // the events of the last evaluation were recorded
@@ -598,8 +598,8 @@ static int evaluate_device(fmm_ctx* ctx, int n, const double* x, const double* m
     // (the two-float positions were made with the tree)
 
     // A5-A6 (upward pass) and A7 (scale estimate) are independent: the upward pass is
-    // queued on the context's second stream, then the estimate, which waits on the host for
-    // its list sizes, runs on s; s waits for the upward pass before the walk
+    // queued on s2, then the estimate, which waits on the host for its list sizes, runs on
+    // s_hi (and s3); s waits for both before the walk
     TRY(ensure(ctx->M, sizeof(double) * nco * (size_t)nc));
     TRY(ensure(ctx->F, sizeof(double) * nco * (size_t)nc));
     TRY(ensure(ctx->Pw, sizeof(double) * (prm.p + 1) * (size_t)nc));
