@@ -600,8 +600,9 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     int* v0 = (int*)(k1 + ncells);
     int* v1 = v0 + ncells;
     int* order = v1 + ncells;
-    unsigned* work = (unsigned*)(order + ncells);  // [0] item counter, [1] sinks, [2] items
-    int* rtmp = (int*)(work + 4);
+    // [0] item counter, [1] sinks, [2] items, [3]-[5] the rotated M2L's units (launch_m2l_rot)
+    unsigned* work = (unsigned*)(order + ncells);
+    int* rtmp = (int*)(work + 8);
     unsigned char* after = (unsigned char*)(rtmp + radix_tmp_ints(ncells));
     float2* Mf = (float2*)(((uintptr_t)after + 255) & ~(uintptr_t)255);
     cd* M64 = (cd*)(((uintptr_t)(Mf + (size_t)ncells * ncoef(p)) + 255) & ~(uintptr_t)255);
@@ -613,7 +614,7 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
     void* gtmp = (void*)(((uintptr_t)(part + (size_t)items_cap * ncoef(p)) + 255) & ~(uintptr_t)255);
     const int* item_q = nullptr;
     bool single = false;
-    cudaMemsetAsync(work, 0, 4 * sizeof(unsigned), s);
+    cudaMemsetAsync(work, 0, 8 * sizeof(unsigned), s);
     k_sink_keys<<<grid_for(ncells, 256), 256, 0, s>>>(seg_start, seg_end, ncells, k0, v0); note_launch();
     // the low 32 bits are the sink's index, already in order: the stable pass over the 8
     // length bits alone keeps ties in index order

@@ -184,12 +184,19 @@ void launch_m2l_split(const int2* list, const int* seg_start, const int* seg_end
 // M2L pairs per work item of the mixed-mode M2L: each sink's list is cut into chunks of
 // this many pairs from its start, summed separately and then added in chunk order
 constexpr int kM2LChunk = 32;
+// items per piece of a long sink in the rotated M2L without the adaptive order: a sink of more
+// items is cut into pieces of this many, summed separately and then added in piece order (a
+// constant, so that a sink is summed the same way whatever else is in the list)
+constexpr int kM2LPieceItems = 8;
 constexpr int kRotMaxP = 16;  // largest order with a rotation-accelerated M2L
 bool m2l_rot_supported(int p);
 // sinks in `order` (work[1] of them, cnt[i] items of sink position i from item_start[i]);
 // Mt (ncells x (p+1)^2 floats) and M64 (ncells x 9) are scratch.  Without adaptive, every
-// warp takes whole sinks (work[3] the sink counter) and writes each sink's F once; nothing
-// is left to reduce.  adaptive: the items are grouped by the largest order of their pairs and
+// warp takes whole sinks, or pieces of kM2LPieceItems items of the longer sinks (work[3] the
+// counter of these units, work[4] their number, work[5] the number of cut sinks; the unit
+// list in gtmp), and writes a whole sink's F once; a piece writes its partial expansion to the
+// part slot of its first item, and the pieces of each cut sink are then added into F in piece
+// order.  adaptive: the items are grouped by the largest order of their pairs and
 // each group runs the kernel of that order (gtmp: m2l_rot_group_bytes(items_cap) bytes; work[0]
 // the item counter, work[2] the number of items); part receives one expansion per item, except
 // that a sink whose list is a single item has its expansion written to F (zeroed beforehand)

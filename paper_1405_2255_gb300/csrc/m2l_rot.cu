@@ -98,6 +98,39 @@ __global__ void k_item_groups(const unsigned* __restrict__ qcount, unsigned* __r
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < nitems; k += gridDim.x * blockDim.x)
         ilist[k] = (int)(keys[k] & 0xffffffffu);
 }
+
+// by-sink units: the number of pieces of sorted sink i (0 past the sinks with a list)
+__global__ void k_piece_counts(const int* __restrict__ cnt, const unsigned* __restrict__ nsinks, int ncells,
+                               int* __restrict__ npc) {
+    const int ns = (int)*nsinks;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += gridDim.x * blockDim.x)
+        npc[i] = i < ns ? (cnt[i] + kM2LPieceItems - 1) / kM2LPieceItems : 0;
+}
+// units[pstart[i] + k] = (i, k) in sorted-sink order; the sinks of two or more pieces are
+// listed in splits (in any order: each is summed on its own)
+__global__ void k_units(const int* __restrict__ npc, const int* __restrict__ pstart, int ncells,
+                        int2* __restrict__ units, int* __restrict__ splits, unsigned* __restrict__ nsplit) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += gridDim.x * blockDim.x) {
+        const int np = npc[i];
+        for (int k = 0; k < np; ++k) units[pstart[i] + k] = make_int2(i, k);
+        if (np > 1) splits[atomicAdd(nsplit, 1u)] = i;
+    }
+}
+// F of a cut sink = its pieces' partial expansions added in piece order
+__global__ void k_piece_reduce(const int* __restrict__ order, const int* __restrict__ item_start,
+                               const int* __restrict__ cnt, const int* __restrict__ splits,
+                               const unsigned* __restrict__ nsplit, int nco, const double* __restrict__ part,
+                               double* __restrict__ F) {
+    const long long total = (long long)*nsplit * nco;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = splits[t / nco], j = (int)(t % nco);
+        const int a = item_start[i], c = cnt[i];
+        double v = 0.0;
+        for (int k = 0; k < c; k += kM2LPieceItems) v += part[(size_t)(a + k) * nco + j];
+        F[(size_t)order[i] * nco + j] = v;
+    }
+}
 }  // namespace
 
 size_t m2l_rot_group_bytes(long long items_cap) {
@@ -116,9 +149,11 @@ const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg
 #define GB3_ROT(PP)                                                                                      \
     case PP:                                                                                             \
         rot_launch<PP>(RotArgs{list, seg_start, seg_end, order, item_start, work, cen, Mt, M64, part, F, il,  \
-                               go, gq, ctr, nco, adapt, by_sink ? cnt : nullptr, by_sink ? work + 3 : nullptr}, \
+                               go, gq, ctr, nco, adapt, by_sink ? cnt : nullptr, by_sink ? work + 3 : nullptr,  \
+                               units, work + 4},                                                         \
                        s);                                                                               \
         break;
+    const int2* units = nullptr;
     auto launch_p = [&](int q, const int* il, const unsigned* go, int gq, unsigned* ctr, int adapt, bool by_sink) {
         switch (q) {
             GB3_ROT(3) GB3_ROT(4) GB3_ROT(5) GB3_ROT(6) GB3_ROT(7) GB3_ROT(8) GB3_ROT(9) GB3_ROT(10) GB3_ROT(11)
@@ -128,11 +163,27 @@ const int* launch_m2l_rot(const int2* list, const int* seg_start, const int* seg
     };
 #undef GB3_ROT
     if (!adaptive) {
-        // every pair at p: whole sinks, counted by work[3] (the sink count is on the device,
-        // work[1]); F is written once per sink and needs no reduction
+        // every pair at p: units of whole sinks and of pieces of the longer ones (the sink
+        // count is on the device, work[1]), taken through work[3]; a whole sink's F is written
+        // once by the kernel, the cut sinks' pieces are added after it.  gtmp holds the units
+        // (at most one per item), the piece counts and starts, the cut sinks and scan scratch.
+        const size_t cap = (size_t)(items_cap > 0 ? items_cap : 1);
+        int2* u = (int2*)gtmp;
+        int* npc = (int*)(u + cap);
+        int* pstart = npc + ncells;
+        int* splits = pstart + ncells;
+        int* stmp = splits + ncells;
+        k_piece_counts<<<grid_for(ncells, 256), 256, 0, s>>>(cnt, work + 1, ncells, npc);
+        note_launch();
+        scan_exclusive_i32(npc, pstart, ncells, (int*)(work + 4), stmp, s);
+        k_units<<<grid_for(ncells, 256), 256, 0, s>>>(npc, pstart, ncells, u, splits, work + 5);
+        note_launch();
+        units = u;
         mark_begin(s);
         launch_p(p, nullptr, nullptr, 0, work, 0, true);
         mark_end(s);
+        k_piece_reduce<<<sm_count() * 8, 256, 0, s>>>(order, item_start, cnt, splits, work + 5, nco, part, F);
+        note_launch();
         return nullptr;
     }
     // group the items by the largest order of their pairs; each group runs its own kernel

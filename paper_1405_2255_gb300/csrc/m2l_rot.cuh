@@ -64,10 +64,13 @@ struct RotArgs {
     unsigned* counter;
     int nco_out;
     int adapt;
-    // by-sink mode (ilist == nullptr and cnt != nullptr): every warp takes whole sinks from
-    // *sink_counter (positions of the sorted order, cnt[i] items each) and writes F once per sink
+    // by-sink mode (ilist == nullptr and cnt != nullptr): every warp takes units from
+    // *sink_counter: units[u] = (position i of the sorted order, piece k); sink i has cnt[i]
+    // items, and a sink of more than kM2LPieceItems items is cut into pieces of that many
     const int* cnt;
     unsigned* sink_counter;
+    const int2* units;
+    const unsigned* nunits;
 };
 
 namespace {
@@ -345,9 +348,11 @@ constexpr int rot_warps() {
 }
 
 // One warp per work item: up to kM2LChunk pairs of one sink, lane = pair.  By sink (cnt !=
-// nullptr, every pair at p): a warp takes a whole sink from *sink_counter (longest lists first)
-// and its items one after the other, adds their expansions in item order into its
-// shared-memory accumulator and writes F + B * nco_out once.  By item (the adaptive walk's
+// nullptr, every pair at p): a warp takes a unit from *sink_counter (longest lists first) --
+// a whole sink, or a piece of kM2LPieceItems items of a longer one -- and its items one after
+// the other, adds their expansions in item order into its shared-memory accumulator and writes
+// it once: to F + B * nco_out for a whole sink, to the part slot of the piece's first item for
+// a piece.  By item (the adaptive walk's
 // groups): the items are ilist[goff[gq] .. goff[gq + 1]) taken from *counter; item w's partial
 // expansion goes to part + w * nco_out, nco_out = (p+1)^2 of the global order p >= P, which is
 // also the row length of Mt (a sink whose whole list is one item has its expansion written to F
@@ -381,8 +386,10 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1) k_m2l_rot(const RotArg
     const unsigned nsinks = work[1];
     const unsigned lbase = ilist ? goff[gq] : 0u, nlist = ilist ? goff[gq + 1] - goff[gq] : work[2];
     const bool by_sink = !ilist && args.cnt;
-    int cur = -1, cur_it = 0, cur_end = 0;  // by sink: the warp's sink position and item cursor
-    bool done = false;
+    // by sink: the warp's sink position, item cursor and end, and where its sum goes
+    int cur = -1, cur_it = 0, cur_end = 0, cur_first = 0;
+    bool cur_piece = false, done = false;
+    const unsigned nunits = by_sink ? *args.nunits : 0u;
     for (;;) {
         bool has;
         unsigned w;
@@ -391,20 +398,25 @@ __global__ void __launch_bounds__(32 * rot_warps<P>(), 1) k_m2l_rot(const RotArg
             // the warp's sink is used up: write its expansion, take the next sink
             while (!done && cur_it >= cur_end) {
                 if (cur >= 0) {
-                    double* o = args.F + (size_t)order[cur] * nco_out;
+                    double* o = cur_piece ? args.part + (size_t)cur_first * nco_out
+                                          : args.F + (size_t)order[cur] * nco_out;
                     for (int c = lane; c < NCO; c += 32) o[c] = accF[c];
                 }
                 unsigned nx = 0;
                 if (lane == 0) nx = atomicAdd(args.sink_counter, 1u);
                 nx = __shfl_sync(0xffffffffu, nx, 0);
-                if (nx >= nsinks) {
+                if (nx >= nunits) {
                     done = true;
                     cur = -1;
                     break;
                 }
-                cur = (int)nx;
-                cur_it = item_start[cur];
-                cur_end = cur_it + args.cnt[cur];
+                const int2 un = args.units[nx];
+                cur = un.x;
+                const int c0 = item_start[cur], nit = args.cnt[cur];
+                cur_it = c0 + un.y * kM2LPieceItems;
+                cur_end = min(cur_it + kM2LPieceItems, c0 + nit);
+                cur_first = cur_it;
+                cur_piece = nit > kM2LPieceItems;
                 for (int c = lane; c < NCO; c += 32) accF[c] = 0.0;
                 __syncwarp();
             }
