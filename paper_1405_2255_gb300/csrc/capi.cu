@@ -443,7 +443,7 @@ static int run_p2p_mixed(fmm_ctx* ctx, const int2* list, int mode, cudaStream_t 
 
 // ------------------------------------------------------------------ the low-order scale (A7)
 static int estimate_scale(fmm_ctx* ctx, cudaStream_t s) {
-    const int n = ctx->n, nc = ctx->ncells;
+    const int nc = ctx->ncells;
     Cells c = cells_of(ctx);
     const bool want_f = ctx->prm.mac == FMM_MAC_F;
     const int nlev = (int)ctx->lev_start.size() - 1;

@@ -756,7 +756,6 @@ void launch_l2p(const d4* xm, Cells c, const d4* cen, const int* leaves, int nle
 // internal covers every leaf below B); they pass through a warp-private tile of
 // 32 in shared memory.
 constexpr int kP2PWarps = 4;
-constexpr int kP2PTile = 128;  // sources per staged tile at the largest replica count (4 x 32)
 
 __global__ void __launch_bounds__(kP2PWarps * 32) k_p2p_fp64(const d4* __restrict__ xm, Cells c,
                                                              const int2* __restrict__ list,
